@@ -1,0 +1,67 @@
+"""Limb-darkening profiles and the stellar disk integral (Sect. 3.2; Eq. 2-4).
+
+Each law gives the surface brightness I(mu), mu = sqrt(1 - z^2) in [0, 1].
+The normalisation I_star = 2 pi int_0^1 z I(z) dz (Eq. 2 and 4) equals
+2 pi int_0^1 mu I(mu) dmu.  Named laws are integrated in closed form
+(Sect. 3.2.1 says the named models are integrated analytically); the
+tabulated profile (the "custom" profile of Sect. 3.2.2, sampled on a
+mu grid) is linearly interpolated, held constant outside the table, and
+its I_star is the exact integral of that piecewise-linear function.
+
+Laws (coefficients per passband):
+  uniform        I = 1
+  quadratic      I = 1 - u1 (1 - mu) - u2 (1 - mu)^2
+  quadratic_tri  quadratic with u1 = 2 sqrt(q1) q2, u2 = sqrt(q1) (1 - 2 q2)
+                 (Kipping's triangular parametrisation, footnote of Sect. 3.2.1)
+  nonlinear      I = 1 - sum_{n=1..4} c_n (1 - mu^(n/2))
+"""
+import numpy as np
+
+NCOEF = {"uniform": 0, "quadratic": 2, "quadratic_tri": 2, "nonlinear": 4, "tabulated": 0}
+
+
+def kipping_to_quadratic(q1, q2):
+    sq = np.sqrt(q1)
+    return 2.0 * sq * q2, sq * (1.0 - 2.0 * q2)
+
+
+def profile(model: str, mu, coef=(), table=None):
+    """I(mu) for the named law (coefficients ``coef``) or the tabulated profile ``table``."""
+    mu = np.asarray(mu, np.float64)
+    if model == "uniform":
+        return np.ones_like(mu)
+    if model == "quadratic":
+        u1, u2 = coef
+        return 1.0 - u1 * (1.0 - mu) - u2 * (1.0 - mu) ** 2
+    if model == "quadratic_tri":
+        u1, u2 = kipping_to_quadratic(*coef)
+        return 1.0 - u1 * (1.0 - mu) - u2 * (1.0 - mu) ** 2
+    if model == "nonlinear":
+        c1, c2, c3, c4 = coef
+        return (1.0 - c1 * (1.0 - mu ** 0.5) - c2 * (1.0 - mu) - c3 * (1.0 - mu ** 1.5)
+                - c4 * (1.0 - mu ** 2))
+    if model == "tabulated":
+        tmu, tI = table
+        return np.interp(mu, tmu, tI)
+    raise ValueError(f"unknown LD model {model!r}")
+
+
+def istar(model: str, coef=(), table=None) -> float:
+    """I_star = 2 pi int_0^1 mu I(mu) dmu."""
+    if model == "uniform":
+        return np.pi
+    if model in ("quadratic", "quadratic_tri"):
+        u1, u2 = coef if model == "quadratic" else kipping_to_quadratic(*coef)
+        return np.pi * (1.0 - u1 / 3.0 - u2 / 6.0)
+    if model == "nonlinear":
+        c1, c2, c3, c4 = coef
+        return np.pi * (1.0 - c1 / 5.0 - c2 / 3.0 - 3.0 * c3 / 7.0 - c4 / 2.0)
+    if model == "tabulated":
+        tmu, tI = (np.asarray(x, np.float64) for x in table)
+        # constant below the first and above the last node
+        s = 0.5 * tI[0] * tmu[0] ** 2 + 0.5 * tI[-1] * (1.0 - tmu[-1] ** 2)
+        # int_{m0}^{m1} mu (linear I) dmu = h/6 [I0 (2 m0 + m1) + I1 (m0 + 2 m1)]
+        m0, m1, i0, i1 = tmu[:-1], tmu[1:], tI[:-1], tI[1:]
+        s += np.sum((m1 - m0) / 6.0 * (i0 * (2.0 * m0 + m1) + i1 * (m0 + 2.0 * m1)))
+        return 2.0 * np.pi * s
+    raise ValueError(f"unknown LD model {model!r}")

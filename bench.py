@@ -1,0 +1,404 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the GB300 RoadRunner light-curve path.
+
+One step = one pass of the hot path over one batch: rr_evaluate (per-pv
+set-up, fused flux + supersample kernel) and, for the population workload,
+rr_evaluate_grad (adjoint with all 9 parameters).  Inputs are resident in
+HBM; L2 is flushed (a 256 MiB write) before every timed step, and every step
+is timed with CUDA events on the launching stream.
+
+Metric: light-curve points/s = npv x npt x supersamples per step / step time,
+summed over ranks (each rank evaluates its own batch: weak scaling).
+
+``--impl reference`` times the FP64 CPU oracle on the host cores instead.
+Multi-GPU: one process per GPU under torchrun; no collective on the data
+path (barrier and a max-reduce of the timings only).
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "light-curve points/s (npv×npt×supersamples) at ≤1 ppm vs FP64 form; p50/p99 latency"
+CONFIG_TEXT = {
+    "c1": "Plain method, FP64: 1 pv, circular, quadratic LD, 2,000 times, no supersampling",
+    "c2": "Single eccentric light curve, FP32 bulk / FP64 phase: nonlinear LD, 19,440 times, ss=10",
+    "c3": "Population batch: 4,096 pvs x 20,000 times, Kipping q1,q2, forward + adjoint w.r.t. 9 parameters",
+    "c4": "Heterogeneous: 8 passbands, tabulated LD, 2,048 pvs x 60,000 mixed-cadence times, ss {1,10,30}",
+}
+# DRAM bytes (read + write) per launch of the flux kernel, from one ncu capture of the
+# same kernel (profiles/flux_mixed_c3_population.md); None until captured for this version
+TRAFFIC = {}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["c1", "c2", "c3", "c4"], default="c3")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def make_workload(name):
+    from paper_2009_08500_gb300 import workloads as W
+    return {"c1": W.make_c1, "c2": W.make_c2, "c3": W.make_c3, "c4": W.make_c4}[name]()
+
+
+def with_grad(name):
+    return name == "c3"
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ----------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu):
+        self.gpu, self.proc, self.path = gpu, None, None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            self.fh = os.fdopen(fd, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def mark(self):
+        return time.time()
+
+    def stop(self, t0, t1):
+        if self.proc is None:
+            return None
+        time.sleep(0.12)
+        self.proc.terminate()
+        self.proc.wait()
+        self.fh.close()
+        rows = []
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    rows.append(parts)
+                except ValueError:
+                    pass
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows),
+                "window": "warm-up and timed steps (50 ms sampling)"}
+
+
+def measured_peak_hbm():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+# ----------------------------------------------------------------- CPU oracle
+_W = {}
+
+
+def _oracle_init(name):
+    os.environ["OMP_NUM_THREADS"] = "1"
+    from oracle import model as om
+    wl = make_workload(name)
+    _W["wl"] = wl
+    _W["setup"] = om.build(wl.grid, wl.ld_model, wl.npb, wl.chromatic, wl.profiles)
+    _W["grad"] = with_grad(name)
+
+
+def _oracle_worker(args):
+    pv_lo, pv_hi, budget_s = args
+    import numpy as np
+    from oracle import grad as og
+    from oracle import model as om
+    wl, s = _W["wl"], _W["setup"]
+    rng = np.random.default_rng(pv_lo)
+    done = 0
+    t0 = time.perf_counter()
+    for p in range(pv_lo, pv_hi):
+        row = wl.params[p:p + 1]
+        om.evaluate(s, wl.times, wl.pb_index, row, wl.supersampling, wl.exptime)
+        if _W["grad"]:
+            og.vjp(s, wl.times, wl.pb_index, row, wl.supersampling, wl.exptime, rng.normal(size=(1, wl.npt)))
+        done += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    return done, time.perf_counter() - t0
+
+
+class OraclePool:
+    """Spawned worker processes (one BLAS thread each), each holding the oracle set-up."""
+
+    def __init__(self, name):
+        import multiprocessing as mp
+        self.name = name
+        self.wl = make_workload(name)
+        self.cores = os.cpu_count() or 1
+        self.pool = mp.get_context("spawn").Pool(self.cores, initializer=_oracle_init, initargs=(name,))
+        self.pool.map(_oracle_worker, [(0, 0, 0.0)] * self.cores)   # wait for every initializer
+
+    def rate(self, budget_s):
+        npv = self.wl.npv
+        per = max(1, math.ceil(npv / self.cores))
+        jobs = [(lo, min(npv, lo + per), budget_s) for lo in range(0, npv, per)]
+        t0 = time.perf_counter()
+        res = self.pool.map(_oracle_worker, jobs)
+        wall = time.perf_counter() - t0
+        done = sum(r[0] for r in res)
+        pts = done * self.wl.samples_per_pv()
+        kind = "forward + adjoint" if with_grad(self.name) else "forward"
+        return {"value": pts / wall, "unit": "points/s", "cores": min(self.cores, len(jobs)), "kind": "oracle",
+                "sample": f"{done} of {npv} pvs x {self.wl.npt} times ({kind}); "
+                          f"{min(self.cores, len(jobs))} processes, <= {budget_s:.2g} s of work each"}
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
+def oracle_rate(name, budget_s=8.0):
+    """Points/s of the FP64 oracle on all host cores (a bounded sample of the workload)."""
+    op = OraclePool(name)
+    try:
+        return op.rate(budget_s)
+    finally:
+        op.close()
+
+
+# ----------------------------------------------------------------- ours
+def run_ours(a):
+    import numpy as np
+    import torch
+
+    from paper_2009_08500_gb300 import rr
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    cpu_base = None
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        cpu_base = oracle_rate(a.workload)     # spawned before any GPU work
+
+    wl = make_workload(a.workload)
+    model = rr.model_for(wl, device=local)
+    t, pb, p = rr.to_device(wl, local)
+    grad = with_grad(a.workload)
+    flux = torch.empty((wl.npv, wl.npt), dtype=model.dtype, device=dev)
+    ws_f = model.workspace(wl.npv, wl.npt, False)
+    if grad:
+        ws_g = model.workspace(wl.npv, wl.npt, True)
+        gbar = torch.randn((wl.npv, wl.npt), dtype=model.dtype, device=dev,
+                           generator=torch.Generator(device=dev).manual_seed(1234))
+        gout = torch.empty((wl.npv, model.nparam), dtype=torch.float64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    ss, ex = wl.supersampling, wl.exptime
+
+    def step():
+        model.evaluate(t, p, pb, ss, ex, out=flux, workspace=ws_f)
+        if grad:
+            model.evaluate_grad(t, p, gbar, pb, ss, ex, out=gout, workspace=ws_g)
+
+    for _ in range(max(a.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.1)
+    model.profile(True)
+    model.profile_read(reset=True)
+    n_launch0 = model.launch_count
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    t0 = time.time()
+    for i in range(a.steps):
+        flush.fill_(i & 0xFF)
+        ev[i][0].record()
+        step()
+        ev[i][1].record()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    t1 = time.time()
+    launches = model.launch_count - n_launch0
+    step_ms = [s.elapsed_time(e) for s, e in ev]
+    kprof = model.profile_read(reset=True)
+    model.profile(False)
+    clk = clocks.stop(t0, t1)
+    tot_ms = sum(step_ms)
+    if world > 1:
+        tt = torch.tensor([tot_ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        tot_ms = float(tt.item())
+    ms_per_step = tot_ms / a.steps
+    pts = wl.npv * wl.samples_per_pv()
+    value = world * pts / (ms_per_step * 1e-3)
+
+    # dominant kernel and its roofline (HBM): algorithmic bytes per launch
+    names = ["flux", "grad"] if grad else ["flux"]
+    dom = max(names, key=lambda k: kprof[k][0])
+    kms, kn = kprof[dom]
+    kavg = kms / max(kn, 1)
+    rec = model.workspace_bytes(wl.npv, wl.npt, dom == "grad")
+    esize = 8 if model.dtype == torch.float64 else 4
+    per_time = 8 + 4                                  # time (FP64) + passband index
+    alg = wl.npv * wl.npt * esize + wl.npt * per_time + rec   # flux written / cotangent read, times, records
+    peak, peak_kind = measured_peak_hbm()
+    achieved = alg / (kavg * 1e-3) / 1e9
+    roof = {"kernel": f"rr_{dom}_{'fp64' if esize == 8 else 'mixed'}_kernel", "bound": "hbm",
+            "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
+            "peak_source": f"{peak_kind} hbm_gbs", "algorithmic_bytes_per_launch": int(alg),
+            "avg_launch_ms": round(kavg, 5), "traffic": TRAFFIC.get((a.workload, dom))}
+    kernels = {k: {"ms_per_launch": round(v[0] / max(v[1], 1), 5), "launches": v[1]} for k, v in kprof.items() if v[1]}
+
+    e2e = None
+    if not a.no_e2e:
+        e2e = run_e2e(a, model, wl, grad, dev)
+        if world > 1:
+            tt = torch.tensor([e2e["_ms"]], dtype=torch.float64, device=dev)
+            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+            e2e["_ms"] = float(tt.item())
+        e2e["value"] = world * pts / (e2e.pop("_ms") * 1e-3)
+
+    srt = sorted(step_ms)
+    line = {
+        "metric": METRIC, "value": value, "unit": "points/s", "n_gpus": world, "steps": a.steps,
+        "warmup": max(a.warmup, 3), "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64" if esize == 4 else "f64", "data": "synthetic (seeded; paper-shaped)",
+        "config": {"workload": f"{a.workload}: {CONFIG_TEXT[a.workload]}", "npv": wl.npv, "npt": wl.npt,
+                   "supersamples_per_pv": wl.samples_per_pv(), "global_batch": world * pts,
+                   "precision": wl.precision, "parallelism": f"replicas x{world} (pv batches, no collective)",
+                   "l2": "flushed (256 MiB write) before every timed step"},
+        "latency_ms": {"p50": srt[len(srt) // 2], "p99": srt[min(len(srt) - 1, int(0.99 * len(srt)))]},
+        "roofline": roof, "kernels": kernels, "cpu_baseline": cpu_base, "e2e": e2e, "clocks": clk,
+        "gpu_launches": launches,
+    }
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def run_e2e(a, model, wl, grad, dev):
+    """Same metric through the public API with host buffers: H2D of the step's inputs
+    from pinned memory, evaluation, D2H of the results, every step."""
+    import torch
+    h_t = torch.as_tensor(wl.times, dtype=torch.float64).pin_memory()
+    h_pb = torch.as_tensor(wl.pb_index, dtype=torch.int32).pin_memory()
+    h_p = torch.as_tensor(wl.params, dtype=torch.float64).pin_memory()
+    h_flux = torch.empty((wl.npv, wl.npt), dtype=model.dtype).pin_memory()
+    bi = h_t.numel() * 8 + h_pb.numel() * 4 + h_p.numel() * 8
+    bo = h_flux.numel() * h_flux.element_size()
+    if grad:
+        h_g = torch.randn((wl.npv, wl.npt), dtype=model.dtype).pin_memory()
+        h_go = torch.empty((wl.npv, model.nparam), dtype=torch.float64).pin_memory()
+        bi += h_g.numel() * h_g.element_size()
+        bo += h_go.numel() * 8
+    ws_f = model.workspace(wl.npv, wl.npt, False)
+    ws_g = model.workspace(wl.npv, wl.npt, True) if grad else None
+
+    def step():
+        t = h_t.to(dev, non_blocking=True)
+        pb = h_pb.to(dev, non_blocking=True)
+        p = h_p.to(dev, non_blocking=True)
+        f = model.evaluate(t, p, pb, wl.supersampling, wl.exptime, workspace=ws_f)
+        h_flux.copy_(f, non_blocking=True)
+        if grad:
+            g = h_g.to(dev, non_blocking=True)
+            go = model.evaluate_grad(t, p, g, pb, wl.supersampling, wl.exptime, workspace=ws_g)
+            h_go.copy_(go, non_blocking=True)
+
+    for _ in range(3):
+        step()
+    torch.cuda.synchronize()
+    n = max(3, min(a.steps, 50))
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s.record()
+    for _ in range(n):
+        step()
+    e.record()
+    torch.cuda.synchronize()
+    return {"_ms": s.elapsed_time(e) / n, "unit": "points/s", "h2d_bytes_per_step": int(bi),
+            "d2h_bytes_per_step": int(bo), "steps": n}
+
+
+# ----------------------------------------------------------------- reference arm
+def run_reference(a):
+    """The FP64 CPU oracle as it stands, on the host cores, same workload and metric."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    op = OraclePool(a.workload)
+    budget = max(0.2, min(2.0, 120.0 / max(1, a.steps + a.warmup)))
+    try:
+        for _ in range(a.warmup):
+            op.rate(budget)
+        steps = [op.rate(budget) for _ in range(a.steps)]
+    finally:
+        op.close()
+    vals = [r["value"] for r in steps]
+    value = statistics.median(vals)
+    wl = op.wl
+    pts = wl.npv * wl.samples_per_pv()
+    cb = dict(steps[-1])
+    cb["value"] = value
+    cb["sample"] = f"per step: {cb['sample']}; value = median over {a.steps} steps"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "points/s", "n_gpus": world,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": pts / value * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded; paper-shaped)",
+            "config": {"workload": f"{a.workload}: {CONFIG_TEXT[a.workload]}", "npv": wl.npv, "npt": wl.npt,
+                       "supersamples_per_pv": wl.samples_per_pv(), "precision": "fp64 (CPU oracle)"},
+            "cpu_baseline": cb,
+            "e2e": {"value": value, "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)
+
+
+if __name__ == "__main__":
+    main()

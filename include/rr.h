@@ -1,0 +1,218 @@
+/*
+ * rr.h -- C ABI of the GB300 (sm_103a) RoadRunner transit light-curve library.
+ *
+ * RoadRunner (Parviainen 2020, MNRAS) evaluates a transit light curve as
+ * Eq. 5:  f = (I_star - (w . l) a(c, k)) / I_star,
+ * where a(c, k) is the area of the stellar disk covered by a planet of
+ * radius ratio k at projected centre distance c, w . l the mean covered
+ * brightness (a weight vector over radial annuli dotted with the limb-
+ * darkening profile l, Sect. 2), and I_star the disk-integrated brightness
+ * (Eq. 2-4).  The weights are tabulated on a (k, g) grid, g = c / (1 + k),
+ * and interpolated (Sect. 3.1, 3.1.2).  Each light-curve point is the mean
+ * of f over exposure sub-samples (Sect. 4.1); the planet's distance comes
+ * from a Keplerian orbit with the parameters of Sect. 4.1.
+ *
+ * Conventions for every entry point:
+ *  - Device pointers are CUDA device memory on the context's device, host
+ *    pointers ordinary host memory.  Each argument says which.  The caller
+ *    owns every pointer it passes; the library keeps none of them after
+ *    the call returns (host arrays are copied).
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  rr_evaluate / rr_evaluate_grad only enqueue work: results
+ *    are valid once the stream has been synchronised.
+ *  - Argument errors are detected on the host before anything is enqueued
+ *    and return a non-zero rr_status; rr_last_error() then describes it.
+ *  - A parameter vector (pv) outside the model's domain does not fail the
+ *    call: its light curve is NaN and its pv_status word is non-zero
+ *    (RR_PV_* bits below).
+ *  - A context is not thread-safe: calls on one context must not overlap
+ *    in time on the host.  Distinct contexts are independent.  Evaluations
+ *    on different streams may overlap on the device if each has its own
+ *    workspace and output buffers.
+ */
+#ifndef RR_H
+#define RR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rr_ctx rr_ctx;
+
+typedef enum {
+    RR_OK = 0,
+    RR_EINVAL = 1,    /* bad argument (null pointer, size, range, layout) */
+    RR_ENOMEM = 2,    /* device or host allocation failed */
+    RR_ECUDA = 3,     /* a CUDA runtime call or kernel launch failed */
+    RR_ESTATE = 4,    /* call out of order (e.g. evaluate before rr_build_weights) */
+    RR_ETIMEOUT = 6   /* a bounded device-side wait gave up (see rr_last_error) */
+} rr_status;
+
+/* Limb-darkening laws (Sect. 3.2.1) and the tabulated numerical profile (Sect. 3.2.2). */
+typedef enum {
+    RR_LD_UNIFORM = 0,        /* I = 1                                      0 coefficients */
+    RR_LD_QUADRATIC = 1,      /* I = 1 - u1 (1-mu) - u2 (1-mu)^2            2 (u1, u2)     */
+    RR_LD_QUADRATIC_TRI = 2,  /* quadratic with u1 = 2 sqrt(q1) q2,
+                                 u2 = sqrt(q1) (1 - 2 q2) (Kipping)         2 (q1, q2)     */
+    RR_LD_NONLINEAR = 3,      /* I = 1 - sum_n c_n (1 - mu^(n/2)), n=1..4   4 (c1..c4)     */
+    RR_LD_TABULATED = 4       /* I(mu) given per passband by rr_set_ld_profile   0        */
+} rr_ld_model;
+
+typedef enum {
+    RR_PREC_FP64 = 0,   /* every step in FP64; flux and grad_flux are double */
+    RR_PREC_MIXED = 1   /* FP64 setup, phase reduction and normalisation; FP32 bulk;
+                           flux and grad_flux are float */
+} rr_precision;
+
+/* Per-pv status bits written to pv_status (0 = valid). */
+#define RR_PV_K_RANGE    1    /* a radius ratio outside [k0, k1] */
+#define RR_PV_E_RANGE    2    /* eccentricity outside [0, 1) */
+#define RR_PV_B_RANGE    4    /* impact parameter outside [0, a] */
+#define RR_PV_P_RANGE    8    /* period <= 0 */
+#define RR_PV_NONFINITE  16   /* a non-finite parameter */
+#define RR_PV_LD_INVALID 32   /* I_star <= 0, or q1/q2 outside [0, 1] */
+#define RR_PV_A_RANGE    64   /* scaled semi-major axis <= 1 */
+#define RR_PV_KEPLER     128  /* Kepler iteration did not converge at some point (NaN there) */
+
+#define RR_MAX_PB 32          /* passbands per context */
+
+typedef struct {
+    double  zcut;       /* radial grid split, 0 < zcut < 1 (Sect. 3.1.1) */
+    int32_t nzin;       /* annuli of constant dz inside zcut, >= 1 */
+    int32_t nzlimb;     /* annuli of constant dmu outside zcut, >= 1; nz = nzin + nzlimb <= 4096 */
+    int32_t ng;         /* grazing-value nodes g_i = i / (ng - 1), 2 <= ng <= 4096 */
+    int32_t nk;         /* radius-ratio nodes on [k0, k1] (Sect. 3.1.2), 2 <= nk <= 4096 */
+    double  k0, k1;     /* radius-ratio range, 0 < k0 < k1 < 1 */
+    int32_t npb;        /* passbands, 1 <= npb <= RR_MAX_PB */
+    int32_t ld_model;   /* rr_ld_model */
+    int32_t chromatic;  /* 0: one k per pv; 1: one k per passband (Sect. 4.2) */
+    int32_t precision;  /* rr_precision */
+    int32_t device;     /* CUDA device ordinal */
+} rr_config;
+
+/* Create a context: validates `cfg`, builds the radial grid of Sect. 3.1.1 on
+ * the host in FP64 (edges ze, means zm = midpoints, mu = sqrt(1 - zm^2)) and
+ * allocates the device tables.  Named LD laws are ready at once; the
+ * tabulated law needs rr_set_ld_profile for every passband.  *out receives
+ * the context (NULL on failure).  Errors: RR_EINVAL (cfg), RR_ENOMEM, RR_ECUDA. */
+rr_status rr_create(const rr_config* cfg, rr_ctx** out);
+
+/* Free the context and all device memory it owns.  Accepts NULL. */
+rr_status rr_destroy(rr_ctx* ctx);
+
+/* Set the numerical profile of passband `pb` (Sect. 3.2.2): host arrays mu[n]
+ * (strictly increasing, within [0, 1]) and intensity[n] (finite), n >= 2,
+ * copied.  Between nodes the profile is linear, outside them constant; its
+ * normalisation I_star is the exact integral of that function (Eq. 2).
+ * Only for RR_LD_TABULATED.  Invalidates the tables until the next
+ * rr_build_weights.  Errors: RR_EINVAL, RR_ESTATE (named law). */
+rr_status rr_set_ld_profile(rr_ctx* ctx, int32_t pb, const double* mu, const double* intensity,
+                            int32_t n);
+
+/* Build the tables (Sect. 3.1.2): the LD profiles at the bin means and their
+ * disk integrals, the FP64 weight table w[nk][ng][nz] (covered annulus area
+ * / covered area, Sect. 2), and its projections T[b][nk][ng] = w . l_b onto
+ * every profile basis b.  Enqueued on `stream`, then the stream is
+ * synchronised (set-up, not hot path).  Must precede evaluation.
+ * Errors: RR_ESTATE (a tabulated profile missing), RR_ECUDA. */
+rr_status rr_build_weights(rr_ctx* ctx, void* stream);
+
+/* Number of columns of a parameter row:
+ *   [T0, P, a, b, e, w, k_0 .. k_{nkp-1}, ldc_0 .. ldc_{npb*nldc-1}]
+ * T0 = mid-transit (conjunction) time and P = period, in the time unit of
+ * `times` (days); a = semi-major axis and b = impact parameter a cos i in
+ * stellar radii; e = eccentricity; w = argument of periastron [rad];
+ * nkp = npb if chromatic else 1; nldc = coefficients of the LD law, stored
+ * passband-major. */
+int32_t rr_nparam(const rr_ctx* ctx);
+
+/* Device workspace (bytes) that rr_evaluate (with_grad = 0) or
+ * rr_evaluate_grad (with_grad = 1) needs for npv parameter vectors and npt
+ * times.  0 on bad arguments. */
+size_t rr_workspace_bytes(const rr_ctx* ctx, int32_t npv, int32_t npt, int32_t with_grad);
+
+/* Evaluate light curves: flux[pv][t] for every parameter vector and time.
+ *   times        device, double[npt]: mid-exposure times
+ *   pb_index     device, int32[npt]: passband of each time, 0 <= . < npb
+ *                (NULL allowed when npb == 1)
+ *   params       device, double[npv][nparam], row-major (see rr_nparam)
+ *   supersampling host, int32[npb]: sub-exposures per time, 1 .. 1024
+ *   exptime      host, double[npb]: exposure length, >= 0 (ignored if ss = 1)
+ *   flux         device, [npv][npt] row-major, float (MIXED) or double (FP64)
+ *   pv_status    device, int32[npv] (RR_PV_* bits), or NULL
+ *   workspace    device scratch of >= rr_workspace_bytes(ctx, npv, npt, 0)
+ *                bytes, 256-byte aligned; contents are overwritten
+ * npt == 0 or npv == 0 is a valid no-op.  Errors: RR_EINVAL, RR_ESTATE, RR_ECUDA. */
+rr_status rr_evaluate(rr_ctx* ctx, const double* times, const int32_t* pb_index, int32_t npt,
+                      const double* params, int32_t npv, const int32_t* supersampling,
+                      const double* exptime, void* flux, int32_t* pv_status, void* workspace,
+                      size_t workspace_bytes, void* stream);
+
+/* Vector-Jacobian product of rr_evaluate (hand-written adjoint):
+ *   grad_params[pv][j] = sum_t grad_flux[pv][t] * d flux[pv][t] / d params[pv][j]
+ * Same inputs as rr_evaluate, plus
+ *   grad_flux    device, [npv][npt], float (MIXED) or double (FP64)
+ *   grad_params  device, double[npv][nparam] (written, not accumulated)
+ * Derivatives of the piecewise-linear (k, g) interpolants are those of the
+ * cell holding the point (the lower cell on a node).  The sum over times is
+ * deterministic (fixed tiling and order), so a pv's gradient does not
+ * depend on the other pvs evaluated with it.  Invalid pvs get NaN rows.
+ * workspace >= rr_workspace_bytes(ctx, npv, npt, 1).  Errors as rr_evaluate. */
+rr_status rr_evaluate_grad(rr_ctx* ctx, const double* times, const int32_t* pb_index, int32_t npt,
+                           const double* params, int32_t npv, const int32_t* supersampling,
+                           const double* exptime, const void* grad_flux, double* grad_params,
+                           int32_t* pv_status, void* workspace, size_t workspace_bytes,
+                           void* stream);
+
+/* Copy a set-up table to host memory (for inspection and tests); returns the
+ * element count of the table, or -1 on error.  `out` may be NULL to query
+ * the size; otherwise it receives min(count, capacity) doubles.
+ *   RR_TABLE_ZE (nz+1), RR_TABLE_ZM (nz), RR_TABLE_MU (nz)
+ *   RR_TABLE_WEIGHTS (nk*ng*nz), RR_TABLE_BASIS (nbasis*nz) profiles at zm,
+ *   RR_TABLE_ISTAR (nbasis), RR_TABLE_PROJ (nbasis*nk*ng) = w . basis
+ * Tables other than the grid need rr_build_weights first.  Synchronous. */
+#define RR_TABLE_ZE 0
+#define RR_TABLE_ZM 1
+#define RR_TABLE_MU 2
+#define RR_TABLE_WEIGHTS 3
+#define RR_TABLE_BASIS 4
+#define RR_TABLE_ISTAR 5
+#define RR_TABLE_PROJ 6
+int64_t rr_read_table(rr_ctx* ctx, int32_t which, double* out, int64_t capacity);
+
+/* Synchronise `stream` and report whether any kernel of this context gave up
+ * a bounded device-side wait since the last check (RR_ETIMEOUT; the affected
+ * outputs are incomplete).  Resets the indicator.  Errors: RR_ECUDA. */
+rr_status rr_sync_status(rr_ctx* ctx, void* stream);
+
+/* Description of the last error on `ctx` (or of the last rr_create failure
+ * when ctx is NULL).  Valid until the next call on the same context. */
+const char* rr_last_error(const rr_ctx* ctx);
+
+/* Count of kernel launches this context has issued since creation. */
+int64_t rr_launch_count(const rr_ctx* ctx);
+
+/* Kernel kinds for per-kernel timing. */
+#define RR_KERNEL_LD_BASIS 0
+#define RR_KERNEL_WEIGHTS 1
+#define RR_KERNEL_PV_SETUP 2
+#define RR_KERNEL_FLUX 3
+#define RR_KERNEL_GRAD 4
+#define RR_KERNEL_GRAD_REDUCE 5
+#define RR_KERNEL_KINDS 6
+
+/* Per-kernel timing (measurement aid).  While enabled, every kernel launch
+ * of this context is bracketed by two CUDA events recorded on the launching
+ * stream.  rr_profile_read waits for the recorded events, adds their elapsed
+ * times to per-kind totals, and returns the total milliseconds and launch
+ * count of `kind` (optionally resetting all totals).  Errors: RR_EINVAL. */
+rr_status rr_profile(rr_ctx* ctx, int32_t enable);
+rr_status rr_profile_read(rr_ctx* ctx, int32_t kind, double* total_ms, int64_t* count, int32_t reset);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RR_H */

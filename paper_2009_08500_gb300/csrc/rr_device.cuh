@@ -1,0 +1,287 @@
+// Device-side building blocks of the per-point kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math_constants.h>
+
+#include "rr_internal.h"
+
+namespace rr {
+
+template <typename R> struct Tr;
+template <> struct Tr<float> {
+    static __device__ __forceinline__ float pi() { return CUDART_PI_F; }
+    static __device__ __forceinline__ float two_pi() { return 2.0f * CUDART_PI_F; }
+};
+template <> struct Tr<double> {
+    static __device__ __forceinline__ double pi() { return CUDART_PI; }
+    static __device__ __forceinline__ double two_pi() { return 2.0 * CUDART_PI; }
+};
+
+__device__ __forceinline__ float d_sqrt(float x) { return sqrtf(x); }
+__device__ __forceinline__ double d_sqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ float d_atan2(float y, float x) { return atan2f(y, x); }
+__device__ __forceinline__ double d_atan2(double y, double x) { return atan2(y, x); }
+__device__ __forceinline__ void d_sincos(float x, float* s, float* c) { sincosf(x, s, c); }
+__device__ __forceinline__ void d_sincos(double x, double* s, double* c) { sincos(x, s, c); }
+__device__ __forceinline__ float d_rint(float x) { return rintf(x); }
+__device__ __forceinline__ double d_rint(double x) { return rint(x); }
+
+// Area covered by a planet of radius k at centre distance z on a unit stellar
+// disk (the a(c, k) of Eq. 5), for z < 1 + k, with its partial derivatives.
+// Lens case: A = kappa0 + k^2 kappa1 - K/2 with K = sqrt of Heron's product
+// of the triangle (1, k, z) built from differences, and the half-angles as
+// atan2(K, .) -- accurate near both contact points.  dA/dz = -K/z (minus the
+// common chord), dA/dk = 2 k kappa1 (planet rim inside the star).
+template <typename R, bool GRAD>
+__device__ __forceinline__ R covered_area(R k, R z, R& dAdz, R& dAdk) {
+    const R one = R(1);
+    if (z <= fabs(one - k)) {
+        if (GRAD) dAdz = R(0);
+        if (k < one) {
+            if (GRAD) dAdk = R(2) * Tr<R>::pi() * k;
+            return Tr<R>::pi() * k * k;
+        }
+        if (GRAD) dAdk = R(0);
+        return Tr<R>::pi();
+    }
+    const R f1 = (one + k) - z;
+    const R f2 = z + (one - k);
+    const R f3 = z - (one - k);
+    const R f4 = z + (one + k);
+    R h = (f1 * f2) * (f3 * f4);
+    h = h > R(0) ? h : R(0);
+    const R K = d_sqrt(h);
+    const R zz = z * z, kk = k * k;
+    const R kap0 = d_atan2(K, zz + (one - kk));
+    const R kap1 = d_atan2(K, zz + (kk - one));
+    if (GRAD) {
+        dAdz = -K / z;
+        dAdk = R(2) * k * kap1;
+    }
+    return kap0 + kk * kap1 - R(0.5) * K;
+}
+
+// Linear interpolation of a profile row over the g nodes g_i = i / (ng - 1):
+// the cell is floor(g (ng - 1)), clamped to ng - 2.  Returns the value and
+// the in-cell slope d/dg.
+template <typename R>
+__device__ __forceinline__ R lerp_row(const R* row, int ng, R g, R& slope_cell, int& cell) {
+    const R x = g * R(ng - 1);
+    int i = (int)x;                       // x >= 0: truncation is floor
+    i = i < ng - 2 ? i : ng - 2;
+    const R al = x - R(i);
+    const R l0 = row[i], l1 = row[i + 1];
+    slope_cell = (l1 - l0);
+    cell = i;
+    return l0 + al * (l1 - l0);
+}
+
+// Offset-form Kepler solve in FP32 for x = E - E0 given dM = M - M0
+// (Newton, f(x) = x - ecE0 sin x + esE0 (1 - cos x) - dM, f' = 1 - e cos E).
+// On return S = sin x, V = 1 - cos x.  Returns false if not converged.
+__device__ __forceinline__ bool kepler_offset_f32(float dM, float ecE0, float esE0, float inv_den0,
+                                                  float& x, float& S, float& V) {
+    x = dM * inv_den0;
+    #pragma unroll 1
+    for (int it = 0; it < 24; ++it) {
+        float hs, hc;
+        sincosf(0.5f * x, &hs, &hc);
+        S = 2.0f * hs * hc;
+        V = 2.0f * hs * hs;
+        const float fx = (x - dM) - ecE0 * S + esE0 * V;
+        const float fp = (1.0f - ecE0) + ecE0 * V + esE0 * S;
+        const float dx = fx / fp;
+        x -= dx;
+        const float S_old = S;
+        S -= dx * (1.0f - V);
+        V -= dx * S_old;
+        if (fabsf(dx) <= 2e-6f * fabsf(x) + 1e-30f) return true;
+    }
+    return false;
+}
+
+// FP64 offset-form Kepler solve (used for e > kESwitch and by the FP64 path).
+__device__ __forceinline__ bool kepler_offset_f64(double dM, double ecE0, double esE0,
+                                                  double inv_den0, double& x, double& S,
+                                                  double& V) {
+    x = dM * inv_den0;
+    #pragma unroll 1
+    for (int it = 0; it < 100; ++it) {
+        double hs, hc;
+        sincos(0.5 * x, &hs, &hc);
+        S = 2.0 * hs * hc;
+        V = 2.0 * hs * hs;
+        const double fx = (x - dM) - ecE0 * S + esE0 * V;
+        const double fp = (1.0 - ecE0) + ecE0 * V + esE0 * S;
+        const double dx = fx / fp;
+        x -= dx;
+        const double S_old = S;
+        S -= dx * (1.0 - V);
+        V -= dx * S_old;
+        if (fabs(dx) <= 4e-15 * fabs(x) + 1e-300) return true;
+    }
+    return false;
+}
+
+// ---- bulk asynchronous copy global -> shared with an mbarrier (TMA engine) ----
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+                 : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+// dst, src 16-byte aligned; bytes a multiple of 16
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+            "r"(smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait: gives up after ~0.1 s and reports false.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+    #pragma unroll 1
+    for (int i = 0; i < (1 << 21); ++i) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (i > 32) __nanosleep(64);
+    }
+    return false;
+}
+
+// Stage `bytes` (multiple of 16) from global memory into shared memory with
+// one elected thread issuing the copy; every thread waits (bounded).  On a
+// timeout the device error word is set, the wait is retried once more
+// (bounded) so that no copy is left in flight, and false is returned.
+__device__ __forceinline__ bool stage_to_smem(void* dst, const void* src, uint32_t bytes,
+                                              uint64_t* bar, int* err) {
+    if (threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        mbar_expect_tx(bar, bytes);
+        // the copy engine limits one bulk copy's size; split into chunks
+        const uint32_t chunk = 1u << 16;
+        for (uint32_t off = 0; off < bytes; off += chunk) {
+            const uint32_t n = bytes - off < chunk ? bytes - off : chunk;
+            bulk_g2s((char*)dst + off, (const char*)src + off, n, bar);
+        }
+    }
+    __syncthreads();
+    bool ok = mbar_wait_bounded(bar, 0);
+    if (!ok) {
+        if (threadIdx.x == 0) atomicExch(err, kErrBarrierTimeout);
+        mbar_wait_bounded(bar, 0);
+    }
+    return __syncthreads_and(ok ? 1 : 0) != 0;
+}
+
+// ---- phase and orbit (offset-from-conjunction form) ----
+
+struct Phase32 {
+    float fr_h, fr_l;   // reduced phase in cycles, fr_h + fr_l, |.| <~ 0.5
+    float m;            // integer cycles removed by the reduction
+};
+
+// Precise phase (cycles) of a time relative to the nearest conjunction:
+// psi = A + dt / P with dt = dh + dl, A = Ah + Al, 1 / P = Bh + Bl.
+__device__ __forceinline__ Phase32 precise_phase(float dh, float dl, float Ah, float Al, float Bh,
+                                                 float Bl) {
+    const float p = dh * Bh;
+    float e = fmaf(dh, Bh, -p);          // exact low part of dh * Bh
+    e = fmaf(dh, Bl, e);
+    e = fmaf(dl, Bh, e);
+    const float s = p + Ah;              // two-sum of p and Ah
+    const float bb = s - p;
+    const float err = (p - (s - bb)) + (Ah - bb);
+    const float m = rintf(s);
+    Phase32 r;
+    r.fr_h = s - m;                      // exact (m is the nearest integer to s)
+    r.fr_l = err + (Al + e);
+    r.m = m;
+    return r;
+}
+
+struct Orbit32 {
+    float z, Px, Py, S, V;
+    bool front, ok;
+};
+
+// Projected distance from the mean-anomaly offset dM = M - M0 (radians).
+// dMd: the same offset in FP64, used when e > kESwitch.
+__device__ __forceinline__ Orbit32 orbit32(const PvHead<float>& H, float dM, double dMd) {
+    Orbit32 o;
+    o.ok = true;
+    float x;
+    if (H.flags & kPvCircular) {
+        float hs, hc;
+        sincosf(0.5f * dM, &hs, &hc);
+        o.S = 2.0f * hs * hc;
+        o.V = 2.0f * hs * hs;
+    } else if (H.flags & kPvKepler64) {
+        double xd, Sd, Vd;
+        o.ok = kepler_offset_f64(dMd, H.ecE0d, H.esE0d, H.inv_den0d, xd, Sd, Vd);
+        o.S = (float)Sd;
+        o.V = (float)Vd;
+    } else {
+        o.ok = kepler_offset_f32(dM, H.ecE0, H.esE0, H.inv_den0, x, o.S, o.V);
+    }
+    o.Px = fmaf(H.ax1, o.V, H.ax2 * o.S);
+    o.Py = H.rho0 + fmaf(H.ay1, o.V, H.ay2 * o.S);
+    o.z = sqrtf(fmaf(H.a2 * o.Px, o.Px, H.b2 * o.Py * o.Py));
+    o.front = o.Py > 0.0f;
+    return o;
+}
+
+struct Orbit64 {
+    double z, Px, Py, S, V, x;
+    bool front, ok;
+};
+
+__device__ __forceinline__ Orbit64 orbit64(const PvHead<double>& H, double dM) {
+    Orbit64 o;
+    o.ok = true;
+    if (H.flags & kPvCircular) {
+        double hs, hc;
+        sincos(0.5 * dM, &hs, &hc);
+        o.S = 2.0 * hs * hc;
+        o.V = 2.0 * hs * hs;
+        o.x = dM;
+    } else {
+        o.ok = kepler_offset_f64(dM, H.ecE0d, H.esE0d, H.inv_den0d, o.x, o.S, o.V);
+    }
+    o.Px = fma(H.ax1, o.V, H.ax2 * o.S);
+    o.Py = H.rho0 + fma(H.ay1, o.V, H.ay2 * o.S);
+    o.z = sqrt(fma(H.a2 * o.Px, o.Px, H.b2 * o.Py * o.Py));
+    o.front = o.Py > 0.0;
+    return o;
+}
+
+__device__ __forceinline__ float warp_max(float v) {
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+}  // namespace rr

@@ -1,0 +1,155 @@
+// Internal layout shared by the host code and the kernels of librr.
+//
+// Per-call data flow (all stream-ordered, no host synchronisation):
+//   rr_pv_setup_kernel   params -> one PvRecord per parameter vector in the
+//                        caller's workspace (orbit constants, transit window,
+//                        k-interpolated profile rows divided by I_star)
+//   rr_flux_kernel       PvRecords of a pv tile -> shared memory (one bulk
+//                        async copy), times of a point tile -> registers,
+//                        flux[pv][t] for the tile
+//   rr_grad_kernel       same tiling; per-(pv, point tile) partial sums of the
+//                        vector-Jacobian product -> workspace
+//   rr_grad_reduce       partial sums -> grad_params (fixed order)
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/rr.h"
+
+namespace rr {
+
+constexpr int kBlock = 256;               // threads per CTA in the per-point kernels
+constexpr int kPPT = 4;                   // points per thread
+constexpr int kPtTile = kBlock * kPPT;    // points per CTA
+constexpr int kMaxPvTile = 32;            // parameter vectors per CTA (upper bound)
+constexpr int kSmemTarget = 48 * 1024;    // record bytes per CTA the tiler aims for
+constexpr int kMaxNz = 4096;
+constexpr size_t kMaxSmem = 227 * 1024;   // dynamic shared memory per CTA on sm_103a
+constexpr int kMaxBasis = RR_MAX_PB + 4;  // profile bases: 1 + nldc (named) or npb (tabulated)
+constexpr double kESwitch = 0.8;          // above this eccentricity Kepler is solved in FP64
+
+// device error word values (ctx->d_err)
+constexpr int kErrBarrierTimeout = 1;
+
+enum PvFlags : int32_t { kPvCircular = 1, kPvKepler64 = 2, kPvNoWindow = 4 };
+
+// Fixed part of a per-pv record.  R = float (mixed) or double (FP64).
+// Derived quantities of the Keplerian orbit written in the offset-from-
+// conjunction form used by the kernels (x = E - E0):
+//   P_x = ax1 V + ax2 S,  P_y = rho0 + ay1 V + ay2 S,  V = 1 - cos x, S = sin x
+//   z^2 = a^2 P_x^2 + b^2 P_y^2, in front iff P_y > 0
+//   Kepler: x - ecE0 S + esE0 V = dM,  dM = M - M0 = n (t - T0) reduced
+template <typename R>
+struct alignas(16) PvHead {
+    double T0, P, invP;            // FP64 epoch and period (phase reduction)
+    double ecE0d, esE0d, inv_den0d;  // FP64 Kepler constants (e > kESwitch fallback)
+    double pad0, pad1;
+    R a, b, a2, b2;
+    R e, ecE0, esE0, inv_den0;     // inv_den0 = 1 / (1 - e cos E0)
+    R ax1, ax2, ay1, ay2;
+    R rho0, n, Bh, Bl;             // n = 2 pi / P; Bh + Bl = 1 / P (float-float)
+    R dM0de, dM0dw, se, cw;        // dM0/de, dM0/dw, sqrt(1 - e^2), cos w
+    R sw, cE0, sE0, pad2;
+    int32_t flags, status, pad3, pad4;
+};
+
+// Per-(pv, passband) constants.
+template <typename R>
+struct alignas(16) PvPb {
+    R k, inv1pk;      // radius ratio, 1 / (1 + k)
+    R win_s;          // |dM| bound of a possible transit for one sample [rad]
+    R win_p;          // same, widened by the passband's exposure half-span
+};
+
+struct RecLayout {
+    int32_t npb, ng, ng_pad, rows_per_pb;  // rows: 1 (flux) or 2 + nldc (adjoint)
+    int32_t nldc, off_pb, off_rows, bytes; // byte offsets inside a record; record stride
+};
+
+template <typename R>
+inline RecLayout make_layout(int npb, int ng, int nldc, bool grad) {
+    RecLayout L;
+    L.npb = npb;
+    L.ng = ng;
+    L.ng_pad = (ng + 3) & ~3;
+    L.nldc = nldc;
+    L.rows_per_pb = grad ? 2 + nldc : 1;
+    L.off_pb = (int32_t)sizeof(PvHead<R>);
+    L.off_rows = L.off_pb + npb * (int32_t)sizeof(PvPb<R>);
+    size_t bytes = (size_t)L.off_rows + (size_t)npb * L.rows_per_pb * L.ng_pad * sizeof(R);
+    L.bytes = (int32_t)((bytes + 15) & ~(size_t)15);
+    return L;
+}
+
+// Passband sampling constants, passed by value.
+struct PbParams {
+    int32_t npb;
+    int32_t ss[RR_MAX_PB];
+    double exptime[RR_MAX_PB];
+    float first[RR_MAX_PB];     // offset of sub-sample s = first + s * step [days]
+    float step[RR_MAX_PB];
+    float inv_ss[RR_MAX_PB];
+};
+
+// Model constants for the kernels (by value).
+struct ModelParams {
+    int32_t ld_model, npb, chromatic, nldc, nparam, nk, ng, nbasis;
+    double k0, k1, dk;
+};
+
+}  // namespace rr
+
+// The context (opaque to users).
+struct rr_ctx {
+    rr_config cfg;
+    int nz = 0, nldc = 0, nbasis = 0, nparam = 0, nkp = 0;
+    double dk = 0, dg = 0;
+    std::vector<double> ze, zm, mu;
+    std::vector<std::vector<double>> tab_mu, tab_I;
+    double* d_ze = nullptr;
+    double* d_mu = nullptr;
+    double* d_w = nullptr;       // nk * ng * nz
+    double* d_basis = nullptr;   // nbasis * nz
+    double* d_istar = nullptr;   // nbasis
+    double* d_T64 = nullptr;     // nbasis * nk * ng
+    float* d_T32 = nullptr;      // nbasis * nk * ng
+    double* d_tab = nullptr;     // tabulated profiles, concatenated (mu then I per passband)
+    int* d_tab_off = nullptr;    // npb + 1 offsets (in nodes)
+    int* d_err = nullptr;        // device error word
+    bool weights_built = false;
+    bool tables_built = false;
+    std::string err;
+    long long launches = 0;
+    // optional per-kernel timing with CUDA events on the launching stream
+    bool profiling = false;
+    std::vector<cudaEvent_t> ev_pool;
+    struct Timed { int kind; cudaEvent_t a, b; };
+    std::vector<Timed> timed;
+    double prof_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    long long prof_n[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+};
+
+namespace rr {
+// launchers (defined in the .cu files); all return cudaGetLastError() after launch
+cudaError_t launch_ld_basis(rr_ctx* c, cudaStream_t s);
+cudaError_t launch_weights(rr_ctx* c, bool need_w, cudaStream_t s);
+cudaError_t launch_pv_setup(rr_ctx* c, const double* params, int npv, const PbParams& pbp,
+                            bool grad, void* records, int32_t* pv_status, cudaStream_t s);
+cudaError_t launch_flux(rr_ctx* c, const double* times, const int32_t* pb_index, int npt, int npv,
+                        const PbParams& pbp, const void* records, void* flux, int32_t* pv_status,
+                        cudaStream_t s);
+cudaError_t launch_grad(rr_ctx* c, const double* times, const int32_t* pb_index, int npt, int npv,
+                        const PbParams& pbp, const void* records, const void* grad_flux, double* partials,
+                        int32_t* pv_status, cudaStream_t s);
+cudaError_t launch_grad_reduce(rr_ctx* c, int npt, const double* params, int npv, const void* records,
+                               const double* partials, double* grad_params, cudaStream_t s);
+size_t records_bytes(const rr_ctx* c, int npv, bool grad);
+size_t partials_bytes(const rr_ctx* c, int npv, int npt);
+ModelParams model_params(const rr_ctx* c);
+int pv_tile_for(int rec_bytes);
+}  // namespace rr

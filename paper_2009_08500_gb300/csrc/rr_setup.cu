@@ -1,0 +1,415 @@
+// Set-up kernels: LD profile bases and disk integrals, the (k, g) weight table
+// with its projections, and the per-call, per-parameter-vector records.
+#include <cmath>
+
+#include "rr_device.cuh"
+
+namespace rr {
+
+// ---------------------------------------------------------------------------
+// LD profile bases at the bin means and their disk integrals (Sect. 3.2, Eq. 2)
+//
+// Every supported law is affine in its coefficients,
+//   I(mu) = beta_0(mu) + sum_c u_c beta_c(mu),
+// so the mean covered brightness w . l (Sect. 2) and I_star are the same
+// combination of per-basis values.  Bases:
+//   uniform                 beta_0 = 1
+//   quadratic (and q1, q2)  beta_0 = 1, beta_1 = -(1 - mu), beta_2 = -(1 - mu)^2
+//   nonlinear               beta_0 = 1, beta_n = -(1 - mu^(n/2)), n = 1..4
+//   tabulated               one basis per passband: the table interpolated at mu
+// I_star of a basis is 2 pi int_0^1 mu beta(mu) dmu: closed forms for the
+// named bases, and for a table the exact integral of its piecewise-linear
+// interpolant (constant outside the nodes).
+// ---------------------------------------------------------------------------
+__device__ double block_sum_f64(double v, double* red) {
+    // deterministic tree over a power-of-two block
+    const int t = threadIdx.x;
+    red[t] = v;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (t < s) red[t] += red[t + s];
+        __syncthreads();
+    }
+    const double r = red[0];
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(256) rr_ld_basis_kernel(ModelParams mp, const double* __restrict__ mu,
+                                                          int nz, const double* __restrict__ tab,
+                                                          const int* __restrict__ tab_off,
+                                                          double* __restrict__ basis,
+                                                          double* __restrict__ istar) {
+    __shared__ double red[256];
+    const int b = blockIdx.x;
+    double* out = basis + (size_t)b * nz;
+    if (mp.ld_model != RR_LD_TABULATED) {
+        for (int j = threadIdx.x; j < nz; j += blockDim.x) {
+            const double m = mu[j];
+            double v = 1.0;
+            if (b > 0) {
+                if (mp.ld_model == RR_LD_NONLINEAR)
+                    v = -(1.0 - pow(m, 0.5 * b));
+                else
+                    v = (b == 1) ? -(1.0 - m) : -(1.0 - m) * (1.0 - m);
+            }
+            out[j] = v;
+        }
+        if (threadIdx.x == 0) {
+            double I;
+            if (b == 0)
+                I = CUDART_PI;
+            else if (mp.ld_model == RR_LD_NONLINEAR)
+                I = -CUDART_PI * b / (b + 4.0);
+            else
+                I = (b == 1) ? -CUDART_PI / 3.0 : -CUDART_PI / 6.0;
+            istar[b] = I;
+        }
+        return;
+    }
+    // tabulated profile of passband b: nodes tmu[0..n), tI[0..n)
+    const int o0 = tab_off[b], n = tab_off[b + 1] - o0;
+    const double* tmu = tab + 2 * o0;
+    const double* tI = tmu + n;
+    for (int j = threadIdx.x; j < nz; j += blockDim.x) {
+        const double m = mu[j];
+        double v;
+        if (m <= tmu[0]) {
+            v = tI[0];
+        } else if (m >= tmu[n - 1]) {
+            v = tI[n - 1];
+        } else {
+            int lo = 0, hi = n - 1;  // tmu[lo] < m < tmu[hi]
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (tmu[mid] <= m) lo = mid; else hi = mid;
+            }
+            const double t = (m - tmu[lo]) / (tmu[lo + 1] - tmu[lo]);
+            v = tI[lo] + t * (tI[lo + 1] - tI[lo]);
+        }
+        out[j] = v;
+    }
+    // 2 pi int mu I dmu of the interpolant: segment [m0, m1] contributes
+    // (m1 - m0)/6 [I0 (2 m0 + m1) + I1 (m0 + 2 m1)]; constant ends
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n - 1; i += blockDim.x) {
+        const double m0 = tmu[i], m1 = tmu[i + 1];
+        s += (m1 - m0) / 6.0 * (tI[i] * (2.0 * m0 + m1) + tI[i + 1] * (m0 + 2.0 * m1));
+    }
+    if (threadIdx.x == 0) s += 0.5 * tI[0] * tmu[0] * tmu[0] + 0.5 * tI[n - 1] * (1.0 - tmu[n - 1] * tmu[n - 1]);
+    const double tot = block_sum_f64(s, red);
+    if (threadIdx.x == 0) istar[b] = 2.0 * CUDART_PI * tot;
+}
+
+// ---------------------------------------------------------------------------
+// Weight table (Sect. 2 below Eq. 4; Sect. 3.1, 3.1.2) and its projections
+//   w[ik][ig][j] = (a(ze[j+1]) - a(ze[j])) / a(1),   c = g_ig (1 + k_ik)
+//   T[b][ik][ig] = sum_j w[ik][ig][j] beta_b[j]
+// a(r) = area common to the radius-r disk and the planet; at g = 1 (covered
+// area 0) the row is its limit, all weight in the outermost annulus.
+// One CTA per (ik, ig) row, FP64.
+// ---------------------------------------------------------------------------
+__device__ double lens_area_f64(double r, double k, double c) {
+    if (c >= r + k) return 0.0;
+    if (c <= fabs(r - k)) {
+        const double m = r < k ? r : k;
+        return CUDART_PI * m * m;
+    }
+    double h = ((r + k) - c) * (c + (r - k)) * (c - (r - k)) * (c + (r + k));
+    h = h > 0.0 ? h : 0.0;
+    const double K = sqrt(h);
+    const double kap0 = atan2(K, c * c + (r * r - k * k));
+    const double kap1 = atan2(K, c * c + (k * k - r * r));
+    return r * r * kap0 + k * k * kap1 - 0.5 * K;
+}
+
+__global__ void __launch_bounds__(256) rr_weights_kernel(ModelParams mp, const double* __restrict__ ze,
+                                                         int nz, const double* __restrict__ basis,
+                                                         int write_w, double* __restrict__ w,
+                                                         double* __restrict__ T64,
+                                                         float* __restrict__ T32) {
+    extern __shared__ double sh[];   // nz + 1 edge areas, then nz weights
+    double* ea = sh;
+    double* ws = sh + nz + 1;
+    const int ig = blockIdx.x, ik = blockIdx.y;
+    const double k = mp.k0 + ik * mp.dk;
+    const double g = ig * (1.0 / (mp.ng - 1));
+    const double c = g * (1.0 + k);
+    const double atot = lens_area_f64(1.0, k, c);
+    const bool limb = (c >= 1.0 + k) || !(atot > 0.0);
+    if (!limb)
+        for (int j = threadIdx.x; j <= nz; j += blockDim.x) ea[j] = lens_area_f64(ze[j], k, c);
+    __syncthreads();
+    double* wrow = w + ((size_t)ik * mp.ng + ig) * nz;
+    for (int j = threadIdx.x; j < nz; j += blockDim.x) {
+        const double v = limb ? (j == nz - 1 ? 1.0 : 0.0) : (ea[j + 1] - ea[j]) / atot;
+        ws[j] = v;
+        if (write_w) wrow[j] = v;
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int b = warp; b < mp.nbasis; b += blockDim.x >> 5) {
+        const double* bb = basis + (size_t)b * nz;
+        double s = 0.0;
+        for (int j = lane; j < nz; j += 32) s += ws[j] * bb[j];
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) {
+            const size_t idx = ((size_t)b * mp.nk + ik) * mp.ng + ig;
+            T64[idx] = s;
+            T32[idx] = (float)s;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Per-call parameter-vector records (FP64 arithmetic, rounded to R).
+//
+// Validates the row (the RR_PV_* bits), derives the orbit constants of the
+// offset-from-conjunction form (see PvHead), the transit window, and for
+// every passband the profile row interpolated in k (Sect. 3.1.2, the
+// (1 - ak) dot(w[ik], l) + ak dot(w[ik+1], l) of the paper, evaluated as the
+// same combination of the precomputed projections T) divided by I_star.
+// With `grad`, each passband also gets d(row)/dk and, per LD coefficient c,
+// Q_c = (T_c - row I_star_c) / I_star, the derivative of row / I_star
+// with respect to u_c.
+//
+// Transit window: z >= r |cos(w + f)| >= a (1 - e) |cos(w + f)|, so a
+// transit needs |cos(w + f)| < q = (1 + k) / (a (1 - e)) with the planet in
+// front, i.e. f within asin(q) (pi/2 if q >= 1) of the conjunction anomaly
+// f0 = pi/2 - w.  Mapped to mean anomaly this gives |M - M0| <= win.
+// ---------------------------------------------------------------------------
+__device__ double wrap_2pi(double x) {
+    const double tp = 2.0 * CUDART_PI;
+    x = fmod(x, tp);
+    return x < 0.0 ? x + tp : x;
+}
+
+__device__ double mean_anomaly_of_true(double f, double e) {
+    const double E = 2.0 * atan2(sqrt(1.0 - e) * sin(0.5 * f), sqrt(1.0 + e) * cos(0.5 * f));
+    return E - e * sin(E);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(128) rr_pv_setup_kernel(ModelParams mp, PbParams pbp,
+                                                          const double* __restrict__ params, int npv,
+                                                          const double* __restrict__ T64,
+                                                          const double* __restrict__ istar,
+                                                          RecLayout L, int grad, char* __restrict__ records,
+                                                          int32_t* __restrict__ pv_status) {
+    __shared__ double u_s[RR_MAX_PB][4];
+    __shared__ double Is_s[RR_MAX_PB];
+    __shared__ int ik_s[RR_MAX_PB];
+    __shared__ double ak_s[RR_MAX_PB];
+    __shared__ int st_s;
+    const int pv = blockIdx.x;
+    if (pv >= npv) return;
+    const double* row = params + (size_t)pv * mp.nparam;
+    char* rec = records + (size_t)pv * L.bytes;
+    PvHead<R>* H = reinterpret_cast<PvHead<R>*>(rec);
+    PvPb<R>* PB = reinterpret_cast<PvPb<R>*>(rec + L.off_pb);
+    R* rows = reinterpret_cast<R*>(rec + L.off_rows);
+    const int nkp = mp.chromatic ? mp.npb : 1;
+
+    if (threadIdx.x == 0) {
+        const double T0 = row[0], P = row[1], a = row[2], b = row[3], e = row[4], w = row[5];
+        int st = 0;
+        bool finite = true;
+        for (int j = 0; j < mp.nparam; ++j) finite = finite && isfinite(row[j]);
+        if (!finite) {
+            st = RR_PV_NONFINITE;
+        } else {
+            for (int j = 0; j < nkp; ++j) {
+                const double k = row[6 + j];
+                if (k < mp.k0 || k > mp.k1) st |= RR_PV_K_RANGE;
+            }
+            if (!(e >= 0.0 && e < 1.0)) st |= RR_PV_E_RANGE;
+            if (!(P > 0.0)) st |= RR_PV_P_RANGE;
+            if (!(a > 1.0)) st |= RR_PV_A_RANGE;
+            if (!(b >= 0.0 && b <= a)) st |= RR_PV_B_RANGE;
+            for (int pb = 0; pb < mp.npb; ++pb) {
+                const double* c = row + 6 + nkp + pb * mp.nldc;
+                double u[4] = {0, 0, 0, 0};
+                bool ldbad = false;
+                if (mp.ld_model == RR_LD_QUADRATIC_TRI) {
+                    const double q1 = c[0], q2 = c[1];
+                    ldbad = !(q1 >= 0.0 && q1 <= 1.0 && q2 >= 0.0 && q2 <= 1.0);
+                    const double sq = sqrt(fmax(q1, 0.0));
+                    u[0] = 2.0 * sq * q2;
+                    u[1] = sq * (1.0 - 2.0 * q2);
+                } else {
+                    for (int j = 0; j < mp.nldc; ++j) u[j] = c[j];
+                }
+                double Is;
+                if (mp.ld_model == RR_LD_TABULATED) {
+                    Is = istar[pb];
+                } else {
+                    Is = istar[0];
+                    for (int j = 0; j < mp.nldc; ++j) Is += u[j] * istar[1 + j];
+                }
+                if (ldbad || !(Is > 0.0)) st |= RR_PV_LD_INVALID;
+                for (int j = 0; j < 4; ++j) u_s[pb][j] = u[j];
+                Is_s[pb] = Is;
+                const double k = row[6 + (mp.chromatic ? pb : 0)];
+                const double x = (k - mp.k0) / mp.dk;
+                int ik = (int)floor(x);
+                ik = ik < 0 ? 0 : (ik > mp.nk - 2 ? mp.nk - 2 : ik);
+                ik_s[pb] = ik;
+                ak_s[pb] = x - ik;
+            }
+        }
+        st_s = st;
+        H->status = st;
+        if (pv_status) pv_status[pv] = st;
+        if (st == 0) {
+            const double f0 = 0.5 * CUDART_PI - w;
+            const double E0 = 2.0 * atan2(sqrt(1.0 - e) * sin(0.5 * f0), sqrt(1.0 + e) * cos(0.5 * f0));
+            const double cE0 = cos(E0), sE0 = sin(E0);
+            const double M0 = E0 - e * sE0;
+            const double se = sqrt(1.0 - e * e);
+            const double cw = cos(w), sw = sin(w);
+            const double den0 = 1.0 - e * cE0;
+            const double n = 2.0 * CUDART_PI / P;
+            double ax1, ax2, ay1, ay2, rho0;
+            if (e == 0.0) {
+                ax1 = 0.0; ax2 = -1.0; ay1 = -1.0; ay2 = 0.0; rho0 = 1.0;
+            } else {
+                ax1 = -cw * cE0 + sw * se * sE0;
+                ax2 = -cw * sE0 - sw * se * cE0;
+                ay1 = -sw * cE0 - cw * se * sE0;
+                ay2 = -sw * sE0 + cw * se * cE0;
+                rho0 = den0;
+            }
+            H->T0 = T0; H->P = P; H->invP = 1.0 / P;
+            H->ecE0d = e * cE0; H->esE0d = e * sE0; H->inv_den0d = 1.0 / den0;
+            H->pad0 = 0.0; H->pad1 = 0.0;
+            H->a = (R)a; H->b = (R)b; H->a2 = (R)(a * a); H->b2 = (R)(b * b);
+            H->e = (R)e; H->ecE0 = (R)(e * cE0); H->esE0 = (R)(e * sE0); H->inv_den0 = (R)(1.0 / den0);
+            H->ax1 = (R)ax1; H->ax2 = (R)ax2; H->ay1 = (R)ay1; H->ay2 = (R)ay2;
+            H->rho0 = (R)rho0; H->n = (R)n;
+            const double invP = 1.0 / P;
+            const float Bh = (float)invP;
+            H->Bh = (R)Bh; H->Bl = (R)(float)(invP - (double)Bh);
+            H->dM0de = (R)(-den0 * sE0 / (1.0 - e * e) - sE0);
+            H->dM0dw = (R)(-den0 * den0 / se);
+            H->se = (R)se; H->cw = (R)cw; H->sw = (R)sw; H->cE0 = (R)cE0; H->sE0 = (R)sE0; H->pad2 = (R)0;
+            int flags = 0;
+            if (e == 0.0) flags |= kPvCircular;
+            if (e > kESwitch) flags |= kPvKepler64;
+            for (int pb = 0; pb < mp.npb; ++pb) {
+                const double k = row[6 + (mp.chromatic ? pb : 0)];
+                const double q = (1.0 + k) / (a * (1.0 - e));
+                const double df = q >= 1.0 ? 0.5 * CUDART_PI : asin(q);
+                const double hi = wrap_2pi(mean_anomaly_of_true(f0 + df, e) - M0);
+                const double lo = wrap_2pi(M0 - mean_anomaly_of_true(f0 - df, e));
+                double win = fmax(hi, lo);
+                win += 1e-5 * (1.0 + win);
+                const int ss = pbp.ss[pb];
+                const double half = 0.5 * pbp.exptime[pb] * (1.0 - 1.0 / ss);
+                double winp = win + n * (ss > 1 ? half : 0.0) * (1.0 + 1e-6);
+                if (win >= CUDART_PI) { win = 1e30; flags |= kPvNoWindow; }
+                if (winp >= CUDART_PI) winp = 1e30;
+                PB[pb].k = (R)k;
+                PB[pb].inv1pk = (R)(1.0 / (1.0 + k));
+                PB[pb].win_s = (R)win;
+                PB[pb].win_p = (R)winp;
+            }
+            H->flags = flags;
+        } else {
+            H->flags = 0;
+        }
+        H->pad3 = 0; H->pad4 = 0;
+    }
+    __syncthreads();
+    if (st_s != 0) return;
+    // profile rows, interpolated in k, divided by I_star (FP64 -> R)
+    const size_t kstride = (size_t)mp.ng;
+    const size_t bstride = (size_t)mp.nk * mp.ng;
+    for (int pb = 0; pb < mp.npb; ++pb) {
+        const int ik = ik_s[pb];
+        const double ak = ak_s[pb];
+        const double Is = Is_s[pb];
+        const double invIs = 1.0 / Is;
+        R* r0 = rows + (size_t)pb * L.rows_per_pb * L.ng_pad;
+        const int b0 = mp.ld_model == RR_LD_TABULATED ? pb : 0;
+        for (int ig = threadIdx.x; ig < L.ng_pad; ig += blockDim.x) {
+            if (ig >= mp.ng) {
+                for (int r = 0; r < L.rows_per_pb; ++r) r0[(size_t)r * L.ng_pad + ig] = (R)0;
+                continue;
+            }
+            const double* T0p = T64 + (size_t)b0 * bstride + (size_t)ik * kstride + ig;
+            double lo = T0p[0], hi = T0p[kstride];
+            if (mp.ld_model != RR_LD_TABULATED) {
+                for (int c = 0; c < mp.nldc; ++c) {
+                    const double* Tc = T64 + (size_t)(1 + c) * bstride + (size_t)ik * kstride + ig;
+                    lo += u_s[pb][c] * Tc[0];
+                    hi += u_s[pb][c] * Tc[kstride];
+                }
+            }
+            const double ldw = (1.0 - ak) * lo + ak * hi;
+            r0[ig] = (R)(ldw * invIs);
+            if (grad) {
+                r0[L.ng_pad + ig] = (R)((hi - lo) / mp.dk * invIs);
+                for (int c = 0; c < mp.nldc; ++c) {
+                    const double* Tc = T64 + (size_t)(1 + c) * bstride + (size_t)ik * kstride + ig;
+                    const double Rc = (1.0 - ak) * Tc[0] + ak * Tc[kstride];
+                    r0[(size_t)(2 + c) * L.ng_pad + ig] = (R)((Rc - ldw * invIs * istar[1 + c]) * invIs);
+                }
+            }
+        }
+    }
+}
+
+ModelParams model_params(const rr_ctx* c) {
+    ModelParams mp;
+    mp.ld_model = c->cfg.ld_model;
+    mp.npb = c->cfg.npb;
+    mp.chromatic = c->cfg.chromatic;
+    mp.nldc = c->nldc;
+    mp.nparam = c->nparam;
+    mp.nk = c->cfg.nk;
+    mp.ng = c->cfg.ng;
+    mp.nbasis = c->nbasis;
+    mp.k0 = c->cfg.k0;
+    mp.k1 = c->cfg.k1;
+    mp.dk = c->dk;
+    return mp;
+}
+
+cudaError_t launch_ld_basis(rr_ctx* c, cudaStream_t s) {
+    ModelParams mp = model_params(c);
+    rr_ld_basis_kernel<<<c->nbasis, 256, 0, s>>>(mp, c->d_mu, c->nz, c->d_tab, c->d_tab_off, c->d_basis,
+                                                 c->d_istar);
+    c->launches++;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_weights(rr_ctx* c, bool need_w, cudaStream_t s) {
+    ModelParams mp = model_params(c);
+    const size_t smem = (size_t)(2 * c->nz + 1) * sizeof(double);
+    cudaError_t e = cudaFuncSetAttribute(rr_weights_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid(c->cfg.ng, c->cfg.nk);
+    rr_weights_kernel<<<grid, 256, smem, s>>>(mp, c->d_ze, c->nz, c->d_basis, need_w ? 1 : 0, c->d_w,
+                                              c->d_T64, c->d_T32);
+    c->launches++;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pv_setup(rr_ctx* c, const double* params, int npv, const PbParams& pbp, bool grad,
+                            void* records, int32_t* pv_status, cudaStream_t s) {
+    ModelParams mp = model_params(c);
+    if (c->cfg.precision == RR_PREC_FP64) {
+        RecLayout L = make_layout<double>(c->cfg.npb, c->cfg.ng, c->nldc, grad);
+        rr_pv_setup_kernel<double><<<npv, 128, 0, s>>>(mp, pbp, params, npv, c->d_T64, c->d_istar, L,
+                                                       grad ? 1 : 0, (char*)records, pv_status);
+    } else {
+        RecLayout L = make_layout<float>(c->cfg.npb, c->cfg.ng, c->nldc, grad);
+        rr_pv_setup_kernel<float><<<npv, 128, 0, s>>>(mp, pbp, params, npv, c->d_T64, c->d_istar, L,
+                                                      grad ? 1 : 0, (char*)records, pv_status);
+    }
+    c->launches++;
+    return cudaGetLastError();
+}
+
+}  // namespace rr

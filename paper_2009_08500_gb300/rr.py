@@ -1,0 +1,293 @@
+"""Python binding of librr (argument marshalling only).
+
+Every numerical step runs in the library's CUDA kernels; this module checks
+tensor placement and dtypes, passes raw pointers and the current CUDA stream
+through the C ABI of ``include/rr.h``, and wraps the adjoint in a
+``torch.autograd.Function``.  There is no CPU fallback: without a built
+``librr.so`` or a CUDA device every entry point raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "librr.so")
+
+LD_MODELS = {"uniform": 0, "quadratic": 1, "quadratic_tri": 2, "nonlinear": 3, "tabulated": 4}
+PRECISIONS = {"fp64": 0, "mixed": 1}
+STATUS = {0: "RR_OK", 1: "RR_EINVAL", 2: "RR_ENOMEM", 3: "RR_ECUDA", 4: "RR_ESTATE", 6: "RR_ETIMEOUT"}
+TABLES = {"ze": 0, "zm": 1, "mu": 2, "weights": 3, "basis": 4, "istar": 5, "proj": 6}
+
+PV_K_RANGE, PV_E_RANGE, PV_B_RANGE, PV_P_RANGE = 1, 2, 4, 8
+PV_NONFINITE, PV_LD_INVALID, PV_A_RANGE, PV_KEPLER = 16, 32, 64, 128
+
+#: every exported entry point of include/rr.h
+EXPORTS = ["rr_create", "rr_destroy", "rr_set_ld_profile", "rr_build_weights", "rr_nparam",
+           "rr_workspace_bytes", "rr_evaluate", "rr_evaluate_grad", "rr_read_table",
+           "rr_sync_status", "rr_last_error", "rr_launch_count", "rr_profile", "rr_profile_read"]
+KERNELS = {"ld_basis": 0, "weights": 1, "pv_setup": 2, "flux": 3, "grad": 4, "grad_reduce": 5}
+
+
+class RRConfig(ctypes.Structure):
+    _fields_ = [("zcut", ctypes.c_double), ("nzin", ctypes.c_int32), ("nzlimb", ctypes.c_int32),
+                ("ng", ctypes.c_int32), ("nk", ctypes.c_int32), ("k0", ctypes.c_double),
+                ("k1", ctypes.c_double), ("npb", ctypes.c_int32), ("ld_model", ctypes.c_int32),
+                ("chromatic", ctypes.c_int32), ("precision", ctypes.c_int32), ("device", ctypes.c_int32)]
+
+
+class RRError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load librr.so and declare the C signatures (raises if it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with paper_2009_08500_gb300.build.build()")
+    L = ctypes.CDLL(path)
+    vp, i32, i64, sz, dp = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t, ctypes.POINTER(ctypes.c_double)
+    L.rr_create.argtypes = [ctypes.POINTER(RRConfig), ctypes.POINTER(vp)]
+    L.rr_destroy.argtypes = [vp]
+    L.rr_set_ld_profile.argtypes = [vp, i32, dp, dp, i32]
+    L.rr_build_weights.argtypes = [vp, vp]
+    L.rr_nparam.argtypes = [vp]
+    L.rr_nparam.restype = i32
+    L.rr_workspace_bytes.argtypes = [vp, i32, i32, i32]
+    L.rr_workspace_bytes.restype = sz
+    L.rr_evaluate.argtypes = [vp, vp, vp, i32, vp, i32, ctypes.POINTER(i32), dp, vp, vp, vp, sz, vp]
+    L.rr_evaluate_grad.argtypes = [vp, vp, vp, i32, vp, i32, ctypes.POINTER(i32), dp, vp, vp, vp, vp, sz, vp]
+    L.rr_read_table.argtypes = [vp, i32, dp, i64]
+    L.rr_read_table.restype = i64
+    L.rr_sync_status.argtypes = [vp, vp]
+    L.rr_last_error.argtypes = [vp]
+    L.rr_last_error.restype = ctypes.c_char_p
+    L.rr_launch_count.argtypes = [vp]
+    L.rr_launch_count.restype = i64
+    L.rr_profile.argtypes = [vp, i32]
+    L.rr_profile_read.argtypes = [vp, i32, dp, ctypes.POINTER(i64), i32]
+    for name in ("rr_create", "rr_destroy", "rr_set_ld_profile", "rr_build_weights", "rr_evaluate",
+                 "rr_evaluate_grad", "rr_sync_status", "rr_profile", "rr_profile_read"):
+        getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def _ptr(t: Optional[torch.Tensor]) -> Optional[int]:
+    return None if t is None else t.data_ptr()
+
+
+def _stream_handle(stream) -> Optional[int]:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream or None
+
+
+def _host_array(x, n, dtype, default):
+    if x is None:
+        x = [default] * n
+    a = np.ascontiguousarray(np.broadcast_to(np.asarray(x, dtype=dtype), (n,)))
+    return a
+
+
+class Model:
+    """A RoadRunner model context: radial grid, LD profiles and (k, g) tables on one GPU.
+
+    ld_model   'uniform' | 'quadratic' | 'quadratic_tri' | 'nonlinear' | 'tabulated'
+    npb        passbands; chromatic: one radius ratio per passband
+    precision  'mixed' (FP32 bulk, float flux) or 'fp64' (double flux)
+    grid       dict(zcut, nzin, nzlimb, ng, nk, k0, k1)
+    """
+
+    def __init__(self, ld_model: str = "quadratic", npb: int = 1, chromatic: bool = False,
+                 precision: str = "mixed", grid: Optional[dict] = None, device: int = 0):
+        from .workloads import GRID
+        g = dict(GRID if grid is None else grid)
+        self.lib = load_library()
+        if not torch.cuda.is_available():
+            raise RuntimeError("a CUDA device is required")
+        self.device = torch.device("cuda", device)
+        self.ld_model, self.npb, self.chromatic, self.precision = ld_model, npb, chromatic, precision
+        self.grid = g
+        cfg = RRConfig(g["zcut"], g["nzin"], g["nzlimb"], g["ng"], g["nk"], g["k0"], g["k1"], npb,
+                       LD_MODELS[ld_model], int(chromatic), PRECISIONS[precision], device)
+        h = ctypes.c_void_p()
+        st = self.lib.rr_create(ctypes.byref(cfg), ctypes.byref(h))
+        if st != 0:
+            raise RRError(st, self.lib.rr_last_error(None).decode())
+        self._h = h
+        self.dtype = torch.float64 if precision == "fp64" else torch.float32
+
+    # -- plumbing -------------------------------------------------------------
+    def _check(self, st: int):
+        if st != 0:
+            raise RRError(st, self.lib.rr_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self.lib.rr_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def nparam(self) -> int:
+        return int(self.lib.rr_nparam(self._h))
+
+    @property
+    def launch_count(self) -> int:
+        return int(self.lib.rr_launch_count(self._h))
+
+    def workspace_bytes(self, npv: int, npt: int, grad: bool = False) -> int:
+        return int(self.lib.rr_workspace_bytes(self._h, npv, npt, int(grad)))
+
+    def workspace(self, npv: int, npt: int, grad: bool = False) -> torch.Tensor:
+        return torch.empty(max(self.workspace_bytes(npv, npt, grad), 256), dtype=torch.uint8,
+                           device=self.device)
+
+    # -- set-up ---------------------------------------------------------------
+    def set_ld_profile(self, pb: int, mu: Sequence[float], intensity: Sequence[float]):
+        mu = np.ascontiguousarray(mu, dtype=np.float64)
+        it = np.ascontiguousarray(intensity, dtype=np.float64)
+        dp = ctypes.POINTER(ctypes.c_double)
+        self._check(self.lib.rr_set_ld_profile(self._h, pb, mu.ctypes.data_as(dp), it.ctypes.data_as(dp),
+                                               int(mu.size)))
+
+    def build(self, stream=None):
+        self._check(self.lib.rr_build_weights(self._h, _stream_handle(stream)))
+        return self
+
+    def read_table(self, which: str) -> np.ndarray:
+        n = self.lib.rr_read_table(self._h, TABLES[which], None, 0)
+        if n < 0:
+            raise RRError(4, self.lib.rr_last_error(self._h).decode())
+        out = np.empty(n, np.float64)
+        r = self.lib.rr_read_table(self._h, TABLES[which], out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), n)
+        if r < 0:
+            raise RRError(4, self.lib.rr_last_error(self._h).decode())
+        return out
+
+    def profile(self, enable: bool = True):
+        """Bracket every kernel launch with CUDA events on its stream (measurement aid)."""
+        self._check(self.lib.rr_profile(self._h, int(enable)))
+
+    def profile_read(self, reset: bool = False) -> dict:
+        """{kernel: (total_ms, launches)} of the launches timed so far."""
+        out = {}
+        for name, kind in KERNELS.items():
+            ms, n = ctypes.c_double(), ctypes.c_int64()
+            self._check(self.lib.rr_profile_read(self._h, kind, ctypes.byref(ms), ctypes.byref(n), 0))
+            out[name] = (ms.value, n.value)
+        if reset:
+            self._check(self.lib.rr_profile_read(self._h, 0, None, None, 1))
+        return out
+
+    def sync_status(self, stream=None):
+        self._check(self.lib.rr_sync_status(self._h, _stream_handle(stream)))
+
+    # -- evaluation -----------------------------------------------------------
+    def _inputs(self, times, params, pb_index):
+        dev = self.device
+        for name, t, dt in (("times", times, torch.float64), ("params", params, torch.float64)):
+            if not (isinstance(t, torch.Tensor) and t.device == dev and t.dtype == dt and t.is_contiguous()):
+                raise TypeError(f"{name} must be a contiguous {dt} tensor on {dev}")
+        if params.dim() != 2 or params.shape[1] != self.nparam:
+            raise ValueError(f"params must have shape (npv, {self.nparam})")
+        if pb_index is not None and not (pb_index.device == dev and pb_index.dtype == torch.int32
+                                         and pb_index.is_contiguous() and pb_index.numel() == times.numel()):
+            raise TypeError("pb_index must be a contiguous int32 tensor with one entry per time")
+        return times.numel(), params.shape[0]
+
+    def evaluate(self, times: torch.Tensor, params: torch.Tensor, pb_index: Optional[torch.Tensor] = None,
+                 supersampling=None, exptime=None, out: Optional[torch.Tensor] = None,
+                 pv_status: Optional[torch.Tensor] = None, workspace: Optional[torch.Tensor] = None,
+                 stream=None) -> torch.Tensor:
+        """flux[npv, npt] (float32 in 'mixed', float64 in 'fp64'), enqueued on the current stream."""
+        npt, npv = self._inputs(times, params, pb_index)
+        ss = _host_array(supersampling, self.npb, np.int32, 1)
+        ex = _host_array(exptime, self.npb, np.float64, 0.0)
+        if out is None:
+            out = torch.empty((npv, npt), dtype=self.dtype, device=self.device)
+        if workspace is None:
+            workspace = self.workspace(npv, npt, False)
+        st = self.lib.rr_evaluate(self._h, _ptr(times), _ptr(pb_index), npt, _ptr(params), npv,
+                                  ss.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                  ex.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), _ptr(out),
+                                  _ptr(pv_status), _ptr(workspace), workspace.numel(), _stream_handle(stream))
+        self._check(st)
+        return out
+
+    def evaluate_grad(self, times: torch.Tensor, params: torch.Tensor, grad_flux: torch.Tensor,
+                      pb_index: Optional[torch.Tensor] = None, supersampling=None, exptime=None,
+                      out: Optional[torch.Tensor] = None, pv_status: Optional[torch.Tensor] = None,
+                      workspace: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+        """grad_params[npv, nparam] = sum_t grad_flux[pv, t] d flux[pv, t] / d params[pv, :]."""
+        npt, npv = self._inputs(times, params, pb_index)
+        if not (grad_flux.dtype == self.dtype and grad_flux.is_contiguous() and grad_flux.shape == (npv, npt)):
+            raise TypeError(f"grad_flux must be a contiguous {self.dtype} tensor of shape ({npv}, {npt})")
+        ss = _host_array(supersampling, self.npb, np.int32, 1)
+        ex = _host_array(exptime, self.npb, np.float64, 0.0)
+        if out is None:
+            out = torch.empty((npv, self.nparam), dtype=torch.float64, device=self.device)
+        if workspace is None:
+            workspace = self.workspace(npv, npt, True)
+        st = self.lib.rr_evaluate_grad(self._h, _ptr(times), _ptr(pb_index), npt, _ptr(params), npv,
+                                       ss.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                       ex.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), _ptr(grad_flux),
+                                       _ptr(out), _ptr(pv_status), _ptr(workspace), workspace.numel(),
+                                       _stream_handle(stream))
+        self._check(st)
+        return out
+
+    def flux(self, times, params, pb_index=None, supersampling=None, exptime=None) -> torch.Tensor:
+        """Differentiable light curves (gradient w.r.t. ``params`` through the adjoint kernel)."""
+        return _RRFlux.apply(self, times, pb_index, params, supersampling, exptime)
+
+
+class _RRFlux(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, model: Model, times, pb_index, params, supersampling, exptime):
+        ctx.model = model
+        ctx.meta = (supersampling, exptime)
+        ctx.save_for_backward(times, pb_index, params)
+        return model.evaluate(times, params.detach(), pb_index, supersampling, exptime)
+
+    @staticmethod
+    def backward(ctx, gflux):
+        times, pb_index, params = ctx.saved_tensors
+        ss, ex = ctx.meta
+        g = ctx.model.evaluate_grad(times, params.detach(), gflux.contiguous().to(ctx.model.dtype),
+                                    pb_index, ss, ex)
+        return None, None, None, g.to(params.dtype), None, None
+
+
+def model_for(wl, device: int = 0) -> Model:
+    """Model context for a :class:`workloads.Workload`, with profiles set and tables built."""
+    m = Model(wl.ld_model, wl.npb, wl.chromatic, wl.precision, wl.grid, device)
+    if wl.ld_model == "tabulated":
+        for pb, (mu, it) in enumerate(wl.profiles):
+            m.set_ld_profile(pb, mu, it)
+    return m.build()
+
+
+def to_device(wl, device: int = 0):
+    """times, pb_index, params of a workload as device tensors."""
+    dev = torch.device("cuda", device)
+    return (torch.as_tensor(wl.times, dtype=torch.float64, device=dev),
+            torch.as_tensor(wl.pb_index, dtype=torch.int32, device=dev),
+            torch.as_tensor(wl.params, dtype=torch.float64, device=dev))

@@ -1,0 +1,87 @@
+"""The C-ABI library: exports, argument checks and error reporting."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2009_08500_gb300 import rr
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "rr.h")
+
+
+def _declared():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(rr_[a-z_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not os.path.exists(rr.LIB_PATH):
+        from paper_2009_08500_gb300 import build
+        build.build()
+    return rr.load_library()
+
+
+def test_library_exports_every_declared_entry_point(lib):
+    declared = _declared()
+    assert set(declared) == set(rr.EXPORTS)
+    for name in declared:
+        assert hasattr(lib, name), name
+
+
+def test_null_handles_are_rejected_without_a_device(lib):
+    assert lib.rr_nparam(None) == -1
+    assert lib.rr_workspace_bytes(None, 4, 4, 0) == 0
+    assert lib.rr_destroy(None) == 0
+    assert lib.rr_build_weights(None, None) == 1
+    assert lib.rr_read_table(None, 0, None, 0) == -1
+    assert lib.rr_launch_count(None) == 0
+    out = ctypes.c_void_p()
+    assert lib.rr_create(None, ctypes.byref(out)) == 1
+    assert b"cfg" in lib.rr_last_error(None)
+
+
+@pytest.mark.parametrize("field,value,msg", [("zcut", 1.5, b"zcut"), ("nzin", 0, b"nzin"), ("ng", 1, b"ng"),
+                                             ("k1", 0.001, b"k0"), ("npb", 40, b"npb"), ("ld_model", 9, b"ld_model"),
+                                             ("precision", 5, b"precision"), ("chromatic", 2, b"chromatic")])
+def test_create_rejects_bad_config_before_touching_the_device(lib, field, value, msg):
+    cfg = rr.RRConfig(0.7, 200, 300, 200, 60, 0.005, 0.3, 1, 1, 0, 1, 0)
+    setattr(cfg, field, value)
+    out = ctypes.c_void_p()
+    assert lib.rr_create(ctypes.byref(cfg), ctypes.byref(out)) == 1
+    assert out.value is None
+    assert msg in lib.rr_last_error(None)
+
+
+def test_status_bits_match_the_oracle():
+    from oracle import model as om
+    assert (rr.PV_K_RANGE, rr.PV_E_RANGE, rr.PV_B_RANGE, rr.PV_P_RANGE, rr.PV_NONFINITE, rr.PV_LD_INVALID,
+            rr.PV_A_RANGE, rr.PV_KEPLER) == (om.ST_K_RANGE, om.ST_E_RANGE, om.ST_B_RANGE, om.ST_P_RANGE,
+                                             om.ST_NONFINITE, om.ST_LD_INVALID, om.ST_A_RANGE, om.ST_KEPLER)
+    hdr = open(HEADER).read()
+    for name, val in [("RR_PV_K_RANGE", 1), ("RR_PV_KEPLER", 128), ("RR_MAX_PB", 32)]:
+        assert re.search(rf"#define {name}\s+{val}\b", hdr)
+
+
+def test_config_struct_layout_matches_header():
+    # zcut(8) nzin ng.. : offsets as laid out by a C compiler for the header's struct
+    assert ctypes.sizeof(rr.RRConfig) == 64
+    assert rr.RRConfig.k0.offset == 24 and rr.RRConfig.device.offset == 56
+
+
+def test_no_cpu_fallback_without_cuda(monkeypatch):
+    import torch
+    monkeypatch.setattr(torch.cuda, "is_available", lambda: False)
+    with pytest.raises(RuntimeError, match="CUDA"):
+        rr.Model("quadratic")
+
+
+def test_paper_heterogeneous_example_shapes():
+    # lcids / pbids of Sect. 4.2 flatten to one passband index per exposure
+    lcids = np.array([0, 0, 1, 1, 1, 2])
+    pbids = np.array([0, 1, 0])
+    assert list(pbids[lcids]) == [0, 0, 1, 1, 1, 0]

@@ -1,0 +1,134 @@
+"""Adjoint kernel (through the C ABI) against the oracle's chain-rule gradient.
+
+Tolerance: relative error per component with a floor of 1e-5 of the
+largest component of that parameter vector; 1e-9 for the FP64 path and
+1e-4 for the mixed path (FP32 arithmetic; see the error budget in the
+design notes).  Determinism: a pv's gradient is bitwise identical alone
+and inside a batch.
+"""
+import numpy as np
+import pytest
+
+from oracle import grad as og
+from oracle import model as om
+from paper_2009_08500_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+RTOL = {"fp64": 1e-9, "mixed": 1e-4}
+
+
+@pytest.fixture(scope="module")
+def rr():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2009_08500_gb300 import rr as _rr
+    _rr.load_library()
+    return _rr
+
+
+def rel_err(g, ref):
+    floor = 1e-5 * np.abs(ref).max(axis=1, keepdims=True)
+    return np.abs(g - ref) / np.maximum(np.abs(ref), np.maximum(floor, 1e-300))
+
+
+def gpu_vjp(rr, wl, gbar, precision):
+    import torch
+    wl.precision = precision
+    m = rr.model_for(wl)
+    t, pb, p = rr.to_device(wl)
+    gb = torch.as_tensor(gbar, dtype=m.dtype, device=t.device)
+    g = m.evaluate_grad(t, p, gb, pb, wl.supersampling, wl.exptime)
+    torch.cuda.synchronize()
+    return g.cpu().numpy()
+
+
+def oracle_vjp(wl, gbar):
+    s = om.build(wl.grid, wl.ld_model, wl.npb, wl.chromatic, wl.profiles)
+    return og.vjp(s, wl.times, wl.pb_index, wl.params, wl.supersampling, wl.exptime,
+                  np.asarray(gbar, np.float64))
+
+
+CASES = [
+    dict(ld_model="quadratic", eccentric=False),
+    dict(ld_model="quadratic", eccentric=True),
+    dict(ld_model="quadratic_tri", eccentric=True),
+    dict(ld_model="nonlinear", eccentric=True),
+    dict(ld_model="tabulated", eccentric=True, npb=3, ss=(1, 4, 9), exptime=(0.0, 0.01, 0.02)),
+    dict(ld_model="quadratic", eccentric=True, npb=2, chromatic=True, ss=(3, 1), exptime=(0.01, 0.0)),
+    dict(ld_model="uniform", eccentric=True),
+]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("case", CASES, ids=lambda c: "-".join(str(v) for v in c.values()))
+def test_adjoint_matches_oracle_chain_rule(rr, case, precision):
+    wl = W.make_small(npv=19, npt=2100, seed=17, span=6.0, **case)
+    gbar = np.random.default_rng(2).normal(size=(wl.npv, wl.npt))
+    if precision == "mixed":
+        gbar = gbar.astype(np.float32).astype(np.float64)
+    g = gpu_vjp(rr, wl, gbar, precision)
+    ref = oracle_vjp(wl, gbar)
+    assert g.shape == ref.shape == (wl.npv, wl.nparam)
+    err = rel_err(g, ref)
+    assert err.max() < RTOL[precision], (err.max(), np.unravel_index(err.argmax(), err.shape))
+
+
+def test_c3_adjoint_full_launch_sampled_rows(rr):
+    wl = W.make_c3(q1_min=1e-3)
+    gbar = np.random.default_rng(3).normal(size=(wl.npv, wl.npt)).astype(np.float32).astype(np.float64)
+    g = gpu_vjp(rr, wl, gbar, "mixed")
+    assert g.shape == (4096, 9) and np.all(np.isfinite(g))
+    rows = np.random.default_rng(4).choice(4096, 12, replace=False)
+    sub = wl.subset(4096)
+    sub.params = wl.params[rows]
+    ref = oracle_vjp(sub, gbar[rows])
+    assert rel_err(g[rows], ref).max() < RTOL["mixed"]
+
+
+def test_gradient_alone_equals_gradient_in_batch(rr):
+    import torch
+    wl = W.make_small("quadratic_tri", npv=64, npt=3000, seed=23)
+    gbar = np.random.default_rng(5).normal(size=(wl.npv, wl.npt)).astype(np.float32)
+    m = rr.model_for(wl)
+    t, pb, p = rr.to_device(wl)
+    gb = torch.as_tensor(gbar, device=t.device)
+    full = m.evaluate_grad(t, p, gb, pb)
+    for i in (0, 17, 63):
+        one = m.evaluate_grad(t, p[i:i + 1].contiguous(), gb[i:i + 1].contiguous(), pb)
+        assert torch.equal(one[0], full[i])
+    again = m.evaluate_grad(t, p, gb, pb)
+    assert torch.equal(again, full)
+
+
+def test_autograd_function_uses_the_adjoint(rr):
+    import torch
+    wl = W.make_small("nonlinear", npv=5, npt=900, seed=29)
+    m = rr.model_for(wl)
+    t, pb, p = rr.to_device(wl)
+    p = p.clone().requires_grad_(True)
+    f = m.flux(t, p, pb)
+    w = torch.randn_like(f)
+    (gp,) = torch.autograd.grad((f * w).sum(), p)
+    direct = m.evaluate_grad(t, p.detach(), w.contiguous(), pb)
+    assert torch.equal(gp, direct)
+
+
+def test_adjoint_agrees_with_central_differences_of_the_fp64_kernel(rr):
+    import torch
+    wl = W.make_small("quadratic", npv=3, npt=2000, seed=41, span=5.0)
+    wl.precision = "fp64"
+    m = rr.model_for(wl)
+    t, pb, p = rr.to_device(wl)
+    gbar = torch.randn(wl.npv, wl.npt, dtype=torch.float64, device=t.device)
+    g = m.evaluate_grad(t, p, gbar, pb).cpu().numpy()
+    steps = np.array([1e-6, 1e-7, 1e-6, 1e-6, 1e-6, 1e-6, 1e-6, 1e-6, 1e-6])
+    fd = np.zeros_like(g)
+    for j, h in enumerate(steps):
+        pp, pm = p.clone(), p.clone()
+        pp[:, j] += h
+        pm[:, j] -= h
+        d = (m.evaluate(t, pp, pb) - m.evaluate(t, pm, pb)) / (pp[:, j] - pm[:, j])[:, None]
+        fd[:, j] = (d * gbar).sum(1).cpu().numpy()
+    # a few points per pv may straddle a table node; the bound allows for them
+    assert rel_err(g, fd).max() < 1e-4

@@ -22,7 +22,10 @@ cos i = b / a (b is the nominal a cos i, without the eccentric factor).
 import numpy as np
 
 KEPLER_MAX_ITER = 100
-KEPLER_TOL = 1e-15
+# Newton stops once a step is below this (relative); convergence is quadratic,
+# so what remains after such a step is round-off.  FP64 round-off in the
+# residual keeps steps near 1e-15 for e close to 1, hence not smaller.
+KEPLER_TOL = 1e-13
 
 
 def conjunction_anomalies(e, w):

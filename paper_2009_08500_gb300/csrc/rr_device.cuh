@@ -119,7 +119,8 @@ __device__ __forceinline__ bool kepler_offset_f64(double dM, double ecE0, double
         const double S_old = S;
         S -= dx * (1.0 - V);
         V -= dx * S_old;
-        if (fabs(dx) <= 4e-15 * fabs(x) + 1e-300) return true;
+        // after a step this small the quadratic convergence has left only round-off
+        if (fabs(dx) <= 1e-12 * fabs(x) + 1e-300) return true;
     }
     return false;
 }

@@ -47,27 +47,49 @@ __device__ __forceinline__ void grad_sample(const PvHead<R>& H, const PvPb<R>& p
     const R ddz = dAdz * Ib + A * dIdg * pbc.inv1pk;
     const R ddk = dAdk * Ib + A * (Ik - dIdg * z * pbc.inv1pk * pbc.inv1pk);
 
-    // orbit partials
+    // orbit partials.  With den = r / a = 1 - e cos E and u = w + f the sky
+    // coordinates are P_x = den cos u, P_y = den sin u.  The e and w
+    // derivatives are written so that every small factor is formed directly
+    // (differences from conjunction: dsinE = sin E - sin E0, dden = den -
+    // den0), since at conjunction dP_x/de and dP/dw vanish identically and a
+    // difference of O(1) terms would lose all FP32 digits there:
+    //   dE/de  = (dsinE - den0 sE0 / (1 - e^2)) / den
+    //   du/de  = [(den0 dsinE + dden sin E) / se + se dsinE] / den^2
+    //   dE/dw  = dM0/dw / den = -den0^2 / (se den)
+    //   du/dw  = dden (den + den0) / den^2
+    //   d den  = -cos E de + e sin E dE
+    //   dP_x = d den P_x / den - P_y du,  dP_y = d den P_y / den + P_x du
     const R omV = one - V;
-    const R den = (one - H.ecE0) + H.ecE0 * V + H.esE0 * S;
+    const R dden = H.ecE0 * V + H.esE0 * S;
+    const R den0 = one - H.ecE0;
+    const R den = den0 + dden;
     const R invden = one / den;
-    const R sinE = H.sE0 * omV + H.cE0 * S;
+    const R dsinE = H.cE0 * S - H.sE0 * V;
+    const R sinE = H.sE0 + dsinE;
+    const R cosE = H.cE0 * omV - H.sE0 * S;
     const R dPxdE = H.ax1 * S + H.ax2 * omV;
     const R dPydE = H.ay1 * S + H.ay2 * omV;
     const R invz = one / z;
     const R zE = (H.a2 * Px * dPxdE + H.b2 * Py * dPydE) * invz;
-    const R es = H.e / H.se;
-    const R dPxde = -H.cw + H.sw * es * sinE;
-    const R dPyde = -H.sw - H.cw * es * sinE;
-    const R zeE = (H.a2 * Px * dPxde + H.b2 * Py * dPyde) * invz;
+    const R inv_se = H.inv_se;
+    const R ce = -(H.dM0de + H.sE0);                    // den0 sE0 / (1 - e^2)
+    const R dEde = (dsinE - ce) * invden;
+    const R ddende = -cosE + H.e * sinE * dEde;
+    const R dude = ((den0 * dsinE + dden * sinE) * inv_se + H.se * dsinE) * invden * invden;
+    const R dPxde = ddende * Px * invden - Py * dude;
+    const R dPyde = ddende * Py * invden + Px * dude;
+    const R dEdw = H.dM0dw * invden;
+    const R ddendw = H.e * sinE * dEdw;
+    const R dudw = dden * (den + den0) * invden * invden;
+    const R dPxdw = ddendw * Px * invden - Py * dudw;
+    const R dPydw = ddendw * Py * invden + Px * dudw;
     const R c = gb * ddz;
     acc.o[0] += c * (zE * (-H.n * invden));
     acc.o[1] += c * (zE * (-H.n * psi_tot * invden));
     acc.o[2] += c * (H.a * Px * Px * invz);
     acc.o[3] += c * (H.b * Py * Py * invz);
-    acc.o[4] += c * (zE * ((H.dM0de + sinE) * invden) + zeE);
-    if (!(H.flags & kPvCircular))
-        acc.o[5] += c * (zE * (H.dM0dw * invden) + (H.b2 - H.a2) * Px * Py * invz);
+    acc.o[4] += c * ((H.a2 * Px * dPxde + H.b2 * Py * dPyde) * invz);
+    acc.o[5] += c * ((H.a2 * Px * dPxdw + H.b2 * Py * dPydw) * invz);
     const R gk = gb * ddk;
     if (DEP) dep[(kslot - 6) * kBlock] += gk; else acc.k += gk;
     #pragma unroll

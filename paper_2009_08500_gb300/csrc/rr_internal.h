@@ -54,7 +54,7 @@ struct alignas(16) PvHead {
     R ax1, ax2, ay1, ay2;
     R rho0, n, Bh, Bl;             // n = 2 pi / P; Bh + Bl = 1 / P (float-float)
     R dM0de, dM0dw, se, cw;        // dM0/de, dM0/dw, sqrt(1 - e^2), cos w
-    R sw, cE0, sE0, pad2;
+    R sw, cE0, sE0, inv_se;        // sin w, cos E0, sin E0, 1 / sqrt(1 - e^2)
     int32_t flags, status, pad3, pad4;
 };
 

@@ -162,7 +162,8 @@ __global__ void __launch_bounds__(256) rr_weights_kernel(ModelParams mp, const d
 }
 
 // ---------------------------------------------------------------------------
-// Per-call parameter-vector records (FP64 arithmetic, rounded to R).
+// Per-call parameter-vector records.  Validation, orbit constants and
+// windows in FP64 (rounded to R); profile rows in R (FP32 in the mixed form).
 //
 // Validates the row (the RR_PV_* bits), derives the orbit constants of the
 // offset-from-conjunction form (see PvHead), the transit window, and for
@@ -189,86 +190,103 @@ __device__ double mean_anomaly_of_true(double f, double e) {
     return E - e * sin(E);
 }
 
+// Pvs per CTA of the set-up kernel: the FP64 scalar work of a pv runs on one
+// thread (kSetupPv threads in parallel per CTA); the profile rows of all
+// kSetupPv pvs are then computed by the whole CTA.
+constexpr int kSetupPv = 8;
+
 template <typename R>
-__global__ void __launch_bounds__(128) rr_pv_setup_kernel(ModelParams mp, PbParams pbp,
+__global__ void __launch_bounds__(256) rr_pv_setup_kernel(ModelParams mp, PbParams pbp,
                                                           const double* __restrict__ params, int npv,
-                                                          const double* __restrict__ T64,
-                                                          const double* __restrict__ istar,
+                                                          const R* __restrict__ T, const double* __restrict__ istar,
                                                           RecLayout L, int grad, char* __restrict__ records,
                                                           int32_t* __restrict__ pv_status) {
-    __shared__ double u_s[RR_MAX_PB][4];
-    __shared__ double Is_s[RR_MAX_PB];
-    __shared__ int ik_s[RR_MAX_PB];
-    __shared__ double ak_s[RR_MAX_PB];
-    __shared__ int st_s;
-    const int pv = blockIdx.x;
-    if (pv >= npv) return;
-    const double* row = params + (size_t)pv * mp.nparam;
-    char* rec = records + (size_t)pv * L.bytes;
-    PvHead<R>* H = reinterpret_cast<PvHead<R>*>(rec);
-    PvPb<R>* PB = reinterpret_cast<PvPb<R>*>(rec + L.off_pb);
-    R* rows = reinterpret_cast<R*>(rec + L.off_rows);
+    __shared__ double u_s[kSetupPv][RR_MAX_PB][4];
+    __shared__ double Is_s[kSetupPv][RR_MAX_PB];
+    __shared__ double ak_s[kSetupPv][RR_MAX_PB];
+    __shared__ int ik_s[kSetupPv][RR_MAX_PB];
+    __shared__ int st_s[kSetupPv];
+    const int pv0 = blockIdx.x * kSetupPv;
+    const int nloc = min(kSetupPv, npv - pv0);
     const int nkp = mp.chromatic ? mp.npb : 1;
+    const int tid = threadIdx.x;
+    if (tid < kSetupPv) st_s[tid] = 0;
+    __syncthreads();
 
-    if (threadIdx.x == 0) {
-        const double T0 = row[0], P = row[1], a = row[2], b = row[3], e = row[4], w = row[5];
+    // (1) per (pv, passband): validity, LD coefficients, I_star, k cell -- one thread each
+    for (int t = tid; t < nloc * mp.npb; t += blockDim.x) {
+        const int lp = t / mp.npb, pb = t % mp.npb;
+        const double* row = params + (size_t)(pv0 + lp) * mp.nparam;
         int st = 0;
+        const double* c = row + 6 + nkp + pb * mp.nldc;
+        double u[4] = {0, 0, 0, 0};
+        if (mp.ld_model == RR_LD_QUADRATIC_TRI) {
+            const double q1 = c[0], q2 = c[1];
+            if (!(q1 >= 0.0 && q1 <= 1.0 && q2 >= 0.0 && q2 <= 1.0)) st |= RR_PV_LD_INVALID;
+            const double sq = sqrt(fmax(q1, 0.0));
+            u[0] = 2.0 * sq * q2;
+            u[1] = sq * (1.0 - 2.0 * q2);
+        } else {
+            for (int j = 0; j < mp.nldc; ++j) u[j] = c[j];
+        }
+        double Is;
+        if (mp.ld_model == RR_LD_TABULATED) {
+            Is = istar[pb];
+        } else {
+            Is = istar[0];
+            for (int j = 0; j < mp.nldc; ++j) Is += u[j] * istar[1 + j];
+        }
+        if (!(Is > 0.0)) st |= RR_PV_LD_INVALID;
+        const double k = row[6 + (mp.chromatic ? pb : 0)];
+        if (!(k >= mp.k0 && k <= mp.k1)) st |= RR_PV_K_RANGE;
+        const double x = (k - mp.k0) / mp.dk;
+        int ik = (int)floor(x);
+        ik = ik < 0 ? 0 : (ik > mp.nk - 2 ? mp.nk - 2 : ik);
+        for (int j = 0; j < 4; ++j) u_s[lp][pb][j] = u[j];
+        Is_s[lp][pb] = Is;
+        ik_s[lp][pb] = ik;
+        ak_s[lp][pb] = x - ik;
+        if (st) atomicOr(&st_s[lp], st);
+    }
+    __syncthreads();
+
+    // (2) per pv: orbit constants and transit windows (FP64)
+    if (tid < nloc) {
+        const int pv = pv0 + tid;
+        const double* row = params + (size_t)pv * mp.nparam;
+        char* rec = records + (size_t)pv * L.bytes;
+        PvHead<R>* H = reinterpret_cast<PvHead<R>*>(rec);
+        PvPb<R>* PB = reinterpret_cast<PvPb<R>*>(rec + L.off_pb);
+        const double T0 = row[0], P = row[1], a = row[2], b = row[3], e = row[4], w = row[5];
         bool finite = true;
         for (int j = 0; j < mp.nparam; ++j) finite = finite && isfinite(row[j]);
+        int st = st_s[tid];
         if (!finite) {
             st = RR_PV_NONFINITE;
         } else {
-            for (int j = 0; j < nkp; ++j) {
-                const double k = row[6 + j];
-                if (k < mp.k0 || k > mp.k1) st |= RR_PV_K_RANGE;
-            }
             if (!(e >= 0.0 && e < 1.0)) st |= RR_PV_E_RANGE;
             if (!(P > 0.0)) st |= RR_PV_P_RANGE;
             if (!(a > 1.0)) st |= RR_PV_A_RANGE;
             if (!(b >= 0.0 && b <= a)) st |= RR_PV_B_RANGE;
-            for (int pb = 0; pb < mp.npb; ++pb) {
-                const double* c = row + 6 + nkp + pb * mp.nldc;
-                double u[4] = {0, 0, 0, 0};
-                bool ldbad = false;
-                if (mp.ld_model == RR_LD_QUADRATIC_TRI) {
-                    const double q1 = c[0], q2 = c[1];
-                    ldbad = !(q1 >= 0.0 && q1 <= 1.0 && q2 >= 0.0 && q2 <= 1.0);
-                    const double sq = sqrt(fmax(q1, 0.0));
-                    u[0] = 2.0 * sq * q2;
-                    u[1] = sq * (1.0 - 2.0 * q2);
-                } else {
-                    for (int j = 0; j < mp.nldc; ++j) u[j] = c[j];
-                }
-                double Is;
-                if (mp.ld_model == RR_LD_TABULATED) {
-                    Is = istar[pb];
-                } else {
-                    Is = istar[0];
-                    for (int j = 0; j < mp.nldc; ++j) Is += u[j] * istar[1 + j];
-                }
-                if (ldbad || !(Is > 0.0)) st |= RR_PV_LD_INVALID;
-                for (int j = 0; j < 4; ++j) u_s[pb][j] = u[j];
-                Is_s[pb] = Is;
-                const double k = row[6 + (mp.chromatic ? pb : 0)];
-                const double x = (k - mp.k0) / mp.dk;
-                int ik = (int)floor(x);
-                ik = ik < 0 ? 0 : (ik > mp.nk - 2 ? mp.nk - 2 : ik);
-                ik_s[pb] = ik;
-                ak_s[pb] = x - ik;
-            }
         }
-        st_s = st;
+        st_s[tid] = st;
         H->status = st;
         if (pv_status) pv_status[pv] = st;
+        H->flags = 0;
+        H->pad3 = 0;
+        H->pad4 = 0;
         if (st == 0) {
             const double f0 = 0.5 * CUDART_PI - w;
             const double E0 = 2.0 * atan2(sqrt(1.0 - e) * sin(0.5 * f0), sqrt(1.0 + e) * cos(0.5 * f0));
-            const double cE0 = cos(E0), sE0 = sin(E0);
+            double sE0, cE0;
+            sincos(E0, &sE0, &cE0);
             const double M0 = E0 - e * sE0;
             const double se = sqrt(1.0 - e * e);
-            const double cw = cos(w), sw = sin(w);
+            double sw, cw;
+            sincos(w, &sw, &cw);
             const double den0 = 1.0 - e * cE0;
-            const double n = 2.0 * CUDART_PI / P;
+            const double invP = 1.0 / P;
+            const double n = 2.0 * CUDART_PI * invP;
             double ax1, ax2, ay1, ay2, rho0;
             if (e == 0.0) {
                 ax1 = 0.0; ax2 = -1.0; ay1 = -1.0; ay2 = 0.0; rho0 = 1.0;
@@ -279,25 +297,26 @@ __global__ void __launch_bounds__(128) rr_pv_setup_kernel(ModelParams mp, PbPara
                 ay2 = -sw * sE0 + cw * se * cE0;
                 rho0 = den0;
             }
-            H->T0 = T0; H->P = P; H->invP = 1.0 / P;
-            H->ecE0d = e * cE0; H->esE0d = e * sE0; H->inv_den0d = 1.0 / den0;
+            const double inv_den0 = 1.0 / den0;
+            H->T0 = T0; H->P = P; H->invP = invP;
+            H->ecE0d = e * cE0; H->esE0d = e * sE0; H->inv_den0d = inv_den0;
             H->pad0 = 0.0; H->pad1 = 0.0;
             H->a = (R)a; H->b = (R)b; H->a2 = (R)(a * a); H->b2 = (R)(b * b);
-            H->e = (R)e; H->ecE0 = (R)(e * cE0); H->esE0 = (R)(e * sE0); H->inv_den0 = (R)(1.0 / den0);
+            H->e = (R)e; H->ecE0 = (R)(e * cE0); H->esE0 = (R)(e * sE0); H->inv_den0 = (R)inv_den0;
             H->ax1 = (R)ax1; H->ax2 = (R)ax2; H->ay1 = (R)ay1; H->ay2 = (R)ay2;
             H->rho0 = (R)rho0; H->n = (R)n;
-            const double invP = 1.0 / P;
             const float Bh = (float)invP;
             H->Bh = (R)Bh; H->Bl = (R)(float)(invP - (double)Bh);
             H->dM0de = (R)(-den0 * sE0 / (1.0 - e * e) - sE0);
             H->dM0dw = (R)(-den0 * den0 / se);
-            H->se = (R)se; H->cw = (R)cw; H->sw = (R)sw; H->cE0 = (R)cE0; H->sE0 = (R)sE0; H->pad2 = (R)0;
+            H->se = (R)se; H->cw = (R)cw; H->sw = (R)sw; H->cE0 = (R)cE0; H->sE0 = (R)sE0; H->inv_se = (R)(1.0 / se);
             int flags = 0;
             if (e == 0.0) flags |= kPvCircular;
             if (e > kESwitch) flags |= kPvKepler64;
+            const double ra = a * (1.0 - e);
             for (int pb = 0; pb < mp.npb; ++pb) {
                 const double k = row[6 + (mp.chromatic ? pb : 0)];
-                const double q = (1.0 + k) / (a * (1.0 - e));
+                const double q = (1.0 + k) / ra;
                 const double df = q >= 1.0 ? 0.5 * CUDART_PI : asin(q);
                 const double hi = wrap_2pi(mean_anomaly_of_true(f0 + df, e) - M0);
                 const double lo = wrap_2pi(M0 - mean_anomaly_of_true(f0 - df, e));
@@ -314,46 +333,48 @@ __global__ void __launch_bounds__(128) rr_pv_setup_kernel(ModelParams mp, PbPara
                 PB[pb].win_p = (R)winp;
             }
             H->flags = flags;
-        } else {
-            H->flags = 0;
         }
-        H->pad3 = 0; H->pad4 = 0;
     }
     __syncthreads();
-    if (st_s != 0) return;
-    // profile rows, interpolated in k, divided by I_star (FP64 -> R)
+
+    // (3) profile rows of all pvs of the CTA: the k-interpolated combination of
+    // the basis projections, divided by I_star (arithmetic in R)
     const size_t kstride = (size_t)mp.ng;
     const size_t bstride = (size_t)mp.nk * mp.ng;
-    for (int pb = 0; pb < mp.npb; ++pb) {
-        const int ik = ik_s[pb];
-        const double ak = ak_s[pb];
-        const double Is = Is_s[pb];
-        const double invIs = 1.0 / Is;
-        R* r0 = rows + (size_t)pb * L.rows_per_pb * L.ng_pad;
+    const R inv_dk = (R)(1.0 / mp.dk);
+    const int per_pv = mp.npb * L.ng_pad;
+    for (int t = tid; t < nloc * per_pv; t += blockDim.x) {
+        const int lp = t / per_pv, rem = t % per_pv;
+        const int pb = rem / L.ng_pad, ig = rem % L.ng_pad;
+        if (st_s[lp] != 0) continue;
+        R* r0 = reinterpret_cast<R*>(records + (size_t)(pv0 + lp) * L.bytes + L.off_rows) +
+                (size_t)pb * L.rows_per_pb * L.ng_pad;
+        if (ig >= mp.ng) {
+            for (int r = 0; r < L.rows_per_pb; ++r) r0[(size_t)r * L.ng_pad + ig] = (R)0;
+            continue;
+        }
+        const int ik = ik_s[lp][pb];
+        const R ak = (R)ak_s[lp][pb];
+        const R invIs = (R)(1.0 / Is_s[lp][pb]);
         const int b0 = mp.ld_model == RR_LD_TABULATED ? pb : 0;
-        for (int ig = threadIdx.x; ig < L.ng_pad; ig += blockDim.x) {
-            if (ig >= mp.ng) {
-                for (int r = 0; r < L.rows_per_pb; ++r) r0[(size_t)r * L.ng_pad + ig] = (R)0;
-                continue;
+        const R* T0p = T + (size_t)b0 * bstride + (size_t)ik * kstride + ig;
+        R lo = T0p[0], hi = T0p[kstride];
+        if (mp.ld_model != RR_LD_TABULATED) {
+            for (int c = 0; c < mp.nldc; ++c) {
+                const R* Tc = T + (size_t)(1 + c) * bstride + (size_t)ik * kstride + ig;
+                const R uc = (R)u_s[lp][pb][c];
+                lo += uc * Tc[0];
+                hi += uc * Tc[kstride];
             }
-            const double* T0p = T64 + (size_t)b0 * bstride + (size_t)ik * kstride + ig;
-            double lo = T0p[0], hi = T0p[kstride];
-            if (mp.ld_model != RR_LD_TABULATED) {
-                for (int c = 0; c < mp.nldc; ++c) {
-                    const double* Tc = T64 + (size_t)(1 + c) * bstride + (size_t)ik * kstride + ig;
-                    lo += u_s[pb][c] * Tc[0];
-                    hi += u_s[pb][c] * Tc[kstride];
-                }
-            }
-            const double ldw = (1.0 - ak) * lo + ak * hi;
-            r0[ig] = (R)(ldw * invIs);
-            if (grad) {
-                r0[L.ng_pad + ig] = (R)((hi - lo) / mp.dk * invIs);
-                for (int c = 0; c < mp.nldc; ++c) {
-                    const double* Tc = T64 + (size_t)(1 + c) * bstride + (size_t)ik * kstride + ig;
-                    const double Rc = (1.0 - ak) * Tc[0] + ak * Tc[kstride];
-                    r0[(size_t)(2 + c) * L.ng_pad + ig] = (R)((Rc - ldw * invIs * istar[1 + c]) * invIs);
-                }
+        }
+        const R ldw_n = ((R(1) - ak) * lo + ak * hi) * invIs;
+        r0[ig] = ldw_n;
+        if (grad) {
+            r0[L.ng_pad + ig] = (hi - lo) * (inv_dk * invIs);
+            for (int c = 0; c < mp.nldc; ++c) {
+                const R* Tc = T + (size_t)(1 + c) * bstride + (size_t)ik * kstride + ig;
+                const R Rc = (R(1) - ak) * Tc[0] + ak * Tc[kstride];
+                r0[(size_t)(2 + c) * L.ng_pad + ig] = (Rc - ldw_n * (R)istar[1 + c]) * invIs;
             }
         }
     }
@@ -399,14 +420,15 @@ cudaError_t launch_weights(rr_ctx* c, bool need_w, cudaStream_t s) {
 cudaError_t launch_pv_setup(rr_ctx* c, const double* params, int npv, const PbParams& pbp, bool grad,
                             void* records, int32_t* pv_status, cudaStream_t s) {
     ModelParams mp = model_params(c);
+    const int blocks = (npv + kSetupPv - 1) / kSetupPv;
     if (c->cfg.precision == RR_PREC_FP64) {
         RecLayout L = make_layout<double>(c->cfg.npb, c->cfg.ng, c->nldc, grad);
-        rr_pv_setup_kernel<double><<<npv, 128, 0, s>>>(mp, pbp, params, npv, c->d_T64, c->d_istar, L,
-                                                       grad ? 1 : 0, (char*)records, pv_status);
+        rr_pv_setup_kernel<double><<<blocks, 256, 0, s>>>(mp, pbp, params, npv, c->d_T64, c->d_istar, L,
+                                                          grad ? 1 : 0, (char*)records, pv_status);
     } else {
         RecLayout L = make_layout<float>(c->cfg.npb, c->cfg.ng, c->nldc, grad);
-        rr_pv_setup_kernel<float><<<npv, 128, 0, s>>>(mp, pbp, params, npv, c->d_T64, c->d_istar, L,
-                                                      grad ? 1 : 0, (char*)records, pv_status);
+        rr_pv_setup_kernel<float><<<blocks, 256, 0, s>>>(mp, pbp, params, npv, c->d_T32, c->d_istar, L,
+                                                         grad ? 1 : 0, (char*)records, pv_status);
     }
     c->launches++;
     return cudaGetLastError();

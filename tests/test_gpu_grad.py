@@ -1,10 +1,10 @@
 """Adjoint kernel (through the C ABI) against the oracle's chain-rule gradient.
 
-Tolerance: relative error per component with a floor of 1e-5 of the
-largest component of that parameter vector; 1e-9 for the FP64 path and
-1e-4 for the mixed path (FP32 arithmetic; see the error budget in the
-design notes).  Determinism: a pv's gradient is bitwise identical alone
-and inside a batch.
+Each component g_j = sum_t gbar_t J_tj is a sum of terms of both signs, so
+its rounding error scales with S_j = sum_t |gbar_t J_tj| (the sum's
+condition), not with |g_j|.  The bound is |g_j - ref_j| <= rtol S_j with
+rtol 1e-10 (FP64 path) and 1e-5 (mixed path).  Determinism: a pv's
+gradient is bitwise identical alone and inside a batch.
 """
 import numpy as np
 import pytest
@@ -15,7 +15,7 @@ from paper_2009_08500_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 
-RTOL = {"fp64": 1e-9, "mixed": 1e-4}
+RTOL = {"fp64": 1e-10, "mixed": 1e-5}
 
 
 @pytest.fixture(scope="module")
@@ -27,9 +27,10 @@ def rr():
     return _rr
 
 
-def rel_err(g, ref):
-    floor = 1e-5 * np.abs(ref).max(axis=1, keepdims=True)
-    return np.abs(g - ref) / np.maximum(np.abs(ref), np.maximum(floor, 1e-300))
+def cond_err(g, ref, scale):
+    """|g - ref| / S with S = sum_t |gbar_t J_tj| (tiny S floored at 1e-12 of the row's largest)."""
+    floor = 1e-12 * scale.max(axis=1, keepdims=True)
+    return np.abs(g - ref) / np.maximum(scale, np.maximum(floor, 1e-300))
 
 
 def gpu_vjp(rr, wl, gbar, precision):
@@ -44,9 +45,16 @@ def gpu_vjp(rr, wl, gbar, precision):
 
 
 def oracle_vjp(wl, gbar):
+    """Oracle gradient and the condition scale S of every component."""
     s = om.build(wl.grid, wl.ld_model, wl.npb, wl.chromatic, wl.profiles)
-    return og.vjp(s, wl.times, wl.pb_index, wl.params, wl.supersampling, wl.exptime,
-                  np.asarray(gbar, np.float64))
+    gbar = np.asarray(gbar, np.float64)
+    ref = np.zeros(wl.params.shape)
+    scale = np.zeros(wl.params.shape)
+    for p in range(wl.npv):
+        J = og.jacobian(s, wl.times, wl.pb_index, wl.params[p], wl.supersampling, wl.exptime)
+        ref[p] = gbar[p] @ J
+        scale[p] = np.abs(gbar[p]) @ np.abs(J)
+    return ref, scale
 
 
 CASES = [
@@ -68,9 +76,9 @@ def test_adjoint_matches_oracle_chain_rule(rr, case, precision):
     if precision == "mixed":
         gbar = gbar.astype(np.float32).astype(np.float64)
     g = gpu_vjp(rr, wl, gbar, precision)
-    ref = oracle_vjp(wl, gbar)
+    ref, scale = oracle_vjp(wl, gbar)
     assert g.shape == ref.shape == (wl.npv, wl.nparam)
-    err = rel_err(g, ref)
+    err = cond_err(g, ref, scale)
     assert err.max() < RTOL[precision], (err.max(), np.unravel_index(err.argmax(), err.shape))
 
 
@@ -82,8 +90,8 @@ def test_c3_adjoint_full_launch_sampled_rows(rr):
     rows = np.random.default_rng(4).choice(4096, 12, replace=False)
     sub = wl.subset(4096)
     sub.params = wl.params[rows]
-    ref = oracle_vjp(sub, gbar[rows])
-    assert rel_err(g[rows], ref).max() < RTOL["mixed"]
+    ref, scale = oracle_vjp(sub, gbar[rows])
+    assert cond_err(g[rows], ref, scale).max() < RTOL["mixed"]
 
 
 def test_gradient_alone_equals_gradient_in_batch(rr):
@@ -131,4 +139,5 @@ def test_adjoint_agrees_with_central_differences_of_the_fp64_kernel(rr):
         d = (m.evaluate(t, pp, pb) - m.evaluate(t, pm, pb)) / (pp[:, j] - pm[:, j])[:, None]
         fd[:, j] = (d * gbar).sum(1).cpu().numpy()
     # a few points per pv may straddle a table node; the bound allows for them
-    assert rel_err(g, fd).max() < 1e-4
+    floor = 1e-5 * np.abs(fd).max(axis=1, keepdims=True)
+    assert (np.abs(g - fd) / np.maximum(np.abs(fd), floor)).max() < 1e-4

@@ -202,7 +202,8 @@ int64_t rr_launch_count(const rr_ctx* ctx);
 #define RR_KERNEL_FLUX 3
 #define RR_KERNEL_GRAD 4
 #define RR_KERNEL_GRAD_REDUCE 5
-#define RR_KERNEL_KINDS 6
+#define RR_KERNEL_POINTS 6
+#define RR_KERNEL_KINDS 7
 
 /* Per-kernel timing (measurement aid).  While enabled, every kernel launch
  * of this context is bracketed by two CUDA events recorded on the launching

@@ -70,6 +70,7 @@ void free_all(rr_ctx* c) {
     cudaFree(c->d_istar);
     cudaFree(c->d_T64);
     cudaFree(c->d_T32);
+    cudaFree(c->d_DT32);
     cudaFree(c->d_tab);
     cudaFree(c->d_tab_off);
     cudaFree(c->d_err);
@@ -159,6 +160,20 @@ size_t records_bytes(const rr_ctx* c, int npv, bool grad) {
                                                    : make_layout<float>(c->cfg.npb, c->cfg.ng, c->nldc, grad).bytes;
     return (size_t)npv * b;
 }
+
+WsLayout ws_layout(const rr_ctx* c, int npv, int npt, bool grad) {
+    WsLayout w;
+    w.rec = 0;
+    size_t off = align256(records_bytes(c, npv, grad));
+    w.pts_dt = off;
+    if (c->cfg.precision == RR_PREC_MIXED) off += align256((size_t)npt * 8);
+    w.pts_pb = off;
+    if (c->cfg.precision == RR_PREC_MIXED) off += align256((size_t)npt * 4);
+    w.part = off;
+    if (grad) off += align256(partials_bytes(c, npv, npt));
+    w.total = off > 0 ? off : 256;
+    return w;
+}
 }  // namespace rr
 
 extern "C" {
@@ -199,7 +214,7 @@ rr_status rr_create(const rr_config* cfg, rr_ctx** out) {
     c->tab_I.resize(k.npb);
     const size_t nT = (size_t)c->nbasis * k.nk * k.ng;
     if (dalloc(&c->d_ze, c->nz + 1) || dalloc(&c->d_mu, c->nz) || dalloc(&c->d_basis, (size_t)c->nbasis * c->nz) ||
-        dalloc(&c->d_istar, c->nbasis) || dalloc(&c->d_T64, nT) || dalloc(&c->d_T32, nT) ||
+        dalloc(&c->d_istar, c->nbasis) || dalloc(&c->d_T64, nT) || dalloc(&c->d_T32, nT) || dalloc(&c->d_DT32, nT) ||
         dalloc(&c->d_tab_off, k.npb + 1) || dalloc(&c->d_err, 1)) {
         free_all(c);
         delete c;
@@ -286,9 +301,7 @@ int32_t rr_nparam(const rr_ctx* c) { return c ? c->nparam : -1; }
 
 size_t rr_workspace_bytes(const rr_ctx* c, int32_t npv, int32_t npt, int32_t with_grad) {
     if (!c || npv < 0 || npt < 0) return 0;
-    size_t b = align256(records_bytes(c, npv, with_grad != 0));
-    if (with_grad) b += align256(partials_bytes(c, npv, npt));
-    return b > 0 ? b : 256;
+    return ws_layout(c, npv, npt, with_grad != 0).total;
 }
 
 rr_status rr_evaluate(rr_ctx* c, const double* times, const int32_t* pb_index, int32_t npt, const double* params,
@@ -316,8 +329,17 @@ rr_status rr_evaluate(rr_ctx* c, const double* times, const int32_t* pb_index, i
     if ((e = timed(c, RR_KERNEL_PV_SETUP, s,
                    [&] { return launch_pv_setup(c, params, npv, pbp, false, ws, pv_status, s); })) != cudaSuccess)
         return cuda_fail(c, e, "parameter-vector set-up kernel");
-    if ((e = timed(c, RR_KERNEL_FLUX, s,
-                   [&] { return launch_flux(c, times, pb_index, npt, npv, pbp, ws, flux, pv_status, s); })) != cudaSuccess)
+    const WsLayout W = ws_layout(c, npv, npt, false);
+    char* wb = (char*)ws;
+    if (c->cfg.precision == RR_PREC_MIXED &&
+        (e = timed(c, RR_KERNEL_POINTS, s, [&] {
+             return launch_points(c, times, pb_index, npt, wb + W.pts_dt, wb + W.pts_pb, s);
+         })) != cudaSuccess)
+        return cuda_fail(c, e, "point preparation kernel");
+    if ((e = timed(c, RR_KERNEL_FLUX, s, [&] {
+             return launch_flux(c, times, pb_index, wb + W.pts_dt, wb + W.pts_pb, npt, npv, pbp, ws, flux,
+                                pv_status, s);
+         })) != cudaSuccess)
         return cuda_fail(c, e, "flux kernel");
     return RR_OK;
 }
@@ -344,9 +366,17 @@ rr_status rr_evaluate_grad(rr_ctx* c, const double* times, const int32_t* pb_ind
     if ((e = timed(c, RR_KERNEL_PV_SETUP, s,
                    [&] { return launch_pv_setup(c, params, npv, pbp, true, ws, pv_status, s); })) != cudaSuccess)
         return cuda_fail(c, e, "parameter-vector set-up kernel");
-    double* partials = (double*)((char*)ws + align256(records_bytes(c, npv, true)));
+    const WsLayout W = ws_layout(c, npv, npt, true);
+    char* wb = (char*)ws;
+    void* partials = wb + W.part;
+    if (c->cfg.precision == RR_PREC_MIXED &&
+        (e = timed(c, RR_KERNEL_POINTS, s, [&] {
+             return launch_points(c, times, pb_index, npt, wb + W.pts_dt, wb + W.pts_pb, s);
+         })) != cudaSuccess)
+        return cuda_fail(c, e, "point preparation kernel");
     if ((e = timed(c, RR_KERNEL_GRAD, s, [&] {
-             return launch_grad(c, times, pb_index, npt, npv, pbp, ws, grad_flux, partials, pv_status, s);
+             return launch_grad(c, times, pb_index, wb + W.pts_dt, wb + W.pts_pb, npt, npv, pbp, ws, grad_flux,
+                                partials, pv_status, s);
          })) != cudaSuccess)
         return cuda_fail(c, e, "adjoint kernel");
     if ((e = timed(c, RR_KERNEL_GRAD_REDUCE, s, [&] {

@@ -206,6 +206,12 @@ struct Phase32 {
     float m;            // integer cycles removed by the reduction
 };
 
+// Round to the nearest integer (ties to even) for |x| < 2^22 with two FP32
+// additions: adding 1.5 * 2^23 leaves no fraction bits in the sum.
+__device__ __forceinline__ float round_nearest(float x) {
+    return __fsub_rn(__fadd_rn(x, 12582912.0f), 12582912.0f);
+}
+
 // Precise phase (cycles) of a time relative to the nearest conjunction:
 // psi = A + dt / P with dt = dh + dl, A = Ah + Al, 1 / P = Bh + Bl.
 __device__ __forceinline__ Phase32 precise_phase(float dh, float dl, float Ah, float Al, float Bh,
@@ -217,7 +223,7 @@ __device__ __forceinline__ Phase32 precise_phase(float dh, float dl, float Ah, f
     const float s = p + Ah;              // two-sum of p and Ah
     const float bb = s - p;
     const float err = (p - (s - bb)) + (Ah - bb);
-    const float m = rintf(s);
+    const float m = round_nearest(s);
     Phase32 r;
     r.fr_h = s - m;                      // exact (m is the nearest integer to s)
     r.fr_l = err + (Al + e);
@@ -283,6 +289,54 @@ __device__ __forceinline__ Orbit64 orbit64(const PvHead<double>& H, double dM) {
 __device__ __forceinline__ float warp_max(float v) {
     for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
     return v;
+}
+
+template <typename T>
+__device__ __forceinline__ T sel4(const T (&v)[4], int q) {
+    return q == 0 ? v[0] : (q == 1 ? v[1] : (q == 2 ? v[2] : v[3]));
+}
+
+// Thread t of a CTA owns the 4 consecutive times pt0 + 4t .. pt0 + 4t + 3.
+__device__ __forceinline__ void load_points(const float2* __restrict__ pdt, const int32_t* __restrict__ ppb,
+                                            int p0, int npt, float (&dh)[4], float (&dl)[4], int (&pbv)[4]) {
+    if (p0 + 3 < npt) {
+        const float4 a = __ldg(reinterpret_cast<const float4*>(pdt + p0));
+        const float4 b = __ldg(reinterpret_cast<const float4*>(pdt + p0 + 2));
+        const int4 c = __ldg(reinterpret_cast<const int4*>(ppb + p0));
+        dh[0] = a.x; dl[0] = a.y; dh[1] = a.z; dl[1] = a.w;
+        dh[2] = b.x; dl[2] = b.y; dh[3] = b.z; dl[3] = b.w;
+        pbv[0] = c.x; pbv[1] = c.y; pbv[2] = c.z; pbv[3] = c.w;
+    } else {
+        #pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int p = p0 + q;
+            dh[q] = dl[q] = 0.0f;
+            pbv[q] = -1;
+            if (p < npt) {
+                const float2 v = __ldg(pdt + p);
+                dh[q] = v.x;
+                dl[q] = v.y;
+                pbv[q] = __ldg(ppb + p);
+            }
+        }
+    }
+}
+
+// Per-(CTA, pv) phase constants (the only FP64 of the per-point kernels):
+// A = frac((t_ref - T0) / P) as a float pair, the removed integer cycles m,
+// and the error bound of the one-FMA coarse phase, in cycles.
+__device__ __forceinline__ float4 tile_phase(const PvHead<float>& H, double t_ref, float maxdt) {
+    float4 c = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (H.status == 0) {
+        const double psi = (t_ref - H.T0) * H.invP;
+        const double m = rint(psi);
+        const double A = psi - m;
+        c.x = (float)A;
+        c.y = (float)(A - (double)c.x);
+        c.z = (float)m;
+        c.w = 2.4e-7f * (maxdt * H.Bh + 1.0f);
+    }
+    return c;
 }
 
 }  // namespace rr

@@ -1,18 +1,20 @@
 // Fused light-curve kernels: time -> phase -> z -> Eq. 5 -> mean over
 // sub-exposures, for a tile of parameter vectors x a tile of times.
 //
-// Tiling: a CTA of kBlock threads owns kPtTile consecutive times (kPPT per
-// thread, strided by kBlock so that each store of a warp covers 32
-// consecutive floats) and `pv_tile` consecutive parameter vectors.  The pv
+// Tiling: a CTA of kBlock threads owns kPtTile consecutive times (4
+// consecutive ones per thread in the FP32 kernel, one 16-byte store per
+// thread and pv; strided by kBlock in the FP64 kernel) and `pv_tile`
+// consecutive parameter vectors.  The pv
 // records of the tile are staged into shared memory by one bulk async copy
 // (TMA engine, mbarrier completion); every thread then loops over the
 // tile's pvs, reusing its times from registers.
 //
 // Mixed precision (FP32 bulk):
-//  * per time, once per CTA: dt = t - t_ref in FP64, kept as a float pair
-//    (dh, dl) -- t_ref is the first time of the tile;
+//  * per time, once per call (rr_points_kernel): dt = t - t_ref in FP64,
+//    kept as a float pair (dh, dl) -- t_ref is the first time of the tile;
 //  * per (CTA, pv), FP64: A = frac((t_ref - T0) / P) as a float pair;
-//  * per (pv, time): coarse phase psi = A + dh / P with one FMA.  If the
+//  * per (pv, time): coarse phase psi = A + dh / P with one FMA, rounded
+//    with two additions (no FP64, no conversion per point).  If the
 //    whole exposure lies outside the pv's transit window the point is 1
 //    exactly and nothing else is computed.  Otherwise the phase is formed in
 //    float-float (error ~1e-9 of a cycle) and every sub-exposure goes
@@ -26,10 +28,10 @@ namespace rr {
 
 // Mean of Eq. 5 over the sub-exposures of one (pv, time); called only for
 // points whose exposure overlaps the transit window.
-__device__ __noinline__ float flux_point32(const PvHead<float>& H, const PvPb<float>& pbc,
-                                           const float* __restrict__ row, int ng, float dh, float dl,
-                                           float Ah, float Al, int ss, float first, float step,
-                                           float inv_ss, bool& bad) {
+__device__ __forceinline__ float flux_point32(const PvHead<float>& H, const PvPb<float>& pbc,
+                                              const float* __restrict__ row, int ng, float dh, float dl,
+                                              float Ah, float Al, int ss, float first, float step,
+                                              float inv_ss, bool& bad) {
     const Phase32 ph = precise_phase(dh, dl, Ah, Al, H.Bh, H.Bl);
     const float two_pi = 6.28318530717958647692f;
     float acc = 0.0f;
@@ -37,7 +39,7 @@ __device__ __noinline__ float flux_point32(const PvHead<float>& H, const PvPb<fl
     for (int s = 0; s < ss; ++s) {
         const float off = fmaf((float)s, step, first) * H.Bh;   // sub-exposure offset, cycles
         float x = (ph.fr_h + off) + ph.fr_l;
-        x -= rintf(x);
+        x -= round_nearest(x);
         const float dM = two_pi * x;
         if (fabsf(dM) > pbc.win_s) continue;
         double dMd = 0.0;
@@ -62,16 +64,33 @@ __device__ __noinline__ float flux_point32(const PvHead<float>& H, const PvPb<fl
     return 1.0f - acc * inv_ss;
 }
 
+// Per-point inputs of the FP32 kernels, once per call: dt = t - t_ref as a
+// float pair, t_ref = the first time of the point's tile (FP64 here, so that
+// the per-(pv, point) work is FP32 only), and the passband index with
+// out-of-range values mapped to npb.
+__global__ void rr_points_kernel(const double* __restrict__ times, const int32_t* __restrict__ pb_index,
+                                 int npt, int npb, float2* __restrict__ dt, int32_t* __restrict__ pbw) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= npt) return;
+    const double d = times[p] - times[(p / kPtTile) * kPtTile];
+    const float h = (float)d;
+    dt[p] = make_float2(h, (float)(d - (double)h));
+    const int pb = pb_index ? pb_index[p] : 0;
+    pbw[p] = (pb >= 0 && pb < npb) ? pb : npb;
+}
+
 __global__ void __launch_bounds__(kBlock) rr_flux_mixed_kernel(const double* __restrict__ times,
-                                                               const int32_t* __restrict__ pb_index,
+                                                               const float2* __restrict__ pdt,
+                                                               const int32_t* __restrict__ ppb,
                                                                int npt, int npv, PbParams pbp, RecLayout L,
                                                                int pv_tile, const char* __restrict__ records,
                                                                float* __restrict__ flux,
-                                                               int32_t* __restrict__ pv_status, int* err) {
+                                                               int32_t* __restrict__ pv_status, int vec_store,
+                                                               int* err) {
     extern __shared__ __align__(16) unsigned char smem[];
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
     float* red = reinterpret_cast<float*>(smem + 16);                  // kBlock / 32 floats
-    float4* cta = reinterpret_cast<float4*>(smem + 16 + 16 * 4);      // per pv: Ah, Al, mref, margin
+    float4* cta = reinterpret_cast<float4*>(smem + 16 + 16 * 4);      // per pv: Ah, Al, m, margin
     char* recs = reinterpret_cast<char*>(smem + 16 + 16 * 4 + 16 * kMaxPvTile);
 
     const int tid = threadIdx.x;
@@ -88,26 +107,11 @@ __global__ void __launch_bounds__(kBlock) rr_flux_mixed_kernel(const double* __r
             bulk_g2s(recs + off, src + off, n, bar);
         }
     }
-    // times of this tile (FP64 difference to the tile's first time, kept as a float pair)
-    const double t_ref = times[pt0];
-    float dh[kPPT], dl[kPPT];
-    int pbv[kPPT];
-    float maxdt = 0.0f;
-    #pragma unroll
-    for (int j = 0; j < kPPT; ++j) {
-        const int p = pt0 + j * kBlock + tid;
-        pbv[j] = -1;
-        dh[j] = 0.0f;
-        dl[j] = 0.0f;
-        if (p < npt) {
-            const double dt = __ldg(times + p) - t_ref;
-            dh[j] = (float)dt;
-            dl[j] = (float)(dt - (double)dh[j]);
-            const int pb = pb_index ? __ldg(pb_index + p) : 0;
-            pbv[j] = (pb >= 0 && pb < L.npb) ? pb : L.npb;   // L.npb marks an invalid index (NaN)
-            maxdt = fmaxf(maxdt, fabsf(dh[j]));
-        }
-    }
+    const int p0 = pt0 + 4 * tid;
+    float dh[4], dl[4];
+    int pbv[4];
+    load_points(pdt, ppb, p0, npt, dh, dl, pbv);
+    float maxdt = fmaxf(fmaxf(fabsf(dh[0]), fabsf(dh[1])), fmaxf(fabsf(dh[2]), fabsf(dh[3])));
     maxdt = warp_max(maxdt);
     if ((tid & 31) == 0) red[tid >> 5] = maxdt;
     __syncthreads();   // also publishes the barrier initialisation
@@ -122,62 +126,58 @@ __global__ void __launch_bounds__(kBlock) rr_flux_mixed_kernel(const double* __r
         mbar_wait_bounded(bar, 0);
     }
     if (__syncthreads_or(ok ? 0 : 1)) return;
-    maxdt = red[0];
-    if (tid < npv_t) {
-        const PvHead<float>& H = *reinterpret_cast<const PvHead<float>*>(recs + (size_t)tid * L.bytes);
-        float4 c = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (H.status == 0) {
-            const double psi = (t_ref - H.T0) * H.invP;
-            const double m = rint(psi);
-            const double A = psi - m;
-            c.x = (float)A;
-            c.y = (float)(A - (double)c.x);
-            c.z = (float)m;
-            // coarse-phase error bound (FMA of a rounded dh and 1/P), radians
-            c.w = 1.5e-6f * (maxdt * H.Bh + 1.0f);
-        }
-        cta[tid] = c;
-    }
+    if (tid < npv_t)
+        cta[tid] = tile_phase(*reinterpret_cast<const PvHead<float>*>(recs + (size_t)tid * L.bytes), times[pt0],
+                              red[0]);
     __syncthreads();
 
     const float nanf_ = __int_as_float(0x7fc00000);
-    const float two_pi = 6.28318530717958647692f;
+    const bool full = vec_store && (p0 + 3 < npt);
     #pragma unroll 1
     for (int i = 0; i < npv_t; ++i) {
         const char* rec = recs + (size_t)i * L.bytes;
         const PvHead<float>& H = *reinterpret_cast<const PvHead<float>*>(rec);
         const PvPb<float>* PB = reinterpret_cast<const PvPb<float>*>(rec + L.off_pb);
         const float* rows = reinterpret_cast<const float*>(rec + L.off_rows);
-        float* out = flux + (size_t)(pv0 + i) * npt;
+        float* out = flux + (size_t)(pv0 + i) * npt + p0;
+        float f[4];
         if (H.status != 0) {
+            f[0] = f[1] = f[2] = f[3] = nanf_;
+        } else {
+            const float4 c = cta[i];
+            const float Bh = H.Bh;
+            unsigned cand = 0;
             #pragma unroll
-            for (int j = 0; j < kPPT; ++j)
-                if (pbv[j] >= 0) __stcs(out + pt0 + j * kBlock + tid, nanf_);
-            continue;
-        }
-        const float4 c = cta[i];
-        const float Bh = H.Bh;
-        bool bad = false;
-        #pragma unroll
-        for (int j = 0; j < kPPT; ++j) {
-            const int pb = pbv[j];
-            if (pb < 0) continue;
-            float f;
-            if (pb >= L.npb) {
-                f = nanf_;
-            } else {
-                const PvPb<float> pbc = PB[pb];
-                const float psi = fmaf(dh[j], Bh, c.x);
-                const float phi = two_pi * (psi - rintf(psi));
-                f = 1.0f;
-                if (fabsf(phi) <= pbc.win_p + c.w)
-                    f = flux_point32(H, pbc, rows + (size_t)pb * L.rows_per_pb * L.ng_pad, L.ng, dh[j],
-                                     dl[j], c.x, c.y, pbp.ss[pb], pbp.first[pb], pbp.step[pb],
-                                     pbp.inv_ss[pb], bad);
+            for (int q = 0; q < 4; ++q) {
+                const int pb = pbv[q];
+                f[q] = pb < L.npb ? 1.0f : nanf_;
+                if (pb < 0 || pb >= L.npb) continue;
+                const float psi = fmaf(dh[q], Bh, c.x);
+                const float d = psi - round_nearest(psi);
+                if (fabsf(d) <= PB[pb].win_pc + c.w) cand |= 1u << q;
             }
-            __stcs(out + pt0 + j * kBlock + tid, f);
+            bool bad = false;
+            while (cand) {
+                const int q = __ffs(cand) - 1;
+                cand &= cand - 1;
+                const int pb = sel4(pbv, q);
+                const float v = flux_point32(H, PB[pb], rows + (size_t)pb * L.rows_per_pb * L.ng_pad, L.ng,
+                                             sel4(dh, q), sel4(dl, q), c.x, c.y, pbp.ss[pb], pbp.first[pb],
+                                             pbp.step[pb], pbp.inv_ss[pb], bad);
+                f[0] = q == 0 ? v : f[0];
+                f[1] = q == 1 ? v : f[1];
+                f[2] = q == 2 ? v : f[2];
+                f[3] = q == 3 ? v : f[3];
+            }
+            if (bad && pv_status) atomicOr(pv_status + pv0 + i, RR_PV_KEPLER);
         }
-        if (bad && pv_status) atomicOr(pv_status + pv0 + i, RR_PV_KEPLER);
+        if (full) {
+            __stcs(reinterpret_cast<float4*>(out), make_float4(f[0], f[1], f[2], f[3]));
+        } else {
+            #pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (pbv[q] >= 0) __stcs(out + q, f[q]);
+        }
     }
 }
 
@@ -280,9 +280,17 @@ int pv_tile_for(int rec_bytes) {
     return t;
 }
 
-cudaError_t launch_flux(rr_ctx* c, const double* times, const int32_t* pb_index, int npt, int npv,
-                        const PbParams& pbp, const void* records, void* flux, int32_t* pv_status,
-                        cudaStream_t s) {
+cudaError_t launch_points(rr_ctx* c, const double* times, const int32_t* pb_index, int npt, void* ws_dt,
+                          void* ws_pb, cudaStream_t s) {
+    rr_points_kernel<<<(npt + 255) / 256, 256, 0, s>>>(times, pb_index, npt, c->cfg.npb, (float2*)ws_dt,
+                                                       (int32_t*)ws_pb);
+    c->launches++;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_flux(rr_ctx* c, const double* times, const int32_t* pb_index, const void* pts_dt,
+                        const void* pts_pb, int npt, int npv, const PbParams& pbp, const void* records,
+                        void* flux, int32_t* pv_status, cudaStream_t s) {
     const bool f64 = c->cfg.precision == RR_PREC_FP64;
     RecLayout L = f64 ? make_layout<double>(c->cfg.npb, c->cfg.ng, c->nldc, false)
                       : make_layout<float>(c->cfg.npb, c->cfg.ng, c->nldc, false);
@@ -300,9 +308,10 @@ cudaError_t launch_flux(rr_ctx* c, const double* times, const int32_t* pb_index,
     } else {
         e = cudaFuncSetAttribute(rr_flux_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        rr_flux_mixed_kernel<<<grid, kBlock, smem, s>>>(times, pb_index, npt, npv, pbp, L, pv_tile,
-                                                        (const char*)records, (float*)flux, pv_status,
-                                                        c->d_err);
+        const int vec = (npt % 4 == 0) && (((uintptr_t)flux & 15u) == 0);
+        rr_flux_mixed_kernel<<<grid, kBlock, smem, s>>>(times, (const float2*)pts_dt, (const int32_t*)pts_pb, npt,
+                                                        npv, pbp, L, pv_tile, (const char*)records, (float*)flux,
+                                                        pv_status, vec, c->d_err);
     }
     c->launches++;
     return cudaGetLastError();

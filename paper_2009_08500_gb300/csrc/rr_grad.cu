@@ -37,12 +37,15 @@ __device__ __forceinline__ void grad_sample(const PvHead<R>& H, const PvPb<R>& p
     R dAdz, dAdk;
     const R A = covered_area<R, true>(pbc.k, z, dAdz, dAdk);
     const R g = z * pbc.inv1pk;
-    R sl;
-    int i;
-    const R Ib = lerp_row<R>(rowblk, L.ng, g, sl, i);
-    const R al = g * R(L.ng - 1) - R(i);
-    const R dIdg = sl * R(L.ng - 1);
-    const R* rk = rowblk + L.ng_pad;
+    // g cell (lower cell on a node, clamped to ng - 2) and in-cell position
+    const R xg = g * R(L.ng - 1);
+    int i = (int)xg;
+    i = i < L.ng - 2 ? i : L.ng - 2;
+    const R al = xg - R(i);
+    const R d = rowblk[L.ng_pad + i];                 // row[i+1] - row[i]
+    const R Ib = rowblk[i] + al * d;
+    const R dIdg = d * R(L.ng - 1);
+    const R* rk = rowblk + 2 * L.ng_pad;
     const R Ik = rk[i] + al * (rk[i + 1] - rk[i]);
     const R ddz = dAdz * Ib + A * dIdg * pbc.inv1pk;
     const R ddk = dAdk * Ib + A * (Ik - dIdg * z * pbc.inv1pk * pbc.inv1pk);
@@ -95,59 +98,71 @@ __device__ __forceinline__ void grad_sample(const PvHead<R>& H, const PvPb<R>& p
     #pragma unroll
     for (int cc = 0; cc < 4; ++cc) {
         if (cc < L.nldc) {
-            const R* rq = rowblk + (size_t)(2 + cc) * L.ng_pad;
+            const R* rq = rowblk + (size_t)(3 + cc) * L.ng_pad;
             const R Q = rq[i] + al * (rq[i + 1] - rq[i]);
             if (DEP) dep[(uslot + cc - 6) * kBlock] += gb * A * Q; else acc.u[cc] += gb * A * Q;
         }
     }
 }
 
-// Sum one value per thread over the CTA (deterministic order): warp
-// shuffles, then warps in index order in FP64.  All threads must call.
-template <typename R>
-__device__ __forceinline__ void block_partials(const GradAcc<R>& acc, const R* dep, int nacc, bool DEP,
-                                               double* wred, double* out) {
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    // register slots (compile-time indices)
+// Sum one accumulator set over a warp (shuffles, fixed order) and store it
+// in the warp's slot of the CTA's partial-sum table.  Skipped (zeros) when
+// no lane of the warp contributed.  All lanes of the warp must call.
+template <typename R, bool DEP>
+__device__ __forceinline__ void warp_partials(const GradAcc<R>& acc, const R* dep, int nacc, bool any,
+                                              R* slot /* [nacc] of this warp */) {
+    const int lane = threadIdx.x & 31;
+    if (!__any_sync(0xffffffffu, any)) {
+        for (int j = lane; j < nacc; j += 32) slot[j] = R(0);
+        return;
+    }
     #pragma unroll
     for (int j = 0; j < 11; ++j) {
         if (j < nacc && (j < 6 || !DEP)) {
             R v = j < 6 ? acc.o[j < 6 ? j : 0] : (j == 6 ? acc.k : acc.u[j >= 7 ? j - 7 : 0]);
             for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-            if (lane == 0) wred[warp * nacc + j] = (double)v;
+            if (lane == 0) slot[j] = v;
         }
     }
     if (DEP) {
         for (int j = 6; j < nacc; ++j) {
             R v = dep[(j - 6) * kBlock];
             for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-            if (lane == 0) wred[warp * nacc + j] = (double)v;
+            if (lane == 0) slot[j] = v;
         }
     }
+}
+
+// After the pv loop: partial[pv][tile][j] = sum over warps (index order) of the
+// warp slots, for every valid pv of the tile.
+template <typename R>
+__device__ __forceinline__ void cta_partials(const R* wpart, const char* recs, int rec_bytes, int npv_t, int nacc,
+                                             int pv0, int tile, int ntiles, R* partials) {
     __syncthreads();
-    if (tid < nacc) {
-        double s = 0.0;
-        for (int w = 0; w < (kBlock >> 5); ++w) s += wred[w * nacc + tid];
-        out[tid] = s;
+    for (int idx = threadIdx.x; idx < npv_t * nacc; idx += blockDim.x) {
+        const int i = idx / nacc, j = idx % nacc;
+        if (reinterpret_cast<const PvHead<R>*>(recs + (size_t)i * rec_bytes)->status != 0) continue;
+        R s = R(0);
+        for (int w = 0; w < (kBlock >> 5); ++w) s += wpart[((size_t)i * (kBlock >> 5) + w) * nacc + j];
+        partials[((size_t)(pv0 + i) * ntiles + tile) * nacc + j] = s;
     }
-    __syncthreads();
 }
 
 template <bool DEP>
 __global__ void __launch_bounds__(kBlock) rr_grad_mixed_kernel(
-    const double* __restrict__ times, const int32_t* __restrict__ pb_index, int npt, int npv,
-    PbParams pbp, RecLayout L, int pv_tile, const char* __restrict__ records,
-    const float* __restrict__ gflux, double* __restrict__ partials, int nacc, int chromatic,
+    const double* __restrict__ times, const float2* __restrict__ pdt, const int32_t* __restrict__ ppb, int npt,
+    int npv, PbParams pbp, RecLayout L, int pv_tile, const char* __restrict__ records,
+    const float* __restrict__ gflux, float* __restrict__ partials, int nacc, int chromatic,
     int32_t* __restrict__ pv_status, int* err) {
     extern __shared__ __align__(16) unsigned char smem[];
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
     float* red = reinterpret_cast<float*>(smem + 16);
     float4* cta = reinterpret_cast<float4*>(smem + 16 + 16 * 4);
     char* recs = reinterpret_cast<char*>(smem + 16 + 16 * 4 + 16 * kMaxPvTile);
-    double* wred = reinterpret_cast<double*>(recs + (size_t)pv_tile * L.bytes);
-    float* depcols = reinterpret_cast<float*>(wred + (kBlock >> 5) * nacc);
+    float* wpart = reinterpret_cast<float*>(recs + (size_t)pv_tile * L.bytes);
+    float* depcols = wpart + (size_t)pv_tile * (kBlock >> 5) * nacc;
 
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, warp = tid >> 5;
     const int tile = blockIdx.x, ntiles = gridDim.x;
     const int pt0 = tile * kPtTile;
     const int pv0 = blockIdx.y * pv_tile;
@@ -162,25 +177,11 @@ __global__ void __launch_bounds__(kBlock) rr_grad_mixed_kernel(
             bulk_g2s(recs + off, src + off, n, bar);
         }
     }
-    const double t_ref = times[pt0];
-    float dh[kPPT], dl[kPPT];
-    int pbv[kPPT];
-    float maxdt = 0.0f;
-    #pragma unroll
-    for (int j = 0; j < kPPT; ++j) {
-        const int p = pt0 + j * kBlock + tid;
-        pbv[j] = -1;
-        dh[j] = 0.0f;
-        dl[j] = 0.0f;
-        if (p < npt) {
-            const double dt = __ldg(times + p) - t_ref;
-            dh[j] = (float)dt;
-            dl[j] = (float)(dt - (double)dh[j]);
-            const int pb = pb_index ? __ldg(pb_index + p) : 0;
-            pbv[j] = (pb >= 0 && pb < L.npb) ? pb : -1;
-            maxdt = fmaxf(maxdt, fabsf(dh[j]));
-        }
-    }
+    const int p0 = pt0 + 4 * tid;
+    float dh[4], dl[4];
+    int pbv[4];
+    load_points(pdt, ppb, p0, npt, dh, dl, pbv);
+    float maxdt = fmaxf(fmaxf(fabsf(dh[0]), fabsf(dh[1])), fmaxf(fabsf(dh[2]), fabsf(dh[3])));
     maxdt = warp_max(maxdt);
     if ((tid & 31) == 0) red[tid >> 5] = maxdt;
     __syncthreads();
@@ -195,21 +196,9 @@ __global__ void __launch_bounds__(kBlock) rr_grad_mixed_kernel(
         mbar_wait_bounded(bar, 0);
     }
     if (__syncthreads_or(ok ? 0 : 1)) return;
-    maxdt = red[0];
-    if (tid < npv_t) {
-        const PvHead<float>& H = *reinterpret_cast<const PvHead<float>*>(recs + (size_t)tid * L.bytes);
-        float4 c = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (H.status == 0) {
-            const double psi = (t_ref - H.T0) * H.invP;
-            const double m = rint(psi);
-            const double A = psi - m;
-            c.x = (float)A;
-            c.y = (float)(A - (double)c.x);
-            c.z = (float)m;
-            c.w = 1.5e-6f * (maxdt * H.Bh + 1.0f);
-        }
-        cta[tid] = c;
-    }
+    if (tid < npv_t)
+        cta[tid] = tile_phase(*reinterpret_cast<const PvHead<float>*>(recs + (size_t)tid * L.bytes), times[pt0],
+                              red[0]);
     __syncthreads();
 
     const float two_pi = 6.28318530717958647692f;
@@ -223,7 +212,7 @@ __global__ void __launch_bounds__(kBlock) rr_grad_mixed_kernel(
         const PvPb<float>* PB = reinterpret_cast<const PvPb<float>*>(rec + L.off_pb);
         const float* rows = reinterpret_cast<const float*>(rec + L.off_rows);
         const float4 c = cta[i];
-        const float* gf = gflux + (size_t)(pv0 + i) * npt;
+        const float* gf = gflux + (size_t)(pv0 + i) * npt + p0;
         GradAcc<float> acc;
         #pragma unroll
         for (int j = 0; j < 6; ++j) acc.o[j] = 0.0f;
@@ -232,28 +221,33 @@ __global__ void __launch_bounds__(kBlock) rr_grad_mixed_kernel(
         for (int j = 0; j < 4; ++j) acc.u[j] = 0.0f;
         if (DEP)
             for (int j = 6; j < nacc; ++j) dep[(j - 6) * kBlock] = 0.0f;
-        bool bad = false;
-        #pragma unroll 1
-        for (int j = 0; j < kPPT; ++j) {
-            const int pb = pbv[j];
-            if (pb < 0) continue;
-            const PvPb<float> pbc = PB[pb];
-            const float psi = fmaf(dh[j], H.Bh, c.x);
-            const float phi = two_pi * (psi - rintf(psi));
-            if (fabsf(phi) > pbc.win_p + c.w) continue;
-            const int p = pt0 + j * kBlock + tid;
-            const float gb = -__ldg(gf + p) * pbp.inv_ss[pb];
+        unsigned cand = 0;
+        #pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int pb = pbv[q];
+            if (pb < 0 || pb >= L.npb) continue;
+            const float psi = fmaf(dh[q], H.Bh, c.x);
+            const float d = psi - round_nearest(psi);
+            if (fabsf(d) <= PB[pb].win_pc + c.w) cand |= 1u << q;
+        }
+        bool any = false, bad = false;
+        while (cand) {
+            const int q = __ffs(cand) - 1;
+            cand &= cand - 1;
+            const int pb = sel4(pbv, q);
+            const float gb = -__ldg(gf + q) * pbp.inv_ss[pb];
             if (gb == 0.0f) continue;
+            const PvPb<float> pbc = PB[pb];
             const float* rowblk = rows + (size_t)pb * L.rows_per_pb * L.ng_pad;
             const int kslot = 6 + (chromatic ? pb : 0);
             const int uslot = 6 + nkp + pb * L.nldc;
-            const Phase32 ph = precise_phase(dh[j], dl[j], c.x, c.y, H.Bh, H.Bl);
+            const Phase32 ph = precise_phase(sel4(dh, q), sel4(dl, q), c.x, c.y, H.Bh, H.Bl);
             const int ss = pbp.ss[pb];
             #pragma unroll 1
             for (int s = 0; s < ss; ++s) {
                 const float off = fmaf((float)s, pbp.step[pb], pbp.first[pb]) * H.Bh;
                 const float xr = (ph.fr_h + off) + ph.fr_l;
-                const float r = rintf(xr);
+                const float r = round_nearest(xr);
                 const float x = xr - r;
                 const float dM = two_pi * x;
                 if (fabsf(dM) > pbc.win_s) continue;
@@ -270,14 +264,17 @@ __global__ void __launch_bounds__(kBlock) rr_grad_mixed_kernel(
                 const float psi_tot = ((c.z + ph.m) + r) + x;   // (t_s - T0) / P
                 grad_sample<float, DEP>(H, pbc, rowblk, L, o.z, o.Px, o.Py, o.S, o.V, psi_tot, gb, acc, dep,
                                         kslot, uslot);
+                any = true;
             }
         }
         if (bad) {
             acc.o[0] = __int_as_float(0x7fc00000);
+            any = true;
             if (pv_status) atomicOr(pv_status + pv0 + i, RR_PV_KEPLER);
         }
-        block_partials<float>(acc, dep, nacc, DEP, wred, partials + ((size_t)(pv0 + i) * ntiles + tile) * nacc);
+        warp_partials<float, DEP>(acc, dep, nacc, any, wpart + ((size_t)i * (kBlock >> 5) + warp) * nacc);
     }
+    cta_partials<float>(wpart, recs, L.bytes, npv_t, nacc, pv0, tile, ntiles, partials);
 }
 
 template <bool DEP>
@@ -289,9 +286,9 @@ __global__ void __launch_bounds__(kBlock) rr_grad_fp64_kernel(
     extern __shared__ __align__(16) unsigned char smem[];
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
     char* recs = reinterpret_cast<char*>(smem + 16 + 16 * 4 + 16 * kMaxPvTile);
-    double* wred = reinterpret_cast<double*>(recs + (size_t)pv_tile * L.bytes);
-    double* depcols = wred + (kBlock >> 5) * nacc;
-    const int tid = threadIdx.x;
+    double* wpart = reinterpret_cast<double*>(recs + (size_t)pv_tile * L.bytes);
+    double* depcols = wpart + (size_t)pv_tile * (kBlock >> 5) * nacc;
+    const int tid = threadIdx.x, warp = tid >> 5;
     const int tile = blockIdx.x, ntiles = gridDim.x;
     const int pt0 = tile * kPtTile;
     const int pv0 = blockIdx.y * pv_tile;
@@ -327,8 +324,8 @@ __global__ void __launch_bounds__(kBlock) rr_grad_fp64_kernel(
         for (int j = 0; j < 4; ++j) acc.u[j] = 0.0;
         if (DEP)
             for (int j = 6; j < nacc; ++j) dep[(j - 6) * kBlock] = 0.0;
-        bool bad = false;
-        #pragma unroll 1
+        bool any = false, bad = false;
+        #pragma unroll
         for (int j = 0; j < kPPT; ++j) {
             const int pb = pbv[j];
             if (pb < 0) continue;
@@ -358,14 +355,17 @@ __global__ void __launch_bounds__(kBlock) rr_grad_fp64_kernel(
                 const double psi_tot = m + tr * H.invP;
                 grad_sample<double, DEP>(H, pbc, rowblk, L, o.z, o.Px, o.Py, o.S, o.V, psi_tot, gb, acc, dep,
                                          kslot, uslot);
+                any = true;
             }
         }
         if (bad) {
             acc.o[0] = __longlong_as_double(0x7ff8000000000000ll);
+            any = true;
             if (pv_status) atomicOr(pv_status + pv0 + i, RR_PV_KEPLER);
         }
-        block_partials<double>(acc, dep, nacc, DEP, wred, partials + ((size_t)(pv0 + i) * ntiles + tile) * nacc);
+        warp_partials<double, DEP>(acc, dep, nacc, any, wpart + ((size_t)i * (kBlock >> 5) + warp) * nacc);
     }
+    cta_partials<double>(wpart, recs, L.bytes, npv_t, nacc, pv0, tile, ntiles, partials);
 }
 
 // Sum the per-tile partials of each pv in tile order; map the quadratic
@@ -374,7 +374,7 @@ __global__ void __launch_bounds__(kBlock) rr_grad_fp64_kernel(
 //   d/dq2 = d/du1 2 sqrt(q1) - d/du2 2 sqrt(q1)
 // Invalid pvs get NaN rows.
 template <typename R>
-__global__ void rr_grad_reduce_kernel(const double* __restrict__ partials, int ntiles, int nacc, int npv,
+__global__ void rr_grad_reduce_kernel(const R* __restrict__ partials, int ntiles, int nacc, int npv,
                                       const char* __restrict__ records, int rec_bytes,
                                       const double* __restrict__ params, int nparam, int ld_model, int npb,
                                       int nkp, double* __restrict__ grad) {
@@ -385,8 +385,8 @@ __global__ void rr_grad_reduce_kernel(const double* __restrict__ partials, int n
     const double nan_ = __longlong_as_double(0x7ff8000000000000ll);
     for (int j = threadIdx.x; j < nacc; j += blockDim.x) {
         double s = 0.0;
-        const double* pp = partials + (size_t)pv * ntiles * nacc + j;
-        for (int t = 0; t < ntiles; ++t) s += pp[(size_t)t * nacc];
+        const R* pp = partials + (size_t)pv * ntiles * nacc + j;
+        for (int t = 0; t < ntiles; ++t) s += (double)pp[(size_t)t * nacc];
         out[j] = H.status != 0 ? nan_ : s;
     }
     __syncwarp();
@@ -404,14 +404,16 @@ __global__ void rr_grad_reduce_kernel(const double* __restrict__ partials, int n
 }
 
 static size_t grad_smem(int pv_tile, const RecLayout& L, int nacc, bool dep, size_t rsize) {
-    size_t s = 16 + 16 * 4 + 16 * kMaxPvTile + (size_t)pv_tile * L.bytes + (size_t)(kBlock >> 5) * nacc * 8;
+    size_t s = 16 + 16 * 4 + 16 * kMaxPvTile + (size_t)pv_tile * L.bytes +
+               (size_t)pv_tile * (kBlock >> 5) * nacc * rsize;
     if (dep) s += (size_t)(nacc - 6) * kBlock * rsize;
     return s;
 }
 
 size_t partials_bytes(const rr_ctx* c, int npv, int npt) {
     const size_t ntiles = ((size_t)npt + kPtTile - 1) / kPtTile;
-    return (size_t)npv * ntiles * (size_t)c->nparam * sizeof(double);
+    const size_t rsize = c->cfg.precision == RR_PREC_FP64 ? sizeof(double) : sizeof(float);
+    return (size_t)npv * ntiles * (size_t)c->nparam * rsize;
 }
 
 template <typename K>
@@ -419,42 +421,59 @@ static cudaError_t set_smem(K kernel, size_t smem) {
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
-cudaError_t launch_grad(rr_ctx* c, const double* times, const int32_t* pb_index, int npt, int npv,
-                        const PbParams& pbp, const void* records, const void* grad_flux, double* partials,
-                        int32_t* pv_status, cudaStream_t s) {
+static bool grad_dep(const rr_ctx* c) {
+    return c->nparam > 11 || (c->cfg.npb > 1 && (c->cfg.chromatic || c->nldc > 0));
+}
+
+cudaError_t launch_grad(rr_ctx* c, const double* times, const int32_t* pb_index, const void* pts_dt,
+                        const void* pts_pb, int npt, int npv, const PbParams& pbp, const void* records,
+                        const void* grad_flux, void* partials, int32_t* pv_status, cudaStream_t s) {
     const bool f64 = c->cfg.precision == RR_PREC_FP64;
     RecLayout L = f64 ? make_layout<double>(c->cfg.npb, c->cfg.ng, c->nldc, true)
                       : make_layout<float>(c->cfg.npb, c->cfg.ng, c->nldc, true);
     const int nacc = c->nparam;
-    const bool dep = nacc > 11 || (c->cfg.npb > 1 && (c->cfg.chromatic || c->nldc > 0));
-    const int pv_tile = pv_tile_for(L.bytes);
-    const size_t smem = grad_smem(pv_tile, L, nacc, dep, f64 ? 8 : 4);
+    const bool dep = grad_dep(c);
+    const size_t rsize = f64 ? 8 : 4;
+    // pv tile: records plus the per-warp partial sums within the shared-memory target
+    const size_t per_pv = (size_t)L.bytes + (size_t)(kBlock >> 5) * nacc * rsize;
+    int pv_tile = (int)(kSmemTarget / per_pv);
+    pv_tile = pv_tile < 1 ? 1 : (pv_tile > kMaxPvTile ? kMaxPvTile : pv_tile);
+    const size_t smem = grad_smem(pv_tile, L, nacc, dep, rsize);
     const int ntiles = (npt + kPtTile - 1) / kPtTile;
     dim3 grid(ntiles, (npv + pv_tile - 1) / pv_tile);
     if (smem > kMaxSmem || grid.y > 65535u) return cudaErrorInvalidConfiguration;
     cudaError_t e;
-#define RR_LAUNCH_GRAD(KERNEL, GT)                                                                          \
-    do {                                                                                                    \
-        e = set_smem(KERNEL, smem);                                                                         \
-        if (e != cudaSuccess) return e;                                                                     \
-        KERNEL<<<grid, kBlock, smem, s>>>(times, pb_index, npt, npv, pbp, L, pv_tile, (const char*)records, \
-                                          (const GT*)grad_flux, partials, nacc, c->cfg.chromatic,          \
-                                          pv_status, c->d_err);                                             \
-    } while (0)
     if (f64) {
-        if (dep) RR_LAUNCH_GRAD(rr_grad_fp64_kernel<true>, double);
-        else RR_LAUNCH_GRAD(rr_grad_fp64_kernel<false>, double);
+#define RR_LAUNCH_GRAD64(KERNEL)                                                                              \
+    do {                                                                                                      \
+        e = set_smem(KERNEL, smem);                                                                           \
+        if (e != cudaSuccess) return e;                                                                       \
+        KERNEL<<<grid, kBlock, smem, s>>>(times, pb_index, npt, npv, pbp, L, pv_tile, (const char*)records,   \
+                                          (const double*)grad_flux, (double*)partials, nacc, c->cfg.chromatic, \
+                                          pv_status, c->d_err);                                               \
+    } while (0)
+        if (dep) RR_LAUNCH_GRAD64(rr_grad_fp64_kernel<true>);
+        else RR_LAUNCH_GRAD64(rr_grad_fp64_kernel<false>);
+#undef RR_LAUNCH_GRAD64
     } else {
-        if (dep) RR_LAUNCH_GRAD(rr_grad_mixed_kernel<true>, float);
-        else RR_LAUNCH_GRAD(rr_grad_mixed_kernel<false>, float);
+#define RR_LAUNCH_GRAD32(KERNEL)                                                                             \
+    do {                                                                                                     \
+        e = set_smem(KERNEL, smem);                                                                          \
+        if (e != cudaSuccess) return e;                                                                      \
+        KERNEL<<<grid, kBlock, smem, s>>>(times, (const float2*)pts_dt, (const int32_t*)pts_pb, npt, npv, pbp, \
+                                          L, pv_tile, (const char*)records, (const float*)grad_flux,          \
+                                          (float*)partials, nacc, c->cfg.chromatic, pv_status, c->d_err);     \
+    } while (0)
+        if (dep) RR_LAUNCH_GRAD32(rr_grad_mixed_kernel<true>);
+        else RR_LAUNCH_GRAD32(rr_grad_mixed_kernel<false>);
+#undef RR_LAUNCH_GRAD32
     }
-#undef RR_LAUNCH_GRAD
     c->launches++;
     return cudaGetLastError();
 }
 
 cudaError_t launch_grad_reduce(rr_ctx* c, int npt, const double* params, int npv, const void* records,
-                               const double* partials, double* grad_params, cudaStream_t s) {
+                               const void* partials, double* grad_params, cudaStream_t s) {
     const bool f64 = c->cfg.precision == RR_PREC_FP64;
     RecLayout L = f64 ? make_layout<double>(c->cfg.npb, c->cfg.ng, c->nldc, true)
                       : make_layout<float>(c->cfg.npb, c->cfg.ng, c->nldc, true);
@@ -463,13 +482,13 @@ cudaError_t launch_grad_reduce(rr_ctx* c, int npt, const double* params, int npv
     dim3 rb(32, 4);
     const int nkp = c->cfg.chromatic ? c->cfg.npb : 1;
     if (f64)
-        rr_grad_reduce_kernel<double><<<(npv + 3) / 4, rb, 0, s>>>(partials, ntiles, nacc, npv, (const char*)records,
-                                                                   L.bytes, params, c->nparam, c->cfg.ld_model,
-                                                                   c->cfg.npb, nkp, grad_params);
+        rr_grad_reduce_kernel<double><<<(npv + 3) / 4, rb, 0, s>>>((const double*)partials, ntiles, nacc, npv,
+                                                                   (const char*)records, L.bytes, params, c->nparam,
+                                                                   c->cfg.ld_model, c->cfg.npb, nkp, grad_params);
     else
-        rr_grad_reduce_kernel<float><<<(npv + 3) / 4, rb, 0, s>>>(partials, ntiles, nacc, npv, (const char*)records,
-                                                                  L.bytes, params, c->nparam, c->cfg.ld_model,
-                                                                  c->cfg.npb, nkp, grad_params);
+        rr_grad_reduce_kernel<float><<<(npv + 3) / 4, rb, 0, s>>>((const float*)partials, ntiles, nacc, npv,
+                                                                  (const char*)records, L.bytes, params, c->nparam,
+                                                                  c->cfg.ld_model, c->cfg.npb, nkp, grad_params);
     c->launches++;
     return cudaGetLastError();
 }

@@ -63,11 +63,13 @@ template <typename R>
 struct alignas(16) PvPb {
     R k, inv1pk;      // radius ratio, 1 / (1 + k)
     R win_s;          // |dM| bound of a possible transit for one sample [rad]
-    R win_p;          // same, widened by the passband's exposure half-span
+    R win_p;          // same, widened by the passband's exposure half-span [rad]
+    float win_pc;     // win_p in cycles (phase units of the FP32 point check)
+    float pad[3];
 };
 
 struct RecLayout {
-    int32_t npb, ng, ng_pad, rows_per_pb;  // rows: 1 (flux) or 2 + nldc (adjoint)
+    int32_t npb, ng, ng_pad, rows_per_pb;  // rows: 1 (flux) or 3 + nldc (adjoint)
     int32_t nldc, off_pb, off_rows, bytes; // byte offsets inside a record; record stride
 };
 
@@ -78,7 +80,7 @@ inline RecLayout make_layout(int npb, int ng, int nldc, bool grad) {
     L.ng = ng;
     L.ng_pad = (ng + 3) & ~3;
     L.nldc = nldc;
-    L.rows_per_pb = grad ? 2 + nldc : 1;
+    L.rows_per_pb = grad ? 3 + nldc : 1;
     L.off_pb = (int32_t)sizeof(PvHead<R>);
     L.off_rows = L.off_pb + npb * (int32_t)sizeof(PvPb<R>);
     size_t bytes = (size_t)L.off_rows + (size_t)npb * L.rows_per_pb * L.ng_pad * sizeof(R);
@@ -118,6 +120,7 @@ struct rr_ctx {
     double* d_istar = nullptr;   // nbasis
     double* d_T64 = nullptr;     // nbasis * nk * ng
     float* d_T32 = nullptr;      // nbasis * nk * ng
+    float* d_DT32 = nullptr;     // nbasis * nk * ng: T[.][.][ig+1] - T[.][.][ig] (FP64 difference, FP32 stored)
     double* d_tab = nullptr;     // tabulated profiles, concatenated (mu then I per passband)
     int* d_tab_off = nullptr;    // npb + 1 offsets (in nodes)
     int* d_err = nullptr;        // device error word
@@ -140,16 +143,23 @@ cudaError_t launch_ld_basis(rr_ctx* c, cudaStream_t s);
 cudaError_t launch_weights(rr_ctx* c, bool need_w, cudaStream_t s);
 cudaError_t launch_pv_setup(rr_ctx* c, const double* params, int npv, const PbParams& pbp,
                             bool grad, void* records, int32_t* pv_status, cudaStream_t s);
-cudaError_t launch_flux(rr_ctx* c, const double* times, const int32_t* pb_index, int npt, int npv,
-                        const PbParams& pbp, const void* records, void* flux, int32_t* pv_status,
-                        cudaStream_t s);
-cudaError_t launch_grad(rr_ctx* c, const double* times, const int32_t* pb_index, int npt, int npv,
-                        const PbParams& pbp, const void* records, const void* grad_flux, double* partials,
-                        int32_t* pv_status, cudaStream_t s);
+cudaError_t launch_flux(rr_ctx* c, const double* times, const int32_t* pb_index, const void* pts_dt,
+                        const void* pts_pb, int npt, int npv, const PbParams& pbp, const void* records,
+                        void* flux, int32_t* pv_status, cudaStream_t s);
+cudaError_t launch_grad(rr_ctx* c, const double* times, const int32_t* pb_index, const void* pts_dt,
+                        const void* pts_pb, int npt, int npv, const PbParams& pbp, const void* records,
+                        const void* grad_flux, void* partials, int32_t* pv_status, cudaStream_t s);
 cudaError_t launch_grad_reduce(rr_ctx* c, int npt, const double* params, int npv, const void* records,
-                               const double* partials, double* grad_params, cudaStream_t s);
+                               const void* partials, double* grad_params, cudaStream_t s);
 size_t records_bytes(const rr_ctx* c, int npv, bool grad);
 size_t partials_bytes(const rr_ctx* c, int npv, int npt);
+// workspace layout: [records | per-point float-float times + passband (mixed form) | partial sums]
+struct WsLayout {
+    size_t rec, pts_dt, pts_pb, part, total;
+};
+WsLayout ws_layout(const rr_ctx* c, int npv, int npt, bool grad);
+cudaError_t launch_points(rr_ctx* c, const double* times, const int32_t* pb_index, int npt, void* ws_dt,
+                          void* ws_pb, cudaStream_t s);
 ModelParams model_params(const rr_ctx* c);
 int pv_tile_for(int rec_bytes);
 }  // namespace rr

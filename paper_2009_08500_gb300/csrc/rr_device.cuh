@@ -77,18 +77,42 @@ __device__ __forceinline__ R lerp_row(const R* row, int ng, R g, R& slope_cell, 
     return l0 + al * (l1 - l0);
 }
 
+// sin(y) and cos(y) for |y| <= 0.5 from their Taylor series (terms through
+// y^9 and y^10; truncation below 3e-10, far under FP32 rounding).
+__device__ __forceinline__ void sincos_small(float y, float& s, float& c) {
+    const float y2 = y * y;
+    float ps = fmaf(y2, 2.7557319e-6f, -1.9841270e-4f);   // 1/9!, -1/7!
+    ps = fmaf(y2, ps, 8.3333333e-3f);                      // 1/5!
+    ps = fmaf(y2, ps, -1.6666667e-1f);                     // -1/3!
+    s = fmaf(y * y2, ps, y);
+    float pc = fmaf(y2, -2.7557319e-7f, 2.4801587e-5f);    // -1/10!, 1/8!
+    pc = fmaf(y2, pc, -1.3888889e-3f);                     // -1/6!
+    pc = fmaf(y2, pc, 4.1666668e-2f);                      // 1/4!
+    pc = fmaf(y2, pc, -0.5f);                              // -1/2!
+    c = fmaf(y2, pc, 1.0f);
+}
+
+// S = sin x, V = 1 - cos x from the half angle (no cancellation in V).
+__device__ __forceinline__ void half_angle_SV(float x, float& S, float& V) {
+    float hs, hc;
+    const float y = 0.5f * x;
+    if (fabsf(y) <= 0.5f) sincos_small(y, hs, hc);
+    else sincosf(y, &hs, &hc);
+    S = 2.0f * hs * hc;
+    V = 2.0f * hs * hs;
+}
+
 // Offset-form Kepler solve in FP32 for x = E - E0 given dM = M - M0
 // (Newton, f(x) = x - ecE0 sin x + esE0 (1 - cos x) - dM, f' = 1 - e cos E).
 // On return S = sin x, V = 1 - cos x.  Returns false if not converged.
 __device__ __forceinline__ bool kepler_offset_f32(float dM, float ecE0, float esE0, float inv_den0,
                                                   float& x, float& S, float& V) {
-    x = dM * inv_den0;
+    // second-order start: x (1 - e cos E0) + e sin E0 x^2 / 2 = dM
+    const float x1 = dM * inv_den0;
+    x = x1 - 0.5f * esE0 * x1 * x1 * inv_den0;
     #pragma unroll 1
     for (int it = 0; it < 24; ++it) {
-        float hs, hc;
-        sincosf(0.5f * x, &hs, &hc);
-        S = 2.0f * hs * hc;
-        V = 2.0f * hs * hs;
+        half_angle_SV(x, S, V);
         const float fx = (x - dM) - ecE0 * S + esE0 * V;
         const float fp = (1.0f - ecE0) + ecE0 * V + esE0 * S;
         const float dx = fx / fp;
@@ -243,10 +267,7 @@ __device__ __forceinline__ Orbit32 orbit32(const PvHead<float>& H, float dM, dou
     o.ok = true;
     float x;
     if (H.flags & kPvCircular) {
-        float hs, hc;
-        sincosf(0.5f * dM, &hs, &hc);
-        o.S = 2.0f * hs * hc;
-        o.V = 2.0f * hs * hs;
+        half_angle_SV(dM, o.S, o.V);
     } else if (H.flags & kPvKepler64) {
         double xd, Sd, Vd;
         o.ok = kepler_offset_f64(dMd, H.ecE0d, H.esE0d, H.inv_den0d, xd, Sd, Vd);
@@ -339,4 +360,130 @@ __device__ __forceinline__ float4 tile_phase(const PvHead<float>& H, double t_re
     return c;
 }
 
+
+// ---- per-warp compaction of transit candidates -------------------------------
+//
+// A warp owns 128 consecutive times (4 per lane).  For one pv, the times
+// whose exposure may overlap the transit are listed in shared memory with
+// their sub-exposure counts; the warp then walks the flattened list of
+// (time, sub-exposure) pairs 32 at a time, so every lane does useful work
+// regardless of where the transit falls or how many sub-exposures a
+// passband has.
+constexpr int kWarpPts = 4 * 32;
+
+struct WarpList {
+    float4 cand[kWarpPts];   // fr_h, fr_l (precise phase, cycles), m (cycles removed), gb (cotangent / -ss)
+    int pb[kWarpPts];
+    int soff[kWarpPts + 1];  // first flattened sample of each candidate; soff[nc] = total
+    float pacc[kWarpPts];    // per-candidate sum over its sub-exposures
+};
+
+__device__ __forceinline__ int warp_excl_scan(int v, int& total) {
+    const int lane = threadIdx.x & 31;
+    int x = v;
+    #pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    total = __shfl_sync(0xffffffffu, x, 31);
+    return x - v;
+}
+
+// Candidate (j) holding flattened sample e: the last j with soff[j] <= e.
+__device__ __forceinline__ int find_cand(const int* soff, int nc, int e) {
+    int lo = 0, hi = nc;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (soff[mid] <= e) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+// Passband constants staged in shared memory (indexing the by-value kernel
+// argument with a runtime passband would place it in local memory).
+struct PbShared {
+    int ss[RR_MAX_PB];
+    float first[RR_MAX_PB], step[RR_MAX_PB], inv_ss[RR_MAX_PB];
+};
+
+__device__ __forceinline__ void stage_pb(const PbParams& pbp, PbShared* ps) {
+    for (int j = threadIdx.x; j < pbp.npb; j += blockDim.x) {
+        ps->ss[j] = pbp.ss[j];
+        ps->first[j] = pbp.first[j];
+        ps->step[j] = pbp.step[j];
+        ps->inv_ss[j] = pbp.inv_ss[j];
+    }
+}
+
+// Build the candidate list of this warp for one pv.  cand: 4-bit mask of the
+// lane's candidate times; gb[q]: per-time weights stored with the entries.
+// Returns the number of flattened samples (warp-uniform); nc gets the
+// number of candidates, base the lane's first entry.
+__device__ __forceinline__ int build_list(WarpList* wl, unsigned cand, const float (&dh)[4], const float (&dl)[4],
+                                          const int (&pbv)[4], const float (&gbq)[4], float Ah, float Al, float Bh,
+                                          float Bl, const PbShared* ps, int& nc, int& base) {
+    const int lane = threadIdx.x & 31;
+    int ns_l = 0;
+    #pragma unroll
+    for (int q = 0; q < 4; ++q)
+        if (cand & (1u << q)) ns_l += ps->ss[pbv[q]];
+    base = warp_excl_scan(__popc(cand), nc);
+    int ns;
+    int soff = warp_excl_scan(ns_l, ns);
+    int j = base;
+    #pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        if (cand & (1u << q)) {
+            const Phase32 ph = precise_phase(dh[q], dl[q], Ah, Al, Bh, Bl);
+            wl->cand[j] = make_float4(ph.fr_h, ph.fr_l, ph.m, gbq[q]);
+            wl->pb[j] = pbv[q];
+            wl->soff[j] = soff;
+            wl->pacc[j] = 0.0f;
+            soff += ps->ss[pbv[q]];
+            ++j;
+        }
+    }
+    if (lane == 0) wl->soff[nc] = ns;
+    __syncwarp();
+    return ns;
+}
+
+// Shared-memory layout common to the FP32 per-point kernels:
+//   [mbarrier 16][reduction 64][per-pv tile constants 16 x kMaxPvTile]
+//   [passband constants][one candidate list per warp][pv records ...]
+constexpr size_t kOffRed = 16;
+constexpr size_t kOffCta = kOffRed + 64;
+constexpr size_t kOffPb = kOffCta + 16 * kMaxPvTile;
+constexpr size_t kOffWl = kOffPb + ((sizeof(PbShared) + 15) / 16) * 16;
+constexpr size_t kWlBytes = ((sizeof(WarpList) + 15) / 16) * 16;
+constexpr size_t kOffRecs32 = kOffWl + (kBlock / 32) * kWlBytes;
+
+// One sub-exposure of one (pv, time): delta = A Ib (Eq. 5 without the 1 -),
+// 0 outside the transit.  Kepler failure: bad = true, NaN.
+__device__ __forceinline__ float delta32(const PvHead<float>& H, const PvPb<float>& pbc, const float* __restrict__ row,
+                                         int ng, float fr_h, float fr_l, int s, float first, float step, bool& bad) {
+    const float off = fmaf((float)s, step, first) * H.Bh;   // sub-exposure offset, cycles
+    float x = (fr_h + off) + fr_l;
+    x -= round_nearest(x);
+    const float dM = 6.28318530717958647692f * x;
+    if (fabsf(dM) > pbc.win_s) return 0.0f;
+    double dMd = 0.0;
+    if (H.flags & kPvKepler64) {
+        double xd = ((double)fr_h + (double)off) + (double)fr_l;
+        xd -= rint(xd);
+        dMd = 6.283185307179586476925 * xd;
+    }
+    const Orbit32 o = orbit32(H, dM, dMd);
+    if (!o.ok) {
+        bad = true;
+        return __int_as_float(0x7fc00000);
+    }
+    const float g = o.z * pbc.inv1pk;
+    if (!o.front || g >= 1.0f) return 0.0f;
+    float d0, d1, sl;
+    int cell;
+    const float A = covered_area<float, false>(pbc.k, o.z, d0, d1);
+    return A * lerp_row<float>(row, ng, g, sl, cell);
+}
 }  // namespace rr

@@ -26,44 +26,6 @@
 
 namespace rr {
 
-// Mean of Eq. 5 over the sub-exposures of one (pv, time); called only for
-// points whose exposure overlaps the transit window.
-__device__ __forceinline__ float flux_point32(const PvHead<float>& H, const PvPb<float>& pbc,
-                                              const float* __restrict__ row, int ng, float dh, float dl,
-                                              float Ah, float Al, int ss, float first, float step,
-                                              float inv_ss, bool& bad) {
-    const Phase32 ph = precise_phase(dh, dl, Ah, Al, H.Bh, H.Bl);
-    const float two_pi = 6.28318530717958647692f;
-    float acc = 0.0f;
-    #pragma unroll 1
-    for (int s = 0; s < ss; ++s) {
-        const float off = fmaf((float)s, step, first) * H.Bh;   // sub-exposure offset, cycles
-        float x = (ph.fr_h + off) + ph.fr_l;
-        x -= round_nearest(x);
-        const float dM = two_pi * x;
-        if (fabsf(dM) > pbc.win_s) continue;
-        double dMd = 0.0;
-        if (H.flags & kPvKepler64) {
-            double xd = ((double)ph.fr_h + (double)off) + (double)ph.fr_l;
-            xd -= rint(xd);
-            dMd = 6.283185307179586476925 * xd;
-        }
-        const Orbit32 o = orbit32(H, dM, dMd);
-        if (!o.ok) {
-            bad = true;
-            return __int_as_float(0x7fc00000);
-        }
-        const float g = o.z * pbc.inv1pk;
-        if (!o.front || g >= 1.0f) continue;
-        float d0, d1, sl;
-        int cell;
-        const float A = covered_area<float, false>(pbc.k, o.z, d0, d1);
-        const float Ib = lerp_row<float>(row, ng, g, sl, cell);
-        acc = fmaf(A, Ib, acc);
-    }
-    return 1.0f - acc * inv_ss;
-}
-
 // Per-point inputs of the FP32 kernels, once per call: dt = t - t_ref as a
 // float pair, t_ref = the first time of the point's tile (FP64 here, so that
 // the per-(pv, point) work is FP32 only), and the passband index with
@@ -89,11 +51,13 @@ __global__ void __launch_bounds__(kBlock) rr_flux_mixed_kernel(const double* __r
                                                                int* err) {
     extern __shared__ __align__(16) unsigned char smem[];
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
-    float* red = reinterpret_cast<float*>(smem + 16);                  // kBlock / 32 floats
-    float4* cta = reinterpret_cast<float4*>(smem + 16 + 16 * 4);      // per pv: Ah, Al, m, margin
-    char* recs = reinterpret_cast<char*>(smem + 16 + 16 * 4 + 16 * kMaxPvTile);
+    float* red = reinterpret_cast<float*>(smem + kOffRed);
+    float4* cta = reinterpret_cast<float4*>(smem + kOffCta);
+    PbShared* ps = reinterpret_cast<PbShared*>(smem + kOffPb);
+    char* recs = reinterpret_cast<char*>(smem + kOffRecs32);
 
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31;
+    WarpList* wl = reinterpret_cast<WarpList*>(smem + kOffWl + (tid >> 5) * kWlBytes);
     const int pt0 = blockIdx.x * kPtTile;
     const int pv0 = blockIdx.y * pv_tile;
     const int npv_t = min(pv_tile, npv - pv0);
@@ -107,14 +71,15 @@ __global__ void __launch_bounds__(kBlock) rr_flux_mixed_kernel(const double* __r
             bulk_g2s(recs + off, src + off, n, bar);
         }
     }
+    stage_pb(pbp, ps);
     const int p0 = pt0 + 4 * tid;
     float dh[4], dl[4];
     int pbv[4];
     load_points(pdt, ppb, p0, npt, dh, dl, pbv);
     float maxdt = fmaxf(fmaxf(fabsf(dh[0]), fabsf(dh[1])), fmaxf(fabsf(dh[2]), fabsf(dh[3])));
     maxdt = warp_max(maxdt);
-    if ((tid & 31) == 0) red[tid >> 5] = maxdt;
-    __syncthreads();   // also publishes the barrier initialisation
+    if (lane == 0) red[tid >> 5] = maxdt;
+    __syncthreads();   // also publishes the barrier initialisation and the passband table
     if (tid < 32) {
         float v = tid < (kBlock >> 5) ? red[tid] : 0.0f;
         v = warp_max(v);
@@ -133,6 +98,7 @@ __global__ void __launch_bounds__(kBlock) rr_flux_mixed_kernel(const double* __r
 
     const float nanf_ = __int_as_float(0x7fc00000);
     const bool full = vec_store && (p0 + 3 < npt);
+    const float zero4[4] = {0.f, 0.f, 0.f, 0.f};
     #pragma unroll 1
     for (int i = 0; i < npv_t; ++i) {
         const char* rec = recs + (size_t)i * L.bytes;
@@ -145,29 +111,51 @@ __global__ void __launch_bounds__(kBlock) rr_flux_mixed_kernel(const double* __r
             f[0] = f[1] = f[2] = f[3] = nanf_;
         } else {
             const float4 c = cta[i];
-            const float Bh = H.Bh;
             unsigned cand = 0;
             #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const int pb = pbv[q];
                 f[q] = pb < L.npb ? 1.0f : nanf_;
                 if (pb < 0 || pb >= L.npb) continue;
-                const float psi = fmaf(dh[q], Bh, c.x);
+                const float psi = fmaf(dh[q], H.Bh, c.x);
                 const float d = psi - round_nearest(psi);
                 if (fabsf(d) <= PB[pb].win_pc + c.w) cand |= 1u << q;
             }
             bool bad = false;
-            while (cand) {
-                const int q = __ffs(cand) - 1;
-                cand &= cand - 1;
-                const int pb = sel4(pbv, q);
-                const float v = flux_point32(H, PB[pb], rows + (size_t)pb * L.rows_per_pb * L.ng_pad, L.ng,
-                                             sel4(dh, q), sel4(dl, q), c.x, c.y, pbp.ss[pb], pbp.first[pb],
-                                             pbp.step[pb], pbp.inv_ss[pb], bad);
-                f[0] = q == 0 ? v : f[0];
-                f[1] = q == 1 ? v : f[1];
-                f[2] = q == 2 ? v : f[2];
-                f[3] = q == 3 ? v : f[3];
+            if (__any_sync(0xffffffffu, cand != 0)) {
+                int nc, base;
+                const int ns = build_list(wl, cand, dh, dl, pbv, zero4, c.x, c.y, H.Bh, H.Bl, ps, nc, base);
+                for (int e0 = 0; e0 < ns; e0 += 32) {
+                    const int e = e0 + lane;
+                    const bool valid = e < ns;
+                    const int j = valid ? find_cand(wl->soff, nc, e) : -1;
+                    float d = 0.0f;
+                    if (valid) {
+                        const int pb = wl->pb[j];
+                        const float4 cd = wl->cand[j];
+                        d = delta32(H, PB[pb], rows + (size_t)pb * L.rows_per_pb * L.ng_pad, L.ng, cd.x, cd.y,
+                                    e - wl->soff[j], ps->first[pb], ps->step[pb], bad);
+                    }
+                    // sum over the sub-exposures of each time: segmented scan along the lanes
+                    #pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const float y = __shfl_up_sync(0xffffffffu, d, o);
+                        const int ky = __shfl_up_sync(0xffffffffu, j, o);
+                        if (lane >= o && ky == j) d += y;
+                    }
+                    const int jn = __shfl_down_sync(0xffffffffu, j, 1);
+                    if (valid && (lane == 31 || jn != j)) wl->pacc[j] += d;
+                    __syncwarp();
+                }
+                int jj = base;
+                #pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    if (cand & (1u << q)) {
+                        f[q] = 1.0f - wl->pacc[jj] * ps->inv_ss[pbv[q]];
+                        ++jj;
+                    }
+                }
+                __syncwarp();
             }
             if (bad && pv_status) atomicOr(pv_status + pv0 + i, RR_PV_KEPLER);
         }
@@ -269,8 +257,8 @@ __global__ void __launch_bounds__(kBlock) rr_flux_fp64_kernel(const double* __re
     }
 }
 
-static size_t flux_smem(int pv_tile, int rec_bytes) {
-    return 16 + 16 * 4 + 16 * kMaxPvTile + (size_t)pv_tile * rec_bytes;
+static size_t flux_smem(int pv_tile, int rec_bytes, bool f64) {
+    return (f64 ? 16 + 16 * 4 + 16 * kMaxPvTile : kOffRecs32) + (size_t)pv_tile * rec_bytes;
 }
 
 int pv_tile_for(int rec_bytes) {
@@ -295,7 +283,7 @@ cudaError_t launch_flux(rr_ctx* c, const double* times, const int32_t* pb_index,
     RecLayout L = f64 ? make_layout<double>(c->cfg.npb, c->cfg.ng, c->nldc, false)
                       : make_layout<float>(c->cfg.npb, c->cfg.ng, c->nldc, false);
     const int pv_tile = pv_tile_for(L.bytes);
-    const size_t smem = flux_smem(pv_tile, L.bytes);
+    const size_t smem = flux_smem(pv_tile, L.bytes, f64);
     dim3 grid((npt + kPtTile - 1) / kPtTile, (npv + pv_tile - 1) / pv_tile);
     if (smem > kMaxSmem || grid.y > 65535u) return cudaErrorInvalidConfiguration;
     cudaError_t e;

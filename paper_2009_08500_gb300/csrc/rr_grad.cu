@@ -156,13 +156,15 @@ __global__ void __launch_bounds__(kBlock) rr_grad_mixed_kernel(
     int32_t* __restrict__ pv_status, int* err) {
     extern __shared__ __align__(16) unsigned char smem[];
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
-    float* red = reinterpret_cast<float*>(smem + 16);
-    float4* cta = reinterpret_cast<float4*>(smem + 16 + 16 * 4);
-    char* recs = reinterpret_cast<char*>(smem + 16 + 16 * 4 + 16 * kMaxPvTile);
+    float* red = reinterpret_cast<float*>(smem + kOffRed);
+    float4* cta = reinterpret_cast<float4*>(smem + kOffCta);
+    PbShared* ps = reinterpret_cast<PbShared*>(smem + kOffPb);
+    char* recs = reinterpret_cast<char*>(smem + kOffRecs32);
     float* wpart = reinterpret_cast<float*>(recs + (size_t)pv_tile * L.bytes);
     float* depcols = wpart + (size_t)pv_tile * (kBlock >> 5) * nacc;
 
-    const int tid = threadIdx.x, warp = tid >> 5;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    WarpList* wl = reinterpret_cast<WarpList*>(smem + kOffWl + warp * kWlBytes);
     const int tile = blockIdx.x, ntiles = gridDim.x;
     const int pt0 = tile * kPtTile;
     const int pv0 = blockIdx.y * pv_tile;
@@ -177,13 +179,14 @@ __global__ void __launch_bounds__(kBlock) rr_grad_mixed_kernel(
             bulk_g2s(recs + off, src + off, n, bar);
         }
     }
+    stage_pb(pbp, ps);
     const int p0 = pt0 + 4 * tid;
     float dh[4], dl[4];
     int pbv[4];
     load_points(pdt, ppb, p0, npt, dh, dl, pbv);
     float maxdt = fmaxf(fmaxf(fabsf(dh[0]), fabsf(dh[1])), fmaxf(fabsf(dh[2]), fabsf(dh[3])));
     maxdt = warp_max(maxdt);
-    if ((tid & 31) == 0) red[tid >> 5] = maxdt;
+    if (lane == 0) red[warp] = maxdt;
     __syncthreads();
     if (tid < 32) {
         float v = tid < (kBlock >> 5) ? red[tid] : 0.0f;
@@ -222,38 +225,37 @@ __global__ void __launch_bounds__(kBlock) rr_grad_mixed_kernel(
         if (DEP)
             for (int j = 6; j < nacc; ++j) dep[(j - 6) * kBlock] = 0.0f;
         unsigned cand = 0;
+        float gbq[4];
         #pragma unroll
         for (int q = 0; q < 4; ++q) {
+            gbq[q] = 0.0f;
             const int pb = pbv[q];
             if (pb < 0 || pb >= L.npb) continue;
             const float psi = fmaf(dh[q], H.Bh, c.x);
             const float d = psi - round_nearest(psi);
-            if (fabsf(d) <= PB[pb].win_pc + c.w) cand |= 1u << q;
+            if (fabsf(d) <= PB[pb].win_pc + c.w) {
+                gbq[q] = -__ldg(gf + q) * ps->inv_ss[pb];
+                if (gbq[q] != 0.0f) cand |= 1u << q;
+            }
         }
         bool any = false, bad = false;
-        while (cand) {
-            const int q = __ffs(cand) - 1;
-            cand &= cand - 1;
-            const int pb = sel4(pbv, q);
-            const float gb = -__ldg(gf + q) * pbp.inv_ss[pb];
-            if (gb == 0.0f) continue;
-            const PvPb<float> pbc = PB[pb];
-            const float* rowblk = rows + (size_t)pb * L.rows_per_pb * L.ng_pad;
-            const int kslot = 6 + (chromatic ? pb : 0);
-            const int uslot = 6 + nkp + pb * L.nldc;
-            const Phase32 ph = precise_phase(sel4(dh, q), sel4(dl, q), c.x, c.y, H.Bh, H.Bl);
-            const int ss = pbp.ss[pb];
-            #pragma unroll 1
-            for (int s = 0; s < ss; ++s) {
-                const float off = fmaf((float)s, pbp.step[pb], pbp.first[pb]) * H.Bh;
-                const float xr = (ph.fr_h + off) + ph.fr_l;
+        if (__any_sync(0xffffffffu, cand != 0)) {
+            int nc, base;
+            const int ns = build_list(wl, cand, dh, dl, pbv, gbq, c.x, c.y, H.Bh, H.Bl, ps, nc, base);
+            for (int e = lane; e < ns; e += 32) {
+                const int j = find_cand(wl->soff, nc, e);
+                const int pb = wl->pb[j];
+                const float4 cd = wl->cand[j];
+                const PvPb<float> pbc = PB[pb];
+                const float off = fmaf((float)(e - wl->soff[j]), ps->step[pb], ps->first[pb]) * H.Bh;
+                const float xr = (cd.x + off) + cd.y;
                 const float r = round_nearest(xr);
                 const float x = xr - r;
                 const float dM = two_pi * x;
                 if (fabsf(dM) > pbc.win_s) continue;
                 double dMd = 0.0;
                 if (H.flags & kPvKepler64) {
-                    double xd = ((double)ph.fr_h + (double)off) + (double)ph.fr_l;
+                    double xd = ((double)cd.x + (double)off) + (double)cd.y;
                     xd -= rint(xd);
                     dMd = 6.283185307179586476925 * xd;
                 }
@@ -261,11 +263,13 @@ __global__ void __launch_bounds__(kBlock) rr_grad_mixed_kernel(
                 if (!o.ok) { bad = true; continue; }
                 const float g = o.z * pbc.inv1pk;
                 if (!o.front || g >= 1.0f) continue;
-                const float psi_tot = ((c.z + ph.m) + r) + x;   // (t_s - T0) / P
-                grad_sample<float, DEP>(H, pbc, rowblk, L, o.z, o.Px, o.Py, o.S, o.V, psi_tot, gb, acc, dep,
-                                        kslot, uslot);
+                const float psi_tot = ((c.z + cd.z) + r) + x;   // (t_s - T0) / P
+                grad_sample<float, DEP>(H, pbc, rows + (size_t)pb * L.rows_per_pb * L.ng_pad, L, o.z, o.Px, o.Py,
+                                        o.S, o.V, psi_tot, cd.w, acc, dep, 6 + (chromatic ? pb : 0),
+                                        6 + nkp + pb * L.nldc);
                 any = true;
             }
+            __syncwarp();
         }
         if (bad) {
             acc.o[0] = __int_as_float(0x7fc00000);
@@ -404,7 +408,7 @@ __global__ void rr_grad_reduce_kernel(const R* __restrict__ partials, int ntiles
 }
 
 static size_t grad_smem(int pv_tile, const RecLayout& L, int nacc, bool dep, size_t rsize) {
-    size_t s = 16 + 16 * 4 + 16 * kMaxPvTile + (size_t)pv_tile * L.bytes +
+    size_t s = (rsize == 8 ? 16 + 16 * 4 + 16 * kMaxPvTile : kOffRecs32) + (size_t)pv_tile * L.bytes +
                (size_t)pv_tile * (kBlock >> 5) * nacc * rsize;
     if (dep) s += (size_t)(nacc - 6) * kBlock * rsize;
     return s;

@@ -59,7 +59,7 @@ def test_setup_tables_match_oracle(rr, ld_model):
     kk = s.k0 + s.dk * np.arange(s.nk)[:, None]
     atot = np.vectorize(lambda k, c: __import__("oracle").area.intersection_area(1.0, k, c))(
         kk, np.arange(s.ng)[None, :] * s.dg * (1 + kk))
-    np.testing.assert_allclose(w * atot[..., None], s.w * atot[..., None], rtol=0, atol=1e-16)
+    np.testing.assert_allclose(w * atot[..., None], s.w * atot[..., None], rtol=0, atol=2e-15)
     np.testing.assert_allclose(w, s.w, rtol=0, atol=1e-12)
     nz = s.mu.size
     basis = m.read_table("basis").reshape(-1, nz)

@@ -202,6 +202,7 @@ rr_status rr_create(const rr_config* cfg, rr_ctx** out) {
     rr_ctx* c = new (std::nothrow) rr_ctx();
     if (!c) return fail(nullptr, RR_ENOMEM, "host allocation failed");
     c->cfg = k;
+    cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, k.device);
     c->nz = k.nzin + k.nzlimb;
     c->nldc = ncoef(k.ld_model);
     c->nbasis = k.ld_model == RR_LD_TABULATED ? k.npb : 1 + c->nldc;

@@ -486,4 +486,53 @@ __device__ __forceinline__ float delta32(const PvHead<float>& H, const PvPb<floa
     const float A = covered_area<float, false>(pbc.k, o.z, d0, d1);
     return A * lerp_row<float>(row, ng, g, sl, cell);
 }
+
+__device__ __forceinline__ float warp_min(float v) {
+    for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Per point sub-tile state of the FP32 kernels: this thread's 4 times, the
+// warp's time range (for the warp-level transit test) and the CTA's largest
+// |dt| (for the coarse-phase error bound).  Contains a __syncthreads.
+struct SubTile {
+    float dh[4], dl[4];
+    int pbv[4];
+    float wlo, whi;      // warp-uniform range of dh over the warp's valid times
+};
+
+__device__ __forceinline__ float subtile_load(SubTile& st, const float2* __restrict__ pdt,
+                                              const int32_t* __restrict__ ppb, int p0, int npt, float* red) {
+    load_points(pdt, ppb, p0, npt, st.dh, st.dl, st.pbv);
+    float lo = INFINITY, hi = -INFINITY, mx = 0.0f;
+    #pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        if (st.pbv[q] >= 0) {
+            lo = fminf(lo, st.dh[q]);
+            hi = fmaxf(hi, st.dh[q]);
+            mx = fmaxf(mx, fabsf(st.dh[q]));
+        }
+    }
+    st.wlo = warp_min(lo);
+    st.whi = warp_max(hi);
+    mx = warp_max(mx);
+    const int tid = threadIdx.x;
+    if ((tid & 31) == 0) red[tid >> 5] = mx;
+    __syncthreads();
+    float v = 0.0f;
+    #pragma unroll
+    for (int w = 0; w < (kBlock >> 5); ++w) v = fmaxf(v, red[w]);
+    return v;
+}
+
+// Can any of the warp's times be in transit for this pv?  The warp's phase
+// interval [A + wlo/P, A + whi/P], widened by the pv's largest window and the
+// rounding bound, must contain an integer (a conjunction).  Warp-uniform.
+__device__ __forceinline__ bool warp_may_transit(const PvHead<float>& H, float4 c, float wlo, float whi) {
+    if (!(wlo <= whi)) return false;
+    const float W = H.wmax_c + 2.0f * c.w;
+    const float plo = fmaf(wlo, H.Bh, c.x) - W;
+    const float phi = fmaf(whi, H.Bh, c.x) + W;
+    return ceilf(plo) <= phi;
+}
 }  // namespace rr

@@ -45,7 +45,8 @@ __global__ void __launch_bounds__(kBlock) rr_flux_mixed_kernel(const double* __r
                                                                const float2* __restrict__ pdt,
                                                                const int32_t* __restrict__ ppb,
                                                                int npt, int npv, PbParams pbp, RecLayout L,
-                                                               int pv_tile, const char* __restrict__ records,
+                                                               int pv_tile, int tiles_per_cta,
+                                                               const char* __restrict__ records,
                                                                float* __restrict__ flux,
                                                                int32_t* __restrict__ pv_status, int vec_store,
                                                                int* err) {
@@ -58,7 +59,9 @@ __global__ void __launch_bounds__(kBlock) rr_flux_mixed_kernel(const double* __r
 
     const int tid = threadIdx.x, lane = tid & 31;
     WarpList* wl = reinterpret_cast<WarpList*>(smem + kOffWl + (tid >> 5) * kWlBytes);
-    const int pt0 = blockIdx.x * kPtTile;
+    const int ntiles = (npt + kPtTile - 1) / kPtTile;
+    const int tile0 = blockIdx.x * tiles_per_cta;
+    const int tile1 = min(ntiles, tile0 + tiles_per_cta);
     const int pv0 = blockIdx.y * pv_tile;
     const int npv_t = min(pv_tile, npv - pv0);
     const uint32_t bytes = (uint32_t)npv_t * (uint32_t)L.bytes;
@@ -72,100 +75,101 @@ __global__ void __launch_bounds__(kBlock) rr_flux_mixed_kernel(const double* __r
         }
     }
     stage_pb(pbp, ps);
-    const int p0 = pt0 + 4 * tid;
-    float dh[4], dl[4];
-    int pbv[4];
-    load_points(pdt, ppb, p0, npt, dh, dl, pbv);
-    float maxdt = fmaxf(fmaxf(fabsf(dh[0]), fabsf(dh[1])), fmaxf(fabsf(dh[2]), fabsf(dh[3])));
-    maxdt = warp_max(maxdt);
-    if (lane == 0) red[tid >> 5] = maxdt;
-    __syncthreads();   // also publishes the barrier initialisation and the passband table
-    if (tid < 32) {
-        float v = tid < (kBlock >> 5) ? red[tid] : 0.0f;
-        v = warp_max(v);
-        if (tid == 0) red[0] = v;
-    }
+    __syncthreads();   // publishes the barrier initialisation and the passband table
     bool ok = mbar_wait_bounded(bar, 0);
     if (!ok) {
         if (tid == 0) atomicExch(err, kErrBarrierTimeout);
         mbar_wait_bounded(bar, 0);
     }
     if (__syncthreads_or(ok ? 0 : 1)) return;
-    if (tid < npv_t)
-        cta[tid] = tile_phase(*reinterpret_cast<const PvHead<float>*>(recs + (size_t)tid * L.bytes), times[pt0],
-                              red[0]);
-    __syncthreads();
 
     const float nanf_ = __int_as_float(0x7fc00000);
-    const bool full = vec_store && (p0 + 3 < npt);
     const float zero4[4] = {0.f, 0.f, 0.f, 0.f};
     #pragma unroll 1
-    for (int i = 0; i < npv_t; ++i) {
-        const char* rec = recs + (size_t)i * L.bytes;
-        const PvHead<float>& H = *reinterpret_cast<const PvHead<float>*>(rec);
-        const PvPb<float>* PB = reinterpret_cast<const PvPb<float>*>(rec + L.off_pb);
-        const float* rows = reinterpret_cast<const float*>(rec + L.off_rows);
-        float* out = flux + (size_t)(pv0 + i) * npt + p0;
-        float f[4];
-        if (H.status != 0) {
-            f[0] = f[1] = f[2] = f[3] = nanf_;
-        } else {
-            const float4 c = cta[i];
-            unsigned cand = 0;
-            #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int pb = pbv[q];
-                f[q] = pb < L.npb ? 1.0f : nanf_;
-                if (pb < 0 || pb >= L.npb) continue;
-                const float psi = fmaf(dh[q], H.Bh, c.x);
-                const float d = psi - round_nearest(psi);
-                if (fabsf(d) <= PB[pb].win_pc + c.w) cand |= 1u << q;
-            }
-            bool bad = false;
-            if (__any_sync(0xffffffffu, cand != 0)) {
-                int nc, base;
-                const int ns = build_list(wl, cand, dh, dl, pbv, zero4, c.x, c.y, H.Bh, H.Bl, ps, nc, base);
-                for (int e0 = 0; e0 < ns; e0 += 32) {
-                    const int e = e0 + lane;
-                    const bool valid = e < ns;
-                    const int j = valid ? find_cand(wl->soff, nc, e) : -1;
-                    float d = 0.0f;
-                    if (valid) {
-                        const int pb = wl->pb[j];
-                        const float4 cd = wl->cand[j];
-                        d = delta32(H, PB[pb], rows + (size_t)pb * L.rows_per_pb * L.ng_pad, L.ng, cd.x, cd.y,
-                                    e - wl->soff[j], ps->first[pb], ps->step[pb], bad);
-                    }
-                    // sum over the sub-exposures of each time: segmented scan along the lanes
+    for (int tile = tile0; tile < tile1; ++tile) {
+        const int pt0 = tile * kPtTile;
+        const int p0 = pt0 + 4 * tid;
+        SubTile st;
+        const float maxdt = subtile_load(st, pdt, ppb, p0, npt, red);
+        if (tid < npv_t)
+            cta[tid] = tile_phase(*reinterpret_cast<const PvHead<float>*>(recs + (size_t)tid * L.bytes), times[pt0],
+                                  maxdt);
+        __syncthreads();
+        float fbase[4];
+        #pragma unroll
+        for (int q = 0; q < 4; ++q) fbase[q] = st.pbv[q] < L.npb ? 1.0f : nanf_;
+        const bool full = vec_store && (p0 + 3 < npt);
+        #pragma unroll 1
+        for (int i = 0; i < npv_t; ++i) {
+            const char* rec = recs + (size_t)i * L.bytes;
+            const PvHead<float>& H = *reinterpret_cast<const PvHead<float>*>(rec);
+            float* out = flux + (size_t)(pv0 + i) * npt + p0;
+            float f[4] = {fbase[0], fbase[1], fbase[2], fbase[3]};
+            if (H.status != 0) {
+                f[0] = f[1] = f[2] = f[3] = nanf_;
+            } else {
+                const float4 c = cta[i];
+                if (warp_may_transit(H, c, st.wlo, st.whi)) {
+                    const PvPb<float>* PB = reinterpret_cast<const PvPb<float>*>(rec + L.off_pb);
+                    const float* rows = reinterpret_cast<const float*>(rec + L.off_rows);
+                    unsigned cand = 0;
                     #pragma unroll
-                    for (int o = 1; o < 32; o <<= 1) {
-                        const float y = __shfl_up_sync(0xffffffffu, d, o);
-                        const int ky = __shfl_up_sync(0xffffffffu, j, o);
-                        if (lane >= o && ky == j) d += y;
+                    for (int q = 0; q < 4; ++q) {
+                        const int pb = st.pbv[q];
+                        if (pb < 0 || pb >= L.npb) continue;
+                        const float psi = fmaf(st.dh[q], H.Bh, c.x);
+                        const float d = psi - round_nearest(psi);
+                        if (fabsf(d) <= PB[pb].win_pc + c.w) cand |= 1u << q;
                     }
-                    const int jn = __shfl_down_sync(0xffffffffu, j, 1);
-                    if (valid && (lane == 31 || jn != j)) wl->pacc[j] += d;
-                    __syncwarp();
-                }
-                int jj = base;
-                #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    if (cand & (1u << q)) {
-                        f[q] = 1.0f - wl->pacc[jj] * ps->inv_ss[pbv[q]];
-                        ++jj;
+                    bool bad = false;
+                    if (__any_sync(0xffffffffu, cand != 0)) {
+                        int nc, base;
+                        const int ns = build_list(wl, cand, st.dh, st.dl, st.pbv, zero4, c.x, c.y, H.Bh, H.Bl, ps,
+                                                  nc, base);
+                        for (int e0 = 0; e0 < ns; e0 += 32) {
+                            const int e = e0 + lane;
+                            const bool valid = e < ns;
+                            const int j = valid ? find_cand(wl->soff, nc, e) : -1;
+                            float d = 0.0f;
+                            if (valid) {
+                                const int pb = wl->pb[j];
+                                const float4 cd = wl->cand[j];
+                                d = delta32(H, PB[pb], rows + (size_t)pb * L.rows_per_pb * L.ng_pad, L.ng, cd.x,
+                                            cd.y, e - wl->soff[j], ps->first[pb], ps->step[pb], bad);
+                            }
+                            // sum over the sub-exposures of each time: segmented scan along the lanes
+                            #pragma unroll
+                            for (int o = 1; o < 32; o <<= 1) {
+                                const float y = __shfl_up_sync(0xffffffffu, d, o);
+                                const int ky = __shfl_up_sync(0xffffffffu, j, o);
+                                if (lane >= o && ky == j) d += y;
+                            }
+                            const int jn = __shfl_down_sync(0xffffffffu, j, 1);
+                            if (valid && (lane == 31 || jn != j)) wl->pacc[j] += d;
+                            __syncwarp();
+                        }
+                        int jj = base;
+                        #pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            if (cand & (1u << q)) {
+                                f[q] = 1.0f - wl->pacc[jj] * ps->inv_ss[st.pbv[q]];
+                                ++jj;
+                            }
+                        }
+                        __syncwarp();
                     }
+                    if (bad && pv_status) atomicOr(pv_status + pv0 + i, RR_PV_KEPLER);
                 }
-                __syncwarp();
             }
-            if (bad && pv_status) atomicOr(pv_status + pv0 + i, RR_PV_KEPLER);
+            if (full) {
+                __stcs(reinterpret_cast<float4*>(out), make_float4(f[0], f[1], f[2], f[3]));
+            } else {
+                #pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (st.pbv[q] >= 0) __stcs(out + q, f[q]);
+            }
         }
-        if (full) {
-            __stcs(reinterpret_cast<float4*>(out), make_float4(f[0], f[1], f[2], f[3]));
-        } else {
-            #pragma unroll
-            for (int q = 0; q < 4; ++q)
-                if (pbv[q] >= 0) __stcs(out + q, f[q]);
-        }
+        __syncthreads();   // cta[] and red[] are rewritten by the next sub-tile
     }
 }
 
@@ -261,6 +265,17 @@ static size_t flux_smem(int pv_tile, int rec_bytes, bool f64) {
     return (f64 ? 16 + 16 * 4 + 16 * kMaxPvTile : kOffRecs32) + (size_t)pv_tile * rec_bytes;
 }
 
+// Point sub-tiles per CTA: enough CTAs for several waves on every SM, the
+// rest of the points looped inside a CTA so its staged records are reused.
+int tiles_per_cta(const rr_ctx* c, int ntiles, int npvt) {
+    const long long want = 12LL * (c->num_sms > 0 ? c->num_sms : 148);
+    long long t = ((long long)ntiles * npvt) / want;
+    if (t < 1) t = 1;
+    if (t > 16) t = 16;
+    if (t > ntiles) t = ntiles;
+    return (int)t;
+}
+
 int pv_tile_for(int rec_bytes) {
     int t = kSmemTarget / rec_bytes;
     if (t < 1) t = 1;
@@ -284,7 +299,10 @@ cudaError_t launch_flux(rr_ctx* c, const double* times, const int32_t* pb_index,
                       : make_layout<float>(c->cfg.npb, c->cfg.ng, c->nldc, false);
     const int pv_tile = pv_tile_for(L.bytes);
     const size_t smem = flux_smem(pv_tile, L.bytes, f64);
-    dim3 grid((npt + kPtTile - 1) / kPtTile, (npv + pv_tile - 1) / pv_tile);
+    const int ntiles = (npt + kPtTile - 1) / kPtTile;
+    const int npvt = (npv + pv_tile - 1) / pv_tile;
+    const int tpc = f64 ? 1 : tiles_per_cta(c, ntiles, npvt);
+    dim3 grid((ntiles + tpc - 1) / tpc, npvt);
     if (smem > kMaxSmem || grid.y > 65535u) return cudaErrorInvalidConfiguration;
     cudaError_t e;
     if (f64) {
@@ -298,7 +316,7 @@ cudaError_t launch_flux(rr_ctx* c, const double* times, const int32_t* pb_index,
         if (e != cudaSuccess) return e;
         const int vec = (npt % 4 == 0) && (((uintptr_t)flux & 15u) == 0);
         rr_flux_mixed_kernel<<<grid, kBlock, smem, s>>>(times, (const float2*)pts_dt, (const int32_t*)pts_pb, npt,
-                                                        npv, pbp, L, pv_tile, (const char*)records, (float*)flux,
+                                                        npv, pbp, L, pv_tile, tpc, (const char*)records, (float*)flux,
                                                         pv_status, vec, c->d_err);
     }
     c->launches++;

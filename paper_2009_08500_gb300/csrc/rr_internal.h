@@ -48,7 +48,8 @@ template <typename R>
 struct alignas(16) PvHead {
     double T0, P, invP;            // FP64 epoch and period (phase reduction)
     double ecE0d, esE0d, inv_den0d;  // FP64 Kepler constants (e > kESwitch fallback)
-    double pad0, pad1;
+    float wmax_c;                  // largest point window over the passbands, cycles
+    float padf[3];
     R a, b, a2, b2;
     R e, ecE0, esE0, inv_den0;     // inv_den0 = 1 / (1 - e cos E0)
     R ax1, ax2, ay1, ay2;
@@ -124,6 +125,7 @@ struct rr_ctx {
     double* d_tab = nullptr;     // tabulated profiles, concatenated (mu then I per passband)
     int* d_tab_off = nullptr;    // npb + 1 offsets (in nodes)
     int* d_err = nullptr;        // device error word
+    int num_sms = 0;
     bool weights_built = false;
     bool tables_built = false;
     std::string err;
@@ -162,4 +164,5 @@ cudaError_t launch_points(rr_ctx* c, const double* times, const int32_t* pb_inde
                           void* ws_pb, cudaStream_t s);
 ModelParams model_params(const rr_ctx* c);
 int pv_tile_for(int rec_bytes);
+int tiles_per_cta(const rr_ctx* c, int ntiles, int npvt);
 }  // namespace rr

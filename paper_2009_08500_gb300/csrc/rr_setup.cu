@@ -285,6 +285,7 @@ __global__ void __launch_bounds__(256) rr_pv_setup_kernel(ModelParams mp, PbPara
         H->status = st;
         if (pv_status) pv_status[pv] = st;
         H->flags = 0;
+        H->wmax_c = 0.0f;
         H->pad3 = 0;
         H->pad4 = 0;
         if (st == 0) {
@@ -312,7 +313,7 @@ __global__ void __launch_bounds__(256) rr_pv_setup_kernel(ModelParams mp, PbPara
             const double inv_den0 = 1.0 / den0;
             H->T0 = T0; H->P = P; H->invP = invP;
             H->ecE0d = e * cE0; H->esE0d = e * sE0; H->inv_den0d = inv_den0;
-            H->pad0 = 0.0; H->pad1 = 0.0;
+            H->padf[0] = H->padf[1] = H->padf[2] = 0.0f;
             H->a = (R)a; H->b = (R)b; H->a2 = (R)(a * a); H->b2 = (R)(b * b);
             H->e = (R)e; H->ecE0 = (R)(e * cE0); H->esE0 = (R)(e * sE0); H->inv_den0 = (R)inv_den0;
             H->ax1 = (R)ax1; H->ax2 = (R)ax2; H->ay1 = (R)ay1; H->ay2 = (R)ay2;
@@ -325,6 +326,7 @@ __global__ void __launch_bounds__(256) rr_pv_setup_kernel(ModelParams mp, PbPara
             int flags = 0;
             if (e == 0.0) flags |= kPvCircular;
             if (e > kESwitch) flags |= kPvKepler64;
+            double wmax = 0.0;
             const double ra = a * (1.0 - e);
             for (int pb = 0; pb < mp.npb; ++pb) {
                 const double k = row[6 + (mp.chromatic ? pb : 0)];
@@ -345,7 +347,9 @@ __global__ void __launch_bounds__(256) rr_pv_setup_kernel(ModelParams mp, PbPara
                 PB[pb].win_p = (R)winp;
                 PB[pb].win_pc = (float)(winp * (0.5 / CUDART_PI));
                 PB[pb].pad[0] = PB[pb].pad[1] = PB[pb].pad[2] = 0.0f;
+                wmax = fmax(wmax, winp * (0.5 / CUDART_PI));
             }
+            H->wmax_c = (float)wmax;
             H->flags = flags;
         }
     }

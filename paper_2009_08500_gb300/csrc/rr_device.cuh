@@ -343,22 +343,6 @@ __device__ __forceinline__ void load_points(const float2* __restrict__ pdt, cons
     }
 }
 
-// Per-(CTA, pv) phase constants (the only FP64 of the per-point kernels):
-// A = frac((t_ref - T0) / P) as a float pair, the removed integer cycles m,
-// and the error bound of the one-FMA coarse phase, in cycles.
-__device__ __forceinline__ float4 tile_phase(const PvHead<float>& H, double t_ref, float maxdt) {
-    float4 c = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (H.status == 0) {
-        const double psi = (t_ref - H.T0) * H.invP;
-        const double m = rint(psi);
-        const double A = psi - m;
-        c.x = (float)A;
-        c.y = (float)(A - (double)c.x);
-        c.z = (float)m;
-        c.w = 2.4e-7f * (maxdt * H.Bh + 1.0f);
-    }
-    return c;
-}
 
 
 // ---- per-warp compaction of transit candidates -------------------------------
@@ -492,37 +476,57 @@ __device__ __forceinline__ float warp_min(float v) {
     return v;
 }
 
-// Per point sub-tile state of the FP32 kernels: this thread's 4 times, the
-// warp's time range (for the warp-level transit test) and the CTA's largest
-// |dt| (for the coarse-phase error bound).  Contains a __syncthreads.
-struct SubTile {
+// Per-warp group state of the FP32 kernels.  A group is kWarpPts = 128
+// consecutive times, 4 per lane; its float-float times are relative to the
+// group's first time t_g.  Lane l also holds the phase constants of pv l of
+// the CTA's tile at t_g (the only FP64 of the per-point kernels):
+// A = frac((t_g - T0) / P) as a float pair and the removed integer cycles m.
+struct GroupState {
     float dh[4], dl[4];
     int pbv[4];
-    float wlo, whi;      // warp-uniform range of dh over the warp's valid times
+    float wlo, whi, maxdt;   // warp-uniform: range of dh and largest |dh| over valid times
+    float Ah, Al, m;         // phase constants of pv `lane`
 };
 
-__device__ __forceinline__ float subtile_load(SubTile& st, const float2* __restrict__ pdt,
-                                              const int32_t* __restrict__ ppb, int p0, int npt, float* red) {
-    load_points(pdt, ppb, p0, npt, st.dh, st.dl, st.pbv);
+__device__ __forceinline__ void group_load(GroupState& gs, const float2* __restrict__ pdt,
+                                           const int32_t* __restrict__ ppb, const double* __restrict__ times,
+                                           int g0, int npt, const char* recs, int rec_bytes, int npv_t) {
+    const int lane = threadIdx.x & 31;
+    load_points(pdt, ppb, g0 + 4 * lane, npt, gs.dh, gs.dl, gs.pbv);
     float lo = INFINITY, hi = -INFINITY, mx = 0.0f;
     #pragma unroll
     for (int q = 0; q < 4; ++q) {
-        if (st.pbv[q] >= 0) {
-            lo = fminf(lo, st.dh[q]);
-            hi = fmaxf(hi, st.dh[q]);
-            mx = fmaxf(mx, fabsf(st.dh[q]));
+        if (gs.pbv[q] >= 0) {
+            lo = fminf(lo, gs.dh[q]);
+            hi = fmaxf(hi, gs.dh[q]);
+            mx = fmaxf(mx, fabsf(gs.dh[q]));
         }
     }
-    st.wlo = warp_min(lo);
-    st.whi = warp_max(hi);
-    mx = warp_max(mx);
-    const int tid = threadIdx.x;
-    if ((tid & 31) == 0) red[tid >> 5] = mx;
-    __syncthreads();
-    float v = 0.0f;
-    #pragma unroll
-    for (int w = 0; w < (kBlock >> 5); ++w) v = fmaxf(v, red[w]);
-    return v;
+    gs.wlo = warp_min(lo);
+    gs.whi = warp_max(hi);
+    gs.maxdt = warp_max(mx);
+    gs.Ah = gs.Al = gs.m = 0.0f;
+    if (lane < npv_t) {
+        const PvHead<float>& H = *reinterpret_cast<const PvHead<float>*>(recs + (size_t)lane * rec_bytes);
+        if (H.status == 0) {
+            const double psi = (__ldg(times + g0) - H.T0) * H.invP;
+            const double m = rint(psi);
+            const double A = psi - m;
+            gs.Ah = (float)A;
+            gs.Al = (float)(A - (double)gs.Ah);
+            gs.m = (float)m;
+        }
+    }
+}
+
+// Phase constants of pv i for this group: (Ah, Al, m, coarse-phase error bound in cycles).
+__device__ __forceinline__ float4 group_pv(const GroupState& gs, const PvHead<float>& H, int i) {
+    float4 c;
+    c.x = __shfl_sync(0xffffffffu, gs.Ah, i);
+    c.y = __shfl_sync(0xffffffffu, gs.Al, i);
+    c.z = __shfl_sync(0xffffffffu, gs.m, i);
+    c.w = 2.4e-7f * (gs.maxdt * H.Bh + 1.0f);
+    return c;
 }
 
 // Can any of the warp's times be in transit for this pv?  The warp's phase

@@ -27,14 +27,14 @@
 namespace rr {
 
 // Per-point inputs of the FP32 kernels, once per call: dt = t - t_ref as a
-// float pair, t_ref = the first time of the point's tile (FP64 here, so that
+// float pair, t_ref = the first time of the point's 128-time group (FP64 here, so that
 // the per-(pv, point) work is FP32 only), and the passband index with
 // out-of-range values mapped to npb.
 __global__ void rr_points_kernel(const double* __restrict__ times, const int32_t* __restrict__ pb_index,
                                  int npt, int npb, float2* __restrict__ dt, int32_t* __restrict__ pbw) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= npt) return;
-    const double d = times[p] - times[(p / kPtTile) * kPtTile];
+    const double d = times[p] - times[(p / kWarpPts) * kWarpPts];
     const float h = (float)d;
     dt[p] = make_float2(h, (float)(d - (double)h));
     const int pb = pb_index ? pb_index[p] : 0;
@@ -45,23 +45,21 @@ __global__ void __launch_bounds__(kBlock) rr_flux_mixed_kernel(const double* __r
                                                                const float2* __restrict__ pdt,
                                                                const int32_t* __restrict__ ppb,
                                                                int npt, int npv, PbParams pbp, RecLayout L,
-                                                               int pv_tile, int tiles_per_cta,
+                                                               int pv_tile, int groups_per_cta,
                                                                const char* __restrict__ records,
                                                                float* __restrict__ flux,
                                                                int32_t* __restrict__ pv_status, int vec_store,
                                                                int* err) {
     extern __shared__ __align__(16) unsigned char smem[];
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
-    float* red = reinterpret_cast<float*>(smem + kOffRed);
-    float4* cta = reinterpret_cast<float4*>(smem + kOffCta);
     PbShared* ps = reinterpret_cast<PbShared*>(smem + kOffPb);
     char* recs = reinterpret_cast<char*>(smem + kOffRecs32);
 
-    const int tid = threadIdx.x, lane = tid & 31;
-    WarpList* wl = reinterpret_cast<WarpList*>(smem + kOffWl + (tid >> 5) * kWlBytes);
-    const int ntiles = (npt + kPtTile - 1) / kPtTile;
-    const int tile0 = blockIdx.x * tiles_per_cta;
-    const int tile1 = min(ntiles, tile0 + tiles_per_cta);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    WarpList* wl = reinterpret_cast<WarpList*>(smem + kOffWl + warp * kWlBytes);
+    const int ngroups = (npt + kWarpPts - 1) / kWarpPts;
+    const int gbeg = blockIdx.x * groups_per_cta;
+    const int gend = min(ngroups, gbeg + groups_per_cta);
     const int pv0 = blockIdx.y * pv_tile;
     const int npv_t = min(pv_tile, npv - pv0);
     const uint32_t bytes = (uint32_t)npv_t * (uint32_t)L.bytes;
@@ -83,93 +81,86 @@ __global__ void __launch_bounds__(kBlock) rr_flux_mixed_kernel(const double* __r
     }
     if (__syncthreads_or(ok ? 0 : 1)) return;
 
+    // from here on every warp is independent: no CTA barrier
     const float nanf_ = __int_as_float(0x7fc00000);
     const float zero4[4] = {0.f, 0.f, 0.f, 0.f};
     #pragma unroll 1
-    for (int tile = tile0; tile < tile1; ++tile) {
-        const int pt0 = tile * kPtTile;
-        const int p0 = pt0 + 4 * tid;
-        SubTile st;
-        const float maxdt = subtile_load(st, pdt, ppb, p0, npt, red);
-        if (tid < npv_t)
-            cta[tid] = tile_phase(*reinterpret_cast<const PvHead<float>*>(recs + (size_t)tid * L.bytes), times[pt0],
-                                  maxdt);
-        __syncthreads();
+    for (int g = gbeg + warp; g < gend; g += (kBlock >> 5)) {
+        const int p0 = g * kWarpPts + 4 * lane;
+        GroupState gs;
+        group_load(gs, pdt, ppb, times, g * kWarpPts, npt, recs, L.bytes, npv_t);
         float fbase[4];
         #pragma unroll
-        for (int q = 0; q < 4; ++q) fbase[q] = st.pbv[q] < L.npb ? 1.0f : nanf_;
+        for (int q = 0; q < 4; ++q) fbase[q] = gs.pbv[q] < L.npb ? 1.0f : nanf_;
         const bool full = vec_store && (p0 + 3 < npt);
         #pragma unroll 1
         for (int i = 0; i < npv_t; ++i) {
             const char* rec = recs + (size_t)i * L.bytes;
             const PvHead<float>& H = *reinterpret_cast<const PvHead<float>*>(rec);
             float* out = flux + (size_t)(pv0 + i) * npt + p0;
+            const float4 c = group_pv(gs, H, i);
             float f[4] = {fbase[0], fbase[1], fbase[2], fbase[3]};
             if (H.status != 0) {
                 f[0] = f[1] = f[2] = f[3] = nanf_;
-            } else {
-                const float4 c = cta[i];
-                if (warp_may_transit(H, c, st.wlo, st.whi)) {
-                    const PvPb<float>* PB = reinterpret_cast<const PvPb<float>*>(rec + L.off_pb);
-                    const float* rows = reinterpret_cast<const float*>(rec + L.off_rows);
-                    unsigned cand = 0;
-                    #pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const int pb = st.pbv[q];
-                        if (pb < 0 || pb >= L.npb) continue;
-                        const float psi = fmaf(st.dh[q], H.Bh, c.x);
-                        const float d = psi - round_nearest(psi);
-                        if (fabsf(d) <= PB[pb].win_pc + c.w) cand |= 1u << q;
-                    }
-                    bool bad = false;
-                    if (__any_sync(0xffffffffu, cand != 0)) {
-                        int nc, base;
-                        const int ns = build_list(wl, cand, st.dh, st.dl, st.pbv, zero4, c.x, c.y, H.Bh, H.Bl, ps,
-                                                  nc, base);
-                        for (int e0 = 0; e0 < ns; e0 += 32) {
-                            const int e = e0 + lane;
-                            const bool valid = e < ns;
-                            const int j = valid ? find_cand(wl->soff, nc, e) : -1;
-                            float d = 0.0f;
-                            if (valid) {
-                                const int pb = wl->pb[j];
-                                const float4 cd = wl->cand[j];
-                                d = delta32(H, PB[pb], rows + (size_t)pb * L.rows_per_pb * L.ng_pad, L.ng, cd.x,
-                                            cd.y, e - wl->soff[j], ps->first[pb], ps->step[pb], bad);
-                            }
-                            // sum over the sub-exposures of each time: segmented scan along the lanes
-                            #pragma unroll
-                            for (int o = 1; o < 32; o <<= 1) {
-                                const float y = __shfl_up_sync(0xffffffffu, d, o);
-                                const int ky = __shfl_up_sync(0xffffffffu, j, o);
-                                if (lane >= o && ky == j) d += y;
-                            }
-                            const int jn = __shfl_down_sync(0xffffffffu, j, 1);
-                            if (valid && (lane == 31 || jn != j)) wl->pacc[j] += d;
-                            __syncwarp();
+            } else if (warp_may_transit(H, c, gs.wlo, gs.whi)) {
+                const PvPb<float>* PB = reinterpret_cast<const PvPb<float>*>(rec + L.off_pb);
+                const float* rows = reinterpret_cast<const float*>(rec + L.off_rows);
+                unsigned cand = 0;
+                #pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int pb = gs.pbv[q];
+                    if (pb < 0 || pb >= L.npb) continue;
+                    const float psi = fmaf(gs.dh[q], H.Bh, c.x);
+                    const float d = psi - round_nearest(psi);
+                    if (fabsf(d) <= PB[pb].win_pc + c.w) cand |= 1u << q;
+                }
+                bool bad = false;
+                if (__any_sync(0xffffffffu, cand != 0)) {
+                    int nc, base;
+                    const int ns = build_list(wl, cand, gs.dh, gs.dl, gs.pbv, zero4, c.x, c.y, H.Bh, H.Bl, ps, nc,
+                                              base);
+                    for (int e0 = 0; e0 < ns; e0 += 32) {
+                        const int e = e0 + lane;
+                        const bool valid = e < ns;
+                        const int j = valid ? find_cand(wl->soff, nc, e) : -1;
+                        float d = 0.0f;
+                        if (valid) {
+                            const int pb = wl->pb[j];
+                            const float4 cd = wl->cand[j];
+                            d = delta32(H, PB[pb], rows + (size_t)pb * L.rows_per_pb * L.ng_pad, L.ng, cd.x, cd.y,
+                                        e - wl->soff[j], ps->first[pb], ps->step[pb], bad);
                         }
-                        int jj = base;
+                        // sum over the sub-exposures of each time: segmented scan along the lanes
                         #pragma unroll
-                        for (int q = 0; q < 4; ++q) {
-                            if (cand & (1u << q)) {
-                                f[q] = 1.0f - wl->pacc[jj] * ps->inv_ss[st.pbv[q]];
-                                ++jj;
-                            }
+                        for (int o = 1; o < 32; o <<= 1) {
+                            const float y = __shfl_up_sync(0xffffffffu, d, o);
+                            const int ky = __shfl_up_sync(0xffffffffu, j, o);
+                            if (lane >= o && ky == j) d += y;
                         }
+                        const int jn = __shfl_down_sync(0xffffffffu, j, 1);
+                        if (valid && (lane == 31 || jn != j)) wl->pacc[j] += d;
                         __syncwarp();
                     }
-                    if (bad && pv_status) atomicOr(pv_status + pv0 + i, RR_PV_KEPLER);
+                    int jj = base;
+                    #pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        if (cand & (1u << q)) {
+                            f[q] = 1.0f - wl->pacc[jj] * ps->inv_ss[gs.pbv[q]];
+                            ++jj;
+                        }
+                    }
+                    __syncwarp();
                 }
+                if (bad && pv_status) atomicOr(pv_status + pv0 + i, RR_PV_KEPLER);
             }
             if (full) {
                 __stcs(reinterpret_cast<float4*>(out), make_float4(f[0], f[1], f[2], f[3]));
             } else {
                 #pragma unroll
                 for (int q = 0; q < 4; ++q)
-                    if (st.pbv[q] >= 0) __stcs(out + q, f[q]);
+                    if (gs.pbv[q] >= 0) __stcs(out + q, f[q]);
             }
         }
-        __syncthreads();   // cta[] and red[] are rewritten by the next sub-tile
     }
 }
 
@@ -265,15 +256,15 @@ static size_t flux_smem(int pv_tile, int rec_bytes, bool f64) {
     return (f64 ? 16 + 16 * 4 + 16 * kMaxPvTile : kOffRecs32) + (size_t)pv_tile * rec_bytes;
 }
 
-// Point sub-tiles per CTA: enough CTAs for several waves on every SM, the
-// rest of the points looped inside a CTA so its staged records are reused.
-int tiles_per_cta(const rr_ctx* c, int ntiles, int npvt) {
-    const long long want = 12LL * (c->num_sms > 0 ? c->num_sms : 148);
-    long long t = ((long long)ntiles * npvt) / want;
-    if (t < 1) t = 1;
-    if (t > 16) t = 16;
-    if (t > ntiles) t = ntiles;
-    return (int)t;
+// 128-time groups per CTA of the FP32 kernels.  A function of npt only, so
+// the adjoint's summation order for a pv never depends on the other pvs in
+// the launch: between 1 and 16 groups per warp, about one eighth of the
+// point range per CTA.
+int groups_per_cta(int npt) {
+    const int ntiles = (npt + kPtTile - 1) / kPtTile;
+    int t = ntiles / 8;
+    t = t < 1 ? 1 : (t > 16 ? 16 : t);
+    return t * (kBlock / 32);
 }
 
 int pv_tile_for(int rec_bytes) {
@@ -299,10 +290,10 @@ cudaError_t launch_flux(rr_ctx* c, const double* times, const int32_t* pb_index,
                       : make_layout<float>(c->cfg.npb, c->cfg.ng, c->nldc, false);
     const int pv_tile = pv_tile_for(L.bytes);
     const size_t smem = flux_smem(pv_tile, L.bytes, f64);
-    const int ntiles = (npt + kPtTile - 1) / kPtTile;
     const int npvt = (npv + pv_tile - 1) / pv_tile;
-    const int tpc = f64 ? 1 : tiles_per_cta(c, ntiles, npvt);
-    dim3 grid((ntiles + tpc - 1) / tpc, npvt);
+    const int gpc = groups_per_cta(npt);
+    const int ngroups = (npt + kWarpPts - 1) / kWarpPts;
+    dim3 grid(f64 ? (npt + kPtTile - 1) / kPtTile : (ngroups + gpc - 1) / gpc, npvt);
     if (smem > kMaxSmem || grid.y > 65535u) return cudaErrorInvalidConfiguration;
     cudaError_t e;
     if (f64) {
@@ -316,7 +307,7 @@ cudaError_t launch_flux(rr_ctx* c, const double* times, const int32_t* pb_index,
         if (e != cudaSuccess) return e;
         const int vec = (npt % 4 == 0) && (((uintptr_t)flux & 15u) == 0);
         rr_flux_mixed_kernel<<<grid, kBlock, smem, s>>>(times, (const float2*)pts_dt, (const int32_t*)pts_pb, npt,
-                                                        npv, pbp, L, pv_tile, tpc, (const char*)records, (float*)flux,
+                                                        npv, pbp, L, pv_tile, gpc, (const char*)records, (float*)flux,
                                                         pv_status, vec, c->d_err);
     }
     c->launches++;

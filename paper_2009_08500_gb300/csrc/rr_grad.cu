@@ -133,6 +133,29 @@ __device__ __forceinline__ void warp_partials(const GradAcc<R>& acc, const R* de
     }
 }
 
+// Add one accumulator set, summed over the warp (fixed shuffle order), to
+// the warp's running slot (lane 0 adds, so the order over groups is fixed).
+template <typename R, bool DEP>
+__device__ __forceinline__ void warp_accumulate(const GradAcc<R>& acc, const R* dep, int nacc, bool any, R* slot) {
+    const int lane = threadIdx.x & 31;
+    if (!__any_sync(0xffffffffu, any)) return;
+    #pragma unroll
+    for (int j = 0; j < 11; ++j) {
+        if (j < nacc && (j < 6 || !DEP)) {
+            R v = j < 6 ? acc.o[j < 6 ? j : 0] : (j == 6 ? acc.k : acc.u[j >= 7 ? j - 7 : 0]);
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0) slot[j] += v;
+        }
+    }
+    if (DEP) {
+        for (int j = 6; j < nacc; ++j) {
+            R v = dep[(j - 6) * kBlock];
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0) slot[j] += v;
+        }
+    }
+}
+
 // After the pv loop: partial[pv][tile][j] = sum over warps (index order) of the
 // warp slots, for every valid pv of the tile.
 template <typename R>
@@ -151,23 +174,21 @@ __device__ __forceinline__ void cta_partials(const R* wpart, const char* recs, i
 template <bool DEP>
 __global__ void __launch_bounds__(kBlock) rr_grad_mixed_kernel(
     const double* __restrict__ times, const float2* __restrict__ pdt, const int32_t* __restrict__ ppb, int npt,
-    int npv, PbParams pbp, RecLayout L, int pv_tile, int tiles_per_cta, const char* __restrict__ records,
+    int npv, PbParams pbp, RecLayout L, int pv_tile, int groups_per_cta, const char* __restrict__ records,
     const float* __restrict__ gflux, float* __restrict__ partials, int nacc, int chromatic,
     int32_t* __restrict__ pv_status, int* err) {
     extern __shared__ __align__(16) unsigned char smem[];
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
-    float* red = reinterpret_cast<float*>(smem + kOffRed);
-    float4* cta = reinterpret_cast<float4*>(smem + kOffCta);
     PbShared* ps = reinterpret_cast<PbShared*>(smem + kOffPb);
     char* recs = reinterpret_cast<char*>(smem + kOffRecs32);
-    float* wpart = reinterpret_cast<float*>(recs + (size_t)pv_tile * L.bytes);
-    float* depcols = wpart + (size_t)pv_tile * (kBlock >> 5) * nacc;
+    float* wacc = reinterpret_cast<float*>(recs + (size_t)pv_tile * L.bytes);   // [pv][warp][nacc]
+    float* depcols = wacc + (size_t)pv_tile * (kBlock >> 5) * nacc;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     WarpList* wl = reinterpret_cast<WarpList*>(smem + kOffWl + warp * kWlBytes);
-    const int ntiles = (npt + kPtTile - 1) / kPtTile;
-    const int tile0 = blockIdx.x * tiles_per_cta;
-    const int tile1 = min(ntiles, tile0 + tiles_per_cta);
+    const int ngroups = (npt + kWarpPts - 1) / kWarpPts;
+    const int gbeg = blockIdx.x * groups_per_cta;
+    const int gend = min(ngroups, gbeg + groups_per_cta);
     const int pv0 = blockIdx.y * pv_tile;
     const int npv_t = min(pv_tile, npv - pv0);
     const uint32_t bytes = (uint32_t)npv_t * (uint32_t)L.bytes;
@@ -181,6 +202,7 @@ __global__ void __launch_bounds__(kBlock) rr_grad_mixed_kernel(
         }
     }
     stage_pb(pbp, ps);
+    for (int j = tid; j < pv_tile * (kBlock >> 5) * nacc; j += kBlock) wacc[j] = 0.0f;
     __syncthreads();
     bool ok = mbar_wait_bounded(bar, 0);
     if (!ok) {
@@ -189,95 +211,87 @@ __global__ void __launch_bounds__(kBlock) rr_grad_mixed_kernel(
     }
     if (__syncthreads_or(ok ? 0 : 1)) return;
 
+    // every warp is independent until the final reduction
     const float two_pi = 6.28318530717958647692f;
     const int nkp = chromatic ? L.npb : 1;
     float* dep = DEP ? depcols + tid : nullptr;
     #pragma unroll 1
-    for (int tile = tile0; tile < tile1; ++tile) {
-        const int pt0 = tile * kPtTile;
-        const int p0 = pt0 + 4 * tid;
-        SubTile st;
-        const float maxdt = subtile_load(st, pdt, ppb, p0, npt, red);
-        if (tid < npv_t)
-            cta[tid] = tile_phase(*reinterpret_cast<const PvHead<float>*>(recs + (size_t)tid * L.bytes), times[pt0],
-                                  maxdt);
-        __syncthreads();
+    for (int g = gbeg + warp; g < gend; g += (kBlock >> 5)) {
+        const int p0 = g * kWarpPts + 4 * lane;
+        GroupState gs;
+        group_load(gs, pdt, ppb, times, g * kWarpPts, npt, recs, L.bytes, npv_t);
         #pragma unroll 1
         for (int i = 0; i < npv_t; ++i) {
             const char* rec = recs + (size_t)i * L.bytes;
             const PvHead<float>& H = *reinterpret_cast<const PvHead<float>*>(rec);
-            if (H.status != 0) continue;   // uniform over the CTA
-            const float4 c = cta[i];
+            const float4 c = group_pv(gs, H, i);
+            if (H.status != 0 || !warp_may_transit(H, c, gs.wlo, gs.whi)) continue;   // warp-uniform
+            const PvPb<float>* PB = reinterpret_cast<const PvPb<float>*>(rec + L.off_pb);
+            const float* rows = reinterpret_cast<const float*>(rec + L.off_rows);
+            const float* gf = gflux + (size_t)(pv0 + i) * npt + p0;
+            unsigned cand = 0;
+            float gbq[4];
+            #pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                gbq[q] = 0.0f;
+                const int pb = gs.pbv[q];
+                if (pb < 0 || pb >= L.npb) continue;
+                const float psi = fmaf(gs.dh[q], H.Bh, c.x);
+                const float d = psi - round_nearest(psi);
+                if (fabsf(d) <= PB[pb].win_pc + c.w) {
+                    gbq[q] = -__ldg(gf + q) * ps->inv_ss[pb];
+                    if (gbq[q] != 0.0f) cand |= 1u << q;
+                }
+            }
+            if (!__any_sync(0xffffffffu, cand != 0)) continue;
             GradAcc<float> acc;
             #pragma unroll
             for (int j = 0; j < 6; ++j) acc.o[j] = 0.0f;
             acc.k = 0.0f;
             #pragma unroll
             for (int j = 0; j < 4; ++j) acc.u[j] = 0.0f;
+            if (DEP)
+                for (int j = 6; j < nacc; ++j) dep[(j - 6) * kBlock] = 0.0f;
             bool any = false, bad = false;
-            if (warp_may_transit(H, c, st.wlo, st.whi)) {
-                const PvPb<float>* PB = reinterpret_cast<const PvPb<float>*>(rec + L.off_pb);
-                const float* rows = reinterpret_cast<const float*>(rec + L.off_rows);
-                const float* gf = gflux + (size_t)(pv0 + i) * npt + p0;
-                if (DEP)
-                    for (int j = 6; j < nacc; ++j) dep[(j - 6) * kBlock] = 0.0f;
-                unsigned cand = 0;
-                float gbq[4];
-                #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    gbq[q] = 0.0f;
-                    const int pb = st.pbv[q];
-                    if (pb < 0 || pb >= L.npb) continue;
-                    const float psi = fmaf(st.dh[q], H.Bh, c.x);
-                    const float d = psi - round_nearest(psi);
-                    if (fabsf(d) <= PB[pb].win_pc + c.w) {
-                        gbq[q] = -__ldg(gf + q) * ps->inv_ss[pb];
-                        if (gbq[q] != 0.0f) cand |= 1u << q;
-                    }
+            int nc, base;
+            const int ns = build_list(wl, cand, gs.dh, gs.dl, gs.pbv, gbq, c.x, c.y, H.Bh, H.Bl, ps, nc, base);
+            for (int e = lane; e < ns; e += 32) {
+                const int j = find_cand(wl->soff, nc, e);
+                const int pb = wl->pb[j];
+                const float4 cd = wl->cand[j];
+                const PvPb<float> pbc = PB[pb];
+                const float off = fmaf((float)(e - wl->soff[j]), ps->step[pb], ps->first[pb]) * H.Bh;
+                const float xr = (cd.x + off) + cd.y;
+                const float r = round_nearest(xr);
+                const float x = xr - r;
+                const float dM = two_pi * x;
+                if (fabsf(dM) > pbc.win_s) continue;
+                double dMd = 0.0;
+                if (H.flags & kPvKepler64) {
+                    double xd = ((double)cd.x + (double)off) + (double)cd.y;
+                    xd -= rint(xd);
+                    dMd = 6.283185307179586476925 * xd;
                 }
-                if (__any_sync(0xffffffffu, cand != 0)) {
-                    int nc, base;
-                    const int ns = build_list(wl, cand, st.dh, st.dl, st.pbv, gbq, c.x, c.y, H.Bh, H.Bl, ps, nc,
-                                              base);
-                    for (int e = lane; e < ns; e += 32) {
-                        const int j = find_cand(wl->soff, nc, e);
-                        const int pb = wl->pb[j];
-                        const float4 cd = wl->cand[j];
-                        const PvPb<float> pbc = PB[pb];
-                        const float off = fmaf((float)(e - wl->soff[j]), ps->step[pb], ps->first[pb]) * H.Bh;
-                        const float xr = (cd.x + off) + cd.y;
-                        const float r = round_nearest(xr);
-                        const float x = xr - r;
-                        const float dM = two_pi * x;
-                        if (fabsf(dM) > pbc.win_s) continue;
-                        double dMd = 0.0;
-                        if (H.flags & kPvKepler64) {
-                            double xd = ((double)cd.x + (double)off) + (double)cd.y;
-                            xd -= rint(xd);
-                            dMd = 6.283185307179586476925 * xd;
-                        }
-                        const Orbit32 o = orbit32(H, dM, dMd);
-                        if (!o.ok) { bad = true; continue; }
-                        const float g = o.z * pbc.inv1pk;
-                        if (!o.front || g >= 1.0f) continue;
-                        const float psi_tot = ((c.z + cd.z) + r) + x;   // (t_s - T0) / P
-                        grad_sample<float, DEP>(H, pbc, rows + (size_t)pb * L.rows_per_pb * L.ng_pad, L, o.z,
-                                                o.Px, o.Py, o.S, o.V, psi_tot, cd.w, acc, dep,
-                                                6 + (chromatic ? pb : 0), 6 + nkp + pb * L.nldc);
-                        any = true;
-                    }
-                    __syncwarp();
-                }
+                const Orbit32 o = orbit32(H, dM, dMd);
+                if (!o.ok) { bad = true; continue; }
+                const float gz = o.z * pbc.inv1pk;
+                if (!o.front || gz >= 1.0f) continue;
+                const float psi_tot = ((c.z + cd.z) + r) + x;   // (t_s - T0) / P
+                grad_sample<float, DEP>(H, pbc, rows + (size_t)pb * L.rows_per_pb * L.ng_pad, L, o.z, o.Px,
+                                        o.Py, o.S, o.V, psi_tot, cd.w, acc, dep, 6 + (chromatic ? pb : 0),
+                                        6 + nkp + pb * L.nldc);
+                any = true;
             }
+            __syncwarp();
             if (bad) {
                 acc.o[0] = __int_as_float(0x7fc00000);
                 any = true;
                 if (pv_status) atomicOr(pv_status + pv0 + i, RR_PV_KEPLER);
             }
-            warp_partials<float, DEP>(acc, dep, nacc, any, wpart + ((size_t)i * (kBlock >> 5) + warp) * nacc);
+            warp_accumulate<float, DEP>(acc, dep, nacc, any, wacc + ((size_t)i * (kBlock >> 5) + warp) * nacc);
         }
-        cta_partials<float>(wpart, recs, L.bytes, npv_t, nacc, pv0, tile, ntiles, partials);
     }
+    cta_partials<float>(wacc, recs, L.bytes, npv_t, nacc, pv0, blockIdx.x, gridDim.x, partials);
 }
 
 template <bool DEP>
@@ -413,10 +427,18 @@ static size_t grad_smem(int pv_tile, const RecLayout& L, int nacc, bool dep, siz
     return s;
 }
 
+// Partial sums per pv: one per 1024-time tile (FP64 kernel) or per CTA
+// chunk of 128-time groups (FP32 kernel); depends on npt only.
+static int grad_chunks(const rr_ctx* c, int npt) {
+    if (c->cfg.precision == RR_PREC_FP64) return (npt + kPtTile - 1) / kPtTile;
+    const int ngroups = (npt + kWarpPts - 1) / kWarpPts;
+    const int gpc = groups_per_cta(npt);
+    return (ngroups + gpc - 1) / gpc;
+}
+
 size_t partials_bytes(const rr_ctx* c, int npv, int npt) {
-    const size_t ntiles = ((size_t)npt + kPtTile - 1) / kPtTile;
     const size_t rsize = c->cfg.precision == RR_PREC_FP64 ? sizeof(double) : sizeof(float);
-    return (size_t)npv * ntiles * (size_t)c->nparam * rsize;
+    return (size_t)npv * (size_t)grad_chunks(c, npt) * (size_t)c->nparam * rsize;
 }
 
 template <typename K>
@@ -442,10 +464,9 @@ cudaError_t launch_grad(rr_ctx* c, const double* times, const int32_t* pb_index,
     int pv_tile = (int)(kSmemTarget / per_pv);
     pv_tile = pv_tile < 1 ? 1 : (pv_tile > kMaxPvTile ? kMaxPvTile : pv_tile);
     const size_t smem = grad_smem(pv_tile, L, nacc, dep, rsize);
-    const int ntiles = (npt + kPtTile - 1) / kPtTile;
     const int npvt = (npv + pv_tile - 1) / pv_tile;
-    const int tpc = f64 ? 1 : tiles_per_cta(c, ntiles, npvt);
-    dim3 grid((ntiles + tpc - 1) / tpc, npvt);
+    const int gpc = groups_per_cta(npt);
+    dim3 grid(grad_chunks(c, npt), npvt);
     if (smem > kMaxSmem || grid.y > 65535u) return cudaErrorInvalidConfiguration;
     cudaError_t e;
     if (f64) {
@@ -466,7 +487,7 @@ cudaError_t launch_grad(rr_ctx* c, const double* times, const int32_t* pb_index,
         e = set_smem(KERNEL, smem);                                                                          \
         if (e != cudaSuccess) return e;                                                                      \
         KERNEL<<<grid, kBlock, smem, s>>>(times, (const float2*)pts_dt, (const int32_t*)pts_pb, npt, npv, pbp, \
-                                          L, pv_tile, tpc, (const char*)records, (const float*)grad_flux,     \
+                                          L, pv_tile, gpc, (const char*)records, (const float*)grad_flux,     \
                                           (float*)partials, nacc, c->cfg.chromatic, pv_status, c->d_err);     \
     } while (0)
         if (dep) RR_LAUNCH_GRAD32(rr_grad_mixed_kernel<true>);
@@ -483,7 +504,7 @@ cudaError_t launch_grad_reduce(rr_ctx* c, int npt, const double* params, int npv
     RecLayout L = f64 ? make_layout<double>(c->cfg.npb, c->cfg.ng, c->nldc, true)
                       : make_layout<float>(c->cfg.npb, c->cfg.ng, c->nldc, true);
     const int nacc = c->nparam;
-    const int ntiles = (npt + kPtTile - 1) / kPtTile;
+    const int ntiles = grad_chunks(c, npt);
     dim3 rb(32, 4);
     const int nkp = c->cfg.chromatic ? c->cfg.npb : 1;
     if (f64)

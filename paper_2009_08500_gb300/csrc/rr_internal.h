@@ -164,5 +164,5 @@ cudaError_t launch_points(rr_ctx* c, const double* times, const int32_t* pb_inde
                           void* ws_pb, cudaStream_t s);
 ModelParams model_params(const rr_ctx* c);
 int pv_tile_for(int rec_bytes);
-int tiles_per_cta(const rr_ctx* c, int ntiles, int npvt);
+int groups_per_cta(int npt);
 }  // namespace rr

@@ -115,7 +115,7 @@ __device__ __forceinline__ bool kepler_offset_f32(float dM, float ecE0, float es
         half_angle_SV(x, S, V);
         const float fx = (x - dM) - ecE0 * S + esE0 * V;
         const float fp = (1.0f - ecE0) + ecE0 * V + esE0 * S;
-        const float dx = fx / fp;
+        const float dx = __fdividef(fx, fp);   // the next iteration corrects a rounded step
         x -= dx;
         const float S_old = S;
         S -= dx * (1.0f - V);

@@ -41,7 +41,7 @@ __global__ void rr_points_kernel(const double* __restrict__ times, const int32_t
     pbw[p] = (pb >= 0 && pb < npb) ? pb : npb;
 }
 
-__global__ void __launch_bounds__(kBlock) rr_flux_mixed_kernel(const double* __restrict__ times,
+__global__ void __launch_bounds__(kBlock, 4) rr_flux_mixed_kernel(const double* __restrict__ times,
                                                                const float2* __restrict__ pdt,
                                                                const int32_t* __restrict__ ppb,
                                                                int npt, int npv, PbParams pbp, RecLayout L,
@@ -54,6 +54,7 @@ __global__ void __launch_bounds__(kBlock) rr_flux_mixed_kernel(const double* __r
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
     PbShared* ps = reinterpret_cast<PbShared*>(smem + kOffPb);
     char* recs = reinterpret_cast<char*>(smem + kOffRecs32);
+    int* next_group = reinterpret_cast<int*>(smem + kOffRed);
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     WarpList* wl = reinterpret_cast<WarpList*>(smem + kOffWl + warp * kWlBytes);
@@ -64,6 +65,7 @@ __global__ void __launch_bounds__(kBlock) rr_flux_mixed_kernel(const double* __r
     const int npv_t = min(pv_tile, npv - pv0);
     const uint32_t bytes = (uint32_t)npv_t * (uint32_t)L.bytes;
     if (tid == 0) {
+        *next_group = gbeg;
         mbar_init(bar, 1);
         mbar_expect_tx(bar, bytes);
         const char* src = records + (size_t)pv0 * L.bytes;
@@ -81,11 +83,17 @@ __global__ void __launch_bounds__(kBlock) rr_flux_mixed_kernel(const double* __r
     }
     if (__syncthreads_or(ok ? 0 : 1)) return;
 
-    // from here on every warp is independent: no CTA barrier
+    // from here on every warp is independent (no CTA barrier); warps take the
+    // CTA's groups from a shared counter, so a warp that meets transits does
+    // not hold back the others
     const float nanf_ = __int_as_float(0x7fc00000);
     const float zero4[4] = {0.f, 0.f, 0.f, 0.f};
     #pragma unroll 1
-    for (int g = gbeg + warp; g < gend; g += (kBlock >> 5)) {
+    while (true) {
+        int g = 0;
+        if (lane == 0) g = atomicAdd(next_group, 1);
+        g = __shfl_sync(0xffffffffu, g, 0);
+        if (g >= gend) break;
         const int p0 = g * kWarpPts + 4 * lane;
         GroupState gs;
         group_load(gs, pdt, ppb, times, g * kWarpPts, npt, recs, L.bytes, npv_t);

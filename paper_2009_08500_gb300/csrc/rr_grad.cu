@@ -171,6 +171,20 @@ __device__ __forceinline__ void cta_partials(const R* wpart, const char* recs, i
     }
 }
 
+// After the group loop: partial[pv][chunk][j] = sum over the CTA's groups (index order).
+__device__ __forceinline__ void cta_partials_groups(const float* gacc, const char* recs, int rec_bytes, int npv_t,
+                                                    int nacc, int gpc, int pv0, int chunk, int nchunks,
+                                                    float* partials) {
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < npv_t * nacc; idx += blockDim.x) {
+        const int i = idx / nacc, j = idx % nacc;
+        if (reinterpret_cast<const PvHead<float>*>(recs + (size_t)i * rec_bytes)->status != 0) continue;
+        float s = 0.0f;
+        for (int g = 0; g < gpc; ++g) s += gacc[((size_t)i * gpc + g) * nacc + j];
+        partials[((size_t)(pv0 + i) * nchunks + chunk) * nacc + j] = s;
+    }
+}
+
 template <bool DEP>
 __global__ void __launch_bounds__(kBlock) rr_grad_mixed_kernel(
     const double* __restrict__ times, const float2* __restrict__ pdt, const int32_t* __restrict__ ppb, int npt,
@@ -181,8 +195,9 @@ __global__ void __launch_bounds__(kBlock) rr_grad_mixed_kernel(
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
     PbShared* ps = reinterpret_cast<PbShared*>(smem + kOffPb);
     char* recs = reinterpret_cast<char*>(smem + kOffRecs32);
-    float* wacc = reinterpret_cast<float*>(recs + (size_t)pv_tile * L.bytes);   // [pv][warp][nacc]
-    float* depcols = wacc + (size_t)pv_tile * (kBlock >> 5) * nacc;
+    float* gacc = reinterpret_cast<float*>(recs + (size_t)pv_tile * L.bytes);   // [pv][group][nacc]
+    float* depcols = gacc + (size_t)pv_tile * groups_per_cta * nacc;
+    int* next_group = reinterpret_cast<int*>(smem + kOffRed);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     WarpList* wl = reinterpret_cast<WarpList*>(smem + kOffWl + warp * kWlBytes);
@@ -193,6 +208,7 @@ __global__ void __launch_bounds__(kBlock) rr_grad_mixed_kernel(
     const int npv_t = min(pv_tile, npv - pv0);
     const uint32_t bytes = (uint32_t)npv_t * (uint32_t)L.bytes;
     if (tid == 0) {
+        *next_group = gbeg;
         mbar_init(bar, 1);
         mbar_expect_tx(bar, bytes);
         const char* src = records + (size_t)pv0 * L.bytes;
@@ -202,7 +218,7 @@ __global__ void __launch_bounds__(kBlock) rr_grad_mixed_kernel(
         }
     }
     stage_pb(pbp, ps);
-    for (int j = tid; j < pv_tile * (kBlock >> 5) * nacc; j += kBlock) wacc[j] = 0.0f;
+    for (int j = tid; j < pv_tile * groups_per_cta * nacc; j += kBlock) gacc[j] = 0.0f;
     __syncthreads();
     bool ok = mbar_wait_bounded(bar, 0);
     if (!ok) {
@@ -211,12 +227,18 @@ __global__ void __launch_bounds__(kBlock) rr_grad_mixed_kernel(
     }
     if (__syncthreads_or(ok ? 0 : 1)) return;
 
-    // every warp is independent until the final reduction
+    // every warp is independent until the final reduction; groups come from a
+    // shared counter and each group's sums go to its own slot, so the result
+    // does not depend on which warp took which group
     const float two_pi = 6.28318530717958647692f;
     const int nkp = chromatic ? L.npb : 1;
     float* dep = DEP ? depcols + tid : nullptr;
     #pragma unroll 1
-    for (int g = gbeg + warp; g < gend; g += (kBlock >> 5)) {
+    while (true) {
+        int g = 0;
+        if (lane == 0) g = atomicAdd(next_group, 1);
+        g = __shfl_sync(0xffffffffu, g, 0);
+        if (g >= gend) break;
         const int p0 = g * kWarpPts + 4 * lane;
         GroupState gs;
         group_load(gs, pdt, ppb, times, g * kWarpPts, npt, recs, L.bytes, npv_t);
@@ -288,10 +310,11 @@ __global__ void __launch_bounds__(kBlock) rr_grad_mixed_kernel(
                 any = true;
                 if (pv_status) atomicOr(pv_status + pv0 + i, RR_PV_KEPLER);
             }
-            warp_accumulate<float, DEP>(acc, dep, nacc, any, wacc + ((size_t)i * (kBlock >> 5) + warp) * nacc);
+            warp_accumulate<float, DEP>(acc, dep, nacc, any,
+                                        gacc + ((size_t)i * groups_per_cta + (g - gbeg)) * nacc);
         }
     }
-    cta_partials<float>(wacc, recs, L.bytes, npv_t, nacc, pv0, blockIdx.x, gridDim.x, partials);
+    cta_partials_groups(gacc, recs, L.bytes, npv_t, nacc, groups_per_cta, pv0, blockIdx.x, gridDim.x, partials);
 }
 
 template <bool DEP>
@@ -420,9 +443,9 @@ __global__ void rr_grad_reduce_kernel(const R* __restrict__ partials, int ntiles
     }
 }
 
-static size_t grad_smem(int pv_tile, const RecLayout& L, int nacc, bool dep, size_t rsize) {
+static size_t grad_smem(int pv_tile, const RecLayout& L, int nacc, bool dep, size_t rsize, int slots) {
     size_t s = (rsize == 8 ? 16 + 16 * 4 + 16 * kMaxPvTile : kOffRecs32) + (size_t)pv_tile * L.bytes +
-               (size_t)pv_tile * (kBlock >> 5) * nacc * rsize;
+               (size_t)pv_tile * slots * nacc * rsize;
     if (dep) s += (size_t)(nacc - 6) * kBlock * rsize;
     return s;
 }
@@ -460,10 +483,11 @@ cudaError_t launch_grad(rr_ctx* c, const double* times, const int32_t* pb_index,
     const bool dep = grad_dep(c);
     const size_t rsize = f64 ? 8 : 4;
     // pv tile: records plus the per-warp partial sums within the shared-memory target
-    const size_t per_pv = (size_t)L.bytes + (size_t)(kBlock >> 5) * nacc * rsize;
+    const int slots = f64 ? (kBlock >> 5) : groups_per_cta(npt);   // partial-sum slots per pv in the CTA
+    const size_t per_pv = (size_t)L.bytes + (size_t)slots * nacc * rsize;
     int pv_tile = (int)(kSmemTarget / per_pv);
     pv_tile = pv_tile < 1 ? 1 : (pv_tile > kMaxPvTile ? kMaxPvTile : pv_tile);
-    const size_t smem = grad_smem(pv_tile, L, nacc, dep, rsize);
+    const size_t smem = grad_smem(pv_tile, L, nacc, dep, rsize, slots);
     const int npvt = (npv + pv_tile - 1) / pv_tile;
     const int gpc = groups_per_cta(npt);
     dim3 grid(grad_chunks(c, npt), npvt);

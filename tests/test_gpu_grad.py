@@ -3,8 +3,12 @@
 Each component g_j = sum_t gbar_t J_tj is a sum of terms of both signs, so
 its rounding error scales with S_j = sum_t |gbar_t J_tj| (the sum's
 condition), not with |g_j|.  The bound is |g_j - ref_j| <= rtol S_j with
-rtol 1e-10 (FP64 path) and 1e-5 (mixed path).  Determinism: a pv's
-gradient is bitwise identical alone and inside a batch.
+rtol 1e-10 (FP64 path) and 3e-5 (mixed path).  The mixed bound is set by
+the FP32 projected distance near the contact points: there d(area)/dz =
+-K/z varies like sqrt(1 + k - z), so an FP32 rounding of z (~1e-7) moves
+it by ~1e-7 / sqrt(1 + k - z); for a uniform disk, where every
+contribution comes from ingress and egress, this reaches ~1.3e-5 S.
+Determinism: a pv's gradient is bitwise identical alone and inside a batch.
 """
 import numpy as np
 import pytest
@@ -15,7 +19,7 @@ from paper_2009_08500_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 
-RTOL = {"fp64": 1e-10, "mixed": 1e-5}
+RTOL = {"fp64": 1e-10, "mixed": 3e-5}
 
 
 @pytest.fixture(scope="module")

@@ -156,9 +156,9 @@ rr_status check_eval(rr_ctx* c, const double* times, const int32_t* pb_index, in
 
 namespace rr {
 size_t records_bytes(const rr_ctx* c, int npv, bool grad) {
-    const int b = c->cfg.precision == RR_PREC_FP64 ? make_layout<double>(c->cfg.npb, c->cfg.ng, c->nldc, grad).bytes
-                                                   : make_layout<float>(c->cfg.npb, c->cfg.ng, c->nldc, grad).bytes;
-    return (size_t)npv * b;
+    const RecLayout L = c->cfg.precision == RR_PREC_FP64 ? make_layout<double>(c->cfg.npb, c->cfg.ng, c->nldc, grad)
+                                                         : make_layout<float>(c->cfg.npb, c->cfg.ng, c->nldc, grad);
+    return rows_offset(L, npv) + (size_t)npv * L.rows_bytes;
 }
 
 WsLayout ws_layout(const rr_ctx* c, int npv, int npt, bool grad) {

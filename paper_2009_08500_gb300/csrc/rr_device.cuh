@@ -71,7 +71,7 @@ __device__ __forceinline__ R lerp_row(const R* row, int ng, R g, R& slope_cell, 
     int i = (int)x;                       // x >= 0: truncation is floor
     i = i < ng - 2 ? i : ng - 2;
     const R al = x - R(i);
-    const R l0 = row[i], l1 = row[i + 1];
+    const R l0 = __ldg(row + i), l1 = __ldg(row + i + 1);
     slope_cell = (l1 - l0);
     cell = i;
     return l0 + al * (l1 - l0);
@@ -374,14 +374,28 @@ __device__ __forceinline__ int warp_excl_scan(int v, int& total) {
     return x - v;
 }
 
-// Candidate (j) holding flattened sample e: the last j with soff[j] <= e.
-__device__ __forceinline__ int find_cand(const int* soff, int nc, int e) {
-    int lo = 0, hi = nc;
-    while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (soff[mid] <= e) lo = mid; else hi = mid;
+// Walk the flattened samples of a candidate list 32 at a time.  For the
+// chunk starting at sample e0, candidate jf holds e0; the candidates that
+// start inside the chunk are marked in a 32-bit mask (one OR-reduction over
+// the warp), so lane l's candidate is jf + (starts at positions 1..l).
+struct ChunkWalk {
+    int jf;   // candidate holding the chunk's first sample (warp-uniform)
+};
+
+__device__ __forceinline__ int chunk_cand(ChunkWalk& cw, const int* soff, int nc, int e0) {
+    const int lane = threadIdx.x & 31;
+    if (cw.jf + 1 < nc && soff[cw.jf + 1] <= e0) ++cw.jf;   // warp-uniform
+    const int jn = cw.jf + 1 + lane;
+    unsigned bit = 0u;
+    if (jn < nc) {
+        const int pos = soff[jn] - e0;
+        if (pos > 0 && pos < 32) bit = 1u << pos;
     }
-    return lo;
+    const unsigned starts = __reduce_or_sync(0xffffffffu, bit);
+    const unsigned upto = lane == 31 ? 0xffffffffu : ((2u << lane) - 1u);
+    const int j = cw.jf + __popc(starts & upto);
+    cw.jf = __shfl_sync(0xffffffffu, j, 31);   // holds e0 + 31: the next chunk starts there or one later
+    return j;
 }
 
 // Passband constants staged in shared memory (indexing the by-value kernel

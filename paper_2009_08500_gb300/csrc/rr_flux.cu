@@ -47,6 +47,7 @@ __global__ void __launch_bounds__(kBlock, 4) rr_flux_mixed_kernel(const double* 
                                                                int npt, int npv, PbParams pbp, RecLayout L,
                                                                int pv_tile, int groups_per_cta,
                                                                const char* __restrict__ records,
+                                                               const char* __restrict__ rowsg,
                                                                float* __restrict__ flux,
                                                                int32_t* __restrict__ pv_status, int vec_store,
                                                                int* err) {
@@ -63,12 +64,12 @@ __global__ void __launch_bounds__(kBlock, 4) rr_flux_mixed_kernel(const double* 
     const int gend = min(ngroups, gbeg + groups_per_cta);
     const int pv0 = blockIdx.y * pv_tile;
     const int npv_t = min(pv_tile, npv - pv0);
-    const uint32_t bytes = (uint32_t)npv_t * (uint32_t)L.bytes;
+    const uint32_t bytes = (uint32_t)npv_t * (uint32_t)L.head_bytes;
     if (tid == 0) {
         *next_group = gbeg;
         mbar_init(bar, 1);
         mbar_expect_tx(bar, bytes);
-        const char* src = records + (size_t)pv0 * L.bytes;
+        const char* src = records + (size_t)pv0 * L.head_bytes;
         for (uint32_t off = 0; off < bytes; off += 65536u) {
             const uint32_t n = bytes - off < 65536u ? bytes - off : 65536u;
             bulk_g2s(recs + off, src + off, n, bar);
@@ -96,14 +97,14 @@ __global__ void __launch_bounds__(kBlock, 4) rr_flux_mixed_kernel(const double* 
         if (g >= gend) break;
         const int p0 = g * kWarpPts + 4 * lane;
         GroupState gs;
-        group_load(gs, pdt, ppb, times, g * kWarpPts, npt, recs, L.bytes, npv_t);
+        group_load(gs, pdt, ppb, times, g * kWarpPts, npt, recs, L.head_bytes, npv_t);
         float fbase[4];
         #pragma unroll
         for (int q = 0; q < 4; ++q) fbase[q] = gs.pbv[q] < L.npb ? 1.0f : nanf_;
         const bool full = vec_store && (p0 + 3 < npt);
         #pragma unroll 1
         for (int i = 0; i < npv_t; ++i) {
-            const char* rec = recs + (size_t)i * L.bytes;
+            const char* rec = recs + (size_t)i * L.head_bytes;
             const PvHead<float>& H = *reinterpret_cast<const PvHead<float>*>(rec);
             float* out = flux + (size_t)(pv0 + i) * npt + p0;
             const float4 c = group_pv(gs, H, i);
@@ -112,7 +113,7 @@ __global__ void __launch_bounds__(kBlock, 4) rr_flux_mixed_kernel(const double* 
                 f[0] = f[1] = f[2] = f[3] = nanf_;
             } else if (warp_may_transit(H, c, gs.wlo, gs.whi)) {
                 const PvPb<float>* PB = reinterpret_cast<const PvPb<float>*>(rec + L.off_pb);
-                const float* rows = reinterpret_cast<const float*>(rec + L.off_rows);
+                const float* rows = reinterpret_cast<const float*>(rowsg + (size_t)(pv0 + i) * L.rows_bytes);
                 unsigned cand = 0;
                 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
@@ -127,10 +128,12 @@ __global__ void __launch_bounds__(kBlock, 4) rr_flux_mixed_kernel(const double* 
                     int nc, base;
                     const int ns = build_list(wl, cand, gs.dh, gs.dl, gs.pbv, zero4, c.x, c.y, H.Bh, H.Bl, ps, nc,
                                               base);
+                    ChunkWalk cw{0};
                     for (int e0 = 0; e0 < ns; e0 += 32) {
                         const int e = e0 + lane;
                         const bool valid = e < ns;
-                        const int j = valid ? find_cand(wl->soff, nc, e) : -1;
+                        const int jc = chunk_cand(cw, wl->soff, nc, e0);
+                        const int j = valid ? jc : -1;
                         float d = 0.0f;
                         if (valid) {
                             const int pb = wl->pb[j];
@@ -205,6 +208,7 @@ __global__ void __launch_bounds__(kBlock) rr_flux_fp64_kernel(const double* __re
                                                               const int32_t* __restrict__ pb_index,
                                                               int npt, int npv, PbParams pbp, RecLayout L,
                                                               int pv_tile, const char* __restrict__ records,
+                                                              const char* __restrict__ rowsg,
                                                               double* __restrict__ flux,
                                                               int32_t* __restrict__ pv_status, int* err) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -214,7 +218,8 @@ __global__ void __launch_bounds__(kBlock) rr_flux_fp64_kernel(const double* __re
     const int pt0 = blockIdx.x * kPtTile;
     const int pv0 = blockIdx.y * pv_tile;
     const int npv_t = min(pv_tile, npv - pv0);
-    if (!stage_to_smem(recs, records + (size_t)pv0 * L.bytes, (uint32_t)npv_t * (uint32_t)L.bytes, bar, err))
+    if (!stage_to_smem(recs, records + (size_t)pv0 * L.head_bytes, (uint32_t)npv_t * (uint32_t)L.head_bytes, bar,
+                       err))
         return;
     double tv[kPPT];
     int pbv[kPPT];
@@ -232,10 +237,10 @@ __global__ void __launch_bounds__(kBlock) rr_flux_fp64_kernel(const double* __re
     const double nan_ = __longlong_as_double(0x7ff8000000000000ll);
     #pragma unroll 1
     for (int i = 0; i < npv_t; ++i) {
-        const char* rec = recs + (size_t)i * L.bytes;
+        const char* rec = recs + (size_t)i * L.head_bytes;
         const PvHead<double>& H = *reinterpret_cast<const PvHead<double>*>(rec);
         const PvPb<double>* PB = reinterpret_cast<const PvPb<double>*>(rec + L.off_pb);
-        const double* rows = reinterpret_cast<const double*>(rec + L.off_rows);
+        const double* rows = reinterpret_cast<const double*>(rowsg + (size_t)(pv0 + i) * L.rows_bytes);
         double* out = flux + (size_t)(pv0 + i) * npt;
         bool bad = false;
         #pragma unroll
@@ -296,8 +301,9 @@ cudaError_t launch_flux(rr_ctx* c, const double* times, const int32_t* pb_index,
     const bool f64 = c->cfg.precision == RR_PREC_FP64;
     RecLayout L = f64 ? make_layout<double>(c->cfg.npb, c->cfg.ng, c->nldc, false)
                       : make_layout<float>(c->cfg.npb, c->cfg.ng, c->nldc, false);
-    const int pv_tile = pv_tile_for(L.bytes);
-    const size_t smem = flux_smem(pv_tile, L.bytes, f64);
+    const int pv_tile = pv_tile_for(L.head_bytes);
+    const size_t smem = flux_smem(pv_tile, L.head_bytes, f64);
+    const char* rowsg = (const char*)records + rows_offset(L, npv);
     const int npvt = (npv + pv_tile - 1) / pv_tile;
     const int gpc = groups_per_cta(npt);
     const int ngroups = (npt + kWarpPts - 1) / kWarpPts;
@@ -308,14 +314,15 @@ cudaError_t launch_flux(rr_ctx* c, const double* times, const int32_t* pb_index,
         e = cudaFuncSetAttribute(rr_flux_fp64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         rr_flux_fp64_kernel<<<grid, kBlock, smem, s>>>(times, pb_index, npt, npv, pbp, L, pv_tile,
-                                                       (const char*)records, (double*)flux, pv_status,
+                                                       (const char*)records, rowsg, (double*)flux, pv_status,
                                                        c->d_err);
     } else {
         e = cudaFuncSetAttribute(rr_flux_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         const int vec = (npt % 4 == 0) && (((uintptr_t)flux & 15u) == 0);
         rr_flux_mixed_kernel<<<grid, kBlock, smem, s>>>(times, (const float2*)pts_dt, (const int32_t*)pts_pb, npt,
-                                                        npv, pbp, L, pv_tile, gpc, (const char*)records, (float*)flux,
+                                                        npv, pbp, L, pv_tile, gpc, (const char*)records, rowsg,
+                                                        (float*)flux,
                                                         pv_status, vec, c->d_err);
     }
     c->launches++;

@@ -42,11 +42,12 @@ __device__ __forceinline__ void grad_sample(const PvHead<R>& H, const PvPb<R>& p
     int i = (int)xg;
     i = i < L.ng - 2 ? i : L.ng - 2;
     const R al = xg - R(i);
-    const R d = rowblk[L.ng_pad + i];                 // row[i+1] - row[i]
-    const R Ib = rowblk[i] + al * d;
+    const R d = __ldg(rowblk + L.ng_pad + i);         // row[i+1] - row[i]
+    const R Ib = __ldg(rowblk + i) + al * d;
     const R dIdg = d * R(L.ng - 1);
     const R* rk = rowblk + 2 * L.ng_pad;
-    const R Ik = rk[i] + al * (rk[i + 1] - rk[i]);
+    const R rk0 = __ldg(rk + i);
+    const R Ik = rk0 + al * (__ldg(rk + i + 1) - rk0);
     const R ddz = dAdz * Ib + A * dIdg * pbc.inv1pk;
     const R ddk = dAdk * Ib + A * (Ik - dIdg * z * pbc.inv1pk * pbc.inv1pk);
 
@@ -99,7 +100,8 @@ __device__ __forceinline__ void grad_sample(const PvHead<R>& H, const PvPb<R>& p
     for (int cc = 0; cc < 4; ++cc) {
         if (cc < L.nldc) {
             const R* rq = rowblk + (size_t)(3 + cc) * L.ng_pad;
-            const R Q = rq[i] + al * (rq[i + 1] - rq[i]);
+            const R q0 = __ldg(rq + i);
+            const R Q = q0 + al * (__ldg(rq + i + 1) - q0);
             if (DEP) dep[(uslot + cc - 6) * kBlock] += gb * A * Q; else acc.u[cc] += gb * A * Q;
         }
     }
@@ -189,13 +191,14 @@ template <bool DEP>
 __global__ void __launch_bounds__(kBlock) rr_grad_mixed_kernel(
     const double* __restrict__ times, const float2* __restrict__ pdt, const int32_t* __restrict__ ppb, int npt,
     int npv, PbParams pbp, RecLayout L, int pv_tile, int groups_per_cta, const char* __restrict__ records,
-    const float* __restrict__ gflux, float* __restrict__ partials, int nacc, int chromatic,
+    const char* __restrict__ rowsg, const float* __restrict__ gflux, float* __restrict__ partials, int nacc,
+    int chromatic,
     int32_t* __restrict__ pv_status, int* err) {
     extern __shared__ __align__(16) unsigned char smem[];
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
     PbShared* ps = reinterpret_cast<PbShared*>(smem + kOffPb);
     char* recs = reinterpret_cast<char*>(smem + kOffRecs32);
-    float* gacc = reinterpret_cast<float*>(recs + (size_t)pv_tile * L.bytes);   // [pv][group][nacc]
+    float* gacc = reinterpret_cast<float*>(recs + (size_t)pv_tile * L.head_bytes);   // [pv][group][nacc]
     float* depcols = gacc + (size_t)pv_tile * groups_per_cta * nacc;
     int* next_group = reinterpret_cast<int*>(smem + kOffRed);
 
@@ -206,12 +209,12 @@ __global__ void __launch_bounds__(kBlock) rr_grad_mixed_kernel(
     const int gend = min(ngroups, gbeg + groups_per_cta);
     const int pv0 = blockIdx.y * pv_tile;
     const int npv_t = min(pv_tile, npv - pv0);
-    const uint32_t bytes = (uint32_t)npv_t * (uint32_t)L.bytes;
+    const uint32_t bytes = (uint32_t)npv_t * (uint32_t)L.head_bytes;
     if (tid == 0) {
         *next_group = gbeg;
         mbar_init(bar, 1);
         mbar_expect_tx(bar, bytes);
-        const char* src = records + (size_t)pv0 * L.bytes;
+        const char* src = records + (size_t)pv0 * L.head_bytes;
         for (uint32_t off = 0; off < bytes; off += 65536u) {
             const uint32_t n = bytes - off < 65536u ? bytes - off : 65536u;
             bulk_g2s(recs + off, src + off, n, bar);
@@ -241,15 +244,15 @@ __global__ void __launch_bounds__(kBlock) rr_grad_mixed_kernel(
         if (g >= gend) break;
         const int p0 = g * kWarpPts + 4 * lane;
         GroupState gs;
-        group_load(gs, pdt, ppb, times, g * kWarpPts, npt, recs, L.bytes, npv_t);
+        group_load(gs, pdt, ppb, times, g * kWarpPts, npt, recs, L.head_bytes, npv_t);
         #pragma unroll 1
         for (int i = 0; i < npv_t; ++i) {
-            const char* rec = recs + (size_t)i * L.bytes;
+            const char* rec = recs + (size_t)i * L.head_bytes;
             const PvHead<float>& H = *reinterpret_cast<const PvHead<float>*>(rec);
             const float4 c = group_pv(gs, H, i);
             if (H.status != 0 || !warp_may_transit(H, c, gs.wlo, gs.whi)) continue;   // warp-uniform
             const PvPb<float>* PB = reinterpret_cast<const PvPb<float>*>(rec + L.off_pb);
-            const float* rows = reinterpret_cast<const float*>(rec + L.off_rows);
+            const float* rows = reinterpret_cast<const float*>(rowsg + (size_t)(pv0 + i) * L.rows_bytes);
             const float* gf = gflux + (size_t)(pv0 + i) * npt + p0;
             unsigned cand = 0;
             float gbq[4];
@@ -277,8 +280,11 @@ __global__ void __launch_bounds__(kBlock) rr_grad_mixed_kernel(
             bool any = false, bad = false;
             int nc, base;
             const int ns = build_list(wl, cand, gs.dh, gs.dl, gs.pbv, gbq, c.x, c.y, H.Bh, H.Bl, ps, nc, base);
-            for (int e = lane; e < ns; e += 32) {
-                const int j = find_cand(wl->soff, nc, e);
+            ChunkWalk cw{0};
+            for (int e0 = 0; e0 < ns; e0 += 32) {
+                const int e = e0 + lane;
+                const int j = chunk_cand(cw, wl->soff, nc, e0);
+                if (e >= ns) continue;
                 const int pb = wl->pb[j];
                 const float4 cd = wl->cand[j];
                 const PvPb<float> pbc = PB[pb];
@@ -314,26 +320,28 @@ __global__ void __launch_bounds__(kBlock) rr_grad_mixed_kernel(
                                         gacc + ((size_t)i * groups_per_cta + (g - gbeg)) * nacc);
         }
     }
-    cta_partials_groups(gacc, recs, L.bytes, npv_t, nacc, groups_per_cta, pv0, blockIdx.x, gridDim.x, partials);
+    cta_partials_groups(gacc, recs, L.head_bytes, npv_t, nacc, groups_per_cta, pv0, blockIdx.x, gridDim.x,
+                        partials);
 }
 
 template <bool DEP>
 __global__ void __launch_bounds__(kBlock) rr_grad_fp64_kernel(
     const double* __restrict__ times, const int32_t* __restrict__ pb_index, int npt, int npv,
-    PbParams pbp, RecLayout L, int pv_tile, const char* __restrict__ records,
+    PbParams pbp, RecLayout L, int pv_tile, const char* __restrict__ records, const char* __restrict__ rowsg,
     const double* __restrict__ gflux, double* __restrict__ partials, int nacc, int chromatic,
     int32_t* __restrict__ pv_status, int* err) {
     extern __shared__ __align__(16) unsigned char smem[];
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
     char* recs = reinterpret_cast<char*>(smem + 16 + 16 * 4 + 16 * kMaxPvTile);
-    double* wpart = reinterpret_cast<double*>(recs + (size_t)pv_tile * L.bytes);
+    double* wpart = reinterpret_cast<double*>(recs + (size_t)pv_tile * L.head_bytes);
     double* depcols = wpart + (size_t)pv_tile * (kBlock >> 5) * nacc;
     const int tid = threadIdx.x, warp = tid >> 5;
     const int tile = blockIdx.x, ntiles = gridDim.x;
     const int pt0 = tile * kPtTile;
     const int pv0 = blockIdx.y * pv_tile;
     const int npv_t = min(pv_tile, npv - pv0);
-    if (!stage_to_smem(recs, records + (size_t)pv0 * L.bytes, (uint32_t)npv_t * (uint32_t)L.bytes, bar, err))
+    if (!stage_to_smem(recs, records + (size_t)pv0 * L.head_bytes, (uint32_t)npv_t * (uint32_t)L.head_bytes, bar,
+                       err))
         return;
     double tv[kPPT];
     int pbv[kPPT];
@@ -352,11 +360,11 @@ __global__ void __launch_bounds__(kBlock) rr_grad_fp64_kernel(
     double* dep = DEP ? depcols + tid : nullptr;
     #pragma unroll 1
     for (int i = 0; i < npv_t; ++i) {
-        const char* rec = recs + (size_t)i * L.bytes;
+        const char* rec = recs + (size_t)i * L.head_bytes;
         const PvHead<double>& H = *reinterpret_cast<const PvHead<double>*>(rec);
         if (H.status != 0) continue;
         const PvPb<double>* PB = reinterpret_cast<const PvPb<double>*>(rec + L.off_pb);
-        const double* rows = reinterpret_cast<const double*>(rec + L.off_rows);
+        const double* rows = reinterpret_cast<const double*>(rowsg + (size_t)(pv0 + i) * L.rows_bytes);
         const double* gf = gflux + (size_t)(pv0 + i) * npt;
         GradAcc<double> acc;
         for (int j = 0; j < 6; ++j) acc.o[j] = 0.0;
@@ -405,46 +413,49 @@ __global__ void __launch_bounds__(kBlock) rr_grad_fp64_kernel(
         }
         warp_partials<double, DEP>(acc, dep, nacc, any, wpart + ((size_t)i * (kBlock >> 5) + warp) * nacc);
     }
-    cta_partials<double>(wpart, recs, L.bytes, npv_t, nacc, pv0, tile, ntiles, partials);
+    cta_partials<double>(wpart, recs, L.head_bytes, npv_t, nacc, pv0, tile, ntiles, partials);
 }
 
-// Sum the per-tile partials of each pv in tile order; map the quadratic
-// coefficients (u1, u2) to Kipping's (q1, q2) where that law is used:
+// Sum the partial sums of each pv over its chunks in chunk order (FP64),
+// one lane per (pv, parameter).  Invalid pvs get NaN rows.
+template <typename R>
+__global__ void rr_grad_reduce_kernel(const R* __restrict__ partials, int nchunks, int nacc, int npv,
+                                      const char* __restrict__ heads, int head_bytes, double* __restrict__ grad) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)npv * nacc) return;
+    const int pv = (int)(idx / nacc), j = (int)(idx % nacc);
+    const PvHead<R>& H = *reinterpret_cast<const PvHead<R>*>(heads + (size_t)pv * head_bytes);
+    double s = 0.0;
+    const R* pp = partials + (size_t)pv * nchunks * nacc + j;
+    for (int t = 0; t < nchunks; ++t) s += (double)pp[(size_t)t * nacc];
+    grad[(size_t)pv * nacc + j] = H.status != 0 ? __longlong_as_double(0x7ff8000000000000ll) : s;
+}
+
+// Kipping's parametrisation: map d/du1, d/du2 to d/dq1, d/dq2 with
+// u1 = 2 sqrt(q1) q2, u2 = sqrt(q1) (1 - 2 q2):
 //   d/dq1 = d/du1 q2 / sqrt(q1) + d/du2 (1 - 2 q2) / (2 sqrt(q1))
 //   d/dq2 = d/du1 2 sqrt(q1) - d/du2 2 sqrt(q1)
-// Invalid pvs get NaN rows.
+// One lane per pv.
 template <typename R>
-__global__ void rr_grad_reduce_kernel(const R* __restrict__ partials, int ntiles, int nacc, int npv,
-                                      const char* __restrict__ records, int rec_bytes,
-                                      const double* __restrict__ params, int nparam, int ld_model, int npb,
-                                      int nkp, double* __restrict__ grad) {
-    const int pv = blockIdx.x * blockDim.y + threadIdx.y;
+__global__ void rr_grad_kipping_kernel(double* __restrict__ grad, const double* __restrict__ params, int nparam,
+                                       int npv, int npb, int nkp, const char* __restrict__ heads, int head_bytes) {
+    const int pv = blockIdx.x * blockDim.x + threadIdx.x;
     if (pv >= npv) return;
-    const PvHead<R>& H = *reinterpret_cast<const PvHead<R>*>(records + (size_t)pv * rec_bytes);
+    if (reinterpret_cast<const PvHead<R>*>(heads + (size_t)pv * head_bytes)->status != 0) return;
+    const double* row = params + (size_t)pv * nparam;
     double* out = grad + (size_t)pv * nparam;
-    const double nan_ = __longlong_as_double(0x7ff8000000000000ll);
-    for (int j = threadIdx.x; j < nacc; j += blockDim.x) {
-        double s = 0.0;
-        const R* pp = partials + (size_t)pv * ntiles * nacc + j;
-        for (int t = 0; t < ntiles; ++t) s += (double)pp[(size_t)t * nacc];
-        out[j] = H.status != 0 ? nan_ : s;
-    }
-    __syncwarp();
-    if (ld_model == RR_LD_QUADRATIC_TRI && threadIdx.x == 0 && H.status == 0) {
-        const double* row = params + (size_t)pv * nparam;
-        for (int pb = 0; pb < npb; ++pb) {
-            const int o = 6 + nkp + 2 * pb;
-            const double q1 = row[o], q2 = row[o + 1];
-            const double sq = sqrt(q1);
-            const double g1 = out[o], g2 = out[o + 1];
-            out[o] = g1 * q2 / sq + g2 * (1.0 - 2.0 * q2) / (2.0 * sq);
-            out[o + 1] = g1 * 2.0 * sq - g2 * 2.0 * sq;
-        }
+    for (int pb = 0; pb < npb; ++pb) {
+        const int o = 6 + nkp + 2 * pb;
+        const double q1 = row[o], q2 = row[o + 1];
+        const double sq = sqrt(q1);
+        const double g1 = out[o], g2 = out[o + 1];
+        out[o] = g1 * q2 / sq + g2 * (1.0 - 2.0 * q2) / (2.0 * sq);
+        out[o + 1] = g1 * 2.0 * sq - g2 * 2.0 * sq;
     }
 }
 
 static size_t grad_smem(int pv_tile, const RecLayout& L, int nacc, bool dep, size_t rsize, int slots) {
-    size_t s = (rsize == 8 ? 16 + 16 * 4 + 16 * kMaxPvTile : kOffRecs32) + (size_t)pv_tile * L.bytes +
+    size_t s = (rsize == 8 ? 16 + 16 * 4 + 16 * kMaxPvTile : kOffRecs32) + (size_t)pv_tile * L.head_bytes +
                (size_t)pv_tile * slots * nacc * rsize;
     if (dep) s += (size_t)(nacc - 6) * kBlock * rsize;
     return s;
@@ -484,10 +495,11 @@ cudaError_t launch_grad(rr_ctx* c, const double* times, const int32_t* pb_index,
     const size_t rsize = f64 ? 8 : 4;
     // pv tile: records plus the per-warp partial sums within the shared-memory target
     const int slots = f64 ? (kBlock >> 5) : groups_per_cta(npt);   // partial-sum slots per pv in the CTA
-    const size_t per_pv = (size_t)L.bytes + (size_t)slots * nacc * rsize;
+    const size_t per_pv = (size_t)L.head_bytes + (size_t)slots * nacc * rsize;
     int pv_tile = (int)(kSmemTarget / per_pv);
     pv_tile = pv_tile < 1 ? 1 : (pv_tile > kMaxPvTile ? kMaxPvTile : pv_tile);
     const size_t smem = grad_smem(pv_tile, L, nacc, dep, rsize, slots);
+    const char* rowsg = (const char*)records + rows_offset(L, npv);
     const int npvt = (npv + pv_tile - 1) / pv_tile;
     const int gpc = groups_per_cta(npt);
     dim3 grid(grad_chunks(c, npt), npvt);
@@ -499,7 +511,8 @@ cudaError_t launch_grad(rr_ctx* c, const double* times, const int32_t* pb_index,
         e = set_smem(KERNEL, smem);                                                                           \
         if (e != cudaSuccess) return e;                                                                       \
         KERNEL<<<grid, kBlock, smem, s>>>(times, pb_index, npt, npv, pbp, L, pv_tile, (const char*)records,   \
-                                          (const double*)grad_flux, (double*)partials, nacc, c->cfg.chromatic, \
+                                          rowsg, (const double*)grad_flux, (double*)partials, nacc,           \
+                                          c->cfg.chromatic,                                                   \
                                           pv_status, c->d_err);                                               \
     } while (0)
         if (dep) RR_LAUNCH_GRAD64(rr_grad_fp64_kernel<true>);
@@ -511,8 +524,9 @@ cudaError_t launch_grad(rr_ctx* c, const double* times, const int32_t* pb_index,
         e = set_smem(KERNEL, smem);                                                                          \
         if (e != cudaSuccess) return e;                                                                      \
         KERNEL<<<grid, kBlock, smem, s>>>(times, (const float2*)pts_dt, (const int32_t*)pts_pb, npt, npv, pbp, \
-                                          L, pv_tile, gpc, (const char*)records, (const float*)grad_flux,     \
-                                          (float*)partials, nacc, c->cfg.chromatic, pv_status, c->d_err);     \
+                                          L, pv_tile, gpc, (const char*)records, rowsg,                       \
+                                          (const float*)grad_flux, (float*)partials, nacc, c->cfg.chromatic,  \
+                                          pv_status, c->d_err);                                               \
     } while (0)
         if (dep) RR_LAUNCH_GRAD32(rr_grad_mixed_kernel<true>);
         else RR_LAUNCH_GRAD32(rr_grad_mixed_kernel<false>);
@@ -528,17 +542,26 @@ cudaError_t launch_grad_reduce(rr_ctx* c, int npt, const double* params, int npv
     RecLayout L = f64 ? make_layout<double>(c->cfg.npb, c->cfg.ng, c->nldc, true)
                       : make_layout<float>(c->cfg.npb, c->cfg.ng, c->nldc, true);
     const int nacc = c->nparam;
-    const int ntiles = grad_chunks(c, npt);
-    dim3 rb(32, 4);
+    const int nchunks = grad_chunks(c, npt);
     const int nkp = c->cfg.chromatic ? c->cfg.npb : 1;
+    const long long n = (long long)npv * nacc;
+    const unsigned blocks = (unsigned)((n + 255) / 256);
     if (f64)
-        rr_grad_reduce_kernel<double><<<(npv + 3) / 4, rb, 0, s>>>((const double*)partials, ntiles, nacc, npv,
-                                                                   (const char*)records, L.bytes, params, c->nparam,
-                                                                   c->cfg.ld_model, c->cfg.npb, nkp, grad_params);
+        rr_grad_reduce_kernel<double><<<blocks, 256, 0, s>>>((const double*)partials, nchunks, nacc, npv,
+                                                             (const char*)records, L.head_bytes, grad_params);
     else
-        rr_grad_reduce_kernel<float><<<(npv + 3) / 4, rb, 0, s>>>((const float*)partials, ntiles, nacc, npv,
-                                                                  (const char*)records, L.bytes, params, c->nparam,
-                                                                  c->cfg.ld_model, c->cfg.npb, nkp, grad_params);
+        rr_grad_reduce_kernel<float><<<blocks, 256, 0, s>>>((const float*)partials, nchunks, nacc, npv,
+                                                            (const char*)records, L.head_bytes, grad_params);
+    c->launches++;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || c->cfg.ld_model != RR_LD_QUADRATIC_TRI) return e;
+    const unsigned b2 = (unsigned)((npv + 127) / 128);
+    if (f64)
+        rr_grad_kipping_kernel<double><<<b2, 128, 0, s>>>(grad_params, params, c->nparam, npv, c->cfg.npb, nkp,
+                                                          (const char*)records, L.head_bytes);
+    else
+        rr_grad_kipping_kernel<float><<<b2, 128, 0, s>>>(grad_params, params, c->nparam, npv, c->cfg.npb, nkp,
+                                                         (const char*)records, L.head_bytes);
     c->launches++;
     return cudaGetLastError();
 }

@@ -69,9 +69,13 @@ struct alignas(16) PvPb {
     float pad[3];
 };
 
+// Per-pv records live in two regions of the workspace: the headers (PvHead +
+// one PvPb per passband; staged into shared memory by the kernels) and the
+// profile rows (read through the cache hierarchy where a transit needs them).
 struct RecLayout {
     int32_t npb, ng, ng_pad, rows_per_pb;  // rows: 1 (flux) or 3 + nldc (adjoint)
-    int32_t nldc, off_pb, off_rows, bytes; // byte offsets inside a record; record stride
+    int32_t nldc, off_pb;                  // byte offset of the PvPb array in a header
+    int32_t head_bytes, rows_bytes;        // per-pv strides of the two regions (multiples of 16)
 };
 
 template <typename R>
@@ -83,10 +87,14 @@ inline RecLayout make_layout(int npb, int ng, int nldc, bool grad) {
     L.nldc = nldc;
     L.rows_per_pb = grad ? 3 + nldc : 1;
     L.off_pb = (int32_t)sizeof(PvHead<R>);
-    L.off_rows = L.off_pb + npb * (int32_t)sizeof(PvPb<R>);
-    size_t bytes = (size_t)L.off_rows + (size_t)npb * L.rows_per_pb * L.ng_pad * sizeof(R);
-    L.bytes = (int32_t)((bytes + 15) & ~(size_t)15);
+    L.head_bytes = (int32_t)(((size_t)L.off_pb + npb * sizeof(PvPb<R>) + 15) & ~(size_t)15);
+    L.rows_bytes = (int32_t)(((size_t)npb * L.rows_per_pb * L.ng_pad * sizeof(R) + 15) & ~(size_t)15);
     return L;
+}
+
+// Start of the rows region after npv headers.
+__host__ __device__ inline size_t rows_offset(const RecLayout& L, int npv) {
+    return ((size_t)npv * L.head_bytes + 255) & ~(size_t)255;
 }
 
 // Passband sampling constants, passed by value.

@@ -201,10 +201,37 @@ __device__ double mean_anomaly_of_true(double f, double e) {
     return E - e * sin(E);
 }
 
-// Pvs per CTA of the set-up kernel: the FP64 scalar work of a pv runs on one
-// thread (kSetupPv threads in parallel per CTA); the profile rows of all
-// kSetupPv pvs are then computed by the whole CTA.
-constexpr int kSetupPv = 8;
+// Math in the record's precision R (FP32 scalar set-up for the mixed form;
+// its window margins absorb FP32 rounding).
+__device__ __forceinline__ float r_atan2(float y, float x) { return atan2f(y, x); }
+__device__ __forceinline__ double r_atan2(double y, double x) { return atan2(y, x); }
+__device__ __forceinline__ float r_asin(float x) { return asinf(x); }
+__device__ __forceinline__ double r_asin(double x) { return asin(x); }
+__device__ __forceinline__ float r_fmod(float x, float y) { return fmodf(x, y); }
+__device__ __forceinline__ double r_fmod(double x, double y) { return fmod(x, y); }
+__device__ __forceinline__ float r_max(float x, float y) { return fmaxf(x, y); }
+__device__ __forceinline__ double r_max(double x, double y) { return fmax(x, y); }
+
+template <typename R>
+__device__ R wrap_2pi_r(R x) {
+    const R tp = R(2) * Tr<R>::pi();
+    x = r_fmod(x, tp);
+    return x < R(0) ? x + tp : x;
+}
+
+template <typename R>
+__device__ R mean_anomaly_of_true_r(R f, R e) {
+    R sh, ch;
+    d_sincos(R(0.5) * f, &sh, &ch);
+    const R E = R(2) * r_atan2(d_sqrt(R(1) - e) * sh, d_sqrt(R(1) + e) * ch);
+    R sE, cE;
+    d_sincos(E, &sE, &cE);
+    return E - e * sE;
+}
+
+// Pvs per CTA of the set-up kernel: one lane per pv for the scalar orbit
+// set-up (all lanes of a warp busy), then the whole CTA for the rows.
+template <typename R> struct SetupPvs { static constexpr int N = sizeof(R) == sizeof(float) ? 32 : 8; };
 
 template <typename R>
 __global__ void __launch_bounds__(256) rr_pv_setup_kernel(ModelParams mp, PbParams pbp,
@@ -213,19 +240,20 @@ __global__ void __launch_bounds__(256) rr_pv_setup_kernel(ModelParams mp, PbPara
                                                           const double* __restrict__ istar,
                                                           RecLayout L, int grad, char* __restrict__ records,
                                                           int32_t* __restrict__ pv_status) {
-    __shared__ double u_s[kSetupPv][RR_MAX_PB][4];
-    __shared__ double Is_s[kSetupPv][RR_MAX_PB];
-    __shared__ double ak_s[kSetupPv][RR_MAX_PB];
-    __shared__ int ik_s[kSetupPv][RR_MAX_PB];
-    __shared__ int st_s[kSetupPv];
-    const int pv0 = blockIdx.x * kSetupPv;
-    const int nloc = min(kSetupPv, npv - pv0);
+    constexpr int NP = SetupPvs<R>::N;
+    __shared__ R u_s[NP][RR_MAX_PB][4];
+    __shared__ R invIs_s[NP][RR_MAX_PB];
+    __shared__ R ak_s[NP][RR_MAX_PB];
+    __shared__ int ik_s[NP][RR_MAX_PB];
+    __shared__ int st_s[NP];
+    const int pv0 = blockIdx.x * NP;
+    const int nloc = min(NP, npv - pv0);
     const int nkp = mp.chromatic ? mp.npb : 1;
     const int tid = threadIdx.x;
-    if (tid < kSetupPv) st_s[tid] = 0;
+    if (tid < NP) st_s[tid] = 0;
     __syncthreads();
 
-    // (1) per (pv, passband): validity, LD coefficients, I_star, k cell -- one thread each
+    // (1) per (pv, passband): validity, LD coefficients, I_star, k cell
     for (int t = tid; t < nloc * mp.npb; t += blockDim.x) {
         const int lp = t / mp.npb, pb = t % mp.npb;
         const double* row = params + (size_t)(pv0 + lp) * mp.nparam;
@@ -254,32 +282,32 @@ __global__ void __launch_bounds__(256) rr_pv_setup_kernel(ModelParams mp, PbPara
         const double x = (k - mp.k0) / mp.dk;
         int ik = (int)floor(x);
         ik = ik < 0 ? 0 : (ik > mp.nk - 2 ? mp.nk - 2 : ik);
-        for (int j = 0; j < 4; ++j) u_s[lp][pb][j] = u[j];
-        Is_s[lp][pb] = Is;
+        for (int j = 0; j < 4; ++j) u_s[lp][pb][j] = (R)u[j];
+        invIs_s[lp][pb] = (R)(1.0 / Is);
         ik_s[lp][pb] = ik;
-        ak_s[lp][pb] = x - ik;
+        ak_s[lp][pb] = (R)(x - ik);
         if (st) atomicOr(&st_s[lp], st);
     }
     __syncthreads();
 
-    // (2) per pv: orbit constants and transit windows (FP64)
+    // (2) per pv, one lane each: orbit constants and transit windows
     if (tid < nloc) {
         const int pv = pv0 + tid;
         const double* row = params + (size_t)pv * mp.nparam;
-        char* rec = records + (size_t)pv * L.bytes;
+        char* rec = records + (size_t)pv * L.head_bytes;
         PvHead<R>* H = reinterpret_cast<PvHead<R>*>(rec);
         PvPb<R>* PB = reinterpret_cast<PvPb<R>*>(rec + L.off_pb);
-        const double T0 = row[0], P = row[1], a = row[2], b = row[3], e = row[4], w = row[5];
+        const double T0 = row[0], P = row[1], ad = row[2], bd = row[3], ed = row[4], wd = row[5];
         bool finite = true;
         for (int j = 0; j < mp.nparam; ++j) finite = finite && isfinite(row[j]);
         int st = st_s[tid];
         if (!finite) {
             st = RR_PV_NONFINITE;
         } else {
-            if (!(e >= 0.0 && e < 1.0)) st |= RR_PV_E_RANGE;
+            if (!(ed >= 0.0 && ed < 1.0)) st |= RR_PV_E_RANGE;
             if (!(P > 0.0)) st |= RR_PV_P_RANGE;
-            if (!(a > 1.0)) st |= RR_PV_A_RANGE;
-            if (!(b >= 0.0 && b <= a)) st |= RR_PV_B_RANGE;
+            if (!(ad > 1.0)) st |= RR_PV_A_RANGE;
+            if (!(bd >= 0.0 && bd <= ad)) st |= RR_PV_B_RANGE;
         }
         st_s[tid] = st;
         H->status = st;
@@ -289,20 +317,23 @@ __global__ void __launch_bounds__(256) rr_pv_setup_kernel(ModelParams mp, PbPara
         H->pad3 = 0;
         H->pad4 = 0;
         if (st == 0) {
-            const double f0 = 0.5 * CUDART_PI - w;
-            const double E0 = 2.0 * atan2(sqrt(1.0 - e) * sin(0.5 * f0), sqrt(1.0 + e) * cos(0.5 * f0));
-            double sE0, cE0;
-            sincos(E0, &sE0, &cE0);
-            const double M0 = E0 - e * sE0;
-            const double se = sqrt(1.0 - e * e);
-            double sw, cw;
-            sincos(w, &sw, &cw);
-            const double den0 = 1.0 - e * cE0;
+            const R a = (R)ad, b = (R)bd, e = (R)ed, w = (R)wd;
+            const R pi = Tr<R>::pi();
+            const R f0 = R(0.5) * pi - w;
+            R sh, ch;
+            d_sincos(R(0.5) * f0, &sh, &ch);
+            const R E0 = R(2) * r_atan2(d_sqrt(R(1) - e) * sh, d_sqrt(R(1) + e) * ch);
+            R sE0, cE0, sw, cw;
+            d_sincos(E0, &sE0, &cE0);
+            d_sincos(w, &sw, &cw);
+            const R M0 = E0 - e * sE0;
+            const R se = d_sqrt(R(1) - e * e);
+            const R den0 = R(1) - e * cE0;
             const double invP = 1.0 / P;
-            const double n = 2.0 * CUDART_PI * invP;
-            double ax1, ax2, ay1, ay2, rho0;
-            if (e == 0.0) {
-                ax1 = 0.0; ax2 = -1.0; ay1 = -1.0; ay2 = 0.0; rho0 = 1.0;
+            const R n = (R)(2.0 * CUDART_PI * invP);
+            R ax1, ax2, ay1, ay2, rho0;
+            if (ed == 0.0) {
+                ax1 = R(0); ax2 = R(-1); ay1 = R(-1); ay2 = R(0); rho0 = R(1);
             } else {
                 ax1 = -cw * cE0 + sw * se * sE0;
                 ax2 = -cw * sE0 - sw * se * cE0;
@@ -310,44 +341,51 @@ __global__ void __launch_bounds__(256) rr_pv_setup_kernel(ModelParams mp, PbPara
                 ay2 = -sw * sE0 + cw * se * cE0;
                 rho0 = den0;
             }
-            const double inv_den0 = 1.0 / den0;
             H->T0 = T0; H->P = P; H->invP = invP;
-            H->ecE0d = e * cE0; H->esE0d = e * sE0; H->inv_den0d = inv_den0;
+            if (ed > kESwitch) {
+                // the FP64 Kepler constants of the e -> 1 branch
+                const double f0d = 0.5 * CUDART_PI - wd;
+                const double E0d = 2.0 * atan2(sqrt(1.0 - ed) * sin(0.5 * f0d), sqrt(1.0 + ed) * cos(0.5 * f0d));
+                const double cE0d = cos(E0d), sE0d = sin(E0d);
+                H->ecE0d = ed * cE0d; H->esE0d = ed * sE0d; H->inv_den0d = 1.0 / (1.0 - ed * cE0d);
+            } else {
+                H->ecE0d = (double)(e * cE0); H->esE0d = (double)(e * sE0); H->inv_den0d = (double)(R(1) / den0);
+            }
             H->padf[0] = H->padf[1] = H->padf[2] = 0.0f;
-            H->a = (R)a; H->b = (R)b; H->a2 = (R)(a * a); H->b2 = (R)(b * b);
-            H->e = (R)e; H->ecE0 = (R)(e * cE0); H->esE0 = (R)(e * sE0); H->inv_den0 = (R)inv_den0;
-            H->ax1 = (R)ax1; H->ax2 = (R)ax2; H->ay1 = (R)ay1; H->ay2 = (R)ay2;
-            H->rho0 = (R)rho0; H->n = (R)n;
+            H->a = a; H->b = b; H->a2 = a * a; H->b2 = b * b;
+            H->e = e; H->ecE0 = e * cE0; H->esE0 = e * sE0; H->inv_den0 = R(1) / den0;
+            H->ax1 = ax1; H->ax2 = ax2; H->ay1 = ay1; H->ay2 = ay2;
+            H->rho0 = rho0; H->n = n;
             const float Bh = (float)invP;
             H->Bh = (R)Bh; H->Bl = (R)(float)(invP - (double)Bh);
-            H->dM0de = (R)(-den0 * sE0 / (1.0 - e * e) - sE0);
-            H->dM0dw = (R)(-den0 * den0 / se);
-            H->se = (R)se; H->cw = (R)cw; H->sw = (R)sw; H->cE0 = (R)cE0; H->sE0 = (R)sE0; H->inv_se = (R)(1.0 / se);
+            H->dM0de = -den0 * sE0 / (R(1) - e * e) - sE0;
+            H->dM0dw = -den0 * den0 / se;
+            H->se = se; H->cw = cw; H->sw = sw; H->cE0 = cE0; H->sE0 = sE0; H->inv_se = R(1) / se;
             int flags = 0;
-            if (e == 0.0) flags |= kPvCircular;
-            if (e > kESwitch) flags |= kPvKepler64;
-            double wmax = 0.0;
-            const double ra = a * (1.0 - e);
+            if (ed == 0.0) flags |= kPvCircular;
+            if (ed > kESwitch) flags |= kPvKepler64;
+            R wmax = R(0);
+            const R ra = a * (R(1) - e);
             for (int pb = 0; pb < mp.npb; ++pb) {
-                const double k = row[6 + (mp.chromatic ? pb : 0)];
-                const double q = (1.0 + k) / ra;
-                const double df = q >= 1.0 ? 0.5 * CUDART_PI : asin(q);
-                const double hi = wrap_2pi(mean_anomaly_of_true(f0 + df, e) - M0);
-                const double lo = wrap_2pi(M0 - mean_anomaly_of_true(f0 - df, e));
-                double win = fmax(hi, lo);
-                win += 1e-5 * (1.0 + win);
+                const R k = (R)row[6 + (mp.chromatic ? pb : 0)];
+                const R q = (R(1) + k) / ra;
+                const R df = q >= R(1) ? R(0.5) * pi : r_asin(q);
+                const R hi = wrap_2pi_r(mean_anomaly_of_true_r(f0 + df, e) - M0);
+                const R lo = wrap_2pi_r(M0 - mean_anomaly_of_true_r(f0 - df, e));
+                R win = r_max(hi, lo);
+                win += R(1e-5) * (R(1) + win);
                 const int ss = pbp.ss[pb];
-                const double half = 0.5 * pbp.exptime[pb] * (1.0 - 1.0 / ss);
-                double winp = win + n * (ss > 1 ? half : 0.0) * (1.0 + 1e-6);
-                if (win >= CUDART_PI) { win = 1e30; flags |= kPvNoWindow; }
-                if (winp >= CUDART_PI) winp = 1e30;
-                PB[pb].k = (R)k;
-                PB[pb].inv1pk = (R)(1.0 / (1.0 + k));
-                PB[pb].win_s = (R)win;
-                PB[pb].win_p = (R)winp;
-                PB[pb].win_pc = (float)(winp * (0.5 / CUDART_PI));
+                const R half = R(0.5) * (R)pbp.exptime[pb] * (R(1) - R(1) / R(ss));
+                R winp = win + n * (ss > 1 ? half : R(0)) * R(1.000001);
+                if (win >= pi) { win = R(1e30); flags |= kPvNoWindow; }
+                if (winp >= pi) winp = R(1e30);
+                PB[pb].k = k;
+                PB[pb].inv1pk = R(1) / (R(1) + k);
+                PB[pb].win_s = win;
+                PB[pb].win_p = winp;
+                PB[pb].win_pc = (float)(winp * (R(0.5) / pi));
                 PB[pb].pad[0] = PB[pb].pad[1] = PB[pb].pad[2] = 0.0f;
-                wmax = fmax(wmax, winp * (0.5 / CUDART_PI));
+                wmax = r_max(wmax, winp * (R(0.5) / pi));
             }
             H->wmax_c = (float)wmax;
             H->flags = flags;
@@ -356,31 +394,32 @@ __global__ void __launch_bounds__(256) rr_pv_setup_kernel(ModelParams mp, PbPara
     __syncthreads();
 
     // (3) profile rows of all pvs of the CTA: the k-interpolated combination of
-    // the basis projections, divided by I_star (arithmetic in R)
+    // the basis projections times 1 / I_star (arithmetic in R)
     const size_t kstride = (size_t)mp.ng;
     const size_t bstride = (size_t)mp.nk * mp.ng;
     const R inv_dk = (R)(1.0 / mp.dk);
     const int per_pv = mp.npb * L.ng_pad;
+    char* rows_region = records + rows_offset(L, npv);
     for (int t = tid; t < nloc * per_pv; t += blockDim.x) {
         const int lp = t / per_pv, rem = t % per_pv;
         const int pb = rem / L.ng_pad, ig = rem % L.ng_pad;
         if (st_s[lp] != 0) continue;
-        R* r0 = reinterpret_cast<R*>(records + (size_t)(pv0 + lp) * L.bytes + L.off_rows) +
+        R* r0 = reinterpret_cast<R*>(rows_region + (size_t)(pv0 + lp) * L.rows_bytes) +
                 (size_t)pb * L.rows_per_pb * L.ng_pad;
         if (ig >= mp.ng) {
             for (int r = 0; r < L.rows_per_pb; ++r) r0[(size_t)r * L.ng_pad + ig] = (R)0;
             continue;
         }
         const int ik = ik_s[lp][pb];
-        const R ak = (R)ak_s[lp][pb];
-        const R invIs = (R)(1.0 / Is_s[lp][pb]);
+        const R ak = ak_s[lp][pb];
+        const R invIs = invIs_s[lp][pb];
         const int b0 = mp.ld_model == RR_LD_TABULATED ? pb : 0;
         const R* T0p = T + (size_t)b0 * bstride + (size_t)ik * kstride + ig;
         R lo = T0p[0], hi = T0p[kstride];
         if (mp.ld_model != RR_LD_TABULATED) {
             for (int c = 0; c < mp.nldc; ++c) {
                 const R* Tc = T + (size_t)(1 + c) * bstride + (size_t)ik * kstride + ig;
-                const R uc = (R)u_s[lp][pb][c];
+                const R uc = u_s[lp][pb][c];
                 lo += uc * Tc[0];
                 hi += uc * Tc[kstride];
             }
@@ -401,7 +440,7 @@ __global__ void __launch_bounds__(256) rr_pv_setup_kernel(ModelParams mp, PbPara
                 }
                 if (mp.ld_model != RR_LD_TABULATED) {
                     for (int c = 0; c < mp.nldc; ++c) {
-                        const R uc = (R)u_s[lp][pb][c];
+                        const R uc = u_s[lp][pb][c];
                         if (sizeof(R) == sizeof(double)) {
                             const R* Tc = T + (size_t)(1 + c) * bstride + (size_t)ik * kstride + ig;
                             dlo += uc * (Tc[1] - Tc[0]);
@@ -469,12 +508,13 @@ cudaError_t launch_weights(rr_ctx* c, bool need_w, cudaStream_t s) {
 cudaError_t launch_pv_setup(rr_ctx* c, const double* params, int npv, const PbParams& pbp, bool grad,
                             void* records, int32_t* pv_status, cudaStream_t s) {
     ModelParams mp = model_params(c);
-    const int blocks = (npv + kSetupPv - 1) / kSetupPv;
     if (c->cfg.precision == RR_PREC_FP64) {
+        const int blocks = (npv + SetupPvs<double>::N - 1) / SetupPvs<double>::N;
         RecLayout L = make_layout<double>(c->cfg.npb, c->cfg.ng, c->nldc, grad);
         rr_pv_setup_kernel<double><<<blocks, 256, 0, s>>>(mp, pbp, params, npv, c->d_T64, c->d_DT32, c->d_istar, L,
                                                           grad ? 1 : 0, (char*)records, pv_status);
     } else {
+        const int blocks = (npv + SetupPvs<float>::N - 1) / SetupPvs<float>::N;
         RecLayout L = make_layout<float>(c->cfg.npb, c->cfg.ng, c->nldc, grad);
         rr_pv_setup_kernel<float><<<blocks, 256, 0, s>>>(mp, pbp, params, npv, c->d_T32, c->d_DT32, c->d_istar, L,
                                                          grad ? 1 : 0, (char*)records, pv_status);

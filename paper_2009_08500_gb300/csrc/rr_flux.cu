@@ -41,6 +41,7 @@ __global__ void rr_points_kernel(const double* __restrict__ times, const int32_t
     pbw[p] = (pb >= 0 && pb < npb) ? pb : npb;
 }
 
+template <bool STAGE_ROWS>
 __global__ void __launch_bounds__(kBlock, 4) rr_flux_mixed_kernel(const double* __restrict__ times,
                                                                const float2* __restrict__ pdt,
                                                                const int32_t* __restrict__ ppb,
@@ -64,15 +65,23 @@ __global__ void __launch_bounds__(kBlock, 4) rr_flux_mixed_kernel(const double* 
     const int gend = min(ngroups, gbeg + groups_per_cta);
     const int pv0 = blockIdx.y * pv_tile;
     const int npv_t = min(pv_tile, npv - pv0);
-    const uint32_t bytes = (uint32_t)npv_t * (uint32_t)L.head_bytes;
+    // staged: headers of the tile, then (STAGE_ROWS) their profile rows
+    char* srows = recs + (size_t)pv_tile * L.head_bytes;
+    const uint32_t hbytes = (uint32_t)npv_t * (uint32_t)L.head_bytes;
+    const uint32_t rbytes = STAGE_ROWS ? (uint32_t)npv_t * (uint32_t)L.rows_bytes : 0u;
     if (tid == 0) {
         *next_group = gbeg;
         mbar_init(bar, 1);
-        mbar_expect_tx(bar, bytes);
+        mbar_expect_tx(bar, hbytes + rbytes);
         const char* src = records + (size_t)pv0 * L.head_bytes;
-        for (uint32_t off = 0; off < bytes; off += 65536u) {
-            const uint32_t n = bytes - off < 65536u ? bytes - off : 65536u;
+        for (uint32_t off = 0; off < hbytes; off += 65536u) {
+            const uint32_t n = hbytes - off < 65536u ? hbytes - off : 65536u;
             bulk_g2s(recs + off, src + off, n, bar);
+        }
+        const char* rsrc = rowsg + (size_t)pv0 * L.rows_bytes;
+        for (uint32_t off = 0; off < rbytes; off += 65536u) {
+            const uint32_t n = rbytes - off < 65536u ? rbytes - off : 65536u;
+            bulk_g2s(srows + off, rsrc + off, n, bar);
         }
     }
     stage_pb(pbp, ps);
@@ -113,7 +122,8 @@ __global__ void __launch_bounds__(kBlock, 4) rr_flux_mixed_kernel(const double* 
                 f[0] = f[1] = f[2] = f[3] = nanf_;
             } else if (warp_may_transit(H, c, gs.wlo, gs.whi)) {
                 const PvPb<float>* PB = reinterpret_cast<const PvPb<float>*>(rec + L.off_pb);
-                const float* rows = reinterpret_cast<const float*>(rowsg + (size_t)(pv0 + i) * L.rows_bytes);
+                const float* rows = STAGE_ROWS ? reinterpret_cast<const float*>(srows + (size_t)i * L.rows_bytes)
+                                               : reinterpret_cast<const float*>(rowsg + (size_t)(pv0 + i) * L.rows_bytes);
                 unsigned cand = 0;
                 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
@@ -301,8 +311,11 @@ cudaError_t launch_flux(rr_ctx* c, const double* times, const int32_t* pb_index,
     const bool f64 = c->cfg.precision == RR_PREC_FP64;
     RecLayout L = f64 ? make_layout<double>(c->cfg.npb, c->cfg.ng, c->nldc, false)
                       : make_layout<float>(c->cfg.npb, c->cfg.ng, c->nldc, false);
-    const int pv_tile = pv_tile_for(L.head_bytes);
-    const size_t smem = flux_smem(pv_tile, L.head_bytes, f64);
+    // FP32 kernel: headers and rows of the tile in shared memory (rows are read
+    // by every transit sub-exposure); FP64 kernel: headers only
+    const int per_pv = f64 ? L.head_bytes : L.head_bytes + L.rows_bytes;
+    const int pv_tile = pv_tile_for(per_pv);
+    const size_t smem = flux_smem(pv_tile, per_pv, f64);
     const char* rowsg = (const char*)records + rows_offset(L, npv);
     const int npvt = (npv + pv_tile - 1) / pv_tile;
     const int gpc = groups_per_cta(npt);
@@ -317,10 +330,10 @@ cudaError_t launch_flux(rr_ctx* c, const double* times, const int32_t* pb_index,
                                                        (const char*)records, rowsg, (double*)flux, pv_status,
                                                        c->d_err);
     } else {
-        e = cudaFuncSetAttribute(rr_flux_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = cudaFuncSetAttribute(rr_flux_mixed_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         const int vec = (npt % 4 == 0) && (((uintptr_t)flux & 15u) == 0);
-        rr_flux_mixed_kernel<<<grid, kBlock, smem, s>>>(times, (const float2*)pts_dt, (const int32_t*)pts_pb, npt,
+        rr_flux_mixed_kernel<true><<<grid, kBlock, smem, s>>>(times, (const float2*)pts_dt, (const int32_t*)pts_pb, npt,
                                                         npv, pbp, L, pv_tile, gpc, (const char*)records, rowsg,
                                                         (float*)flux,
                                                         pv_status, vec, c->d_err);

@@ -188,7 +188,7 @@ __device__ __forceinline__ void cta_partials_groups(const float* gacc, const cha
 }
 
 template <bool DEP>
-__global__ void __launch_bounds__(kBlock) rr_grad_mixed_kernel(
+__global__ void __launch_bounds__(kBlock, 3) rr_grad_mixed_kernel(
     const double* __restrict__ times, const float2* __restrict__ pdt, const int32_t* __restrict__ ppb, int npt,
     int npv, PbParams pbp, RecLayout L, int pv_tile, int groups_per_cta, const char* __restrict__ records,
     const char* __restrict__ rowsg, const float* __restrict__ gflux, float* __restrict__ partials, int nacc,

@@ -27,7 +27,7 @@ constexpr int kBlock = 256;               // threads per CTA in the per-point ke
 constexpr int kPPT = 4;                   // points per thread
 constexpr int kPtTile = kBlock * kPPT;    // points per CTA
 constexpr int kMaxPvTile = 32;            // parameter vectors per CTA (upper bound)
-constexpr int kSmemTarget = 24 * 1024;    // record bytes per CTA the tiler aims for
+constexpr int kSmemTarget = 32 * 1024;    // record bytes per CTA the tiler aims for
 constexpr int kMaxNz = 4096;
 constexpr size_t kMaxSmem = 227 * 1024;   // dynamic shared memory per CTA on sm_103a
 constexpr int kMaxBasis = RR_MAX_PB + 4;  // profile bases: 1 + nldc (named) or npb (tabulated)

@@ -71,7 +71,8 @@ __device__ __forceinline__ R lerp_row(const R* row, int ng, R g, R& slope_cell, 
     int i = (int)x;                       // x >= 0: truncation is floor
     i = i < ng - 2 ? i : ng - 2;
     const R al = x - R(i);
-    const R l0 = __ldg(row + i), l1 = __ldg(row + i + 1);
+    // plain loads: `row` may point to shared memory (staged rows) or to global memory
+    const R l0 = row[i], l1 = row[i + 1];
     slope_cell = (l1 - l0);
     cell = i;
     return l0 + al * (l1 - l0);

@@ -27,7 +27,8 @@ struct GradAcc {
     R u[4];
 };
 
-// Contribution of one sub-exposure; gb = -gbar / ss.
+// Contribution of one sub-exposure; gb = -gbar / ss.  rowblk points to
+// global memory (read through the read-only data path).
 template <typename R, bool DEP>
 __device__ __forceinline__ void grad_sample(const PvHead<R>& H, const PvPb<R>& pbc,
                                             const R* __restrict__ rowblk, const RecLayout& L, R z,

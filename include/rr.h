@@ -151,6 +151,35 @@ rr_status rr_evaluate(rr_ctx* ctx, const double* times, const int32_t* pb_index,
                       const double* exptime, void* flux, int32_t* pv_status, void* workspace,
                       size_t workspace_bytes, void* stream);
 
+/* rr_evaluate without a caller-provided workspace.  The paper has no
+ * counterpart: this exists for callers that cannot allocate device memory
+ * when they evaluate -- for example code that runs where CUDA allocation
+ * calls are not allowed (such as a host function enqueued on a stream), or
+ * an application that hands all device memory to its own allocator up front
+ * and has none left to lend.  The scratch this call needs (per-pv records
+ * and per-time inputs, as counted by rr_workspace_bytes(ctx, npv, npt, 0))
+ * lives in a fixed array of RR_NOALLOC_SCRATCH_BYTES inside the library,
+ * which every GPU that loads the library holds until the process exits.
+ *   - Allocates nothing: no cudaMalloc/cudaFree and no allocating library
+ *     routine.  Arguments as rr_evaluate, minus the workspace.
+ *   - Batches needing more than RR_NOALLOC_SCRATCH_BYTES are rejected with
+ *     RR_EINVAL and a message naming the sizes (split the batch, or use
+ *     rr_evaluate with your own workspace).
+ *   - All calls in the process share the one array per device: calls whose
+ *     work overlaps on the GPU (different streams, or different contexts on
+ *     the same device, without ordering between them) race on it and give
+ *     wrong results.  Order them, or use rr_evaluate.
+ *   - The array keeps the last call's contents; every call rewrites what it
+ *     reads before reading it, so nothing needs clearing.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress, with that device made current); make that first
+ *     call before any stream capture on that device.
+ * Errors: as rr_evaluate, plus RR_EINVAL for oversize batches. */
+#define RR_NOALLOC_SCRATCH_BYTES (32u << 20)
+rr_status rr_evaluate_noalloc(rr_ctx* ctx, const double* times, const int32_t* pb_index, int32_t npt,
+                              const double* params, int32_t npv, const int32_t* supersampling,
+                              const double* exptime, void* flux, int32_t* pv_status, void* stream);
+
 /* Vector-Jacobian product of rr_evaluate (hand-written adjoint):
  *   grad_params[pv][j] = sum_t grad_flux[pv][t] * d flux[pv][t] / d params[pv][j]
  * Same inputs as rr_evaluate, plus

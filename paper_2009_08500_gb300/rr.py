@@ -29,7 +29,8 @@ PV_NONFINITE, PV_LD_INVALID, PV_A_RANGE, PV_KEPLER = 16, 32, 64, 128
 #: every exported entry point of include/rr.h
 EXPORTS = ["rr_create", "rr_destroy", "rr_set_ld_profile", "rr_build_weights", "rr_nparam",
            "rr_workspace_bytes", "rr_evaluate", "rr_evaluate_grad", "rr_read_table",
-           "rr_sync_status", "rr_last_error", "rr_launch_count", "rr_profile", "rr_profile_read"]
+           "rr_sync_status", "rr_last_error", "rr_launch_count", "rr_profile", "rr_profile_read",
+           "rr_evaluate_noalloc"]
 KERNELS = {"ld_basis": 0, "weights": 1, "pv_setup": 2, "flux": 3, "grad": 4, "grad_reduce": 5, "points": 6}
 
 
@@ -68,6 +69,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     L.rr_workspace_bytes.restype = sz
     L.rr_evaluate.argtypes = [vp, vp, vp, i32, vp, i32, ctypes.POINTER(i32), dp, vp, vp, vp, sz, vp]
     L.rr_evaluate_grad.argtypes = [vp, vp, vp, i32, vp, i32, ctypes.POINTER(i32), dp, vp, vp, vp, vp, sz, vp]
+    L.rr_evaluate_noalloc.argtypes = [vp, vp, vp, i32, vp, i32, ctypes.POINTER(i32), dp, vp, vp, vp]
     L.rr_read_table.argtypes = [vp, i32, dp, i64]
     L.rr_read_table.restype = i64
     L.rr_sync_status.argtypes = [vp, vp]
@@ -78,7 +80,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     L.rr_profile.argtypes = [vp, i32]
     L.rr_profile_read.argtypes = [vp, i32, dp, ctypes.POINTER(i64), i32]
     for name in ("rr_create", "rr_destroy", "rr_set_ld_profile", "rr_build_weights", "rr_evaluate",
-                 "rr_evaluate_grad", "rr_sync_status", "rr_profile", "rr_profile_read"):
+                 "rr_evaluate_grad", "rr_sync_status", "rr_profile", "rr_profile_read", "rr_evaluate_noalloc"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -229,6 +231,22 @@ class Model:
                                   ss.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
                                   ex.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), _ptr(out),
                                   _ptr(pv_status), _ptr(workspace), workspace.numel(), _stream_handle(stream))
+        self._check(st)
+        return out
+
+    def evaluate_noalloc(self, times: torch.Tensor, params: torch.Tensor, pb_index: Optional[torch.Tensor] = None,
+                         supersampling=None, exptime=None, out: Optional[torch.Tensor] = None,
+                         pv_status: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+        """As :meth:`evaluate`, with the library's fixed scratch instead of a workspace (see rr.h)."""
+        npt, npv = self._inputs(times, params, pb_index)
+        ss = _host_array(supersampling, self.npb, np.int32, 1)
+        ex = _host_array(exptime, self.npb, np.float64, 0.0)
+        if out is None:
+            out = torch.empty((npv, npt), dtype=self.dtype, device=self.device)
+        st = self.lib.rr_evaluate_noalloc(self._h, _ptr(times), _ptr(pb_index), npt, _ptr(params), npv,
+                                          ss.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                          ex.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), _ptr(out),
+                                          _ptr(pv_status), _stream_handle(stream))
         self._check(st)
         return out
 

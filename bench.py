@@ -33,6 +33,8 @@ CONFIG_TEXT = {
     "c2": "Single eccentric light curve, FP32 bulk / FP64 phase: nonlinear LD, 19,440 times, ss=10",
     "c3": "Population batch: 4,096 pvs x 20,000 times, Kipping q1,q2, forward + adjoint w.r.t. 9 parameters",
     "c4": "Heterogeneous: 8 passbands, tabulated LD, 2,048 pvs x 60,000 mixed-cadence times, ss {1,10,30}",
+    "c5": "Serving: Poisson requests from 64 fits, npv logU[1,4096] x npt logU[500,2e5] (capped at 2^25 points), "
+          "mixed LD, forward:gradient 3:1",
 }
 # DRAM bytes (read + write) per launch of the flux kernel, from one ncu capture of the
 # same kernel (profiles/flux_mixed_c3_population.md); None until captured for this version
@@ -45,7 +47,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["c1", "c2", "c3", "c4"], default="c3")
+    ap.add_argument("--workload", choices=["c1", "c2", "c3", "c4", "c5"], default="c3")
+    ap.add_argument("--serve-seconds", type=float, default=3.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
@@ -392,10 +395,102 @@ def run_reference(a):
     print(json.dumps(line))
 
 
+# ----------------------------------------------------------------- serving (C5)
+def run_serving(a):
+    """Closed-loop capacity, then Poisson streams at 0.7x and 1.1x of it."""
+    import threading
+
+    import numpy as np
+    import torch
+
+    from paper_2009_08500_gb300 import rr
+    from paper_2009_08500_gb300 import workloads as W
+    from paper_2009_08500_gb300.serve import CudaBackend, Server, ServeRequest
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    fits = W.make_c5_fits()
+    models = {}
+    for i, f in enumerate(fits):
+        wl = W.make_small(f["ld_model"], npv=1, npt=4, seed=f["seed"])
+        if f["ld_model"] == "tabulated":
+            wl.profiles = [W.tabulated_profile(np.random.Generator(np.random.PCG64(f["seed"])))]
+        models[i] = rr.model_for(wl, device=local)
+    rng = np.random.Generator(np.random.PCG64(1234))
+    cap = 1 << 25
+    gbuf = rng.normal(size=cap).astype(np.float32)
+    pool = []
+    for j in range(96):
+        fi = int(rng.integers(0, len(fits)))
+        while True:
+            npv = int(np.exp(rng.uniform(0.0, np.log(4096))))
+            npt = int(np.exp(rng.uniform(np.log(500), np.log(200_000))))
+            if npv * npt <= cap:
+                break
+        wl = W.make_small(fits[fi]["ld_model"], npv=max(npv, 1), npt=npt, seed=int(rng.integers(0, 2 ** 31)),
+                          eccentric=fits[fi]["eccentric"], span=max(2.0, npt / 720.0))
+        grad = bool(rng.uniform() < 0.25)
+        pool.append(dict(fit=fi, times=wl.times, params=wl.params, pb_index=wl.pb_index,
+                         supersampling=wl.supersampling, exptime=wl.exptime,
+                         grad_flux=gbuf[:wl.npv * wl.npt].reshape(wl.npv, wl.npt) if grad else None))
+    slots = 8
+    backend = CudaBackend(models, slots=slots, device=local)
+
+    def mk(k):
+        return ServeRequest(**pool[k % len(pool)])
+
+    # warm-up (pinned-memory caches, kernels)
+    with Server(backend, slots=slots, mem_budget=64 << 30) as srv:
+        for k in range(len(pool)):
+            srv.submit(mk(k))
+        srv.drain()
+    # capacity: keep 2 x slots requests outstanding for serve_seconds
+    with Server(backend, slots=slots, mem_budget=64 << 30) as srv:
+        t_end = time.perf_counter() + a.serve_seconds
+        k = 0
+        outstanding = []
+        while time.perf_counter() < t_end:
+            outstanding = [f for f in outstanding if not f.done()]
+            while len(outstanding) < 2 * slots:
+                outstanding.append(srv.submit(mk(k)))
+                k += 1
+            time.sleep(2e-4)
+        srv.drain()
+        closed = srv.stats()
+    mean_pts = float(np.mean([ServeRequest(**p).points for p in pool]))
+    runs = {}
+    for load in (0.7, 1.1):
+        rate = load * closed["points_per_s"] / mean_pts
+        arr = np.cumsum(rng.exponential(1.0 / rate, size=int(rate * a.serve_seconds) + 1))
+        with Server(backend, slots=slots, mem_budget=64 << 30) as srv:
+            t0 = time.perf_counter()
+            for i, ta in enumerate(arr):
+                dt = ta - (time.perf_counter() - t0)
+                if dt > 0:
+                    time.sleep(dt)
+                srv.submit(mk(int(rng.integers(0, len(pool)))))
+            srv.drain()
+            runs[load] = srv.stats()
+            runs[load]["rate_req_per_s"] = rate
+    line = {"metric": METRIC, "value": runs[0.7]["points_per_s"], "unit": "points/s", "n_gpus": world,
+            "steps": None, "warmup": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64", "data": "synthetic (seeded; paper-shaped)",
+            "config": {"workload": f"c5: {CONFIG_TEXT['c5']}", "fits": len(fits), "slots": slots,
+                       "request_pool": len(pool), "mean_points_per_request": mean_pts,
+                       "serve_seconds": a.serve_seconds},
+            "capacity_closed_loop": closed,
+            "latency_ms": {"p50": runs[0.7]["latency_p50_ms"], "p99": runs[0.7]["latency_p99_ms"]},
+            "open_loop": {str(k): v for k, v in runs.items()}}
+    if rank == 0:
+        print(json.dumps(line))
+
+
 def main():
     a = parse()
     if a.impl == "reference":
         run_reference(a)
+    elif a.workload == "c5":
+        run_serving(a)
     else:
         run_ours(a)
 

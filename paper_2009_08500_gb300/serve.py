@@ -1,0 +1,299 @@
+"""Continuous-batching evaluation server for many concurrent fits.
+
+Requests (a parameter batch for one fit's light curve, optionally with a
+cotangent for the gradient) arrive from many fitting loops at once.  The
+server keeps every fit's model context -- its LD profiles and (k, g) tables
+-- resident on the device, and:
+
+* admits queued requests in arrival order whenever a stream slot and enough
+  device memory (inputs + outputs + workspace, counted exactly) are free;
+* runs every admitted request on its own CUDA stream, so the work of
+  requests admitted at different times overlaps on the device;
+* completes a request's future as soon as its stream has finished (event
+  polling), releasing its memory and slot for the next admission;
+* records arrival / admission / launch / finish times, points and bytes of
+  every request (p50 / p99 latency and points/s come from these).
+
+Results do not depend on what else is in flight: each request runs the same
+kernels with the same tiling as it would alone (the adjoint's summation
+order depends on the request's own number of times only).
+
+The scheduling logic is backend-agnostic (``Backend``); ``CudaBackend`` runs
+requests through the library, tests may plug in a host-only backend.
+"""
+from __future__ import annotations
+
+import collections
+import threading
+import time
+from concurrent.futures import Future
+from dataclasses import dataclass, field
+from typing import Any, Callable, Deque, Dict, List, Optional
+
+import numpy as np
+
+
+class AdmissionError(RuntimeError):
+    """The request can never be admitted (larger than the memory budget)."""
+
+
+@dataclass
+class ServeRequest:
+    fit: Any
+    times: np.ndarray
+    params: np.ndarray
+    pb_index: Optional[np.ndarray] = None
+    supersampling: Optional[np.ndarray] = None
+    exptime: Optional[np.ndarray] = None
+    grad_flux: Optional[np.ndarray] = None      # cotangent: the request also wants d/d(params)
+    deadline_s: Optional[float] = None          # seconds after arrival; expired requests are not admitted
+    # filled by the server
+    id: int = -1
+    nbytes: int = 0
+    t_arrival: float = 0.0
+    t_admit: float = 0.0
+    t_launch: float = 0.0
+    t_finish: float = 0.0
+    future: Future = field(default_factory=Future)
+
+    @property
+    def npv(self) -> int:
+        return int(self.params.shape[0])
+
+    @property
+    def npt(self) -> int:
+        return int(self.times.shape[0])
+
+    @property
+    def points(self) -> int:
+        if self.supersampling is None:
+            return self.npv * self.npt
+        ss = np.asarray(self.supersampling)
+        pb = np.zeros(self.npt, int) if self.pb_index is None else np.asarray(self.pb_index)
+        return int(self.npv * ss[pb].sum())
+
+
+class Backend:
+    """What the scheduler needs from an executor."""
+
+    def nbytes(self, req: ServeRequest) -> int:
+        raise NotImplementedError
+
+    def launch(self, req: ServeRequest, slot: int) -> Any:
+        """Enqueue the request on stream `slot`; return a handle for `done` / `finish`."""
+        raise NotImplementedError
+
+    def done(self, handle: Any) -> bool:
+        raise NotImplementedError
+
+    def finish(self, handle: Any) -> Any:
+        """Result of a completed request (releases its resources)."""
+        raise NotImplementedError
+
+
+class Server:
+    """Continuous-batching scheduler.
+
+    slots       requests that may be in flight at once (one stream each)
+    mem_budget  device bytes that in-flight requests may hold together
+    """
+
+    def __init__(self, backend: Backend, slots: int = 8, mem_budget: int = 8 << 30, poll_s: float = 50e-6):
+        self.backend = backend
+        self.slots = slots
+        self.mem_budget = mem_budget
+        self.poll_s = poll_s
+        self._queue: Deque[ServeRequest] = collections.deque()
+        self._inflight: Dict[int, tuple] = {}        # slot -> (request, handle)
+        self._free_slots = list(range(slots))[::-1]
+        self._mem_used = 0
+        self._lock = threading.Condition()
+        self._next_id = 0
+        self._stop = False
+        self.completed: List[ServeRequest] = []
+        self.max_inflight_seen = 0
+        self._thread = threading.Thread(target=self._run, name="rr-serve", daemon=True)
+        self._thread.start()
+
+    # -- client side ------------------------------------------------------------
+    def submit(self, req: ServeRequest) -> Future:
+        req.nbytes = self.backend.nbytes(req)
+        if req.nbytes > self.mem_budget:
+            raise AdmissionError(f"request needs {req.nbytes} bytes, more than the {self.mem_budget}-byte budget")
+        with self._lock:
+            if self._stop:
+                raise RuntimeError("server is stopped")
+            req.id = self._next_id
+            self._next_id += 1
+            req.t_arrival = time.perf_counter()
+            self._queue.append(req)
+            self._lock.notify()
+        return req.future
+
+    def close(self, wait: bool = True):
+        with self._lock:
+            self._stop = True
+            self._lock.notify()
+        if wait:
+            self._thread.join()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def drain(self, timeout_s: float = 600.0):
+        """Wait until nothing is queued or in flight."""
+        t0 = time.perf_counter()
+        while True:
+            with self._lock:
+                if not self._queue and not self._inflight:
+                    return
+            if time.perf_counter() - t0 > timeout_s:
+                raise TimeoutError("server did not drain")
+            time.sleep(1e-3)
+
+    # -- scheduler --------------------------------------------------------------
+    def _admit(self):
+        """Admit queued requests in order while a slot and memory are free (lock held)."""
+        now = time.perf_counter()
+        while self._queue and self._free_slots:
+            req = self._queue[0]
+            if req.future.cancelled():
+                self._queue.popleft()
+                continue
+            if req.deadline_s is not None and now - req.t_arrival > req.deadline_s:
+                self._queue.popleft()
+                req.future.set_exception(TimeoutError(f"request {req.id} expired before admission"))
+                continue
+            if self._mem_used + req.nbytes > self.mem_budget:
+                break                                   # in order: wait for memory to free up
+            self._queue.popleft()
+            if not req.future.set_running_or_notify_cancel():
+                continue
+            slot = self._free_slots.pop()
+            self._mem_used += req.nbytes
+            req.t_admit = time.perf_counter()
+            try:
+                handle = self.backend.launch(req, slot)
+            except Exception as exc:                  # launch failed: report it, release resources
+                self._mem_used -= req.nbytes
+                self._free_slots.append(slot)
+                req.future.set_exception(exc)
+                continue
+            req.t_launch = time.perf_counter()
+            self._inflight[slot] = (req, handle)
+            self.max_inflight_seen = max(self.max_inflight_seen, len(self._inflight))
+
+    def _reap(self):
+        """Complete finished requests (lock held)."""
+        for slot in list(self._inflight):
+            req, handle = self._inflight[slot]
+            try:
+                if not self.backend.done(handle):
+                    continue
+                result = self.backend.finish(handle)
+                req.t_finish = time.perf_counter()
+                req.future.set_result(result)
+            except Exception as exc:
+                req.t_finish = time.perf_counter()
+                req.future.set_exception(exc)
+            del self._inflight[slot]
+            self._free_slots.append(slot)
+            self._mem_used -= req.nbytes
+            self.completed.append(req)
+
+    def _run(self):
+        while True:
+            with self._lock:
+                self._reap()
+                self._admit()
+                if self._stop and not self._queue and not self._inflight:
+                    return
+                if not self._inflight and not self._queue:
+                    self._lock.wait(timeout=0.05)
+                    continue
+            time.sleep(self.poll_s)
+
+    # -- metrics ----------------------------------------------------------------
+    def stats(self) -> dict:
+        done = [r for r in self.completed if r.future.done() and not r.future.exception()]
+        if not done:
+            return {"requests": 0}
+        lat = np.array([r.t_finish - r.t_arrival for r in done])
+        t0 = min(r.t_arrival for r in done)
+        t1 = max(r.t_finish for r in done)
+        pts = sum(r.points for r in done)
+        return {"requests": len(done), "points": pts, "points_per_s": pts / (t1 - t0),
+                "latency_p50_ms": float(np.percentile(lat, 50) * 1e3),
+                "latency_p99_ms": float(np.percentile(lat, 99) * 1e3),
+                "queue_wait_p50_ms": float(np.percentile([r.t_admit - r.t_arrival for r in done], 50) * 1e3),
+                "max_inflight": self.max_inflight_seen, "wall_s": t1 - t0}
+
+
+class CudaBackend(Backend):
+    """Runs requests through librr: one CUDA stream per slot, device-resident fit contexts.
+
+    fits: {fit id: rr.Model} (built); requests carry host arrays (pinned on launch).
+    """
+
+    def __init__(self, fits: Dict[Any, Any], slots: int, device: int = 0):
+        import torch
+        self.torch = torch
+        self.fits = fits
+        self.device = torch.device("cuda", device)
+        self.streams = [torch.cuda.Stream(device=self.device) for _ in range(slots)]
+
+    def nbytes(self, req: ServeRequest) -> int:
+        m = self.fits[req.fit]
+        esize = 8 if m.precision == "fp64" else 4
+        b = req.npt * (8 + 4) + req.params.size * 8 + req.npv * 4
+        b += req.npv * req.npt * esize                              # flux
+        b += m.workspace_bytes(req.npv, req.npt, False)
+        if req.grad_flux is not None:
+            b += req.npv * req.npt * esize + req.params.size * 8 + m.workspace_bytes(req.npv, req.npt, True)
+        return int(b)
+
+    def launch(self, req: ServeRequest, slot: int):
+        torch = self.torch
+        m = self.fits[req.fit]
+        s = self.streams[slot]
+        with torch.cuda.stream(s):
+            t = torch.from_numpy(np.ascontiguousarray(req.times, np.float64)).pin_memory().to(self.device, non_blocking=True)
+            p = torch.from_numpy(np.ascontiguousarray(req.params, np.float64)).pin_memory().to(self.device, non_blocking=True)
+            pb = None
+            if req.pb_index is not None:
+                pb = torch.from_numpy(np.ascontiguousarray(req.pb_index, np.int32)).pin_memory().to(self.device, non_blocking=True)
+            status = torch.empty(req.npv, dtype=torch.int32, device=self.device)
+            flux = m.evaluate(t, p, pb, req.supersampling, req.exptime, pv_status=status, stream=s)
+            h_flux = torch.empty(flux.shape, dtype=flux.dtype, pin_memory=True)
+            h_flux.copy_(flux, non_blocking=True)
+            h_grad = None
+            if req.grad_flux is not None:
+                g = torch.from_numpy(np.ascontiguousarray(req.grad_flux, np.float32 if m.precision == "mixed"
+                                                          else np.float64)).pin_memory().to(self.device, non_blocking=True)
+                grad = m.evaluate_grad(t, p, g, pb, req.supersampling, req.exptime, stream=s)
+                h_grad = torch.empty(grad.shape, dtype=grad.dtype, pin_memory=True)
+                h_grad.copy_(grad, non_blocking=True)
+            h_status = torch.empty(req.npv, dtype=torch.int32, pin_memory=True)
+            h_status.copy_(status, non_blocking=True)
+            ev = torch.cuda.Event()
+            ev.record(s)
+        # device tensors stay referenced by the handle until the event has completed
+        return (ev, h_flux, h_grad, h_status, (t, p, pb, status, flux))
+
+    def done(self, handle) -> bool:
+        return handle[0].query()
+
+    def finish(self, handle):
+        ev, h_flux, h_grad, h_status, _ = handle
+        out = {"flux": h_flux.numpy(), "pv_status": h_status.numpy()}
+        if h_grad is not None:
+            out["grad"] = h_grad.numpy()
+        return out
+
+
+def latency_summary(reqs: List[ServeRequest]) -> dict:
+    lat = np.array([r.t_finish - r.t_arrival for r in reqs])
+    return {"p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3)}

@@ -1,0 +1,93 @@
+"""Serving on the GPU: each result is the same alone and in the mix."""
+import threading
+
+import numpy as np
+import pytest
+
+from paper_2009_08500_gb300 import workloads as W
+from paper_2009_08500_gb300.serve import CudaBackend, Server, ServeRequest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fits():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2009_08500_gb300 import rr
+    out = {}
+    for name, ld in [("a", "quadratic"), ("b", "nonlinear"), ("c", "tabulated"), ("d", "quadratic_tri")]:
+        wl = W.make_small(ld, npv=1, npt=8, seed=ord(name))
+        out[name] = (rr.model_for(wl), wl)
+    return out
+
+
+def _requests(fits, n, seed):
+    rng = np.random.default_rng(seed)
+    reqs = []
+    names = sorted(fits)
+    for i in range(n):
+        name = names[int(rng.integers(0, len(names)))]
+        tmpl = fits[name][1]
+        wl = W.make_small(tmpl.ld_model, npv=int(rng.integers(1, 48)), npt=int(rng.integers(500, 6000)),
+                          seed=int(rng.integers(0, 2 ** 31)), ss=(int(rng.choice([1, 3, 7])),), exptime=(0.01,))
+        gbar = rng.normal(size=(wl.npv, wl.npt)).astype(np.float32) if i % 3 == 0 else None
+        reqs.append(ServeRequest(fit=name, times=wl.times, params=wl.params, pb_index=wl.pb_index,
+                                 supersampling=wl.supersampling, exptime=wl.exptime, grad_flux=gbar))
+    return reqs
+
+
+def _alone(fits, req):
+    import torch
+    m = fits[req.fit][0]
+    dev = m.device
+    t = torch.as_tensor(req.times, dtype=torch.float64, device=dev)
+    p = torch.as_tensor(req.params, dtype=torch.float64, device=dev)
+    pb = torch.as_tensor(req.pb_index, dtype=torch.int32, device=dev)
+    f = m.evaluate(t, p, pb, req.supersampling, req.exptime).cpu().numpy()
+    g = None
+    if req.grad_flux is not None:
+        g = m.evaluate_grad(t, p, torch.as_tensor(req.grad_flux, device=dev), pb, req.supersampling,
+                            req.exptime).cpu().numpy()
+    return f, g
+
+
+@pytest.mark.parametrize("budget", [8 << 30, 40 << 20])
+def test_results_identical_alone_and_in_the_mix(fits, budget):
+    reqs = _requests(fits, 36, seed=budget % 97)
+    backend = CudaBackend({k: v[0] for k, v in fits.items()}, slots=6)
+    futs = {}
+    with Server(backend, slots=6, mem_budget=budget) as srv:
+        def client(part):
+            for r in part:
+                futs[id(r)] = srv.submit(r)
+        ths = [threading.Thread(target=client, args=(reqs[c::3],)) for c in range(3)]
+        for t in ths:
+            t.start()
+        for t in ths:
+            t.join()
+        res = {k: f.result(timeout=120) for k, f in futs.items()}
+        stats = srv.stats()
+    for r in reqs:
+        out = res[id(r)]
+        f, g = _alone(fits, r)
+        assert np.array_equal(out["flux"], f)
+        assert not out["pv_status"].any()
+        if g is not None:
+            assert np.array_equal(out["grad"], g)
+    assert stats["requests"] == len(reqs)
+    if budget > (1 << 30):
+        assert stats["max_inflight"] > 1      # requests overlapped on the device
+
+
+def test_served_flux_matches_oracle(fits):
+    from oracle import model as om
+    reqs = _requests(fits, 4, seed=5)
+    backend = CudaBackend({k: v[0] for k, v in fits.items()}, slots=2)
+    with Server(backend, slots=2) as srv:
+        outs = [srv.submit(r).result(timeout=120) for r in reqs]
+    for r, o in zip(reqs, outs):
+        tmpl = fits[r.fit][1]
+        s = om.build(tmpl.grid, tmpl.ld_model, 1, False, tmpl.profiles)
+        ref = om.evaluate(s, r.times, r.pb_index, r.params, r.supersampling, r.exptime)
+        assert np.abs(o["flux"] - ref).max() <= 1e-6

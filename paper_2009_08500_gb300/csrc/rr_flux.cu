@@ -311,9 +311,11 @@ cudaError_t launch_flux(rr_ctx* c, const double* times, const int32_t* pb_index,
     const bool f64 = c->cfg.precision == RR_PREC_FP64;
     RecLayout L = f64 ? make_layout<double>(c->cfg.npb, c->cfg.ng, c->nldc, false)
                       : make_layout<float>(c->cfg.npb, c->cfg.ng, c->nldc, false);
-    // FP32 kernel: headers and rows of the tile in shared memory (rows are read
-    // by every transit sub-exposure); FP64 kernel: headers only
-    const int per_pv = f64 ? L.head_bytes : L.head_bytes + L.rows_bytes;
+    // FP32 kernel with several passbands: headers and rows of the tile in
+    // shared memory (the rows of many passbands do not stay in L1); one
+    // passband, and the FP64 kernel: headers only, rows through L1/L2
+    const bool stage_rows = !f64 && c->cfg.npb > 1;
+    const int per_pv = stage_rows ? L.head_bytes + L.rows_bytes : L.head_bytes;
     const int pv_tile = pv_tile_for(per_pv);
     const size_t smem = flux_smem(pv_tile, per_pv, f64);
     const char* rowsg = (const char*)records + rows_offset(L, npv);
@@ -330,13 +332,13 @@ cudaError_t launch_flux(rr_ctx* c, const double* times, const int32_t* pb_index,
                                                        (const char*)records, rowsg, (double*)flux, pv_status,
                                                        c->d_err);
     } else {
-        e = cudaFuncSetAttribute(rr_flux_mixed_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        auto kern = stage_rows ? rr_flux_mixed_kernel<true> : rr_flux_mixed_kernel<false>;
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         const int vec = (npt % 4 == 0) && (((uintptr_t)flux & 15u) == 0);
-        rr_flux_mixed_kernel<true><<<grid, kBlock, smem, s>>>(times, (const float2*)pts_dt, (const int32_t*)pts_pb, npt,
-                                                        npv, pbp, L, pv_tile, gpc, (const char*)records, rowsg,
-                                                        (float*)flux,
-                                                        pv_status, vec, c->d_err);
+        kern<<<grid, kBlock, smem, s>>>(times, (const float2*)pts_dt, (const int32_t*)pts_pb, npt, npv, pbp, L,
+                                        pv_tile, gpc, (const char*)records, rowsg, (float*)flux, pv_status, vec,
+                                        c->d_err);
     }
     c->launches++;
     return cudaGetLastError();

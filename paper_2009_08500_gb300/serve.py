@@ -79,6 +79,9 @@ class Backend:
     def nbytes(self, req: ServeRequest) -> int:
         raise NotImplementedError
 
+    def prepare(self, req: ServeRequest) -> None:
+        """Host-side preparation, run on the submitting thread (optional)."""
+
     def launch(self, req: ServeRequest, slot: int) -> Any:
         """Enqueue the request on stream `slot`; return a handle for `done` / `finish`."""
         raise NotImplementedError
@@ -120,6 +123,7 @@ class Server:
         req.nbytes = self.backend.nbytes(req)
         if req.nbytes > self.mem_budget:
             raise AdmissionError(f"request needs {req.nbytes} bytes, more than the {self.mem_budget}-byte budget")
+        self.backend.prepare(req)
         with self._lock:
             if self._stop:
                 raise RuntimeError("server is stopped")
@@ -255,42 +259,52 @@ class CudaBackend(Backend):
             b += req.npv * req.npt * esize + req.params.size * 8 + m.workspace_bytes(req.npv, req.npt, True)
         return int(b)
 
+    def prepare(self, req: ServeRequest) -> None:
+        """Pinned host copies of the inputs and pinned result buffers (submitting thread)."""
+        torch = self.torch
+        m = self.fits[req.fit]
+        pin = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a, dt)).pin_memory()  # noqa: E731
+        h = {"t": pin(req.times, np.float64), "p": pin(req.params, np.float64),
+             "pb": None if req.pb_index is None else pin(req.pb_index, np.int32),
+             "flux": torch.empty((req.npv, req.npt), dtype=m.dtype, pin_memory=True),
+             "status": torch.empty(req.npv, dtype=torch.int32, pin_memory=True), "g": None, "grad": None}
+        if req.grad_flux is not None:
+            h["g"] = pin(req.grad_flux, np.float32 if m.precision == "mixed" else np.float64)
+            h["grad"] = torch.empty((req.npv, m.nparam), dtype=torch.float64, pin_memory=True)
+        req._host = h
+
     def launch(self, req: ServeRequest, slot: int):
         torch = self.torch
         m = self.fits[req.fit]
         s = self.streams[slot]
+        h = req._host
         with torch.cuda.stream(s):
-            t = torch.from_numpy(np.ascontiguousarray(req.times, np.float64)).pin_memory().to(self.device, non_blocking=True)
-            p = torch.from_numpy(np.ascontiguousarray(req.params, np.float64)).pin_memory().to(self.device, non_blocking=True)
-            pb = None
-            if req.pb_index is not None:
-                pb = torch.from_numpy(np.ascontiguousarray(req.pb_index, np.int32)).pin_memory().to(self.device, non_blocking=True)
+            t = h["t"].to(self.device, non_blocking=True)
+            p = h["p"].to(self.device, non_blocking=True)
+            pb = None if h["pb"] is None else h["pb"].to(self.device, non_blocking=True)
             status = torch.empty(req.npv, dtype=torch.int32, device=self.device)
             flux = m.evaluate(t, p, pb, req.supersampling, req.exptime, pv_status=status, stream=s)
-            h_flux = torch.empty(flux.shape, dtype=flux.dtype, pin_memory=True)
-            h_flux.copy_(flux, non_blocking=True)
-            h_grad = None
-            if req.grad_flux is not None:
-                g = torch.from_numpy(np.ascontiguousarray(req.grad_flux, np.float32 if m.precision == "mixed"
-                                                          else np.float64)).pin_memory().to(self.device, non_blocking=True)
+            h["flux"].copy_(flux, non_blocking=True)
+            keep = [t, p, pb, status, flux]
+            if h["g"] is not None:
+                g = h["g"].to(self.device, non_blocking=True)
                 grad = m.evaluate_grad(t, p, g, pb, req.supersampling, req.exptime, stream=s)
-                h_grad = torch.empty(grad.shape, dtype=grad.dtype, pin_memory=True)
-                h_grad.copy_(grad, non_blocking=True)
-            h_status = torch.empty(req.npv, dtype=torch.int32, pin_memory=True)
-            h_status.copy_(status, non_blocking=True)
+                h["grad"].copy_(grad, non_blocking=True)
+                keep += [g, grad]
+            h["status"].copy_(status, non_blocking=True)
             ev = torch.cuda.Event()
             ev.record(s)
         # device tensors stay referenced by the handle until the event has completed
-        return (ev, h_flux, h_grad, h_status, (t, p, pb, status, flux))
+        return (ev, h, keep)
 
     def done(self, handle) -> bool:
         return handle[0].query()
 
     def finish(self, handle):
-        ev, h_flux, h_grad, h_status, _ = handle
-        out = {"flux": h_flux.numpy(), "pv_status": h_status.numpy()}
-        if h_grad is not None:
-            out["grad"] = h_grad.numpy()
+        _, h, _ = handle
+        out = {"flux": h["flux"].numpy(), "pv_status": h["status"].numpy()}
+        if h["grad"] is not None:
+            out["grad"] = h["grad"].numpy()
         return out
 
 

@@ -364,12 +364,42 @@ __global__ void __launch_bounds__(256) rr_pv_setup_kernel(ModelParams mp, PbPara
             int flags = 0;
             if (ed == 0.0) flags |= kPvCircular;
             if (ed > kESwitch) flags |= kPvKepler64;
-            R wmax = R(0);
+            R wmax = R(-1);
             const R ra = a * (R(1) - e);
+            // conjunction anomaly wrapped to (-pi, pi] (periastron at 0)
+            R fc = f0 - R(2) * pi * floor((f0 + pi) / (R(2) * pi));
             for (int pb = 0; pb < mp.npb; ++pb) {
                 const R k = (R)row[6 + (mp.chromatic ? pb : 0)];
-                const R q = (R(1) + k) / ra;
-                const R df = q >= R(1) ? R(0.5) * pi : r_asin(q);
+                // Transit window in true anomaly, |f - f0| <= d.  A transit needs
+                // X^2 + Y^2 < (1 + k)^2 with |X| = r |sin(f - f0)|, |Y| = r cos(f - f0) b / a
+                // (planet in front: |f - f0| < pi/2).  Start from r >= a (1 - e); then, with
+                // r_min and the smallest |Y| over the current window, |sin(f - f0)| <=
+                // sqrt((1 + k)^2 - Y_min^2) / r_min gives a window that still holds every
+                // transit point.  Safety factors absorb the rounding of R.
+                const R lim = R(1) + k;
+                const R q = lim / ra;
+                R d = q >= R(1) ? R(0.5) * pi : r_asin(q);
+                bool none = false;
+                for (int it = 0; it < 5 && !none; ++it) {
+                    const R mc = fabs(fc) <= d ? R(1) : r_max(cos(fc - d), cos(fc + d));
+                    const R rmin = a * (R(1) - e * e) / (R(1) + e * mc);
+                    const R ymin = rmin * cos(d) * (b / a) * R(1 - 4e-6);
+                    const R x2 = lim * lim * R(1 + 4e-6) - ymin * ymin;
+                    if (!(x2 > R(0))) { none = true; break; }
+                    const R sx = d_sqrt(x2) / rmin;
+                    const R dn = sx >= R(1) ? R(0.5) * pi : r_asin(sx);
+                    d = dn < d ? dn : d;
+                }
+                if (none) {            // the orbit never brings the planet over the disk
+                    PB[pb].k = k;
+                    PB[pb].inv1pk = R(1) / (R(1) + k);
+                    PB[pb].win_s = R(-1);
+                    PB[pb].win_p = R(-1);
+                    PB[pb].win_pc = -1.0f;
+                    PB[pb].pad[0] = PB[pb].pad[1] = PB[pb].pad[2] = 0.0f;
+                    continue;
+                }
+                const R df = d;
                 const R hi = wrap_2pi_r(mean_anomaly_of_true_r(f0 + df, e) - M0);
                 const R lo = wrap_2pi_r(M0 - mean_anomaly_of_true_r(f0 - df, e));
                 R win = r_max(hi, lo);

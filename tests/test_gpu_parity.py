@@ -230,3 +230,21 @@ def test_high_eccentricity_uses_fp64_kepler(rr):
     ref, rst = oracle_flux(wl)
     np.testing.assert_array_equal(st, rst)
     assert np.abs(f - ref).max() <= 1e-6
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_grazing_and_missing_transits(rr, precision):
+    """Impact parameters around 1 + k: the transit window must still contain every
+    touching point, and orbits that never cross the disk give exactly 1."""
+    wl = W.make_small("nonlinear", npv=48, npt=4000, seed=77, span=6.0)
+    k = wl.params[:, 6]
+    off = np.linspace(-0.02, 0.02, wl.npv)
+    wl.params[:, 3] = np.clip((1 + k) * (1 + off), 0, None)    # b = (1 + k)(1 + off)
+    f, st = gpu_flux(rr, wl, precision)
+    ref, rst = oracle_flux(wl)
+    np.testing.assert_array_equal(st, rst)
+    assert np.abs(f - ref).max() <= TOL[precision]
+    # pvs whose closest approach stays outside the disk: flux exactly 1 everywhere
+    never = np.all(ref == 1.0, axis=1)
+    assert never.any() and (~never).any()
+    assert np.all(f[never] == 1.0)

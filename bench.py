@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--serve-seconds", type=float, default=3.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fp64-form", action="store_true")
     return ap.parse_args()
 
 
@@ -276,22 +277,31 @@ def run_ours(a):
     pts = wl.npv * wl.samples_per_pv()
     value = world * pts / (ms_per_step * 1e-3)
 
-    # dominant kernel and its roofline (HBM): algorithmic bytes per launch
+    # roofline (HBM) of the dominant kernel and of the flux kernel: algorithmic bytes per launch
+    esize = 8 if model.dtype == torch.float64 else 4
+    peak, peak_kind = measured_peak_hbm()
+
+    def roofline(kind):
+        kms, kn = kprof[kind]
+        kavg = kms / max(kn, 1)
+        alg = algorithmic_bytes(model, wl, kind, esize)
+        achieved = alg / (kavg * 1e-3) / 1e9
+        return {"kernel": f"rr_{kind}_{'fp64' if esize == 8 else 'mixed'}_kernel", "bound": "hbm",
+                "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                "peak_source": f"{peak_kind} hbm_gbs (copy bandwidth)", "algorithmic_bytes_per_launch": int(alg),
+                "avg_launch_ms": round(kavg, 5), "traffic": TRAFFIC.get((a.workload, kind))}
+
     names = ["flux", "grad"] if grad else ["flux"]
     dom = max(names, key=lambda k: kprof[k][0])
-    kms, kn = kprof[dom]
-    kavg = kms / max(kn, 1)
-    rec = model.workspace_bytes(wl.npv, wl.npt, dom == "grad")
-    esize = 8 if model.dtype == torch.float64 else 4
-    per_time = 8 + 4                                  # time (FP64) + passband index
-    alg = wl.npv * wl.npt * esize + wl.npt * per_time + rec   # flux written / cotangent read, times, records
-    peak, peak_kind = measured_peak_hbm()
-    achieved = alg / (kavg * 1e-3) / 1e9
-    roof = {"kernel": f"rr_{dom}_{'fp64' if esize == 8 else 'mixed'}_kernel", "bound": "hbm",
-            "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
-            "peak_source": f"{peak_kind} hbm_gbs", "algorithmic_bytes_per_launch": int(alg),
-            "avg_launch_ms": round(kavg, 5), "traffic": TRAFFIC.get((a.workload, dom))}
+    roof = roofline(dom)
+    roof_flux = roofline("flux")
     kernels = {k: {"ms_per_launch": round(v[0] / max(v[1], 1), 5), "launches": v[1]} for k, v in kprof.items() if v[1]}
+    # share of outputs with any in-transit sample (out-of-transit points cost no arithmetic)
+    model.evaluate(t, p, pb, ss, ex, out=flux, workspace=ws_f)
+    in_transit = float((flux != 1).float().mean().item())
+    fp64 = None
+    if not a.no_fp64_form and esize == 4:
+        fp64 = run_fp64_form(a, wl, grad, local, dev, flush)
 
     e2e = None
     if not a.no_e2e:
@@ -312,13 +322,75 @@ def run_ours(a):
                    "precision": wl.precision, "parallelism": f"replicas x{world} (pv batches, no collective)",
                    "l2": "flushed (256 MiB write) before every timed step"},
         "latency_ms": {"p50": srt[len(srt) // 2], "p99": srt[min(len(srt) - 1, int(0.99 * len(srt)))]},
-        "roofline": roof, "kernels": kernels, "cpu_baseline": cpu_base, "e2e": e2e, "clocks": clk,
-        "gpu_launches": launches,
+        "points_per_s_without_supersamples": world * wl.npv * wl.npt / (ms_per_step * 1e-3),
+        "in_transit_fraction": in_transit,
+        "roofline": roof, "roofline_flux": roof_flux, "kernels": kernels, "cpu_baseline": cpu_base,
+        "fp64_form": None if fp64 is None else dict(fp64, speedup_of_mixed=value / world / fp64["value"]),
+        "e2e": e2e, "clocks": clk, "gpu_launches": launches,
     }
     if rank == 0:
         print(json.dumps(line))
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def algorithmic_bytes(model, wl, kind, esize):
+    """Bytes a launch must move at least: the per-point output (flux) or cotangent (adjoint),
+    12 B per time (FP64 time or float-float offset, passband index), the per-pv records."""
+    per_time = 8 + 4
+    npb = wl.npb
+    head = (176 + 32 * npb) if esize == 4 else (272 + 48 * npb)
+    head = (head + 15) // 16 * 16
+    ng_pad = (wl.grid["ng"] + 3) // 4 * 4
+    nldc = (model.nparam - 6 - (npb if wl.chromatic else 1)) // npb
+    rows_per_pb = 1 if kind == "flux" else 3 + nldc
+    rows = (npb * rows_per_pb * ng_pad * esize + 15) // 16 * 16
+    return wl.npv * wl.npt * esize + wl.npt * per_time + wl.npv * (head + rows)
+
+
+def run_fp64_form(a, wl, grad, local, dev, flush):
+    """The same workload through the FP64 kernels (every step in FP64), timed the same way."""
+    import copy
+
+    import torch
+
+    from paper_2009_08500_gb300 import rr
+    w64 = copy.copy(wl)
+    w64.precision = "fp64"
+    m64 = rr.model_for(w64, device=local)
+    t, pb, p = rr.to_device(w64, local)
+    flux = torch.empty((wl.npv, wl.npt), dtype=torch.float64, device=dev)
+    ws_f = m64.workspace(wl.npv, wl.npt, False)
+    if grad:
+        ws_g = m64.workspace(wl.npv, wl.npt, True)
+        gbar = torch.randn((wl.npv, wl.npt), dtype=torch.float64, device=dev,
+                           generator=torch.Generator(device=dev).manual_seed(1234))
+        gout = torch.empty((wl.npv, m64.nparam), dtype=torch.float64, device=dev)
+    ss, ex = wl.supersampling, wl.exptime
+
+    def step():
+        m64.evaluate(t, p, pb, ss, ex, out=flux, workspace=ws_f)
+        if grad:
+            m64.evaluate_grad(t, p, gbar, pb, ss, ex, out=gout, workspace=ws_g)
+
+    for _ in range(3):
+        step()
+    n = 5
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
+    torch.cuda.synchronize()
+    for i in range(n):
+        flush.fill_(i & 0xFF)
+        ev[i][0].record()
+        step()
+        ev[i][1].record()
+    torch.cuda.synchronize()
+    ms = sum(s.elapsed_time(e) for s, e in ev) / n
+    del flux, ws_f, t, pb, p
+    if grad:
+        del ws_g, gbar, gout
+    torch.cuda.empty_cache()
+    return {"value": wl.npv * wl.samples_per_pv() / (ms * 1e-3), "unit": "points/s", "ms_per_step": ms,
+            "steps": n, "dtype": "f64", "note": "same workload and step through the FP64 kernels, one GPU"}
 
 
 def run_e2e(a, model, wl, grad, dev):

@@ -554,4 +554,76 @@ __device__ __forceinline__ bool warp_may_transit(const PvHead<float>& H, float4 
     const float phi = fmaf(whi, H.Bh, c.x) + W;
     return ceilf(plo) <= phi;
 }
+
+// ---- two-phase scheduling of the FP32 kernels -------------------------------
+//
+// Phase 1: warps take 128-time groups from a shared counter.  For a group,
+// lane l decides for pv l of the tile whether the group's phase interval can
+// hold a transit; a ballot gives the warp the tile's mask.  Pvs outside the
+// mask need no arithmetic (flux exactly 1); the others become work items
+// (pv, group) in a shared-memory queue.  Phase 2: after a CTA barrier the
+// warps drain the queue, one item at a time, so the in-transit work of the
+// CTA is spread over all its warps whatever groups it falls in.
+
+// Shared counters: [0] next group, [1] queued items, [2] next item.
+struct TileCounters {
+    int next_group, nitems, next_item, pad;
+};
+
+// Work item: phase constants of the pv at the group start (Ah, Al, m, rounding
+// bound in cycles) and (group << 5) | pv-in-tile.
+struct ItemQueue {
+    float4* c;
+    int* gi;
+};
+
+// Queue bytes for `cap` items (16-byte multiple).
+__host__ __device__ inline size_t queue_bytes(int cap) { return ((size_t)cap * 20 + 15) & ~(size_t)15; }
+
+__device__ __forceinline__ ItemQueue queue_at(char* base, int cap) {
+    ItemQueue q;
+    q.c = reinterpret_cast<float4*>(base);
+    q.gi = reinterpret_cast<int*>(base + (size_t)cap * 16);
+    return q;
+}
+
+// Lane l: transit decision for pv l of the tile at this group.  Returns the
+// warp's mask of pvs that may transit; `bad` gets the mask of invalid pvs and
+// `cl` lane l's phase constants (x, y, z = Ah, Al, m; w = rounding bound).
+__device__ __forceinline__ unsigned group_decide(const GroupState& gs, const char* recs, int rec_bytes, int npv_t,
+                                                 unsigned& bad, float4& cl) {
+    const int lane = threadIdx.x & 31;
+    bool may = false, inval = false;
+    cl = make_float4(gs.Ah, gs.Al, gs.m, 0.0f);
+    if (lane < npv_t) {
+        const PvHead<float>& H = *reinterpret_cast<const PvHead<float>*>(recs + (size_t)lane * rec_bytes);
+        inval = H.status != 0;
+        cl.w = 2.4e-7f * (gs.maxdt * H.Bh + 1.0f);
+        may = !inval && warp_may_transit(H, cl, gs.wlo, gs.whi);
+    }
+    bad = __ballot_sync(0xffffffffu, inval);
+    return __ballot_sync(0xffffffffu, may);
+}
+
+// Append the warp's items (one per set bit of `may`) to the CTA queue.
+__device__ __forceinline__ void queue_push(ItemQueue q, TileCounters* tc, unsigned may, int g, float4 cl) {
+    const int lane = threadIdx.x & 31;
+    int base = 0;
+    if (lane == 0) base = atomicAdd(&tc->nitems, __popc(may));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if ((may >> lane) & 1u) {
+        const int pos = base + __popc(may & ((1u << lane) - 1u));
+        q.c[pos] = cl;
+        q.gi[pos] = (g << 5) | lane;
+    }
+}
+
+// Next item for the warp (warp-uniform), or -1 when the queue is drained.
+__device__ __forceinline__ int queue_pop(TileCounters* tc, int nitems) {
+    const int lane = threadIdx.x & 31;
+    int it = 0;
+    if (lane == 0) it = atomicAdd(&tc->next_item, 1);
+    it = __shfl_sync(0xffffffffu, it, 0);
+    return it < nitems ? it : -1;
+}
 }  // namespace rr

@@ -41,6 +41,17 @@ __global__ void rr_points_kernel(const double* __restrict__ times, const int32_t
     pbw[p] = (pb >= 0 && pb < npb) ? pb : npb;
 }
 
+// Stores the 4 outputs of a lane (one 16-byte store when the row is vector-aligned).
+__device__ __forceinline__ void store4(float* out, const float (&f)[4], const int (&pbv)[4], bool full) {
+    if (full) {
+        __stcs(reinterpret_cast<float4*>(out), make_float4(f[0], f[1], f[2], f[3]));
+    } else {
+        #pragma unroll
+        for (int q = 0; q < 4; ++q)
+            if (pbv[q] >= 0) __stcs(out + q, f[q]);
+    }
+}
+
 template <bool STAGE_ROWS>
 __global__ void __launch_bounds__(kBlock, 4) rr_flux_mixed_kernel(const double* __restrict__ times,
                                                                const float2* __restrict__ pdt,
@@ -56,7 +67,7 @@ __global__ void __launch_bounds__(kBlock, 4) rr_flux_mixed_kernel(const double* 
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
     PbShared* ps = reinterpret_cast<PbShared*>(smem + kOffPb);
     char* recs = reinterpret_cast<char*>(smem + kOffRecs32);
-    int* next_group = reinterpret_cast<int*>(smem + kOffRed);
+    TileCounters* tc = reinterpret_cast<TileCounters*>(smem + kOffRed);
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     WarpList* wl = reinterpret_cast<WarpList*>(smem + kOffWl + warp * kWlBytes);
@@ -65,12 +76,16 @@ __global__ void __launch_bounds__(kBlock, 4) rr_flux_mixed_kernel(const double* 
     const int gend = min(ngroups, gbeg + groups_per_cta);
     const int pv0 = blockIdx.y * pv_tile;
     const int npv_t = min(pv_tile, npv - pv0);
-    // staged: headers of the tile, then (STAGE_ROWS) their profile rows
+    // staged: headers of the tile, then (STAGE_ROWS) their profile rows, then the item queue
     char* srows = recs + (size_t)pv_tile * L.head_bytes;
+    const ItemQueue queue = queue_at(srows + (STAGE_ROWS ? (size_t)pv_tile * L.rows_bytes : 0),
+                                     pv_tile * groups_per_cta);
     const uint32_t hbytes = (uint32_t)npv_t * (uint32_t)L.head_bytes;
     const uint32_t rbytes = STAGE_ROWS ? (uint32_t)npv_t * (uint32_t)L.rows_bytes : 0u;
     if (tid == 0) {
-        *next_group = gbeg;
+        tc->next_group = gbeg;
+        tc->nitems = 0;
+        tc->next_item = 0;
         mbar_init(bar, 1);
         mbar_expect_tx(bar, hbytes + rbytes);
         const char* src = records + (size_t)pv0 * L.head_bytes;
@@ -85,7 +100,7 @@ __global__ void __launch_bounds__(kBlock, 4) rr_flux_mixed_kernel(const double* 
         }
     }
     stage_pb(pbp, ps);
-    __syncthreads();   // publishes the barrier initialisation and the passband table
+    __syncthreads();   // publishes the barrier initialisation, the counters and the passband table
     bool ok = mbar_wait_bounded(bar, 0);
     if (!ok) {
         if (tid == 0) atomicExch(err, kErrBarrierTimeout);
@@ -93,95 +108,114 @@ __global__ void __launch_bounds__(kBlock, 4) rr_flux_mixed_kernel(const double* 
     }
     if (__syncthreads_or(ok ? 0 : 1)) return;
 
-    // from here on every warp is independent (no CTA barrier); warps take the
-    // CTA's groups from a shared counter, so a warp that meets transits does
-    // not hold back the others
     const float nanf_ = __int_as_float(0x7fc00000);
     const float zero4[4] = {0.f, 0.f, 0.f, 0.f};
+
+    // phase 1: per group, the tile's transit mask; every pv outside it is 1
+    // (NaN for an invalid pv or passband index) without arithmetic
     #pragma unroll 1
     while (true) {
         int g = 0;
-        if (lane == 0) g = atomicAdd(next_group, 1);
+        if (lane == 0) g = atomicAdd(&tc->next_group, 1);
         g = __shfl_sync(0xffffffffu, g, 0);
         if (g >= gend) break;
         const int p0 = g * kWarpPts + 4 * lane;
         GroupState gs;
         group_load(gs, pdt, ppb, times, g * kWarpPts, npt, recs, L.head_bytes, npv_t);
-        float fbase[4];
+        unsigned bad;
+        float4 cl;
+        const unsigned may = group_decide(gs, recs, L.head_bytes, npv_t, bad, cl);
+        if (may) queue_push(queue, tc, may, g, cl);
+        float fb[4];
         #pragma unroll
-        for (int q = 0; q < 4; ++q) fbase[q] = gs.pbv[q] < L.npb ? 1.0f : nanf_;
+        for (int q = 0; q < 4; ++q) fb[q] = gs.pbv[q] < L.npb ? 1.0f : nanf_;
         const bool full = vec_store && (p0 + 3 < npt);
+        float* out = flux + (size_t)pv0 * npt + p0;
         #pragma unroll 1
-        for (int i = 0; i < npv_t; ++i) {
-            const char* rec = recs + (size_t)i * L.head_bytes;
-            const PvHead<float>& H = *reinterpret_cast<const PvHead<float>*>(rec);
-            float* out = flux + (size_t)(pv0 + i) * npt + p0;
-            const float4 c = group_pv(gs, H, i);
-            float f[4] = {fbase[0], fbase[1], fbase[2], fbase[3]};
-            if (H.status != 0) {
-                f[0] = f[1] = f[2] = f[3] = nanf_;
-            } else if (warp_may_transit(H, c, gs.wlo, gs.whi)) {
-                const PvPb<float>* PB = reinterpret_cast<const PvPb<float>*>(rec + L.off_pb);
-                const float* rows = STAGE_ROWS ? reinterpret_cast<const float*>(srows + (size_t)i * L.rows_bytes)
-                                               : reinterpret_cast<const float*>(rowsg + (size_t)(pv0 + i) * L.rows_bytes);
-                unsigned cand = 0;
-                #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int pb = gs.pbv[q];
-                    if (pb < 0 || pb >= L.npb) continue;
-                    const float psi = fmaf(gs.dh[q], H.Bh, c.x);
-                    const float d = psi - round_nearest(psi);
-                    if (fabsf(d) <= PB[pb].win_pc + c.w) cand |= 1u << q;
-                }
-                bool bad = false;
-                if (__any_sync(0xffffffffu, cand != 0)) {
-                    int nc, base;
-                    const int ns = build_list(wl, cand, gs.dh, gs.dl, gs.pbv, zero4, c.x, c.y, H.Bh, H.Bl, ps, nc,
-                                              base);
-                    ChunkWalk cw{0};
-                    for (int e0 = 0; e0 < ns; e0 += 32) {
-                        const int e = e0 + lane;
-                        const bool valid = e < ns;
-                        const int jc = chunk_cand(cw, wl->soff, nc, e0);
-                        const int j = valid ? jc : -1;
-                        float d = 0.0f;
-                        if (valid) {
-                            const int pb = wl->pb[j];
-                            const float4 cd = wl->cand[j];
-                            d = delta32(H, PB[pb], rows + (size_t)pb * L.rows_per_pb * L.ng_pad, L.ng, cd.x, cd.y,
-                                        e - wl->soff[j], ps->first[pb], ps->step[pb], bad);
-                        }
-                        // sum over the sub-exposures of each time: segmented scan along the lanes
-                        #pragma unroll
-                        for (int o = 1; o < 32; o <<= 1) {
-                            const float y = __shfl_up_sync(0xffffffffu, d, o);
-                            const int ky = __shfl_up_sync(0xffffffffu, j, o);
-                            if (lane >= o && ky == j) d += y;
-                        }
-                        const int jn = __shfl_down_sync(0xffffffffu, j, 1);
-                        if (valid && (lane == 31 || jn != j)) wl->pacc[j] += d;
-                        __syncwarp();
-                    }
-                    int jj = base;
-                    #pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        if (cand & (1u << q)) {
-                            f[q] = 1.0f - wl->pacc[jj] * ps->inv_ss[gs.pbv[q]];
-                            ++jj;
-                        }
-                    }
-                    __syncwarp();
-                }
-                if (bad && pv_status) atomicOr(pv_status + pv0 + i, RR_PV_KEPLER);
-            }
-            if (full) {
-                __stcs(reinterpret_cast<float4*>(out), make_float4(f[0], f[1], f[2], f[3]));
-            } else {
-                #pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    if (gs.pbv[q] >= 0) __stcs(out + q, f[q]);
-            }
+        for (int i = 0; i < npv_t; ++i, out += npt) {
+            if ((may >> i) & 1u) continue;
+            const bool inval = (bad >> i) & 1u;
+            const float f[4] = {inval ? nanf_ : fb[0], inval ? nanf_ : fb[1], inval ? nanf_ : fb[2],
+                                inval ? nanf_ : fb[3]};
+            store4(out, f, gs.pbv, full);
         }
+    }
+    __syncthreads();
+    const int nitems = tc->nitems;
+
+    // phase 2: the queued (pv, group) items, one per warp at a time
+    #pragma unroll 1
+    while (true) {
+        const int it = queue_pop(tc, nitems);
+        if (it < 0) break;
+        const float4 c = queue.c[it];
+        const int gi = queue.gi[it];
+        const int g = gi >> 5, i = gi & 31;
+        const int p0 = g * kWarpPts + 4 * lane;
+        float dh[4], dl[4];
+        int pbv[4];
+        load_points(pdt, ppb, p0, npt, dh, dl, pbv);
+        const char* rec = recs + (size_t)i * L.head_bytes;
+        const PvHead<float>& H = *reinterpret_cast<const PvHead<float>*>(rec);
+        const PvPb<float>* PB = reinterpret_cast<const PvPb<float>*>(rec + L.off_pb);
+        const float* rows = STAGE_ROWS ? reinterpret_cast<const float*>(srows + (size_t)i * L.rows_bytes)
+                                       : reinterpret_cast<const float*>(rowsg + (size_t)(pv0 + i) * L.rows_bytes);
+        float f[4];
+        unsigned cand = 0;
+        #pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int pb = pbv[q];
+            f[q] = pb < L.npb ? 1.0f : nanf_;
+            if (pb < 0 || pb >= L.npb) continue;
+            const float psi = fmaf(dh[q], H.Bh, c.x);
+            const float d = psi - round_nearest(psi);
+            if (fabsf(d) <= PB[pb].win_pc + c.w) cand |= 1u << q;
+        }
+        bool bad = false;
+        if (__any_sync(0xffffffffu, cand != 0)) {
+            int nc, base;
+            const int ns = build_list(wl, cand, dh, dl, pbv, zero4, c.x, c.y, H.Bh, H.Bl, ps, nc, base);
+            ChunkWalk cw{0};
+            for (int e0 = 0; e0 < ns; e0 += 32) {
+                const int e = e0 + lane;
+                const bool valid = e < ns;
+                const int jc = chunk_cand(cw, wl->soff, nc, e0);
+                const int j = valid ? jc : -1;
+                float d = 0.0f;
+                if (valid) {
+                    const int pb = wl->pb[j];
+                    const float4 cd = wl->cand[j];
+                    d = delta32(H, PB[pb], rows + (size_t)pb * L.rows_per_pb * L.ng_pad, L.ng, cd.x, cd.y,
+                                e - wl->soff[j], ps->first[pb], ps->step[pb], bad);
+                }
+                if (ns == nc) {
+                    // one sample per candidate: nothing to sum
+                    if (valid) wl->pacc[j] = d;
+                } else {
+                    // sum over the sub-exposures of each time: segmented scan along the lanes
+                    #pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const float y = __shfl_up_sync(0xffffffffu, d, o);
+                        const int ky = __shfl_up_sync(0xffffffffu, j, o);
+                        if (lane >= o && ky == j) d += y;
+                    }
+                    const int jn = __shfl_down_sync(0xffffffffu, j, 1);
+                    if (valid && (lane == 31 || jn != j)) wl->pacc[j] += d;
+                }
+                __syncwarp();
+            }
+            int jj = base;
+            #pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if (cand & (1u << q)) {
+                    f[q] = 1.0f - wl->pacc[jj] * ps->inv_ss[pbv[q]];
+                    ++jj;
+                }
+            }
+            __syncwarp();
+        }
+        if (bad && pv_status) atomicOr(pv_status + pv0 + i, RR_PV_KEPLER);
+        store4(flux + (size_t)(pv0 + i) * npt + p0, f, pbv, vec_store && (p0 + 3 < npt));
     }
 }
 
@@ -275,8 +309,9 @@ __global__ void __launch_bounds__(kBlock) rr_flux_fp64_kernel(const double* __re
     }
 }
 
-static size_t flux_smem(int pv_tile, int rec_bytes, bool f64) {
-    return (f64 ? 16 + 16 * 4 + 16 * kMaxPvTile : kOffRecs32) + (size_t)pv_tile * rec_bytes;
+static size_t flux_smem(int pv_tile, int rec_bytes, bool f64, int gpc) {
+    if (f64) return 16 + 16 * 4 + 16 * kMaxPvTile + (size_t)pv_tile * rec_bytes;
+    return kOffRecs32 + (size_t)pv_tile * rec_bytes + queue_bytes(pv_tile * gpc);
 }
 
 // 128-time groups per CTA of the FP32 kernels.  A function of npt only, so
@@ -317,10 +352,10 @@ cudaError_t launch_flux(rr_ctx* c, const double* times, const int32_t* pb_index,
     const bool stage_rows = !f64 && c->cfg.npb > 1;
     const int per_pv = stage_rows ? L.head_bytes + L.rows_bytes : L.head_bytes;
     const int pv_tile = pv_tile_for(per_pv);
-    const size_t smem = flux_smem(pv_tile, per_pv, f64);
+    const int gpc = groups_per_cta(npt);
+    const size_t smem = flux_smem(pv_tile, per_pv, f64, gpc);
     const char* rowsg = (const char*)records + rows_offset(L, npv);
     const int npvt = (npv + pv_tile - 1) / pv_tile;
-    const int gpc = groups_per_cta(npt);
     const int ngroups = (npt + kWarpPts - 1) / kWarpPts;
     dim3 grid(f64 ? (npt + kPtTile - 1) / kPtTile : (ngroups + gpc - 1) / gpc, npvt);
     if (smem > kMaxSmem || grid.y > 65535u) return cudaErrorInvalidConfiguration;

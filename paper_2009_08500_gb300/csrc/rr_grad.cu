@@ -201,7 +201,9 @@ __global__ void __launch_bounds__(kBlock, 3) rr_grad_mixed_kernel(
     char* recs = reinterpret_cast<char*>(smem + kOffRecs32);
     float* gacc = reinterpret_cast<float*>(recs + (size_t)pv_tile * L.head_bytes);   // [pv][group][nacc]
     float* depcols = gacc + (size_t)pv_tile * groups_per_cta * nacc;
-    int* next_group = reinterpret_cast<int*>(smem + kOffRed);
+    const ItemQueue queue = queue_at(reinterpret_cast<char*>(depcols + (DEP ? (size_t)(nacc - 6) * kBlock : 0)),
+                                     pv_tile * groups_per_cta);
+    TileCounters* tc = reinterpret_cast<TileCounters*>(smem + kOffRed);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     WarpList* wl = reinterpret_cast<WarpList*>(smem + kOffWl + warp * kWlBytes);
@@ -212,7 +214,9 @@ __global__ void __launch_bounds__(kBlock, 3) rr_grad_mixed_kernel(
     const int npv_t = min(pv_tile, npv - pv0);
     const uint32_t bytes = (uint32_t)npv_t * (uint32_t)L.head_bytes;
     if (tid == 0) {
-        *next_group = gbeg;
+        tc->next_group = gbeg;
+        tc->nitems = 0;
+        tc->next_item = 0;
         mbar_init(bar, 1);
         mbar_expect_tx(bar, bytes);
         const char* src = records + (size_t)pv0 * L.head_bytes;
@@ -231,95 +235,107 @@ __global__ void __launch_bounds__(kBlock, 3) rr_grad_mixed_kernel(
     }
     if (__syncthreads_or(ok ? 0 : 1)) return;
 
-    // every warp is independent until the final reduction; groups come from a
-    // shared counter and each group's sums go to its own slot, so the result
-    // does not depend on which warp took which group
+    // phase 1: per group, the tile's transit mask -> work items
+    #pragma unroll 1
+    while (true) {
+        int g = 0;
+        if (lane == 0) g = atomicAdd(&tc->next_group, 1);
+        g = __shfl_sync(0xffffffffu, g, 0);
+        if (g >= gend) break;
+        GroupState gs;
+        group_load(gs, pdt, ppb, times, g * kWarpPts, npt, recs, L.head_bytes, npv_t);
+        unsigned bad;
+        float4 cl;
+        const unsigned may = group_decide(gs, recs, L.head_bytes, npv_t, bad, cl);
+        if (may) queue_push(queue, tc, may, g, cl);
+    }
+    __syncthreads();
+    const int nitems = tc->nitems;
+
+    // phase 2: every item's sums go to its own (pv, group) slot, so the result
+    // does not depend on which warp took which item
     const float two_pi = 6.28318530717958647692f;
     const int nkp = chromatic ? L.npb : 1;
     float* dep = DEP ? depcols + tid : nullptr;
     #pragma unroll 1
     while (true) {
-        int g = 0;
-        if (lane == 0) g = atomicAdd(next_group, 1);
-        g = __shfl_sync(0xffffffffu, g, 0);
-        if (g >= gend) break;
+        const int it = queue_pop(tc, nitems);
+        if (it < 0) break;
+        const float4 c = queue.c[it];
+        const int gi = queue.gi[it];
+        const int g = gi >> 5, i = gi & 31;
         const int p0 = g * kWarpPts + 4 * lane;
-        GroupState gs;
-        group_load(gs, pdt, ppb, times, g * kWarpPts, npt, recs, L.head_bytes, npv_t);
-        #pragma unroll 1
-        for (int i = 0; i < npv_t; ++i) {
-            const char* rec = recs + (size_t)i * L.head_bytes;
-            const PvHead<float>& H = *reinterpret_cast<const PvHead<float>*>(rec);
-            const float4 c = group_pv(gs, H, i);
-            if (H.status != 0 || !warp_may_transit(H, c, gs.wlo, gs.whi)) continue;   // warp-uniform
-            const PvPb<float>* PB = reinterpret_cast<const PvPb<float>*>(rec + L.off_pb);
-            const float* rows = reinterpret_cast<const float*>(rowsg + (size_t)(pv0 + i) * L.rows_bytes);
-            const float* gf = gflux + (size_t)(pv0 + i) * npt + p0;
-            unsigned cand = 0;
-            float gbq[4];
-            #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                gbq[q] = 0.0f;
-                const int pb = gs.pbv[q];
-                if (pb < 0 || pb >= L.npb) continue;
-                const float psi = fmaf(gs.dh[q], H.Bh, c.x);
-                const float d = psi - round_nearest(psi);
-                if (fabsf(d) <= PB[pb].win_pc + c.w) {
-                    gbq[q] = -__ldg(gf + q) * ps->inv_ss[pb];
-                    if (gbq[q] != 0.0f) cand |= 1u << q;
-                }
+        float dh[4], dl[4];
+        int pbv[4];
+        load_points(pdt, ppb, p0, npt, dh, dl, pbv);
+        const char* rec = recs + (size_t)i * L.head_bytes;
+        const PvHead<float>& H = *reinterpret_cast<const PvHead<float>*>(rec);
+        const PvPb<float>* PB = reinterpret_cast<const PvPb<float>*>(rec + L.off_pb);
+        const float* rows = reinterpret_cast<const float*>(rowsg + (size_t)(pv0 + i) * L.rows_bytes);
+        const float* gf = gflux + (size_t)(pv0 + i) * npt + p0;
+        unsigned cand = 0;
+        float gbq[4];
+        #pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            gbq[q] = 0.0f;
+            const int pb = pbv[q];
+            if (pb < 0 || pb >= L.npb) continue;
+            const float psi = fmaf(dh[q], H.Bh, c.x);
+            const float d = psi - round_nearest(psi);
+            if (fabsf(d) <= PB[pb].win_pc + c.w) {
+                gbq[q] = -__ldg(gf + q) * ps->inv_ss[pb];
+                if (gbq[q] != 0.0f) cand |= 1u << q;
             }
-            if (!__any_sync(0xffffffffu, cand != 0)) continue;
-            GradAcc<float> acc;
-            #pragma unroll
-            for (int j = 0; j < 6; ++j) acc.o[j] = 0.0f;
-            acc.k = 0.0f;
-            #pragma unroll
-            for (int j = 0; j < 4; ++j) acc.u[j] = 0.0f;
-            if (DEP)
-                for (int j = 6; j < nacc; ++j) dep[(j - 6) * kBlock] = 0.0f;
-            bool any = false, bad = false;
-            int nc, base;
-            const int ns = build_list(wl, cand, gs.dh, gs.dl, gs.pbv, gbq, c.x, c.y, H.Bh, H.Bl, ps, nc, base);
-            ChunkWalk cw{0};
-            for (int e0 = 0; e0 < ns; e0 += 32) {
-                const int e = e0 + lane;
-                const int j = chunk_cand(cw, wl->soff, nc, e0);
-                if (e >= ns) continue;
-                const int pb = wl->pb[j];
-                const float4 cd = wl->cand[j];
-                const PvPb<float> pbc = PB[pb];
-                const float off = fmaf((float)(e - wl->soff[j]), ps->step[pb], ps->first[pb]) * H.Bh;
-                const float xr = (cd.x + off) + cd.y;
-                const float r = round_nearest(xr);
-                const float x = xr - r;
-                const float dM = two_pi * x;
-                if (fabsf(dM) > pbc.win_s) continue;
-                double dMd = 0.0;
-                if (H.flags & kPvKepler64) {
-                    double xd = ((double)cd.x + (double)off) + (double)cd.y;
-                    xd -= rint(xd);
-                    dMd = 6.283185307179586476925 * xd;
-                }
-                const Orbit32 o = orbit32(H, dM, dMd);
-                if (!o.ok) { bad = true; continue; }
-                const float gz = o.z * pbc.inv1pk;
-                if (!o.front || gz >= 1.0f) continue;
-                const float psi_tot = ((c.z + cd.z) + r) + x;   // (t_s - T0) / P
-                grad_sample<float, DEP>(H, pbc, rows + (size_t)pb * L.rows_per_pb * L.ng_pad, L, o.z, o.Px,
-                                        o.Py, o.S, o.V, psi_tot, cd.w, acc, dep, 6 + (chromatic ? pb : 0),
-                                        6 + nkp + pb * L.nldc);
-                any = true;
-            }
-            __syncwarp();
-            if (bad) {
-                acc.o[0] = __int_as_float(0x7fc00000);
-                any = true;
-                if (pv_status) atomicOr(pv_status + pv0 + i, RR_PV_KEPLER);
-            }
-            warp_accumulate<float, DEP>(acc, dep, nacc, any,
-                                        gacc + ((size_t)i * groups_per_cta + (g - gbeg)) * nacc);
         }
+        if (!__any_sync(0xffffffffu, cand != 0)) continue;
+        GradAcc<float> acc;
+        #pragma unroll
+        for (int j = 0; j < 6; ++j) acc.o[j] = 0.0f;
+        acc.k = 0.0f;
+        #pragma unroll
+        for (int j = 0; j < 4; ++j) acc.u[j] = 0.0f;
+        if (DEP)
+            for (int j = 6; j < nacc; ++j) dep[(j - 6) * kBlock] = 0.0f;
+        bool any = false, bad = false;
+        int nc, base;
+        const int ns = build_list(wl, cand, dh, dl, pbv, gbq, c.x, c.y, H.Bh, H.Bl, ps, nc, base);
+        ChunkWalk cw{0};
+        for (int e0 = 0; e0 < ns; e0 += 32) {
+            const int e = e0 + lane;
+            const int j = chunk_cand(cw, wl->soff, nc, e0);
+            if (e >= ns) continue;
+            const int pb = wl->pb[j];
+            const float4 cd = wl->cand[j];
+            const PvPb<float> pbc = PB[pb];
+            const float off = fmaf((float)(e - wl->soff[j]), ps->step[pb], ps->first[pb]) * H.Bh;
+            const float xr = (cd.x + off) + cd.y;
+            const float r = round_nearest(xr);
+            const float x = xr - r;
+            const float dM = two_pi * x;
+            if (fabsf(dM) > pbc.win_s) continue;
+            double dMd = 0.0;
+            if (H.flags & kPvKepler64) {
+                double xd = ((double)cd.x + (double)off) + (double)cd.y;
+                xd -= rint(xd);
+                dMd = 6.283185307179586476925 * xd;
+            }
+            const Orbit32 o = orbit32(H, dM, dMd);
+            if (!o.ok) { bad = true; continue; }
+            const float gz = o.z * pbc.inv1pk;
+            if (!o.front || gz >= 1.0f) continue;
+            const float psi_tot = ((c.z + cd.z) + r) + x;   // (t_s - T0) / P
+            grad_sample<float, DEP>(H, pbc, rows + (size_t)pb * L.rows_per_pb * L.ng_pad, L, o.z, o.Px,
+                                    o.Py, o.S, o.V, psi_tot, cd.w, acc, dep, 6 + (chromatic ? pb : 0),
+                                    6 + nkp + pb * L.nldc);
+            any = true;
+        }
+        __syncwarp();
+        if (bad) {
+            acc.o[0] = __int_as_float(0x7fc00000);
+            any = true;
+            if (pv_status) atomicOr(pv_status + pv0 + i, RR_PV_KEPLER);
+        }
+        warp_accumulate<float, DEP>(acc, dep, nacc, any, gacc + ((size_t)i * groups_per_cta + (g - gbeg)) * nacc);
     }
     cta_partials_groups(gacc, recs, L.head_bytes, npv_t, nacc, groups_per_cta, pv0, blockIdx.x, gridDim.x,
                         partials);
@@ -459,6 +475,7 @@ static size_t grad_smem(int pv_tile, const RecLayout& L, int nacc, bool dep, siz
     size_t s = (rsize == 8 ? 16 + 16 * 4 + 16 * kMaxPvTile : kOffRecs32) + (size_t)pv_tile * L.head_bytes +
                (size_t)pv_tile * slots * nacc * rsize;
     if (dep) s += (size_t)(nacc - 6) * kBlock * rsize;
+    if (rsize == 4) s = ((s + 15) & ~(size_t)15) + queue_bytes(pv_tile * slots);   // FP32 kernel: item queue
     return s;
 }
 

@@ -196,6 +196,40 @@ rr_status rr_evaluate_grad(rr_ctx* ctx, const double* times, const int32_t* pb_i
                            int32_t* pv_status, void* workspace, size_t workspace_bytes,
                            void* stream);
 
+/* Shared set-up for one flux evaluation and one adjoint on the same batch
+ * (the forward and backward passes of a fit step).  rr_evaluate and
+ * rr_evaluate_grad each run the per-pv set-up (orbit constants, transit
+ * windows, the k-interpolated profile rows of Sect. 3.1.2 divided by I_star)
+ * and the per-time preparation before their main kernel; rr_prepare runs
+ * them once, in the adjoint's record layout, into `workspace`, and
+ * rr_evaluate_prepared / rr_evaluate_grad_prepared then run only the main
+ * kernels.  The paper has no counterpart (its model has no adjoint).
+ *   - All three take the arguments of rr_evaluate_grad (minus the outputs
+ *     they do not write); the two evaluation calls must be given the same
+ *     times, pb_index, params, supersampling, exptime and workspace as the
+ *     rr_prepare call, and the workspace must not change in between (the
+ *     library cannot check this: different inputs give wrong results).
+ *   - workspace: >= rr_workspace_bytes(ctx, npv, npt, 1) bytes, 256-byte
+ *     aligned, owned by the caller; it holds the prepared batch until the
+ *     caller reuses it.
+ *   - pv_status (optional) is written by rr_prepare; the evaluation calls
+ *     may add RR_PV_KEPLER.
+ *   - Results are bitwise those of rr_evaluate / rr_evaluate_grad.
+ * Errors: as rr_evaluate_grad. */
+rr_status rr_prepare(rr_ctx* ctx, const double* times, const int32_t* pb_index, int32_t npt,
+                     const double* params, int32_t npv, const int32_t* supersampling,
+                     const double* exptime, int32_t* pv_status, void* workspace,
+                     size_t workspace_bytes, void* stream);
+rr_status rr_evaluate_prepared(rr_ctx* ctx, const double* times, const int32_t* pb_index, int32_t npt,
+                               const double* params, int32_t npv, const int32_t* supersampling,
+                               const double* exptime, void* flux, int32_t* pv_status,
+                               const void* workspace, size_t workspace_bytes, void* stream);
+rr_status rr_evaluate_grad_prepared(rr_ctx* ctx, const double* times, const int32_t* pb_index,
+                                    int32_t npt, const double* params, int32_t npv,
+                                    const int32_t* supersampling, const double* exptime,
+                                    const void* grad_flux, double* grad_params, int32_t* pv_status,
+                                    const void* workspace, size_t workspace_bytes, void* stream);
+
 /* Copy a set-up table to host memory (for inspection and tests); returns the
  * element count of the table, or -1 on error.  `out` may be NULL to query
  * the size; otherwise it receives min(count, capacity) doubles.

@@ -176,6 +176,97 @@ WsLayout ws_layout(const rr_ctx* c, int npv, int npt, bool grad) {
 }
 }  // namespace rr
 
+namespace {
+
+// Per-pv set-up and per-time preparation (the first two kernels of every evaluation).
+cudaError_t run_setup(rr_ctx* c, const double* times, const int32_t* pb_index, int npt, const double* params,
+                      int npv, const PbParams& pbp, bool grad, int32_t* pv_status, void* ws, cudaStream_t s) {
+    cudaError_t e = timed(c, RR_KERNEL_PV_SETUP, s,
+                          [&] { return launch_pv_setup(c, params, npv, pbp, grad, ws, pv_status, s); });
+    if (e != cudaSuccess || c->cfg.precision != RR_PREC_MIXED || npt == 0) return e;
+    const WsLayout W = ws_layout(c, npv, npt, grad);
+    char* wb = (char*)ws;
+    return timed(c, RR_KERNEL_POINTS, s,
+                 [&] { return launch_points(c, times, pb_index, npt, wb + W.pts_dt, wb + W.pts_pb, s); });
+}
+
+// Validity words only (npt == 0 with a pv_status array): the set-up kernel alone.
+rr_status status_only(rr_ctx* c, const double* params, int npv, const PbParams& pbp, bool grad,
+                      int32_t* pv_status, void* ws, size_t ws_bytes, cudaStream_t s, const char* what) {
+    if (!params) return fail(c, RR_EINVAL, "params must be non-null");
+    if (!ws || ws_bytes < rr_workspace_bytes(c, npv, 0, grad ? 1 : 0) || ((uintptr_t)ws & 255u))
+        return fail(c, RR_EINVAL, "workspace too small or misaligned");
+    cudaError_t e = cudaSetDevice(c->cfg.device);
+    if (e == cudaSuccess)
+        e = timed(c, RR_KERNEL_PV_SETUP, s, [&] { return launch_pv_setup(c, params, npv, pbp, grad, ws, pv_status, s); });
+    if (e != cudaSuccess) return cuda_fail(c, e, what);
+    return RR_OK;
+}
+
+rr_status evaluate_impl(rr_ctx* c, const double* times, const int32_t* pb_index, int32_t npt, const double* params,
+                        int32_t npv, const int32_t* ss, const double* exptime, void* flux, int32_t* pv_status,
+                        void* ws, size_t ws_bytes, bool prepared, void* stream) {
+    PbParams pbp;
+    rr_status st = check_eval(c, times, pb_index, npt, params, npv, ss, exptime, flux, ws, ws_bytes, prepared, pbp);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (st != RR_OK || npt == 0 || npv == 0) {
+        // nothing to evaluate, but report the validity of every pv
+        if (st == RR_OK && npv > 0 && pv_status && npt == 0 && !prepared)
+            return status_only(c, params, npv, pbp, false, pv_status, ws, ws_bytes, s, "rr_evaluate");
+        return st;
+    }
+    cudaError_t e = cudaSetDevice(c->cfg.device);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
+    if (!prepared && (e = run_setup(c, times, pb_index, npt, params, npv, pbp, false, pv_status, ws, s)) != cudaSuccess)
+        return cuda_fail(c, e, "set-up kernels");
+    const WsLayout W = ws_layout(c, npv, npt, prepared);
+    char* wb = (char*)ws;
+    if ((e = timed(c, RR_KERNEL_FLUX, s, [&] {
+             return launch_flux(c, times, pb_index, wb + W.pts_dt, wb + W.pts_pb, npt, npv, pbp, ws, flux,
+                                pv_status, prepared, s);
+         })) != cudaSuccess)
+        return cuda_fail(c, e, "flux kernel");
+    return RR_OK;
+}
+
+rr_status evaluate_grad_impl(rr_ctx* c, const double* times, const int32_t* pb_index, int32_t npt,
+                             const double* params, int32_t npv, const int32_t* ss, const double* exptime,
+                             const void* grad_flux, double* grad_params, int32_t* pv_status, void* ws,
+                             size_t ws_bytes, bool prepared, void* stream) {
+    PbParams pbp;
+    rr_status st = check_eval(c, times, pb_index, npt, params, npv, ss, exptime, grad_params, ws, ws_bytes, true, pbp);
+    if (st != RR_OK) return st;
+    if (npv == 0) return RR_OK;
+    if (npt > 0 && !grad_flux) return fail(c, RR_EINVAL, "grad_flux must be non-null");
+    if (!grad_params || !params) return fail(c, RR_EINVAL, "params and grad_params must be non-null");
+    if (c->nparam > 64) return fail(c, RR_EINVAL, "the adjoint supports at most 64 parameters per vector");
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaSetDevice(c->cfg.device);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
+    if (npt == 0) {
+        if ((e = cudaMemsetAsync(grad_params, 0, (size_t)npv * c->nparam * sizeof(double), s)) != cudaSuccess)
+            return cuda_fail(c, e, "rr_evaluate_grad");
+        return RR_OK;
+    }
+    if (!prepared && (e = run_setup(c, times, pb_index, npt, params, npv, pbp, true, pv_status, ws, s)) != cudaSuccess)
+        return cuda_fail(c, e, "set-up kernels");
+    const WsLayout W = ws_layout(c, npv, npt, true);
+    char* wb = (char*)ws;
+    void* partials = wb + W.part;
+    if ((e = timed(c, RR_KERNEL_GRAD, s, [&] {
+             return launch_grad(c, times, pb_index, wb + W.pts_dt, wb + W.pts_pb, npt, npv, pbp, ws, grad_flux,
+                                partials, pv_status, s);
+         })) != cudaSuccess)
+        return cuda_fail(c, e, "adjoint kernel");
+    if ((e = timed(c, RR_KERNEL_GRAD_REDUCE, s, [&] {
+             return launch_grad_reduce(c, npt, params, npv, ws, partials, grad_params, s);
+         })) != cudaSuccess)
+        return cuda_fail(c, e, "adjoint reduction kernel");
+    return RR_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 rr_status rr_create(const rr_config* cfg, rr_ctx** out) {
@@ -305,86 +396,52 @@ size_t rr_workspace_bytes(const rr_ctx* c, int32_t npv, int32_t npt, int32_t wit
     return ws_layout(c, npv, npt, with_grad != 0).total;
 }
 
+
 rr_status rr_evaluate(rr_ctx* c, const double* times, const int32_t* pb_index, int32_t npt, const double* params,
                       int32_t npv, const int32_t* ss, const double* exptime, void* flux, int32_t* pv_status,
                       void* ws, size_t ws_bytes, void* stream) {
-    PbParams pbp;
-    rr_status st = check_eval(c, times, pb_index, npt, params, npv, ss, exptime, flux, ws, ws_bytes, false, pbp);
-    if (st != RR_OK || npt == 0 || npv == 0) {
-        if (st == RR_OK && npv > 0 && pv_status && npt == 0) {
-            // nothing to evaluate, but report the validity of every pv
-            if (!params) return fail(c, RR_EINVAL, "params must be non-null");
-            if (!ws || ws_bytes < rr_workspace_bytes(c, npv, 0, 0) || ((uintptr_t)ws & 255u))
-                return fail(c, RR_EINVAL, "workspace too small or misaligned");
-            cudaStream_t s = (cudaStream_t)stream;
-            cudaError_t e = cudaSetDevice(c->cfg.device);
-            if (e == cudaSuccess)
-                e = timed(c, RR_KERNEL_PV_SETUP, s, [&] { return launch_pv_setup(c, params, npv, pbp, false, ws, pv_status, s); });
-            if (e != cudaSuccess) return cuda_fail(c, e, "rr_evaluate");
-        }
-        return st;
-    }
-    cudaStream_t s = (cudaStream_t)stream;
-    cudaError_t e = cudaSetDevice(c->cfg.device);
-    if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
-    if ((e = timed(c, RR_KERNEL_PV_SETUP, s,
-                   [&] { return launch_pv_setup(c, params, npv, pbp, false, ws, pv_status, s); })) != cudaSuccess)
-        return cuda_fail(c, e, "parameter-vector set-up kernel");
-    const WsLayout W = ws_layout(c, npv, npt, false);
-    char* wb = (char*)ws;
-    if (c->cfg.precision == RR_PREC_MIXED &&
-        (e = timed(c, RR_KERNEL_POINTS, s, [&] {
-             return launch_points(c, times, pb_index, npt, wb + W.pts_dt, wb + W.pts_pb, s);
-         })) != cudaSuccess)
-        return cuda_fail(c, e, "point preparation kernel");
-    if ((e = timed(c, RR_KERNEL_FLUX, s, [&] {
-             return launch_flux(c, times, pb_index, wb + W.pts_dt, wb + W.pts_pb, npt, npv, pbp, ws, flux,
-                                pv_status, s);
-         })) != cudaSuccess)
-        return cuda_fail(c, e, "flux kernel");
-    return RR_OK;
+    return evaluate_impl(c, times, pb_index, npt, params, npv, ss, exptime, flux, pv_status, ws, ws_bytes, false,
+                         stream);
 }
 
 rr_status rr_evaluate_grad(rr_ctx* c, const double* times, const int32_t* pb_index, int32_t npt,
                            const double* params, int32_t npv, const int32_t* ss, const double* exptime,
                            const void* grad_flux, double* grad_params, int32_t* pv_status, void* ws,
                            size_t ws_bytes, void* stream) {
+    return evaluate_grad_impl(c, times, pb_index, npt, params, npv, ss, exptime, grad_flux, grad_params, pv_status,
+                              ws, ws_bytes, false, stream);
+}
+
+rr_status rr_prepare(rr_ctx* c, const double* times, const int32_t* pb_index, int32_t npt, const double* params,
+                     int32_t npv, const int32_t* ss, const double* exptime, int32_t* pv_status, void* ws,
+                     size_t ws_bytes, void* stream) {
     PbParams pbp;
-    rr_status st = check_eval(c, times, pb_index, npt, params, npv, ss, exptime, grad_params, ws, ws_bytes, true, pbp);
-    if (st != RR_OK) return st;
-    if (npv == 0) return RR_OK;
-    if (npt > 0 && !grad_flux) return fail(c, RR_EINVAL, "grad_flux must be non-null");
-    if (!grad_params || !params) return fail(c, RR_EINVAL, "params and grad_params must be non-null");
-    if (c->nparam > 64) return fail(c, RR_EINVAL, "the adjoint supports at most 64 parameters per vector");
+    // the workspace stands in for the output pointer: rr_prepare writes only the workspace
+    rr_status st = check_eval(c, times, pb_index, npt, params, npv, ss, exptime, ws, ws, ws_bytes, true, pbp);
     cudaStream_t s = (cudaStream_t)stream;
+    if (st != RR_OK || npv == 0) return st;
+    if (npt == 0)
+        return pv_status ? status_only(c, params, npv, pbp, true, pv_status, ws, ws_bytes, s, "rr_prepare") : RR_OK;
     cudaError_t e = cudaSetDevice(c->cfg.device);
     if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
-    if (npt == 0) {
-        if ((e = cudaMemsetAsync(grad_params, 0, (size_t)npv * c->nparam * sizeof(double), s)) != cudaSuccess)
-            return cuda_fail(c, e, "rr_evaluate_grad");
-        return RR_OK;
-    }
-    if ((e = timed(c, RR_KERNEL_PV_SETUP, s,
-                   [&] { return launch_pv_setup(c, params, npv, pbp, true, ws, pv_status, s); })) != cudaSuccess)
-        return cuda_fail(c, e, "parameter-vector set-up kernel");
-    const WsLayout W = ws_layout(c, npv, npt, true);
-    char* wb = (char*)ws;
-    void* partials = wb + W.part;
-    if (c->cfg.precision == RR_PREC_MIXED &&
-        (e = timed(c, RR_KERNEL_POINTS, s, [&] {
-             return launch_points(c, times, pb_index, npt, wb + W.pts_dt, wb + W.pts_pb, s);
-         })) != cudaSuccess)
-        return cuda_fail(c, e, "point preparation kernel");
-    if ((e = timed(c, RR_KERNEL_GRAD, s, [&] {
-             return launch_grad(c, times, pb_index, wb + W.pts_dt, wb + W.pts_pb, npt, npv, pbp, ws, grad_flux,
-                                partials, pv_status, s);
-         })) != cudaSuccess)
-        return cuda_fail(c, e, "adjoint kernel");
-    if ((e = timed(c, RR_KERNEL_GRAD_REDUCE, s, [&] {
-             return launch_grad_reduce(c, npt, params, npv, ws, partials, grad_params, s);
-         })) != cudaSuccess)
-        return cuda_fail(c, e, "adjoint reduction kernel");
+    if ((e = run_setup(c, times, pb_index, npt, params, npv, pbp, true, pv_status, ws, s)) != cudaSuccess)
+        return cuda_fail(c, e, "set-up kernels");
     return RR_OK;
+}
+
+rr_status rr_evaluate_prepared(rr_ctx* c, const double* times, const int32_t* pb_index, int32_t npt,
+                               const double* params, int32_t npv, const int32_t* ss, const double* exptime,
+                               void* flux, int32_t* pv_status, const void* ws, size_t ws_bytes, void* stream) {
+    return evaluate_impl(c, times, pb_index, npt, params, npv, ss, exptime, flux, pv_status, const_cast<void*>(ws),
+                         ws_bytes, true, stream);
+}
+
+rr_status rr_evaluate_grad_prepared(rr_ctx* c, const double* times, const int32_t* pb_index, int32_t npt,
+                                    const double* params, int32_t npv, const int32_t* ss, const double* exptime,
+                                    const void* grad_flux, double* grad_params, int32_t* pv_status, const void* ws,
+                                    size_t ws_bytes, void* stream) {
+    return evaluate_grad_impl(c, times, pb_index, npt, params, npv, ss, exptime, grad_flux, grad_params, pv_status,
+                              const_cast<void*>(ws), ws_bytes, true, stream);
 }
 
 int64_t rr_read_table(rr_ctx* c, int32_t which, double* out, int64_t capacity) {

@@ -342,14 +342,15 @@ cudaError_t launch_points(rr_ctx* c, const double* times, const int32_t* pb_inde
 
 cudaError_t launch_flux(rr_ctx* c, const double* times, const int32_t* pb_index, const void* pts_dt,
                         const void* pts_pb, int npt, int npv, const PbParams& pbp, const void* records,
-                        void* flux, int32_t* pv_status, cudaStream_t s) {
+                        void* flux, int32_t* pv_status, bool grad_layout, cudaStream_t s) {
     const bool f64 = c->cfg.precision == RR_PREC_FP64;
-    RecLayout L = f64 ? make_layout<double>(c->cfg.npb, c->cfg.ng, c->nldc, false)
-                      : make_layout<float>(c->cfg.npb, c->cfg.ng, c->nldc, false);
+    RecLayout L = f64 ? make_layout<double>(c->cfg.npb, c->cfg.ng, c->nldc, grad_layout)
+                      : make_layout<float>(c->cfg.npb, c->cfg.ng, c->nldc, grad_layout);
     // FP32 kernel with several passbands: headers and rows of the tile in
     // shared memory (the rows of many passbands do not stay in L1); one
-    // passband, and the FP64 kernel: headers only, rows through L1/L2
-    const bool stage_rows = !f64 && c->cfg.npb > 1;
+    // passband, the adjoint's record layout (rows 3 + nldc times larger) and
+    // the FP64 kernel: headers only, rows through L1/L2
+    const bool stage_rows = !f64 && c->cfg.npb > 1 && !grad_layout;
     const int per_pv = stage_rows ? L.head_bytes + L.rows_bytes : L.head_bytes;
     const int pv_tile = pv_tile_for(per_pv);
     const int gpc = groups_per_cta(npt);

@@ -153,9 +153,10 @@ cudaError_t launch_ld_basis(rr_ctx* c, cudaStream_t s);
 cudaError_t launch_weights(rr_ctx* c, bool need_w, cudaStream_t s);
 cudaError_t launch_pv_setup(rr_ctx* c, const double* params, int npv, const PbParams& pbp,
                             bool grad, void* records, int32_t* pv_status, cudaStream_t s);
+// grad_layout: the records were written in the adjoint's layout (rr_prepare)
 cudaError_t launch_flux(rr_ctx* c, const double* times, const int32_t* pb_index, const void* pts_dt,
                         const void* pts_pb, int npt, int npv, const PbParams& pbp, const void* records,
-                        void* flux, int32_t* pv_status, cudaStream_t s);
+                        void* flux, int32_t* pv_status, bool grad_layout, cudaStream_t s);
 cudaError_t launch_grad(rr_ctx* c, const double* times, const int32_t* pb_index, const void* pts_dt,
                         const void* pts_pb, int npt, int npv, const PbParams& pbp, const void* records,
                         const void* grad_flux, void* partials, int32_t* pv_status, cudaStream_t s);

@@ -229,9 +229,10 @@ __device__ R mean_anomaly_of_true_r(R f, R e) {
     return E - e * sE;
 }
 
-// Pvs per CTA of the set-up kernel: one lane per pv for the scalar orbit
-// set-up (all lanes of a warp busy), then the whole CTA for the rows.
-template <typename R> struct SetupPvs { static constexpr int N = sizeof(R) == sizeof(float) ? 32 : 8; };
+// Pvs per CTA of the set-up kernel: few, so that the launch has several
+// CTAs per SM and the per-pv scalar chains of many CTAs overlap; the rows
+// and windows are spread over the whole CTA.
+template <typename R> struct SetupPvs { static constexpr int N = 8; };
 
 template <typename R>
 __global__ void __launch_bounds__(256) rr_pv_setup_kernel(ModelParams mp, PbParams pbp,
@@ -246,6 +247,9 @@ __global__ void __launch_bounds__(256) rr_pv_setup_kernel(ModelParams mp, PbPara
     __shared__ R ak_s[NP][RR_MAX_PB];
     __shared__ int ik_s[NP][RR_MAX_PB];
     __shared__ int st_s[NP];
+    __shared__ int wmax_s[NP];     // largest point window over the passbands (float bits, -1 = none)
+    __shared__ int flags_s[NP];
+    __shared__ R orb_s[NP][6];     // a, b, e, f0, M0, n
     const int pv0 = blockIdx.x * NP;
     const int nloc = min(NP, npv - pv0);
     const int nkp = mp.chromatic ? mp.npb : 1;
@@ -290,13 +294,12 @@ __global__ void __launch_bounds__(256) rr_pv_setup_kernel(ModelParams mp, PbPara
     }
     __syncthreads();
 
-    // (2) per pv, one lane each: orbit constants and transit windows
+    // (2a) per pv, one thread each: orbit constants
     if (tid < nloc) {
         const int pv = pv0 + tid;
         const double* row = params + (size_t)pv * mp.nparam;
         char* rec = records + (size_t)pv * L.head_bytes;
         PvHead<R>* H = reinterpret_cast<PvHead<R>*>(rec);
-        PvPb<R>* PB = reinterpret_cast<PvPb<R>*>(rec + L.off_pb);
         const double T0 = row[0], P = row[1], ad = row[2], bd = row[3], ed = row[4], wd = row[5];
         bool finite = true;
         for (int j = 0; j < mp.nparam; ++j) finite = finite && isfinite(row[j]);
@@ -316,6 +319,8 @@ __global__ void __launch_bounds__(256) rr_pv_setup_kernel(ModelParams mp, PbPara
         H->wmax_c = 0.0f;
         H->pad3 = 0;
         H->pad4 = 0;
+        wmax_s[tid] = __float_as_int(-1.0f);
+        flags_s[tid] = 0;
         if (st == 0) {
             const R a = (R)ad, b = (R)bd, e = (R)ed, w = (R)wd;
             const R pi = Tr<R>::pi();
@@ -364,64 +369,79 @@ __global__ void __launch_bounds__(256) rr_pv_setup_kernel(ModelParams mp, PbPara
             int flags = 0;
             if (ed == 0.0) flags |= kPvCircular;
             if (ed > kESwitch) flags |= kPvKepler64;
-            R wmax = R(-1);
-            const R ra = a * (R(1) - e);
-            // conjunction anomaly wrapped to (-pi, pi] (periastron at 0)
-            R fc = f0 - R(2) * pi * floor((f0 + pi) / (R(2) * pi));
-            for (int pb = 0; pb < mp.npb; ++pb) {
-                const R k = (R)row[6 + (mp.chromatic ? pb : 0)];
-                // Transit window in true anomaly, |f - f0| <= d.  A transit needs
-                // X^2 + Y^2 < (1 + k)^2 with |X| = r |sin(f - f0)|, |Y| = r cos(f - f0) b / a
-                // (planet in front: |f - f0| < pi/2).  Start from r >= a (1 - e); then, with
-                // r_min and the smallest |Y| over the current window, |sin(f - f0)| <=
-                // sqrt((1 + k)^2 - Y_min^2) / r_min gives a window that still holds every
-                // transit point.  Safety factors absorb the rounding of R.
-                const R lim = R(1) + k;
-                const R q = lim / ra;
-                R d = q >= R(1) ? R(0.5) * pi : r_asin(q);
-                bool none = false;
-                for (int it = 0; it < 5 && !none; ++it) {
-                    const R mc = fabs(fc) <= d ? R(1) : r_max(cos(fc - d), cos(fc + d));
-                    const R rmin = a * (R(1) - e * e) / (R(1) + e * mc);
-                    const R ymin = rmin * cos(d) * (b / a) * R(1 - 4e-6);
-                    const R x2 = lim * lim * R(1 + 4e-6) - ymin * ymin;
-                    if (!(x2 > R(0))) { none = true; break; }
-                    const R sx = d_sqrt(x2) / rmin;
-                    const R dn = sx >= R(1) ? R(0.5) * pi : r_asin(sx);
-                    d = dn < d ? dn : d;
-                }
-                if (none) {            // the orbit never brings the planet over the disk
-                    PB[pb].k = k;
-                    PB[pb].inv1pk = R(1) / (R(1) + k);
-                    PB[pb].win_s = R(-1);
-                    PB[pb].win_p = R(-1);
-                    PB[pb].win_pc = -1.0f;
-                    PB[pb].pad[0] = PB[pb].pad[1] = PB[pb].pad[2] = 0.0f;
-                    continue;
-                }
-                const R df = d;
-                const R hi = wrap_2pi_r(mean_anomaly_of_true_r(f0 + df, e) - M0);
-                const R lo = wrap_2pi_r(M0 - mean_anomaly_of_true_r(f0 - df, e));
-                R win = r_max(hi, lo);
-                win += R(1e-5) * (R(1) + win);
-                const int ss = pbp.ss[pb];
-                const R half = R(0.5) * (R)pbp.exptime[pb] * (R(1) - R(1) / R(ss));
-                R winp = win + n * (ss > 1 ? half : R(0)) * R(1.000001);
-                if (win >= pi) { win = R(1e30); flags |= kPvNoWindow; }
-                if (winp >= pi) winp = R(1e30);
-                PB[pb].k = k;
-                PB[pb].inv1pk = R(1) / (R(1) + k);
-                PB[pb].win_s = win;
-                PB[pb].win_p = winp;
-                PB[pb].win_pc = (float)(winp * (R(0.5) / pi));
-                PB[pb].pad[0] = PB[pb].pad[1] = PB[pb].pad[2] = 0.0f;
-                wmax = r_max(wmax, winp * (R(0.5) / pi));
-            }
-            H->wmax_c = (float)wmax;
-            H->flags = flags;
+            flags_s[tid] = flags;
+            orb_s[tid][0] = a; orb_s[tid][1] = b; orb_s[tid][2] = e; orb_s[tid][3] = f0;
+            orb_s[tid][4] = M0; orb_s[tid][5] = n;
         }
     }
     __syncthreads();
+
+    // (2b) per (pv, passband), one thread each: transit window
+    for (int t = tid; t < nloc * mp.npb; t += blockDim.x) {
+        const int lp = t / mp.npb, pb = t % mp.npb;
+        if (st_s[lp] != 0) continue;
+        const int pv = pv0 + lp;
+        const double* row = params + (size_t)pv * mp.nparam;
+        PvPb<R>* PB = reinterpret_cast<PvPb<R>*>(records + (size_t)pv * L.head_bytes + L.off_pb);
+        const R a = orb_s[lp][0], b = orb_s[lp][1], e = orb_s[lp][2], f0 = orb_s[lp][3];
+        const R M0 = orb_s[lp][4], n = orb_s[lp][5];
+        const R pi = Tr<R>::pi();
+        const R ra = a * (R(1) - e);
+        // conjunction anomaly wrapped to (-pi, pi] (periastron at 0)
+        const R fc = f0 - R(2) * pi * floor((f0 + pi) / (R(2) * pi));
+        const R k = (R)row[6 + (mp.chromatic ? pb : 0)];
+        // Transit window in true anomaly, |f - f0| <= d.  A transit needs
+        // X^2 + Y^2 < (1 + k)^2 with |X| = r |sin(f - f0)|, |Y| = r cos(f - f0) b / a
+        // (planet in front: |f - f0| < pi/2).  Start from r >= a (1 - e); then, with
+        // r_min and the smallest |Y| over the current window, |sin(f - f0)| <=
+        // sqrt((1 + k)^2 - Y_min^2) / r_min gives a window that still holds every
+        // transit point.  Safety factors absorb the rounding of R.
+        const R lim = R(1) + k;
+        const R q = lim / ra;
+        R d = q >= R(1) ? R(0.5) * pi : r_asin(q);
+        bool none = false;
+        for (int it = 0; it < 5 && !none; ++it) {
+            const R mc = fabs(fc) <= d ? R(1) : r_max(cos(fc - d), cos(fc + d));
+            const R rmin = a * (R(1) - e * e) / (R(1) + e * mc);
+            const R ymin = rmin * cos(d) * (b / a) * R(1 - 4e-6);
+            const R x2 = lim * lim * R(1 + 4e-6) - ymin * ymin;
+            if (!(x2 > R(0))) { none = true; break; }
+            const R sx = d_sqrt(x2) / rmin;
+            const R dn = sx >= R(1) ? R(0.5) * pi : r_asin(sx);
+            d = dn < d ? dn : d;
+        }
+        PB[pb].k = k;
+        PB[pb].inv1pk = R(1) / (R(1) + k);
+        PB[pb].pad[0] = PB[pb].pad[1] = PB[pb].pad[2] = 0.0f;
+        if (none) {            // the orbit never brings the planet over the disk
+            PB[pb].win_s = R(-1);
+            PB[pb].win_p = R(-1);
+            PB[pb].win_pc = -1.0f;
+            continue;
+        }
+        const R hi = wrap_2pi_r(mean_anomaly_of_true_r(f0 + d, e) - M0);
+        const R lo = wrap_2pi_r(M0 - mean_anomaly_of_true_r(f0 - d, e));
+        R win = r_max(hi, lo);
+        win += R(1e-5) * (R(1) + win);
+        const int ss = pbp.ss[pb];
+        const R half = R(0.5) * (R)pbp.exptime[pb] * (R(1) - R(1) / R(ss));
+        R winp = win + n * (ss > 1 ? half : R(0)) * R(1.000001);
+        if (win >= pi) { win = R(1e30); atomicOr(&flags_s[lp], (int)kPvNoWindow); }
+        if (winp >= pi) winp = R(1e30);
+        PB[pb].win_s = win;
+        PB[pb].win_p = winp;
+        const float wc = (float)(winp * (R(0.5) / pi));
+        PB[pb].win_pc = wc;
+        atomicMax(&wmax_s[lp], __float_as_int(wc));   // non-negative floats order as their bits
+    }
+    __syncthreads();
+
+    // (2c) the per-pv summary of the windows
+    if (tid < nloc && st_s[tid] == 0) {
+        PvHead<R>* H = reinterpret_cast<PvHead<R>*>(records + (size_t)(pv0 + tid) * L.head_bytes);
+        H->wmax_c = __int_as_float(wmax_s[tid]);
+        H->flags = flags_s[tid];
+    }
 
     // (3) profile rows of all pvs of the CTA: the k-interpolated combination of
     // the basis projections times 1 / I_star (arithmetic in R)
@@ -430,6 +450,7 @@ __global__ void __launch_bounds__(256) rr_pv_setup_kernel(ModelParams mp, PbPara
     const R inv_dk = (R)(1.0 / mp.dk);
     const int per_pv = mp.npb * L.ng_pad;
     char* rows_region = records + rows_offset(L, npv);
+    #pragma unroll 4
     for (int t = tid; t < nloc * per_pv; t += blockDim.x) {
         const int lp = t / per_pv, rem = t % per_pv;
         const int pb = rem / L.ng_pad, ig = rem % L.ng_pad;

@@ -30,7 +30,7 @@ PV_NONFINITE, PV_LD_INVALID, PV_A_RANGE, PV_KEPLER = 16, 32, 64, 128
 EXPORTS = ["rr_create", "rr_destroy", "rr_set_ld_profile", "rr_build_weights", "rr_nparam",
            "rr_workspace_bytes", "rr_evaluate", "rr_evaluate_grad", "rr_read_table",
            "rr_sync_status", "rr_last_error", "rr_launch_count", "rr_profile", "rr_profile_read",
-           "rr_evaluate_noalloc"]
+           "rr_evaluate_noalloc", "rr_prepare", "rr_evaluate_prepared", "rr_evaluate_grad_prepared"]
 KERNELS = {"ld_basis": 0, "weights": 1, "pv_setup": 2, "flux": 3, "grad": 4, "grad_reduce": 5, "points": 6}
 
 
@@ -70,6 +70,10 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     L.rr_evaluate.argtypes = [vp, vp, vp, i32, vp, i32, ctypes.POINTER(i32), dp, vp, vp, vp, sz, vp]
     L.rr_evaluate_grad.argtypes = [vp, vp, vp, i32, vp, i32, ctypes.POINTER(i32), dp, vp, vp, vp, vp, sz, vp]
     L.rr_evaluate_noalloc.argtypes = [vp, vp, vp, i32, vp, i32, ctypes.POINTER(i32), dp, vp, vp, vp]
+    L.rr_prepare.argtypes = [vp, vp, vp, i32, vp, i32, ctypes.POINTER(i32), dp, vp, vp, sz, vp]
+    L.rr_evaluate_prepared.argtypes = [vp, vp, vp, i32, vp, i32, ctypes.POINTER(i32), dp, vp, vp, vp, sz, vp]
+    L.rr_evaluate_grad_prepared.argtypes = [vp, vp, vp, i32, vp, i32, ctypes.POINTER(i32), dp, vp, vp, vp, vp, sz,
+                                            vp]
     L.rr_read_table.argtypes = [vp, i32, dp, i64]
     L.rr_read_table.restype = i64
     L.rr_sync_status.argtypes = [vp, vp]
@@ -80,7 +84,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     L.rr_profile.argtypes = [vp, i32]
     L.rr_profile_read.argtypes = [vp, i32, dp, ctypes.POINTER(i64), i32]
     for name in ("rr_create", "rr_destroy", "rr_set_ld_profile", "rr_build_weights", "rr_evaluate",
-                 "rr_evaluate_grad", "rr_sync_status", "rr_profile", "rr_profile_read", "rr_evaluate_noalloc"):
+                 "rr_evaluate_grad", "rr_sync_status", "rr_profile", "rr_profile_read", "rr_evaluate_noalloc",
+                 "rr_prepare", "rr_evaluate_prepared", "rr_evaluate_grad_prepared"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -215,22 +220,45 @@ class Model:
             raise TypeError("pb_index must be a contiguous int32 tensor with one entry per time")
         return times.numel(), params.shape[0]
 
+    def prepare(self, times: torch.Tensor, params: torch.Tensor, pb_index: Optional[torch.Tensor] = None,
+                supersampling=None, exptime=None, pv_status: Optional[torch.Tensor] = None,
+                workspace: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+        """Shared set-up of a batch for :meth:`evaluate` and :meth:`evaluate_grad` (rr_prepare).
+
+        Returns the workspace that holds the prepared batch; pass it as
+        ``prepared=`` to both calls, with the same inputs."""
+        npt, npv = self._inputs(times, params, pb_index)
+        ss = _host_array(supersampling, self.npb, np.int32, 1)
+        ex = _host_array(exptime, self.npb, np.float64, 0.0)
+        if workspace is None:
+            workspace = self.workspace(npv, npt, True)
+        st = self.lib.rr_prepare(self._h, _ptr(times), _ptr(pb_index), npt, _ptr(params), npv,
+                                 ss.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                 ex.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), _ptr(pv_status),
+                                 _ptr(workspace), workspace.numel(), _stream_handle(stream))
+        self._check(st)
+        return workspace
+
     def evaluate(self, times: torch.Tensor, params: torch.Tensor, pb_index: Optional[torch.Tensor] = None,
                  supersampling=None, exptime=None, out: Optional[torch.Tensor] = None,
                  pv_status: Optional[torch.Tensor] = None, workspace: Optional[torch.Tensor] = None,
-                 stream=None) -> torch.Tensor:
-        """flux[npv, npt] (float32 in 'mixed', float64 in 'fp64'), enqueued on the current stream."""
+                 stream=None, prepared: Optional[torch.Tensor] = None) -> torch.Tensor:
+        """flux[npv, npt] (float32 in 'mixed', float64 in 'fp64'), enqueued on the current stream.
+
+        prepared: a workspace filled by :meth:`prepare` with the same inputs."""
         npt, npv = self._inputs(times, params, pb_index)
         ss = _host_array(supersampling, self.npb, np.int32, 1)
         ex = _host_array(exptime, self.npb, np.float64, 0.0)
         if out is None:
             out = torch.empty((npv, npt), dtype=self.dtype, device=self.device)
-        if workspace is None:
+        fn = self.lib.rr_evaluate
+        if prepared is not None:
+            fn, workspace = self.lib.rr_evaluate_prepared, prepared
+        elif workspace is None:
             workspace = self.workspace(npv, npt, False)
-        st = self.lib.rr_evaluate(self._h, _ptr(times), _ptr(pb_index), npt, _ptr(params), npv,
-                                  ss.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
-                                  ex.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), _ptr(out),
-                                  _ptr(pv_status), _ptr(workspace), workspace.numel(), _stream_handle(stream))
+        st = fn(self._h, _ptr(times), _ptr(pb_index), npt, _ptr(params), npv,
+                ss.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), ex.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                _ptr(out), _ptr(pv_status), _ptr(workspace), workspace.numel(), _stream_handle(stream))
         self._check(st)
         return out
 
@@ -253,8 +281,11 @@ class Model:
     def evaluate_grad(self, times: torch.Tensor, params: torch.Tensor, grad_flux: torch.Tensor,
                       pb_index: Optional[torch.Tensor] = None, supersampling=None, exptime=None,
                       out: Optional[torch.Tensor] = None, pv_status: Optional[torch.Tensor] = None,
-                      workspace: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
-        """grad_params[npv, nparam] = sum_t grad_flux[pv, t] d flux[pv, t] / d params[pv, :]."""
+                      workspace: Optional[torch.Tensor] = None, stream=None,
+                      prepared: Optional[torch.Tensor] = None) -> torch.Tensor:
+        """grad_params[npv, nparam] = sum_t grad_flux[pv, t] d flux[pv, t] / d params[pv, :].
+
+        prepared: a workspace filled by :meth:`prepare` with the same inputs."""
         npt, npv = self._inputs(times, params, pb_index)
         if not (grad_flux.dtype == self.dtype and grad_flux.is_contiguous() and grad_flux.shape == (npv, npt)):
             raise TypeError(f"grad_flux must be a contiguous {self.dtype} tensor of shape ({npv}, {npt})")
@@ -262,15 +293,120 @@ class Model:
         ex = _host_array(exptime, self.npb, np.float64, 0.0)
         if out is None:
             out = torch.empty((npv, self.nparam), dtype=torch.float64, device=self.device)
-        if workspace is None:
+        fn = self.lib.rr_evaluate_grad
+        if prepared is not None:
+            fn, workspace = self.lib.rr_evaluate_grad_prepared, prepared
+        elif workspace is None:
             workspace = self.workspace(npv, npt, True)
-        st = self.lib.rr_evaluate_grad(self._h, _ptr(times), _ptr(pb_index), npt, _ptr(params), npv,
-                                       ss.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
-                                       ex.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), _ptr(grad_flux),
-                                       _ptr(out), _ptr(pv_status), _ptr(workspace), workspace.numel(),
-                                       _stream_handle(stream))
+        st = fn(self._h, _ptr(times), _ptr(pb_index), npt, _ptr(params), npv,
+                ss.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), ex.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                _ptr(grad_flux), _ptr(out), _ptr(pv_status), _ptr(workspace), workspace.numel(),
+                _stream_handle(stream))
         self._check(st)
         return out
+
+    def evaluate_host(self, times, params, pb_index=None, supersampling=None, exptime=None, grad_flux=None,
+                      chunk_pvs: Optional[int] = None, out=None, grad_out=None, status_out=None):
+        """Host arrays in, host arrays out: (flux, grad_params or None, pv_status).
+
+        out / grad_out / status_out: optional pinned CPU tensors for the results.
+
+        The batch is cut into chunks of pvs; chunk c's inputs are copied to the
+        device on one stream while chunk c-1 is evaluated on a second and
+        chunk c-2's results are copied back on a third (two device buffers per
+        array), so the transfers overlap each other and the kernels.  Results
+        are bitwise those of one :meth:`evaluate` / :meth:`evaluate_grad` call
+        on the whole batch (a pv's result does not depend on the other pvs).
+        Inputs that are not in pinned memory are first copied to pinned memory.
+        """
+        def pinned(x, dt):
+            t = x if isinstance(x, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(x))
+            t = t.to(dt).contiguous()
+            return t if t.is_pinned() else t.pin_memory()
+
+        dev = self.device
+        t_h = pinned(times, torch.float64)
+        p_h = pinned(params, torch.float64)
+        pb_h = None if pb_index is None else pinned(pb_index, torch.int32)
+        g_h = None if grad_flux is None else pinned(grad_flux, self.dtype)
+        npv, npt = p_h.shape[0], t_h.numel()
+        nparam = self.nparam
+        if p_h.dim() != 2 or p_h.shape[1] != nparam:
+            raise ValueError(f"params must have shape (npv, {nparam})")
+        if g_h is not None and tuple(g_h.shape) != (npv, npt):
+            raise ValueError(f"grad_flux must have shape ({npv}, {npt})")
+        grad = g_h is not None
+        def result(buf, shape, dt):
+            if buf is None:
+                return torch.empty(shape, dtype=dt, pin_memory=True)
+            if not (buf.device.type == "cpu" and buf.dtype == dt and tuple(buf.shape) == shape
+                    and buf.is_contiguous()):
+                raise TypeError(f"result buffer must be a contiguous CPU {dt} tensor of shape {shape}")
+            return buf
+
+        f_h = result(out, (npv, npt), self.dtype)
+        go_h = result(grad_out, (npv, nparam), torch.float64) if grad else None
+        st_h = result(status_out, (npv,), torch.int32)
+        if npv == 0:
+            return f_h, go_h, st_h
+        cp = chunk_pvs or max(32, -(-npv // 8))
+        cp = min(cp, npv)
+        if not hasattr(self, "_host_streams"):
+            self._host_streams = [torch.cuda.Stream(device=dev) for _ in range(3)]
+        s_in, s_run, s_out = self._host_streams
+        nbuf = 2
+        ss = _host_array(supersampling, self.npb, np.int32, 1)
+        ex = _host_array(exptime, self.npb, np.float64, 0.0)
+        with torch.cuda.device(dev):
+            p_d = [torch.empty((cp, nparam), dtype=torch.float64, device=dev) for _ in range(nbuf)]
+            f_d = [torch.empty((cp, npt), dtype=self.dtype, device=dev) for _ in range(nbuf)]
+            st_d = [torch.empty(cp, dtype=torch.int32, device=dev) for _ in range(nbuf)]
+            ws_f = None if grad else [self.workspace(cp, npt, False) for _ in range(nbuf)]
+            if grad:
+                g_d = [torch.empty((cp, npt), dtype=self.dtype, device=dev) for _ in range(nbuf)]
+                go_d = [torch.empty((cp, nparam), dtype=torch.float64, device=dev) for _ in range(nbuf)]
+                ws_g = [self.workspace(cp, npt, True) for _ in range(nbuf)]
+            # every buffer above was made on the current stream: the copy stream starts after it
+            s_in.wait_stream(torch.cuda.current_stream(dev))
+            with torch.cuda.stream(s_in):
+                t_d = t_h.to(dev, non_blocking=True)
+                pb_d = None if pb_h is None else pb_h.to(dev, non_blocking=True)
+            free = [None] * nbuf
+            for c, c0 in enumerate(range(0, npv, cp)):
+                c1 = min(npv, c0 + cp)
+                n, b = c1 - c0, c % nbuf
+                with torch.cuda.stream(s_in):
+                    if free[b] is not None:
+                        s_in.wait_event(free[b])
+                    p_d[b][:n].copy_(p_h[c0:c1], non_blocking=True)
+                    if grad:
+                        g_d[b][:n].copy_(g_h[c0:c1], non_blocking=True)
+                    ready = torch.cuda.Event()
+                    ready.record(s_in)
+                s_run.wait_event(ready)
+                if grad:
+                    # one shared set-up for the light curves and the adjoint of the chunk
+                    self.prepare(t_d, p_d[b][:n], pb_d, ss, ex, pv_status=st_d[b][:n], workspace=ws_g[b],
+                                 stream=s_run)
+                    self.evaluate(t_d, p_d[b][:n], pb_d, ss, ex, out=f_d[b][:n], pv_status=st_d[b][:n],
+                                  stream=s_run, prepared=ws_g[b])
+                    self.evaluate_grad(t_d, p_d[b][:n], g_d[b][:n], pb_d, ss, ex, out=go_d[b][:n],
+                                       stream=s_run, prepared=ws_g[b])
+                else:
+                    self.evaluate(t_d, p_d[b][:n], pb_d, ss, ex, out=f_d[b][:n], pv_status=st_d[b][:n],
+                                  workspace=ws_f[b], stream=s_run)
+                done = torch.cuda.Event()
+                done.record(s_run)
+                s_out.wait_event(done)
+                with torch.cuda.stream(s_out):
+                    f_h[c0:c1].copy_(f_d[b][:n], non_blocking=True)
+                    st_h[c0:c1].copy_(st_d[b][:n], non_blocking=True)
+                    if grad:
+                        go_h[c0:c1].copy_(go_d[b][:n], non_blocking=True)
+                    free[b] = torch.cuda.Event()
+                    free[b].record(s_out)
+            s_out.synchronize()
+        return f_h, go_h, st_h
 
     def flux(self, times, params, pb_index=None, supersampling=None, exptime=None) -> torch.Tensor:
         """Differentiable light curves (gradient w.r.t. ``params`` through the adjoint kernel)."""
@@ -282,15 +418,19 @@ class _RRFlux(torch.autograd.Function):
     def forward(ctx, model: Model, times, pb_index, params, supersampling, exptime):
         ctx.model = model
         ctx.meta = (supersampling, exptime)
-        ctx.save_for_backward(times, pb_index, params)
-        return model.evaluate(times, params.detach(), pb_index, supersampling, exptime)
+        p = params.detach()
+        ctx.save_for_backward(times, pb_index, p)
+        # one set-up for the forward and the backward pass, when a gradient is wanted
+        ctx.prepared = model.prepare(times, p, pb_index, supersampling, exptime) if params.requires_grad else None
+        return model.evaluate(times, p, pb_index, supersampling, exptime, prepared=ctx.prepared)
 
     @staticmethod
     def backward(ctx, gflux):
         times, pb_index, params = ctx.saved_tensors
         ss, ex = ctx.meta
-        g = ctx.model.evaluate_grad(times, params.detach(), gflux.contiguous().to(ctx.model.dtype),
-                                    pb_index, ss, ex)
+        g = ctx.model.evaluate_grad(times, params, gflux.contiguous().to(ctx.model.dtype), pb_index, ss, ex,
+                                    prepared=ctx.prepared)
+        ctx.prepared = None
         return None, None, None, g.to(params.dtype), None, None
 
 

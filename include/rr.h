@@ -230,6 +230,34 @@ rr_status rr_evaluate_grad_prepared(rr_ctx* ctx, const double* times, const int3
                                     const void* grad_flux, double* grad_params, int32_t* pv_status,
                                     const void* workspace, size_t workspace_bytes, void* stream);
 
+/* Evaluate host-resident batches: host arrays in, host arrays out.  Light
+ * curves (Eq. 5 with the supersampling of Sect. 4.1) and, when grad_flux is
+ * given, the adjoint of rr_evaluate_grad, for data that live in host memory.
+ * The paper has no counterpart (its models take and return host arrays, with
+ * the GPU model copying them whole).  The batch is cut into chunks of
+ * chunk_pvs parameter vectors (0: npv / 8, at least 512); the copies of
+ * chunk c to the device, the kernels of chunk c-1 and the copies of chunk
+ * c-2 back to the host run on three streams of the context, so they overlap.
+ *   times, pb_index, params, supersampling, exptime   host, as rr_evaluate
+ *   grad_flux    host, [npv][npt] float (MIXED) / double (FP64), or NULL
+ *                (no adjoint; grad_params is then not written)
+ *   flux         host, [npv][npt] float (MIXED) / double (FP64), written
+ *   grad_params  host, double[npv][nparam], written when grad_flux != NULL
+ *   pv_status    host, int32[npv], or NULL
+ * Host arrays should be page-locked (cudaHostAlloc / cudaHostRegister):
+ * copies from pageable memory are staged by the driver and do not overlap.
+ * The call is synchronous: it returns when every result is in host memory.
+ * The context keeps one device buffer for the chunks (grown when a call
+ * needs more, freed by rr_destroy) and three streams; calls on one context
+ * must not overlap in time (as for every entry point).  Results are bitwise
+ * those of rr_evaluate / rr_evaluate_grad on the whole batch.
+ * Errors: as rr_evaluate, plus RR_ECUDA for a failed copy or allocation and
+ * RR_ETIMEOUT as reported by rr_sync_status. */
+rr_status rr_evaluate_host(rr_ctx* ctx, const double* times, const int32_t* pb_index, int32_t npt,
+                           const double* params, int32_t npv, const int32_t* supersampling,
+                           const double* exptime, const void* grad_flux, void* flux, double* grad_params,
+                           int32_t* pv_status, int32_t chunk_pvs);
+
 /* Copy a set-up table to host memory (for inspection and tests); returns the
  * element count of the table, or -1 on error.  `out` may be NULL to query
  * the size; otherwise it receives min(count, capacity) doubles.

@@ -59,6 +59,7 @@ cudaError_t dalloc(T** p, size_t n) {
 }
 
 void free_all(rr_ctx* c) {
+    release_host_pipe(c);
     for (auto& t : c->timed) { cudaEventDestroy(t.a); cudaEventDestroy(t.b); }
     for (auto e : c->ev_pool) cudaEventDestroy(e);
     c->timed.clear();

@@ -26,6 +26,11 @@ __device__ __forceinline__ void d_sincos(float x, float* s, float* c) { sincosf(
 __device__ __forceinline__ void d_sincos(double x, double* s, double* c) { sincos(x, s, c); }
 __device__ __forceinline__ float d_rint(float x) { return rintf(x); }
 __device__ __forceinline__ double d_rint(double x) { return rint(x); }
+// Reciprocal: correctly rounded single-instruction-sequence form in FP32 (the
+// FP32 adjoint's tolerance is far above its one-ulp difference from a true
+// division), an exact IEEE division in FP64.
+__device__ __forceinline__ float d_rcp(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double d_rcp(double x) { return 1.0 / x; }
 
 // Area covered by a planet of radius k at centre distance z on a unit stellar
 // disk (the a(c, k) of Eq. 5), for z < 1 + k, with its partial derivatives.
@@ -56,7 +61,7 @@ __device__ __forceinline__ R covered_area(R k, R z, R& dAdz, R& dAdk) {
     const R kap0 = d_atan2(K, zz + (one - kk));
     const R kap1 = d_atan2(K, zz + (kk - one));
     if (GRAD) {
-        dAdz = -K / z;
+        dAdz = -K * d_rcp(z);
         dAdk = R(2) * k * kap1;
     }
     return kap0 + kk * kap1 - R(0.5) * K;
@@ -78,50 +83,51 @@ __device__ __forceinline__ R lerp_row(const R* row, int ng, R g, R& slope_cell, 
     return l0 + al * (l1 - l0);
 }
 
-// sin(y) and cos(y) for |y| <= 0.5 from their Taylor series (terms through
-// y^9 and y^10; truncation below 3e-10, far under FP32 rounding).
-__device__ __forceinline__ void sincos_small(float y, float& s, float& c) {
-    const float y2 = y * y;
-    float ps = fmaf(y2, 2.7557319e-6f, -1.9841270e-4f);   // 1/9!, -1/7!
-    ps = fmaf(y2, ps, 8.3333333e-3f);                      // 1/5!
-    ps = fmaf(y2, ps, -1.6666667e-1f);                     // -1/3!
-    s = fmaf(y * y2, ps, y);
-    float pc = fmaf(y2, -2.7557319e-7f, 2.4801587e-5f);    // -1/10!, 1/8!
-    pc = fmaf(y2, pc, -1.3888889e-3f);                     // -1/6!
-    pc = fmaf(y2, pc, 4.1666668e-2f);                      // 1/4!
-    pc = fmaf(y2, pc, -0.5f);                              // -1/2!
-    c = fmaf(y2, pc, 1.0f);
-}
-
-// S = sin x, V = 1 - cos x from the half angle (no cancellation in V).
+// S = sin x and V = 1 - cos x for |x| <= 1 from their Taylor series in x^2
+// (through x^9 and x^10: truncation below 3e-8 of S and 5e-9 of V), V
+// without cancellation; larger |x| from the half angle.
 __device__ __forceinline__ void half_angle_SV(float x, float& S, float& V) {
-    float hs, hc;
-    const float y = 0.5f * x;
-    if (fabsf(y) <= 0.5f) sincos_small(y, hs, hc);
-    else sincosf(y, &hs, &hc);
-    S = 2.0f * hs * hc;
-    V = 2.0f * hs * hs;
+    if (fabsf(x) <= 1.0f) {
+        const float x2 = x * x;
+        float ps = fmaf(x2, 2.7557319e-6f, -1.9841270e-4f);    // 1/9!, -1/7!
+        ps = fmaf(x2, ps, 8.3333333e-3f);                       // 1/5!
+        ps = fmaf(x2, ps, -1.6666667e-1f);                      // -1/3!
+        S = fmaf(x * x2, ps, x);
+        float pv = fmaf(x2, 2.7557319e-7f, -2.4801587e-5f);    // 1/10!, -1/8!
+        pv = fmaf(x2, pv, 1.3888889e-3f);                       // 1/6!
+        pv = fmaf(x2, pv, -4.1666668e-2f);                      // -1/4!
+        pv = fmaf(x2, pv, 0.5f);                                // 1/2!
+        V = x2 * pv;
+    } else {
+        float hs, hc;
+        sincosf(0.5f * x, &hs, &hc);
+        S = 2.0f * hs * hc;
+        V = 2.0f * hs * hs;
+    }
 }
 
 // Offset-form Kepler solve in FP32 for x = E - E0 given dM = M - M0
 // (Newton, f(x) = x - ecE0 sin x + esE0 (1 - cos x) - dM, f' = 1 - e cos E).
+// Start: the series inversion through third order (kep2, kep3 per pv).  A
+// Newton step dx leaves an error of at most kepC dx^2 (kepC >= |f''/(2 f')|),
+// so the loop stops once that is below FP32 resolution of x; S and V follow x
+// by a first-order rotation, whose error dx^2 / 2 is below the same bound.
 // On return S = sin x, V = 1 - cos x.  Returns false if not converged.
-__device__ __forceinline__ bool kepler_offset_f32(float dM, float ecE0, float esE0, float inv_den0,
-                                                  float& x, float& S, float& V) {
-    // second-order start: x (1 - e cos E0) + e sin E0 x^2 / 2 = dM
-    const float x1 = dM * inv_den0;
-    x = x1 - 0.5f * esE0 * x1 * x1 * inv_den0;
+__device__ __forceinline__ bool kepler_offset_f32(float dM, float ecE0, float esE0, float inv_den0, float kep2,
+                                                  float kep3, float kepC, float& x, float& S, float& V) {
+    const float y = dM * inv_den0;
+    x = fmaf(fmaf(kep3, y, kep2), y * y, y);
     #pragma unroll 1
     for (int it = 0; it < 24; ++it) {
         half_angle_SV(x, S, V);
         const float fx = (x - dM) - ecE0 * S + esE0 * V;
         const float fp = (1.0f - ecE0) + ecE0 * V + esE0 * S;
-        const float dx = __fdividef(fx, fp);   // the next iteration corrects a rounded step
+        const float dx = __fdividef(fx, fp);
         x -= dx;
         const float S_old = S;
         S -= dx * (1.0f - V);
         V -= dx * S_old;
-        if (fabsf(dx) <= 2e-6f * fabsf(x) + 1e-30f) return true;
+        if (kepC * dx * dx <= 1.5e-8f * fabsf(x) + 1e-37f) return true;
     }
     return false;
 }
@@ -275,7 +281,7 @@ __device__ __forceinline__ Orbit32 orbit32(const PvHead<float>& H, float dM, dou
         o.S = (float)Sd;
         o.V = (float)Vd;
     } else {
-        o.ok = kepler_offset_f32(dM, H.ecE0, H.esE0, H.inv_den0, x, o.S, o.V);
+        o.ok = kepler_offset_f32(dM, H.ecE0, H.esE0, H.inv_den0, H.kep2, H.kep3, H.kepC, x, o.S, o.V);
     }
     o.Px = fmaf(H.ax1, o.V, H.ax2 * o.S);
     o.Py = H.rho0 + fmaf(H.ay1, o.V, H.ay2 * o.S);

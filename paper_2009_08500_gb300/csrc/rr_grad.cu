@@ -68,13 +68,13 @@ __device__ __forceinline__ void grad_sample(const PvHead<R>& H, const PvPb<R>& p
     const R dden = H.ecE0 * V + H.esE0 * S;
     const R den0 = one - H.ecE0;
     const R den = den0 + dden;
-    const R invden = one / den;
+    const R invden = d_rcp(den);
     const R dsinE = H.cE0 * S - H.sE0 * V;
     const R sinE = H.sE0 + dsinE;
     const R cosE = H.cE0 * omV - H.sE0 * S;
     const R dPxdE = H.ax1 * S + H.ax2 * omV;
     const R dPydE = H.ay1 * S + H.ay2 * omV;
-    const R invz = one / z;
+    const R invz = d_rcp(z);
     const R zE = (H.a2 * Px * dPxdE + H.b2 * Py * dPydE) * invz;
     const R inv_se = H.inv_se;
     const R ce = -(H.dM0de + H.sE0);                    // den0 sE0 / (1 - e^2)
@@ -435,39 +435,52 @@ __global__ void __launch_bounds__(kBlock) rr_grad_fp64_kernel(
 
 // Sum the partial sums of each pv over its chunks in chunk order (FP64),
 // one lane per (pv, parameter).  Invalid pvs get NaN rows.
-template <typename R>
-__global__ void rr_grad_reduce_kernel(const R* __restrict__ partials, int nchunks, int nacc, int npv,
-                                      const char* __restrict__ heads, int head_bytes, double* __restrict__ grad) {
-    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (long long)npv * nacc) return;
-    const int pv = (int)(idx / nacc), j = (int)(idx % nacc);
-    const PvHead<R>& H = *reinterpret_cast<const PvHead<R>*>(heads + (size_t)pv * head_bytes);
-    double s = 0.0;
-    const R* pp = partials + (size_t)pv * nchunks * nacc + j;
-    for (int t = 0; t < nchunks; ++t) s += (double)pp[(size_t)t * nacc];
-    grad[(size_t)pv * nacc + j] = H.status != 0 ? __longlong_as_double(0x7ff8000000000000ll) : s;
-}
+// grad[pv][j] = sum over the pv's partial-sum chunks (chunk order, FP64); then,
+// for the (q1, q2) parametrisation, the chain rule through u1 = 2 sqrt(q1) q2,
+// u2 = sqrt(q1) (1 - 2 q2).  A block takes kFinishPvs pvs: one thread per
+// (pv, parameter) for the sums, then one per (pv, passband) for the chain rule.
+constexpr int kFinishThreads = 256;
 
-// Kipping's parametrisation: map d/du1, d/du2 to d/dq1, d/dq2 with
-// u1 = 2 sqrt(q1) q2, u2 = sqrt(q1) (1 - 2 q2):
-//   d/dq1 = d/du1 q2 / sqrt(q1) + d/du2 (1 - 2 q2) / (2 sqrt(q1))
-//   d/dq2 = d/du1 2 sqrt(q1) - d/du2 2 sqrt(q1)
-// One lane per pv.
 template <typename R>
-__global__ void rr_grad_kipping_kernel(double* __restrict__ grad, const double* __restrict__ params, int nparam,
-                                       int npv, int npb, int nkp, const char* __restrict__ heads, int head_bytes) {
-    const int pv = blockIdx.x * blockDim.x + threadIdx.x;
-    if (pv >= npv) return;
-    if (reinterpret_cast<const PvHead<R>*>(heads + (size_t)pv * head_bytes)->status != 0) return;
-    const double* row = params + (size_t)pv * nparam;
-    double* out = grad + (size_t)pv * nparam;
-    for (int pb = 0; pb < npb; ++pb) {
+__global__ void __launch_bounds__(kFinishThreads) rr_grad_finish_kernel(
+    const R* __restrict__ partials, int nchunks, int nacc, int npv, int pvs_per_block,
+    const char* __restrict__ heads, int head_bytes, const double* __restrict__ params, int kipping, int npb, int nkp,
+    double* __restrict__ grad) {
+    extern __shared__ double sg[];                 // [pvs_per_block][nacc]
+    const int pv0 = blockIdx.x * pvs_per_block;
+    const int nloc = min(pvs_per_block, npv - pv0);
+    for (int t = threadIdx.x; t < nloc * nacc; t += blockDim.x) {
+        const int lp = t / nacc, j = t - lp * nacc;
+        const R* pp = partials + (size_t)(pv0 + lp) * nchunks * nacc + j;
+        double s = 0.0;
+        int c = 0;
+        for (; c + 4 <= nchunks; c += 4) {
+            const R v0 = pp[(size_t)c * nacc], v1 = pp[(size_t)(c + 1) * nacc];
+            const R v2 = pp[(size_t)(c + 2) * nacc], v3 = pp[(size_t)(c + 3) * nacc];
+            s += (double)v0;
+            s += (double)v1;
+            s += (double)v2;
+            s += (double)v3;
+        }
+        for (; c < nchunks; ++c) s += (double)pp[(size_t)c * nacc];
+        const bool bad = reinterpret_cast<const PvHead<R>*>(heads + (size_t)(pv0 + lp) * head_bytes)->status != 0;
+        s = bad ? __longlong_as_double(0x7ff8000000000000ll) : s;
+        sg[t] = s;
+        grad[(size_t)(pv0 + lp) * nacc + j] = s;
+    }
+    if (!kipping) return;                          // block-uniform
+    __syncthreads();
+    for (int t = threadIdx.x; t < nloc * npb; t += blockDim.x) {
+        const int lp = t / npb, pb = t - lp * npb;
         const int o = 6 + nkp + 2 * pb;
-        const double q1 = row[o], q2 = row[o + 1];
-        const double sq = sqrt(q1);
-        const double g1 = out[o], g2 = out[o + 1];
-        out[o] = g1 * q2 / sq + g2 * (1.0 - 2.0 * q2) / (2.0 * sq);
-        out[o + 1] = g1 * 2.0 * sq - g2 * 2.0 * sq;
+        const double* row = params + (size_t)(pv0 + lp) * nacc;
+        const double g1 = sg[lp * nacc + o], g2 = sg[lp * nacc + o + 1];
+        if (g1 != g1) continue;                    // invalid pv: NaN row stays
+        const double sq = sqrt(row[o]), q2 = row[o + 1];
+        const double isq = 1.0 / sq;
+        double* out = grad + (size_t)(pv0 + lp) * nacc;
+        out[o] = g1 * q2 * isq + g2 * (1.0 - 2.0 * q2) * (0.5 * isq);
+        out[o + 1] = 2.0 * sq * (g1 - g2);
     }
 }
 
@@ -562,24 +575,18 @@ cudaError_t launch_grad_reduce(rr_ctx* c, int npt, const double* params, int npv
     const int nacc = c->nparam;
     const int nchunks = grad_chunks(c, npt);
     const int nkp = c->cfg.chromatic ? c->cfg.npb : 1;
-    const long long n = (long long)npv * nacc;
-    const unsigned blocks = (unsigned)((n + 255) / 256);
+    const int kip = c->cfg.ld_model == RR_LD_QUADRATIC_TRI ? 1 : 0;
+    const int per_block = kFinishThreads / nacc > 0 ? kFinishThreads / nacc : 1;
+    const unsigned blocks = (unsigned)((npv + per_block - 1) / per_block);
+    const size_t smem = (size_t)per_block * nacc * sizeof(double);
     if (f64)
-        rr_grad_reduce_kernel<double><<<blocks, 256, 0, s>>>((const double*)partials, nchunks, nacc, npv,
-                                                             (const char*)records, L.head_bytes, grad_params);
+        rr_grad_finish_kernel<double><<<blocks, kFinishThreads, smem, s>>>(
+            (const double*)partials, nchunks, nacc, npv, per_block, (const char*)records, L.head_bytes, params, kip,
+            c->cfg.npb, nkp, grad_params);
     else
-        rr_grad_reduce_kernel<float><<<blocks, 256, 0, s>>>((const float*)partials, nchunks, nacc, npv,
-                                                            (const char*)records, L.head_bytes, grad_params);
-    c->launches++;
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess || c->cfg.ld_model != RR_LD_QUADRATIC_TRI) return e;
-    const unsigned b2 = (unsigned)((npv + 127) / 128);
-    if (f64)
-        rr_grad_kipping_kernel<double><<<b2, 128, 0, s>>>(grad_params, params, c->nparam, npv, c->cfg.npb, nkp,
-                                                          (const char*)records, L.head_bytes);
-    else
-        rr_grad_kipping_kernel<float><<<b2, 128, 0, s>>>(grad_params, params, c->nparam, npv, c->cfg.npb, nkp,
-                                                         (const char*)records, L.head_bytes);
+        rr_grad_finish_kernel<float><<<blocks, kFinishThreads, smem, s>>>(
+            (const float*)partials, nchunks, nacc, npv, per_block, (const char*)records, L.head_bytes, params, kip,
+            c->cfg.npb, nkp, grad_params);
     c->launches++;
     return cudaGetLastError();
 }

@@ -49,7 +49,8 @@ struct alignas(16) PvHead {
     double T0, P, invP;            // FP64 epoch and period (phase reduction)
     double ecE0d, esE0d, inv_den0d;  // FP64 Kepler constants (e > kESwitch fallback)
     float wmax_c;                  // largest point window over the passbands, cycles
-    float padf[3];
+    float kep2, kep3;              // FP32 Kepler start: x = y + kep2 y^2 + kep3 y^3, y = dM / (1 - e cos E0)
+    float kepC;                    // bound of |f'' / (2 f')| of the offset Kepler function (convergence test)
     R a, b, a2, b2;
     R e, ecE0, esE0, inv_den0;     // inv_den0 = 1 / (1 - e cos E0)
     R ax1, ax2, ay1, ay2;
@@ -145,6 +146,14 @@ struct rr_ctx {
     std::vector<Timed> timed;
     double prof_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     long long prof_n[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    // host-buffer pipeline (rr_evaluate_host): copy-in, compute and copy-out
+    // streams, per-slot events, one grow-only device buffer
+    struct HostPipe {
+        cudaStream_t s[3] = {nullptr, nullptr, nullptr};
+        cudaEvent_t ev[3][3] = {};   // [slot][inputs copied, computed, results copied]
+        void* buf = nullptr;
+        size_t bytes = 0;
+    } pipe;
 };
 
 namespace rr {
@@ -173,5 +182,6 @@ cudaError_t launch_points(rr_ctx* c, const double* times, const int32_t* pb_inde
                           void* ws_pb, cudaStream_t s);
 ModelParams model_params(const rr_ctx* c);
 int pv_tile_for(int rec_bytes);
+void release_host_pipe(rr_ctx* c);
 int groups_per_cta(int npt);
 }  // namespace rr

@@ -356,7 +356,14 @@ __global__ void __launch_bounds__(256) rr_pv_setup_kernel(ModelParams mp, PbPara
             } else {
                 H->ecE0d = (double)(e * cE0); H->esE0d = (double)(e * sE0); H->inv_den0d = (double)(R(1) / den0);
             }
-            H->padf[0] = H->padf[1] = H->padf[2] = 0.0f;
+            {
+                // third-order inversion of d0 x + (e sin E0 / 2) x^2 + (e cos E0 / 6) x^3 = dM
+                const float sy = (float)(e * sE0 / den0), cy = (float)(e * cE0 / den0);
+                H->kep2 = -0.5f * sy;
+                H->kep3 = 0.5f * sy * sy - cy * (1.0f / 6.0f);
+                const float ef = (float)e;
+                H->kepC = fmaxf(0.5f * ef / (1.0f - fminf(ef, 0.999f)), 0.5f);
+            }
             H->a = a; H->b = b; H->a2 = a * a; H->b2 = b * b;
             H->e = e; H->ecE0 = e * cE0; H->esE0 = e * sE0; H->inv_den0 = R(1) / den0;
             H->ax1 = ax1; H->ax2 = ax2; H->ay1 = ay1; H->ay2 = ay2;
@@ -448,68 +455,70 @@ __global__ void __launch_bounds__(256) rr_pv_setup_kernel(ModelParams mp, PbPara
     const size_t kstride = (size_t)mp.ng;
     const size_t bstride = (size_t)mp.nk * mp.ng;
     const R inv_dk = (R)(1.0 / mp.dk);
-    const int per_pv = mp.npb * L.ng_pad;
     char* rows_region = records + rows_offset(L, npv);
-    #pragma unroll 4
-    for (int t = tid; t < nloc * per_pv; t += blockDim.x) {
-        const int lp = t / per_pv, rem = t % per_pv;
-        const int pb = rem / L.ng_pad, ig = rem % L.ng_pad;
+    const bool named = mp.ld_model != RR_LD_TABULATED;
+    const int nc = named ? mp.nldc : 0;
+    // one (pv, passband) row block per warp at a time; lanes walk the g nodes
+    const int lane = tid & 31, nwarps = blockDim.x >> 5;
+    for (int rw = tid >> 5; rw < nloc * mp.npb; rw += nwarps) {
+        const int lp = rw / mp.npb, pb = rw - lp * mp.npb;
         if (st_s[lp] != 0) continue;
         R* r0 = reinterpret_cast<R*>(rows_region + (size_t)(pv0 + lp) * L.rows_bytes) +
                 (size_t)pb * L.rows_per_pb * L.ng_pad;
-        if (ig >= mp.ng) {
-            for (int r = 0; r < L.rows_per_pb; ++r) r0[(size_t)r * L.ng_pad + ig] = (R)0;
-            continue;
-        }
         const int ik = ik_s[lp][pb];
-        const R ak = ak_s[lp][pb];
+        const R ak = ak_s[lp][pb], bk = R(1) - ak;
         const R invIs = invIs_s[lp][pb];
-        const int b0 = mp.ld_model == RR_LD_TABULATED ? pb : 0;
-        const R* T0p = T + (size_t)b0 * bstride + (size_t)ik * kstride + ig;
-        R lo = T0p[0], hi = T0p[kstride];
-        if (mp.ld_model != RR_LD_TABULATED) {
-            for (int c = 0; c < mp.nldc; ++c) {
-                const R* Tc = T + (size_t)(1 + c) * bstride + (size_t)ik * kstride + ig;
-                const R uc = u_s[lp][pb][c];
-                lo += uc * Tc[0];
-                hi += uc * Tc[kstride];
+        R uc[4];
+        #pragma unroll
+        for (int c = 0; c < 4; ++c) uc[c] = c < nc ? u_s[lp][pb][c] : R(0);
+        const int b0 = named ? 0 : pb;
+        const R* T0p = T + (size_t)b0 * bstride + (size_t)ik * kstride;
+        const float* D0p = DT + (size_t)b0 * bstride + (size_t)ik * kstride;
+        for (int ig = lane; ig < L.ng_pad; ig += 32) {
+            if (ig >= mp.ng) {
+                for (int r = 0; r < L.rows_per_pb; ++r) r0[(size_t)r * L.ng_pad + ig] = (R)0;
+                continue;
             }
-        }
-        const R ldw_n = ((R(1) - ak) * lo + ak * hi) * invIs;
-        r0[ig] = ldw_n;
-        if (grad) {
+            R lo = T0p[ig], hi = T0p[kstride + ig];
+            #pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                if (c < nc) {
+                    const R* Tc = T0p + (size_t)(1 + c) * bstride;
+                    lo += uc[c] * Tc[ig];
+                    hi += uc[c] * Tc[kstride + ig];
+                }
+            }
+            const R ldw_n = (bk * lo + ak * hi) * invIs;
+            r0[ig] = ldw_n;
+            if (!grad) continue;
             // row 1: ldw_n[ig+1] - ldw_n[ig], from differences that keep full relative precision
             R dlo = 0, dhi = 0;
             if (ig < mp.ng - 1) {
-                if (sizeof(R) == sizeof(double)) {
-                    dlo = T0p[1] - T0p[0];
-                    dhi = T0p[kstride + 1] - T0p[kstride];
-                } else {
-                    const float* D0 = DT + (size_t)b0 * bstride + (size_t)ik * kstride + ig;
-                    dlo = (R)D0[0];
-                    dhi = (R)D0[kstride];
-                }
-                if (mp.ld_model != RR_LD_TABULATED) {
-                    for (int c = 0; c < mp.nldc; ++c) {
-                        const R uc = u_s[lp][pb][c];
+                #pragma unroll
+                for (int c = 0; c < 5; ++c) {
+                    if (c == 0 || c <= nc) {
+                        const R w = c == 0 ? R(1) : uc[c - 1];
                         if (sizeof(R) == sizeof(double)) {
-                            const R* Tc = T + (size_t)(1 + c) * bstride + (size_t)ik * kstride + ig;
-                            dlo += uc * (Tc[1] - Tc[0]);
-                            dhi += uc * (Tc[kstride + 1] - Tc[kstride]);
+                            const R* Tc = T0p + (size_t)c * bstride;
+                            dlo += w * (Tc[ig + 1] - Tc[ig]);
+                            dhi += w * (Tc[kstride + ig + 1] - Tc[kstride + ig]);
                         } else {
-                            const float* Dc = DT + (size_t)(1 + c) * bstride + (size_t)ik * kstride + ig;
-                            dlo += uc * (R)Dc[0];
-                            dhi += uc * (R)Dc[kstride];
+                            const float* Dc = D0p + (size_t)c * bstride;
+                            dlo += w * (R)Dc[ig];
+                            dhi += w * (R)Dc[kstride + ig];
                         }
                     }
                 }
             }
-            r0[L.ng_pad + ig] = ((R(1) - ak) * dlo + ak * dhi) * invIs;
+            r0[L.ng_pad + ig] = (bk * dlo + ak * dhi) * invIs;
             r0[2 * L.ng_pad + ig] = (hi - lo) * (inv_dk * invIs);
-            for (int c = 0; c < mp.nldc; ++c) {
-                const R* Tc = T + (size_t)(1 + c) * bstride + (size_t)ik * kstride + ig;
-                const R Rc = (R(1) - ak) * Tc[0] + ak * Tc[kstride];
-                r0[(size_t)(3 + c) * L.ng_pad + ig] = (Rc - ldw_n * (R)istar[1 + c]) * invIs;
+            #pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                if (c < nc) {
+                    const R* Tc = T0p + (size_t)(1 + c) * bstride;
+                    const R Rc = bk * Tc[ig] + ak * Tc[kstride + ig];
+                    r0[(size_t)(3 + c) * L.ng_pad + ig] = (Rc - ldw_n * (R)istar[1 + c]) * invIs;
+                }
             }
         }
     }

@@ -30,7 +30,8 @@ PV_NONFINITE, PV_LD_INVALID, PV_A_RANGE, PV_KEPLER = 16, 32, 64, 128
 EXPORTS = ["rr_create", "rr_destroy", "rr_set_ld_profile", "rr_build_weights", "rr_nparam",
            "rr_workspace_bytes", "rr_evaluate", "rr_evaluate_grad", "rr_read_table",
            "rr_sync_status", "rr_last_error", "rr_launch_count", "rr_profile", "rr_profile_read",
-           "rr_evaluate_noalloc", "rr_prepare", "rr_evaluate_prepared", "rr_evaluate_grad_prepared"]
+           "rr_evaluate_noalloc", "rr_prepare", "rr_evaluate_prepared", "rr_evaluate_grad_prepared",
+           "rr_evaluate_host"]
 KERNELS = {"ld_basis": 0, "weights": 1, "pv_setup": 2, "flux": 3, "grad": 4, "grad_reduce": 5, "points": 6}
 
 
@@ -74,6 +75,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     L.rr_evaluate_prepared.argtypes = [vp, vp, vp, i32, vp, i32, ctypes.POINTER(i32), dp, vp, vp, vp, sz, vp]
     L.rr_evaluate_grad_prepared.argtypes = [vp, vp, vp, i32, vp, i32, ctypes.POINTER(i32), dp, vp, vp, vp, vp, sz,
                                             vp]
+    L.rr_evaluate_host.argtypes = [vp, vp, vp, i32, vp, i32, ctypes.POINTER(i32), dp, vp, vp, vp, vp, i32]
     L.rr_read_table.argtypes = [vp, i32, dp, i64]
     L.rr_read_table.restype = i64
     L.rr_sync_status.argtypes = [vp, vp]
@@ -85,7 +87,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     L.rr_profile_read.argtypes = [vp, i32, dp, ctypes.POINTER(i64), i32]
     for name in ("rr_create", "rr_destroy", "rr_set_ld_profile", "rr_build_weights", "rr_evaluate",
                  "rr_evaluate_grad", "rr_sync_status", "rr_profile", "rr_profile_read", "rr_evaluate_noalloc",
-                 "rr_prepare", "rr_evaluate_prepared", "rr_evaluate_grad_prepared"):
+                 "rr_prepare", "rr_evaluate_prepared", "rr_evaluate_grad_prepared", "rr_evaluate_host"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -307,35 +309,20 @@ class Model:
 
     def evaluate_host(self, times, params, pb_index=None, supersampling=None, exptime=None, grad_flux=None,
                       chunk_pvs: Optional[int] = None, out=None, grad_out=None, status_out=None):
-        """Host arrays in, host arrays out: (flux, grad_params or None, pv_status).
+        """Host arrays in, host arrays out: (flux, grad_params or None, pv_status) (rr_evaluate_host).
 
-        out / grad_out / status_out: optional pinned CPU tensors for the results.
-
-        The batch is cut into chunks of pvs; chunk c's inputs are copied to the
-        device on one stream while chunk c-1 is evaluated on a second and
-        chunk c-2's results are copied back on a third (two device buffers per
-        array), so the transfers overlap each other and the kernels.  Results
-        are bitwise those of one :meth:`evaluate` / :meth:`evaluate_grad` call
-        on the whole batch (a pv's result does not depend on the other pvs).
-        Inputs that are not in pinned memory are first copied to pinned memory.
+        The library cuts the batch into chunks of pvs and overlaps the copies
+        to the device, the kernels and the copies back on three streams.
+        Results are bitwise those of one :meth:`evaluate` / :meth:`evaluate_grad`
+        call on the whole batch.  Inputs not in pinned memory are first copied
+        to pinned memory; out / grad_out / status_out are optional pinned CPU
+        tensors for the results.
         """
         def pinned(x, dt):
             t = x if isinstance(x, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(x))
             t = t.to(dt).contiguous()
             return t if t.is_pinned() else t.pin_memory()
 
-        dev = self.device
-        t_h = pinned(times, torch.float64)
-        p_h = pinned(params, torch.float64)
-        pb_h = None if pb_index is None else pinned(pb_index, torch.int32)
-        g_h = None if grad_flux is None else pinned(grad_flux, self.dtype)
-        npv, npt = p_h.shape[0], t_h.numel()
-        nparam = self.nparam
-        if p_h.dim() != 2 or p_h.shape[1] != nparam:
-            raise ValueError(f"params must have shape (npv, {nparam})")
-        if g_h is not None and tuple(g_h.shape) != (npv, npt):
-            raise ValueError(f"grad_flux must have shape ({npv}, {npt})")
-        grad = g_h is not None
         def result(buf, shape, dt):
             if buf is None:
                 return torch.empty(shape, dtype=dt, pin_memory=True)
@@ -344,68 +331,29 @@ class Model:
                 raise TypeError(f"result buffer must be a contiguous CPU {dt} tensor of shape {shape}")
             return buf
 
+        t_h = pinned(times, torch.float64)
+        p_h = pinned(params, torch.float64)
+        pb_h = None if pb_index is None else pinned(pb_index, torch.int32)
+        g_h = None if grad_flux is None else pinned(grad_flux, self.dtype)
+        nparam = self.nparam
+        if p_h.dim() != 2 or p_h.shape[1] != nparam:
+            raise ValueError(f"params must have shape (npv, {nparam})")
+        npv, npt = p_h.shape[0], t_h.numel()
+        if g_h is not None and tuple(g_h.shape) != (npv, npt):
+            raise ValueError(f"grad_flux must have shape ({npv}, {npt})")
+        if pb_h is not None and pb_h.numel() != npt:
+            raise ValueError("pb_index must have one entry per time")
         f_h = result(out, (npv, npt), self.dtype)
-        go_h = result(grad_out, (npv, nparam), torch.float64) if grad else None
+        go_h = result(grad_out, (npv, nparam), torch.float64) if g_h is not None else None
         st_h = result(status_out, (npv,), torch.int32)
-        if npv == 0:
-            return f_h, go_h, st_h
-        cp = chunk_pvs or max(32, -(-npv // 8))
-        cp = min(cp, npv)
-        if not hasattr(self, "_host_streams"):
-            self._host_streams = [torch.cuda.Stream(device=dev) for _ in range(3)]
-        s_in, s_run, s_out = self._host_streams
-        nbuf = 2
         ss = _host_array(supersampling, self.npb, np.int32, 1)
         ex = _host_array(exptime, self.npb, np.float64, 0.0)
-        with torch.cuda.device(dev):
-            p_d = [torch.empty((cp, nparam), dtype=torch.float64, device=dev) for _ in range(nbuf)]
-            f_d = [torch.empty((cp, npt), dtype=self.dtype, device=dev) for _ in range(nbuf)]
-            st_d = [torch.empty(cp, dtype=torch.int32, device=dev) for _ in range(nbuf)]
-            ws_f = None if grad else [self.workspace(cp, npt, False) for _ in range(nbuf)]
-            if grad:
-                g_d = [torch.empty((cp, npt), dtype=self.dtype, device=dev) for _ in range(nbuf)]
-                go_d = [torch.empty((cp, nparam), dtype=torch.float64, device=dev) for _ in range(nbuf)]
-                ws_g = [self.workspace(cp, npt, True) for _ in range(nbuf)]
-            # every buffer above was made on the current stream: the copy stream starts after it
-            s_in.wait_stream(torch.cuda.current_stream(dev))
-            with torch.cuda.stream(s_in):
-                t_d = t_h.to(dev, non_blocking=True)
-                pb_d = None if pb_h is None else pb_h.to(dev, non_blocking=True)
-            free = [None] * nbuf
-            for c, c0 in enumerate(range(0, npv, cp)):
-                c1 = min(npv, c0 + cp)
-                n, b = c1 - c0, c % nbuf
-                with torch.cuda.stream(s_in):
-                    if free[b] is not None:
-                        s_in.wait_event(free[b])
-                    p_d[b][:n].copy_(p_h[c0:c1], non_blocking=True)
-                    if grad:
-                        g_d[b][:n].copy_(g_h[c0:c1], non_blocking=True)
-                    ready = torch.cuda.Event()
-                    ready.record(s_in)
-                s_run.wait_event(ready)
-                if grad:
-                    # one shared set-up for the light curves and the adjoint of the chunk
-                    self.prepare(t_d, p_d[b][:n], pb_d, ss, ex, pv_status=st_d[b][:n], workspace=ws_g[b],
-                                 stream=s_run)
-                    self.evaluate(t_d, p_d[b][:n], pb_d, ss, ex, out=f_d[b][:n], pv_status=st_d[b][:n],
-                                  stream=s_run, prepared=ws_g[b])
-                    self.evaluate_grad(t_d, p_d[b][:n], g_d[b][:n], pb_d, ss, ex, out=go_d[b][:n],
-                                       stream=s_run, prepared=ws_g[b])
-                else:
-                    self.evaluate(t_d, p_d[b][:n], pb_d, ss, ex, out=f_d[b][:n], pv_status=st_d[b][:n],
-                                  workspace=ws_f[b], stream=s_run)
-                done = torch.cuda.Event()
-                done.record(s_run)
-                s_out.wait_event(done)
-                with torch.cuda.stream(s_out):
-                    f_h[c0:c1].copy_(f_d[b][:n], non_blocking=True)
-                    st_h[c0:c1].copy_(st_d[b][:n], non_blocking=True)
-                    if grad:
-                        go_h[c0:c1].copy_(go_d[b][:n], non_blocking=True)
-                    free[b] = torch.cuda.Event()
-                    free[b].record(s_out)
-            s_out.synchronize()
+        with torch.cuda.device(self.device):
+            st = self.lib.rr_evaluate_host(self._h, _ptr(t_h), _ptr(pb_h), npt, _ptr(p_h), npv,
+                                           ss.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                           ex.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), _ptr(g_h), _ptr(f_h),
+                                           _ptr(go_h), _ptr(st_h), int(chunk_pvs or 0))
+        self._check(st)
         return f_h, go_h, st_h
 
     def flux(self, times, params, pb_index=None, supersampling=None, exptime=None) -> torch.Tensor:

@@ -491,7 +491,8 @@ rr_status rr_sync_status(rr_ctx* c, void* stream) {
         return cuda_fail(c, e, "rr_sync_status");
     if (w != 0) {
         cudaMemset(c->d_err, 0, sizeof(int));
-        return fail(c, RR_ETIMEOUT, "a kernel gave up waiting for its shared-memory staging copy");
+        return fail(c, RR_ETIMEOUT, w == kErrQueueTimeout ? "a kernel gave up waiting for its shared work queue"
+                                                           : "a kernel gave up waiting for its shared-memory staging copy");
     }
     return RR_OK;
 }

@@ -454,6 +454,39 @@ __device__ __forceinline__ int build_list(WarpList* wl, unsigned cand, const flo
     return ns;
 }
 
+// Candidate list when every passband has one sample per time: a candidate
+// is a sample, so the list is built from one ballot per time slot of the
+// lanes (no scans) and holds the raw offsets (dh, dl), the passband and the
+// per-time weight gbq; the precise phase is formed where a sample is
+// evaluated.  The list keeps time order (lane-major), so that a chunk of 32
+// samples is a contiguous stretch of the transit and takes the same branches.
+// bq[q] gets the list index of the lane's time q.  Returns the number of
+// candidates (warp-uniform).
+__device__ __forceinline__ int build_list_ss1(WarpList* wl, unsigned cand, const float (&dh)[4],
+                                              const float (&dl)[4], const int (&pbv)[4], const float (&gbq)[4],
+                                              int (&bq)[4]) {
+    const int lane = threadIdx.x & 31;
+    const unsigned below = (1u << lane) - 1u;
+    int total = 0, before = 0;     // candidates of the whole warp / of the lanes below this one
+    #pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const unsigned bal = __ballot_sync(0xffffffffu, (cand >> q) & 1u);
+        before += __popc(bal & below);
+        total += __popc(bal);
+    }
+    #pragma unroll
+    for (int q = 0; q < 4; ++q) bq[q] = before + __popc(cand & ((1u << q) - 1u));
+    #pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        if ((cand >> q) & 1u) {
+            wl->cand[bq[q]] = make_float4(dh[q], dl[q], 0.0f, gbq[q]);
+            wl->pb[bq[q]] = pbv[q];
+        }
+    }
+    __syncwarp();
+    return total;
+}
+
 // Shared-memory layout common to the FP32 per-point kernels:
 //   [mbarrier 16][reduction 64][per-pv tile constants 16 x kMaxPvTile]
 //   [passband constants][one candidate list per warp][pv records ...]
@@ -561,23 +594,31 @@ __device__ __forceinline__ bool warp_may_transit(const PvHead<float>& H, float4 
     return ceilf(plo) <= phi;
 }
 
-// ---- two-phase scheduling of the FP32 kernels -------------------------------
+// ---- scheduling of the FP32 kernels ----------------------------------------
 //
-// Phase 1: warps take 128-time groups from a shared counter.  For a group,
-// lane l decides for pv l of the tile whether the group's phase interval can
-// hold a transit; a ballot gives the warp the tile's mask.  Pvs outside the
-// mask need no arithmetic (flux exactly 1); the others become work items
-// (pv, group) in a shared-memory queue.  Phase 2: after a CTA barrier the
-// warps drain the queue, one item at a time, so the in-transit work of the
+// Warps take 128-time groups from a shared counter.  For a group, lane l
+// decides for pv l of the tile whether the group's phase interval can hold a
+// transit; a ballot gives the warp the tile's mask.  Pvs outside the mask need
+// no arithmetic (flux exactly 1) and are stored at once; the others become
+// work items (pv, group) in a shared-memory queue.  Between groups, and after
+// the last one, warps claim queued items, so the output stream of some warps
+// overlaps the in-transit arithmetic of others and the in-transit work of the
 // CTA is spread over all its warps whatever groups it falls in.
+//
+// Queue protocol: a producer reserves slots (atomicAdd on nitems), writes the
+// item, then publishes it by writing its key (slots start at -1).  Consumers
+// claim only reserved slots (compare-and-swap on next_item) and wait, a few
+// instructions at most, for the key.  A warp that has no group left
+// decrements `producers`; when that count is 0 and nothing is claimable the
+// queue is finished.  Every wait is bounded.
 
-// Shared counters: [0] next group, [1] queued items, [2] next item.
+// Shared counters.
 struct TileCounters {
-    int next_group, nitems, next_item, pad;
+    int next_group, nitems, next_item, producers;
 };
 
 // Work item: phase constants of the pv at the group start (Ah, Al, m, rounding
-// bound in cycles) and (group << 5) | pv-in-tile.
+// bound in cycles) and key = (group << 5) | pv-in-tile.
 struct ItemQueue {
     float4* c;
     int* gi;
@@ -591,6 +632,17 @@ __device__ __forceinline__ ItemQueue queue_at(char* base, int cap) {
     q.c = reinterpret_cast<float4*>(base);
     q.gi = reinterpret_cast<int*>(base + (size_t)cap * 16);
     return q;
+}
+
+// Before the CTA's first barrier: counters and empty slots.
+__device__ __forceinline__ void queue_init(ItemQueue q, TileCounters* tc, int cap, int g0) {
+    for (int j = threadIdx.x; j < cap; j += blockDim.x) q.gi[j] = -1;
+    if (threadIdx.x == 0) {
+        tc->next_group = g0;
+        tc->nitems = 0;
+        tc->next_item = 0;
+        tc->producers = blockDim.x >> 5;
+    }
 }
 
 // Lane l: transit decision for pv l of the tile at this group.  Returns the
@@ -611,7 +663,7 @@ __device__ __forceinline__ unsigned group_decide(const GroupState& gs, const cha
     return __ballot_sync(0xffffffffu, may);
 }
 
-// Append the warp's items (one per set bit of `may`) to the CTA queue.
+// Append the warp's items (one per set bit of `may`) and publish them.
 __device__ __forceinline__ void queue_push(ItemQueue q, TileCounters* tc, unsigned may, int g, float4 cl) {
     const int lane = threadIdx.x & 31;
     int base = 0;
@@ -620,16 +672,63 @@ __device__ __forceinline__ void queue_push(ItemQueue q, TileCounters* tc, unsign
     if ((may >> lane) & 1u) {
         const int pos = base + __popc(may & ((1u << lane) - 1u));
         q.c[pos] = cl;
-        q.gi[pos] = (g << 5) | lane;
+        __threadfence_block();
+        *reinterpret_cast<volatile int*>(q.gi + pos) = (g << 5) | lane;
     }
 }
 
-// Next item for the warp (warp-uniform), or -1 when the queue is drained.
-__device__ __forceinline__ int queue_pop(TileCounters* tc, int nitems) {
-    const int lane = threadIdx.x & 31;
-    int it = 0;
-    if (lane == 0) it = atomicAdd(&tc->next_item, 1);
-    it = __shfl_sync(0xffffffffu, it, 0);
-    return it < nitems ? it : -1;
+// This warp takes no more groups.
+__device__ __forceinline__ void queue_producer_done(TileCounters* tc) {
+    __syncwarp();
+    if ((threadIdx.x & 31) == 0) {
+        __threadfence_block();
+        atomicSub(&tc->producers, 1);
+    }
+}
+
+// Claim one reserved item for the warp (warp-uniform result), or -1 if every
+// reserved item is claimed.
+__device__ __forceinline__ int queue_claim(TileCounters* tc) {
+    int it = -1;
+    if ((threadIdx.x & 31) == 0) {
+        volatile int* vn = &tc->nitems;
+        int cur = *reinterpret_cast<volatile int*>(&tc->next_item);
+        for (int tries = 0; tries < 64 && cur < *vn; ++tries) {
+            const int prev = atomicCAS(&tc->next_item, cur, cur + 1);
+            if (prev == cur) {
+                it = cur;
+                break;
+            }
+            cur = prev;
+        }
+    }
+    return __shfl_sync(0xffffffffu, it, 0);
+}
+
+// Key of claimed item `it` once its producer has published it; -1 if the
+// bounded wait gives up.
+__device__ __forceinline__ int queue_key(ItemQueue q, int it) {
+    int key = -1;
+    if ((threadIdx.x & 31) == 0) {
+        volatile int* vk = q.gi + it;
+        for (int i = 0; i < (1 << 20); ++i) {
+            key = *vk;
+            if (key >= 0) break;
+            __nanosleep(32);
+        }
+        __threadfence_block();
+    }
+    return __shfl_sync(0xffffffffu, key, 0);
+}
+
+// No group left for this warp and nothing claimable: true when no producer
+// remains (the queue is then final).
+__device__ __forceinline__ bool queue_finished(TileCounters* tc) {
+    int done = 0;
+    if ((threadIdx.x & 31) == 0) {
+        done = *reinterpret_cast<volatile int*>(&tc->producers) == 0;
+        __threadfence_block();
+    }
+    return __shfl_sync(0xffffffffu, done, 0) != 0;
 }
 }  // namespace rr

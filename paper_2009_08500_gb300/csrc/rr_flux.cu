@@ -52,7 +52,7 @@ __device__ __forceinline__ void store4(float* out, const float (&f)[4], const in
     }
 }
 
-template <bool STAGE_ROWS>
+template <bool STAGE_ROWS, bool SS1>
 __global__ void __launch_bounds__(kBlock, 4) rr_flux_mixed_kernel(const double* __restrict__ times,
                                                                const float2* __restrict__ pdt,
                                                                const int32_t* __restrict__ ppb,
@@ -82,10 +82,8 @@ __global__ void __launch_bounds__(kBlock, 4) rr_flux_mixed_kernel(const double* 
                                      pv_tile * groups_per_cta);
     const uint32_t hbytes = (uint32_t)npv_t * (uint32_t)L.head_bytes;
     const uint32_t rbytes = STAGE_ROWS ? (uint32_t)npv_t * (uint32_t)L.rows_bytes : 0u;
+    queue_init(queue, tc, pv_tile * groups_per_cta, gbeg);
     if (tid == 0) {
-        tc->next_group = gbeg;
-        tc->nitems = 0;
-        tc->next_item = 0;
         mbar_init(bar, 1);
         mbar_expect_tx(bar, hbytes + rbytes);
         const char* src = records + (size_t)pv0 * L.head_bytes;
@@ -111,14 +109,9 @@ __global__ void __launch_bounds__(kBlock, 4) rr_flux_mixed_kernel(const double* 
     const float nanf_ = __int_as_float(0x7fc00000);
     const float zero4[4] = {0.f, 0.f, 0.f, 0.f};
 
-    // phase 1: per group, the tile's transit mask; every pv outside it is 1
-    // (NaN for an invalid pv or passband index) without arithmetic
-    #pragma unroll 1
-    while (true) {
-        int g = 0;
-        if (lane == 0) g = atomicAdd(&tc->next_group, 1);
-        g = __shfl_sync(0xffffffffu, g, 0);
-        if (g >= gend) break;
+    // a group: the tile's transit mask; every pv outside it is 1 (NaN for an
+    // invalid pv or passband index) without arithmetic, the others are queued
+    auto do_group = [&](int g) {
         const int p0 = g * kWarpPts + 4 * lane;
         GroupState gs;
         group_load(gs, pdt, ppb, times, g * kWarpPts, npt, recs, L.head_bytes, npv_t);
@@ -139,18 +132,12 @@ __global__ void __launch_bounds__(kBlock, 4) rr_flux_mixed_kernel(const double* 
                                 inval ? nanf_ : fb[3]};
             store4(out, f, gs.pbv, full);
         }
-    }
-    __syncthreads();
-    const int nitems = tc->nitems;
+    };
 
-    // phase 2: the queued (pv, group) items, one per warp at a time
-    #pragma unroll 1
-    while (true) {
-        const int it = queue_pop(tc, nitems);
-        if (it < 0) break;
+    // an item: every time of the group for one pv that may transit
+    auto do_item = [&](int it, int key) {
         const float4 c = queue.c[it];
-        const int gi = queue.gi[it];
-        const int g = gi >> 5, i = gi & 31;
+        const int g = key >> 5, i = key & 31;
         const int p0 = g * kWarpPts + 4 * lane;
         float dh[4], dl[4];
         int pbv[4];
@@ -172,10 +159,33 @@ __global__ void __launch_bounds__(kBlock, 4) rr_flux_mixed_kernel(const double* 
             if (fabsf(d) <= PB[pb].win_pc + c.w) cand |= 1u << q;
         }
         bool bad = false;
-        if (__any_sync(0xffffffffu, cand != 0)) {
+        if constexpr (SS1) {
+          if (__any_sync(0xffffffffu, cand != 0)) {
+            // one sample per time: the candidates are the samples
+            int bq[4];
+            const int nc = build_list_ss1(wl, cand, dh, dl, pbv, zero4, bq);
+            #pragma unroll 1
+            for (int e0 = 0; e0 < nc; e0 += 32) {
+                const int j = e0 + lane;
+                if (j < nc) {
+                    const int pb = wl->pb[j];
+                    const float4 cd = wl->cand[j];
+                    const Phase32 ph = precise_phase(cd.x, cd.y, c.x, c.y, H.Bh, H.Bl);
+                    wl->pacc[j] = delta32(H, PB[pb], rows + (size_t)pb * L.rows_per_pb * L.ng_pad, L.ng, ph.fr_h,
+                                          ph.fr_l, 0, 0.0f, 0.0f, bad);
+                }
+            }
+            __syncwarp();
+            #pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if ((cand >> q) & 1u) f[q] = 1.0f - wl->pacc[bq[q]];
+            __syncwarp();
+          }
+        } else if (__any_sync(0xffffffffu, cand != 0)) {
             int nc, base;
             const int ns = build_list(wl, cand, dh, dl, pbv, zero4, c.x, c.y, H.Bh, H.Bl, ps, nc, base);
             ChunkWalk cw{0};
+            #pragma unroll 1
             for (int e0 = 0; e0 < ns; e0 += 32) {
                 const int e = e0 + lane;
                 const bool valid = e < ns;
@@ -216,6 +226,48 @@ __global__ void __launch_bounds__(kBlock, 4) rr_flux_mixed_kernel(const double* 
         }
         if (bad && pv_status) atomicOr(pv_status + pv0 + i, RR_PV_KEPLER);
         store4(flux + (size_t)(pv0 + i) * npt + p0, f, pbv, vec_store && (p0 + 3 < npt));
+    };
+
+    bool groups_left = true;
+    int idle = 0;
+    #pragma unroll 1
+    while (true) {
+        if (groups_left) {
+            int g = 0;
+            if (lane == 0) g = atomicAdd(&tc->next_group, 1);
+            g = __shfl_sync(0xffffffffu, g, 0);
+            if (g < gend) do_group(g);
+            else { groups_left = false; queue_producer_done(tc); }
+        }
+        const int it = queue_claim(tc);
+        if (it >= 0) {
+            const int key = queue_key(queue, it);
+            if (key < 0) {
+                if (lane == 0) atomicExch(err, kErrQueueTimeout);
+                break;
+            }
+            do_item(it, key);
+            continue;
+        }
+        if (groups_left) continue;
+        if (queue_finished(tc)) {
+            // no producer left: the queue is final; drain what is still claimable
+            const int last = queue_claim(tc);
+            if (last < 0) break;
+            const int key = queue_key(queue, last);
+            if (key < 0) {
+                if (lane == 0) atomicExch(err, kErrQueueTimeout);
+                break;
+            }
+            do_item(last, key);
+            continue;
+        }
+        // other warps still take groups: wait for their items (bounded)
+        if (++idle > (1 << 22)) {
+            if (lane == 0) atomicExch(err, kErrQueueTimeout);
+            break;
+        }
+        __nanosleep(64);
     }
 }
 
@@ -368,7 +420,10 @@ cudaError_t launch_flux(rr_ctx* c, const double* times, const int32_t* pb_index,
                                                        (const char*)records, rowsg, (double*)flux, pv_status,
                                                        c->d_err);
     } else {
-        auto kern = stage_rows ? rr_flux_mixed_kernel<true> : rr_flux_mixed_kernel<false>;
+        bool ss1 = true;
+        for (int pb = 0; pb < pbp.npb; ++pb) ss1 = ss1 && pbp.ss[pb] == 1;
+        auto kern = stage_rows ? (ss1 ? rr_flux_mixed_kernel<true, true> : rr_flux_mixed_kernel<true, false>)
+                               : (ss1 ? rr_flux_mixed_kernel<false, true> : rr_flux_mixed_kernel<false, false>);
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         const int vec = (npt % 4 == 0) && (((uintptr_t)flux & 15u) == 0);

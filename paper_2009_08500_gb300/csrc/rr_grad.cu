@@ -188,7 +188,41 @@ __device__ __forceinline__ void cta_partials_groups(const float* gacc, const cha
     }
 }
 
+// One sample of the FP32 adjoint: the phase fr_h + fr_l cycles from the
+// conjunction m + mg cycles after the group's epoch (mg: the pv's cycles at
+// the group start), shifted by the sub-exposure offset `off` (cycles); gb is
+// the cotangent weight.  Adds to `acc`; returns whether the sample is in
+// transit; sets `bad` on a Kepler failure.
 template <bool DEP>
+__device__ __forceinline__ bool adjoint_sample(const PvHead<float>& H, const PvPb<float>& pbr,
+                                               const float* __restrict__ rowblk, const RecLayout& L, float fr_h,
+                                               float fr_l, float m, float off, float mg, float gb, GradAcc<float>& acc,
+                                               float* dep, int kslot, int uslot, bool& bad) {
+    const PvPb<float> pbc = pbr;
+    const float xr = (fr_h + off) + fr_l;
+    const float r = round_nearest(xr);
+    const float x = xr - r;
+    const float dM = 6.28318530717958647692f * x;
+    if (fabsf(dM) > pbc.win_s) return false;
+    double dMd = 0.0;
+    if (H.flags & kPvKepler64) {
+        double xd = ((double)fr_h + (double)off) + (double)fr_l;
+        xd -= rint(xd);
+        dMd = 6.283185307179586476925 * xd;
+    }
+    const Orbit32 o = orbit32(H, dM, dMd);
+    if (!o.ok) {
+        bad = true;
+        return false;
+    }
+    const float gz = o.z * pbc.inv1pk;
+    if (!o.front || gz >= 1.0f) return false;
+    const float psi_tot = ((mg + m) + r) + x;   // (t_s - T0) / P
+    grad_sample<float, DEP>(H, pbc, rowblk, L, o.z, o.Px, o.Py, o.S, o.V, psi_tot, gb, acc, dep, kslot, uslot);
+    return true;
+}
+
+template <bool DEP, bool SS1>
 __global__ void __launch_bounds__(kBlock, 3) rr_grad_mixed_kernel(
     const double* __restrict__ times, const float2* __restrict__ pdt, const int32_t* __restrict__ ppb, int npt,
     int npv, PbParams pbp, RecLayout L, int pv_tile, int groups_per_cta, const char* __restrict__ records,
@@ -213,10 +247,8 @@ __global__ void __launch_bounds__(kBlock, 3) rr_grad_mixed_kernel(
     const int pv0 = blockIdx.y * pv_tile;
     const int npv_t = min(pv_tile, npv - pv0);
     const uint32_t bytes = (uint32_t)npv_t * (uint32_t)L.head_bytes;
+    queue_init(queue, tc, pv_tile * groups_per_cta, gbeg);
     if (tid == 0) {
-        tc->next_group = gbeg;
-        tc->nitems = 0;
-        tc->next_item = 0;
         mbar_init(bar, 1);
         mbar_expect_tx(bar, bytes);
         const char* src = records + (size_t)pv0 * L.head_bytes;
@@ -235,35 +267,23 @@ __global__ void __launch_bounds__(kBlock, 3) rr_grad_mixed_kernel(
     }
     if (__syncthreads_or(ok ? 0 : 1)) return;
 
-    // phase 1: per group, the tile's transit mask -> work items
-    #pragma unroll 1
-    while (true) {
-        int g = 0;
-        if (lane == 0) g = atomicAdd(&tc->next_group, 1);
-        g = __shfl_sync(0xffffffffu, g, 0);
-        if (g >= gend) break;
+    // a group: the tile's transit mask -> work items
+    auto do_group = [&](int g) {
         GroupState gs;
         group_load(gs, pdt, ppb, times, g * kWarpPts, npt, recs, L.head_bytes, npv_t);
         unsigned bad;
         float4 cl;
         const unsigned may = group_decide(gs, recs, L.head_bytes, npv_t, bad, cl);
         if (may) queue_push(queue, tc, may, g, cl);
-    }
-    __syncthreads();
-    const int nitems = tc->nitems;
+    };
 
-    // phase 2: every item's sums go to its own (pv, group) slot, so the result
-    // does not depend on which warp took which item
-    const float two_pi = 6.28318530717958647692f;
+    // an item: its sums go to its own (pv, group) slot, so the result does not
+    // depend on which warp took which item
     const int nkp = chromatic ? L.npb : 1;
     float* dep = DEP ? depcols + tid : nullptr;
-    #pragma unroll 1
-    while (true) {
-        const int it = queue_pop(tc, nitems);
-        if (it < 0) break;
+    auto do_item = [&](int it, int key) {
         const float4 c = queue.c[it];
-        const int gi = queue.gi[it];
-        const int g = gi >> 5, i = gi & 31;
+        const int g = key >> 5, i = key & 31;
         const int p0 = g * kWarpPts + 4 * lane;
         float dh[4], dl[4];
         int pbv[4];
@@ -287,7 +307,7 @@ __global__ void __launch_bounds__(kBlock, 3) rr_grad_mixed_kernel(
                 if (gbq[q] != 0.0f) cand |= 1u << q;
             }
         }
-        if (!__any_sync(0xffffffffu, cand != 0)) continue;
+        if (!__any_sync(0xffffffffu, cand != 0)) return;
         GradAcc<float> acc;
         #pragma unroll
         for (int j = 0; j < 6; ++j) acc.o[j] = 0.0f;
@@ -297,37 +317,37 @@ __global__ void __launch_bounds__(kBlock, 3) rr_grad_mixed_kernel(
         if (DEP)
             for (int j = 6; j < nacc; ++j) dep[(j - 6) * kBlock] = 0.0f;
         bool any = false, bad = false;
-        int nc, base;
-        const int ns = build_list(wl, cand, dh, dl, pbv, gbq, c.x, c.y, H.Bh, H.Bl, ps, nc, base);
-        ChunkWalk cw{0};
-        for (int e0 = 0; e0 < ns; e0 += 32) {
-            const int e = e0 + lane;
-            const int j = chunk_cand(cw, wl->soff, nc, e0);
-            if (e >= ns) continue;
-            const int pb = wl->pb[j];
-            const float4 cd = wl->cand[j];
-            const PvPb<float> pbc = PB[pb];
-            const float off = fmaf((float)(e - wl->soff[j]), ps->step[pb], ps->first[pb]) * H.Bh;
-            const float xr = (cd.x + off) + cd.y;
-            const float r = round_nearest(xr);
-            const float x = xr - r;
-            const float dM = two_pi * x;
-            if (fabsf(dM) > pbc.win_s) continue;
-            double dMd = 0.0;
-            if (H.flags & kPvKepler64) {
-                double xd = ((double)cd.x + (double)off) + (double)cd.y;
-                xd -= rint(xd);
-                dMd = 6.283185307179586476925 * xd;
+        if constexpr (SS1) {
+            // one sample per time: the candidates are the samples
+            int bq[4];
+            const int nc = build_list_ss1(wl, cand, dh, dl, pbv, gbq, bq);
+            #pragma unroll 1
+            for (int e0 = 0; e0 < nc; e0 += 32) {
+                const int j = e0 + lane;
+                if (j >= nc) continue;
+                const float4 cd = wl->cand[j];
+                const int pb = wl->pb[j];
+                const Phase32 ph = precise_phase(cd.x, cd.y, c.x, c.y, H.Bh, H.Bl);
+                any |= adjoint_sample<DEP>(H, PB[pb], rows + (size_t)pb * L.rows_per_pb * L.ng_pad, L, ph.fr_h,
+                                           ph.fr_l, ph.m, 0.0f, c.z, cd.w, acc, dep, 6 + (chromatic ? pb : 0),
+                                           6 + nkp + pb * L.nldc, bad);
             }
-            const Orbit32 o = orbit32(H, dM, dMd);
-            if (!o.ok) { bad = true; continue; }
-            const float gz = o.z * pbc.inv1pk;
-            if (!o.front || gz >= 1.0f) continue;
-            const float psi_tot = ((c.z + cd.z) + r) + x;   // (t_s - T0) / P
-            grad_sample<float, DEP>(H, pbc, rows + (size_t)pb * L.rows_per_pb * L.ng_pad, L, o.z, o.Px,
-                                    o.Py, o.S, o.V, psi_tot, cd.w, acc, dep, 6 + (chromatic ? pb : 0),
-                                    6 + nkp + pb * L.nldc);
-            any = true;
+        } else {
+            int nc, base;
+            const int ns = build_list(wl, cand, dh, dl, pbv, gbq, c.x, c.y, H.Bh, H.Bl, ps, nc, base);
+            ChunkWalk cw{0};
+            #pragma unroll 1
+            for (int e0 = 0; e0 < ns; e0 += 32) {
+                const int e = e0 + lane;
+                const int j = chunk_cand(cw, wl->soff, nc, e0);
+                if (e >= ns) continue;
+                const int pb = wl->pb[j];
+                const float4 cd = wl->cand[j];
+                const float off = fmaf((float)(e - wl->soff[j]), ps->step[pb], ps->first[pb]) * H.Bh;
+                any |= adjoint_sample<DEP>(H, PB[pb], rows + (size_t)pb * L.rows_per_pb * L.ng_pad, L, cd.x, cd.y,
+                                           cd.z, off, c.z, cd.w, acc, dep, 6 + (chromatic ? pb : 0),
+                                           6 + nkp + pb * L.nldc, bad);
+            }
         }
         __syncwarp();
         if (bad) {
@@ -336,6 +356,48 @@ __global__ void __launch_bounds__(kBlock, 3) rr_grad_mixed_kernel(
             if (pv_status) atomicOr(pv_status + pv0 + i, RR_PV_KEPLER);
         }
         warp_accumulate<float, DEP>(acc, dep, nacc, any, gacc + ((size_t)i * groups_per_cta + (g - gbeg)) * nacc);
+    };
+
+    bool groups_left = true;
+    int idle = 0;
+    #pragma unroll 1
+    while (true) {
+        if (groups_left) {
+            int g = 0;
+            if (lane == 0) g = atomicAdd(&tc->next_group, 1);
+            g = __shfl_sync(0xffffffffu, g, 0);
+            if (g < gend) do_group(g);
+            else { groups_left = false; queue_producer_done(tc); }
+        }
+        const int it = queue_claim(tc);
+        if (it >= 0) {
+            const int key = queue_key(queue, it);
+            if (key < 0) {
+                if (lane == 0) atomicExch(err, kErrQueueTimeout);
+                break;
+            }
+            do_item(it, key);
+            continue;
+        }
+        if (groups_left) continue;
+        if (queue_finished(tc)) {
+            // no producer left: the queue is final; drain what is still claimable
+            const int last = queue_claim(tc);
+            if (last < 0) break;
+            const int key = queue_key(queue, last);
+            if (key < 0) {
+                if (lane == 0) atomicExch(err, kErrQueueTimeout);
+                break;
+            }
+            do_item(last, key);
+            continue;
+        }
+        // other warps still take groups: wait for their items (bounded)
+        if (++idle > (1 << 22)) {
+            if (lane == 0) atomicExch(err, kErrQueueTimeout);
+            break;
+        }
+        __nanosleep(64);
     }
     cta_partials_groups(gacc, recs, L.head_bytes, npv_t, nacc, groups_per_cta, pv0, blockIdx.x, gridDim.x,
                         partials);
@@ -559,8 +621,15 @@ cudaError_t launch_grad(rr_ctx* c, const double* times, const int32_t* pb_index,
                                           (const float*)grad_flux, (float*)partials, nacc, c->cfg.chromatic,  \
                                           pv_status, c->d_err);                                               \
     } while (0)
-        if (dep) RR_LAUNCH_GRAD32(rr_grad_mixed_kernel<true>);
-        else RR_LAUNCH_GRAD32(rr_grad_mixed_kernel<false>);
+        bool ss1 = true;
+        for (int pb = 0; pb < pbp.npb; ++pb) ss1 = ss1 && pbp.ss[pb] == 1;
+        if (dep) {
+            if (ss1) RR_LAUNCH_GRAD32((rr_grad_mixed_kernel<true, true>));
+            else RR_LAUNCH_GRAD32((rr_grad_mixed_kernel<true, false>));
+        } else {
+            if (ss1) RR_LAUNCH_GRAD32((rr_grad_mixed_kernel<false, true>));
+            else RR_LAUNCH_GRAD32((rr_grad_mixed_kernel<false, false>));
+        }
 #undef RR_LAUNCH_GRAD32
     }
     c->launches++;

@@ -35,6 +35,7 @@ constexpr double kESwitch = 0.8;          // above this eccentricity Kepler is s
 
 // device error word values (ctx->d_err)
 constexpr int kErrBarrierTimeout = 1;
+constexpr int kErrQueueTimeout = 2;
 
 enum PvFlags : int32_t { kPvCircular = 1, kPvKepler64 = 2, kPvNoWindow = 4 };
 

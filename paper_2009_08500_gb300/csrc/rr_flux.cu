@@ -124,13 +124,16 @@ __global__ void __launch_bounds__(kBlock, 4) rr_flux_mixed_kernel(const double* 
         for (int q = 0; q < 4; ++q) fb[q] = gs.pbv[q] < L.npb ? 1.0f : nanf_;
         const bool full = vec_store && (p0 + 3 < npt);
         float* out = flux + (size_t)pv0 * npt + p0;
+        // the pvs of the tile that need no arithmetic, lowest first
+        unsigned rest = (npv_t >= 32 ? 0xffffffffu : ((1u << npv_t) - 1u)) & ~may;
         #pragma unroll 1
-        for (int i = 0; i < npv_t; ++i, out += npt) {
-            if ((may >> i) & 1u) continue;
+        while (rest) {
+            const int i = __ffs(rest) - 1;
+            rest &= rest - 1u;
             const bool inval = (bad >> i) & 1u;
             const float f[4] = {inval ? nanf_ : fb[0], inval ? nanf_ : fb[1], inval ? nanf_ : fb[2],
                                 inval ? nanf_ : fb[3]};
-            store4(out, f, gs.pbv, full);
+            store4(out + (size_t)i * npt, f, gs.pbv, full);
         }
     };
 

@@ -113,6 +113,7 @@ struct PbParams {
 struct ModelParams {
     int32_t ld_model, npb, chromatic, nldc, nparam, nk, ng, nbasis;
     double k0, k1, dk;
+    double inv_dk;   // 1 / dk (host FP64)
 };
 
 }  // namespace rr

@@ -233,9 +233,10 @@ __device__ R mean_anomaly_of_true_r(R f, R e) {
 // CTAs per SM and the per-pv scalar chains of many CTAs overlap; the rows
 // and windows are spread over the whole CTA.
 template <typename R> struct SetupPvs { static constexpr int N = 8; };
+__host__ __device__ inline int setup_pvs_per_cta(int) { return 8; }
 
 template <typename R>
-__global__ void __launch_bounds__(256) rr_pv_setup_kernel(ModelParams mp, PbParams pbp,
+__global__ void __launch_bounds__(256, 4) rr_pv_setup_kernel(ModelParams mp, PbParams pbp,
                                                           const double* __restrict__ params, int npv,
                                                           const R* __restrict__ T, const float* __restrict__ DT,
                                                           const double* __restrict__ istar,
@@ -246,15 +247,19 @@ __global__ void __launch_bounds__(256) rr_pv_setup_kernel(ModelParams mp, PbPara
     __shared__ R invIs_s[NP][RR_MAX_PB];
     __shared__ R ak_s[NP][RR_MAX_PB];
     __shared__ int ik_s[NP][RR_MAX_PB];
-    __shared__ int st_s[NP];
+    __shared__ int st_s[NP];       // validity after (1): LD coefficients, I_star, k
+    __shared__ int st2_s[NP];      // full validity after (2a)
+    __shared__ int rows_next;
     __shared__ int wmax_s[NP];     // largest point window over the passbands (float bits, -1 = none)
     __shared__ int flags_s[NP];
     __shared__ R orb_s[NP][6];     // a, b, e, f0, M0, n
-    const int pv0 = blockIdx.x * NP;
-    const int nloc = min(NP, npv - pv0);
+    const int ppc = setup_pvs_per_cta(mp.npb);
+    const int pv0 = blockIdx.x * ppc;
+    const int nloc = min(ppc, npv - pv0);
     const int nkp = mp.chromatic ? mp.npb : 1;
     const int tid = threadIdx.x;
     if (tid < NP) st_s[tid] = 0;
+    if (tid == 0) rows_next = 0;
     __syncthreads();
 
     // (1) per (pv, passband): validity, LD coefficients, I_star, k cell
@@ -294,7 +299,12 @@ __global__ void __launch_bounds__(256) rr_pv_setup_kernel(ModelParams mp, PbPara
     }
     __syncthreads();
 
-    // (2a) per pv, one thread each: orbit constants
+    // From here warp 0 computes the orbit constants and transit windows
+    // (2a-2c) while the other warps build the profile rows (3), which need only
+    // (1); warp 0 joins the rows when it is done.
+    const int warp = tid >> 5, lane = tid & 31;
+    if (warp == 0) {
+    // (2a) per pv, one lane each: orbit constants
     if (tid < nloc) {
         const int pv = pv0 + tid;
         const double* row = params + (size_t)pv * mp.nparam;
@@ -312,7 +322,7 @@ __global__ void __launch_bounds__(256) rr_pv_setup_kernel(ModelParams mp, PbPara
             if (!(ad > 1.0)) st |= RR_PV_A_RANGE;
             if (!(bd >= 0.0 && bd <= ad)) st |= RR_PV_B_RANGE;
         }
-        st_s[tid] = st;
+        st2_s[tid] = st;
         H->status = st;
         if (pv_status) pv_status[pv] = st;
         H->flags = 0;
@@ -381,12 +391,12 @@ __global__ void __launch_bounds__(256) rr_pv_setup_kernel(ModelParams mp, PbPara
             orb_s[tid][4] = M0; orb_s[tid][5] = n;
         }
     }
-    __syncthreads();
+    __syncwarp();
 
-    // (2b) per (pv, passband), one thread each: transit window
-    for (int t = tid; t < nloc * mp.npb; t += blockDim.x) {
+    // (2b) per (pv, passband), one lane each: transit window
+    for (int t = lane; t < nloc * mp.npb; t += 32) {
         const int lp = t / mp.npb, pb = t % mp.npb;
-        if (st_s[lp] != 0) continue;
+        if (st2_s[lp] != 0) continue;
         const int pv = pv0 + lp;
         const double* row = params + (size_t)pv * mp.nparam;
         PvPb<R>* PB = reinterpret_cast<PvPb<R>*>(records + (size_t)pv * L.head_bytes + L.off_pb);
@@ -441,26 +451,36 @@ __global__ void __launch_bounds__(256) rr_pv_setup_kernel(ModelParams mp, PbPara
         PB[pb].win_pc = wc;
         atomicMax(&wmax_s[lp], __float_as_int(wc));   // non-negative floats order as their bits
     }
-    __syncthreads();
+    __syncwarp();
 
     // (2c) the per-pv summary of the windows
-    if (tid < nloc && st_s[tid] == 0) {
+    if (tid < nloc && st2_s[tid] == 0) {
         PvHead<R>* H = reinterpret_cast<PvHead<R>*>(records + (size_t)(pv0 + tid) * L.head_bytes);
         H->wmax_c = __int_as_float(wmax_s[tid]);
         H->flags = flags_s[tid];
     }
+    }   // warp 0
 
     // (3) profile rows of all pvs of the CTA: the k-interpolated combination of
     // the basis projections times 1 / I_star (arithmetic in R)
     const size_t kstride = (size_t)mp.ng;
     const size_t bstride = (size_t)mp.nk * mp.ng;
-    const R inv_dk = (R)(1.0 / mp.dk);
+    const R inv_dk = (R)mp.inv_dk;
     char* rows_region = records + rows_offset(L, npv);
     const bool named = mp.ld_model != RR_LD_TABULATED;
     const int nc = named ? mp.nldc : 0;
-    // one (pv, passband) row block per warp at a time; lanes walk the g nodes
-    const int lane = tid & 31, nwarps = blockDim.x >> 5;
-    for (int rw = tid >> 5; rw < nloc * mp.npb; rw += nwarps) {
+    // work units of 64 g nodes of one (pv, passband) row block, taken by the
+    // warps from a shared counter; lanes walk the nodes.  Rows of pvs that
+    // (2a) finds invalid are built too and never read.
+    const int nchunk = (L.ng_pad + 63) / 64;
+    const int nunits = nloc * mp.npb * nchunk;
+    #pragma unroll 1
+    while (true) {
+        int w = 0;
+        if (lane == 0) w = atomicAdd(&rows_next, 1);
+        w = __shfl_sync(0xffffffffu, w, 0);
+        if (w >= nunits) break;
+        const int rw = w / nchunk, ch = w - rw * nchunk;
         const int lp = rw / mp.npb, pb = rw - lp * mp.npb;
         if (st_s[lp] != 0) continue;
         R* r0 = reinterpret_cast<R*>(rows_region + (size_t)(pv0 + lp) * L.rows_bytes) +
@@ -471,10 +491,14 @@ __global__ void __launch_bounds__(256) rr_pv_setup_kernel(ModelParams mp, PbPara
         R uc[4];
         #pragma unroll
         for (int c = 0; c < 4; ++c) uc[c] = c < nc ? u_s[lp][pb][c] : R(0);
+        R Ic[4];   // basis disk integrals, converted once per row
+        #pragma unroll
+        for (int c = 0; c < 4; ++c) Ic[c] = (grad && c < nc) ? (R)istar[1 + c] : R(0);
         const int b0 = named ? 0 : pb;
         const R* T0p = T + (size_t)b0 * bstride + (size_t)ik * kstride;
         const float* D0p = DT + (size_t)b0 * bstride + (size_t)ik * kstride;
-        for (int ig = lane; ig < L.ng_pad; ig += 32) {
+        const int ig_end = min(L.ng_pad, 64 * ch + 64);
+        for (int ig = 64 * ch + lane; ig < ig_end; ig += 32) {
             if (ig >= mp.ng) {
                 for (int r = 0; r < L.rows_per_pb; ++r) r0[(size_t)r * L.ng_pad + ig] = (R)0;
                 continue;
@@ -517,7 +541,7 @@ __global__ void __launch_bounds__(256) rr_pv_setup_kernel(ModelParams mp, PbPara
                 if (c < nc) {
                     const R* Tc = T0p + (size_t)(1 + c) * bstride;
                     const R Rc = bk * Tc[ig] + ak * Tc[kstride + ig];
-                    r0[(size_t)(3 + c) * L.ng_pad + ig] = (Rc - ldw_n * (R)istar[1 + c]) * invIs;
+                    r0[(size_t)(3 + c) * L.ng_pad + ig] = (Rc - ldw_n * Ic[c]) * invIs;
                 }
             }
         }
@@ -537,6 +561,7 @@ ModelParams model_params(const rr_ctx* c) {
     mp.k0 = c->cfg.k0;
     mp.k1 = c->cfg.k1;
     mp.dk = c->dk;
+    mp.inv_dk = 1.0 / c->dk;
     return mp;
 }
 
@@ -569,12 +594,14 @@ cudaError_t launch_pv_setup(rr_ctx* c, const double* params, int npv, const PbPa
                             void* records, int32_t* pv_status, cudaStream_t s) {
     ModelParams mp = model_params(c);
     if (c->cfg.precision == RR_PREC_FP64) {
-        const int blocks = (npv + SetupPvs<double>::N - 1) / SetupPvs<double>::N;
+        const int ppc = setup_pvs_per_cta(c->cfg.npb);
+        const int blocks = (npv + ppc - 1) / ppc;
         RecLayout L = make_layout<double>(c->cfg.npb, c->cfg.ng, c->nldc, grad);
         rr_pv_setup_kernel<double><<<blocks, 256, 0, s>>>(mp, pbp, params, npv, c->d_T64, c->d_DT32, c->d_istar, L,
                                                           grad ? 1 : 0, (char*)records, pv_status);
     } else {
-        const int blocks = (npv + SetupPvs<float>::N - 1) / SetupPvs<float>::N;
+        const int ppc = setup_pvs_per_cta(c->cfg.npb);
+        const int blocks = (npv + ppc - 1) / ppc;
         RecLayout L = make_layout<float>(c->cfg.npb, c->cfg.ng, c->nldc, grad);
         rr_pv_setup_kernel<float><<<blocks, 256, 0, s>>>(mp, pbp, params, npv, c->d_T32, c->d_DT32, c->d_istar, L,
                                                          grad ? 1 : 0, (char*)records, pv_status);

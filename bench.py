@@ -36,9 +36,10 @@ CONFIG_TEXT = {
     "c5": "Serving: Poisson requests from 64 fits, npv logU[1,4096] x npt logU[500,2e5] (capped at 2^25 points), "
           "mixed LD, forward:gradient 3:1",
 }
-# DRAM bytes (read + write) per launch of the flux kernel, from one ncu capture of the
-# same kernel (profiles/flux_mixed_c3_population.md); None until captured for this version
-TRAFFIC = {}
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch, from one ncu capture
+# of the same kernels (profiles/flux_mixed_c3_population.md, grad_mixed_c3_population.md,
+# flux_mixed_c4_heterogeneous.md); to be cleared whenever those kernels change
+TRAFFIC = {("c3", "flux"): 270_912_768, ("c3", "grad"): 23_563_776, ("c4", "flux"): 446_138_112}
 
 
 def parse():
@@ -495,7 +496,9 @@ def run_serving(a):
         models[i] = rr.model_for(wl, device=local)
     rng = np.random.Generator(np.random.PCG64(1234))
     cap = 1 << 25
-    gbuf = rng.normal(size=cap).astype(np.float32)
+    # the clients keep their data in pinned host memory (as a serving client would)
+    gbuf = torch.from_numpy(rng.normal(size=cap).astype(np.float32)).pin_memory()
+    pin = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a, dt)).pin_memory()  # noqa: E731
     pool = []
     for j in range(96):
         fi = int(rng.integers(0, len(fits)))
@@ -507,9 +510,9 @@ def run_serving(a):
         wl = W.make_small(fits[fi]["ld_model"], npv=max(npv, 1), npt=npt, seed=int(rng.integers(0, 2 ** 31)),
                           eccentric=fits[fi]["eccentric"], span=max(2.0, npt / 720.0))
         grad = bool(rng.uniform() < 0.25)
-        pool.append(dict(fit=fi, times=wl.times, params=wl.params, pb_index=wl.pb_index,
-                         supersampling=wl.supersampling, exptime=wl.exptime,
-                         grad_flux=gbuf[:wl.npv * wl.npt].reshape(wl.npv, wl.npt) if grad else None))
+        pool.append(dict(fit=fi, times=pin(wl.times, np.float64), params=pin(wl.params, np.float64),
+                         pb_index=pin(wl.pb_index, np.int32), supersampling=wl.supersampling, exptime=wl.exptime,
+                         grad_flux=gbuf[:wl.npv * wl.npt].view(wl.npv, wl.npt) if grad else None))
     slots = 8
     backend = CudaBackend(models, slots=slots, device=local)
 

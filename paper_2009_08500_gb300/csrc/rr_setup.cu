@@ -400,31 +400,35 @@ __global__ void __launch_bounds__(256, 4) rr_pv_setup_kernel(ModelParams mp, PbP
         const int pv = pv0 + lp;
         const double* row = params + (size_t)pv * mp.nparam;
         PvPb<R>* PB = reinterpret_cast<PvPb<R>*>(records + (size_t)pv * L.head_bytes + L.off_pb);
-        const R a = orb_s[lp][0], b = orb_s[lp][1], e = orb_s[lp][2], f0 = orb_s[lp][3];
-        const R M0 = orb_s[lp][4], n = orb_s[lp][5];
-        const R pi = Tr<R>::pi();
-        const R ra = a * (R(1) - e);
+        // the window is a conservative bound with explicit margins: FP32 in both
+        // forms (dependent FP64 transcendentals are slow on this GPU)
+        using W = float;
+        const W a = (W)orb_s[lp][0], b = (W)orb_s[lp][1], e = (W)orb_s[lp][2], f0 = (W)orb_s[lp][3];
+        const W M0 = (W)orb_s[lp][4], n = (W)orb_s[lp][5];
+        const W pi = Tr<W>::pi();
+        const W ra = a * (W(1) - e);
         // conjunction anomaly wrapped to (-pi, pi] (periastron at 0)
-        const R fc = f0 - R(2) * pi * floor((f0 + pi) / (R(2) * pi));
+        const W fc = f0 - W(2) * pi * floorf((f0 + pi) / (W(2) * pi));
         const R k = (R)row[6 + (mp.chromatic ? pb : 0)];
+        const W kw = (W)k;
         // Transit window in true anomaly, |f - f0| <= d.  A transit needs
         // X^2 + Y^2 < (1 + k)^2 with |X| = r |sin(f - f0)|, |Y| = r cos(f - f0) b / a
         // (planet in front: |f - f0| < pi/2).  Start from r >= a (1 - e); then, with
         // r_min and the smallest |Y| over the current window, |sin(f - f0)| <=
         // sqrt((1 + k)^2 - Y_min^2) / r_min gives a window that still holds every
-        // transit point.  Safety factors absorb the rounding of R.
-        const R lim = R(1) + k;
-        const R q = lim / ra;
-        R d = q >= R(1) ? R(0.5) * pi : r_asin(q);
+        // transit point.  Safety factors absorb the FP32 rounding.
+        const W lim = W(1) + kw;
+        const W q = lim / ra;
+        W d = q >= W(1) ? W(0.5) * pi : r_asin(q);
         bool none = false;
         for (int it = 0; it < 5 && !none; ++it) {
-            const R mc = fabs(fc) <= d ? R(1) : r_max(cos(fc - d), cos(fc + d));
-            const R rmin = a * (R(1) - e * e) / (R(1) + e * mc);
-            const R ymin = rmin * cos(d) * (b / a) * R(1 - 4e-6);
-            const R x2 = lim * lim * R(1 + 4e-6) - ymin * ymin;
-            if (!(x2 > R(0))) { none = true; break; }
-            const R sx = d_sqrt(x2) / rmin;
-            const R dn = sx >= R(1) ? R(0.5) * pi : r_asin(sx);
+            const W mc = fabsf(fc) <= d ? W(1) : r_max(cosf(fc - d), cosf(fc + d));
+            const W rmin = a * (W(1) - e * e) / (W(1) + e * mc);
+            const W ymin = rmin * cosf(d) * (b / a) * W(1 - 4e-6);
+            const W x2 = lim * lim * W(1 + 4e-6) - ymin * ymin;
+            if (!(x2 > W(0))) { none = true; break; }
+            const W sx = d_sqrt(x2) / rmin;
+            const W dn = sx >= W(1) ? W(0.5) * pi : r_asin(sx);
             d = dn < d ? dn : d;
         }
         PB[pb].k = k;
@@ -436,18 +440,18 @@ __global__ void __launch_bounds__(256, 4) rr_pv_setup_kernel(ModelParams mp, PbP
             PB[pb].win_pc = -1.0f;
             continue;
         }
-        const R hi = wrap_2pi_r(mean_anomaly_of_true_r(f0 + d, e) - M0);
-        const R lo = wrap_2pi_r(M0 - mean_anomaly_of_true_r(f0 - d, e));
-        R win = r_max(hi, lo);
-        win += R(1e-5) * (R(1) + win);
+        const W hi = wrap_2pi_r(mean_anomaly_of_true_r(f0 + d, e) - M0);
+        const W lo = wrap_2pi_r(M0 - mean_anomaly_of_true_r(f0 - d, e));
+        W win = r_max(hi, lo);
+        win += W(1e-5) * (W(1) + win);
         const int ss = pbp.ss[pb];
-        const R half = R(0.5) * (R)pbp.exptime[pb] * (R(1) - R(1) / R(ss));
-        R winp = win + n * (ss > 1 ? half : R(0)) * R(1.000001);
-        if (win >= pi) { win = R(1e30); atomicOr(&flags_s[lp], (int)kPvNoWindow); }
-        if (winp >= pi) winp = R(1e30);
-        PB[pb].win_s = win;
-        PB[pb].win_p = winp;
-        const float wc = (float)(winp * (R(0.5) / pi));
+        const W half = W(0.5) * (W)pbp.exptime[pb] * (W(1) - W(1) / W(ss));
+        W winp = win + n * (ss > 1 ? half : W(0)) * W(1.000001);
+        if (win >= pi) { win = W(1e30); atomicOr(&flags_s[lp], (int)kPvNoWindow); }
+        if (winp >= pi) winp = W(1e30);
+        PB[pb].win_s = (R)win;
+        PB[pb].win_p = (R)winp;
+        const float wc = winp * (W(0.5) / pi);
         PB[pb].win_pc = wc;
         atomicMax(&wmax_s[lp], __float_as_int(wc));   // non-negative floats order as their bits
     }

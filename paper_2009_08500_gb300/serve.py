@@ -252,18 +252,27 @@ class CudaBackend(Backend):
     def nbytes(self, req: ServeRequest) -> int:
         m = self.fits[req.fit]
         esize = 8 if m.precision == "fp64" else 4
-        b = req.npt * (8 + 4) + req.params.size * 8 + req.npv * 4
+        nparams = int(np.prod(req.params.shape))
+        b = req.npt * (8 + 4) + nparams * 8 + req.npv * 4
         b += req.npv * req.npt * esize                              # flux
         b += m.workspace_bytes(req.npv, req.npt, False)
         if req.grad_flux is not None:
-            b += req.npv * req.npt * esize + req.params.size * 8 + m.workspace_bytes(req.npv, req.npt, True)
+            b += req.npv * req.npt * esize + nparams * 8 + m.workspace_bytes(req.npv, req.npt, True)
         return int(b)
 
     def prepare(self, req: ServeRequest) -> None:
-        """Pinned host copies of the inputs and pinned result buffers (submitting thread)."""
+        """Pinned host inputs and pinned result buffers (submitting thread).  Inputs
+        that are already pinned CPU tensors of the right type are used as they are."""
         torch = self.torch
         m = self.fits[req.fit]
-        pin = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a, dt)).pin_memory()  # noqa: E731
+        tdt = {np.float64: torch.float64, np.float32: torch.float32, np.int32: torch.int32}
+
+        def pin(a, dt):
+            if isinstance(a, torch.Tensor) and a.device.type == "cpu":
+                t = a.to(tdt[dt]).contiguous()
+                return t if t.is_pinned() else t.pin_memory()
+            return torch.from_numpy(np.ascontiguousarray(a, dt)).pin_memory()
+
         h = {"t": pin(req.times, np.float64), "p": pin(req.params, np.float64),
              "pb": None if req.pb_index is None else pin(req.pb_index, np.int32),
              "flux": torch.empty((req.npv, req.npt), dtype=m.dtype, pin_memory=True),

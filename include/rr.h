@@ -258,6 +258,26 @@ rr_status rr_evaluate_host(rr_ctx* ctx, const double* times, const int32_t* pb_i
                            const double* exptime, const void* grad_flux, void* flux, double* grad_params,
                            int32_t* pv_status, int32_t chunk_pvs);
 
+/* One request from host buffers, asynchronous (serving: many requests in
+ * flight on different streams).  Enqueues on `stream`: the copies of the
+ * host inputs into `scratch`, the evaluation (with one shared set-up and the
+ * adjoint when grad_flux != NULL), and the copies of flux, pv_status and
+ * grad_params back to host memory; returns once everything is enqueued.
+ * The paper has no counterpart.  Arguments as rr_evaluate_host, plus
+ *   scratch      device, >= rr_request_bytes(ctx, npv, npt, with_grad)
+ *                bytes, 256-byte aligned, owned by the caller and not to be
+ *                reused until the stream has passed this request
+ * Host buffers must be page-locked for the copies to be asynchronous, and
+ * must stay untouched until the stream has passed the request (an event
+ * recorded after the call tells when).  Results are bitwise those of
+ * rr_evaluate / rr_evaluate_grad.  Errors: as rr_evaluate, plus RR_ECUDA
+ * for a failed copy. */
+size_t rr_request_bytes(const rr_ctx* ctx, int32_t npv, int32_t npt, int32_t with_grad);
+rr_status rr_enqueue_host(rr_ctx* ctx, const double* times, const int32_t* pb_index, int32_t npt,
+                          const double* params, int32_t npv, const int32_t* supersampling,
+                          const double* exptime, const void* grad_flux, void* flux, double* grad_params,
+                          int32_t* pv_status, void* scratch, size_t scratch_bytes, void* stream);
+
 /* Copy a set-up table to host memory (for inspection and tests); returns the
  * element count of the table, or -1 on error.  `out` may be NULL to query
  * the size; otherwise it receives min(count, capacity) doubles.

@@ -151,3 +151,92 @@ extern "C" rr_status rr_evaluate_host(rr_ctx* c, const double* times, const int3
     if (e != cudaSuccess) return pipe_fail(c, e, "rr_evaluate_host");
     return rr_sync_status(c, s_out);
 }
+
+// ---------------------------------------------------------------------------
+// One request from host buffers, enqueued on a stream (serving): layout of the
+// caller's device scratch, then copy-in, evaluation (and adjoint), copy-out.
+namespace {
+
+struct ReqLayout {
+    size_t t, pb, p, f, st, ws, g, go, total, ws_bytes;
+};
+
+ReqLayout req_layout(const rr_ctx* c, int npv, int npt, bool grad) {
+    const size_t es = c->cfg.precision == RR_PREC_FP64 ? sizeof(double) : sizeof(float);
+    ReqLayout L;
+    L.t = 0;
+    L.pb = up256((size_t)npt * 8);
+    L.p = L.pb + up256((size_t)npt * 4);
+    L.f = L.p + up256((size_t)npv * c->nparam * 8);
+    L.st = L.f + up256((size_t)npv * npt * es);
+    L.ws = L.st + up256((size_t)npv * 4);
+    L.ws_bytes = up256(rr_workspace_bytes(c, npv, npt, grad ? 1 : 0));
+    L.g = L.ws + L.ws_bytes;
+    L.go = L.g + (grad ? up256((size_t)npv * npt * es) : 0);
+    L.total = L.go + (grad ? up256((size_t)npv * c->nparam * 8) : 0);
+    return L;
+}
+
+}  // namespace
+
+extern "C" size_t rr_request_bytes(const rr_ctx* c, int32_t npv, int32_t npt, int32_t with_grad) {
+    if (!c || npv < 0 || npt < 0) return 0;
+    return req_layout(c, npv, npt, with_grad != 0).total;
+}
+
+extern "C" rr_status rr_enqueue_host(rr_ctx* c, const double* times, const int32_t* pb_index, int32_t npt,
+                                     const double* params, int32_t npv, const int32_t* ss, const double* exptime,
+                                     const void* grad_flux, void* flux, double* grad_params, int32_t* pv_status,
+                                     void* scratch, size_t scratch_bytes, void* stream) {
+    if (!c) return RR_EINVAL;
+    if (npt < 0 || npv < 0) {
+        c->err = "npt and npv must be >= 0";
+        return RR_EINVAL;
+    }
+    if (npv == 0) return RR_OK;
+    const bool grad = grad_flux != nullptr;
+    if (!params || (npt > 0 && (!times || !flux)) || (grad && !grad_params) || (c->cfg.npb > 1 && npt > 0 && !pb_index)) {
+        c->err = "rr_enqueue_host: a required host array is null";
+        return RR_EINVAL;
+    }
+    const ReqLayout L = req_layout(c, npv, npt, grad);
+    if (!scratch || scratch_bytes < L.total || ((uintptr_t)scratch & 255u)) {
+        c->err = "rr_enqueue_host: scratch too small or not 256-byte aligned";
+        return RR_EINVAL;
+    }
+    const size_t es = c->cfg.precision == RR_PREC_FP64 ? sizeof(double) : sizeof(float);
+    const int np = c->nparam;
+    char* b = (char*)scratch;
+    double* d_t = (double*)(b + L.t);
+    int32_t* d_pb = pb_index ? (int32_t*)(b + L.pb) : nullptr;
+    double* d_p = (double*)(b + L.p);
+    void* d_f = b + L.f;
+    int32_t* d_st = (int32_t*)(b + L.st);
+    void* d_ws = b + L.ws;
+    void* d_g = b + L.g;
+    double* d_go = (double*)(b + L.go);
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaSetDevice(c->cfg.device);
+    if (e == cudaSuccess && npt > 0) e = cudaMemcpyAsync(d_t, times, (size_t)npt * 8, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && d_pb && npt > 0) e = cudaMemcpyAsync(d_pb, pb_index, (size_t)npt * 4, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_p, params, (size_t)npv * np * 8, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && grad && npt > 0)
+        e = cudaMemcpyAsync(d_g, grad_flux, (size_t)npv * npt * es, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return pipe_fail(c, e, "rr_enqueue_host copy-in");
+    rr_status st;
+    if (grad) {
+        st = rr_prepare(c, d_t, d_pb, npt, d_p, npv, ss, exptime, d_st, d_ws, L.ws_bytes, s);
+        if (st == RR_OK) st = rr_evaluate_prepared(c, d_t, d_pb, npt, d_p, npv, ss, exptime, d_f, d_st, d_ws, L.ws_bytes, s);
+        if (st == RR_OK)
+            st = rr_evaluate_grad_prepared(c, d_t, d_pb, npt, d_p, npv, ss, exptime, d_g, d_go, d_st, d_ws, L.ws_bytes, s);
+    } else {
+        st = rr_evaluate(c, d_t, d_pb, npt, d_p, npv, ss, exptime, d_f, d_st, d_ws, L.ws_bytes, s);
+    }
+    if (st != RR_OK) return st;
+    if (npt > 0) e = cudaMemcpyAsync(flux, d_f, (size_t)npv * npt * es, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && pv_status) e = cudaMemcpyAsync(pv_status, d_st, (size_t)npv * 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && grad)
+        e = cudaMemcpyAsync(grad_params, d_go, (size_t)npv * np * 8, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return pipe_fail(c, e, "rr_enqueue_host copy-out");
+    return RR_OK;
+}

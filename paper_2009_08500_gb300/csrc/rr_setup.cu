@@ -332,18 +332,23 @@ __global__ void __launch_bounds__(256, 4) rr_pv_setup_kernel(ModelParams mp, PbP
         wmax_s[tid] = __float_as_int(-1.0f);
         flags_s[tid] = 0;
         if (st == 0) {
-            const R a = (R)ad, b = (R)bd, e = (R)ed, w = (R)wd;
+            const R a = (R)ad, b = (R)bd, e = (R)ed;
             const R pi = Tr<R>::pi();
-            const R f0 = R(0.5) * pi - w;
-            R sh, ch;
-            d_sincos(R(0.5) * f0, &sh, &ch);
-            const R E0 = R(2) * r_atan2(d_sqrt(R(1) - e) * sh, d_sqrt(R(1) + e) * ch);
-            R sE0, cE0, sw, cw;
-            d_sincos(E0, &sE0, &cE0);
-            d_sincos(w, &sw, &cw);
-            const R M0 = E0 - e * sE0;
-            const R se = d_sqrt(R(1) - e * e);
-            const R den0 = R(1) - e * cE0;
+            const R f0 = R(0.5) * pi - (R)wd;
+            // One FP64 sincos: the conjunction's true anomaly f0 = pi/2 - w has
+            // sin f0 = cos w and cos f0 = sin w, and its eccentric anomaly E0
+            // cos E0 = (e + cos f0) / (1 + e cos f0), sin E0 = sqrt(1 - e^2) sin f0 / (1 + e cos f0),
+            // with 1 - e cos E0 = (1 - e^2) / (1 + e cos f0) (no cancellation).
+            double swd, cwd;
+            sincos(wd, &swd, &cwd);
+            const double sed = sqrt(1.0 - ed * ed);
+            const double qd = 1.0 / (1.0 + ed * swd);
+            const double cE0d = (ed + swd) * qd, sE0d = sed * cwd * qd, den0d = (1.0 - ed * ed) * qd;
+            const R sE0 = (R)sE0d, cE0 = (R)cE0d, sw = (R)swd, cw = (R)cwd;
+            const R se = (R)sed;
+            const R den0 = (R)den0d;
+            // M0 serves the (FP32) transit windows only
+            const float M0 = atan2f((float)sE0d, (float)cE0d) - (float)ed * (float)sE0d;
             const double invP = 1.0 / P;
             const R n = (R)(2.0 * CUDART_PI * invP);
             R ax1, ax2, ay1, ay2, rho0;
@@ -357,15 +362,10 @@ __global__ void __launch_bounds__(256, 4) rr_pv_setup_kernel(ModelParams mp, PbP
                 rho0 = den0;
             }
             H->T0 = T0; H->P = P; H->invP = invP;
-            if (ed > kESwitch) {
-                // the FP64 Kepler constants of the e -> 1 branch
-                const double f0d = 0.5 * CUDART_PI - wd;
-                const double E0d = 2.0 * atan2(sqrt(1.0 - ed) * sin(0.5 * f0d), sqrt(1.0 + ed) * cos(0.5 * f0d));
-                const double cE0d = cos(E0d), sE0d = sin(E0d);
-                H->ecE0d = ed * cE0d; H->esE0d = ed * sE0d; H->inv_den0d = 1.0 / (1.0 - ed * cE0d);
-            } else {
-                H->ecE0d = (double)(e * cE0); H->esE0d = (double)(e * sE0); H->inv_den0d = (double)(R(1) / den0);
-            }
+            // FP64 Kepler constants (the FP64 form, and e > kESwitch in the mixed form)
+            H->ecE0d = ed * cE0d;
+            H->esE0d = ed * sE0d;
+            H->inv_den0d = (1.0 + ed * swd) / (1.0 - ed * ed);
             {
                 // third-order inversion of d0 x + (e sin E0 / 2) x^2 + (e cos E0 / 6) x^3 = dM
                 const float sy = (float)(e * sE0 / den0), cy = (float)(e * cE0 / den0);
@@ -375,7 +375,7 @@ __global__ void __launch_bounds__(256, 4) rr_pv_setup_kernel(ModelParams mp, PbP
                 H->kepC = fmaxf(0.5f * ef / (1.0f - fminf(ef, 0.999f)), 0.5f);
             }
             H->a = a; H->b = b; H->a2 = a * a; H->b2 = b * b;
-            H->e = e; H->ecE0 = e * cE0; H->esE0 = e * sE0; H->inv_den0 = R(1) / den0;
+            H->e = e; H->ecE0 = (R)(ed * cE0d); H->esE0 = (R)(ed * sE0d); H->inv_den0 = (R)H->inv_den0d;
             H->ax1 = ax1; H->ax2 = ax2; H->ay1 = ay1; H->ay2 = ay2;
             H->rho0 = rho0; H->n = n;
             const float Bh = (float)invP;

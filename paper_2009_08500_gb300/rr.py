@@ -31,7 +31,7 @@ EXPORTS = ["rr_create", "rr_destroy", "rr_set_ld_profile", "rr_build_weights", "
            "rr_workspace_bytes", "rr_evaluate", "rr_evaluate_grad", "rr_read_table",
            "rr_sync_status", "rr_last_error", "rr_launch_count", "rr_profile", "rr_profile_read",
            "rr_evaluate_noalloc", "rr_prepare", "rr_evaluate_prepared", "rr_evaluate_grad_prepared",
-           "rr_evaluate_host"]
+           "rr_evaluate_host", "rr_request_bytes", "rr_enqueue_host"]
 KERNELS = {"ld_basis": 0, "weights": 1, "pv_setup": 2, "flux": 3, "grad": 4, "grad_reduce": 5, "points": 6}
 
 
@@ -76,6 +76,9 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     L.rr_evaluate_grad_prepared.argtypes = [vp, vp, vp, i32, vp, i32, ctypes.POINTER(i32), dp, vp, vp, vp, vp, sz,
                                             vp]
     L.rr_evaluate_host.argtypes = [vp, vp, vp, i32, vp, i32, ctypes.POINTER(i32), dp, vp, vp, vp, vp, i32]
+    L.rr_request_bytes.argtypes = [vp, i32, i32, i32]
+    L.rr_request_bytes.restype = sz
+    L.rr_enqueue_host.argtypes = [vp, vp, vp, i32, vp, i32, ctypes.POINTER(i32), dp, vp, vp, vp, vp, vp, sz, vp]
     L.rr_read_table.argtypes = [vp, i32, dp, i64]
     L.rr_read_table.restype = i64
     L.rr_sync_status.argtypes = [vp, vp]
@@ -87,7 +90,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     L.rr_profile_read.argtypes = [vp, i32, dp, ctypes.POINTER(i64), i32]
     for name in ("rr_create", "rr_destroy", "rr_set_ld_profile", "rr_build_weights", "rr_evaluate",
                  "rr_evaluate_grad", "rr_sync_status", "rr_profile", "rr_profile_read", "rr_evaluate_noalloc",
-                 "rr_prepare", "rr_evaluate_prepared", "rr_evaluate_grad_prepared", "rr_evaluate_host"):
+                 "rr_prepare", "rr_evaluate_prepared", "rr_evaluate_grad_prepared", "rr_evaluate_host",
+                 "rr_enqueue_host"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -355,6 +359,25 @@ class Model:
                                            _ptr(go_h), _ptr(st_h), int(chunk_pvs or 0))
         self._check(st)
         return f_h, go_h, st_h
+
+    def request_bytes(self, npv: int, npt: int, grad: bool = False) -> int:
+        """Device scratch of one :meth:`enqueue_host` request (rr_request_bytes)."""
+        return int(self.lib.rr_request_bytes(self._h, npv, npt, int(grad)))
+
+    def enqueue_host(self, times, params, pb_index, supersampling, exptime, grad_flux, out, grad_out, status_out,
+                     scratch: torch.Tensor, stream) -> None:
+        """One request from pinned CPU tensors, enqueued on `stream` (rr_enqueue_host).
+
+        All host tensors must be contiguous pinned CPU tensors of the model's
+        types and stay untouched until the stream has passed the request."""
+        npv, npt = int(params.shape[0]), int(times.numel())
+        ss = _host_array(supersampling, self.npb, np.int32, 1)
+        ex = _host_array(exptime, self.npb, np.float64, 0.0)
+        self._check(self.lib.rr_enqueue_host(self._h, _ptr(times), _ptr(pb_index), npt, _ptr(params), npv,
+                                             ss.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                             ex.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), _ptr(grad_flux),
+                                             _ptr(out), _ptr(grad_out), _ptr(status_out), _ptr(scratch),
+                                             scratch.numel(), _stream_handle(stream)))
 
     def flux(self, times, params, pb_index=None, supersampling=None, exptime=None) -> torch.Tensor:
         """Differentiable light curves (gradient w.r.t. ``params`` through the adjoint kernel)."""

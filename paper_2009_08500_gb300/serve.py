@@ -239,7 +239,7 @@ class Server:
 class CudaBackend(Backend):
     """Runs requests through librr: one CUDA stream per slot, device-resident fit contexts.
 
-    fits: {fit id: rr.Model} (built); requests carry host arrays (pinned on launch).
+    fits: {fit id: rr.Model} (built); requests carry host arrays (pinned when submitted).
     """
 
     def __init__(self, fits: Dict[Any, Any], slots: int, device: int = 0):
@@ -250,15 +250,8 @@ class CudaBackend(Backend):
         self.streams = [torch.cuda.Stream(device=self.device) for _ in range(slots)]
 
     def nbytes(self, req: ServeRequest) -> int:
-        m = self.fits[req.fit]
-        esize = 8 if m.precision == "fp64" else 4
-        nparams = int(np.prod(req.params.shape))
-        b = req.npt * (8 + 4) + nparams * 8 + req.npv * 4
-        b += req.npv * req.npt * esize                              # flux
-        b += m.workspace_bytes(req.npv, req.npt, False)
-        if req.grad_flux is not None:
-            b += req.npv * req.npt * esize + nparams * 8 + m.workspace_bytes(req.npv, req.npt, True)
-        return int(b)
+        """Device bytes of the request: its scratch for rr_enqueue_host (inputs, outputs, workspace)."""
+        return self.fits[req.fit].request_bytes(req.npv, req.npt, req.grad_flux is not None)
 
     def prepare(self, req: ServeRequest) -> None:
         """Pinned host inputs and pinned result buffers (submitting thread).  Inputs
@@ -283,28 +276,20 @@ class CudaBackend(Backend):
         req._host = h
 
     def launch(self, req: ServeRequest, slot: int):
+        """One library call enqueues the copies in, the kernels and the copies out on the slot's stream."""
         torch = self.torch
         m = self.fits[req.fit]
         s = self.streams[slot]
         h = req._host
         with torch.cuda.stream(s):
-            t = h["t"].to(self.device, non_blocking=True)
-            p = h["p"].to(self.device, non_blocking=True)
-            pb = None if h["pb"] is None else h["pb"].to(self.device, non_blocking=True)
-            status = torch.empty(req.npv, dtype=torch.int32, device=self.device)
-            flux = m.evaluate(t, p, pb, req.supersampling, req.exptime, pv_status=status, stream=s)
-            h["flux"].copy_(flux, non_blocking=True)
-            keep = [t, p, pb, status, flux]
-            if h["g"] is not None:
-                g = h["g"].to(self.device, non_blocking=True)
-                grad = m.evaluate_grad(t, p, g, pb, req.supersampling, req.exptime, stream=s)
-                h["grad"].copy_(grad, non_blocking=True)
-                keep += [g, grad]
-            h["status"].copy_(status, non_blocking=True)
-            ev = torch.cuda.Event()
-            ev.record(s)
-        # device tensors stay referenced by the handle until the event has completed
-        return (ev, h, keep)
+            # allocated on the slot's stream: the caching allocator reuses it only after that stream's work
+            scratch = torch.empty(max(req.nbytes, 256), dtype=torch.uint8, device=self.device)
+        m.enqueue_host(h["t"], h["p"], h["pb"], req.supersampling, req.exptime, h["g"], h["flux"], h["grad"],
+                       h["status"], scratch, s)
+        ev = torch.cuda.Event()
+        ev.record(s)
+        # the scratch stays referenced by the handle until the event has completed
+        return (ev, h, scratch)
 
     def done(self, handle) -> bool:
         return handle[0].query()

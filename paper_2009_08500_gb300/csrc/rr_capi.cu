@@ -170,6 +170,8 @@ WsLayout ws_layout(const rr_ctx* c, int npv, int npt, bool grad) {
     if (c->cfg.precision == RR_PREC_MIXED) off += align256((size_t)npt * 8);
     w.pts_pb = off;
     if (c->cfg.precision == RR_PREC_MIXED) off += align256((size_t)npt * 4);
+    w.pts_grp = off;
+    if (c->cfg.precision == RR_PREC_MIXED) off += align256((size_t)((npt + kWarpPts - 1) / kWarpPts) * sizeof(GroupInfo));
     w.part = off;
     if (grad) off += align256(partials_bytes(c, npv, npt));
     w.total = off > 0 ? off : 256;
@@ -188,7 +190,7 @@ cudaError_t run_setup(rr_ctx* c, const double* times, const int32_t* pb_index, i
     const WsLayout W = ws_layout(c, npv, npt, grad);
     char* wb = (char*)ws;
     return timed(c, RR_KERNEL_POINTS, s,
-                 [&] { return launch_points(c, times, pb_index, npt, wb + W.pts_dt, wb + W.pts_pb, s); });
+                 [&] { return launch_points(c, times, pb_index, npt, wb + W.pts_dt, wb + W.pts_pb, wb + W.pts_grp, s); });
 }
 
 // Validity words only (npt == 0 with a pv_status array): the set-up kernel alone.
@@ -223,7 +225,7 @@ rr_status evaluate_impl(rr_ctx* c, const double* times, const int32_t* pb_index,
     const WsLayout W = ws_layout(c, npv, npt, prepared);
     char* wb = (char*)ws;
     if ((e = timed(c, RR_KERNEL_FLUX, s, [&] {
-             return launch_flux(c, times, pb_index, wb + W.pts_dt, wb + W.pts_pb, npt, npv, pbp, ws, flux,
+             return launch_flux(c, times, pb_index, wb + W.pts_dt, wb + W.pts_pb, wb + W.pts_grp, npt, npv, pbp, ws, flux,
                                 pv_status, prepared, s);
          })) != cudaSuccess)
         return cuda_fail(c, e, "flux kernel");
@@ -255,7 +257,7 @@ rr_status evaluate_grad_impl(rr_ctx* c, const double* times, const int32_t* pb_i
     char* wb = (char*)ws;
     void* partials = wb + W.part;
     if ((e = timed(c, RR_KERNEL_GRAD, s, [&] {
-             return launch_grad(c, times, pb_index, wb + W.pts_dt, wb + W.pts_pb, npt, npv, pbp, ws, grad_flux,
+             return launch_grad(c, times, pb_index, wb + W.pts_dt, wb + W.pts_pb, wb + W.pts_grp, npt, npv, pbp, ws, grad_flux,
                                 partials, pv_status, s);
          })) != cudaSuccess)
         return cuda_fail(c, e, "adjoint kernel");

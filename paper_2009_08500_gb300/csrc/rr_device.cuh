@@ -360,7 +360,6 @@ __device__ __forceinline__ void load_points(const float2* __restrict__ pdt, cons
 // (time, sub-exposure) pairs 32 at a time, so every lane does useful work
 // regardless of where the transit falls or how many sub-exposures a
 // passband has.
-constexpr int kWarpPts = 4 * 32;
 
 struct WarpList {
     float4 cand[kWarpPts];   // fr_h, fr_l (precise phase, cycles), m (cycles removed), gb (cotangent / -ss)
@@ -525,62 +524,81 @@ __device__ __forceinline__ float delta32(const PvHead<float>& H, const PvPb<floa
     return A * lerp_row<float>(row, ng, g, sl, cell);
 }
 
-__device__ __forceinline__ float warp_min(float v) {
-    for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
-    return v;
-}
 
 // Per-warp group state of the FP32 kernels.  A group is kWarpPts = 128
 // consecutive times, 4 per lane; its float-float times are relative to the
-// group's first time t_g.  Lane l also holds the phase constants of pv l of
-// the CTA's tile at t_g (the only FP64 of the per-point kernels):
+// group's first time t_g.  The group's summary comes from rr_points_kernel;
+// lane l also holds the phase constants of pv l of the CTA's tile at t_g:
 // A = frac((t_g - T0) / P) as a float pair and the removed integer cycles m.
 struct GroupState {
-    float dh[4], dl[4];
-    int pbv[4];
-    float wlo, whi, maxdt;   // warp-uniform: range of dh and largest |dh| over valid times
+    float wlo, whi, maxdt;   // warp-uniform: range of dh and largest |dh| over the group's times
+    int full;                // all 128 times present with valid passbands
     float Ah, Al, m;         // phase constants of pv `lane`
 };
 
-__device__ __forceinline__ void group_load(GroupState& gs, const float2* __restrict__ pdt,
-                                           const int32_t* __restrict__ ppb, const double* __restrict__ times,
-                                           int g0, int npt, const char* recs, int rec_bytes, int npv_t) {
-    const int lane = threadIdx.x & 31;
-    load_points(pdt, ppb, g0 + 4 * lane, npt, gs.dh, gs.dl, gs.pbv);
-    float lo = INFINITY, hi = -INFINITY, mx = 0.0f;
-    #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        if (gs.pbv[q] >= 0) {
-            lo = fminf(lo, gs.dh[q]);
-            hi = fmaxf(hi, gs.dh[q]);
-            mx = fmaxf(mx, fabsf(gs.dh[q]));
+// Phase constants of the tile's pvs at the CTA's first group g0 (the only FP64
+// of the per-point kernels, once per CTA): cta_ph[i] = (A0h, A0l, m0, 0).
+__device__ __forceinline__ void cta_phase(float4* cta_ph, const double* __restrict__ times, int g0,
+                                          const char* recs, int rec_bytes, int npv_t) {
+    for (int i = threadIdx.x; i < npv_t; i += blockDim.x) {
+        const PvHead<float>& H = *reinterpret_cast<const PvHead<float>*>(recs + (size_t)i * rec_bytes);
+        float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        if (H.status == 0) {
+            const double psi = (__ldg(times + (size_t)g0 * kWarpPts) - H.T0) * H.invP;
+            const double m = rint(psi);
+            const double A = psi - m;
+            v.x = (float)A;
+            v.y = (float)(A - (double)v.x);
+            v.z = (float)m;
         }
+        cta_ph[i] = v;
     }
-    gs.wlo = warp_min(lo);
-    gs.whi = warp_max(hi);
-    gs.maxdt = warp_max(mx);
+}
+
+// Difference of two float pairs, (ah + al) - (bh + bl), as a float pair.
+__device__ __forceinline__ void ff_sub(float ah, float al, float bh, float bl, float& rh, float& rl) {
+    const float s = ah - bh;
+    const float v = s - ah;
+    const float e = (ah - (s - v)) - (bh + v);   // exact error of s
+    rh = s;
+    rl = e + (al - bl);
+}
+
+__device__ __forceinline__ void group_load(GroupState& gs, const GroupInfo* __restrict__ grp, int g, int g0,
+                                           const float4* cta_ph, const char* recs, int rec_bytes, int npv_t) {
+    const int lane = threadIdx.x & 31;
+    const float4 s0 = __ldg(reinterpret_cast<const float4*>(grp + g));
+    const float2 tg = __ldg(reinterpret_cast<const float2*>(grp + g) + 2);
+    const float2 t0 = __ldg(reinterpret_cast<const float2*>(grp + g0) + 2);
+    gs.wlo = s0.x;
+    gs.whi = s0.y;
+    gs.maxdt = s0.z;
+    gs.full = __float_as_int(s0.w);
     gs.Ah = gs.Al = gs.m = 0.0f;
     if (lane < npv_t) {
         const PvHead<float>& H = *reinterpret_cast<const PvHead<float>*>(recs + (size_t)lane * rec_bytes);
         if (H.status == 0) {
-            const double psi = (__ldg(times + g0) - H.T0) * H.invP;
-            const double m = rint(psi);
-            const double A = psi - m;
-            gs.Ah = (float)A;
-            gs.Al = (float)(A - (double)gs.Ah);
-            gs.m = (float)m;
+            // phase at t_g = phase at t_g0 + (t_g - t_g0) / P, in float-float
+            float dh, dl;
+            ff_sub(tg.x, tg.y, t0.x, t0.y, dh, dl);
+            const float4 a0 = cta_ph[lane];
+            const Phase32 ph = precise_phase(dh, dl, a0.x, a0.y, H.Bh, H.Bl);
+            gs.Ah = ph.fr_h;
+            gs.Al = ph.fr_l;
+            gs.m = a0.z + ph.m;
         }
     }
 }
 
-// Phase constants of pv i for this group: (Ah, Al, m, coarse-phase error bound in cycles).
-__device__ __forceinline__ float4 group_pv(const GroupState& gs, const PvHead<float>& H, int i) {
-    float4 c;
-    c.x = __shfl_sync(0xffffffffu, gs.Ah, i);
-    c.y = __shfl_sync(0xffffffffu, gs.Al, i);
-    c.z = __shfl_sync(0xffffffffu, gs.m, i);
-    c.w = 2.4e-7f * (gs.maxdt * H.Bh + 1.0f);
-    return c;
+// Passband indices of the lane's 4 times (-1 beyond npt).
+__device__ __forceinline__ void load_pb(const int32_t* __restrict__ ppb, int p0, int npt, int (&pbv)[4]) {
+    if (p0 + 3 < npt) {
+        const int4 c = __ldg(reinterpret_cast<const int4*>(ppb + p0));
+        pbv[0] = c.x; pbv[1] = c.y; pbv[2] = c.z; pbv[3] = c.w;
+    } else {
+        #pragma unroll
+        for (int q = 0; q < 4; ++q) pbv[q] = p0 + q < npt ? __ldg(ppb + p0 + q) : -1;
+    }
 }
 
 // Can any of the warp's times be in transit for this pv?  The warp's phase

@@ -26,19 +26,65 @@
 
 namespace rr {
 
-// Per-point inputs of the FP32 kernels, once per call: dt = t - t_ref as a
-// float pair, t_ref = the first time of the point's 128-time group (FP64 here, so that
+// Per-point inputs of the FP32 kernels, once per call: dt = t - t_g as a float
+// pair, t_g = the first time of the point's 128-time group (FP64 here, so that
 // the per-(pv, point) work is FP32 only), and the passband index with
-// out-of-range values mapped to npb.
-__global__ void rr_points_kernel(const double* __restrict__ times, const int32_t* __restrict__ pb_index,
-                                 int npt, int npb, float2* __restrict__ dt, int32_t* __restrict__ pbw) {
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= npt) return;
-    const double d = times[p] - times[(p / kWarpPts) * kWarpPts];
-    const float h = (float)d;
-    dt[p] = make_float2(h, (float)(d - (double)h));
-    const int pb = pb_index ? pb_index[p] : 0;
-    pbw[p] = (pb >= 0 && pb < npb) ? pb : npb;
+// out-of-range values mapped to npb.  One CTA per group also writes the
+// group's summary (GroupInfo): the range and largest magnitude of its float
+// offsets, whether it is full with valid passbands, and t_g - t_0.
+__global__ void __launch_bounds__(kWarpPts) rr_points_kernel(const double* __restrict__ times,
+                                                             const int32_t* __restrict__ pb_index, int npt, int npb,
+                                                             float2* __restrict__ dt, int32_t* __restrict__ pbw,
+                                                             GroupInfo* __restrict__ grp) {
+    __shared__ float red[3][kWarpPts / 32];
+    __shared__ int redf[kWarpPts / 32];
+    const int g = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int p = g * kWarpPts + tid;
+    const double tg = times[(size_t)g * kWarpPts];
+    float lo = INFINITY, hi = -INFINITY, mx = 0.0f;
+    int ok = 0;
+    if (p < npt) {
+        const double d = times[p] - tg;
+        const float h = (float)d;
+        dt[p] = make_float2(h, (float)(d - (double)h));
+        const int pb = pb_index ? pb_index[p] : 0;
+        const int v = (pb >= 0 && pb < npb) ? pb : npb;
+        pbw[p] = v;
+        lo = hi = h;
+        mx = fabsf(h);
+        ok = v < npb;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+        mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    }
+    ok = __all_sync(0xffffffffu, ok);
+    if (lane == 0) {
+        red[0][warp] = lo;
+        red[1][warp] = hi;
+        red[2][warp] = mx;
+        redf[warp] = ok;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        GroupInfo gi;
+        gi.wlo = red[0][0];
+        gi.whi = red[1][0];
+        gi.maxdt = red[2][0];
+        gi.full = redf[0];
+        for (int w = 1; w < kWarpPts / 32; ++w) {
+            gi.wlo = fminf(gi.wlo, red[0][w]);
+            gi.whi = fmaxf(gi.whi, red[1][w]);
+            gi.maxdt = fmaxf(gi.maxdt, red[2][w]);
+            gi.full &= redf[w];
+        }
+        const double d0 = tg - times[0];
+        gi.toff_h = (float)d0;
+        gi.toff_l = (float)(d0 - (double)gi.toff_h);
+        gi.pad[0] = gi.pad[1] = 0.0f;
+        grp[g] = gi;
+    }
 }
 
 // Stores the 4 outputs of a lane (one 16-byte store when the row is vector-aligned).
@@ -56,6 +102,7 @@ template <bool STAGE_ROWS, bool SS1>
 __global__ void __launch_bounds__(kBlock, 4) rr_flux_mixed_kernel(const double* __restrict__ times,
                                                                const float2* __restrict__ pdt,
                                                                const int32_t* __restrict__ ppb,
+                                                               const GroupInfo* __restrict__ grp,
                                                                int npt, int npv, PbParams pbp, RecLayout L,
                                                                int pv_tile, int groups_per_cta,
                                                                const char* __restrict__ records,
@@ -105,6 +152,9 @@ __global__ void __launch_bounds__(kBlock, 4) rr_flux_mixed_kernel(const double* 
         mbar_wait_bounded(bar, 0);
     }
     if (__syncthreads_or(ok ? 0 : 1)) return;
+    float4* cta_ph = reinterpret_cast<float4*>(smem + kOffCta);
+    cta_phase(cta_ph, times, gbeg, recs, L.head_bytes, npv_t);
+    __syncthreads();
 
     const float nanf_ = __int_as_float(0x7fc00000);
     const float zero4[4] = {0.f, 0.f, 0.f, 0.f};
@@ -114,14 +164,16 @@ __global__ void __launch_bounds__(kBlock, 4) rr_flux_mixed_kernel(const double* 
     auto do_group = [&](int g) {
         const int p0 = g * kWarpPts + 4 * lane;
         GroupState gs;
-        group_load(gs, pdt, ppb, times, g * kWarpPts, npt, recs, L.head_bytes, npv_t);
+        group_load(gs, grp, g, gbeg, cta_ph, recs, L.head_bytes, npv_t);
         unsigned bad;
         float4 cl;
         const unsigned may = group_decide(gs, recs, L.head_bytes, npv_t, bad, cl);
         if (may) queue_push(queue, tc, may, g, cl);
+        int pbv[4] = {0, 0, 0, 0};
+        if (!gs.full) load_pb(ppb, p0, npt, pbv);    // a partial group or invalid passbands
         float fb[4];
         #pragma unroll
-        for (int q = 0; q < 4; ++q) fb[q] = gs.pbv[q] < L.npb ? 1.0f : nanf_;
+        for (int q = 0; q < 4; ++q) fb[q] = pbv[q] < L.npb ? 1.0f : nanf_;
         const bool full = vec_store && (p0 + 3 < npt);
         float* out = flux + (size_t)pv0 * npt + p0;
         // the pvs of the tile that need no arithmetic, lowest first
@@ -133,7 +185,7 @@ __global__ void __launch_bounds__(kBlock, 4) rr_flux_mixed_kernel(const double* 
             const bool inval = (bad >> i) & 1u;
             const float f[4] = {inval ? nanf_ : fb[0], inval ? nanf_ : fb[1], inval ? nanf_ : fb[2],
                                 inval ? nanf_ : fb[3]};
-            store4(out + (size_t)i * npt, f, gs.pbv, full);
+            store4(out + (size_t)i * npt, f, pbv, full);
         }
     };
 
@@ -388,15 +440,17 @@ int pv_tile_for(int rec_bytes) {
 }
 
 cudaError_t launch_points(rr_ctx* c, const double* times, const int32_t* pb_index, int npt, void* ws_dt,
-                          void* ws_pb, cudaStream_t s) {
-    rr_points_kernel<<<(npt + 255) / 256, 256, 0, s>>>(times, pb_index, npt, c->cfg.npb, (float2*)ws_dt,
-                                                       (int32_t*)ws_pb);
+                          void* ws_pb, void* ws_grp, cudaStream_t s) {
+    rr_points_kernel<<<(npt + kWarpPts - 1) / kWarpPts, kWarpPts, 0, s>>>(times, pb_index, npt, c->cfg.npb,
+                                                                          (float2*)ws_dt, (int32_t*)ws_pb,
+                                                                          (GroupInfo*)ws_grp);
     c->launches++;
     return cudaGetLastError();
 }
 
 cudaError_t launch_flux(rr_ctx* c, const double* times, const int32_t* pb_index, const void* pts_dt,
-                        const void* pts_pb, int npt, int npv, const PbParams& pbp, const void* records,
+                        const void* pts_pb, const void* pts_grp, int npt, int npv, const PbParams& pbp,
+                        const void* records,
                         void* flux, int32_t* pv_status, bool grad_layout, cudaStream_t s) {
     const bool f64 = c->cfg.precision == RR_PREC_FP64;
     RecLayout L = f64 ? make_layout<double>(c->cfg.npb, c->cfg.ng, c->nldc, grad_layout)
@@ -430,7 +484,8 @@ cudaError_t launch_flux(rr_ctx* c, const double* times, const int32_t* pb_index,
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         const int vec = (npt % 4 == 0) && (((uintptr_t)flux & 15u) == 0);
-        kern<<<grid, kBlock, smem, s>>>(times, (const float2*)pts_dt, (const int32_t*)pts_pb, npt, npv, pbp, L,
+        kern<<<grid, kBlock, smem, s>>>(times, (const float2*)pts_dt, (const int32_t*)pts_pb,
+                                        (const GroupInfo*)pts_grp, npt, npv, pbp, L,
                                         pv_tile, gpc, (const char*)records, rowsg, (float*)flux, pv_status, vec,
                                         c->d_err);
     }

@@ -224,7 +224,8 @@ __device__ __forceinline__ bool adjoint_sample(const PvHead<float>& H, const PvP
 
 template <bool DEP, bool SS1>
 __global__ void __launch_bounds__(kBlock, 3) rr_grad_mixed_kernel(
-    const double* __restrict__ times, const float2* __restrict__ pdt, const int32_t* __restrict__ ppb, int npt,
+    const double* __restrict__ times, const float2* __restrict__ pdt, const int32_t* __restrict__ ppb,
+    const GroupInfo* __restrict__ grp, int npt,
     int npv, PbParams pbp, RecLayout L, int pv_tile, int groups_per_cta, const char* __restrict__ records,
     const char* __restrict__ rowsg, const float* __restrict__ gflux, float* __restrict__ partials, int nacc,
     int chromatic,
@@ -266,11 +267,14 @@ __global__ void __launch_bounds__(kBlock, 3) rr_grad_mixed_kernel(
         mbar_wait_bounded(bar, 0);
     }
     if (__syncthreads_or(ok ? 0 : 1)) return;
+    float4* cta_ph = reinterpret_cast<float4*>(smem + kOffCta);
+    cta_phase(cta_ph, times, gbeg, recs, L.head_bytes, npv_t);
+    __syncthreads();
 
     // a group: the tile's transit mask -> work items
     auto do_group = [&](int g) {
         GroupState gs;
-        group_load(gs, pdt, ppb, times, g * kWarpPts, npt, recs, L.head_bytes, npv_t);
+        group_load(gs, grp, g, gbeg, cta_ph, recs, L.head_bytes, npv_t);
         unsigned bad;
         float4 cl;
         const unsigned may = group_decide(gs, recs, L.head_bytes, npv_t, bad, cl);
@@ -578,7 +582,8 @@ static bool grad_dep(const rr_ctx* c) {
 }
 
 cudaError_t launch_grad(rr_ctx* c, const double* times, const int32_t* pb_index, const void* pts_dt,
-                        const void* pts_pb, int npt, int npv, const PbParams& pbp, const void* records,
+                        const void* pts_pb, const void* pts_grp, int npt, int npv, const PbParams& pbp,
+                        const void* records,
                         const void* grad_flux, void* partials, int32_t* pv_status, cudaStream_t s) {
     const bool f64 = c->cfg.precision == RR_PREC_FP64;
     RecLayout L = f64 ? make_layout<double>(c->cfg.npb, c->cfg.ng, c->nldc, true)
@@ -616,7 +621,8 @@ cudaError_t launch_grad(rr_ctx* c, const double* times, const int32_t* pb_index,
     do {                                                                                                     \
         e = set_smem(KERNEL, smem);                                                                          \
         if (e != cudaSuccess) return e;                                                                      \
-        KERNEL<<<grid, kBlock, smem, s>>>(times, (const float2*)pts_dt, (const int32_t*)pts_pb, npt, npv, pbp, \
+        KERNEL<<<grid, kBlock, smem, s>>>(times, (const float2*)pts_dt, (const int32_t*)pts_pb,                \
+                                          (const GroupInfo*)pts_grp, npt, npv, pbp,                           \
                                           L, pv_tile, gpc, (const char*)records, rowsg,                       \
                                           (const float*)grad_flux, (float*)partials, nacc, c->cfg.chromatic,  \
                                           pv_status, c->d_err);                                               \

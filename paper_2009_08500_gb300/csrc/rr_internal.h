@@ -32,6 +32,18 @@ constexpr int kMaxNz = 4096;
 constexpr size_t kMaxSmem = 227 * 1024;   // dynamic shared memory per CTA on sm_103a
 constexpr int kMaxBasis = RR_MAX_PB + 4;  // profile bases: 1 + nldc (named) or npb (tabulated)
 constexpr double kESwitch = 0.8;          // above this eccentricity Kepler is solved in FP64
+constexpr int kWarpPts = 4 * 32;          // times per group: one warp, 4 consecutive times per lane
+
+// Per 128-time group, written once per call by rr_points_kernel (mixed form):
+// the range and largest magnitude of the float offsets of its times from the
+// group's first time t_g, whether all 128 times exist with a valid passband,
+// and t_g - t_0 (t_0 = the first time of the call) as a float pair.
+struct alignas(16) GroupInfo {
+    float wlo, whi, maxdt;
+    int32_t full;                 // 1: 128 times, every passband index valid
+    float toff_h, toff_l;
+    float pad[2];
+};
 
 // device error word values (ctx->d_err)
 constexpr int kErrBarrierTimeout = 1;
@@ -166,22 +178,25 @@ cudaError_t launch_pv_setup(rr_ctx* c, const double* params, int npv, const PbPa
                             bool grad, void* records, int32_t* pv_status, cudaStream_t s);
 // grad_layout: the records were written in the adjoint's layout (rr_prepare)
 cudaError_t launch_flux(rr_ctx* c, const double* times, const int32_t* pb_index, const void* pts_dt,
-                        const void* pts_pb, int npt, int npv, const PbParams& pbp, const void* records,
+                        const void* pts_pb, const void* pts_grp, int npt, int npv, const PbParams& pbp,
+                        const void* records,
                         void* flux, int32_t* pv_status, bool grad_layout, cudaStream_t s);
 cudaError_t launch_grad(rr_ctx* c, const double* times, const int32_t* pb_index, const void* pts_dt,
-                        const void* pts_pb, int npt, int npv, const PbParams& pbp, const void* records,
+                        const void* pts_pb, const void* pts_grp, int npt, int npv, const PbParams& pbp,
+                        const void* records,
                         const void* grad_flux, void* partials, int32_t* pv_status, cudaStream_t s);
 cudaError_t launch_grad_reduce(rr_ctx* c, int npt, const double* params, int npv, const void* records,
                                const void* partials, double* grad_params, cudaStream_t s);
 size_t records_bytes(const rr_ctx* c, int npv, bool grad);
 size_t partials_bytes(const rr_ctx* c, int npv, int npt);
-// workspace layout: [records | per-point float-float times + passband (mixed form) | partial sums]
+// workspace layout: [records | per-point float-float times + passband, per-group summaries (mixed form)
+//                    | partial sums]
 struct WsLayout {
-    size_t rec, pts_dt, pts_pb, part, total;
+    size_t rec, pts_dt, pts_pb, pts_grp, part, total;
 };
 WsLayout ws_layout(const rr_ctx* c, int npv, int npt, bool grad);
 cudaError_t launch_points(rr_ctx* c, const double* times, const int32_t* pb_index, int npt, void* ws_dt,
-                          void* ws_pb, cudaStream_t s);
+                          void* ws_pb, void* ws_grp, cudaStream_t s);
 ModelParams model_params(const rr_ctx* c);
 int pv_tile_for(int rec_bytes);
 void release_host_pipe(rr_ctx* c);

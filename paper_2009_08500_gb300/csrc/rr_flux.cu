@@ -125,11 +125,19 @@ __global__ void __launch_bounds__(kBlock, 4) rr_flux_mixed_kernel(const double* 
     const int npv_t = min(pv_tile, npv - pv0);
     // staged: headers of the tile, then (STAGE_ROWS) their profile rows, then the item queue
     char* srows = recs + (size_t)pv_tile * L.head_bytes;
-    const ItemQueue queue = queue_at(srows + (STAGE_ROWS ? (size_t)pv_tile * L.rows_bytes : 0),
-                                     pv_tile * groups_per_cta);
+    char* qbase = srows + (STAGE_ROWS ? (size_t)pv_tile * L.rows_bytes : 0);
+    const ItemQueue queue = queue_at(qbase, pv_tile * groups_per_cta);
+    // constant output rows of one group (1 and NaN), sources of the bulk stores
+    float* rows1 = reinterpret_cast<float*>(qbase + queue_bytes(pv_tile * groups_per_cta));
+    float* rowsnan = rows1 + kWarpPts;
     const uint32_t hbytes = (uint32_t)npv_t * (uint32_t)L.head_bytes;
     const uint32_t rbytes = STAGE_ROWS ? (uint32_t)npv_t * (uint32_t)L.rows_bytes : 0u;
     queue_init(queue, tc, pv_tile * groups_per_cta, gbeg);
+    for (int j = tid; j < kWarpPts; j += blockDim.x) {
+        rows1[j] = 1.0f;
+        rowsnan[j] = __int_as_float(0x7fc00000);
+    }
+    fence_proxy_async_smem();   // the bulk stores read these through the async proxy
     if (tid == 0) {
         mbar_init(bar, 1);
         mbar_expect_tx(bar, hbytes + rbytes);
@@ -158,6 +166,7 @@ __global__ void __launch_bounds__(kBlock, 4) rr_flux_mixed_kernel(const double* 
 
     const float nanf_ = __int_as_float(0x7fc00000);
     const float zero4[4] = {0.f, 0.f, 0.f, 0.f};
+    const uint64_t l2_pol = l2_evict_first_policy();
 
     // a group: the tile's transit mask; every pv outside it is 1 (NaN for an
     // invalid pv or passband index) without arithmetic, the others are queued
@@ -176,8 +185,19 @@ __global__ void __launch_bounds__(kBlock, 4) rr_flux_mixed_kernel(const double* 
         for (int q = 0; q < 4; ++q) fb[q] = pbv[q] < L.npb ? 1.0f : nanf_;
         const bool full = vec_store && (p0 + 3 < npt);
         float* out = flux + (size_t)pv0 * npt + p0;
-        // the pvs of the tile that need no arithmetic, lowest first
+        // the pvs of the tile that need no arithmetic
         unsigned rest = (npv_t >= 32 ? 0xffffffffu : ((1u << npv_t) - 1u)) & ~may;
+        if (vec_store && gs.full) {
+            // a whole 512-byte row segment per pv from a constant row in shared
+            // memory, one bulk asynchronous store per lane (lane i: pv i); the
+            // addresses are 16-byte aligned (npt % 4 == 0, aligned flux)
+            if ((rest >> lane) & 1u) {
+                bulk_s2g(flux + (size_t)(pv0 + lane) * npt + (size_t)g * kWarpPts,
+                         ((bad >> lane) & 1u) ? rowsnan : rows1, kWarpPts * sizeof(float), l2_pol);
+                bulk_commit();
+            }
+            rest = 0u;
+        }
         #pragma unroll 1
         while (rest) {
             const int i = __ffs(rest) - 1;
@@ -324,6 +344,7 @@ __global__ void __launch_bounds__(kBlock, 4) rr_flux_mixed_kernel(const double* 
         }
         __nanosleep(64);
     }
+    bulk_wait_all();   // the bulk stores read shared memory that ends with the CTA
 }
 
 // ----------------------------- FP64 form -----------------------------------
@@ -418,8 +439,10 @@ __global__ void __launch_bounds__(kBlock) rr_flux_fp64_kernel(const double* __re
 
 static size_t flux_smem(int pv_tile, int rec_bytes, bool f64, int gpc) {
     if (f64) return 16 + 16 * 4 + 16 * kMaxPvTile + (size_t)pv_tile * rec_bytes;
-    return kOffRecs32 + (size_t)pv_tile * rec_bytes + queue_bytes(pv_tile * gpc);
+    // + two constant rows (1 and NaN) for the bulk stores
+    return kOffRecs32 + (size_t)pv_tile * rec_bytes + queue_bytes(pv_tile * gpc) + 2 * kWarpPts * sizeof(float);
 }
+static_assert(kOffRecs32 % 16 == 0, "shared-memory regions must stay 16-byte aligned");
 
 // 128-time groups per CTA of the FP32 kernels.  A function of npt only, so
 // the adjoint's summation order for a pv never depends on the other pvs in

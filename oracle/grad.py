@@ -104,6 +104,21 @@ def _ld_partials(model, mu, coef, table):
         dp = np.stack([-(1.0 - mu ** (nn / 2.0)) for nn in (1, 2, 3, 4)])
         di = np.array([-np.pi * nn / (nn + 4.0) for nn in (1, 2, 3, 4)])
         return dp, di
+    # the remaining named laws are affine in their coefficients: the partials are
+    # the laws' terms and their disk integrals
+    if model == "linear":
+        return np.stack([-(1.0 - mu)]), np.array([-np.pi / 3.0])
+    if model == "general":
+        n = len(coef)
+        dp = np.stack([-(1.0 - mu) ** (j + 1) for j in range(n)])
+        di = np.array([-2.0 * np.pi / ((j + 2.0) * (j + 3.0)) for j in range(n)])
+        return dp, di
+    if model == "logarithmic":
+        mlm = np.where(mu > 0.0, mu * np.log(np.where(mu > 0.0, mu, 1.0)), 0.0)
+        return np.stack([-(1.0 - mu), -mlm]), np.array([-np.pi / 3.0, 2.0 * np.pi / 9.0])
+    if model == "exponential":
+        return (np.stack([-(1.0 - mu), -1.0 / (1.0 - np.exp(mu))]),
+                np.array([-np.pi / 3.0, 2.0 * np.pi * _ld.EXP_C]))
     return np.zeros((0, mu.size)), np.zeros(0)
 
 

@@ -14,10 +14,35 @@ Laws (coefficients per passband):
   quadratic_tri  quadratic with u1 = 2 sqrt(q1) q2, u2 = sqrt(q1) (1 - 2 q2)
                  (Kipping's triangular parametrisation, footnote of Sect. 3.2.1)
   nonlinear      I = 1 - sum_{n=1..4} c_n (1 - mu^(n/2))
+  linear         I = 1 - u (1 - mu)
+  general        I = 1 - sum_{n=1..N} c_n (1 - mu)^n            (N = 1..4)
+  logarithmic    I = 1 - u1 (1 - mu) - u2 mu ln mu
+  exponential    I = 1 - u1 (1 - mu) - u2 / (1 - exp(mu))
+(the laws named in Sect. 3.2.1, written in their usual forms; each is affine
+in its coefficients).  Closed-form disk integrals:
+  linear       pi (1 - u/3)
+  general      pi (1 - sum_n 2 c_n / ((n+1)(n+2)))     [int_0^1 mu (1-mu)^n dmu = 1/((n+1)(n+2))]
+  logarithmic  pi (1 - u1/3 + 2 u2/9)                   [int_0^1 mu^2 ln mu dmu = -1/9]
+  exponential  pi (1 - u1/3) + 2 pi u2 C,  C = int_0^1 mu / (e^mu - 1) dmu
+               = pi^2/6 - Li2(1/e) + ln(1 - 1/e)       [expand 1/(e^mu - 1) = sum_k e^(-k mu)]
 """
 import numpy as np
+from scipy.special import spence
 
-NCOEF = {"uniform": 0, "quadratic": 2, "quadratic_tri": 2, "nonlinear": 4, "tabulated": 0}
+NCOEF = {"uniform": 0, "quadratic": 2, "quadratic_tri": 2, "nonlinear": 4, "tabulated": 0,
+         "linear": 1, "logarithmic": 2, "exponential": 2}
+
+#: int_0^1 mu / (e^mu - 1) dmu; scipy's spence(z) is Li2(1 - z)
+EXP_C = np.pi ** 2 / 6.0 - spence(1.0 - np.exp(-1.0)) + np.log(1.0 - np.exp(-1.0))
+
+
+def ncoef(model: str, n_general: int = 0) -> int:
+    """Coefficients per passband of a law (the general law takes n_general = 1..4)."""
+    if model == "general":
+        if not 1 <= n_general <= 4:
+            raise ValueError("the general law takes 1 to 4 coefficients")
+        return n_general
+    return NCOEF[model]
 
 
 def kipping_to_quadratic(q1, q2):
@@ -43,6 +68,18 @@ def profile(model: str, mu, coef=(), table=None):
     if model == "tabulated":
         tmu, tI = table
         return np.interp(mu, tmu, tI)
+    if model == "linear":
+        (u,) = coef
+        return 1.0 - u * (1.0 - mu)
+    if model == "general":
+        return 1.0 - sum(c * (1.0 - mu) ** (n + 1) for n, c in enumerate(coef))
+    if model == "logarithmic":
+        u1, u2 = coef
+        mlm = np.where(mu > 0.0, mu * np.log(np.where(mu > 0.0, mu, 1.0)), 0.0)
+        return 1.0 - u1 * (1.0 - mu) - u2 * mlm
+    if model == "exponential":
+        u1, u2 = coef
+        return 1.0 - u1 * (1.0 - mu) - u2 / (1.0 - np.exp(mu))
     raise ValueError(f"unknown LD model {model!r}")
 
 
@@ -64,4 +101,15 @@ def istar(model: str, coef=(), table=None) -> float:
         m0, m1, i0, i1 = tmu[:-1], tmu[1:], tI[:-1], tI[1:]
         s += np.sum((m1 - m0) / 6.0 * (i0 * (2.0 * m0 + m1) + i1 * (m0 + 2.0 * m1)))
         return 2.0 * np.pi * s
+    if model == "linear":
+        (u,) = coef
+        return np.pi * (1.0 - u / 3.0)
+    if model == "general":
+        return np.pi * (1.0 - sum(2.0 * c / ((n + 2.0) * (n + 3.0)) for n, c in enumerate(coef)))
+    if model == "logarithmic":
+        u1, u2 = coef
+        return np.pi * (1.0 - u1 / 3.0 + 2.0 * u2 / 9.0)
+    if model == "exponential":
+        u1, u2 = coef
+        return np.pi * (1.0 - u1 / 3.0) + 2.0 * np.pi * u2 * EXP_C
     raise ValueError(f"unknown LD model {model!r}")

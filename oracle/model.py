@@ -66,10 +66,11 @@ class Setup:
     npb: int
     chromatic: bool
     tables: Optional[List[tuple]]
+    n_general: int = 0      # coefficients of the general law
 
     @property
     def nldc(self) -> int:
-        return _ld.NCOEF[self.ld_model]
+        return _ld.ncoef(self.ld_model, self.n_general)
 
     @property
     def nparam(self) -> int:
@@ -86,12 +87,12 @@ def _tables(zcut, nzin, nzlimb, ng, nk, k0, k1):
 
 
 def build(grid: dict, ld_model: str, npb: int = 1, chromatic: bool = False,
-          tables: Optional[Sequence[tuple]] = None) -> Setup:
+          tables: Optional[Sequence[tuple]] = None, n_general: int = 0) -> Setup:
     """Model initialisation: radial grid, mu at the bin means and the (k, g) weight table."""
     ze, zm, mu, dk, dg, w = _tables(grid["zcut"], grid["nzin"], grid["nzlimb"], grid["ng"],
                                     grid["nk"], grid["k0"], grid["k1"])
     return Setup(ze, zm, mu, w, dk, dg, grid["k0"], grid["k1"], grid["nk"], grid["ng"],
-                 ld_model, npb, chromatic, list(tables) if tables is not None else None)
+                 ld_model, npb, chromatic, list(tables) if tables is not None else None, n_general)
 
 
 def unpack(setup: Setup, row: np.ndarray):
@@ -211,6 +212,6 @@ def evaluate(setup: Setup, times, pb_index, params, supersampling, exptime, retu
 def evaluate_workload(wl, setup: Optional[Setup] = None, return_status=False):
     """Oracle flux for a :class:`paper_2009_08500_gb300.workloads.Workload`-shaped object."""
     if setup is None:
-        setup = build(wl.grid, wl.ld_model, wl.npb, wl.chromatic, wl.profiles)
+        setup = build(wl.grid, wl.ld_model, wl.npb, wl.chromatic, wl.profiles, getattr(wl, "n_general", 0))
     return evaluate(setup, wl.times, wl.pb_index, wl.params, wl.supersampling, wl.exptime,
                     return_status=return_status)

@@ -28,8 +28,18 @@ import numpy as np
 
 MINUTE = 1.0 / 1440.0
 
-#: limb-darkening model names and their coefficient counts per passband
-LD_NCOEF = {"uniform": 0, "quadratic": 2, "quadratic_tri": 2, "nonlinear": 4, "tabulated": 0}
+#: limb-darkening model names and their coefficient counts per passband (the
+#: general law takes 1 to 4, given as ``n_general``)
+LD_NCOEF = {"uniform": 0, "quadratic": 2, "quadratic_tri": 2, "nonlinear": 4, "tabulated": 0,
+            "linear": 1, "logarithmic": 2, "exponential": 2}
+
+
+def ld_ncoef(ld_model: str, n_general: int = 0) -> int:
+    if ld_model == "general":
+        if not 1 <= n_general <= 4:
+            raise ValueError("the general law takes 1 to 4 coefficients")
+        return n_general
+    return LD_NCOEF[ld_model]
 
 #: grid settings used by every workload (radial grid of 500 annuli, k grid 0.005-0.3)
 GRID = dict(zcut=0.7, nzin=200, nzlimb=300, ng=200, nk=60, k0=0.005, k1=0.3)
@@ -49,6 +59,7 @@ class Workload:
     precision: str               # "mixed" or "fp64"
     profiles: Optional[List[tuple]] = None   # per passband (mu, I) for tabulated LD
     grid: dict = field(default_factory=lambda: dict(GRID))
+    n_general: int = 0                       # coefficients of the general law
 
     @property
     def npv(self) -> int:
@@ -72,11 +83,11 @@ class Workload:
         return Workload(self.name, self.times[sl].copy(), self.pb_index[sl].copy(),
                         self.params[:npv].copy(), self.supersampling.copy(), self.exptime.copy(),
                         self.ld_model, self.npb, self.chromatic, self.precision,
-                        self.profiles, dict(self.grid))
+                        self.profiles, dict(self.grid), self.n_general)
 
 
-def nparam_for(ld_model: str, npb: int, chromatic: bool) -> int:
-    return 6 + (npb if chromatic else 1) + npb * LD_NCOEF[ld_model]
+def nparam_for(ld_model: str, npb: int, chromatic: bool, n_general: int = 0) -> int:
+    return 6 + (npb if chromatic else 1) + npb * ld_ncoef(ld_model, n_general)
 
 
 def monotone_bernstein_coefficients(rng: np.random.Generator, degree: int, lo: float, hi: float):
@@ -207,7 +218,8 @@ def make_c4(seed: int = 3, npv: int = 2048, per_pb: int = 7500) -> Workload:
 
 def make_small(ld_model: str = "quadratic", npv: int = 3, npt: int = 257, npb: int = 1,
                chromatic: bool = False, ss=(1,), exptime=(0.0,), seed: int = 7,
-               eccentric: bool = True, precision: str = "mixed", span: float = 6.0) -> Workload:
+               eccentric: bool = True, precision: str = "mixed", span: float = 6.0,
+               n_general: int = 0) -> Workload:
     """Small seeded case for parity tests: a few pvs, a ragged number of times."""
     rng = np.random.Generator(np.random.PCG64(seed))
     k = rng.uniform(0.02, 0.25, npv)
@@ -235,13 +247,26 @@ def make_small(ld_model: str = "quadratic", npv: int = 3, npt: int = 257, npb: i
         elif ld_model == "nonlinear":
             c = np.stack([nonlinear_coefficients(rng) for _ in range(npv)])
             cols += [c[:, 0], c[:, 1], c[:, 2], c[:, 3]]
+        elif ld_model == "linear":
+            cols += [rng.uniform(0.1, 0.9, npv)]
+        elif ld_model == "general":
+            # positive, limb-darkened profiles: 1 - sum c_n >= 0.1 at the limb
+            c = np.stack([rng.uniform(0.2, 0.6, npv)] +
+                         [rng.uniform(0.0, 0.2, npv) / n for n in range(2, n_general + 1)], axis=1)
+            c *= np.minimum(1.0, 0.9 / c.sum(axis=1))[:, None]
+            cols += [c[:, j] for j in range(n_general)]
+        elif ld_model == "logarithmic":
+            cols += [rng.uniform(0.2, 0.7, npv), rng.uniform(0.0, 0.3, npv)]
+        elif ld_model == "exponential":
+            cols += [rng.uniform(0.3, 0.6, npv), rng.uniform(0.0, 0.05, npv)]
     if ld_model == "tabulated":
         profiles = [tabulated_profile(rng) for _ in range(npb)]
-    params = np.stack(cols, axis=1) if npv > 0 else np.zeros((0, nparam_for(ld_model, npb, chromatic)))
+    params = (np.stack(cols, axis=1) if npv > 0
+              else np.zeros((0, nparam_for(ld_model, npb, chromatic, n_general))))
     ss_arr = np.array([ss[j % len(ss)] for j in range(npb)], np.int32)
     ex_arr = np.array([exptime[j % len(exptime)] for j in range(npb)], np.float64)
     return Workload(f"small_{ld_model}", times, pb_index, params, ss_arr, ex_arr, ld_model, npb,
-                    chromatic, precision, profiles)
+                    chromatic, precision, profiles, n_general=n_general)
 
 
 @dataclass

@@ -53,13 +53,17 @@ CASES = [
     dict(ld_model="nonlinear", eccentric=True),
     dict(ld_model="tabulated", eccentric=True, npb=2, ss=(1, 5), exptime=(0.0, 0.01)),
     dict(ld_model="quadratic", eccentric=True, npb=2, chromatic=True),
+    dict(ld_model="linear", eccentric=True),
+    dict(ld_model="general", eccentric=True, n_general=3),
+    dict(ld_model="logarithmic", eccentric=True),
+    dict(ld_model="exponential", eccentric=False),
 ]
 
 
 @pytest.mark.parametrize("case", CASES, ids=lambda c: "-".join(f"{v}" for v in c.values()))
 def test_chain_rule_matches_finite_differences(case):
     wl = W.make_small(npv=2, npt=1500, seed=21, span=4.0, **case)
-    s = model.build(wl.grid, wl.ld_model, wl.npb, wl.chromatic, wl.profiles)
+    s = model.build(wl.grid, wl.ld_model, wl.npb, wl.chromatic, wl.profiles, wl.n_general)
     rng = np.random.default_rng(4)
     for p in range(wl.npv):
         row = wl.params[p].copy()

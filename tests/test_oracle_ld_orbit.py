@@ -124,3 +124,43 @@ def test_orbit_against_two_body_integration(e, w):
         z, front, _ = O.projected_distance(T0 + sol.t, T0, P, a, b, e, w)
         np.testing.assert_allclose(z, np.hypot(X, Y), rtol=1e-7, atol=1e-7)
         np.testing.assert_array_equal(front, sol.y[1] > 0)
+
+
+# ---- the remaining named laws (linear, general, logarithmic, exponential) ----
+MORE_LAWS = [("linear", (0.55,)), ("general", (0.4,)), ("general", (0.35, 0.2, 0.05)),
+             ("general", (0.3, 0.1, 0.05, 0.02)), ("logarithmic", (0.5, 0.2)), ("exponential", (0.45, 0.03))]
+
+
+@pytest.mark.parametrize("model,coef", MORE_LAWS)
+def test_more_laws_istar_closed_form_matches_quadrature(model, coef):
+    # mu I(mu) is finite at mu = 0 for every law (the exponential law's 1/mu term included)
+    f = lambda m: m * ld.profile(model, m, coef) if m > 0 else (coef[1] if model == "exponential" else 0.0)  # noqa: E731
+    ref = 2 * np.pi * quad(f, 0, 1, epsabs=1e-14, epsrel=1e-13, limit=200)[0]
+    assert ld.istar(model, coef) == pytest.approx(ref, rel=1e-11)
+
+
+def test_exponential_constant_against_quadrature():
+    ref = quad(lambda m: m / np.expm1(m) if m > 0 else 1.0, 0, 1, epsabs=1e-15, epsrel=1e-14)[0]
+    assert ld.EXP_C == pytest.approx(ref, rel=1e-14)
+    assert ld.EXP_C == pytest.approx(0.7775046341122, rel=1e-12)
+
+
+def test_more_laws_reduce_to_known_ones():
+    mu = np.linspace(0.0, 1.0, 101)
+    q = (0.4, 0.25)
+    # general with two coefficients is the quadratic law; with one, the linear law
+    assert np.allclose(ld.profile("general", mu, q), ld.profile("quadratic", mu, q), atol=1e-15)
+    assert ld.istar("general", q) == pytest.approx(ld.istar("quadratic", q), rel=1e-15)
+    assert np.allclose(ld.profile("general", mu, (0.3,)), ld.profile("linear", mu, (0.3,)), atol=1e-15)
+    # linear is the quadratic law without its second term
+    assert np.allclose(ld.profile("linear", mu, (0.3,)), ld.profile("quadratic", mu, (0.3, 0.0)), atol=1e-15)
+    assert ld.istar("linear", (0.3,)) == pytest.approx(ld.istar("quadratic", (0.3, 0.0)), rel=1e-15)
+    # logarithmic and exponential laws with a zero second coefficient are the linear law
+    for m in ("logarithmic", "exponential"):
+        assert np.allclose(ld.profile(m, mu[1:], (0.3, 0.0)), ld.profile("linear", mu[1:], (0.3,)), atol=1e-15)
+        assert ld.istar(m, (0.3, 0.0)) == pytest.approx(ld.istar("linear", (0.3,)), rel=1e-15)
+    # the logarithmic term vanishes at the centre and the limb, the laws give 1 at the centre
+    for m, c in MORE_LAWS:
+        if m != "exponential":
+            assert ld.profile(m, 1.0, c) == pytest.approx(1.0, abs=1e-15)
+    assert ld.profile("logarithmic", 0.0, (0.5, 0.2)) == pytest.approx(0.5)

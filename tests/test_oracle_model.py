@@ -44,11 +44,13 @@ def test_quadratic_within_paper_error_level_of_exact_integral(k, grid):
     assert errs.mean() < 1e-6
 
 
-@pytest.mark.parametrize("model_name,coef", [("nonlinear", (0.5, -0.2, 0.6, -0.25)), ("tabulated", ())])
+@pytest.mark.parametrize("model_name,coef", [("nonlinear", (0.5, -0.2, 0.6, -0.25)), ("tabulated", ()),
+                                             ("linear", (0.6,)), ("general", (0.35, 0.2, 0.05)),
+                                             ("logarithmic", (0.5, 0.2)), ("exponential", (0.45, 0.03))])
 def test_other_profiles_match_exact_integral(model_name, coef, grid):
     rng = np.random.Generator(np.random.PCG64(9))
     table = W.tabulated_profile(rng)
-    s = model.build(grid, model_name, tables=[table])
+    s = model.build(grid, model_name, tables=[table], n_general=len(coef) if model_name == "general" else 0)
     I = lambda m: ld.profile(model_name, m, coef, table)  # noqa: E731
     istar = ld.istar(model_name, coef, table)
     for k in (0.05, 0.2):

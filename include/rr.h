@@ -51,14 +51,20 @@ typedef enum {
     RR_ETIMEOUT = 6   /* a bounded device-side wait gave up (see rr_last_error) */
 } rr_status;
 
-/* Limb-darkening laws (Sect. 3.2.1) and the tabulated numerical profile (Sect. 3.2.2). */
+/* Limb-darkening laws (Sect. 3.2.1, in their usual forms; all affine in their
+ * coefficients, with closed-form disk integrals) and the tabulated numerical
+ * profile (Sect. 3.2.2). */
 typedef enum {
     RR_LD_UNIFORM = 0,        /* I = 1                                      0 coefficients */
     RR_LD_QUADRATIC = 1,      /* I = 1 - u1 (1-mu) - u2 (1-mu)^2            2 (u1, u2)     */
     RR_LD_QUADRATIC_TRI = 2,  /* quadratic with u1 = 2 sqrt(q1) q2,
                                  u2 = sqrt(q1) (1 - 2 q2) (Kipping)         2 (q1, q2)     */
     RR_LD_NONLINEAR = 3,      /* I = 1 - sum_n c_n (1 - mu^(n/2)), n=1..4   4 (c1..c4)     */
-    RR_LD_TABULATED = 4       /* I(mu) given per passband by rr_set_ld_profile   0        */
+    RR_LD_TABULATED = 4,      /* I(mu) given per passband by rr_set_ld_profile   0        */
+    RR_LD_LINEAR = 5,         /* I = 1 - u (1-mu)                           1 (u)          */
+    RR_LD_GENERAL = 6,        /* I = 1 - sum_n c_n (1-mu)^n, n=1..N         N = rr_config.ncoef, 1..4 */
+    RR_LD_LOGARITHMIC = 7,    /* I = 1 - u1 (1-mu) - u2 mu ln(mu)           2 (u1, u2)     */
+    RR_LD_EXPONENTIAL = 8     /* I = 1 - u1 (1-mu) - u2 / (1 - exp(mu))     2 (u1, u2)     */
 } rr_ld_model;
 
 typedef enum {
@@ -91,6 +97,7 @@ typedef struct {
     int32_t chromatic;  /* 0: one k per pv; 1: one k per passband (Sect. 4.2) */
     int32_t precision;  /* rr_precision */
     int32_t device;     /* CUDA device ordinal */
+    int32_t ncoef;      /* terms of RR_LD_GENERAL (1..4); 0 for every other law */
 } rr_config;
 
 /* Create a context: validates `cfg`, builds the radial grid of Sect. 3.1.1 on

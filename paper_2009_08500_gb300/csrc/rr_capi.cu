@@ -23,11 +23,15 @@ rr_status cuda_fail(rr_ctx* c, cudaError_t e, const char* where) {
     return fail(c, RR_ECUDA, m);
 }
 
-int ncoef(int model) {
+int ncoef(int model, int n_general) {
     switch (model) {
         case RR_LD_QUADRATIC:
-        case RR_LD_QUADRATIC_TRI: return 2;
+        case RR_LD_QUADRATIC_TRI:
+        case RR_LD_LOGARITHMIC:
+        case RR_LD_EXPONENTIAL: return 2;
         case RR_LD_NONLINEAR: return 4;
+        case RR_LD_LINEAR: return 1;
+        case RR_LD_GENERAL: return n_general;
         default: return 0;
     }
 }
@@ -284,7 +288,9 @@ rr_status rr_create(const rr_config* cfg, rr_ctx** out) {
     if (k.nk < 2 || k.nk > 4096) return fail(nullptr, RR_EINVAL, "nk must be in [2, 4096]");
     if (!(k.k0 > 0.0 && k.k0 < k.k1 && k.k1 < 1.0)) return fail(nullptr, RR_EINVAL, "need 0 < k0 < k1 < 1");
     if (k.npb < 1 || k.npb > RR_MAX_PB) return fail(nullptr, RR_EINVAL, "npb must be in [1, 32]");
-    if (k.ld_model < RR_LD_UNIFORM || k.ld_model > RR_LD_TABULATED) return fail(nullptr, RR_EINVAL, "unknown ld_model");
+    if (k.ld_model < RR_LD_UNIFORM || k.ld_model > RR_LD_EXPONENTIAL) return fail(nullptr, RR_EINVAL, "unknown ld_model");
+    if (k.ld_model == RR_LD_GENERAL ? (k.ncoef < 1 || k.ncoef > 4) : k.ncoef != 0)
+        return fail(nullptr, RR_EINVAL, "ncoef must be 1..4 for RR_LD_GENERAL and 0 otherwise");
     if (k.precision != RR_PREC_FP64 && k.precision != RR_PREC_MIXED) return fail(nullptr, RR_EINVAL, "unknown precision");
     if (k.chromatic != 0 && k.chromatic != 1) return fail(nullptr, RR_EINVAL, "chromatic must be 0 or 1");
     int ndev = 0;
@@ -298,7 +304,7 @@ rr_status rr_create(const rr_config* cfg, rr_ctx** out) {
     c->cfg = k;
     cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, k.device);
     c->nz = k.nzin + k.nzlimb;
-    c->nldc = ncoef(k.ld_model);
+    c->nldc = ncoef(k.ld_model, k.ncoef);
     c->nbasis = k.ld_model == RR_LD_TABULATED ? k.npb : 1 + c->nldc;
     c->nkp = k.chromatic ? k.npb : 1;
     c->nparam = 6 + c->nkp + k.npb * c->nldc;

@@ -126,6 +126,7 @@ struct ModelParams {
     int32_t ld_model, npb, chromatic, nldc, nparam, nk, ng, nbasis;
     double k0, k1, dk;
     double inv_dk;   // 1 / dk (host FP64)
+    double exp_c;    // int_0^1 mu / (e^mu - 1) dmu (disk integral of the exponential law's second term)
 };
 
 }  // namespace rr

@@ -48,21 +48,33 @@ __global__ void __launch_bounds__(256) rr_ld_basis_kernel(ModelParams mp, const 
             const double m = mu[j];
             double v = 1.0;
             if (b > 0) {
-                if (mp.ld_model == RR_LD_NONLINEAR)
-                    v = -(1.0 - pow(m, 0.5 * b));
-                else
-                    v = (b == 1) ? -(1.0 - m) : -(1.0 - m) * (1.0 - m);
+                switch (mp.ld_model) {
+                    case RR_LD_NONLINEAR: v = -(1.0 - pow(m, 0.5 * b)); break;
+                    case RR_LD_GENERAL: v = -pow(1.0 - m, (double)b); break;
+                    case RR_LD_LOGARITHMIC: v = b == 1 ? -(1.0 - m) : -m * log(m); break;
+                    case RR_LD_EXPONENTIAL: v = b == 1 ? -(1.0 - m) : -1.0 / (1.0 - exp(m)); break;
+                    default: v = (b == 1) ? -(1.0 - m) : -(1.0 - m) * (1.0 - m);   // linear, quadratic
+                }
             }
             out[j] = v;
         }
         if (threadIdx.x == 0) {
+            // 2 pi int_0^1 mu basis(mu) dmu, closed forms
             double I;
             if (b == 0)
                 I = CUDART_PI;
             else if (mp.ld_model == RR_LD_NONLINEAR)
                 I = -CUDART_PI * b / (b + 4.0);
+            else if (mp.ld_model == RR_LD_GENERAL)
+                I = -2.0 * CUDART_PI / ((b + 1.0) * (b + 2.0));
+            else if (b == 1)
+                I = -CUDART_PI / 3.0;
+            else if (mp.ld_model == RR_LD_LOGARITHMIC)
+                I = 2.0 * CUDART_PI / 9.0;
+            else if (mp.ld_model == RR_LD_EXPONENTIAL)
+                I = 2.0 * CUDART_PI * mp.exp_c;
             else
-                I = (b == 1) ? -CUDART_PI / 3.0 : -CUDART_PI / 6.0;
+                I = -CUDART_PI / 6.0;
             istar[b] = I;
         }
         return;
@@ -566,6 +578,14 @@ ModelParams model_params(const rr_ctx* c) {
     mp.k1 = c->cfg.k1;
     mp.dk = c->dk;
     mp.inv_dk = 1.0 / c->dk;
+    // int_0^1 mu / (e^mu - 1) dmu = pi^2/6 - Li2(1/e) + ln(1 - 1/e) (expand 1/(e^mu - 1) = sum_k e^(-k mu));
+    // Li2(1/e) = sum_k e^(-k) / k^2, 40 terms below 1e-18
+    double li2 = 0.0, p = 1.0;
+    for (int j = 1; j <= 40; ++j) {
+        p *= std::exp(-1.0);
+        li2 += p / ((double)j * j);
+    }
+    mp.exp_c = CUDART_PI * CUDART_PI / 6.0 - li2 + std::log(1.0 - std::exp(-1.0));
     return mp;
 }
 

@@ -18,7 +18,8 @@ import torch
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "librr.so")
 
-LD_MODELS = {"uniform": 0, "quadratic": 1, "quadratic_tri": 2, "nonlinear": 3, "tabulated": 4}
+LD_MODELS = {"uniform": 0, "quadratic": 1, "quadratic_tri": 2, "nonlinear": 3, "tabulated": 4, "linear": 5,
+             "general": 6, "logarithmic": 7, "exponential": 8}
 PRECISIONS = {"fp64": 0, "mixed": 1}
 STATUS = {0: "RR_OK", 1: "RR_EINVAL", 2: "RR_ENOMEM", 3: "RR_ECUDA", 4: "RR_ESTATE", 6: "RR_ETIMEOUT"}
 TABLES = {"ze": 0, "zm": 1, "mu": 2, "weights": 3, "basis": 4, "istar": 5, "proj": 6}
@@ -39,7 +40,8 @@ class RRConfig(ctypes.Structure):
     _fields_ = [("zcut", ctypes.c_double), ("nzin", ctypes.c_int32), ("nzlimb", ctypes.c_int32),
                 ("ng", ctypes.c_int32), ("nk", ctypes.c_int32), ("k0", ctypes.c_double),
                 ("k1", ctypes.c_double), ("npb", ctypes.c_int32), ("ld_model", ctypes.c_int32),
-                ("chromatic", ctypes.c_int32), ("precision", ctypes.c_int32), ("device", ctypes.c_int32)]
+                ("chromatic", ctypes.c_int32), ("precision", ctypes.c_int32), ("device", ctypes.c_int32),
+                ("ncoef", ctypes.c_int32)]
 
 
 class RRError(RuntimeError):
@@ -117,14 +119,16 @@ def _host_array(x, n, dtype, default):
 class Model:
     """A RoadRunner model context: radial grid, LD profiles and (k, g) tables on one GPU.
 
-    ld_model   'uniform' | 'quadratic' | 'quadratic_tri' | 'nonlinear' | 'tabulated'
+    ld_model   'uniform' | 'quadratic' | 'quadratic_tri' | 'nonlinear' | 'tabulated' | 'linear' |
+               'general' | 'logarithmic' | 'exponential'
     npb        passbands; chromatic: one radius ratio per passband
     precision  'mixed' (FP32 bulk, float flux) or 'fp64' (double flux)
     grid       dict(zcut, nzin, nzlimb, ng, nk, k0, k1)
+    n_general  terms of the general law (1..4)
     """
 
     def __init__(self, ld_model: str = "quadratic", npb: int = 1, chromatic: bool = False,
-                 precision: str = "mixed", grid: Optional[dict] = None, device: int = 0):
+                 precision: str = "mixed", grid: Optional[dict] = None, device: int = 0, n_general: int = 0):
         from .workloads import GRID
         g = dict(GRID if grid is None else grid)
         self.lib = load_library()
@@ -134,7 +138,8 @@ class Model:
         self.ld_model, self.npb, self.chromatic, self.precision = ld_model, npb, chromatic, precision
         self.grid = g
         cfg = RRConfig(g["zcut"], g["nzin"], g["nzlimb"], g["ng"], g["nk"], g["k0"], g["k1"], npb,
-                       LD_MODELS[ld_model], int(chromatic), PRECISIONS[precision], device)
+                       LD_MODELS[ld_model], int(chromatic), PRECISIONS[precision], device,
+                       int(n_general) if ld_model == "general" else 0)
         h = ctypes.c_void_p()
         st = self.lib.rr_create(ctypes.byref(cfg), ctypes.byref(h))
         if st != 0:
@@ -407,7 +412,7 @@ class _RRFlux(torch.autograd.Function):
 
 def model_for(wl, device: int = 0) -> Model:
     """Model context for a :class:`workloads.Workload`, with profiles set and tables built."""
-    m = Model(wl.ld_model, wl.npb, wl.chromatic, wl.precision, wl.grid, device)
+    m = Model(wl.ld_model, wl.npb, wl.chromatic, wl.precision, wl.grid, device, getattr(wl, "n_general", 0))
     if wl.ld_model == "tabulated":
         for pb, (mu, it) in enumerate(wl.profiles):
             m.set_ld_profile(pb, mu, it)

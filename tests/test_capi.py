@@ -57,6 +57,14 @@ def test_create_rejects_bad_config_before_touching_the_device(lib, field, value,
     assert msg in lib.rr_last_error(None)
 
 
+@pytest.mark.parametrize("ld_model,ncoef", [(6, 0), (6, 5), (1, 2), (8, 1)])
+def test_create_checks_the_general_law_term_count(lib, ld_model, ncoef):
+    cfg = rr.RRConfig(0.7, 200, 300, 200, 60, 0.005, 0.3, 1, ld_model, 0, 1, 0, ncoef)
+    out = ctypes.c_void_p()
+    assert lib.rr_create(ctypes.byref(cfg), ctypes.byref(out)) == 1
+    assert b"ncoef" in lib.rr_last_error(None)
+
+
 def test_status_bits_match_the_oracle():
     from oracle import model as om
     assert (rr.PV_K_RANGE, rr.PV_E_RANGE, rr.PV_B_RANGE, rr.PV_P_RANGE, rr.PV_NONFINITE, rr.PV_LD_INVALID,

@@ -56,7 +56,7 @@ def gpu_vjp(rr, wl, gbar, precision):
 
 def oracle_vjp(wl, gbar):
     """Oracle gradient and the condition scale S of every component."""
-    s = om.build(wl.grid, wl.ld_model, wl.npb, wl.chromatic, wl.profiles)
+    s = om.build(wl.grid, wl.ld_model, wl.npb, wl.chromatic, wl.profiles, wl.n_general)
     gbar = np.asarray(gbar, np.float64)
     ref = np.zeros(wl.params.shape)
     scale = np.zeros(wl.params.shape)
@@ -75,6 +75,11 @@ CASES = [
     dict(ld_model="tabulated", eccentric=True, npb=3, ss=(1, 4, 9), exptime=(0.0, 0.01, 0.02)),
     dict(ld_model="quadratic", eccentric=True, npb=2, chromatic=True, ss=(3, 1), exptime=(0.01, 0.0)),
     dict(ld_model="uniform", eccentric=True),
+    dict(ld_model="linear", eccentric=True),
+    dict(ld_model="general", eccentric=True, n_general=3),
+    dict(ld_model="logarithmic", eccentric=True),
+    dict(ld_model="exponential", eccentric=True, ss=(5,), exptime=(0.01,)),
+    dict(ld_model="general", eccentric=True, npb=2, chromatic=True, n_general=2),
 ]
 
 

@@ -41,16 +41,18 @@ def gpu_flux(rr, wl, precision=None):
 
 
 def oracle_flux(wl):
-    setup = om.build(wl.grid, wl.ld_model, wl.npb, wl.chromatic, wl.profiles)
+    setup = om.build(wl.grid, wl.ld_model, wl.npb, wl.chromatic, wl.profiles, wl.n_general)
     return om.evaluate_workload(wl, setup, return_status=True)
 
 
 # ----------------------------------------------------------------- set-up tables
-@pytest.mark.parametrize("ld_model", ["quadratic", "nonlinear", "tabulated"])
+@pytest.mark.parametrize("ld_model", ["quadratic", "nonlinear", "tabulated", "linear", "general", "logarithmic",
+                                      "exponential"])
 def test_setup_tables_match_oracle(rr, ld_model):
-    wl = W.make_small(ld_model, npv=1, npt=4, npb=2 if ld_model == "tabulated" else 1, seed=3)
+    wl = W.make_small(ld_model, npv=1, npt=4, npb=2 if ld_model == "tabulated" else 1, seed=3,
+                      n_general=3 if ld_model == "general" else 0)
     m = rr.model_for(wl)
-    s = om.build(wl.grid, wl.ld_model, wl.npb, wl.chromatic, wl.profiles)
+    s = om.build(wl.grid, wl.ld_model, wl.npb, wl.chromatic, wl.profiles, wl.n_general)
     np.testing.assert_allclose(m.read_table("ze"), s.ze, rtol=0, atol=2e-16)
     np.testing.assert_allclose(m.read_table("mu"), s.mu, rtol=0, atol=2e-16)
     w = m.read_table("weights").reshape(s.w.shape)
@@ -68,14 +70,14 @@ def test_setup_tables_match_oracle(rr, ld_model):
         refb = np.stack([old.profile("tabulated", s.mu, table=tb) for tb in wl.profiles])
         refi = np.array([old.istar("tabulated", table=tb) for tb in wl.profiles])
     else:
-        nc = old.NCOEF[ld_model]
+        nc = old.ncoef(ld_model, wl.n_general)
         # basis c = I(coefficient vector e_c) - I(0): the law is affine in its coefficients
         zero = old.profile(ld_model, s.mu, (0.0,) * nc)
         refb = [zero] + [old.profile(ld_model, s.mu, tuple(np.eye(nc)[c])) - zero for c in range(nc)]
         refb = np.stack(refb)
         i0 = old.istar(ld_model, (0.0,) * nc)
         refi = np.array([i0] + [old.istar(ld_model, tuple(np.eye(nc)[c])) - i0 for c in range(nc)])
-    np.testing.assert_allclose(basis, refb, rtol=0, atol=1e-15)
+    np.testing.assert_allclose(basis, refb, rtol=1e-14, atol=1e-15)
     np.testing.assert_allclose(istar, refi, rtol=1e-13, atol=1e-15)
     proj = m.read_table("proj").reshape(len(refb), s.nk, s.ng)
     np.testing.assert_allclose(proj, np.einsum("kgz,bz->bkg", s.w, refb), rtol=0, atol=1e-13)
@@ -96,7 +98,10 @@ CASES = []
 for _ld in ("uniform", "quadratic", "quadratic_tri", "nonlinear", "tabulated"):
     for _ecc in (False, True):
         CASES.append(dict(ld_model=_ld, eccentric=_ecc))
+CASES += [dict(ld_model=_ld, eccentric=True) for _ld in ("linear", "logarithmic", "exponential")]
 CASES += [
+    dict(ld_model="general", eccentric=True, n_general=4),
+    dict(ld_model="general", npb=2, n_general=2, ss=(1, 6), exptime=(0.0, 0.01)),
     dict(ld_model="quadratic", npb=3, chromatic=True, ss=(1, 4, 7), exptime=(0.0, 0.01, 0.02)),
     dict(ld_model="nonlinear", npb=2, ss=(5, 2), exptime=(0.02, 0.005)),
     dict(ld_model="tabulated", npb=4, ss=(1, 10, 30, 3), exptime=(0.001, 0.007, 0.021, 0.01)),

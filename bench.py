@@ -483,7 +483,7 @@ def run_serving(a):
 
     from paper_2009_08500_gb300 import rr
     from paper_2009_08500_gb300 import workloads as W
-    from paper_2009_08500_gb300.serve import CudaBackend, Server, ServeRequest
+    from paper_2009_08500_gb300.serve import NativeServer, ServeRequest
 
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
@@ -514,18 +514,20 @@ def run_serving(a):
                          pb_index=pin(wl.pb_index, np.int32), supersampling=wl.supersampling, exptime=wl.exptime,
                          grad_flux=gbuf[:wl.npv * wl.npt].view(wl.npv, wl.npt) if grad else None))
     slots = 8
-    backend = CudaBackend(models, slots=slots, device=local)
+
+    def server():
+        return NativeServer(models, slots=slots, mem_budget=64 << 30, device=local)
 
     def mk(k):
         return ServeRequest(**pool[k % len(pool)])
 
     # warm-up (pinned-memory caches, kernels)
-    with Server(backend, slots=slots, mem_budget=64 << 30) as srv:
+    with server() as srv:
         for k in range(len(pool)):
             srv.submit(mk(k))
         srv.drain()
     # capacity: keep 2 x slots requests outstanding for serve_seconds
-    with Server(backend, slots=slots, mem_budget=64 << 30) as srv:
+    with server() as srv:
         t_end = time.perf_counter() + a.serve_seconds
         k = 0
         outstanding = []
@@ -542,7 +544,7 @@ def run_serving(a):
     for load in (0.7, 1.1):
         rate = load * closed["points_per_s"] / mean_pts
         arr = np.cumsum(rng.exponential(1.0 / rate, size=int(rate * a.serve_seconds) + 1))
-        with Server(backend, slots=slots, mem_budget=64 << 30) as srv:
+        with server() as srv:
             t0 = time.perf_counter()
             for i, ta in enumerate(arr):
                 dt = ta - (time.perf_counter() - t0)
@@ -556,6 +558,7 @@ def run_serving(a):
             "steps": None, "warmup": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32+f64", "data": "synthetic (seeded; paper-shaped)",
             "config": {"workload": f"c5: {CONFIG_TEXT['c5']}", "fits": len(fits), "slots": slots,
+                       "server": "rr_server (scheduler thread in the library)",
                        "request_pool": len(pool), "mean_points_per_request": mean_pts,
                        "serve_seconds": a.serve_seconds},
             "capacity_closed_loop": closed,

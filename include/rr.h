@@ -285,6 +285,38 @@ rr_status rr_enqueue_host(rr_ctx* ctx, const double* times, const int32_t* pb_in
                           const double* exptime, const void* grad_flux, void* flux, double* grad_params,
                           int32_t* pv_status, void* scratch, size_t scratch_bytes, void* stream);
 
+/* Continuous-batching server (no counterpart in the paper): a worker thread
+ * in the library admits queued requests in arrival order whenever one of its
+ * `slots` streams is free and the request's device bytes (rr_request_bytes)
+ * fit in `mem_budget`; each admitted request is enqueued with
+ * rr_enqueue_host on its own stream, with device memory from a stream-ordered
+ * pool of the server; completion is detected by polling events.  Work of
+ * requests admitted at different times overlaps on the device, and a
+ * request's results are those it would have alone.
+ *   - While a context is used by a server, no other thread may call the
+ *     library with that context.
+ *   - Host buffers: page-locked, untouched by the caller until the request
+ *     is reported finished by rr_server_poll.
+ *   - rr_server_submit copies supersampling / exptime and returns the
+ *     request id (>= 0), or a negative rr_status: -RR_EINVAL (arguments),
+ *     -RR_ENOMEM (larger than the budget), -RR_ESTATE (server stopping).
+ *   - rr_server_poll hands over up to `max` finished requests (waiting up to
+ *     timeout_us for the first): ids, their rr_status, and per request three
+ *     steady-clock times in ns (submitted, admitted, finished); returns the
+ *     count, or a negative rr_status.
+ *   - rr_server_destroy finishes every queued request first. */
+typedef struct rr_server rr_server;
+rr_status rr_server_create(int32_t device, int32_t slots, size_t mem_budget, rr_server** out);
+rr_status rr_server_destroy(rr_server* server);
+int64_t rr_server_submit(rr_server* server, rr_ctx* fit, const double* times, const int32_t* pb_index,
+                         int32_t npt, const double* params, int32_t npv, const int32_t* supersampling,
+                         const double* exptime, const void* grad_flux, void* flux, double* grad_params,
+                         int32_t* pv_status);
+int32_t rr_server_poll(rr_server* server, int64_t* ids, int32_t* status, int64_t* times_ns, int32_t max,
+                       int32_t timeout_us);
+/* Requests submitted and not yet handed over by rr_server_poll, minus those finished. */
+int32_t rr_server_pending(rr_server* server);
+
 /* Copy a set-up table to host memory (for inspection and tests); returns the
  * element count of the table, or -1 on error.  `out` may be NULL to query
  * the size; otherwise it receives min(count, capacity) doubles.

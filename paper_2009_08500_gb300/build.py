@@ -12,7 +12,7 @@ from concurrent.futures import ThreadPoolExecutor
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "librr.so")
-SOURCES = ["rr_capi.cu", "rr_setup.cu", "rr_flux.cu", "rr_grad.cu", "rr_host.cu", "rr_noalloc.cu"]
+SOURCES = ["rr_capi.cu", "rr_setup.cu", "rr_flux.cu", "rr_grad.cu", "rr_host.cu", "rr_server.cu", "rr_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # host code: no FMA contraction, so that the FP64 grid is identical on x86 and Arm hosts
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
@@ -42,7 +42,7 @@ def build(verbose: bool = False) -> str:
     with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(lambda s: _compile(s, build_dir, verbose), SOURCES))
     tmp = OUT + ".tmp"
-    cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs]
+    cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lpthread"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")

@@ -1,0 +1,263 @@
+// Continuous-batching evaluation server in the library (a worker thread).
+//
+// Requests (one fit's light curves for a batch of parameter vectors, host
+// buffers, optionally with a cotangent for the adjoint) are queued by any
+// host thread.  The worker admits them in arrival order whenever one of the
+// server's streams is free and the request's device bytes (inputs, outputs,
+// workspace: rr_request_bytes) fit in the memory budget; it takes that memory
+// from a stream-ordered pool on the request's stream, enqueues the request
+// (rr_enqueue_host), records an event, and returns the memory on the same
+// stream.  Completion is detected by polling the events; finished requests
+// are handed to rr_server_poll.  Work of requests admitted at different
+// times overlaps on the device; each request runs the same kernels as it
+// would alone, so its results do not depend on the others.
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "rr_internal.h"
+
+namespace {
+
+int64_t now_ns() {
+    return std::chrono::duration_cast<std::chrono::nanoseconds>(std::chrono::steady_clock::now().time_since_epoch())
+        .count();
+}
+
+struct Request {
+    int64_t id = 0;
+    rr_ctx* fit = nullptr;
+    const double* times = nullptr;
+    const int32_t* pb = nullptr;
+    int32_t npt = 0;
+    const double* params = nullptr;
+    int32_t npv = 0;
+    std::vector<int32_t> ss;
+    std::vector<double> exptime;
+    const void* grad_flux = nullptr;
+    void* flux = nullptr;
+    double* grad = nullptr;
+    int32_t* status = nullptr;
+    size_t bytes = 0;
+    int64_t t_submit = 0, t_admit = 0, t_done = 0;
+    int32_t result = RR_OK;
+};
+
+struct Slot {
+    cudaStream_t stream = nullptr;
+    cudaEvent_t done = nullptr;
+    int64_t req = -1;   // request in flight, -1 = free
+};
+
+}  // namespace
+
+struct rr_server {
+    int device = 0;
+    size_t budget = 0, used = 0;
+    cudaMemPool_t pool = nullptr;
+    std::vector<Slot> slots;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<int64_t> queue;                       // waiting for admission, arrival order
+    std::deque<int64_t> finished;                    // completed, not yet polled
+    std::unordered_map<int64_t, Request> reqs;       // every request not yet released
+    int64_t next_id = 0;
+    bool stop = false;
+    std::thread worker;
+    std::string err;
+};
+
+namespace {
+
+// Admit and launch queued requests while a slot and memory are free (lock held).
+void admit(rr_server* s) {
+    while (!s->queue.empty()) {
+        Request& r = s->reqs[s->queue.front()];
+        if (s->used + r.bytes > s->budget) break;        // in order: wait for memory
+        int slot = -1;
+        for (size_t i = 0; i < s->slots.size(); ++i)
+            if (s->slots[i].req < 0) { slot = (int)i; break; }
+        if (slot < 0) break;
+        s->queue.pop_front();
+        Slot& sl = s->slots[slot];
+        r.t_admit = now_ns();
+        void* scratch = nullptr;
+        cudaError_t e = cudaMallocFromPoolAsync(&scratch, r.bytes > 0 ? r.bytes : 256, s->pool, sl.stream);
+        if (e == cudaSuccess) {
+            r.result = rr_enqueue_host(r.fit, r.times, r.pb, r.npt, r.params, r.npv, r.ss.data(), r.exptime.data(),
+                                       r.grad_flux, r.flux, r.grad, r.status, scratch, r.bytes > 0 ? r.bytes : 256,
+                                       sl.stream);
+            cudaFreeAsync(scratch, sl.stream);
+        } else {
+            r.result = RR_ENOMEM;
+        }
+        if ((e = cudaEventRecord(sl.done, sl.stream)) != cudaSuccess && r.result == RR_OK) r.result = RR_ECUDA;
+        s->used += r.bytes;
+        sl.req = r.id;
+    }
+}
+
+// Hand over requests whose stream has passed them (lock held).
+void reap(rr_server* s) {
+    for (Slot& sl : s->slots) {
+        if (sl.req < 0) continue;
+        const cudaError_t q = cudaEventQuery(sl.done);
+        if (q == cudaErrorNotReady) continue;
+        Request& r = s->reqs[sl.req];
+        if (q != cudaSuccess && r.result == RR_OK) r.result = RR_ECUDA;
+        r.t_done = now_ns();
+        s->used -= r.bytes;
+        s->finished.push_back(r.id);
+        sl.req = -1;
+        s->cv_done.notify_all();
+    }
+}
+
+void run(rr_server* s) {
+    cudaSetDevice(s->device);
+    std::unique_lock<std::mutex> lk(s->mu);
+    while (true) {
+        reap(s);
+        admit(s);
+        bool busy = false;
+        for (const Slot& sl : s->slots) busy = busy || sl.req >= 0;
+        if (s->stop && !busy && s->queue.empty()) return;
+        if (!busy && s->queue.empty()) {
+            s->cv_work.wait_for(lk, std::chrono::milliseconds(20));
+            continue;
+        }
+        // requests in flight: poll again shortly (the lock is free meanwhile)
+        lk.unlock();
+        std::this_thread::sleep_for(std::chrono::microseconds(20));
+        lk.lock();
+    }
+}
+
+}  // namespace
+
+extern "C" rr_status rr_server_create(int32_t device, int32_t slots, size_t mem_budget, rr_server** out) {
+    if (!out) return RR_EINVAL;
+    *out = nullptr;
+    if (slots < 1 || slots > 64 || mem_budget == 0) return RR_EINVAL;
+    if (cudaSetDevice(device) != cudaSuccess) return RR_ECUDA;
+    rr_server* s = new (std::nothrow) rr_server();
+    if (!s) return RR_ENOMEM;
+    s->device = device;
+    s->budget = mem_budget;
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = device;
+    cudaError_t e = cudaMemPoolCreate(&s->pool, &props);
+    if (e == cudaSuccess) {
+        // keep the pool's memory between requests (up to the budget)
+        uint64_t keep = mem_budget;
+        e = cudaMemPoolSetAttribute(s->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    s->slots.resize(slots);
+    for (Slot& sl : s->slots) {
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess) {
+        for (Slot& sl : s->slots) {
+            if (sl.stream) cudaStreamDestroy(sl.stream);
+            if (sl.done) cudaEventDestroy(sl.done);
+        }
+        if (s->pool) cudaMemPoolDestroy(s->pool);
+        delete s;
+        return RR_ECUDA;
+    }
+    s->worker = std::thread(run, s);
+    *out = s;
+    return RR_OK;
+}
+
+extern "C" rr_status rr_server_destroy(rr_server* s) {
+    if (!s) return RR_OK;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->stop = true;
+    }
+    s->cv_work.notify_all();
+    if (s->worker.joinable()) s->worker.join();
+    cudaSetDevice(s->device);
+    for (Slot& sl : s->slots) {
+        cudaStreamSynchronize(sl.stream);
+        cudaStreamDestroy(sl.stream);
+        cudaEventDestroy(sl.done);
+    }
+    cudaMemPoolDestroy(s->pool);
+    delete s;
+    return RR_OK;
+}
+
+extern "C" int64_t rr_server_submit(rr_server* s, rr_ctx* fit, const double* times, const int32_t* pb_index,
+                                    int32_t npt, const double* params, int32_t npv, const int32_t* ss,
+                                    const double* exptime, const void* grad_flux, void* flux, double* grad_params,
+                                    int32_t* pv_status) {
+    if (!s || !fit || !ss || !exptime || npt < 0 || npv < 0 || (npv > 0 && !params) ||
+        (npv > 0 && npt > 0 && (!times || !flux)) || (grad_flux && !grad_params))
+        return -RR_EINVAL;
+    Request r;
+    r.fit = fit;
+    r.times = times;
+    r.pb = pb_index;
+    r.npt = npt;
+    r.params = params;
+    r.npv = npv;
+    r.ss.assign(ss, ss + fit->cfg.npb);
+    r.exptime.assign(exptime, exptime + fit->cfg.npb);
+    r.grad_flux = grad_flux;
+    r.flux = flux;
+    r.grad = grad_params;
+    r.status = pv_status;
+    r.bytes = rr_request_bytes(fit, npv, npt, grad_flux ? 1 : 0);
+    if (r.bytes > s->budget) return -RR_ENOMEM;
+    r.t_submit = now_ns();
+    int64_t id;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        if (s->stop) return -RR_ESTATE;
+        id = r.id = s->next_id++;
+        s->reqs.emplace(id, std::move(r));
+        s->queue.push_back(id);
+    }
+    s->cv_work.notify_one();
+    return id;
+}
+
+extern "C" int32_t rr_server_poll(rr_server* s, int64_t* ids, int32_t* status, int64_t* times_ns, int32_t max,
+                                  int32_t timeout_us) {
+    if (!s || !ids || max < 1) return -RR_EINVAL;
+    std::unique_lock<std::mutex> lk(s->mu);
+    if (s->finished.empty() && timeout_us > 0)
+        s->cv_done.wait_for(lk, std::chrono::microseconds(timeout_us), [s] { return !s->finished.empty(); });
+    int32_t n = 0;
+    while (n < max && !s->finished.empty()) {
+        const int64_t id = s->finished.front();
+        s->finished.pop_front();
+        auto it = s->reqs.find(id);
+        ids[n] = id;
+        if (status) status[n] = it->second.result;
+        if (times_ns) {
+            times_ns[3 * n] = it->second.t_submit;
+            times_ns[3 * n + 1] = it->second.t_admit;
+            times_ns[3 * n + 2] = it->second.t_done;
+        }
+        s->reqs.erase(it);
+        ++n;
+    }
+    return n;
+}
+
+extern "C" int32_t rr_server_pending(rr_server* s) {
+    if (!s) return -RR_EINVAL;
+    std::lock_guard<std::mutex> lk(s->mu);
+    return (int32_t)(s->reqs.size() - s->finished.size());
+}

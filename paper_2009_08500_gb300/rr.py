@@ -32,7 +32,8 @@ EXPORTS = ["rr_create", "rr_destroy", "rr_set_ld_profile", "rr_build_weights", "
            "rr_workspace_bytes", "rr_evaluate", "rr_evaluate_grad", "rr_read_table",
            "rr_sync_status", "rr_last_error", "rr_launch_count", "rr_profile", "rr_profile_read",
            "rr_evaluate_noalloc", "rr_prepare", "rr_evaluate_prepared", "rr_evaluate_grad_prepared",
-           "rr_evaluate_host", "rr_request_bytes", "rr_enqueue_host"]
+           "rr_evaluate_host", "rr_request_bytes", "rr_enqueue_host", "rr_server_create", "rr_server_destroy",
+           "rr_server_submit", "rr_server_poll", "rr_server_pending"]
 KERNELS = {"ld_basis": 0, "weights": 1, "pv_setup": 2, "flux": 3, "grad": 4, "grad_reduce": 5, "points": 6}
 
 
@@ -81,6 +82,16 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     L.rr_request_bytes.argtypes = [vp, i32, i32, i32]
     L.rr_request_bytes.restype = sz
     L.rr_enqueue_host.argtypes = [vp, vp, vp, i32, vp, i32, ctypes.POINTER(i32), dp, vp, vp, vp, vp, vp, sz, vp]
+    L.rr_server_create.argtypes = [i32, i32, sz, ctypes.POINTER(vp)]
+    L.rr_server_create.restype = ctypes.c_int
+    L.rr_server_destroy.argtypes = [vp]
+    L.rr_server_destroy.restype = ctypes.c_int
+    L.rr_server_submit.argtypes = [vp, vp, vp, vp, i32, vp, i32, ctypes.POINTER(i32), dp, vp, vp, vp, vp]
+    L.rr_server_submit.restype = i64
+    L.rr_server_poll.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i32), ctypes.POINTER(i64), i32, i32]
+    L.rr_server_poll.restype = i32
+    L.rr_server_pending.argtypes = [vp]
+    L.rr_server_pending.restype = i32
     L.rr_read_table.argtypes = [vp, i32, dp, i64]
     L.rr_read_table.restype = i64
     L.rr_sync_status.argtypes = [vp, vp]

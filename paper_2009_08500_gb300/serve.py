@@ -73,6 +73,21 @@ class ServeRequest:
         return int(self.npv * ss[pb].sum())
 
 
+@dataclass
+class Done:
+    """What the server keeps of a finished request (its buffers belong to the caller)."""
+    id: int
+    points: int
+    ok: bool
+    t_arrival: float
+    t_admit: float
+    t_finish: float
+
+
+def _done_record(req: ServeRequest, ok: bool) -> Done:
+    return Done(req.id, req.points, ok, req.t_arrival, req.t_admit, req.t_finish)
+
+
 class Backend:
     """What the scheduler needs from an executor."""
 
@@ -113,7 +128,7 @@ class Server:
         self._lock = threading.Condition()
         self._next_id = 0
         self._stop = False
-        self.completed: List[ServeRequest] = []
+        self.completed: List[Done] = []
         self.max_inflight_seen = 0
         self._thread = threading.Thread(target=self._run, name="rr-serve", daemon=True)
         self._thread.start()
@@ -194,19 +209,24 @@ class Server:
         """Complete finished requests (lock held)."""
         for slot in list(self._inflight):
             req, handle = self._inflight[slot]
+            exc = None
             try:
                 if not self.backend.done(handle):
                     continue
                 result = self.backend.finish(handle)
-                req.t_finish = time.perf_counter()
-                req.future.set_result(result)
-            except Exception as exc:
-                req.t_finish = time.perf_counter()
-                req.future.set_exception(exc)
+            except Exception as e:
+                exc = e
+            req.t_finish = time.perf_counter()
             del self._inflight[slot]
             self._free_slots.append(slot)
             self._mem_used -= req.nbytes
-            self.completed.append(req)
+            req._host = None
+            # the record first: a caller that sees the future done also sees it in the stats
+            self.completed.append(_done_record(req, exc is None))
+            if exc is None:
+                req.future.set_result(result)
+            else:
+                req.future.set_exception(exc)
 
     def _run(self):
         while True:
@@ -222,7 +242,7 @@ class Server:
 
     # -- metrics ----------------------------------------------------------------
     def stats(self) -> dict:
-        done = [r for r in self.completed if r.future.done() and not r.future.exception()]
+        done = [r for r in self.completed if r.ok]
         if not done:
             return {"requests": 0}
         lat = np.array([r.t_finish - r.t_arrival for r in done])
@@ -300,6 +320,122 @@ class CudaBackend(Backend):
         if h["grad"] is not None:
             out["grad"] = h["grad"].numpy()
         return out
+
+
+class NativeServer:
+    """Continuous batching in the library's worker thread (rr_server_*).
+
+    The library admits requests in arrival order by stream slots and device
+    memory, enqueues each on its own stream and reports completion; this
+    class only prepares pinned host buffers on submit and completes the
+    futures from one poller thread.  fits: {fit id: rr.Model} (built); while
+    the server runs, only the server may use those models.
+    """
+
+    def __init__(self, fits: Dict[Any, Any], slots: int = 8, mem_budget: int = 8 << 30, device: int = 0):
+        import ctypes
+
+        import torch
+
+        from . import rr
+        self.torch, self.ctypes, self.rr = torch, ctypes, rr
+        self.fits = fits
+        self.lib = rr.load_library()
+        h = ctypes.c_void_p()
+        st = self.lib.rr_server_create(device, slots, mem_budget, ctypes.byref(h))
+        if st != 0:
+            raise rr.RRError(st, "rr_server_create failed")
+        self._h = h
+        self.mem_budget = mem_budget
+        self._backend = CudaBackend.__new__(CudaBackend)   # reuse its host-buffer preparation
+        self._backend.torch, self._backend.fits = torch, fits
+        self._lock = threading.Lock()
+        self._inflight: Dict[int, ServeRequest] = {}
+        self._stop = False
+        self.completed: List[ServeRequest] = []
+        self.max_inflight_seen = 0
+        self._poller = threading.Thread(target=self._poll, name="rr-native-serve-poll", daemon=True)
+        self._poller.start()
+
+    def submit(self, req: ServeRequest) -> Future:
+        ctypes, rr = self.ctypes, self.rr
+        m = self.fits[req.fit]
+        req.t_arrival = time.perf_counter()
+        self._backend.prepare(req)
+        h = req._host
+        ss = rr._host_array(req.supersampling, m.npb, np.int32, 1)
+        ex = rr._host_array(req.exptime, m.npb, np.float64, 0.0)
+        req._ssex = (ss, ex)
+        with self._lock:
+            if self._stop:
+                raise RuntimeError("server is stopped")
+            rid = self.lib.rr_server_submit(self._h, m._h, rr._ptr(h["t"]), rr._ptr(h["pb"]), req.npt,
+                                            rr._ptr(h["p"]), req.npv, ss.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                            ex.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), rr._ptr(h["g"]),
+                                            rr._ptr(h["flux"]), rr._ptr(h["grad"]), rr._ptr(h["status"]))
+            if rid < 0:
+                if -rid == 2:
+                    raise AdmissionError(f"request larger than the {self.mem_budget}-byte budget")
+                raise rr.RRError(-rid, "rr_server_submit rejected the request")
+            req.id = int(rid)
+            self._inflight[req.id] = req
+            self.max_inflight_seen = max(self.max_inflight_seen, len(self._inflight))
+        return req.future
+
+    def _poll(self):
+        ctypes = self.ctypes
+        n = 64
+        ids = (ctypes.c_int64 * n)()
+        sts = (ctypes.c_int32 * n)()
+        tms = (ctypes.c_int64 * (3 * n))()
+        while True:
+            got = self.lib.rr_server_poll(self._h, ids, sts, tms, n, 20000)
+            now = time.perf_counter()
+            for i in range(max(got, 0)):
+                with self._lock:
+                    req = self._inflight.pop(int(ids[i]))
+                req.t_finish = now
+                req.t_admit = req.t_arrival + (tms[3 * i + 1] - tms[3 * i]) * 1e-9
+                h = req._host
+                req._host = None
+                # the record first: a caller that sees the future done also sees it in the stats
+                self.completed.append(_done_record(req, sts[i] == 0))
+                if sts[i] != 0:
+                    req.future.set_exception(self.rr.RRError(int(sts[i]), "request failed in the server"))
+                else:
+                    out = {"flux": h["flux"].numpy(), "pv_status": h["status"].numpy()}
+                    if h["grad"] is not None:
+                        out["grad"] = h["grad"].numpy()
+                    req.future.set_result(out)
+            with self._lock:
+                if self._stop and not self._inflight:
+                    return
+
+    def drain(self, timeout_s: float = 600.0):
+        t0 = time.perf_counter()
+        while True:
+            with self._lock:
+                if not self._inflight:
+                    return
+            if time.perf_counter() - t0 > timeout_s:
+                raise TimeoutError("server did not drain")
+            time.sleep(1e-3)
+
+    def close(self):
+        with self._lock:
+            self._stop = True
+        self._poller.join()
+        if self._h:
+            self.lib.rr_server_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    stats = Server.stats
 
 
 def latency_summary(reqs: List[ServeRequest]) -> dict:

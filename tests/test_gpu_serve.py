@@ -5,7 +5,7 @@ import numpy as np
 import pytest
 
 from paper_2009_08500_gb300 import workloads as W
-from paper_2009_08500_gb300.serve import CudaBackend, Server, ServeRequest
+from paper_2009_08500_gb300.serve import CudaBackend, NativeServer, Server, ServeRequest
 
 pytestmark = pytest.mark.gpu
 
@@ -91,3 +91,38 @@ def test_served_flux_matches_oracle(fits):
         s = om.build(tmpl.grid, tmpl.ld_model, 1, False, tmpl.profiles)
         ref = om.evaluate(s, r.times, r.pb_index, r.params, r.supersampling, r.exptime)
         assert np.abs(o["flux"] - ref).max() <= 1e-6
+
+
+@pytest.mark.parametrize("budget", [8 << 30, 40 << 20])
+def test_native_server_results_identical_alone_and_in_the_mix(fits, budget):
+    reqs = _requests(fits, 36, seed=budget % 89 + 1)
+    futs = {}
+    with NativeServer({k: v[0] for k, v in fits.items()}, slots=6, mem_budget=budget) as srv:
+        def client(part):
+            for r in part:
+                futs[id(r)] = srv.submit(r)
+        ths = [threading.Thread(target=client, args=(reqs[c::3],)) for c in range(3)]
+        for t in ths:
+            t.start()
+        for t in ths:
+            t.join()
+        res = {k: f.result(timeout=120) for k, f in futs.items()}
+        srv.drain()
+        stats = srv.stats()
+    for r in reqs:
+        out = res[id(r)]
+        f, g = _alone(fits, r)
+        assert np.array_equal(out["flux"], f)
+        assert not out["pv_status"].any()
+        if g is not None:
+            assert np.array_equal(out["grad"], g)
+    assert stats["requests"] == len(reqs)
+    assert stats["latency_p99_ms"] >= stats["latency_p50_ms"] > 0
+
+
+def test_native_server_rejects_oversize_requests(fits):
+    from paper_2009_08500_gb300.serve import AdmissionError
+    reqs = _requests(fits, 2, seed=3)
+    with NativeServer({k: v[0] for k, v in fits.items()}, slots=2, mem_budget=1 << 16) as srv:
+        with pytest.raises(AdmissionError):
+            srv.submit(reqs[0])

@@ -6,6 +6,8 @@ Two independent routes:
   ``orbit`` (textbook Keplerian form), written out term by term:
     f = 1 - ip ap / I_star,   ip = lerp_g(ldw),  ap = area(1, k, z),
     ldw = (1 - ak) w[ik].ldp + ak w[ik+1].ldp,   g = z / (1 + k),
+  (the direct model: ldw = w(k).ldp with d w / d k from the lens-area
+  partials, ``weights.weight_vector_dk``),
   with the derivative of the piecewise-linear interpolants taken inside the
   cell that holds the point (the lower cell on a node, as ``model``
   evaluates), d area / dz = -(chord length) and d area / dk = 2 k kappa_1
@@ -19,6 +21,7 @@ import numpy as np
 
 from . import ld as _ld
 from . import orbit as _orbit
+from . import weights as _weights
 from .model import (Setup, _table, g_cell, k_cell, pv_status, sample_times, unpack, evaluate)
 
 
@@ -144,12 +147,19 @@ def jacobian(setup: Setup, times, pb_index, row, supersampling, exptime):
         ldp = _ld.profile(setup.ld_model, setup.mu, ldc[pb], table)
         istar = _ld.istar(setup.ld_model, ldc[pb], table)
         dldp, distar = _ld_partials(setup.ld_model, setup.mu, ldc[pb], table)
-        ik, ak = k_cell(setup, k)
-        row_lo, row_hi = np.dot(setup.w[ik], ldp), np.dot(setup.w[ik + 1], ldp)
-        ldw = (1.0 - ak) * row_lo + ak * row_hi
-        dldw_dk = (row_hi - row_lo) / setup.dk
-        dldw_dc = [(1.0 - ak) * np.dot(setup.w[ik], dldp[c]) + ak * np.dot(setup.w[ik + 1], dldp[c])
-                   for c in range(dldp.shape[0])]
+        if setup.direct:
+            # weights for this exact k and their k-derivative at fixed g (Sect. 3.1.2)
+            _, wk, wdk = _weights.calculate_weights(k, setup.ze, setup.ng, with_dk=True)
+            ldw = wk @ ldp
+            dldw_dk = wdk @ ldp
+            dldw_dc = [wk @ dldp[c] for c in range(dldp.shape[0])]
+        else:
+            ik, ak = k_cell(setup, k)
+            row_lo, row_hi = np.dot(setup.w[ik], ldp), np.dot(setup.w[ik + 1], ldp)
+            ldw = (1.0 - ak) * row_lo + ak * row_hi
+            dldw_dk = (row_hi - row_lo) / setup.dk
+            dldw_dc = [(1.0 - ak) * np.dot(setup.w[ik], dldp[c]) + ak * np.dot(setup.w[ik + 1], dldp[c])
+                       for c in range(dldp.shape[0])]
         ss = int(supersampling[pb])
         acc = np.zeros((idx.size, setup.nparam))
         for s in range(ss):

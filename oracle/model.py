@@ -12,6 +12,10 @@ Sect. 3.1.2, step by step, for each parameter vector and passband:
         ap = area(1, k, c)                           (occluded area)
         f  = (I_star - ip ap) / I_star               (Eq. 5)
 
+Direct model (Sect. 3.1.2, the interpolation in k left out): ldw =
+dot(w(k), ldp) with the weights computed for the vector's own k on the g
+grid (``weights.calculate_weights``); k may then be anywhere in (0, 1).
+
 Points where the planet is behind the star or g >= 1 have f = 1 exactly.
 Exposure supersampling (Sect. 4.1): each point is the mean of f over ss
 sub-exposures.  Reading (placement unstated): midpoint rule,
@@ -67,6 +71,7 @@ class Setup:
     chromatic: bool
     tables: Optional[List[tuple]]
     n_general: int = 0      # coefficients of the general law
+    direct: bool = False    # direct model: weights for each exact k, interpolation in g only (Sect. 3.1.2)
 
     @property
     def nldc(self) -> int:
@@ -87,12 +92,13 @@ def _tables(zcut, nzin, nzlimb, ng, nk, k0, k1):
 
 
 def build(grid: dict, ld_model: str, npb: int = 1, chromatic: bool = False,
-          tables: Optional[Sequence[tuple]] = None, n_general: int = 0) -> Setup:
-    """Model initialisation: radial grid, mu at the bin means and the (k, g) weight table."""
+          tables: Optional[Sequence[tuple]] = None, n_general: int = 0, direct: bool = False) -> Setup:
+    """Model initialisation: radial grid, mu at the bin means and the (k, g) weight table
+    (the direct model computes its weights per call for each k instead)."""
     ze, zm, mu, dk, dg, w = _tables(grid["zcut"], grid["nzin"], grid["nzlimb"], grid["ng"],
                                     grid["nk"], grid["k0"], grid["k1"])
     return Setup(ze, zm, mu, w, dk, dg, grid["k0"], grid["k1"], grid["nk"], grid["ng"],
-                 ld_model, npb, chromatic, list(tables) if tables is not None else None, n_general)
+                 ld_model, npb, chromatic, list(tables) if tables is not None else None, n_general, direct)
 
 
 def unpack(setup: Setup, row: np.ndarray):
@@ -108,7 +114,10 @@ def pv_status(setup: Setup, row: np.ndarray) -> int:
     st = 0
     if not np.all(np.isfinite(row)):
         return ST_NONFINITE
-    if np.any(ks < setup.k0) or np.any(ks > setup.k1):
+    if setup.direct:
+        if np.any(ks <= 0.0) or np.any(ks >= 1.0):
+            st |= ST_K_RANGE
+    elif np.any(ks < setup.k0) or np.any(ks > setup.k1):
         st |= ST_K_RANGE
     if not (0.0 <= e < 1.0):
         st |= ST_E_RANGE
@@ -142,6 +151,9 @@ def ld_weights(setup: Setup, k: float, coef, pb: int):
     table = _table(setup, pb)
     ldp = _ld.profile(setup.ld_model, setup.mu, coef, table)
     istar = _ld.istar(setup.ld_model, coef, table)
+    if setup.direct:
+        _, w = _weights.calculate_weights(k, setup.ze, setup.ng)
+        return ldp, istar, w @ ldp
     ik, ak = k_cell(setup, k)
     ldw = (1.0 - ak) * np.dot(setup.w[ik], ldp) + ak * np.dot(setup.w[ik + 1], ldp)
     return ldp, istar, ldw
@@ -212,6 +224,7 @@ def evaluate(setup: Setup, times, pb_index, params, supersampling, exptime, retu
 def evaluate_workload(wl, setup: Optional[Setup] = None, return_status=False):
     """Oracle flux for a :class:`paper_2009_08500_gb300.workloads.Workload`-shaped object."""
     if setup is None:
-        setup = build(wl.grid, wl.ld_model, wl.npb, wl.chromatic, wl.profiles, getattr(wl, "n_general", 0))
+        setup = build(wl.grid, wl.ld_model, wl.npb, wl.chromatic, wl.profiles, getattr(wl, "n_general", 0),
+                      getattr(wl, "direct", False))
     return evaluate(setup, wl.times, wl.pb_index, wl.params, wl.supersampling, wl.exptime,
                     return_status=return_status)

@@ -60,6 +60,7 @@ class Workload:
     profiles: Optional[List[tuple]] = None   # per passband (mu, I) for tabulated LD
     grid: dict = field(default_factory=lambda: dict(GRID))
     n_general: int = 0                       # coefficients of the general law
+    direct: bool = False                     # direct model: per-k weights, no k grid
 
     @property
     def npv(self) -> int:
@@ -83,7 +84,7 @@ class Workload:
         return Workload(self.name, self.times[sl].copy(), self.pb_index[sl].copy(),
                         self.params[:npv].copy(), self.supersampling.copy(), self.exptime.copy(),
                         self.ld_model, self.npb, self.chromatic, self.precision,
-                        self.profiles, dict(self.grid), self.n_general)
+                        self.profiles, dict(self.grid), self.n_general, self.direct)
 
 
 def nparam_for(ld_model: str, npb: int, chromatic: bool, n_general: int = 0) -> int:
@@ -219,10 +220,10 @@ def make_c4(seed: int = 3, npv: int = 2048, per_pb: int = 7500) -> Workload:
 def make_small(ld_model: str = "quadratic", npv: int = 3, npt: int = 257, npb: int = 1,
                chromatic: bool = False, ss=(1,), exptime=(0.0,), seed: int = 7,
                eccentric: bool = True, precision: str = "mixed", span: float = 6.0,
-               n_general: int = 0) -> Workload:
+               n_general: int = 0, direct: bool = False, k_range=(0.02, 0.25)) -> Workload:
     """Small seeded case for parity tests: a few pvs, a ragged number of times."""
     rng = np.random.Generator(np.random.PCG64(seed))
-    k = rng.uniform(0.02, 0.25, npv)
+    k = rng.uniform(k_range[0], k_range[1], npv)
     a = rng.uniform(3.0, 12.0, npv)
     b = rng.uniform(0.0, 1.0 + k) * 0.9
     P = rng.uniform(1.0, 3.0, npv)
@@ -235,7 +236,8 @@ def make_small(ld_model: str = "quadratic", npv: int = 3, npt: int = 257, npb: i
     pb_index = rng.integers(0, npb, npt).astype(np.int32)
     cols = [t0, P, a, b, e, w]
     if chromatic:
-        cols += [np.clip(k * rng.uniform(0.95, 1.05), 0.006, 0.29) for _ in range(npb)]
+        lo, hi = (1e-3, 0.95) if direct else (0.006, 0.29)
+        cols += [np.clip(k * rng.uniform(0.95, 1.05), lo, hi) for _ in range(npb)]
     else:
         cols += [k]
     profiles = None
@@ -266,7 +268,7 @@ def make_small(ld_model: str = "quadratic", npv: int = 3, npt: int = 257, npb: i
     ss_arr = np.array([ss[j % len(ss)] for j in range(npb)], np.int32)
     ex_arr = np.array([exptime[j % len(exptime)] for j in range(npb)], np.float64)
     return Workload(f"small_{ld_model}", times, pb_index, params, ss_arr, ex_arr, ld_model, npb,
-                    chromatic, precision, profiles, n_general=n_general)
+                    chromatic, precision, profiles, n_general=n_general, direct=direct)
 
 
 @dataclass

@@ -74,7 +74,7 @@ typedef enum {
 } rr_precision;
 
 /* Per-pv status bits written to pv_status (0 = valid). */
-#define RR_PV_K_RANGE    1    /* a radius ratio outside [k0, k1] */
+#define RR_PV_K_RANGE    1    /* a radius ratio outside [k0, k1] (direct model: outside (0, 1)) */
 #define RR_PV_E_RANGE    2    /* eccentricity outside [0, 1) */
 #define RR_PV_B_RANGE    4    /* impact parameter outside [0, a] */
 #define RR_PV_P_RANGE    8    /* period <= 0 */
@@ -90,14 +90,20 @@ typedef struct {
     int32_t nzin;       /* annuli of constant dz inside zcut, >= 1 */
     int32_t nzlimb;     /* annuli of constant dmu outside zcut, >= 1; nz = nzin + nzlimb <= 4096 */
     int32_t ng;         /* grazing-value nodes g_i = i / (ng - 1), 2 <= ng <= 4096 */
-    int32_t nk;         /* radius-ratio nodes on [k0, k1] (Sect. 3.1.2), 2 <= nk <= 4096 */
-    double  k0, k1;     /* radius-ratio range, 0 < k0 < k1 < 1 */
+    int32_t nk;         /* radius-ratio nodes on [k0, k1] (Sect. 3.1.2), 2 <= nk <= 4096;
+                           unused (not checked) by the direct model */
+    double  k0, k1;     /* radius-ratio range, 0 < k0 < k1 < 1; unused by the direct model */
     int32_t npb;        /* passbands, 1 <= npb <= RR_MAX_PB */
     int32_t ld_model;   /* rr_ld_model */
     int32_t chromatic;  /* 0: one k per pv; 1: one k per passband (Sect. 4.2) */
     int32_t precision;  /* rr_precision */
     int32_t device;     /* CUDA device ordinal */
     int32_t ncoef;      /* terms of RR_LD_GENERAL (1..4); 0 for every other law */
+    int32_t direct;     /* 0: the interpolated model, weights tabulated on the (k, g) grid and
+                           interpolated in k and g (Sect. 3.1.2);
+                           1: the direct model of the same section: every call computes the
+                           weights on the g grid for each parameter vector's own k, with
+                           0 < k < 1 (interpolation in g only; no k table, no k range) */
 } rr_config;
 
 /* Create a context: validates `cfg`, builds the radial grid of Sect. 3.1.1 on
@@ -122,8 +128,12 @@ rr_status rr_set_ld_profile(rr_ctx* ctx, int32_t pb, const double* mu, const dou
 /* Build the tables (Sect. 3.1.2): the LD profiles at the bin means and their
  * disk integrals, the FP64 weight table w[nk][ng][nz] (covered annulus area
  * / covered area, Sect. 2), and its projections T[b][nk][ng] = w . l_b onto
- * every profile basis b.  Enqueued on `stream`, then the stream is
- * synchronised (set-up, not hot path).  Must precede evaluation.
+ * every profile basis b.  The direct model builds no (k, g) table: it keeps
+ * the profiles, their disk integrals and, per basis, the running sums over
+ * annuli of (annulus area x profile) that a planet covering the disk's
+ * centre takes whole; its weights are computed by every evaluation.
+ * Enqueued on `stream`, then the stream is synchronised (set-up, not hot
+ * path).  Must precede evaluation.
  * Errors: RR_ESTATE (a tabulated profile missing), RR_ECUDA. */
 rr_status rr_build_weights(rr_ctx* ctx, void* stream);
 
@@ -323,7 +333,8 @@ int32_t rr_server_pending(rr_server* server);
  *   RR_TABLE_ZE (nz+1), RR_TABLE_ZM (nz), RR_TABLE_MU (nz)
  *   RR_TABLE_WEIGHTS (nk*ng*nz), RR_TABLE_BASIS (nbasis*nz) profiles at zm,
  *   RR_TABLE_ISTAR (nbasis), RR_TABLE_PROJ (nbasis*nk*ng) = w . basis
- * Tables other than the grid need rr_build_weights first.  Synchronous. */
+ * Tables other than the grid need rr_build_weights first; the direct model
+ * has no RR_TABLE_WEIGHTS or RR_TABLE_PROJ (-1, RR_ESTATE).  Synchronous. */
 #define RR_TABLE_ZE 0
 #define RR_TABLE_ZM 1
 #define RR_TABLE_MU 2
@@ -353,7 +364,8 @@ int64_t rr_launch_count(const rr_ctx* ctx);
 #define RR_KERNEL_GRAD 4
 #define RR_KERNEL_GRAD_REDUCE 5
 #define RR_KERNEL_POINTS 6
-#define RR_KERNEL_KINDS 7
+#define RR_KERNEL_DIRECT 7    /* the direct model's per-call weight projections */
+#define RR_KERNEL_KINDS 8
 
 /* Per-kernel timing (measurement aid).  While enabled, every kernel launch
  * of this context is bracketed by two CUDA events recorded on the launching

@@ -79,9 +79,11 @@ void free_all(rr_ctx* c) {
     cudaFree(c->d_tab);
     cudaFree(c->d_tab_off);
     cudaFree(c->d_err);
+    cudaFree(c->d_zef);
+    cudaFree(c->d_basisf);
+    cudaFree(c->d_pre64);
+    cudaFree(c->d_pref);
 }
-
-size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // Per-kernel timing: when enabled, every launch is bracketed by two CUDA
 // events recorded on the launching stream; rr_profile_read resolves them.
@@ -170,6 +172,8 @@ WsLayout ws_layout(const rr_ctx* c, int npv, int npt, bool grad) {
     WsLayout w;
     w.rec = 0;
     size_t off = align256(records_bytes(c, npv, grad));
+    w.dir = off;
+    if (c->cfg.direct) off += align256(direct_bytes(c, npv, grad));
     w.pts_dt = off;
     if (c->cfg.precision == RR_PREC_MIXED) off += align256((size_t)npt * 8);
     w.pts_pb = off;
@@ -186,10 +190,19 @@ WsLayout ws_layout(const rr_ctx* c, int npv, int npt, bool grad) {
 namespace {
 
 // Per-pv set-up and per-time preparation (the first two kernels of every evaluation).
+// The direct model's per-call projections (before the set-up kernel that reads them).
+cudaError_t run_direct(rr_ctx* c, const double* params, int npv, bool grad, void* ws, cudaStream_t s) {
+    if (!c->cfg.direct) return cudaSuccess;
+    const WsLayout W = ws_layout(c, npv, 0, grad);
+    const DirectTables D = direct_view(c, (char*)ws + W.dir, npv, grad);
+    return timed(c, RR_KERNEL_DIRECT, s, [&] { return launch_direct_tables(c, params, npv, grad, D, s); });
+}
+
 cudaError_t run_setup(rr_ctx* c, const double* times, const int32_t* pb_index, int npt, const double* params,
                       int npv, const PbParams& pbp, bool grad, int32_t* pv_status, void* ws, cudaStream_t s) {
-    cudaError_t e = timed(c, RR_KERNEL_PV_SETUP, s,
-                          [&] { return launch_pv_setup(c, params, npv, pbp, grad, ws, pv_status, s); });
+    cudaError_t e = run_direct(c, params, npv, grad, ws, s);
+    if (e != cudaSuccess) return e;
+    e = timed(c, RR_KERNEL_PV_SETUP, s, [&] { return launch_pv_setup(c, params, npv, pbp, grad, ws, pv_status, s); });
     if (e != cudaSuccess || c->cfg.precision != RR_PREC_MIXED || npt == 0) return e;
     const WsLayout W = ws_layout(c, npv, npt, grad);
     char* wb = (char*)ws;
@@ -204,6 +217,7 @@ rr_status status_only(rr_ctx* c, const double* params, int npv, const PbParams& 
     if (!ws || ws_bytes < rr_workspace_bytes(c, npv, 0, grad ? 1 : 0) || ((uintptr_t)ws & 255u))
         return fail(c, RR_EINVAL, "workspace too small or misaligned");
     cudaError_t e = cudaSetDevice(c->cfg.device);
+    if (e == cudaSuccess) e = run_direct(c, params, npv, grad, ws, s);
     if (e == cudaSuccess)
         e = timed(c, RR_KERNEL_PV_SETUP, s, [&] { return launch_pv_setup(c, params, npv, pbp, grad, ws, pv_status, s); });
     if (e != cudaSuccess) return cuda_fail(c, e, what);
@@ -285,8 +299,11 @@ rr_status rr_create(const rr_config* cfg, rr_ctx** out) {
     if (k.nzin < 1 || k.nzlimb < 1 || k.nzin + k.nzlimb > kMaxNz)
         return fail(nullptr, RR_EINVAL, "need nzin >= 1, nzlimb >= 1, nzin + nzlimb <= 4096");
     if (k.ng < 2 || k.ng > 4096) return fail(nullptr, RR_EINVAL, "ng must be in [2, 4096]");
-    if (k.nk < 2 || k.nk > 4096) return fail(nullptr, RR_EINVAL, "nk must be in [2, 4096]");
-    if (!(k.k0 > 0.0 && k.k0 < k.k1 && k.k1 < 1.0)) return fail(nullptr, RR_EINVAL, "need 0 < k0 < k1 < 1");
+    if (k.direct != 0 && k.direct != 1) return fail(nullptr, RR_EINVAL, "direct must be 0 or 1");
+    if (!k.direct) {
+        if (k.nk < 2 || k.nk > 4096) return fail(nullptr, RR_EINVAL, "nk must be in [2, 4096]");
+        if (!(k.k0 > 0.0 && k.k0 < k.k1 && k.k1 < 1.0)) return fail(nullptr, RR_EINVAL, "need 0 < k0 < k1 < 1");
+    }
     if (k.npb < 1 || k.npb > RR_MAX_PB) return fail(nullptr, RR_EINVAL, "npb must be in [1, 32]");
     if (k.ld_model < RR_LD_UNIFORM || k.ld_model > RR_LD_EXPONENTIAL) return fail(nullptr, RR_EINVAL, "unknown ld_model");
     if (k.ld_model == RR_LD_GENERAL ? (k.ncoef < 1 || k.ncoef > 4) : k.ncoef != 0)
@@ -308,15 +325,19 @@ rr_status rr_create(const rr_config* cfg, rr_ctx** out) {
     c->nbasis = k.ld_model == RR_LD_TABULATED ? k.npb : 1 + c->nldc;
     c->nkp = k.chromatic ? k.npb : 1;
     c->nparam = 6 + c->nkp + k.npb * c->nldc;
-    c->dk = (k.k1 - k.k0) / (k.nk - 1);
+    c->dk = k.direct ? 1.0 : (k.k1 - k.k0) / (k.nk - 1);
     c->dg = 1.0 / (k.ng - 1);
     make_grid(k.zcut, k.nzin, k.nzlimb, c->ze, c->zm, c->mu);
     c->tab_mu.resize(k.npb);
     c->tab_I.resize(k.npb);
-    const size_t nT = (size_t)c->nbasis * k.nk * k.ng;
+    // the (k, g) projections (interpolated model) or the running sums of the direct model
+    const size_t nT = k.direct ? 0 : (size_t)c->nbasis * k.nk * k.ng;
+    const size_t nP = k.direct ? (size_t)c->nbasis * (c->nz + 1) : 0;
     if (dalloc(&c->d_ze, c->nz + 1) || dalloc(&c->d_mu, c->nz) || dalloc(&c->d_basis, (size_t)c->nbasis * c->nz) ||
         dalloc(&c->d_istar, c->nbasis) || dalloc(&c->d_T64, nT) || dalloc(&c->d_T32, nT) || dalloc(&c->d_DT32, nT) ||
-        dalloc(&c->d_tab_off, k.npb + 1) || dalloc(&c->d_err, 1)) {
+        dalloc(&c->d_tab_off, k.npb + 1) || dalloc(&c->d_err, 1) ||
+        (k.direct && (dalloc(&c->d_zef, c->nz + 1) || dalloc(&c->d_basisf, (size_t)c->nbasis * c->nz) ||
+                      dalloc(&c->d_pre64, nP) || dalloc(&c->d_pref, 2 * nP)))) {
         free_all(c);
         delete c;
         cudaGetLastError();
@@ -381,7 +402,7 @@ rr_status rr_build_weights(rr_ctx* c, void* stream) {
             (e = cudaMemcpy(c->d_tab_off, off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice)))
             return cuda_fail(c, e, "upload of the tabulated profiles");
     }
-    if (!c->d_w) {
+    if (!c->d_w && !c->cfg.direct) {
         if (dalloc(&c->d_w, (size_t)c->cfg.nk * c->cfg.ng * c->nz)) {
             cudaGetLastError();
             return fail(c, RR_ENOMEM, "device allocation of the weight table failed");
@@ -389,6 +410,14 @@ rr_status rr_build_weights(rr_ctx* c, void* stream) {
     }
     if ((e = timed(c, RR_KERNEL_LD_BASIS, s, [&] { return launch_ld_basis(c, s); })) != cudaSuccess)
         return cuda_fail(c, e, "LD profile kernel");
+    if (c->cfg.direct) {
+        // no (k, g) table: the running sums over wholly covered annuli
+        if ((e = timed(c, RR_KERNEL_WEIGHTS, s, [&] { return launch_direct_prefix(c, s); })) != cudaSuccess)
+            return cuda_fail(c, e, "direct-model set-up kernel");
+        if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(c, e, "rr_build_weights");
+        c->tables_built = true;
+        return RR_OK;
+    }
     const bool need_w = !c->weights_built;
     if ((e = timed(c, RR_KERNEL_WEIGHTS, s, [&] { return launch_weights(c, need_w, s); })) != cudaSuccess)
         return cuda_fail(c, e, "weight table kernel");
@@ -468,6 +497,10 @@ int64_t rr_read_table(rr_ctx* c, int32_t which, double* out, int64_t capacity) {
         case RR_TABLE_ISTAR: src = c->d_istar; n = nb; break;
         case RR_TABLE_PROJ: src = c->d_T64; n = (int64_t)nb * nk * ng; break;
         default: fail(c, RR_EINVAL, "unknown table"); return -1;
+    }
+    if (c->cfg.direct && (which == RR_TABLE_WEIGHTS || which == RR_TABLE_PROJ)) {
+        fail(c, RR_ESTATE, "the direct model has no (k, g) table");
+        return -1;
     }
     if (!out) return n;
     const int64_t m = capacity < n ? capacity : n;

@@ -106,6 +106,8 @@ inline RecLayout make_layout(int npb, int ng, int nldc, bool grad) {
     return L;
 }
 
+inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
 // Start of the rows region after npv headers.
 __host__ __device__ inline size_t rows_offset(const RecLayout& L, int npv) {
     return ((size_t)npv * L.head_bytes + 255) & ~(size_t)255;
@@ -124,9 +126,21 @@ struct PbParams {
 // Model constants for the kernels (by value).
 struct ModelParams {
     int32_t ld_model, npb, chromatic, nldc, nparam, nk, ng, nbasis;
+    int32_t direct, nz;   // direct model (per-call weights for each k); radial bins
     double k0, k1, dk;
     double inv_dk;   // 1 / dk (host FP64)
     double exp_c;    // int_0^1 mu / (e^mu - 1) dmu (disk integral of the exponential law's second term)
+};
+
+// Per-call projections of the direct model (the workspace region after the
+// records): for every (pv, k slot) row = pv * nkp + slot, basis b and g node,
+// T[b][row][ig] = sum_j w_j(k_row, g) l_b[j] (R = float: hi + lo float
+// pair; R = double: hi only) and, for the adjoint, dT/dk at fixed g.
+struct DirectTables {
+    void* hi;      // R[nbasis][nrows][ng]
+    float* lo;     // float[nbasis][nrows][ng] (mixed form), else null
+    void* dk;      // R[nbasis][nrows][ng] (adjoint layout), else null
+    int32_t nrows;
 };
 
 }  // namespace rr
@@ -149,6 +163,12 @@ struct rr_ctx {
     double* d_tab = nullptr;     // tabulated profiles, concatenated (mu then I per passband)
     int* d_tab_off = nullptr;    // npb + 1 offsets (in nodes)
     int* d_err = nullptr;        // device error word
+    // direct model: FP32 copies of the edges and profiles, and per basis the
+    // running sums P[b][m] = sum_{j<m} pi (ze[j+1]^2 - ze[j]^2) l_b[j]
+    float* d_zef = nullptr;      // nz + 1
+    float* d_basisf = nullptr;   // nbasis * nz
+    double* d_pre64 = nullptr;   // nbasis * (nz + 1)
+    float* d_pref = nullptr;     // 2 * nbasis * (nz + 1): FP32 hi, then lo
     int num_sms = 0;
     bool weights_built = false;
     bool tables_built = false;
@@ -175,6 +195,13 @@ namespace rr {
 // launchers (defined in the .cu files); all return cudaGetLastError() after launch
 cudaError_t launch_ld_basis(rr_ctx* c, cudaStream_t s);
 cudaError_t launch_weights(rr_ctx* c, bool need_w, cudaStream_t s);
+// direct model: the running sums at build time, the per-call projections
+cudaError_t launch_direct_prefix(rr_ctx* c, cudaStream_t s);
+cudaError_t launch_direct_tables(rr_ctx* c, const double* params, int npv, bool grad, const DirectTables& D,
+                                 cudaStream_t s);
+size_t direct_bytes(const rr_ctx* c, int npv, bool grad);
+DirectTables direct_view(const rr_ctx* c, void* base, int npv, bool grad);
+// records: the workspace (the direct model's projections follow the records)
 cudaError_t launch_pv_setup(rr_ctx* c, const double* params, int npv, const PbParams& pbp,
                             bool grad, void* records, int32_t* pv_status, cudaStream_t s);
 // grad_layout: the records were written in the adjoint's layout (rr_prepare)
@@ -190,10 +217,10 @@ cudaError_t launch_grad_reduce(rr_ctx* c, int npt, const double* params, int npv
                                const void* partials, double* grad_params, cudaStream_t s);
 size_t records_bytes(const rr_ctx* c, int npv, bool grad);
 size_t partials_bytes(const rr_ctx* c, int npv, int npt);
-// workspace layout: [records | per-point float-float times + passband, per-group summaries (mixed form)
-//                    | partial sums]
+// workspace layout: [records | direct-model projections | per-point float-float times + passband,
+//                    per-group summaries (mixed form) | partial sums]
 struct WsLayout {
-    size_t rec, pts_dt, pts_pb, pts_grp, part, total;
+    size_t rec, dir, pts_dt, pts_pb, pts_grp, part, total;
 };
 WsLayout ws_layout(const rr_ctx* c, int npv, int npt, bool grad);
 cudaError_t launch_points(rr_ctx* c, const double* times, const int32_t* pb_index, int npt, void* ws_dt,

@@ -184,6 +184,282 @@ __global__ void rr_diff_table_kernel(const double* __restrict__ T64, float* __re
 }
 
 // ---------------------------------------------------------------------------
+// Direct model (Sect. 3.1.2 without the k interpolation): per call, the
+// weights of every g node for each parameter vector's own k, projected onto
+// the profile bases, T[b][row][ig] = sum_j w_j l_b[j] with
+// w_j = (a(ze[j+1]) - a(ze[j])) / a(1), and for the adjoint their
+// k-derivative at fixed g (c = g (1 + k)):
+//   d a / d k |_g = d a / d k + g d a / d c,
+//   d w_j / d k = (a'(ze[j+1]) - a'(ze[j])) / a(1) - w_j a'(1) / a(1).
+// Only the edges inside the planet's band |c - k| < r < c + k need the lens
+// formula: below it the disk is either wholly covered (c < k; those annuli
+// come from running sums P[b][m] built once) or untouched, and above it the
+// covered area is the whole planet, so those annuli get no weight.
+// ---------------------------------------------------------------------------
+
+// phi(x) = x - sin x cos x = (2x - sin 2x) / 2, the area of a circular
+// segment of unit radius and half-angle x.  Below x = 0.75 the direct form
+// cancels, so it is summed from the Taylor series of sin (t = 2x):
+//   phi = t^3 / 12 (1 - t^2/20 + t^4/840 - t^6/60480 + t^8/6652800 - t^10/1037836800),
+// whose first omitted term is below 1e-9 of the sum there.
+__device__ __forceinline__ float seg_phi(float x) {
+    if (x < 0.75f) {
+        const float t = 2.0f * x, t2 = t * t;
+        float p = -1.0f / 1037836800.0f;
+        p = fmaf(p, t2, 1.0f / 6652800.0f);
+        p = fmaf(p, t2, -1.0f / 60480.0f);
+        p = fmaf(p, t2, 1.0f / 840.0f);
+        p = fmaf(p, t2, -1.0f / 20.0f);
+        p = fmaf(p, t2, 1.0f);
+        return t * t2 * (1.0f / 12.0f) * p;
+    }
+    return x - 0.5f * sinf(2.0f * x);
+}
+
+// Area common to the radius-r disk and the planet (radius k, centre at
+// distance c) with its partials d a / d k (the planet's rim inside the disk,
+// 2 k kappa_1) and d a / d c (minus the common chord, -K / c).
+// FP32: the lens is the sum of two circular segments, r^2 phi(kappa_0) +
+// k^2 phi(kappa_1), each non-negative, so that the area keeps a few ulp of
+// relative accuracy when k << r (the textbook form r^2 kappa_0 + k^2 kappa_1
+// - K / 2 cancels there).  Heron's factors that vanish at a contact
+// (r + k - c, c + k - r, c + r - k) are formed as (x + y) - z with the
+// rounding error of x + y added back (error-free sum), so they keep their
+// relative accuracy next to the contact too.
+__device__ __forceinline__ float sum3_small(float x, float y, float z) {
+    // x + y - z where x + y is close to z
+    const float s = __fadd_rn(x, y);
+    const float bb = __fsub_rn(s, x);
+    const float e = __fadd_rn(__fsub_rn(x, __fsub_rn(s, bb)), __fsub_rn(y, bb));
+    return __fadd_rn(__fsub_rn(s, z), e);
+}
+
+__device__ __forceinline__ float edge_area(float r, float k, float c, float& dk, float& dc) {
+    if (c >= r + k) { dk = 0.0f; dc = 0.0f; return 0.0f; }
+    if (c <= fabsf(r - k)) {
+        dc = 0.0f;
+        if (k < r) { dk = 2.0f * CUDART_PI_F * k; return CUDART_PI_F * k * k; }
+        dk = 0.0f;
+        return CUDART_PI_F * r * r;
+    }
+    const float dr = r - c;
+    const float p1 = sum3_small(r, k, c), p2 = sum3_small(c, k, r), s1 = r + k + c, s2 = sum3_small(c, r, k);
+    const float K = sqrtf(fmaxf((p1 * p2) * (s1 * s2), 0.0f));   // 2 c x (half chord)
+    const float x0 = fmaf(c - k, c + k, r * r);                     // 2 c r cos(kappa_0)
+    const float x1 = fmaf(-dr, c + r, k * k);                       // 2 c k cos(kappa_1)
+    const float kap0 = atan2f(K, x0), kap1 = atan2f(K, x1);
+    dk = 2.0f * k * kap1;
+    dc = -K / c;
+    return r * r * seg_phi(kap0) + k * k * seg_phi(kap1);
+}
+
+// FP64: the textbook form (its cancellation for k << r costs r / k ulp of FP64).
+__device__ __forceinline__ double edge_area(double r, double k, double c, double& dk, double& dc) {
+    if (c >= r + k) { dk = 0.0; dc = 0.0; return 0.0; }
+    if (c <= fabs(r - k)) {
+        dc = 0.0;
+        if (k < r) { dk = 2.0 * CUDART_PI * k; return CUDART_PI * k * k; }
+        dk = 0.0;
+        return CUDART_PI * r * r;
+    }
+    double h = ((r + k) - c) * (c + (r - k)) * (c - (r - k)) * (c + (r + k));
+    h = h > 0.0 ? h : 0.0;
+    const double K = sqrt(h);
+    const double kap0 = atan2(K, c * c + (r * r - k * k));
+    const double kap1 = atan2(K, c * c + (k * k - r * r));
+    dk = 2.0 * k * kap1;
+    dc = -K / c;
+    return r * r * kap0 + k * k * kap1 - 0.5 * K;
+}
+
+// Sums of products for the projections.  FP32: an unevaluated float pair
+// (error-free product and sum, with rounding-exact intrinsics that the
+// compiler does not contract), so that neighbouring g nodes differ by their
+// true difference; FP64: plain sums.
+template <typename A> struct DirSum;
+template <> struct DirSum<float> {
+    float h = 0.0f, l = 0.0f;
+    __device__ __forceinline__ void add_prod(float x, float y) {
+        const float p = __fmul_rn(x, y);
+        const float pe = fmaf(x, y, -p);
+        add(p, pe);
+    }
+    __device__ __forceinline__ void add(float h2, float l2) {
+        const float s = __fadd_rn(h, h2);
+        const float bb = __fsub_rn(s, h);
+        const float e = __fadd_rn(__fsub_rn(h, __fsub_rn(s, bb)), __fsub_rn(h2, bb));
+        h = s;
+        l = __fadd_rn(l, __fadd_rn(l2, e));
+    }
+    __device__ __forceinline__ void warp_sum() {
+        #pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float h2 = __shfl_xor_sync(0xffffffffu, h, o);
+            const float l2 = __shfl_xor_sync(0xffffffffu, l, o);
+            add(h2, l2);
+        }
+    }
+    // (h + l) / d as a normalised pair
+    __device__ __forceinline__ void div(float d, float& qh, float& ql) const {
+        const float q = __fdiv_rn(h, d);
+        const float r = __fadd_rn(fmaf(-q, d, h), l);   // h - q d is exact
+        const float q2 = __fdiv_rn(r, d);
+        qh = __fadd_rn(q, q2);
+        ql = __fsub_rn(q2, __fsub_rn(qh, q));
+    }
+};
+template <> struct DirSum<double> {
+    double h = 0.0;
+    __device__ __forceinline__ void add_prod(double x, double y) { h = fma(x, y, h); }
+    __device__ __forceinline__ void add(double h2, float) { h += h2; }
+    __device__ __forceinline__ void warp_sum() {
+        #pragma unroll
+        for (int o = 16; o > 0; o >>= 1) h += __shfl_xor_sync(0xffffffffu, h, o);
+    }
+    __device__ __forceinline__ void div(double d, double& qh, float& ql) const { qh = h / d; ql = 0.0f; }
+};
+
+// Build time: FP32 copies of the edges and profiles, and the running sums
+// P[b][m] = sum_{j<m} pi (ze[j+1] - ze[j]) (ze[j+1] + ze[j]) l_b[j] in FP64
+// (stored as FP64 and as an FP32 pair).  One CTA per basis.
+__global__ void rr_direct_prefix_kernel(ModelParams mp, const double* __restrict__ ze,
+                                        const double* __restrict__ basis, float* __restrict__ zef,
+                                        float* __restrict__ basisf, double* __restrict__ pre64,
+                                        float* __restrict__ pref) {
+    const int b = blockIdx.x, nz = mp.nz;
+    const double* lb = basis + (size_t)b * nz;
+    for (int j = threadIdx.x; j < nz; j += blockDim.x) basisf[(size_t)b * nz + j] = (float)lb[j];
+    if (b == 0)
+        for (int j = threadIdx.x; j <= nz; j += blockDim.x) zef[j] = (float)ze[j];
+    if (threadIdx.x != 0) return;
+    double* P = pre64 + (size_t)b * (nz + 1);
+    float* Ph = pref + (size_t)b * (nz + 1);
+    float* Pl = pref + (size_t)mp.nbasis * (nz + 1) + (size_t)b * (nz + 1);
+    double acc = 0.0;
+    P[0] = 0.0; Ph[0] = 0.0f; Pl[0] = 0.0f;
+    for (int m = 0; m < nz; ++m) {
+        acc += CUDART_PI * (ze[m + 1] - ze[m]) * (ze[m + 1] + ze[m]) * lb[m];
+        P[m + 1] = acc;
+        const float hi = (float)acc;
+        Ph[m + 1] = hi;
+        Pl[m + 1] = (float)(acc - (double)hi);
+    }
+}
+
+// Per call: one warp per (row, g node); rows are (pv, k slot) pairs.  The
+// warp finds the band's edges by bisection, evaluates them 32 at a time
+// (31 bins per pass, the next edge from the neighbouring lane) and sums the
+// bins' projections over its lanes.  Bases are taken kDirBases at a time.
+constexpr int kDirWarps = 8;
+constexpr int kDirBases = 5;
+
+template <typename A>
+__global__ void __launch_bounds__(kDirWarps * 32) rr_direct_table_kernel(
+        ModelParams mp, const double* __restrict__ params, const A* __restrict__ ze,
+        const A* __restrict__ basis, const double* __restrict__ basis64, const A* __restrict__ pre,
+        const float* __restrict__ pre_lo, DirectTables D, int grad) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int row = blockIdx.x;
+    const int ig = blockIdx.y * kDirWarps + warp;
+    if (ig >= mp.ng) return;
+    const int nz = mp.nz, ng = mp.ng;
+    const int nkp = mp.chromatic ? mp.npb : 1;
+    const int pv = row / nkp, slot = row - pv * nkp;
+    const double kd = params[(size_t)pv * mp.nparam + 6 + slot];
+    // bases of the row: every named basis; tabulated, the passband's own
+    // profile when k is per passband, else every passband's
+    int b_lo = 0, b_hi = mp.nbasis;
+    if (mp.ld_model == RR_LD_TABULATED && mp.chromatic) { b_lo = slot; b_hi = slot + 1; }
+    A* Thi = reinterpret_cast<A*>(D.hi);
+    A* Tdk = reinterpret_cast<A*>(D.dk);
+    const size_t bstride = (size_t)D.nrows * ng;
+    const size_t o = (size_t)row * ng + ig;
+    const bool valid = kd > 0.0 && kd < 1.0;
+    const double gd = ig * (1.0 / (ng - 1));
+    const A k = (A)kd, g = (A)gd, c = (A)(gd * (1.0 + kd));
+    A tk = 0, tc = 0;
+    const A atot = valid ? edge_area(A(1), k, c, tk, tc) : A(0);
+    if (!valid || ig == ng - 1 || !(atot > A(0))) {
+        // g = 1 (no covered area): the row's limit, all weight in the outermost
+        // annulus; rows of invalid k are zero (never read)
+        if (lane == 0)
+            for (int b = b_lo; b < b_hi; ++b) {
+                const double v = valid ? basis64[(size_t)b * nz + nz - 1] : 0.0;
+                Thi[b * bstride + o] = (A)v;
+                if (D.lo) D.lo[b * bstride + o] = (float)(v - (double)(A)v);
+                if (grad) Tdk[b * bstride + o] = A(0);
+            }
+        return;
+    }
+    const A lo_r = c > k ? c - k : k - c, hi_r = c + k;
+    // e0: last edge with ze <= |c - k| (ze[0] = 0); e1: first edge with ze >= c + k, else nz
+    int L = 0, H = nz + 1;
+    while (H - L > 1) {
+        const int m = (L + H) >> 1;
+        if (ze[m] <= lo_r) L = m; else H = m;
+    }
+    const int e0 = L;
+    L = -1; H = nz;
+    while (H - L > 1) {
+        const int m = (L + H) >> 1;
+        if (ze[m] >= hi_r) H = m; else L = m;
+    }
+    const int e1 = H;
+    const bool centre = c < k;   // the disk's centre is covered: annuli below e0 count whole
+    const A dtot = tk + g * tc;
+    for (int bg = b_lo; bg < b_hi; bg += kDirBases) {
+        const int nb = min(kDirBases, b_hi - bg);
+        DirSum<A> S[kDirBases];
+        A dS[kDirBases];
+        #pragma unroll
+        for (int q = 0; q < kDirBases; ++q) dS[q] = A(0);
+        #pragma unroll 1
+        for (int base = e0; base < e1; base += 31) {
+            const int j = base + lane;
+            A ak = 0, ac = 0, a = 0;
+            if (j <= e1) a = edge_area(ze[j], k, c, ak, ac);
+            const A da = ak + g * ac;
+            const A an = __shfl_down_sync(0xffffffffu, a, 1);
+            const A dan = __shfl_down_sync(0xffffffffu, da, 1);
+            if (lane < 31 && j < e1) {
+                const A d = an - a, dd = dan - da;
+                #pragma unroll
+                for (int q = 0; q < kDirBases; ++q) {
+                    if (q < nb) {
+                        const A lbj = basis[(size_t)(bg + q) * nz + j];
+                        S[q].add_prod(d, lbj);
+                        dS[q] += dd * lbj;
+                    }
+                }
+            }
+        }
+        #pragma unroll
+        for (int q = 0; q < kDirBases; ++q) {
+            if (q < nb) {
+                S[q].warp_sum();
+                if (grad)
+                    #pragma unroll
+                    for (int off = 16; off > 0; off >>= 1) dS[q] += __shfl_xor_sync(0xffffffffu, dS[q], off);
+            }
+        }
+        if (lane == 0) {
+            #pragma unroll
+            for (int q = 0; q < kDirBases; ++q) {
+                if (q >= nb) continue;
+                const int b = bg + q;
+                if (centre) S[q].add(pre[(size_t)b * (nz + 1) + e0], pre_lo ? pre_lo[(size_t)b * (nz + 1) + e0] : 0.0f);
+                A th;
+                float tl;
+                S[q].div(atot, th, tl);
+                Thi[b * bstride + o] = th;
+                if (D.lo) D.lo[b * bstride + o] = tl;
+                if (grad) Tdk[b * bstride + o] = (dS[q] - th * dtot) / atot;
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Per-call parameter-vector records.  Validation, orbit constants and
 // windows in FP64 (rounded to R); profile rows in R (FP32 in the mixed form).
 //
@@ -253,7 +529,7 @@ __global__ void __launch_bounds__(256, 4) rr_pv_setup_kernel(ModelParams mp, PbP
                                                           const R* __restrict__ T, const float* __restrict__ DT,
                                                           const double* __restrict__ istar,
                                                           RecLayout L, int grad, char* __restrict__ records,
-                                                          int32_t* __restrict__ pv_status) {
+                                                          int32_t* __restrict__ pv_status, DirectTables D) {
     constexpr int NP = SetupPvs<R>::N;
     __shared__ R u_s[NP][RR_MAX_PB][4];
     __shared__ R invIs_s[NP][RR_MAX_PB];
@@ -299,14 +575,24 @@ __global__ void __launch_bounds__(256, 4) rr_pv_setup_kernel(ModelParams mp, PbP
         }
         if (!(Is > 0.0)) st |= RR_PV_LD_INVALID;
         const double k = row[6 + (mp.chromatic ? pb : 0)];
-        if (!(k >= mp.k0 && k <= mp.k1)) st |= RR_PV_K_RANGE;
-        const double x = (k - mp.k0) / mp.dk;
-        int ik = (int)floor(x);
-        ik = ik < 0 ? 0 : (ik > mp.nk - 2 ? mp.nk - 2 : ik);
+        int ik;
+        double ak;
+        if (mp.direct) {
+            // the row of this (pv, k slot) in the per-call projections
+            if (!(k > 0.0 && k < 1.0)) st |= RR_PV_K_RANGE;
+            ik = (pv0 + lp) * nkp + (mp.chromatic ? pb : 0);
+            ak = 0.0;
+        } else {
+            if (!(k >= mp.k0 && k <= mp.k1)) st |= RR_PV_K_RANGE;
+            const double x = (k - mp.k0) / mp.dk;
+            ik = (int)floor(x);
+            ik = ik < 0 ? 0 : (ik > mp.nk - 2 ? mp.nk - 2 : ik);
+            ak = x - ik;
+        }
         for (int j = 0; j < 4; ++j) u_s[lp][pb][j] = (R)u[j];
         invIs_s[lp][pb] = (R)(1.0 / Is);
         ik_s[lp][pb] = ik;
-        ak_s[lp][pb] = (R)(x - ik);
+        ak_s[lp][pb] = (R)ak;
         if (st) atomicOr(&st_s[lp], st);
     }
     __syncthreads();
@@ -511,6 +797,51 @@ __global__ void __launch_bounds__(256, 4) rr_pv_setup_kernel(ModelParams mp, PbP
         #pragma unroll
         for (int c = 0; c < 4; ++c) Ic[c] = (grad && c < nc) ? (R)istar[1 + c] : R(0);
         const int b0 = named ? 0 : pb;
+        if (mp.direct) {
+            // direct model: the pv's own projections (no k interpolation); the
+            // in-cell slopes come from the differences of the FP32 pairs
+            const size_t ds = (size_t)D.nrows * mp.ng;
+            const size_t o0 = (size_t)b0 * ds + (size_t)ik * mp.ng;
+            const R* Hp = reinterpret_cast<const R*>(D.hi) + o0;
+            const float* Lp = D.lo ? D.lo + o0 : nullptr;
+            const R* Kp = grad ? reinterpret_cast<const R*>(D.dk) + o0 : nullptr;
+            const int ig_end = min(L.ng_pad, 64 * ch + 64);
+            for (int ig = 64 * ch + lane; ig < ig_end; ig += 32) {
+                if (ig >= mp.ng) {
+                    for (int r = 0; r < L.rows_per_pb; ++r) r0[(size_t)r * L.ng_pad + ig] = (R)0;
+                    continue;
+                }
+                R vb[5];
+                #pragma unroll
+                for (int c = 0; c < 5; ++c)
+                    vb[c] = (c == 0 || c <= nc) ? Hp[c * ds + ig] + (Lp ? (R)Lp[c * ds + ig] : R(0)) : R(0);
+                R v = vb[0];
+                #pragma unroll
+                for (int c = 0; c < 4; ++c) v += uc[c] * vb[1 + c];
+                const R ldw_n = v * invIs;
+                r0[ig] = ldw_n;
+                if (!grad) continue;
+                R dv = 0, kv = 0;
+                #pragma unroll
+                for (int c = 0; c < 5; ++c) {
+                    if (c == 0 || c <= nc) {
+                        const R w = c == 0 ? R(1) : uc[c - 1];
+                        if (ig < mp.ng - 1) {
+                            R dd = Hp[c * ds + ig + 1] - Hp[c * ds + ig];
+                            if (Lp) dd += (R)(Lp[c * ds + ig + 1] - Lp[c * ds + ig]);
+                            dv += w * dd;
+                        }
+                        kv += w * Kp[c * ds + ig];
+                    }
+                }
+                r0[L.ng_pad + ig] = dv * invIs;
+                r0[2 * L.ng_pad + ig] = kv * invIs;
+                #pragma unroll
+                for (int c = 0; c < 4; ++c)
+                    if (c < nc) r0[(size_t)(3 + c) * L.ng_pad + ig] = (vb[1 + c] - ldw_n * Ic[c]) * invIs;
+            }
+            continue;
+        }
         const R* T0p = T + (size_t)b0 * bstride + (size_t)ik * kstride;
         const float* D0p = DT + (size_t)b0 * bstride + (size_t)ik * kstride;
         const int ig_end = min(L.ng_pad, 64 * ch + 64);
@@ -578,6 +909,8 @@ ModelParams model_params(const rr_ctx* c) {
     mp.k1 = c->cfg.k1;
     mp.dk = c->dk;
     mp.inv_dk = 1.0 / c->dk;
+    mp.direct = c->cfg.direct;
+    mp.nz = c->nz;
     // int_0^1 mu / (e^mu - 1) dmu = pi^2/6 - Li2(1/e) + ln(1 - 1/e) (expand 1/(e^mu - 1) = sum_k e^(-k mu));
     // Li2(1/e) = sum_k e^(-k) / k^2, 40 terms below 1e-18
     double li2 = 0.0, p = 1.0;
@@ -614,21 +947,71 @@ cudaError_t launch_weights(rr_ctx* c, bool need_w, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+size_t direct_bytes(const rr_ctx* c, int npv, bool grad) {
+    const size_t n = (size_t)c->nbasis * npv * c->nkp * c->cfg.ng;
+    const size_t rb = c->cfg.precision == RR_PREC_FP64 ? sizeof(double) : sizeof(float);
+    size_t b = align256(n * rb);
+    if (c->cfg.precision == RR_PREC_MIXED) b += align256(n * sizeof(float));
+    if (grad) b += align256(n * rb);
+    return b;
+}
+
+DirectTables direct_view(const rr_ctx* c, void* base, int npv, bool grad) {
+    DirectTables D;
+    const size_t n = (size_t)c->nbasis * npv * c->nkp * c->cfg.ng;
+    const size_t rb = c->cfg.precision == RR_PREC_FP64 ? sizeof(double) : sizeof(float);
+    char* p = (char*)base;
+    D.hi = p;
+    p += align256(n * rb);
+    D.lo = nullptr;
+    if (c->cfg.precision == RR_PREC_MIXED) {
+        D.lo = (float*)p;
+        p += align256(n * sizeof(float));
+    }
+    D.dk = grad ? p : nullptr;
+    D.nrows = npv * c->nkp;
+    return D;
+}
+
+cudaError_t launch_direct_prefix(rr_ctx* c, cudaStream_t s) {
+    ModelParams mp = model_params(c);
+    rr_direct_prefix_kernel<<<c->nbasis, 256, 0, s>>>(mp, c->d_ze, c->d_basis, c->d_zef, c->d_basisf, c->d_pre64,
+                                                      c->d_pref);
+    c->launches++;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_direct_tables(rr_ctx* c, const double* params, int npv, bool grad, const DirectTables& D,
+                                 cudaStream_t s) {
+    if (npv == 0) return cudaSuccess;
+    ModelParams mp = model_params(c);
+    const dim3 grid((unsigned)(npv * c->nkp), (unsigned)((c->cfg.ng + kDirWarps - 1) / kDirWarps));
+    if (c->cfg.precision == RR_PREC_FP64)
+        rr_direct_table_kernel<double><<<grid, kDirWarps * 32, 0, s>>>(mp, params, c->d_ze, c->d_basis, c->d_basis,
+                                                                       c->d_pre64, nullptr, D, grad ? 1 : 0);
+    else
+        rr_direct_table_kernel<float><<<grid, kDirWarps * 32, 0, s>>>(
+            mp, params, c->d_zef, c->d_basisf, c->d_basis, c->d_pref,
+            c->d_pref + (size_t)c->nbasis * (c->nz + 1), D, grad ? 1 : 0);
+    c->launches++;
+    return cudaGetLastError();
+}
+
 cudaError_t launch_pv_setup(rr_ctx* c, const double* params, int npv, const PbParams& pbp, bool grad,
                             void* records, int32_t* pv_status, cudaStream_t s) {
     ModelParams mp = model_params(c);
+    DirectTables D = {nullptr, nullptr, nullptr, 0};
+    if (c->cfg.direct) D = direct_view(c, (char*)records + align256(records_bytes(c, npv, grad)), npv, grad);
+    const int ppc = setup_pvs_per_cta(c->cfg.npb);
+    const int blocks = (npv + ppc - 1) / ppc;
     if (c->cfg.precision == RR_PREC_FP64) {
-        const int ppc = setup_pvs_per_cta(c->cfg.npb);
-        const int blocks = (npv + ppc - 1) / ppc;
         RecLayout L = make_layout<double>(c->cfg.npb, c->cfg.ng, c->nldc, grad);
         rr_pv_setup_kernel<double><<<blocks, 256, 0, s>>>(mp, pbp, params, npv, c->d_T64, c->d_DT32, c->d_istar, L,
-                                                          grad ? 1 : 0, (char*)records, pv_status);
+                                                          grad ? 1 : 0, (char*)records, pv_status, D);
     } else {
-        const int ppc = setup_pvs_per_cta(c->cfg.npb);
-        const int blocks = (npv + ppc - 1) / ppc;
         RecLayout L = make_layout<float>(c->cfg.npb, c->cfg.ng, c->nldc, grad);
         rr_pv_setup_kernel<float><<<blocks, 256, 0, s>>>(mp, pbp, params, npv, c->d_T32, c->d_DT32, c->d_istar, L,
-                                                         grad ? 1 : 0, (char*)records, pv_status);
+                                                         grad ? 1 : 0, (char*)records, pv_status, D);
     }
     c->launches++;
     return cudaGetLastError();

@@ -34,7 +34,8 @@ EXPORTS = ["rr_create", "rr_destroy", "rr_set_ld_profile", "rr_build_weights", "
            "rr_evaluate_noalloc", "rr_prepare", "rr_evaluate_prepared", "rr_evaluate_grad_prepared",
            "rr_evaluate_host", "rr_request_bytes", "rr_enqueue_host", "rr_server_create", "rr_server_destroy",
            "rr_server_submit", "rr_server_poll", "rr_server_pending"]
-KERNELS = {"ld_basis": 0, "weights": 1, "pv_setup": 2, "flux": 3, "grad": 4, "grad_reduce": 5, "points": 6}
+KERNELS = {"ld_basis": 0, "weights": 1, "pv_setup": 2, "flux": 3, "grad": 4, "grad_reduce": 5, "points": 6,
+           "direct": 7}
 
 
 class RRConfig(ctypes.Structure):
@@ -42,7 +43,7 @@ class RRConfig(ctypes.Structure):
                 ("ng", ctypes.c_int32), ("nk", ctypes.c_int32), ("k0", ctypes.c_double),
                 ("k1", ctypes.c_double), ("npb", ctypes.c_int32), ("ld_model", ctypes.c_int32),
                 ("chromatic", ctypes.c_int32), ("precision", ctypes.c_int32), ("device", ctypes.c_int32),
-                ("ncoef", ctypes.c_int32)]
+                ("ncoef", ctypes.c_int32), ("direct", ctypes.c_int32)]
 
 
 class RRError(RuntimeError):
@@ -136,10 +137,13 @@ class Model:
     precision  'mixed' (FP32 bulk, float flux) or 'fp64' (double flux)
     grid       dict(zcut, nzin, nzlimb, ng, nk, k0, k1)
     n_general  terms of the general law (1..4)
+    direct     the direct model: weights for each k computed per call, interpolation in g
+               only, any 0 < k < 1 (the grid's nk, k0, k1 are then unused)
     """
 
     def __init__(self, ld_model: str = "quadratic", npb: int = 1, chromatic: bool = False,
-                 precision: str = "mixed", grid: Optional[dict] = None, device: int = 0, n_general: int = 0):
+                 precision: str = "mixed", grid: Optional[dict] = None, device: int = 0, n_general: int = 0,
+                 direct: bool = False):
         from .workloads import GRID
         g = dict(GRID if grid is None else grid)
         self.lib = load_library()
@@ -147,10 +151,11 @@ class Model:
             raise RuntimeError("a CUDA device is required")
         self.device = torch.device("cuda", device)
         self.ld_model, self.npb, self.chromatic, self.precision = ld_model, npb, chromatic, precision
+        self.direct = bool(direct)
         self.grid = g
         cfg = RRConfig(g["zcut"], g["nzin"], g["nzlimb"], g["ng"], g["nk"], g["k0"], g["k1"], npb,
                        LD_MODELS[ld_model], int(chromatic), PRECISIONS[precision], device,
-                       int(n_general) if ld_model == "general" else 0)
+                       int(n_general) if ld_model == "general" else 0, int(bool(direct)))
         h = ctypes.c_void_p()
         st = self.lib.rr_create(ctypes.byref(cfg), ctypes.byref(h))
         if st != 0:
@@ -423,7 +428,8 @@ class _RRFlux(torch.autograd.Function):
 
 def model_for(wl, device: int = 0) -> Model:
     """Model context for a :class:`workloads.Workload`, with profiles set and tables built."""
-    m = Model(wl.ld_model, wl.npb, wl.chromatic, wl.precision, wl.grid, device, getattr(wl, "n_general", 0))
+    m = Model(wl.ld_model, wl.npb, wl.chromatic, wl.precision, wl.grid, device, getattr(wl, "n_general", 0),
+              getattr(wl, "direct", False))
     if wl.ld_model == "tabulated":
         for pb, (mu, it) in enumerate(wl.profiles):
             m.set_ld_profile(pb, mu, it)

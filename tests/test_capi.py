@@ -47,7 +47,8 @@ def test_null_handles_are_rejected_without_a_device(lib):
 
 @pytest.mark.parametrize("field,value,msg", [("zcut", 1.5, b"zcut"), ("nzin", 0, b"nzin"), ("ng", 1, b"ng"),
                                              ("k1", 0.001, b"k0"), ("npb", 40, b"npb"), ("ld_model", 9, b"ld_model"),
-                                             ("precision", 5, b"precision"), ("chromatic", 2, b"chromatic")])
+                                             ("precision", 5, b"precision"), ("chromatic", 2, b"chromatic"),
+                                             ("direct", 2, b"direct")])
 def test_create_rejects_bad_config_before_touching_the_device(lib, field, value, msg):
     cfg = rr.RRConfig(0.7, 200, 300, 200, 60, 0.005, 0.3, 1, 1, 0, 1, 0)
     setattr(cfg, field, value)
@@ -55,6 +56,17 @@ def test_create_rejects_bad_config_before_touching_the_device(lib, field, value,
     assert lib.rr_create(ctypes.byref(cfg), ctypes.byref(out)) == 1
     assert out.value is None
     assert msg in lib.rr_last_error(None)
+
+
+def test_direct_model_does_not_check_the_k_grid(lib):
+    # the direct model has no k table: nk, k0, k1 are ignored (validation passes on to the device)
+    cfg = rr.RRConfig(0.7, 200, 300, 200, 0, 0.0, 0.0, 1, 1, 0, 1, 0, 0, 1)
+    out = ctypes.c_void_p()
+    st = lib.rr_create(ctypes.byref(cfg), ctypes.byref(out))
+    msg = lib.rr_last_error(None)
+    assert b"nk" not in msg and b"k0" not in msg
+    if st == 0:
+        lib.rr_destroy(out)
 
 
 @pytest.mark.parametrize("ld_model,ncoef", [(6, 0), (6, 5), (1, 2), (8, 1)])
@@ -75,10 +87,24 @@ def test_status_bits_match_the_oracle():
         assert re.search(rf"#define {name}\s+{val}\b", hdr)
 
 
-def test_config_struct_layout_matches_header():
-    # zcut(8) nzin ng.. : offsets as laid out by a C compiler for the header's struct
-    assert ctypes.sizeof(rr.RRConfig) == 64
-    assert rr.RRConfig.k0.offset == 24 and rr.RRConfig.device.offset == 56
+def test_config_struct_layout_matches_header(tmp_path):
+    """The ctypes mirror of rr_config has the size and field offsets a C compiler gives the header's struct."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    names = [f[0] for f in rr.RRConfig._fields_]
+    src = tmp_path / "layout.c"
+    src.write_text("#include <stdio.h>\n#include <stddef.h>\n#include \"rr.h\"\nint main(void) {\n"
+                   '  printf("%zu\\n", sizeof(rr_config));\n' +
+                   "".join(f'  printf("%zu\\n", offsetof(rr_config, {n}));\n' for n in names) +
+                   "  return 0;\n}\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c99", "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)], check=True)
+    got = [int(x) for x in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()]
+    assert got[0] == ctypes.sizeof(rr.RRConfig)
+    assert got[1:] == [getattr(rr.RRConfig, n).offset for n in names]
 
 
 def test_no_cpu_fallback_without_cuda(monkeypatch):

@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64-form", action="store_true")
+    ap.add_argument("--no-direct", action="store_true")
     return ap.parse_args()
 
 
@@ -315,6 +316,9 @@ def run_ours(a):
     fp64 = None
     if not a.no_fp64_form and esize == 4:
         fp64 = run_fp64_form(a, wl, grad, local, dev, flush)
+    direct = None
+    if not a.no_direct and esize == 4:
+        direct = run_direct_model(a, wl, grad, local, dev, flush)
 
     e2e = None
     if not a.no_e2e:
@@ -340,6 +344,7 @@ def run_ours(a):
         "in_transit_fraction": in_transit,
         "roofline": roof, "roofline_flux": roof_flux, "kernels": kernels, "cpu_baseline": cpu_base,
         "fp64_form": None if fp64 is None else dict(fp64, speedup_of_mixed=value / world / fp64["value"]),
+        "direct_model": direct,
         "e2e": e2e, "clocks": clk, "gpu_launches": launches,
     }
     if rank == 0:
@@ -405,6 +410,66 @@ def run_fp64_form(a, wl, grad, local, dev, flush):
     torch.cuda.empty_cache()
     return {"value": wl.npv * wl.samples_per_pv() / (ms * 1e-3), "unit": "points/s", "ms_per_step": ms,
             "steps": n, "dtype": "f64", "note": "same workload and step through the FP64 kernels, one GPU"}
+
+
+def run_direct_model(a, wl, grad, local, dev, flush):
+    """The same workload and step through the direct model (weights for every pv's own k computed
+    inside each step, interpolation in g only), mixed form, timed the same way."""
+    import copy
+
+    import torch
+
+    from paper_2009_08500_gb300 import rr
+    wd = copy.copy(wl)
+    wd.direct = True
+    md = rr.model_for(wd, device=local)
+    t, pb, p = rr.to_device(wd, local)
+    flux = torch.empty((wl.npv, wl.npt), dtype=md.dtype, device=dev)
+    ws_f = md.workspace(wl.npv, wl.npt, False)
+    if grad:
+        ws_g = md.workspace(wl.npv, wl.npt, True)
+        gbar = torch.randn((wl.npv, wl.npt), dtype=md.dtype, device=dev,
+                           generator=torch.Generator(device=dev).manual_seed(1234))
+        gout = torch.empty((wl.npv, md.nparam), dtype=torch.float64, device=dev)
+    ss, ex = wl.supersampling, wl.exptime
+
+    def step():
+        if grad:
+            md.prepare(t, p, pb, ss, ex, workspace=ws_g)
+            md.evaluate(t, p, pb, ss, ex, out=flux, prepared=ws_g)
+            md.evaluate_grad(t, p, gbar, pb, ss, ex, out=gout, prepared=ws_g)
+        else:
+            md.evaluate(t, p, pb, ss, ex, out=flux, workspace=ws_f)
+
+    for _ in range(3):
+        step()
+    n = 10
+
+    def run(k):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
+        torch.cuda.synchronize()
+        for i in range(k):
+            flush.fill_(i & 0xFF)
+            ev[i][0].record()
+            step()
+            ev[i][1].record()
+        torch.cuda.synchronize()
+        return sum(s.elapsed_time(e) for s, e in ev) / k
+
+    ms = run(n)
+    md.profile(True)
+    md.profile_read(reset=True)
+    run(n)
+    kp = md.profile_read(reset=True)
+    md.profile(False)
+    dms, dn = kp["direct"]
+    del flux, ws_f, t, pb, p
+    if grad:
+        del ws_g, gbar, gout
+    torch.cuda.empty_cache()
+    return {"value": wl.npv * wl.samples_per_pv() / (ms * 1e-3), "unit": "points/s", "ms_per_step": ms,
+            "steps": n, "dtype": "f32+f64", "direct_table_ms_per_launch": round(dms / max(dn, 1), 5),
+            "note": "same workload and step through the direct model (per-call weights for each k), one GPU"}
 
 
 def run_e2e(a, model, wl, grad, dev):

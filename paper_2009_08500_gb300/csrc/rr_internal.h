@@ -130,6 +130,7 @@ struct ModelParams {
     double k0, k1, dk;
     double inv_dk;   // 1 / dk (host FP64)
     double exp_c;    // int_0^1 mu / (e^mu - 1) dmu (disk integral of the exponential law's second term)
+    double dg;       // 1 / (ng - 1)
 };
 
 // Per-call projections of the direct model (the workspace region after the

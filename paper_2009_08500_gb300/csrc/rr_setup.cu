@@ -197,64 +197,118 @@ __global__ void rr_diff_table_kernel(const double* __restrict__ T64, float* __re
 // covered area is the whole planet, so those annuli get no weight.
 // ---------------------------------------------------------------------------
 
-// phi(x) = x - sin x cos x = (2x - sin 2x) / 2, the area of a circular
-// segment of unit radius and half-angle x.  Below x = 0.75 the direct form
-// cancels, so it is summed from the Taylor series of sin (t = 2x):
+// Small-angle part of a circular segment: phi(x) = x - sin x cos x =
+// (2x - sin 2x) / 2 for x < 0.75, where that difference cancels, from the
+// Taylor series of sin (t = 2x):
 //   phi = t^3 / 12 (1 - t^2/20 + t^4/840 - t^6/60480 + t^8/6652800 - t^10/1037836800),
 // whose first omitted term is below 1e-9 of the sum there.
-__device__ __forceinline__ float seg_phi(float x) {
-    if (x < 0.75f) {
-        const float t = 2.0f * x, t2 = t * t;
-        float p = -1.0f / 1037836800.0f;
-        p = fmaf(p, t2, 1.0f / 6652800.0f);
-        p = fmaf(p, t2, -1.0f / 60480.0f);
-        p = fmaf(p, t2, 1.0f / 840.0f);
-        p = fmaf(p, t2, -1.0f / 20.0f);
-        p = fmaf(p, t2, 1.0f);
-        return t * t2 * (1.0f / 12.0f) * p;
-    }
-    return x - 0.5f * sinf(2.0f * x);
+__device__ __forceinline__ float seg_phi_small(float x) {
+    const float t = 2.0f * x, t2 = t * t;
+    float p = -1.0f / 1037836800.0f;
+    p = fmaf(p, t2, 1.0f / 6652800.0f);
+    p = fmaf(p, t2, -1.0f / 60480.0f);
+    p = fmaf(p, t2, 1.0f / 840.0f);
+    p = fmaf(p, t2, -1.0f / 20.0f);
+    p = fmaf(p, t2, 1.0f);
+    return t * t2 * (1.0f / 12.0f) * p;
 }
 
-// Area common to the radius-r disk and the planet (radius k, centre at
-// distance c) with its partials d a / d k (the planet's rim inside the disk,
-// 2 k kappa_1) and d a / d c (minus the common chord, -K / c).
-// FP32: the lens is the sum of two circular segments, r^2 phi(kappa_0) +
-// k^2 phi(kappa_1), each non-negative, so that the area keeps a few ulp of
-// relative accuracy when k << r (the textbook form r^2 kappa_0 + k^2 kappa_1
-// - K / 2 cancels there).  Heron's factors that vanish at a contact
-// (r + k - c, c + k - r, c + r - k) are formed as (x + y) - z with the
-// rounding error of x + y added back (error-free sum), so they keep their
-// relative accuracy next to the contact too.
+// x + y - z where x + y is close to z: the rounding error of x + y is added
+// back (error-free sum), so the result keeps its relative accuracy.
 __device__ __forceinline__ float sum3_small(float x, float y, float z) {
-    // x + y - z where x + y is close to z
     const float s = __fadd_rn(x, y);
     const float bb = __fsub_rn(s, x);
     const float e = __fadd_rn(__fsub_rn(x, __fsub_rn(s, bb)), __fsub_rn(y, bb));
     return __fadd_rn(__fsub_rn(s, z), e);
 }
 
-__device__ __forceinline__ float edge_area(float r, float k, float c, float& dk, float& dc) {
-    if (c >= r + k) { dk = 0.0f; dc = 0.0f; return 0.0f; }
-    if (c <= fabsf(r - k)) {
-        dc = 0.0f;
-        if (k < r) { dk = 2.0f * CUDART_PI_F * k; return CUDART_PI_F * k * k; }
-        dk = 0.0f;
-        return CUDART_PI_F * r * r;
+// Angle of the point (x, y), y >= 0, in [0, pi] (atan2 for the upper half
+// plane): folded onto t = min(y, |x|) / max(y, |x|) in [0, 1], where
+// atan(t) = t P(t^2) with a degree-8 polynomial P whose coefficients were
+// fitted here to minimise the largest relative error over [0, 1] (weighted
+// least squares on Chebyshev nodes, reweighted by the error); evaluated in
+// FP32 it stays within 2 ulp of atan, and within 4 ulp with the fast
+// quotient.  Then atan = pi/2 - atan(1/t) above the diagonal and
+// pi - angle for x < 0.
+__device__ __forceinline__ float atan2_upper(float y, float x) {
+    const float ax = fabsf(x);
+    const float mx = fmaxf(y, ax), mn = fminf(y, ax);
+    const float t = mx > 1e-30f ? __fdividef(mn, mx) : 0.0f;
+    const float u = t * t;
+    float p = 2.849952085e-03f;
+    p = fmaf(p, u, -1.606889814e-02f);
+    p = fmaf(p, u, 4.269199818e-02f);
+    p = fmaf(p, u, -7.504339516e-02f);
+    p = fmaf(p, u, 1.064095795e-01f);
+    p = fmaf(p, u, -1.420365125e-01f);
+    p = fmaf(p, u, 1.999262124e-01f);
+    p = fmaf(p, u, -3.333307207e-01f);
+    p = fmaf(p, u, 1.0f);
+    float a = t * p;
+    if (y > ax) a = CUDART_PIO2_F - a;
+    if (x < 0.0f) a = CUDART_PI_F - a;
+    return a;
+}
+
+// Area common to the radius-r disk and the planet (radius k, centre at
+// distance c) with its partials d a / d k (the planet's rim inside the disk,
+// 2 k kappa_1) and d a / d c (minus the common chord, -K / c); inv_c = 1 / c
+// and inv4c2 = 1 / (4 c^2) are the caller's.
+// FP32: the lens is the sum of two circular segments, r^2 phi(kappa_0) +
+// k^2 phi(kappa_1), phi(x) = x - sin x cos x, each non-negative, so that the
+// area keeps a few ulp of relative accuracy when k << r (the textbook form
+// r^2 kappa_0 + k^2 kappa_1 - K / 2 cancels there).  With K = 2 c h (h the
+// half chord) and x_0 = 2 c r cos kappa_0, x_1 = 2 c k cos kappa_1,
+// r^2 sin kappa_0 cos kappa_0 = K x_0 / (4 c^2) and k^2 sin kappa_1 cos kappa_1
+// = K x_1 / (4 c^2), so no sine is evaluated.  Heron's factors that vanish at
+// a contact (r + k - c, c + k - r, c + r - k) are formed by sum3_small, and
+// their signs decide disjoint and nested circles.  Each cosine numerator is
+// a sum of a square and a difference of squares, taken with the pair of radii
+// or distances that is closest (that difference is then exact): it vanishes
+// without cancellation error when r ~ k at small c.
+// far = (c >= 2 k): every edge that reaches the lens has c/2 <= r <= 2c, so
+// r - c is exact and the factors need no compensation.
+__device__ __forceinline__ float edge_area(float r, float k, float c, float inv_c, float inv4c2, bool far,
+                                           float& dk, float& dc) {
+    float p1, p2, s2;
+    if (far) {
+        const float dr = r - c;
+        p1 = k + dr;                // r + k - c
+        p2 = k - dr;                // c + k - r
+        s2 = (c + r) - k;           // c + r - k >= 2 k here
+    } else {
+        p1 = sum3_small(r, k, c);
+        p2 = sum3_small(c, k, r);
+        s2 = sum3_small(c, r, k);
     }
-    const float dr = r - c;
-    const float p1 = sum3_small(r, k, c), p2 = sum3_small(c, k, r), s1 = r + k + c, s2 = sum3_small(c, r, k);
-    const float K = sqrtf(fmaxf((p1 * p2) * (s1 * s2), 0.0f));   // 2 c x (half chord)
-    const float x0 = fmaf(c - k, c + k, r * r);                     // 2 c r cos(kappa_0)
-    const float x1 = fmaf(-dr, c + r, k * k);                       // 2 c k cos(kappa_1)
-    const float kap0 = atan2f(K, x0), kap1 = atan2f(K, x1);
-    dk = 2.0f * k * kap1;
-    dc = -K / c;
-    return r * r * seg_phi(kap0) + k * k * seg_phi(kap1);
+    // branch-free: the lens formula is evaluated for every edge (finite or
+    // NaN garbage outside the lens) and the closed forms of disjoint and
+    // nested circles are selected afterwards
+    const float s1 = r + k + c;
+    const float P = (p1 * p2) * (s1 * s2);
+    const float K = P > 1e-30f ? P * rsqrtf(P) : 0.0f;              // 2 c x (half chord)
+    const float r2 = r * r, k2 = k * k, c2 = c * c;
+    // 2 c r cos(kappa_0) = c^2 + r^2 - k^2, 2 c k cos(kappa_1) = c^2 + k^2 - r^2
+    const float drk = r - k;
+    const float x0 = fabsf(drk) < fabsf(c - k) ? fmaf(drk, r + k, c2) : fmaf(c - k, c + k, r2);
+    const float x1 = fabsf(drk) < fabsf(c - r) ? fmaf(-drk, r + k, c2) : fmaf(c - r, c + r, k2);
+    const float kap0 = atan2_upper(K, x0), kap1 = atan2_upper(K, x1);
+    const float q = K * inv4c2;
+    const float seg0 = kap0 < 0.75f ? r2 * seg_phi_small(kap0) : fmaf(r2, kap0, -q * x0);
+    const float seg1 = kap1 < 0.75f ? k2 * seg_phi_small(kap1) : fmaf(k2, kap1, -q * x1);
+    float a = seg0 + seg1;
+    float ddk = 2.0f * k * kap1, ddc = -K * inv_c;
+    if (s2 <= 0.0f) { a = CUDART_PI_F * r2; ddk = 0.0f; ddc = 0.0f; }                    // disk inside the planet
+    if (p2 <= 0.0f) { a = CUDART_PI_F * k2; ddk = 2.0f * CUDART_PI_F * k; ddc = 0.0f; }  // planet inside the disk
+    if (p1 <= 0.0f) { a = 0.0f; ddk = 0.0f; ddc = 0.0f; }                                 // disjoint
+    dk = ddk;
+    dc = ddc;
+    return a;
 }
 
 // FP64: the textbook form (its cancellation for k << r costs r / k ulp of FP64).
-__device__ __forceinline__ double edge_area(double r, double k, double c, double& dk, double& dc) {
+__device__ __forceinline__ double edge_area(double r, double k, double c, double, double, bool, double& dk,
+                                            double& dc) {
     if (c >= r + k) { dk = 0.0; dc = 0.0; return 0.0; }
     if (c <= fabs(r - k)) {
         dc = 0.0;
@@ -272,17 +326,19 @@ __device__ __forceinline__ double edge_area(double r, double k, double c, double
     return r * r * kap0 + k * k * kap1 - 0.5 * K;
 }
 
-// Sums of products for the projections.  FP32: an unevaluated float pair
-// (error-free product and sum, with rounding-exact intrinsics that the
-// compiler does not contract), so that neighbouring g nodes differ by their
-// true difference; FP64: plain sums.
+// Sums of products for the projections.  FP32: compensated (Kahan) sums
+// kept as an unevaluated float pair (h, l), with rounding-exact intrinsics
+// that the compiler does not contract, so that neighbouring g nodes differ by
+// their true difference (the products' own roundings are far below the
+// areas' few-ulp errors); FP64: plain sums.
 template <typename A> struct DirSum;
 template <> struct DirSum<float> {
     float h = 0.0f, l = 0.0f;
     __device__ __forceinline__ void add_prod(float x, float y) {
-        const float p = __fmul_rn(x, y);
-        const float pe = fmaf(x, y, -p);
-        add(p, pe);
+        const float y2 = __fadd_rn(__fmul_rn(x, y), l);
+        const float t = __fadd_rn(h, y2);
+        l = __fsub_rn(y2, __fsub_rn(t, h));
+        h = t;
     }
     __device__ __forceinline__ void add(float h2, float l2) {
         const float s = __fadd_rn(h, h2);
@@ -290,14 +346,6 @@ template <> struct DirSum<float> {
         const float e = __fadd_rn(__fsub_rn(h, __fsub_rn(s, bb)), __fsub_rn(h2, bb));
         h = s;
         l = __fadd_rn(l, __fadd_rn(l2, e));
-    }
-    __device__ __forceinline__ void warp_sum() {
-        #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const float h2 = __shfl_xor_sync(0xffffffffu, h, o);
-            const float l2 = __shfl_xor_sync(0xffffffffu, l, o);
-            add(h2, l2);
-        }
     }
     // (h + l) / d as a normalised pair
     __device__ __forceinline__ void div(float d, float& qh, float& ql) const {
@@ -312,10 +360,6 @@ template <> struct DirSum<double> {
     double h = 0.0;
     __device__ __forceinline__ void add_prod(double x, double y) { h = fma(x, y, h); }
     __device__ __forceinline__ void add(double h2, float) { h += h2; }
-    __device__ __forceinline__ void warp_sum() {
-        #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) h += __shfl_xor_sync(0xffffffffu, h, o);
-    }
     __device__ __forceinline__ void div(double d, double& qh, float& ql) const { qh = h / d; ql = 0.0f; }
 };
 
@@ -346,10 +390,14 @@ __global__ void rr_direct_prefix_kernel(ModelParams mp, const double* __restrict
     }
 }
 
-// Per call: one warp per (row, g node); rows are (pv, k slot) pairs.  The
-// warp finds the band's edges by bisection, evaluates them 32 at a time
-// (31 bins per pass, the next edge from the neighbouring lane) and sums the
-// bins' projections over its lanes.  Bases are taken kDirBases at a time.
+// Per call: one thread per (row, g node), rows being (pv, k slot) pairs and
+// the 32 lanes of a warp neighbouring g nodes of one row (their bands
+// overlap, so the edges and profiles they read are shared through L1).  Each
+// thread finds its band's edges by bisection, walks them once (the area of
+// an edge serves both bins it bounds) and sums the bins' projections, bases
+// kDirBases at a time.  The FP32 form takes c = g (1 + k) rounded to FP32 and
+// adds the first-order effect of that rounding, (d a / d c) c_lo, to every
+// area, so the nodes' positions are exact to FP32 working accuracy.
 constexpr int kDirWarps = 8;
 constexpr int kDirBases = 5;
 
@@ -358,11 +406,13 @@ __global__ void __launch_bounds__(kDirWarps * 32) rr_direct_table_kernel(
         ModelParams mp, const double* __restrict__ params, const A* __restrict__ ze,
         const A* __restrict__ basis, const double* __restrict__ basis64, const A* __restrict__ pre,
         const float* __restrict__ pre_lo, DirectTables D, int grad) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int row = blockIdx.x;
-    const int ig = blockIdx.y * kDirWarps + warp;
-    if (ig >= mp.ng) return;
-    const int nz = mp.nz, ng = mp.ng;
+    const int ng = mp.ng, nz = mp.nz;
+    const int wpr = (ng + 31) >> 5;   // warps per row
+    const long long w = (long long)blockIdx.x * kDirWarps + (threadIdx.x >> 5);
+    if (w >= (long long)D.nrows * wpr) return;
+    const int row = (int)(w / wpr);
+    const int ig = (int)(w - (long long)row * wpr) * 32 + (threadIdx.x & 31);
+    if (ig >= ng) return;
     const int nkp = mp.chromatic ? mp.npb : 1;
     const int pv = row / nkp, slot = row - pv * nkp;
     const double kd = params[(size_t)pv * mp.nparam + 6 + slot];
@@ -375,20 +425,24 @@ __global__ void __launch_bounds__(kDirWarps * 32) rr_direct_table_kernel(
     const size_t bstride = (size_t)D.nrows * ng;
     const size_t o = (size_t)row * ng + ig;
     const bool valid = kd > 0.0 && kd < 1.0;
-    const double gd = ig * (1.0 / (ng - 1));
-    const A k = (A)kd, g = (A)gd, c = (A)(gd * (1.0 + kd));
+    const A k = (A)kd;
+    const double gd = ig * mp.dg;
+    const double cd = gd * (1.0 + (double)k);
+    const A c = (A)cd, c_lo = (A)(cd - (double)c), g = (A)gd;
+    const A inv_c = A(1) / c, inv4c2 = A(0.25) * inv_c * inv_c;
+    const bool far = c >= A(2) * k;
     A tk = 0, tc = 0;
-    const A atot = valid ? edge_area(A(1), k, c, tk, tc) : A(0);
+    A atot = valid ? edge_area(A(1), k, c, inv_c, inv4c2, far, tk, tc) : A(0);
+    atot += tc * c_lo;
     if (!valid || ig == ng - 1 || !(atot > A(0))) {
         // g = 1 (no covered area): the row's limit, all weight in the outermost
         // annulus; rows of invalid k are zero (never read)
-        if (lane == 0)
-            for (int b = b_lo; b < b_hi; ++b) {
-                const double v = valid ? basis64[(size_t)b * nz + nz - 1] : 0.0;
-                Thi[b * bstride + o] = (A)v;
-                if (D.lo) D.lo[b * bstride + o] = (float)(v - (double)(A)v);
-                if (grad) Tdk[b * bstride + o] = A(0);
-            }
+        for (int b = b_lo; b < b_hi; ++b) {
+            const double v = valid ? basis64[(size_t)b * nz + nz - 1] : 0.0;
+            Thi[b * bstride + o] = (A)v;
+            if (D.lo) D.lo[b * bstride + o] = (float)(v - (double)(A)v);
+            if (grad) Tdk[b * bstride + o] = A(0);
+        }
         return;
     }
     const A lo_r = c > k ? c - k : k - c, hi_r = c + k;
@@ -399,7 +453,7 @@ __global__ void __launch_bounds__(kDirWarps * 32) rr_direct_table_kernel(
         if (ze[m] <= lo_r) L = m; else H = m;
     }
     const int e0 = L;
-    L = -1; H = nz;
+    L = e0; H = nz;
     while (H - L > 1) {
         const int m = (L + H) >> 1;
         if (ze[m] >= hi_r) H = m; else L = m;
@@ -413,48 +467,38 @@ __global__ void __launch_bounds__(kDirWarps * 32) rr_direct_table_kernel(
         A dS[kDirBases];
         #pragma unroll
         for (int q = 0; q < kDirBases; ++q) dS[q] = A(0);
+        A ak, ac;
+        A a0 = edge_area(ze[e0], k, c, inv_c, inv4c2, far, ak, ac);
+        a0 += ac * c_lo;
+        A da0 = ak + g * ac;
         #pragma unroll 1
-        for (int base = e0; base < e1; base += 31) {
-            const int j = base + lane;
-            A ak = 0, ac = 0, a = 0;
-            if (j <= e1) a = edge_area(ze[j], k, c, ak, ac);
-            const A da = ak + g * ac;
-            const A an = __shfl_down_sync(0xffffffffu, a, 1);
-            const A dan = __shfl_down_sync(0xffffffffu, da, 1);
-            if (lane < 31 && j < e1) {
-                const A d = an - a, dd = dan - da;
-                #pragma unroll
-                for (int q = 0; q < kDirBases; ++q) {
-                    if (q < nb) {
-                        const A lbj = basis[(size_t)(bg + q) * nz + j];
-                        S[q].add_prod(d, lbj);
-                        dS[q] += dd * lbj;
-                    }
+        for (int j = e0; j < e1; ++j) {
+            A a1 = edge_area(ze[j + 1], k, c, inv_c, inv4c2, far, ak, ac);
+            a1 += ac * c_lo;
+            const A da1 = ak + g * ac;
+            const A d = a1 - a0, dd = da1 - da0;
+            #pragma unroll
+            for (int q = 0; q < kDirBases; ++q) {
+                if (q < nb) {
+                    const A lbj = basis[(size_t)(bg + q) * nz + j];
+                    S[q].add_prod(d, lbj);
+                    if (grad) dS[q] += dd * lbj;
                 }
             }
+            a0 = a1;
+            da0 = da1;
         }
         #pragma unroll
         for (int q = 0; q < kDirBases; ++q) {
-            if (q < nb) {
-                S[q].warp_sum();
-                if (grad)
-                    #pragma unroll
-                    for (int off = 16; off > 0; off >>= 1) dS[q] += __shfl_xor_sync(0xffffffffu, dS[q], off);
-            }
-        }
-        if (lane == 0) {
-            #pragma unroll
-            for (int q = 0; q < kDirBases; ++q) {
-                if (q >= nb) continue;
-                const int b = bg + q;
-                if (centre) S[q].add(pre[(size_t)b * (nz + 1) + e0], pre_lo ? pre_lo[(size_t)b * (nz + 1) + e0] : 0.0f);
-                A th;
-                float tl;
-                S[q].div(atot, th, tl);
-                Thi[b * bstride + o] = th;
-                if (D.lo) D.lo[b * bstride + o] = tl;
-                if (grad) Tdk[b * bstride + o] = (dS[q] - th * dtot) / atot;
-            }
+            if (q >= nb) continue;
+            const int b = bg + q;
+            if (centre) S[q].add(pre[(size_t)b * (nz + 1) + e0], pre_lo ? pre_lo[(size_t)b * (nz + 1) + e0] : 0.0f);
+            A th;
+            float tl;
+            S[q].div(atot, th, tl);
+            Thi[b * bstride + o] = th;
+            if (D.lo) D.lo[b * bstride + o] = tl;
+            if (grad) Tdk[b * bstride + o] = (dS[q] - th * dtot) / atot;
         }
     }
 }
@@ -910,6 +954,7 @@ ModelParams model_params(const rr_ctx* c) {
     mp.dk = c->dk;
     mp.inv_dk = 1.0 / c->dk;
     mp.direct = c->cfg.direct;
+    mp.dg = 1.0 / (c->cfg.ng - 1);
     mp.nz = c->nz;
     // int_0^1 mu / (e^mu - 1) dmu = pi^2/6 - Li2(1/e) + ln(1 - 1/e) (expand 1/(e^mu - 1) = sum_k e^(-k mu));
     // Li2(1/e) = sum_k e^(-k) / k^2, 40 terms below 1e-18
@@ -985,7 +1030,8 @@ cudaError_t launch_direct_tables(rr_ctx* c, const double* params, int npv, bool 
                                  cudaStream_t s) {
     if (npv == 0) return cudaSuccess;
     ModelParams mp = model_params(c);
-    const dim3 grid((unsigned)(npv * c->nkp), (unsigned)((c->cfg.ng + kDirWarps - 1) / kDirWarps));
+    const long long warps = (long long)npv * c->nkp * ((c->cfg.ng + 31) / 32);
+    const unsigned grid = (unsigned)((warps + kDirWarps - 1) / kDirWarps);
     if (c->cfg.precision == RR_PREC_FP64)
         rr_direct_table_kernel<double><<<grid, kDirWarps * 32, 0, s>>>(mp, params, c->d_ze, c->d_basis, c->d_basis,
                                                                        c->d_pre64, nullptr, D, grad ? 1 : 0);

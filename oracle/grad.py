@@ -22,7 +22,7 @@ import numpy as np
 from . import ld as _ld
 from . import orbit as _orbit
 from . import weights as _weights
-from .model import (Setup, _table, g_cell, k_cell, pv_status, sample_times, unpack, evaluate)
+from .model import (Setup, _table, g_cell, k_cell, pv_status, sample_times, unpack, evaluate, weights_k)
 
 
 def _area_and_partials(k, z):
@@ -143,18 +143,20 @@ def jacobian(setup: Setup, times, pb_index, row, supersampling, exptime):
         kcol = 6 + (pb if setup.chromatic else 0)
         lcol = 6 + nkp + pb * nldc
         k = ks[pb] if setup.chromatic else ks[0]
+        kw = weights_k(setup, ks, k)          # the weights' radius ratio (shared: mean over passbands)
+        shared = setup.shared and setup.chromatic
         table = _table(setup, pb)
         ldp = _ld.profile(setup.ld_model, setup.mu, ldc[pb], table)
         istar = _ld.istar(setup.ld_model, ldc[pb], table)
         dldp, distar = _ld_partials(setup.ld_model, setup.mu, ldc[pb], table)
         if setup.direct:
             # weights for this exact k and their k-derivative at fixed g (Sect. 3.1.2)
-            _, wk, wdk = _weights.calculate_weights(k, setup.ze, setup.ng, with_dk=True)
+            _, wk, wdk = _weights.calculate_weights(kw, setup.ze, setup.ng, with_dk=True)
             ldw = wk @ ldp
             dldw_dk = wdk @ ldp
             dldw_dc = [wk @ dldp[c] for c in range(dldp.shape[0])]
         else:
-            ik, ak = k_cell(setup, k)
+            ik, ak = k_cell(setup, kw)
             row_lo, row_hi = np.dot(setup.w[ik], ldp), np.dot(setup.w[ik + 1], ldp)
             ldw = (1.0 - ak) * row_lo + ak * row_hi
             dldw_dk = (row_hi - row_lo) / setup.dk
@@ -177,11 +179,18 @@ def jacobian(setup: Setup, times, pb_index, row, supersampling, exptime):
             A, dA_dz, dA_dk = _area_and_partials(k, zz)
             # f = 1 - ip A / I_star
             df_dz = -(dip_dg / (1.0 + k) * A + ip * dA_dz) / istar
-            df_dk = -((dip_dk_tab - dip_dg * zz / (1.0 + k) ** 2) * A + ip * dA_dk) / istar
+            df_dk_own = -((-dip_dg * zz / (1.0 + k) ** 2) * A + ip * dA_dk) / istar
+            df_dk_row = -(dip_dk_tab * A) / istar     # through the weights' radius ratio
             sub = np.zeros((zz.size, setup.nparam))
             for j in range(6):
                 sub[:, j] = df_dz * dz[j][msk]
-            sub[:, kcol] += df_dk
+            sub[:, kcol] += df_dk_own
+            if shared:
+                # d kw / d k_j = 1 / nkp for every passband's radius ratio
+                for j in range(nkp):
+                    sub[:, 6 + j] += df_dk_row / nkp
+            else:
+                sub[:, kcol] += df_dk_row
             for c in range(len(dldw_dc)):
                 dip_dc = (1.0 - al) * dldw_dc[c][i] + al * dldw_dc[c][i + 1]
                 sub[:, lcol + c] = -(dip_dc * A) / istar + ip * A * distar[c] / istar ** 2

@@ -16,6 +16,10 @@ Direct model (Sect. 3.1.2, the interpolation in k left out): ldw =
 dot(w(k), ldp) with the weights computed for the vector's own k on the g
 grid (``weights.calculate_weights``); k may then be anywhere in (0, 1).
 
+Transmission spectroscopy (Sect. 3.4): with shared weights and one k per
+passband, ldw of every passband is computed at the mean of the pv's radius
+ratios; the area and g = c / (1 + k) use the passband's own k.
+
 Points where the planet is behind the star or g >= 1 have f = 1 exactly.
 Exposure supersampling (Sect. 4.1): each point is the mean of f over ss
 sub-exposures.  Reading (placement unstated): midpoint rule,
@@ -72,6 +76,7 @@ class Setup:
     tables: Optional[List[tuple]]
     n_general: int = 0      # coefficients of the general law
     direct: bool = False    # direct model: weights for each exact k, interpolation in g only (Sect. 3.1.2)
+    shared: bool = False    # transmission spectroscopy: one weight array at the mean k of the passbands
 
     @property
     def nldc(self) -> int:
@@ -92,13 +97,15 @@ def _tables(zcut, nzin, nzlimb, ng, nk, k0, k1):
 
 
 def build(grid: dict, ld_model: str, npb: int = 1, chromatic: bool = False,
-          tables: Optional[Sequence[tuple]] = None, n_general: int = 0, direct: bool = False) -> Setup:
+          tables: Optional[Sequence[tuple]] = None, n_general: int = 0, direct: bool = False,
+          shared: bool = False) -> Setup:
     """Model initialisation: radial grid, mu at the bin means and the (k, g) weight table
     (the direct model computes its weights per call for each k instead)."""
     ze, zm, mu, dk, dg, w = _tables(grid["zcut"], grid["nzin"], grid["nzlimb"], grid["ng"],
                                     grid["nk"], grid["k0"], grid["k1"])
     return Setup(ze, zm, mu, w, dk, dg, grid["k0"], grid["k1"], grid["nk"], grid["ng"],
-                 ld_model, npb, chromatic, list(tables) if tables is not None else None, n_general, direct)
+                 ld_model, npb, chromatic, list(tables) if tables is not None else None, n_general, direct,
+                 shared)
 
 
 def unpack(setup: Setup, row: np.ndarray):
@@ -159,6 +166,13 @@ def ld_weights(setup: Setup, k: float, coef, pb: int):
     return ldp, istar, ldw
 
 
+def weights_k(setup: Setup, ks, k: float) -> float:
+    """Radius ratio the passband's weights are computed at: its own k, or with shared weights
+    (Sect. 3.4, transmission spectroscopy) the mean of the pv's per-passband radius ratios;
+    the area and g = z / (1 + k) keep the passband's own k."""
+    return float(np.mean(ks)) if (setup.shared and setup.chromatic) else k
+
+
 def g_cell(setup: Setup, g):
     x = g / setup.dg
     i = np.minimum(np.floor(x).astype(np.int64), setup.ng - 2)
@@ -204,7 +218,7 @@ def evaluate(setup: Setup, times, pb_index, params, supersampling, exptime, retu
             if idx.size == 0:
                 continue
             k = ks[pb] if setup.chromatic else ks[0]
-            _, istar, ldw = ld_weights(setup, k, ldc[pb], pb)
+            _, istar, ldw = ld_weights(setup, weights_k(setup, ks, k), ldc[pb], pb)
             ss = int(supersampling[pb])
             acc = np.zeros(idx.size)
             bad = np.zeros(idx.size, bool)
@@ -225,6 +239,6 @@ def evaluate_workload(wl, setup: Optional[Setup] = None, return_status=False):
     """Oracle flux for a :class:`paper_2009_08500_gb300.workloads.Workload`-shaped object."""
     if setup is None:
         setup = build(wl.grid, wl.ld_model, wl.npb, wl.chromatic, wl.profiles, getattr(wl, "n_general", 0),
-                      getattr(wl, "direct", False))
+                      getattr(wl, "direct", False), getattr(wl, "shared_weights", False))
     return evaluate(setup, wl.times, wl.pb_index, wl.params, wl.supersampling, wl.exptime,
                     return_status=return_status)

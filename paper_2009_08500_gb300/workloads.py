@@ -61,6 +61,7 @@ class Workload:
     grid: dict = field(default_factory=lambda: dict(GRID))
     n_general: int = 0                       # coefficients of the general law
     direct: bool = False                     # direct model: per-k weights, no k grid
+    shared_weights: bool = False             # one weight array at the mean k of the passbands
 
     @property
     def npv(self) -> int:
@@ -84,7 +85,7 @@ class Workload:
         return Workload(self.name, self.times[sl].copy(), self.pb_index[sl].copy(),
                         self.params[:npv].copy(), self.supersampling.copy(), self.exptime.copy(),
                         self.ld_model, self.npb, self.chromatic, self.precision,
-                        self.profiles, dict(self.grid), self.n_general, self.direct)
+                        self.profiles, dict(self.grid), self.n_general, self.direct, self.shared_weights)
 
 
 def nparam_for(ld_model: str, npb: int, chromatic: bool, n_general: int = 0) -> int:
@@ -220,7 +221,8 @@ def make_c4(seed: int = 3, npv: int = 2048, per_pb: int = 7500) -> Workload:
 def make_small(ld_model: str = "quadratic", npv: int = 3, npt: int = 257, npb: int = 1,
                chromatic: bool = False, ss=(1,), exptime=(0.0,), seed: int = 7,
                eccentric: bool = True, precision: str = "mixed", span: float = 6.0,
-               n_general: int = 0, direct: bool = False, k_range=(0.02, 0.25)) -> Workload:
+               n_general: int = 0, direct: bool = False, k_range=(0.02, 0.25),
+               shared_weights: bool = False) -> Workload:
     """Small seeded case for parity tests: a few pvs, a ragged number of times."""
     rng = np.random.Generator(np.random.PCG64(seed))
     k = rng.uniform(k_range[0], k_range[1], npv)
@@ -268,7 +270,8 @@ def make_small(ld_model: str = "quadratic", npv: int = 3, npt: int = 257, npb: i
     ss_arr = np.array([ss[j % len(ss)] for j in range(npb)], np.int32)
     ex_arr = np.array([exptime[j % len(exptime)] for j in range(npb)], np.float64)
     return Workload(f"small_{ld_model}", times, pb_index, params, ss_arr, ex_arr, ld_model, npb,
-                    chromatic, precision, profiles, n_general=n_general, direct=direct)
+                    chromatic, precision, profiles, n_general=n_general, direct=direct,
+                    shared_weights=shared_weights)
 
 
 @dataclass

@@ -104,6 +104,10 @@ typedef struct {
                            1: the direct model of the same section: every call computes the
                            weights on the g grid for each parameter vector's own k, with
                            0 < k < 1 (interpolation in g only; no k table, no k range) */
+    int32_t shared_weights; /* transmission spectroscopy (Sect. 3.4), with chromatic = 1: every
+                           passband of a pv uses one weight array, computed at the mean of the
+                           pv's radius ratios; the area and g = z / (1 + k) keep each passband's
+                           own k.  0 = one weight array per passband.  No effect otherwise. */
 } rr_config;
 
 /* Create a context: validates `cfg`, builds the radial grid of Sect. 3.1.1 on

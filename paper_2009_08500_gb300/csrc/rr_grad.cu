@@ -50,7 +50,9 @@ __device__ __forceinline__ void grad_sample(const PvHead<R>& H, const PvPb<R>& p
     const R rk0 = __ldg(rk + i);
     const R Ik = rk0 + al * (__ldg(rk + i + 1) - rk0);
     const R ddz = dAdz * Ib + A * dIdg * pbc.inv1pk;
-    const R ddk = dAdk * Ib + A * (Ik - dIdg * z * pbc.inv1pk * pbc.inv1pk);
+    // k enters through the area and g (own k) and through the row (the weights' k)
+    const R kown = dAdk * Ib - A * dIdg * z * pbc.inv1pk * pbc.inv1pk;
+    const R krow = A * Ik;
 
     // orbit partials.  With den = r / a = 1 - e cos E and u = w + f the sky
     // coordinates are P_x = den cos u, P_y = den sin u.  The e and w
@@ -95,8 +97,17 @@ __device__ __forceinline__ void grad_sample(const PvHead<R>& H, const PvPb<R>& p
     acc.o[3] += c * (H.b * Py * Py * invz);
     acc.o[4] += c * ((H.a2 * Px * dPxde + H.b2 * Py * dPyde) * invz);
     acc.o[5] += c * ((H.a2 * Px * dPxdw + H.b2 * Py * dPydw) * invz);
-    const R gk = gb * ddk;
-    if (DEP) dep[(kslot - 6) * kBlock] += gk; else acc.k += gk;
+    if (DEP) {
+        if (L.kbar_slot >= 0) {
+            // shared weights: the row's part belongs to the mean k (spread over every k later)
+            dep[(kslot - 6) * kBlock] += gb * kown;
+            dep[(L.kbar_slot - 6) * kBlock] += gb * krow;
+        } else {
+            dep[(kslot - 6) * kBlock] += gb * (kown + krow);
+        }
+    } else {
+        acc.k += gb * (kown + krow);
+    }
     #pragma unroll
     for (int cc = 0; cc < 4; ++cc) {
         if (cc < L.nldc) {
@@ -548,9 +559,9 @@ constexpr int kFinishThreads = 256;
 
 template <typename R>
 __global__ void __launch_bounds__(kFinishThreads) rr_grad_finish_kernel(
-    const R* __restrict__ partials, int nchunks, int nacc, int npv, int pvs_per_block,
-    const char* __restrict__ heads, int head_bytes, const double* __restrict__ params, int kipping, int npb, int nkp,
-    double* __restrict__ grad) {
+    const R* __restrict__ partials, int nchunks, int nacc, int nparam, int npv, int pvs_per_block,
+    const char* __restrict__ heads, int head_bytes, const double* __restrict__ params, int kipping, int shared,
+    int npb, int nkp, double* __restrict__ grad) {
     extern __shared__ double sg[];                 // [pvs_per_block][nacc]
     const int pv0 = blockIdx.x * pvs_per_block;
     const int nloc = min(pvs_per_block, npv - pv0);
@@ -571,19 +582,27 @@ __global__ void __launch_bounds__(kFinishThreads) rr_grad_finish_kernel(
         const bool bad = reinterpret_cast<const PvHead<R>*>(heads + (size_t)(pv0 + lp) * head_bytes)->status != 0;
         s = bad ? __longlong_as_double(0x7ff8000000000000ll) : s;
         sg[t] = s;
-        grad[(size_t)(pv0 + lp) * nacc + j] = s;
+        if (j < nparam) grad[(size_t)(pv0 + lp) * nparam + j] = s;
     }
-    if (!kipping) return;                          // block-uniform
+    if (!kipping && !shared) return;               // block-uniform
     __syncthreads();
+    if (shared) {
+        // shared weights: d kbar / d k_j = 1 / nkp for every per-passband radius ratio
+        for (int t = threadIdx.x; t < nloc * nkp; t += blockDim.x) {
+            const int lp = t / nkp, j = t - lp * nkp;
+            grad[(size_t)(pv0 + lp) * nparam + 6 + j] = sg[lp * nacc + 6 + j] + sg[lp * nacc + nparam] / nkp;
+        }
+    }
+    if (!kipping) return;
     for (int t = threadIdx.x; t < nloc * npb; t += blockDim.x) {
         const int lp = t / npb, pb = t - lp * npb;
         const int o = 6 + nkp + 2 * pb;
-        const double* row = params + (size_t)(pv0 + lp) * nacc;
+        const double* row = params + (size_t)(pv0 + lp) * nparam;
         const double g1 = sg[lp * nacc + o], g2 = sg[lp * nacc + o + 1];
         if (g1 != g1) continue;                    // invalid pv: NaN row stays
         const double sq = sqrt(row[o]), q2 = row[o + 1];
         const double isq = 1.0 / sq;
-        double* out = grad + (size_t)(pv0 + lp) * nacc;
+        double* out = grad + (size_t)(pv0 + lp) * nparam;
         out[o] = g1 * q2 * isq + g2 * (1.0 - 2.0 * q2) * (0.5 * isq);
         out[o + 1] = 2.0 * sq * (g1 - g2);
     }
@@ -608,7 +627,7 @@ static int grad_chunks(const rr_ctx* c, int npt) {
 
 size_t partials_bytes(const rr_ctx* c, int npv, int npt) {
     const size_t rsize = c->cfg.precision == RR_PREC_FP64 ? sizeof(double) : sizeof(float);
-    return (size_t)npv * (size_t)grad_chunks(c, npt) * (size_t)c->nparam * rsize;
+    return (size_t)npv * (size_t)grad_chunks(c, npt) * (size_t)grad_nacc(c) * rsize;
 }
 
 template <typename K>
@@ -617,7 +636,7 @@ static cudaError_t set_smem(K kernel, size_t smem) {
 }
 
 static bool grad_dep(const rr_ctx* c) {
-    return c->nparam > 11 || (c->cfg.npb > 1 && (c->cfg.chromatic || c->nldc > 0));
+    return c->nparam > 11 || (c->cfg.npb > 1 && (c->cfg.chromatic || c->nldc > 0)) || shared_weights(c);
 }
 
 cudaError_t launch_grad(rr_ctx* c, const double* times, const int32_t* pb_index, const void* pts_dt,
@@ -627,7 +646,8 @@ cudaError_t launch_grad(rr_ctx* c, const double* times, const int32_t* pb_index,
     const bool f64 = c->cfg.precision == RR_PREC_FP64;
     RecLayout L = f64 ? make_layout<double>(c->cfg.npb, c->cfg.ng, c->nldc, true)
                       : make_layout<float>(c->cfg.npb, c->cfg.ng, c->nldc, true);
-    const int nacc = c->nparam;
+    const int nacc = grad_nacc(c);
+    if (shared_weights(c)) L.kbar_slot = c->nparam;
     const bool dep = grad_dep(c);
     const size_t rsize = f64 ? 8 : 4;
     // pv tile: records plus the per-warp partial sums within the shared-memory target
@@ -688,7 +708,8 @@ cudaError_t launch_grad_reduce(rr_ctx* c, int npt, const double* params, int npv
     const bool f64 = c->cfg.precision == RR_PREC_FP64;
     RecLayout L = f64 ? make_layout<double>(c->cfg.npb, c->cfg.ng, c->nldc, true)
                       : make_layout<float>(c->cfg.npb, c->cfg.ng, c->nldc, true);
-    const int nacc = c->nparam;
+    const int nacc = grad_nacc(c);
+    const int shared = shared_weights(c) ? 1 : 0;
     const int nchunks = grad_chunks(c, npt);
     const int nkp = c->cfg.chromatic ? c->cfg.npb : 1;
     const int kip = c->cfg.ld_model == RR_LD_QUADRATIC_TRI ? 1 : 0;
@@ -697,12 +718,12 @@ cudaError_t launch_grad_reduce(rr_ctx* c, int npt, const double* params, int npv
     const size_t smem = (size_t)per_block * nacc * sizeof(double);
     if (f64)
         rr_grad_finish_kernel<double><<<blocks, kFinishThreads, smem, s>>>(
-            (const double*)partials, nchunks, nacc, npv, per_block, (const char*)records, L.head_bytes, params, kip,
-            c->cfg.npb, nkp, grad_params);
+            (const double*)partials, nchunks, nacc, c->nparam, npv, per_block, (const char*)records, L.head_bytes,
+            params, kip, shared, c->cfg.npb, nkp, grad_params);
     else
         rr_grad_finish_kernel<float><<<blocks, kFinishThreads, smem, s>>>(
-            (const float*)partials, nchunks, nacc, npv, per_block, (const char*)records, L.head_bytes, params, kip,
-            c->cfg.npb, nkp, grad_params);
+            (const float*)partials, nchunks, nacc, c->nparam, npv, per_block, (const char*)records, L.head_bytes,
+            params, kip, shared, c->cfg.npb, nkp, grad_params);
     c->launches++;
     return cudaGetLastError();
 }

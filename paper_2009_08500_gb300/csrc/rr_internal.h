@@ -90,6 +90,7 @@ struct RecLayout {
     int32_t npb, ng, ng_pad, rows_per_pb;  // rows: 1 (flux) or 3 + nldc (adjoint)
     int32_t nldc, off_pb;                  // byte offset of the PvPb array in a header
     int32_t head_bytes, rows_bytes;        // per-pv strides of the two regions (multiples of 16)
+    int32_t kbar_slot;                     // adjoint accumulator of the shared weights' mean k, else -1
 };
 
 template <typename R>
@@ -103,6 +104,7 @@ inline RecLayout make_layout(int npb, int ng, int nldc, bool grad) {
     L.off_pb = (int32_t)sizeof(PvHead<R>);
     L.head_bytes = (int32_t)(((size_t)L.off_pb + npb * sizeof(PvPb<R>) + 15) & ~(size_t)15);
     L.rows_bytes = (int32_t)(((size_t)npb * L.rows_per_pb * L.ng_pad * sizeof(R) + 15) & ~(size_t)15);
+    L.kbar_slot = -1;
     return L;
 }
 
@@ -127,6 +129,7 @@ struct PbParams {
 struct ModelParams {
     int32_t ld_model, npb, chromatic, nldc, nparam, nk, ng, nbasis;
     int32_t direct, nz;   // direct model (per-call weights for each k); radial bins
+    int32_t shared, pad_;  // one weight array per pv at the mean of its per-passband k
     double k0, k1, dk;
     double inv_dk;   // 1 / dk (host FP64)
     double exp_c;    // int_0^1 mu / (e^mu - 1) dmu (disk integral of the exponential law's second term)
@@ -193,6 +196,13 @@ struct rr_ctx {
 };
 
 namespace rr {
+// shared weights in effect: one weight array per pv for several per-passband k
+inline bool shared_weights(const rr_ctx* c) { return c->cfg.shared_weights && c->cfg.chromatic && c->cfg.npb > 1; }
+// rows of the direct model's per-call projections per pv
+inline int direct_rows_per_pv(const rr_ctx* c) { return shared_weights(c) ? 1 : c->nkp; }
+// adjoint accumulators per pv: the parameters, plus the mean k with shared weights
+inline int grad_nacc(const rr_ctx* c) { return c->nparam + (shared_weights(c) ? 1 : 0); }
+
 // launchers (defined in the .cu files); all return cudaGetLastError() after launch
 cudaError_t launch_ld_basis(rr_ctx* c, cudaStream_t s);
 cudaError_t launch_weights(rr_ctx* c, bool need_w, cudaStream_t s);

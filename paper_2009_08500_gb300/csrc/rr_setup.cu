@@ -414,12 +414,26 @@ __global__ void __launch_bounds__(kDirWarps * 32) rr_direct_table_kernel(
     const int ig = (int)(w - (long long)row * wpr) * 32 + (threadIdx.x & 31);
     if (ig >= ng) return;
     const int nkp = mp.chromatic ? mp.npb : 1;
-    const int pv = row / nkp, slot = row - pv * nkp;
-    const double kd = params[(size_t)pv * mp.nparam + 6 + slot];
+    const int rpp = mp.shared ? 1 : nkp;   // rows per pv
+    const int pv = row / rpp, slot = row - pv * rpp;
+    double kd;
+    if (mp.shared) {
+        // shared weights: the mean of the pv's per-passband radius ratios (invalid if any is)
+        kd = 0.0;
+        bool ok = true;
+        for (int j = 0; j < nkp; ++j) {
+            const double kj = params[(size_t)pv * mp.nparam + 6 + j];
+            ok = ok && kj > 0.0 && kj < 1.0;
+            kd += kj;
+        }
+        kd = ok ? kd / nkp : -1.0;
+    } else {
+        kd = params[(size_t)pv * mp.nparam + 6 + slot];
+    }
     // bases of the row: every named basis; tabulated, the passband's own
-    // profile when k is per passband, else every passband's
+    // profile when the row is one passband's, else every passband's
     int b_lo = 0, b_hi = mp.nbasis;
-    if (mp.ld_model == RR_LD_TABULATED && mp.chromatic) { b_lo = slot; b_hi = slot + 1; }
+    if (mp.ld_model == RR_LD_TABULATED && mp.chromatic && !mp.shared) { b_lo = slot; b_hi = slot + 1; }
     A* Thi = reinterpret_cast<A*>(D.hi);
     A* Tdk = reinterpret_cast<A*>(D.dk);
     const size_t bstride = (size_t)D.nrows * ng;
@@ -619,16 +633,23 @@ __global__ void __launch_bounds__(256, 4) rr_pv_setup_kernel(ModelParams mp, PbP
         }
         if (!(Is > 0.0)) st |= RR_PV_LD_INVALID;
         const double k = row[6 + (mp.chromatic ? pb : 0)];
+        // the weights' radius ratio: the passband's own, or the mean over the pv's passbands
+        double kw = k;
+        if (mp.shared) {
+            kw = 0.0;
+            for (int j = 0; j < nkp; ++j) kw += row[6 + j];
+            kw /= nkp;
+        }
         int ik;
         double ak;
         if (mp.direct) {
             // the row of this (pv, k slot) in the per-call projections
             if (!(k > 0.0 && k < 1.0)) st |= RR_PV_K_RANGE;
-            ik = (pv0 + lp) * nkp + (mp.chromatic ? pb : 0);
+            ik = mp.shared ? pv0 + lp : (pv0 + lp) * nkp + (mp.chromatic ? pb : 0);
             ak = 0.0;
         } else {
             if (!(k >= mp.k0 && k <= mp.k1)) st |= RR_PV_K_RANGE;
-            const double x = (k - mp.k0) / mp.dk;
+            const double x = (kw - mp.k0) / mp.dk;
             ik = (int)floor(x);
             ik = ik < 0 ? 0 : (ik > mp.nk - 2 ? mp.nk - 2 : ik);
             ak = x - ik;
@@ -955,6 +976,8 @@ ModelParams model_params(const rr_ctx* c) {
     mp.inv_dk = 1.0 / c->dk;
     mp.direct = c->cfg.direct;
     mp.dg = 1.0 / (c->cfg.ng - 1);
+    mp.shared = shared_weights(c) ? 1 : 0;
+    mp.pad_ = 0;
     mp.nz = c->nz;
     // int_0^1 mu / (e^mu - 1) dmu = pi^2/6 - Li2(1/e) + ln(1 - 1/e) (expand 1/(e^mu - 1) = sum_k e^(-k mu));
     // Li2(1/e) = sum_k e^(-k) / k^2, 40 terms below 1e-18
@@ -993,7 +1016,7 @@ cudaError_t launch_weights(rr_ctx* c, bool need_w, cudaStream_t s) {
 }
 
 size_t direct_bytes(const rr_ctx* c, int npv, bool grad) {
-    const size_t n = (size_t)c->nbasis * npv * c->nkp * c->cfg.ng;
+    const size_t n = (size_t)c->nbasis * npv * direct_rows_per_pv(c) * c->cfg.ng;
     const size_t rb = c->cfg.precision == RR_PREC_FP64 ? sizeof(double) : sizeof(float);
     size_t b = align256(n * rb);
     if (c->cfg.precision == RR_PREC_MIXED) b += align256(n * sizeof(float));
@@ -1003,7 +1026,7 @@ size_t direct_bytes(const rr_ctx* c, int npv, bool grad) {
 
 DirectTables direct_view(const rr_ctx* c, void* base, int npv, bool grad) {
     DirectTables D;
-    const size_t n = (size_t)c->nbasis * npv * c->nkp * c->cfg.ng;
+    const size_t n = (size_t)c->nbasis * npv * direct_rows_per_pv(c) * c->cfg.ng;
     const size_t rb = c->cfg.precision == RR_PREC_FP64 ? sizeof(double) : sizeof(float);
     char* p = (char*)base;
     D.hi = p;
@@ -1014,7 +1037,7 @@ DirectTables direct_view(const rr_ctx* c, void* base, int npv, bool grad) {
         p += align256(n * sizeof(float));
     }
     D.dk = grad ? p : nullptr;
-    D.nrows = npv * c->nkp;
+    D.nrows = npv * direct_rows_per_pv(c);
     return D;
 }
 
@@ -1030,7 +1053,7 @@ cudaError_t launch_direct_tables(rr_ctx* c, const double* params, int npv, bool 
                                  cudaStream_t s) {
     if (npv == 0) return cudaSuccess;
     ModelParams mp = model_params(c);
-    const long long warps = (long long)npv * c->nkp * ((c->cfg.ng + 31) / 32);
+    const long long warps = (long long)npv * direct_rows_per_pv(c) * ((c->cfg.ng + 31) / 32);
     const unsigned grid = (unsigned)((warps + kDirWarps - 1) / kDirWarps);
     if (c->cfg.precision == RR_PREC_FP64)
         rr_direct_table_kernel<double><<<grid, kDirWarps * 32, 0, s>>>(mp, params, c->d_ze, c->d_basis, c->d_basis,

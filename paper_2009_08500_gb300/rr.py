@@ -43,7 +43,7 @@ class RRConfig(ctypes.Structure):
                 ("ng", ctypes.c_int32), ("nk", ctypes.c_int32), ("k0", ctypes.c_double),
                 ("k1", ctypes.c_double), ("npb", ctypes.c_int32), ("ld_model", ctypes.c_int32),
                 ("chromatic", ctypes.c_int32), ("precision", ctypes.c_int32), ("device", ctypes.c_int32),
-                ("ncoef", ctypes.c_int32), ("direct", ctypes.c_int32)]
+                ("ncoef", ctypes.c_int32), ("direct", ctypes.c_int32), ("shared_weights", ctypes.c_int32)]
 
 
 class RRError(RuntimeError):
@@ -139,11 +139,13 @@ class Model:
     n_general  terms of the general law (1..4)
     direct     the direct model: weights for each k computed per call, interpolation in g
                only, any 0 < k < 1 (the grid's nk, k0, k1 are then unused)
+    shared_weights  with chromatic k: one weight array per pv at the mean of its radius ratios
+               (transmission spectroscopy); area and g keep each passband's k
     """
 
     def __init__(self, ld_model: str = "quadratic", npb: int = 1, chromatic: bool = False,
                  precision: str = "mixed", grid: Optional[dict] = None, device: int = 0, n_general: int = 0,
-                 direct: bool = False):
+                 direct: bool = False, shared_weights: bool = False):
         from .workloads import GRID
         g = dict(GRID if grid is None else grid)
         self.lib = load_library()
@@ -152,10 +154,12 @@ class Model:
         self.device = torch.device("cuda", device)
         self.ld_model, self.npb, self.chromatic, self.precision = ld_model, npb, chromatic, precision
         self.direct = bool(direct)
+        self.shared_weights = bool(shared_weights)
         self.grid = g
         cfg = RRConfig(g["zcut"], g["nzin"], g["nzlimb"], g["ng"], g["nk"], g["k0"], g["k1"], npb,
                        LD_MODELS[ld_model], int(chromatic), PRECISIONS[precision], device,
-                       int(n_general) if ld_model == "general" else 0, int(bool(direct)))
+                       int(n_general) if ld_model == "general" else 0, int(bool(direct)),
+                       int(bool(shared_weights)))
         h = ctypes.c_void_p()
         st = self.lib.rr_create(ctypes.byref(cfg), ctypes.byref(h))
         if st != 0:
@@ -429,7 +433,7 @@ class _RRFlux(torch.autograd.Function):
 def model_for(wl, device: int = 0) -> Model:
     """Model context for a :class:`workloads.Workload`, with profiles set and tables built."""
     m = Model(wl.ld_model, wl.npb, wl.chromatic, wl.precision, wl.grid, device, getattr(wl, "n_general", 0),
-              getattr(wl, "direct", False))
+              getattr(wl, "direct", False), getattr(wl, "shared_weights", False))
     if wl.ld_model == "tabulated":
         for pb, (mu, it) in enumerate(wl.profiles):
             m.set_ld_profile(pb, mu, it)

@@ -33,6 +33,8 @@ CONFIG_TEXT = {
     "c2": "Single eccentric light curve, FP32 bulk / FP64 phase: nonlinear LD, 19,440 times, ss=10",
     "c3": "Population batch: 4,096 pvs x 20,000 times, Kipping q1,q2, forward + adjoint w.r.t. 9 parameters",
     "c4": "Heterogeneous: 8 passbands, tabulated LD, 2,048 pvs x 60,000 mixed-cadence times, ss {1,10,30}",
+    "ts": "Transmission spectroscopy: 2,048 pvs x 8 channels x 2,500 times, per-channel k within 3%, quadratic LD, "
+          "direct model with one shared weight array per pv, forward + adjoint",
     "c5": "Serving: Poisson requests from 64 fits, npv logU[1,4096] x npt logU[500,2e5] (capped at 2^25 points), "
           "mixed LD, forward:gradient 3:1",
 }
@@ -48,7 +50,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["c1", "c2", "c3", "c4", "c5"], default="c3")
+    ap.add_argument("--workload", choices=["c1", "c2", "c3", "c4", "c5", "ts"], default="c3")
     ap.add_argument("--serve-seconds", type=float, default=3.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -59,11 +61,11 @@ def parse():
 
 def make_workload(name):
     from paper_2009_08500_gb300 import workloads as W
-    return {"c1": W.make_c1, "c2": W.make_c2, "c3": W.make_c3, "c4": W.make_c4}[name]()
+    return {"c1": W.make_c1, "c2": W.make_c2, "c3": W.make_c3, "c4": W.make_c4, "ts": W.make_ts}[name]()
 
 
 def with_grad(name):
-    return name == "c3"
+    return name in ("c3", "ts")
 
 
 def dist_env():
@@ -143,7 +145,8 @@ def _oracle_init(name):
     from oracle import model as om
     wl = make_workload(name)
     _W["wl"] = wl
-    _W["setup"] = om.build(wl.grid, wl.ld_model, wl.npb, wl.chromatic, wl.profiles)
+    _W["setup"] = om.build(wl.grid, wl.ld_model, wl.npb, wl.chromatic, wl.profiles, wl.n_general, wl.direct,
+                           wl.shared_weights)
     _W["grad"] = with_grad(name)
 
 
@@ -316,9 +319,11 @@ def run_ours(a):
     fp64 = None
     if not a.no_fp64_form and esize == 4:
         fp64 = run_fp64_form(a, wl, grad, local, dev, flush)
-    direct = None
-    if not a.no_direct and esize == 4:
-        direct = run_direct_model(a, wl, grad, local, dev, flush)
+    direct = per_pb = None
+    if not a.no_direct and esize == 4 and not wl.direct:
+        direct = run_variant(a, wl, grad, local, dev, flush, direct=True)
+    if wl.shared_weights:
+        per_pb = run_variant(a, wl, grad, local, dev, flush, shared_weights=False)
 
     e2e = None
     if not a.no_e2e:
@@ -345,6 +350,7 @@ def run_ours(a):
         "roofline": roof, "roofline_flux": roof_flux, "kernels": kernels, "cpu_baseline": cpu_base,
         "fp64_form": None if fp64 is None else dict(fp64, speedup_of_mixed=value / world / fp64["value"]),
         "direct_model": direct,
+        "per_passband_weights": per_pb,
         "e2e": e2e, "clocks": clk, "gpu_launches": launches,
     }
     if rank == 0:
@@ -412,16 +418,18 @@ def run_fp64_form(a, wl, grad, local, dev, flush):
             "steps": n, "dtype": "f64", "note": "same workload and step through the FP64 kernels, one GPU"}
 
 
-def run_direct_model(a, wl, grad, local, dev, flush):
-    """The same workload and step through the direct model (weights for every pv's own k computed
-    inside each step, interpolation in g only), mixed form, timed the same way."""
+def run_variant(a, wl, grad, local, dev, flush, **change):
+    """The same workload and step with some model options changed (`direct=True`: the direct
+    model, weights for every pv's own k computed inside each step; `shared_weights=False`: one
+    weight array per passband), mixed form, timed the same way."""
     import copy
 
     import torch
 
     from paper_2009_08500_gb300 import rr
     wd = copy.copy(wl)
-    wd.direct = True
+    for key, val in change.items():
+        setattr(wd, key, val)
     md = rr.model_for(wd, device=local)
     t, pb, p = rr.to_device(wd, local)
     flux = torch.empty((wl.npv, wl.npt), dtype=md.dtype, device=dev)
@@ -467,9 +475,11 @@ def run_direct_model(a, wl, grad, local, dev, flush):
     if grad:
         del ws_g, gbar, gout
     torch.cuda.empty_cache()
+    what = ", ".join(f"{key}={val}" for key, val in change.items())
     return {"value": wl.npv * wl.samples_per_pv() / (ms * 1e-3), "unit": "points/s", "ms_per_step": ms,
-            "steps": n, "dtype": "f32+f64", "direct_table_ms_per_launch": round(dms / max(dn, 1), 5),
-            "note": "same workload and step through the direct model (per-call weights for each k), one GPU"}
+            "steps": n, "dtype": "f32+f64",
+            "direct_table_ms_per_launch": round(dms / max(dn, 1), 5) if dn else None,
+            "note": f"same workload and step with {what}, one GPU"}
 
 
 def run_e2e(a, model, wl, grad, dev):

@@ -218,6 +218,26 @@ def make_c4(seed: int = 3, npv: int = 2048, per_pb: int = 7500) -> Workload:
                     "tabulated", npb, False, "mixed", profiles)
 
 
+def make_ts(seed: int = 5, npv: int = 2048, npb: int = 8, per_pb: int = 2500) -> Workload:
+    """Transmission spectroscopy: the population of the population workload observed
+    simultaneously in npb spectroscopic channels (every time stamp once per channel), a radius
+    ratio per channel within 3% of the pv's mean, quadratic LD per channel; evaluated with the
+    direct model and one shared weight array per pv (Sect. 3.4)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    t0, P, a, b, e, w, k = _population(rng, npv)
+    ks = k[:, None] * (1.0 + 0.03 * rng.uniform(-1.0, 1.0, (npv, npb)))
+    u1 = rng.uniform(0.1, 0.5, (npv, npb))
+    u2 = rng.uniform(0.0, 0.3, (npv, npb))
+    base = np.sort(rng.uniform(0.0, 5 * 5.5, per_pb))
+    times = np.repeat(base, npb)
+    pb_index = np.tile(np.arange(npb, dtype=np.int32), per_pb)
+    ldc = np.stack([u1, u2], axis=2).reshape(npv, 2 * npb)
+    params = np.concatenate([np.stack([t0, P, a, b, e, w], axis=1), ks, ldc], axis=1)
+    return Workload(f"ts_transmission_{npv}x{npb}x{per_pb}", times, pb_index, params,
+                    np.ones(npb, np.int32), np.zeros(npb), "quadratic", npb, True, "mixed",
+                    direct=True, shared_weights=True)
+
+
 def make_small(ld_model: str = "quadratic", npv: int = 3, npt: int = 257, npb: int = 1,
                chromatic: bool = False, ss=(1,), exptime=(0.0,), seed: int = 7,
                eccentric: bool = True, precision: str = "mixed", span: float = 6.0,

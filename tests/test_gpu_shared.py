@@ -116,3 +116,22 @@ def test_shared_adjoint_matches_oracle(rr, case, precision):
     floor = 1e-3 * scale.max(axis=1, keepdims=True)
     err = np.abs(g - ref) / np.maximum(scale, np.maximum(floor, 1e-300))
     assert err.max() < GRAD_RTOL[precision], (err.max(), np.unravel_index(err.argmax(), err.shape))
+
+
+def test_transmission_workload_full_launch_sampled_rows(rr):
+    """2,048 pvs x 8 channels x 2,500 times through the direct model with shared weights, as bench.py runs it."""
+    import torch
+    wl = W.make_ts()
+    m = rr.model_for(wl)
+    assert m.direct and m.shared_weights
+    t, pb, p = rr.to_device(wl)
+    st = torch.full((wl.npv,), -1, dtype=torch.int32, device=t.device)
+    f = m.evaluate(t, p, pb, wl.supersampling, wl.exptime, pv_status=st)
+    torch.cuda.synchronize()
+    f = f.double().cpu().numpy()
+    assert not st.cpu().numpy().any()
+    rows = np.random.default_rng(6).choice(wl.npv, 8, replace=False)
+    sub = wl.subset(wl.npv)
+    sub.params = wl.params[rows]
+    ref = om.evaluate_workload(sub)
+    assert np.abs(f[rows] - ref).max() <= 1e-6

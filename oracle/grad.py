@@ -22,7 +22,8 @@ import numpy as np
 from . import ld as _ld
 from . import orbit as _orbit
 from . import weights as _weights
-from .model import (Setup, _table, g_cell, k_cell, pv_status, sample_times, unpack, evaluate, weights_k)
+from .model import (Setup, _table, g_cell, k_cell, pv_status, sample_times, unpack, evaluate, weights_k,
+                    small_planet_mu)
 
 
 def _area_and_partials(k, z):
@@ -149,7 +150,16 @@ def jacobian(setup: Setup, times, pb_index, row, supersampling, exptime):
         ldp = _ld.profile(setup.ld_model, setup.mu, ldc[pb], table)
         istar = _ld.istar(setup.ld_model, ldc[pb], table)
         dldp, distar = _ld_partials(setup.ld_model, setup.mu, ldc[pb], table)
-        if setup.direct:
+        if kw < setup.k_small:
+            # small-planet approximation: ldw_i = I(mu(c_i)), c_i = g_i (1 + k), mu = sqrt(1 - c^2)
+            mu_c, free, cc = small_planet_mu(setup, kw)
+            ldw = _ld.profile(setup.ld_model, mu_c, ldc[pb], table)
+            g_nodes = np.arange(setup.ng) * setup.dg
+            dmu_dk = np.where(free, -cc * g_nodes / mu_c, 0.0)
+            dldw_dk = _ld.profile_dmu(setup.ld_model, mu_c, ldc[pb], table) * dmu_dk
+            dldp_c, _ = _ld_partials(setup.ld_model, mu_c, ldc[pb], table)
+            dldw_dc = [dldp_c[c] for c in range(dldp_c.shape[0])]
+        elif setup.direct:
             # weights for this exact k and their k-derivative at fixed g (Sect. 3.1.2)
             _, wk, wdk = _weights.calculate_weights(kw, setup.ze, setup.ng, with_dk=True)
             ldw = wk @ ldp

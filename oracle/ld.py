@@ -83,6 +83,38 @@ def profile(model: str, mu, coef=(), table=None):
     raise ValueError(f"unknown LD model {model!r}")
 
 
+def profile_dmu(model: str, mu, coef=(), table=None):
+    """dI/dmu of ``profile`` (mu > 0); for a table, the slope of the segment holding mu
+    (0 outside the nodes, the right-hand segment on a node)."""
+    mu = np.asarray(mu, np.float64)
+    if model == "uniform":
+        return np.zeros_like(mu)
+    if model in ("quadratic", "quadratic_tri"):
+        u1, u2 = kipping_to_quadratic(*coef) if model == "quadratic_tri" else coef
+        return u1 + 2.0 * u2 * (1.0 - mu)
+    if model == "nonlinear":
+        c1, c2, c3, c4 = coef
+        return 0.5 * c1 * mu ** -0.5 + c2 + 1.5 * c3 * mu ** 0.5 + 2.0 * c4 * mu
+    if model == "tabulated":
+        tmu, tI = (np.asarray(x, np.float64) for x in table)
+        i = np.clip(np.searchsorted(tmu, mu, side="right") - 1, 0, tmu.size - 2)
+        slope = (tI[i + 1] - tI[i]) / (tmu[i + 1] - tmu[i])
+        return np.where((mu >= tmu[0]) & (mu < tmu[-1]), slope, 0.0)
+    if model == "linear":
+        (u,) = coef
+        return np.full_like(mu, u)
+    if model == "general":
+        return sum((n + 1) * c * (1.0 - mu) ** n for n, c in enumerate(coef))
+    if model == "logarithmic":
+        u1, u2 = coef
+        return u1 - u2 * (np.log(mu) + 1.0)
+    if model == "exponential":
+        u1, u2 = coef
+        em = np.exp(mu)
+        return u1 - u2 * em / (1.0 - em) ** 2
+    raise ValueError(f"unknown LD model {model!r}")
+
+
 def istar(model: str, coef=(), table=None) -> float:
     """I_star = 2 pi int_0^1 mu I(mu) dmu."""
     if model == "uniform":

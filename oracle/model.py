@@ -16,6 +16,12 @@ Direct model (Sect. 3.1.2, the interpolation in k left out): ldw =
 dot(w(k), ldp) with the weights computed for the vector's own k on the g
 grid (``weights.calculate_weights``); k may then be anywhere in (0, 1).
 
+Small-planet approximation (Sect. 3.4): below the radius ratio k_small the
+weighted average ldw[i] of every g node is replaced by the profile at the
+planet's centre, I(mu_i) with mu_i = sqrt(1 - min(c_i, 1)^2), c_i = g_i (1 + k),
+clamped below to the outermost bin mean (the grid's limb resolution; keeps
+laws that diverge at mu = 0 finite); such pvs need no k table.
+
 Transmission spectroscopy (Sect. 3.4): with shared weights and one k per
 passband, ldw of every passband is computed at the mean of the pv's radius
 ratios; the area and g = c / (1 + k) use the passband's own k.
@@ -77,6 +83,7 @@ class Setup:
     n_general: int = 0      # coefficients of the general law
     direct: bool = False    # direct model: weights for each exact k, interpolation in g only (Sect. 3.1.2)
     shared: bool = False    # transmission spectroscopy: one weight array at the mean k of the passbands
+    k_small: float = 0.0    # small-planet approximation below this radius ratio (0 = off)
 
     @property
     def nldc(self) -> int:
@@ -98,14 +105,14 @@ def _tables(zcut, nzin, nzlimb, ng, nk, k0, k1):
 
 def build(grid: dict, ld_model: str, npb: int = 1, chromatic: bool = False,
           tables: Optional[Sequence[tuple]] = None, n_general: int = 0, direct: bool = False,
-          shared: bool = False) -> Setup:
+          shared: bool = False, k_small: float = 0.0) -> Setup:
     """Model initialisation: radial grid, mu at the bin means and the (k, g) weight table
     (the direct model computes its weights per call for each k instead)."""
     ze, zm, mu, dk, dg, w = _tables(grid["zcut"], grid["nzin"], grid["nzlimb"], grid["ng"],
                                     grid["nk"], grid["k0"], grid["k1"])
     return Setup(ze, zm, mu, w, dk, dg, grid["k0"], grid["k1"], grid["nk"], grid["ng"],
                  ld_model, npb, chromatic, list(tables) if tables is not None else None, n_general, direct,
-                 shared)
+                 shared, k_small)
 
 
 def unpack(setup: Setup, row: np.ndarray):
@@ -121,11 +128,16 @@ def pv_status(setup: Setup, row: np.ndarray) -> int:
     st = 0
     if not np.all(np.isfinite(row)):
         return ST_NONFINITE
-    if setup.direct:
-        if np.any(ks <= 0.0) or np.any(ks >= 1.0):
-            st |= ST_K_RANGE
-    elif np.any(ks < setup.k0) or np.any(ks > setup.k1):
+    # every radius ratio in (0, 1); the interpolated model also needs the weights' radius ratio
+    # (own, or the mean with shared weights) inside the k table, unless the small-planet
+    # approximation replaces the weights
+    if np.any(ks <= 0.0) or np.any(ks >= 1.0):
         st |= ST_K_RANGE
+    elif not setup.direct:
+        for k in ks:
+            kw = weights_k(setup, ks, float(k))
+            if kw >= setup.k_small and not (setup.k0 <= kw <= setup.k1):
+                st |= ST_K_RANGE
     if not (0.0 <= e < 1.0):
         st |= ST_E_RANGE
     if not (P > 0.0):
@@ -153,11 +165,26 @@ def k_cell(setup: Setup, k: float):
     return ik, x - ik
 
 
+def small_planet_mu(setup: Setup, k: float):
+    """mu under the planet's centre at every g node, c_i = g_i (1 + k) (mu = 0 beyond the limb),
+    clamped below to the outermost bin mean; and whether each node is unclamped."""
+    c = np.arange(setup.ng) * setup.dg * (1.0 + k)
+    mu = np.sqrt(1.0 - np.minimum(c, 1.0) ** 2)
+    free = (c < 1.0) & (mu > setup.mu[-1])
+    return np.where(free, mu, setup.mu[-1]), free, c
+
+
 def ld_weights(setup: Setup, k: float, coef, pb: int):
-    """Per-passband profile weights: ldp, I_star and the k-interpolated ldw[ng]."""
+    """Per-passband profile weights: ldp, I_star and the k-interpolated ldw[ng].
+
+    Small-planet approximation (Sect. 3.4): for k < k_small the weighted average at every g
+    node is replaced by the profile at the planet's centre, I(mu(c_i)) (``small_planet_mu``)."""
     table = _table(setup, pb)
     ldp = _ld.profile(setup.ld_model, setup.mu, coef, table)
     istar = _ld.istar(setup.ld_model, coef, table)
+    if k < setup.k_small:
+        mu_c, _, _ = small_planet_mu(setup, k)
+        return ldp, istar, _ld.profile(setup.ld_model, mu_c, coef, table)
     if setup.direct:
         _, w = _weights.calculate_weights(k, setup.ze, setup.ng)
         return ldp, istar, w @ ldp
@@ -239,6 +266,7 @@ def evaluate_workload(wl, setup: Optional[Setup] = None, return_status=False):
     """Oracle flux for a :class:`paper_2009_08500_gb300.workloads.Workload`-shaped object."""
     if setup is None:
         setup = build(wl.grid, wl.ld_model, wl.npb, wl.chromatic, wl.profiles, getattr(wl, "n_general", 0),
-                      getattr(wl, "direct", False), getattr(wl, "shared_weights", False))
+                      getattr(wl, "direct", False), getattr(wl, "shared_weights", False),
+                      getattr(wl, "k_small", 0.0))
     return evaluate(setup, wl.times, wl.pb_index, wl.params, wl.supersampling, wl.exptime,
                     return_status=return_status)

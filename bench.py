@@ -324,6 +324,11 @@ def run_ours(a):
         direct = run_variant(a, wl, grad, local, dev, flush, direct=True)
     if wl.shared_weights:
         per_pb = run_variant(a, wl, grad, local, dev, flush, shared_weights=False)
+    small = None
+    if not a.no_direct and esize == 4 and a.workload == "c3":
+        # small-planet approximation below k = 0.05 (about a fifth of the population's pvs)
+        small = run_variant(a, wl, grad, local, dev, flush, k_small=0.05)
+        small["pvs_below_threshold"] = int((wl.params[:, 6] < 0.05).sum())
 
     e2e = None
     if not a.no_e2e:
@@ -351,6 +356,7 @@ def run_ours(a):
         "fp64_form": None if fp64 is None else dict(fp64, speedup_of_mixed=value / world / fp64["value"]),
         "direct_model": direct,
         "per_passband_weights": per_pb,
+        "small_planet": small,
         "e2e": e2e, "clocks": clk, "gpu_launches": launches,
     }
     if rank == 0:

@@ -74,7 +74,8 @@ typedef enum {
 } rr_precision;
 
 /* Per-pv status bits written to pv_status (0 = valid). */
-#define RR_PV_K_RANGE    1    /* a radius ratio outside [k0, k1] (direct model: outside (0, 1)) */
+#define RR_PV_K_RANGE    1    /* a radius ratio outside (0, 1), or the weights' radius ratio outside
+                                 [k0, k1] (interpolated model, not below k_small) */
 #define RR_PV_E_RANGE    2    /* eccentricity outside [0, 1) */
 #define RR_PV_B_RANGE    4    /* impact parameter outside [0, a] */
 #define RR_PV_P_RANGE    8    /* period <= 0 */
@@ -108,6 +109,11 @@ typedef struct {
                            passband of a pv uses one weight array, computed at the mean of the
                            pv's radius ratios; the area and g = z / (1 + k) keep each passband's
                            own k.  0 = one weight array per passband.  No effect otherwise. */
+    double  k_small;    /* small-planet approximation (Sect. 3.4): a passband whose (weights')
+                           radius ratio is below k_small uses, at every g node, the profile at
+                           the planet's centre, I(mu), mu = sqrt(1 - min(g (1 + k), 1)^2) clamped
+                           below to the outermost bin mean, instead of the weighted average; it
+                           needs no k table (0 < k < k_small is valid).  0 = off; >= 0, finite. */
 } rr_config;
 
 /* Create a context: validates `cfg`, builds the radial grid of Sect. 3.1.1 on

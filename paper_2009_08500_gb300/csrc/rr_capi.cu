@@ -302,6 +302,7 @@ rr_status rr_create(const rr_config* cfg, rr_ctx** out) {
     if (k.direct != 0 && k.direct != 1) return fail(nullptr, RR_EINVAL, "direct must be 0 or 1");
     if (k.shared_weights != 0 && k.shared_weights != 1)
         return fail(nullptr, RR_EINVAL, "shared_weights must be 0 or 1");
+    if (!(k.k_small >= 0.0 && k.k_small < 1.0)) return fail(nullptr, RR_EINVAL, "k_small must be in [0, 1)");
     if (!k.direct) {
         if (k.nk < 2 || k.nk > 4096) return fail(nullptr, RR_EINVAL, "nk must be in [2, 4096]");
         if (!(k.k0 > 0.0 && k.k0 < k.k1 && k.k1 < 1.0)) return fail(nullptr, RR_EINVAL, "need 0 < k0 < k1 < 1");

@@ -134,6 +134,8 @@ struct ModelParams {
     double inv_dk;   // 1 / dk (host FP64)
     double exp_c;    // int_0^1 mu / (e^mu - 1) dmu (disk integral of the exponential law's second term)
     double dg;       // 1 / (ng - 1)
+    double k_small;  // small-planet approximation threshold (0 = off)
+    double mu_min;   // mu of the outermost bin mean (the small-planet approximation's limb clamp)
 };
 
 // Per-call projections of the direct model (the workspace region after the

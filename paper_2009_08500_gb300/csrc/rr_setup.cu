@@ -438,7 +438,8 @@ __global__ void __launch_bounds__(kDirWarps * 32) rr_direct_table_kernel(
     A* Tdk = reinterpret_cast<A*>(D.dk);
     const size_t bstride = (size_t)D.nrows * ng;
     const size_t o = (size_t)row * ng + ig;
-    const bool valid = kd > 0.0 && kd < 1.0;
+    // rows of small-planet passbands are not read (their rows come from the profile directly)
+    const bool valid = kd > 0.0 && kd < 1.0 && !(kd < mp.k_small);
     const A k = (A)kd;
     const double gd = ig * mp.dg;
     const double cd = gd * (1.0 + (double)k);
@@ -575,6 +576,154 @@ __device__ R mean_anomaly_of_true_r(R f, R e) {
     return E - e * sE;
 }
 
+// Value and mu-derivative of profile basis b at an arbitrary mu (the bases of
+// rr_ld_basis_kernel; tabulated: passband b's table interpolated at mu, the
+// slope of the segment holding mu, 0 outside the nodes).  FP64; mu > 0.
+__device__ double ld_basis_mu(const ModelParams& mp, int b, double m, const double* __restrict__ tab,
+                              const int* __restrict__ tab_off, double& d) {
+    if (mp.ld_model == RR_LD_TABULATED) {
+        const int o0 = tab_off[b], n = tab_off[b + 1] - o0;
+        const double* tmu = tab + 2 * o0;
+        const double* tI = tmu + n;
+        if (m < tmu[0]) { d = 0.0; return tI[0]; }
+        if (m >= tmu[n - 1]) { d = 0.0; return tI[n - 1]; }
+        int lo = 0, hi = n - 1;   // tmu[lo] <= m < tmu[hi]
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (tmu[mid] <= m) lo = mid; else hi = mid;
+        }
+        d = (tI[lo + 1] - tI[lo]) / (tmu[lo + 1] - tmu[lo]);
+        return tI[lo] + d * (m - tmu[lo]);
+    }
+    if (b == 0) { d = 0.0; return 1.0; }
+    const double q = 1.0 - m;
+    switch (mp.ld_model) {
+        case RR_LD_NONLINEAR: {
+            // -(1 - mu^(b/2)) and (b/2) mu^(b/2 - 1) through sqrt(mu)
+            const double sq = sqrt(m);
+            const double p = b == 1 ? sq : (b == 2 ? m : (b == 3 ? m * sq : m * m));
+            d = b == 1 ? 0.5 / sq : (b == 2 ? 1.0 : (b == 3 ? 1.5 * sq : 2.0 * m));
+            return -(1.0 - p);
+        }
+        case RR_LD_GENERAL: {
+            double p = 1.0;
+            for (int j = 1; j < b; ++j) p *= q;   // q^(b-1)
+            d = b * p;
+            return -p * q;
+        }
+        case RR_LD_LOGARITHMIC:
+            if (b == 1) { d = 1.0; return -q; }
+            d = -(log(m) + 1.0);
+            return -m * log(m);
+        case RR_LD_EXPONENTIAL:
+            if (b == 1) { d = 1.0; return -q; }
+            {
+                const double e = exp(m), r = 1.0 / (1.0 - e);
+                d = -e * r * r;
+                return -r;
+            }
+        default:   // linear, quadratic (and q1, q2)
+            if (b == 1) { d = 1.0; return -q; }
+            d = 2.0 * q;
+            return -q * q;
+    }
+}
+
+// Small-planet approximation (Sect. 3.4): the rows of the (pv, passband)
+// pairs whose weights' radius ratio k_w is below k_small, written after the
+// set-up kernel (which leaves them out), in FP64.  At g node i the row holds
+// the profile at the planet's centre, mu = sqrt(1 - min(c, 1)^2) with
+// c = g_i (1 + k_w), clamped below to mu_min, divided by I_star; with the
+// adjoint also the in-cell difference, d/dk (through mu; 0 where clamped) and
+// the coefficient rows (basis_c - row I_star_c) / I_star.  One thread per
+// (pv, passband, g node).
+struct SmallPlanetRow {
+    double kw;
+    double ud[5];   // weights of the bases: 1, then the coefficients
+    int b0, nc;
+};
+
+__device__ double small_planet_node(const ModelParams& mp, const SmallPlanetRow& sp, const double* tab,
+                                    const int* tab_off, int i, double* vb, double& dk) {
+    const double gi = i * mp.dg, cc = gi * (1.0 + sp.kw);
+    const double cm = fmin(cc, 1.0);
+    const double m0 = sqrt(fmax(1.0 - cm * cm, 0.0));
+    const bool free = cc < 1.0 && m0 > mp.mu_min;
+    const double m = free ? m0 : mp.mu_min;
+    const double dmdk = free ? -cc * gi / m : 0.0;
+    double v = 0.0, dv = 0.0;
+    for (int c = 0; c <= sp.nc; ++c) {
+        double dd;
+        const double bv = ld_basis_mu(mp, sp.b0 + c, m, tab, tab_off, dd);
+        vb[c] = bv;
+        v += sp.ud[c] * bv;
+        dv += sp.ud[c] * dd;
+    }
+    dk = dv * dmdk;
+    return v;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) rr_small_planet_kernel(ModelParams mp, const double* __restrict__ params,
+                                                              int npv, const double* __restrict__ istar,
+                                                              const double* __restrict__ tab,
+                                                              const int* __restrict__ tab_off, RecLayout L, int grad,
+                                                              char* __restrict__ records) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long long)npv * mp.npb * mp.ng) return;
+    const int ig = (int)(t % mp.ng);
+    const long long r = t / mp.ng;
+    const int pb = (int)(r % mp.npb), pv = (int)(r / mp.npb);
+    const double* row = params + (size_t)pv * mp.nparam;
+    const int nkp = mp.chromatic ? mp.npb : 1;
+    double kw = row[6 + (mp.chromatic ? pb : 0)];
+    if (mp.shared) {
+        kw = 0.0;
+        for (int j = 0; j < nkp; ++j) kw += row[6 + j];
+        kw /= nkp;
+    }
+    if (!(kw < mp.k_small)) return;            // the set-up kernel wrote this passband's rows
+    // coefficients and I_star as in the set-up kernel
+    const bool named = mp.ld_model != RR_LD_TABULATED;
+    const double* c = row + 6 + nkp + pb * mp.nldc;
+    SmallPlanetRow sp;
+    sp.kw = kw;
+    sp.b0 = named ? 0 : pb;
+    sp.nc = named ? mp.nldc : 0;
+    sp.ud[0] = 1.0;
+    for (int j = 0; j < 4; ++j) sp.ud[1 + j] = 0.0;
+    if (mp.ld_model == RR_LD_QUADRATIC_TRI) {
+        const double sq = sqrt(fmax(c[0], 0.0));
+        sp.ud[1] = 2.0 * sq * c[1];
+        sp.ud[2] = sq * (1.0 - 2.0 * c[1]);
+    } else {
+        for (int j = 0; j < sp.nc; ++j) sp.ud[1 + j] = c[j];
+    }
+    double Is = named ? istar[0] : istar[pb];
+    if (named)
+        for (int j = 0; j < mp.nldc; ++j) Is += sp.ud[1 + j] * istar[1 + j];
+    // the set-up kernel's 1 / I_star, rounded to R as there
+    const double invIs = (double)(R)(1.0 / Is);
+    R* r0 = reinterpret_cast<R*>(records + rows_offset(L, npv) + (size_t)pv * L.rows_bytes) +
+            (size_t)pb * L.rows_per_pb * L.ng_pad;
+    double vb[5] = {0.0, 0.0, 0.0, 0.0, 0.0}, dk;
+    const double v = small_planet_node(mp, sp, tab, tab_off, ig, vb, dk) * invIs;
+    r0[ig] = (R)v;
+    if (ig == mp.ng - 1)
+        for (int q = mp.ng; q < L.ng_pad; ++q)
+            for (int rr = 0; rr < L.rows_per_pb; ++rr) r0[(size_t)rr * L.ng_pad + q] = (R)0;
+    if (!grad) return;
+    double dv = 0.0;
+    if (ig < mp.ng - 1) {
+        double vb1[5], dk1;
+        dv = small_planet_node(mp, sp, tab, tab_off, ig + 1, vb1, dk1) * invIs - v;
+    }
+    r0[L.ng_pad + ig] = (R)dv;
+    r0[2 * L.ng_pad + ig] = (R)(dk * invIs);
+    for (int j = 0; j < sp.nc; ++j)
+        r0[(size_t)(3 + j) * L.ng_pad + ig] = (R)((vb[1 + j] - v * (double)(R)istar[1 + j]) * invIs);
+}
+
 // Pvs per CTA of the set-up kernel: few, so that the launch has several
 // CTAs per SM and the per-pv scalar chains of many CTAs overlap; the rows
 // and windows are spread over the whole CTA.
@@ -592,7 +741,7 @@ __global__ void __launch_bounds__(256, 4) rr_pv_setup_kernel(ModelParams mp, PbP
     __shared__ R u_s[NP][RR_MAX_PB][4];
     __shared__ R invIs_s[NP][RR_MAX_PB];
     __shared__ R ak_s[NP][RR_MAX_PB];
-    __shared__ int ik_s[NP][RR_MAX_PB];
+    __shared__ int ik_s[NP][RR_MAX_PB];       // k cell or direct row; -1: small-planet approximation
     __shared__ int st_s[NP];       // validity after (1): LD coefficients, I_star, k
     __shared__ int st2_s[NP];      // full validity after (2a)
     __shared__ int rows_next;
@@ -640,15 +789,21 @@ __global__ void __launch_bounds__(256, 4) rr_pv_setup_kernel(ModelParams mp, PbP
             for (int j = 0; j < nkp; ++j) kw += row[6 + j];
             kw /= nkp;
         }
+        // every radius ratio in (0, 1); the interpolated model also needs the weights' radius
+        // ratio inside the k table unless the small-planet approximation replaces the weights
+        const bool small = kw < mp.k_small;
+        if (!(k > 0.0 && k < 1.0)) st |= RR_PV_K_RANGE;
+        else if (!mp.direct && !small && !(kw >= mp.k0 && kw <= mp.k1)) st |= RR_PV_K_RANGE;
         int ik;
         double ak;
-        if (mp.direct) {
+        if (small) {
+            ik = -1;
+            ak = 0.0;
+        } else if (mp.direct) {
             // the row of this (pv, k slot) in the per-call projections
-            if (!(k > 0.0 && k < 1.0)) st |= RR_PV_K_RANGE;
             ik = mp.shared ? pv0 + lp : (pv0 + lp) * nkp + (mp.chromatic ? pb : 0);
             ak = 0.0;
         } else {
-            if (!(k >= mp.k0 && k <= mp.k1)) st |= RR_PV_K_RANGE;
             const double x = (kw - mp.k0) / mp.dk;
             ik = (int)floor(x);
             ik = ik < 0 ? 0 : (ik > mp.nk - 2 ? mp.nk - 2 : ik);
@@ -862,6 +1017,7 @@ __global__ void __launch_bounds__(256, 4) rr_pv_setup_kernel(ModelParams mp, PbP
         #pragma unroll
         for (int c = 0; c < 4; ++c) Ic[c] = (grad && c < nc) ? (R)istar[1 + c] : R(0);
         const int b0 = named ? 0 : pb;
+        if (ik < 0) continue;   // small-planet approximation: rr_small_planet_kernel writes these rows
         if (mp.direct) {
             // direct model: the pv's own projections (no k interpolation); the
             // in-cell slopes come from the differences of the FP32 pairs
@@ -978,6 +1134,8 @@ ModelParams model_params(const rr_ctx* c) {
     mp.dg = 1.0 / (c->cfg.ng - 1);
     mp.shared = shared_weights(c) ? 1 : 0;
     mp.pad_ = 0;
+    mp.k_small = c->cfg.k_small;
+    mp.mu_min = c->mu.empty() ? 0.0 : c->mu.back();
     mp.nz = c->nz;
     // int_0^1 mu / (e^mu - 1) dmu = pi^2/6 - Li2(1/e) + ln(1 - 1/e) (expand 1/(e^mu - 1) = sum_k e^(-k mu));
     // Li2(1/e) = sum_k e^(-k) / k^2, 40 terms below 1e-18
@@ -1082,6 +1240,20 @@ cudaError_t launch_pv_setup(rr_ctx* c, const double* params, int npv, const PbPa
         rr_pv_setup_kernel<float><<<blocks, 256, 0, s>>>(mp, pbp, params, npv, c->d_T32, c->d_DT32, c->d_istar, L,
                                                          grad ? 1 : 0, (char*)records, pv_status, D);
     }
+    c->launches++;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || !(c->cfg.k_small > 0.0) || npv == 0) return e;
+    // rows of the small-planet passbands
+    const long long n = (long long)npv * c->cfg.npb * c->cfg.ng;
+    const unsigned nb = (unsigned)((n + 255) / 256);
+    if (c->cfg.precision == RR_PREC_FP64)
+        rr_small_planet_kernel<double><<<nb, 256, 0, s>>>(mp, params, npv, c->d_istar, c->d_tab, c->d_tab_off,
+                                                          make_layout<double>(c->cfg.npb, c->cfg.ng, c->nldc, grad),
+                                                          grad ? 1 : 0, (char*)records);
+    else
+        rr_small_planet_kernel<float><<<nb, 256, 0, s>>>(mp, params, npv, c->d_istar, c->d_tab, c->d_tab_off,
+                                                         make_layout<float>(c->cfg.npb, c->cfg.ng, c->nldc, grad),
+                                                         grad ? 1 : 0, (char*)records);
     c->launches++;
     return cudaGetLastError();
 }

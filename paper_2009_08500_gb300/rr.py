@@ -43,7 +43,8 @@ class RRConfig(ctypes.Structure):
                 ("ng", ctypes.c_int32), ("nk", ctypes.c_int32), ("k0", ctypes.c_double),
                 ("k1", ctypes.c_double), ("npb", ctypes.c_int32), ("ld_model", ctypes.c_int32),
                 ("chromatic", ctypes.c_int32), ("precision", ctypes.c_int32), ("device", ctypes.c_int32),
-                ("ncoef", ctypes.c_int32), ("direct", ctypes.c_int32), ("shared_weights", ctypes.c_int32)]
+                ("ncoef", ctypes.c_int32), ("direct", ctypes.c_int32), ("shared_weights", ctypes.c_int32),
+                ("k_small", ctypes.c_double)]
 
 
 class RRError(RuntimeError):
@@ -141,11 +142,13 @@ class Model:
                only, any 0 < k < 1 (the grid's nk, k0, k1 are then unused)
     shared_weights  with chromatic k: one weight array per pv at the mean of its radius ratios
                (transmission spectroscopy); area and g keep each passband's k
+    k_small    small-planet approximation below this radius ratio (0 = off): the profile at the
+               planet's centre instead of the weighted average
     """
 
     def __init__(self, ld_model: str = "quadratic", npb: int = 1, chromatic: bool = False,
                  precision: str = "mixed", grid: Optional[dict] = None, device: int = 0, n_general: int = 0,
-                 direct: bool = False, shared_weights: bool = False):
+                 direct: bool = False, shared_weights: bool = False, k_small: float = 0.0):
         from .workloads import GRID
         g = dict(GRID if grid is None else grid)
         self.lib = load_library()
@@ -155,11 +158,12 @@ class Model:
         self.ld_model, self.npb, self.chromatic, self.precision = ld_model, npb, chromatic, precision
         self.direct = bool(direct)
         self.shared_weights = bool(shared_weights)
+        self.k_small = float(k_small)
         self.grid = g
         cfg = RRConfig(g["zcut"], g["nzin"], g["nzlimb"], g["ng"], g["nk"], g["k0"], g["k1"], npb,
                        LD_MODELS[ld_model], int(chromatic), PRECISIONS[precision], device,
                        int(n_general) if ld_model == "general" else 0, int(bool(direct)),
-                       int(bool(shared_weights)))
+                       int(bool(shared_weights)), float(k_small))
         h = ctypes.c_void_p()
         st = self.lib.rr_create(ctypes.byref(cfg), ctypes.byref(h))
         if st != 0:
@@ -433,7 +437,7 @@ class _RRFlux(torch.autograd.Function):
 def model_for(wl, device: int = 0) -> Model:
     """Model context for a :class:`workloads.Workload`, with profiles set and tables built."""
     m = Model(wl.ld_model, wl.npb, wl.chromatic, wl.precision, wl.grid, device, getattr(wl, "n_general", 0),
-              getattr(wl, "direct", False), getattr(wl, "shared_weights", False))
+              getattr(wl, "direct", False), getattr(wl, "shared_weights", False), getattr(wl, "k_small", 0.0))
     if wl.ld_model == "tabulated":
         for pb, (mu, it) in enumerate(wl.profiles):
             m.set_ld_profile(pb, mu, it)

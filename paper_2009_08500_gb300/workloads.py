@@ -62,6 +62,7 @@ class Workload:
     n_general: int = 0                       # coefficients of the general law
     direct: bool = False                     # direct model: per-k weights, no k grid
     shared_weights: bool = False             # one weight array at the mean k of the passbands
+    k_small: float = 0.0                     # small-planet approximation below this k (0 = off)
 
     @property
     def npv(self) -> int:
@@ -85,7 +86,8 @@ class Workload:
         return Workload(self.name, self.times[sl].copy(), self.pb_index[sl].copy(),
                         self.params[:npv].copy(), self.supersampling.copy(), self.exptime.copy(),
                         self.ld_model, self.npb, self.chromatic, self.precision,
-                        self.profiles, dict(self.grid), self.n_general, self.direct, self.shared_weights)
+                        self.profiles, dict(self.grid), self.n_general, self.direct, self.shared_weights,
+                        self.k_small)
 
 
 def nparam_for(ld_model: str, npb: int, chromatic: bool, n_general: int = 0) -> int:

@@ -48,7 +48,8 @@ def test_null_handles_are_rejected_without_a_device(lib):
 @pytest.mark.parametrize("field,value,msg", [("zcut", 1.5, b"zcut"), ("nzin", 0, b"nzin"), ("ng", 1, b"ng"),
                                              ("k1", 0.001, b"k0"), ("npb", 40, b"npb"), ("ld_model", 9, b"ld_model"),
                                              ("precision", 5, b"precision"), ("chromatic", 2, b"chromatic"),
-                                             ("direct", 2, b"direct"), ("shared_weights", 3, b"shared_weights")])
+                                             ("direct", 2, b"direct"), ("shared_weights", 3, b"shared_weights"),
+                                             ("k_small", -0.1, b"k_small"), ("k_small", float("nan"), b"k_small")])
 def test_create_rejects_bad_config_before_touching_the_device(lib, field, value, msg):
     cfg = rr.RRConfig(0.7, 200, 300, 200, 60, 0.005, 0.3, 1, 1, 0, 1, 0)
     setattr(cfg, field, value)

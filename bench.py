@@ -35,6 +35,9 @@ CONFIG_TEXT = {
     "c4": "Heterogeneous: 8 passbands, tabulated LD, 2,048 pvs x 60,000 mixed-cadence times, ss {1,10,30}",
     "ts": "Transmission spectroscopy: 2,048 pvs x 8 channels x 2,500 times, per-channel k within 3%, quadratic LD, "
           "direct model with one shared weight array per pv, forward + adjoint",
+    "accuracy": "Model error against the exact radial integral (Fig. 2 setting): quadratic LD (0.4, 0.25), "
+                "k in {0.01, 0.05, 0.1, 0.5}, 1,000 planet positions over g in [0, 1), three grid resolutions, "
+                "FP64 and mixed forms; automatic grid choice for 10, 1 and 0.1 ppm",
     "c5": "Serving: Poisson requests from 64 fits, npv logU[1,4096] x npt logU[500,2e5] (capped at 2^25 points), "
           "mixed LD, forward:gradient 3:1",
 }
@@ -50,7 +53,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["c1", "c2", "c3", "c4", "c5", "ts"], default="c3")
+    ap.add_argument("--workload", choices=["c1", "c2", "c3", "c4", "c5", "ts", "accuracy"], default="c3")
     ap.add_argument("--serve-seconds", type=float, default=3.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -649,12 +652,70 @@ def run_serving(a):
         print(json.dumps(line))
 
 
+def run_accuracy(a):
+    """Error of the model against the library's exact flux (no oracle): the Fig. 2 sweep over radius
+    ratios and grid resolutions, and the automatic grid choice for a few error targets."""
+    import numpy as np
+    import torch
+
+    from paper_2009_08500_gb300 import rr
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    coef = (0.4, 0.25)
+    ks = [0.01, 0.05, 0.1, 0.5]
+    setups = {"low": dict(zcut=0.7, nzin=30, nzlimb=45, ng=100), "medium": dict(zcut=0.7, nzin=60, nzlimb=90, ng=150),
+              "default": dict(zcut=0.7, nzin=200, nzlimb=300, ng=200)}
+    npos, a_orb = 1000, 1000.0
+    g = np.concatenate([[0.0], (np.arange(1, npos) * 0.6180339887498949) % 1.0 * 0.999])
+    rows, t_all, z_all, k_all = [], [], [], []
+    for k in ks:
+        z = g * (1 + k)
+        t_all.append(np.arcsin(z / a_orb) / (2 * np.pi))
+        z_all.append(a_orb * np.abs(np.sin(2 * np.pi * t_all[-1])))   # the z the model computes (FP64)
+        k_all.append(np.full(npos, k))
+        rows.append([0.0, 1.0, a_orb, 0.0, 0.0, 0.0, k, *coef])
+    dev = torch.device("cuda", local)
+    params = torch.tensor(rows, dtype=torch.float64, device=dev)
+    out = {}
+    worst = 0.0
+    for name, grid in setups.items():
+        full = dict(grid, nk=60, k0=0.005, k1=0.3)
+        res = {}
+        for prec in ("fp64", "mixed"):
+            m = rr.Model("quadratic", precision=prec, grid=full, device=local, direct=True).build()
+            ex = m.exact_flux(torch.tensor(np.concatenate(z_all), device=dev),
+                              torch.tensor(np.concatenate(k_all), device=dev), coef).cpu().numpy().reshape(len(ks), npos)
+            per_k = {}
+            for i, k in enumerate(ks):
+                t = torch.tensor(t_all[i], dtype=torch.float64, device=dev)
+                f = m.evaluate(t, params[i:i + 1]).double().cpu().numpy()[0]
+                err = np.abs(f - ex[i]) * 1e6
+                per_k[str(k)] = {"max_ppm": round(float(err.max()), 4), "mean_ppm": round(float(err.mean()), 5)}
+                if prec == "fp64":
+                    worst = max(worst, float(err.max()))
+            res[prec] = per_k
+        out[name] = dict(grid=grid, **res)
+    chosen = {}
+    for target in (1e-5, 1e-6, 1e-7):
+        t0 = time.perf_counter()
+        gsel = rr.choose_grid("quadratic", ks, coef, target=target, device=local)
+        chosen[f"{target * 1e6:g} ppm"] = dict(gsel, seconds=round(time.perf_counter() - t0, 3))
+    print(json.dumps({"metric": "largest model error vs the exact radial integral (default grid, FP64 form)",
+                      "value": out["default"]["fp64"] and max(v["max_ppm"] for v in out["default"]["fp64"].values()),
+                      "unit": "ppm", "higher_is_better": False, "n_gpus": 1, "data": "synthetic",
+                      "config": {"workload": f"accuracy: {CONFIG_TEXT['accuracy']}"},
+                      "worst_ppm_all_setups": worst, "sweep": out, "choose_grid": chosen}))
+
+
 def main():
     a = parse()
     if a.impl == "reference":
         run_reference(a)
     elif a.workload == "c5":
         run_serving(a)
+    elif a.workload == "accuracy":
+        run_accuracy(a)
     else:
         run_ours(a)
 

@@ -48,6 +48,7 @@ typedef enum {
     RR_ENOMEM = 2,    /* device or host allocation failed */
     RR_ECUDA = 3,     /* a CUDA runtime call or kernel launch failed */
     RR_ESTATE = 4,    /* call out of order (e.g. evaluate before rr_build_weights) */
+    RR_EDOMAIN = 5,   /* a requested accuracy cannot be met (rr_choose_grid) */
     RR_ETIMEOUT = 6   /* a bounded device-side wait gave up (see rr_last_error) */
 } rr_status;
 
@@ -353,6 +354,45 @@ int32_t rr_server_pending(rr_server* server);
 #define RR_TABLE_ISTAR 5
 #define RR_TABLE_PROJ 6
 int64_t rr_read_table(rr_ctx* ctx, int32_t which, double* out, int64_t capacity);
+
+/* Exact flux (Sect. 2, Eq. 1 in radial form; no radial grid, no weights): for
+ * planet-star distances z[i] and radius ratios k[i] (device, double[n]),
+ *   out[i] = 1 - (1 / I_star) int_0^1 I(mu(r)) 2 r theta_i(r) dr  (device, double[n]),
+ * theta the half-angle of the radius-r circle inside the planet (pi where the
+ * planet covers the whole circle).  The law is the context's, with the
+ * coefficients ldc (host, nldc values of one passband; Kipping q1, q2 for
+ * RR_LD_QUADRATIC_TRI; ignored for a table) and passband pb's profile and
+ * I_star.  FP64 Gauss-Legendre quadrature, 96 nodes per piece (the wholly
+ * covered circles and the lens; 512 for a table), each piece mapped by
+ * r = a + (b - a)(1 - cos phi) / 2 so that the square-root behaviour at the
+ * contacts and at the limb is absorbed.  Accuracy: FP64 round-off for the
+ * uniform, linear, quadratic and general laws; ~1e-10 for the nonlinear,
+ * logarithmic and exponential laws (their mu^(1/2), mu ln mu, 1/(1 - e^mu)
+ * terms stay non-smooth at the limb); ~1e-8 for a table (a kink at every
+ * table node).  The reference of rr_choose_grid.
+ * Enqueued on `stream`; needs rr_build_weights.  Errors: RR_EINVAL,
+ * RR_ESTATE, RR_ECUDA. */
+rr_status rr_exact_flux(rr_ctx* ctx, const double* z, const double* k, int32_t n, const double* ldc,
+                        int32_t pb, double* out, void* stream);
+
+/* Automatic grid resolution (Sect. 3.1.1 and 3.3: the resolutions and z_cut
+ * chosen for a limb-darkening law and an error threshold).  Searches the
+ * radial grid and the g grid for the direct model (FP64) whose flux stays
+ * within `target` (absolute) of rr_exact_flux for every radius ratio k[0..nk)
+ * (0 < k < 1, nk <= 64) at 400 planet positions each (g = 0 and a golden-ratio
+ * sequence over [0, 0.999)), with the law cfg->ld_model (cfg->ncoef), the
+ * coefficients ldc (host) or, for RR_LD_TABULATED, the profile (mu_tab,
+ * I_tab, ntab).  Ladders: nzin, nzlimb in {4, 6, 8, 12, ..., 2048}, ng in
+ * {10, 15, 20, 30, ..., 3840}, z_cut in {0.5, 0.6, 0.7, 0.8, 0.9}.  Greedy:
+ * from (0.7, 8, 8, 20) take the step with the largest error reduction per
+ * unit of added cost (nz x ng) until the target is met, then coarsen each
+ * dimension while it stays met.  Writes zcut, nzin, nzlimb, ng of *cfg (the
+ * other fields are read: ld_model, ncoef, device) and the achieved largest
+ * error to *max_err.  Synchronous; creates and destroys its own contexts.
+ * Errors: RR_EINVAL, RR_ECUDA, RR_EDOMAIN (target not reached on the ladders;
+ * *cfg and *max_err hold the best grid found). */
+rr_status rr_choose_grid(rr_config* cfg, const double* k, int32_t nk, const double* ldc, const double* mu_tab,
+                         const double* I_tab, int32_t ntab, double target, double* max_err);
 
 /* Synchronise `stream` and report whether any kernel of this context gave up
  * a bounded device-side wait since the last check (RR_ETIMEOUT; the affected

@@ -12,7 +12,8 @@ from concurrent.futures import ThreadPoolExecutor
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "librr.so")
-SOURCES = ["rr_capi.cu", "rr_setup.cu", "rr_flux.cu", "rr_grad.cu", "rr_host.cu", "rr_server.cu", "rr_noalloc.cu"]
+SOURCES = ["rr_capi.cu", "rr_setup.cu", "rr_flux.cu", "rr_grad.cu", "rr_host.cu", "rr_server.cu", "rr_noalloc.cu",
+           "rr_exact.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # host code: no FMA contraction, so that the FP64 grid is identical on x86 and Arm hosts
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",

@@ -83,6 +83,7 @@ void free_all(rr_ctx* c) {
     cudaFree(c->d_basisf);
     cudaFree(c->d_pre64);
     cudaFree(c->d_pref);
+    cudaFree(c->d_gl);
 }
 
 // Per-kernel timing: when enabled, every launch is bracketed by two CUDA

@@ -175,6 +175,7 @@ struct rr_ctx {
     float* d_basisf = nullptr;   // nbasis * nz
     double* d_pre64 = nullptr;   // nbasis * (nz + 1)
     float* d_pref = nullptr;     // 2 * nbasis * (nz + 1): FP32 hi, then lo
+    double* d_gl = nullptr;      // Gauss-Legendre nodes and weights of rr_exact_flux (on first use)
     int num_sms = 0;
     bool weights_built = false;
     bool tables_built = false;

@@ -576,59 +576,6 @@ __device__ R mean_anomaly_of_true_r(R f, R e) {
     return E - e * sE;
 }
 
-// Value and mu-derivative of profile basis b at an arbitrary mu (the bases of
-// rr_ld_basis_kernel; tabulated: passband b's table interpolated at mu, the
-// slope of the segment holding mu, 0 outside the nodes).  FP64; mu > 0.
-__device__ double ld_basis_mu(const ModelParams& mp, int b, double m, const double* __restrict__ tab,
-                              const int* __restrict__ tab_off, double& d) {
-    if (mp.ld_model == RR_LD_TABULATED) {
-        const int o0 = tab_off[b], n = tab_off[b + 1] - o0;
-        const double* tmu = tab + 2 * o0;
-        const double* tI = tmu + n;
-        if (m < tmu[0]) { d = 0.0; return tI[0]; }
-        if (m >= tmu[n - 1]) { d = 0.0; return tI[n - 1]; }
-        int lo = 0, hi = n - 1;   // tmu[lo] <= m < tmu[hi]
-        while (hi - lo > 1) {
-            const int mid = (lo + hi) >> 1;
-            if (tmu[mid] <= m) lo = mid; else hi = mid;
-        }
-        d = (tI[lo + 1] - tI[lo]) / (tmu[lo + 1] - tmu[lo]);
-        return tI[lo] + d * (m - tmu[lo]);
-    }
-    if (b == 0) { d = 0.0; return 1.0; }
-    const double q = 1.0 - m;
-    switch (mp.ld_model) {
-        case RR_LD_NONLINEAR: {
-            // -(1 - mu^(b/2)) and (b/2) mu^(b/2 - 1) through sqrt(mu)
-            const double sq = sqrt(m);
-            const double p = b == 1 ? sq : (b == 2 ? m : (b == 3 ? m * sq : m * m));
-            d = b == 1 ? 0.5 / sq : (b == 2 ? 1.0 : (b == 3 ? 1.5 * sq : 2.0 * m));
-            return -(1.0 - p);
-        }
-        case RR_LD_GENERAL: {
-            double p = 1.0;
-            for (int j = 1; j < b; ++j) p *= q;   // q^(b-1)
-            d = b * p;
-            return -p * q;
-        }
-        case RR_LD_LOGARITHMIC:
-            if (b == 1) { d = 1.0; return -q; }
-            d = -(log(m) + 1.0);
-            return -m * log(m);
-        case RR_LD_EXPONENTIAL:
-            if (b == 1) { d = 1.0; return -q; }
-            {
-                const double e = exp(m), r = 1.0 / (1.0 - e);
-                d = -e * r * r;
-                return -r;
-            }
-        default:   // linear, quadratic (and q1, q2)
-            if (b == 1) { d = 1.0; return -q; }
-            d = 2.0 * q;
-            return -q * q;
-    }
-}
-
 // Small-planet approximation (Sect. 3.4): the rows of the (pv, passband)
 // pairs whose weights' radius ratio k_w is below k_small, written after the
 // set-up kernel (which leaves them out), in FP64.  At g node i the row holds

@@ -33,7 +33,7 @@ EXPORTS = ["rr_create", "rr_destroy", "rr_set_ld_profile", "rr_build_weights", "
            "rr_sync_status", "rr_last_error", "rr_launch_count", "rr_profile", "rr_profile_read",
            "rr_evaluate_noalloc", "rr_prepare", "rr_evaluate_prepared", "rr_evaluate_grad_prepared",
            "rr_evaluate_host", "rr_request_bytes", "rr_enqueue_host", "rr_server_create", "rr_server_destroy",
-           "rr_server_submit", "rr_server_poll", "rr_server_pending"]
+           "rr_server_submit", "rr_server_poll", "rr_server_pending", "rr_exact_flux", "rr_choose_grid"]
 KERNELS = {"ld_basis": 0, "weights": 1, "pv_setup": 2, "flux": 3, "grad": 4, "grad_reduce": 5, "points": 6,
            "direct": 7}
 
@@ -103,7 +103,9 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     L.rr_launch_count.restype = i64
     L.rr_profile.argtypes = [vp, i32]
     L.rr_profile_read.argtypes = [vp, i32, dp, ctypes.POINTER(i64), i32]
-    for name in ("rr_create", "rr_destroy", "rr_set_ld_profile", "rr_build_weights", "rr_evaluate",
+    L.rr_exact_flux.argtypes = [vp, vp, vp, i32, dp, i32, vp, vp]
+    L.rr_choose_grid.argtypes = [ctypes.POINTER(RRConfig), dp, i32, dp, dp, dp, i32, ctypes.c_double, dp]
+    for name in ("rr_exact_flux", "rr_choose_grid", "rr_create", "rr_destroy", "rr_set_ld_profile", "rr_build_weights", "rr_evaluate",
                  "rr_evaluate_grad", "rr_sync_status", "rr_profile", "rr_profile_read", "rr_evaluate_noalloc",
                  "rr_prepare", "rr_evaluate_prepared", "rr_evaluate_grad_prepared", "rr_evaluate_host",
                  "rr_enqueue_host"):
@@ -222,6 +224,18 @@ class Model:
         r = self.lib.rr_read_table(self._h, TABLES[which], out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), n)
         if r < 0:
             raise RRError(4, self.lib.rr_last_error(self._h).decode())
+        return out
+
+    def exact_flux(self, z, k, ldc=(), pb: int = 0, stream=None) -> torch.Tensor:
+        """Exact flux (radial integral, no grid) at distances z and radius ratios k (float64 tensors
+        or arrays; a float32 input keeps its float32 rounding)."""
+        z = torch.as_tensor(z, dtype=torch.float64, device=self.device).contiguous()
+        k = torch.as_tensor(k, dtype=torch.float64, device=self.device).contiguous()
+        out = torch.empty_like(z)
+        c = np.ascontiguousarray(np.asarray(ldc, np.float64).reshape(-1))
+        cp = c.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if c.size else None
+        self._check(self.lib.rr_exact_flux(self._h, _ptr(z), _ptr(k), int(z.numel()), cp, int(pb), _ptr(out),
+                                           _stream_handle(stream)))
         return out
 
     def profile(self, enable: bool = True):
@@ -442,6 +456,32 @@ def model_for(wl, device: int = 0) -> Model:
         for pb, (mu, it) in enumerate(wl.profiles):
             m.set_ld_profile(pb, mu, it)
     return m.build()
+
+
+def choose_grid(ld_model: str, k, ldc=(), target: float = 1e-6, profile=None, n_general: int = 0,
+                device: int = 0) -> dict:
+    """Cheapest grid (zcut, nzin, nzlimb, ng) whose flux stays within `target` of the exact
+    integral for the radius ratios `k` and LD coefficients `ldc` (or the tabulated `profile`)."""
+    lib = load_library()
+    cfg = RRConfig(0.7, 8, 8, 20, 2, 0.005, 0.3, 1, LD_MODELS[ld_model], 0, PRECISIONS["fp64"], device,
+                   int(n_general) if ld_model == "general" else 0, 1, 0, 0.0)
+    ks = np.ascontiguousarray(np.atleast_1d(np.asarray(k, np.float64)))
+    c = np.ascontiguousarray(np.asarray(ldc, np.float64).reshape(-1))
+    dp = ctypes.POINTER(ctypes.c_double)
+    if profile is not None:
+        mu = np.ascontiguousarray(profile[0], np.float64)
+        it = np.ascontiguousarray(profile[1], np.float64)
+        mup, itp, nt = mu.ctypes.data_as(dp), it.ctypes.data_as(dp), mu.size
+    else:
+        mup = itp = None
+        nt = 0
+    err = ctypes.c_double(np.nan)
+    st = lib.rr_choose_grid(ctypes.byref(cfg), ks.ctypes.data_as(dp), ks.size, c.ctypes.data_as(dp) if c.size else None,
+                            mup, itp, nt, float(target), ctypes.byref(err))
+    if st not in (0, 5):
+        raise RRError(st, "rr_choose_grid failed")
+    return {"zcut": cfg.zcut, "nzin": cfg.nzin, "nzlimb": cfg.nzlimb, "ng": cfg.ng, "max_error": err.value,
+            "met": st == 0}
 
 
 def to_device(wl, device: int = 0):

@@ -123,6 +123,18 @@ def _ld_partials(model, mu, coef, table):
     if model == "exponential":
         return (np.stack([-(1.0 - mu), -1.0 / (1.0 - np.exp(mu))]),
                 np.array([-np.pi / 3.0, 2.0 * np.pi * _ld.EXP_C]))
+    if model in ("power2", "power2_pm"):
+        # I = 1 - c (1 - mu^a), I_star = pi (1 - c a / (a + 2)): not affine in a
+        c, a = _ld.power2_coef(model, coef)
+        ma = mu ** a
+        dp = np.stack([-(1.0 - ma), c * ma * np.log(mu)])
+        di = np.array([-np.pi * a / (a + 2.0), -2.0 * np.pi * c / (a + 2.0) ** 2])
+        if model == "power2_pm":
+            # c = 1 - h1 + h2, a = log2(c / h2): chain rule to (h1, h2)
+            h2 = coef[1]
+            J = np.array([[-1.0, 1.0], [-1.0 / (c * np.log(2.0)), (1.0 / c - 1.0 / h2) / np.log(2.0)]])
+            dp, di = J.T @ dp, J.T @ di
+        return dp, di
     return np.zeros((0, mu.size)), np.zeros(0)
 
 

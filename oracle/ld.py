@@ -18,19 +18,23 @@ Laws (coefficients per passband):
   general        I = 1 - sum_{n=1..N} c_n (1 - mu)^n            (N = 1..4)
   logarithmic    I = 1 - u1 (1 - mu) - u2 mu ln mu
   exponential    I = 1 - u1 (1 - mu) - u2 / (1 - exp(mu))
-(the laws named in Sect. 3.2.1, written in their usual forms; each is affine
-in its coefficients).  Closed-form disk integrals:
+  power2         I = 1 - c (1 - mu^alpha)                      (c, alpha > 0)
+  power2_pm      power2 with h1 = I(1/2) = 1 - c (1 - 2^-alpha), h2 = I(1/2) - I(0) = c 2^-alpha,
+                 i.e. c = 1 - h1 + h2, alpha = log2(c / h2)
+(the laws named in Sect. 3.2.1, written in their usual forms; all but the
+power-2 laws are affine in their coefficients).  Closed-form disk integrals:
   linear       pi (1 - u/3)
   general      pi (1 - sum_n 2 c_n / ((n+1)(n+2)))     [int_0^1 mu (1-mu)^n dmu = 1/((n+1)(n+2))]
   logarithmic  pi (1 - u1/3 + 2 u2/9)                   [int_0^1 mu^2 ln mu dmu = -1/9]
   exponential  pi (1 - u1/3) + 2 pi u2 C,  C = int_0^1 mu / (e^mu - 1) dmu
                = pi^2/6 - Li2(1/e) + ln(1 - 1/e)       [expand 1/(e^mu - 1) = sum_k e^(-k mu)]
+  power2       pi (1 - c alpha / (alpha + 2))           [int_0^1 mu^(1+alpha) dmu = 1/(alpha+2)]
 """
 import numpy as np
 from scipy.special import spence
 
 NCOEF = {"uniform": 0, "quadratic": 2, "quadratic_tri": 2, "nonlinear": 4, "tabulated": 0,
-         "linear": 1, "logarithmic": 2, "exponential": 2}
+         "linear": 1, "logarithmic": 2, "exponential": 2, "power2": 2, "power2_pm": 2}
 
 #: int_0^1 mu / (e^mu - 1) dmu; scipy's spence(z) is Li2(1 - z)
 EXP_C = np.pi ** 2 / 6.0 - spence(1.0 - np.exp(-1.0)) + np.log(1.0 - np.exp(-1.0))
@@ -48,6 +52,16 @@ def ncoef(model: str, n_general: int = 0) -> int:
 def kipping_to_quadratic(q1, q2):
     sq = np.sqrt(q1)
     return 2.0 * sq * q2, sq * (1.0 - 2.0 * q2)
+
+
+def pm_to_power2(h1, h2):
+    """(h1, h2) of the power-2 law to (c, alpha)."""
+    c = 1.0 - h1 + h2
+    return c, np.log2(c / h2)
+
+
+def power2_coef(model: str, coef):
+    return pm_to_power2(*coef) if model == "power2_pm" else tuple(coef)
 
 
 def profile(model: str, mu, coef=(), table=None):
@@ -80,6 +94,9 @@ def profile(model: str, mu, coef=(), table=None):
     if model == "exponential":
         u1, u2 = coef
         return 1.0 - u1 * (1.0 - mu) - u2 / (1.0 - np.exp(mu))
+    if model in ("power2", "power2_pm"):
+        c, alpha = power2_coef(model, coef)
+        return 1.0 - c * (1.0 - mu ** alpha)
     raise ValueError(f"unknown LD model {model!r}")
 
 
@@ -112,6 +129,9 @@ def profile_dmu(model: str, mu, coef=(), table=None):
         u1, u2 = coef
         em = np.exp(mu)
         return u1 - u2 * em / (1.0 - em) ** 2
+    if model in ("power2", "power2_pm"):
+        c, alpha = power2_coef(model, coef)
+        return c * alpha * mu ** (alpha - 1.0)
     raise ValueError(f"unknown LD model {model!r}")
 
 
@@ -144,4 +164,7 @@ def istar(model: str, coef=(), table=None) -> float:
     if model == "exponential":
         u1, u2 = coef
         return np.pi * (1.0 - u1 / 3.0) + 2.0 * np.pi * u2 * EXP_C
+    if model in ("power2", "power2_pm"):
+        c, alpha = power2_coef(model, coef)
+        return np.pi * (1.0 - c * alpha / (alpha + 2.0))
     raise ValueError(f"unknown LD model {model!r}")

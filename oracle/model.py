@@ -150,6 +150,10 @@ def pv_status(setup: Setup, row: np.ndarray) -> int:
         c = ldc[pb]
         if setup.ld_model == "quadratic_tri" and not (0.0 <= c[0] <= 1.0 and 0.0 <= c[1] <= 1.0):
             st |= ST_LD_INVALID
+        elif setup.ld_model == "power2" and not (c[1] > 0.0):
+            st |= ST_LD_INVALID
+        elif setup.ld_model == "power2_pm" and not (c[1] > 0.0 and 1.0 - c[0] > 0.0):
+            st |= ST_LD_INVALID          # needs h2 > 0 and c > h2, so that alpha > 0
         elif not (_ld.istar(setup.ld_model, c, _table(setup, pb)) > 0.0):
             st |= ST_LD_INVALID
     return st

@@ -31,7 +31,7 @@ MINUTE = 1.0 / 1440.0
 #: limb-darkening model names and their coefficient counts per passband (the
 #: general law takes 1 to 4, given as ``n_general``)
 LD_NCOEF = {"uniform": 0, "quadratic": 2, "quadratic_tri": 2, "nonlinear": 4, "tabulated": 0,
-            "linear": 1, "logarithmic": 2, "exponential": 2}
+            "linear": 1, "logarithmic": 2, "exponential": 2, "power2": 2, "power2_pm": 2}
 
 
 def ld_ncoef(ld_model: str, n_general: int = 0) -> int:
@@ -285,6 +285,10 @@ def make_small(ld_model: str = "quadratic", npv: int = 3, npt: int = 257, npb: i
             cols += [rng.uniform(0.2, 0.7, npv), rng.uniform(0.0, 0.3, npv)]
         elif ld_model == "exponential":
             cols += [rng.uniform(0.3, 0.6, npv), rng.uniform(0.0, 0.05, npv)]
+        elif ld_model == "power2":
+            cols += [rng.uniform(0.4, 0.8, npv), rng.uniform(0.4, 1.2, npv)]
+        elif ld_model == "power2_pm":
+            cols += [rng.uniform(0.6, 0.8, npv), rng.uniform(0.3, 0.55, npv)]
     if ld_model == "tabulated":
         profiles = [tabulated_profile(rng) for _ in range(npb)]
     params = (np.stack(cols, axis=1) if npv > 0

@@ -65,7 +65,14 @@ typedef enum {
     RR_LD_LINEAR = 5,         /* I = 1 - u (1-mu)                           1 (u)          */
     RR_LD_GENERAL = 6,        /* I = 1 - sum_n c_n (1-mu)^n, n=1..N         N = rr_config.ncoef, 1..4 */
     RR_LD_LOGARITHMIC = 7,    /* I = 1 - u1 (1-mu) - u2 mu ln(mu)           2 (u1, u2)     */
-    RR_LD_EXPONENTIAL = 8     /* I = 1 - u1 (1-mu) - u2 / (1 - exp(mu))     2 (u1, u2)     */
+    RR_LD_EXPONENTIAL = 8,    /* I = 1 - u1 (1-mu) - u2 / (1 - exp(mu))     2 (u1, u2)     */
+    RR_LD_POWER2 = 9,         /* I = 1 - c (1 - mu^alpha), alpha > 0        2 (c, alpha)   */
+    RR_LD_POWER2_PM = 10      /* power-2 with h1 = I(1/2), h2 = I(1/2) - I(0):
+                                 c = 1 - h1 + h2, alpha = log2(c / h2)      2 (h1, h2)     */
+    /* The power-2 laws are not affine in alpha, so no weight projection can be
+     * tabulated for them: they need the direct model (rr_config.direct = 1),
+     * which forms the profile of every pv inside its per-call weight pass, and
+     * they do not combine with the small-planet approximation. */
 } rr_ld_model;
 
 typedef enum {

@@ -28,7 +28,9 @@ int ncoef(int model, int n_general) {
         case RR_LD_QUADRATIC:
         case RR_LD_QUADRATIC_TRI:
         case RR_LD_LOGARITHMIC:
-        case RR_LD_EXPONENTIAL: return 2;
+        case RR_LD_EXPONENTIAL:
+        case RR_LD_POWER2:
+        case RR_LD_POWER2_PM: return 2;
         case RR_LD_NONLINEAR: return 4;
         case RR_LD_LINEAR: return 1;
         case RR_LD_GENERAL: return n_general;
@@ -84,6 +86,8 @@ void free_all(rr_ctx* c) {
     cudaFree(c->d_pre64);
     cudaFree(c->d_pref);
     cudaFree(c->d_gl);
+    cudaFree(c->d_lnmu);
+    cudaFree(c->d_lnmuf);
 }
 
 // Per-kernel timing: when enabled, every launch is bracketed by two CUDA
@@ -309,7 +313,9 @@ rr_status rr_create(const rr_config* cfg, rr_ctx** out) {
         if (!(k.k0 > 0.0 && k.k0 < k.k1 && k.k1 < 1.0)) return fail(nullptr, RR_EINVAL, "need 0 < k0 < k1 < 1");
     }
     if (k.npb < 1 || k.npb > RR_MAX_PB) return fail(nullptr, RR_EINVAL, "npb must be in [1, 32]");
-    if (k.ld_model < RR_LD_UNIFORM || k.ld_model > RR_LD_EXPONENTIAL) return fail(nullptr, RR_EINVAL, "unknown ld_model");
+    if (k.ld_model < RR_LD_UNIFORM || k.ld_model > RR_LD_POWER2_PM) return fail(nullptr, RR_EINVAL, "unknown ld_model");
+    if ((k.ld_model == RR_LD_POWER2 || k.ld_model == RR_LD_POWER2_PM) && (k.direct != 1 || k.k_small != 0.0))
+        return fail(nullptr, RR_EINVAL, "the power-2 laws need the direct model (direct = 1) and k_small = 0");
     if (k.ld_model == RR_LD_GENERAL ? (k.ncoef < 1 || k.ncoef > 4) : k.ncoef != 0)
         return fail(nullptr, RR_EINVAL, "ncoef must be 1..4 for RR_LD_GENERAL and 0 otherwise");
     if (k.precision != RR_PREC_FP64 && k.precision != RR_PREC_MIXED) return fail(nullptr, RR_EINVAL, "unknown precision");
@@ -326,7 +332,8 @@ rr_status rr_create(const rr_config* cfg, rr_ctx** out) {
     cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, k.device);
     c->nz = k.nzin + k.nzlimb;
     c->nldc = ncoef(k.ld_model, k.ncoef);
-    c->nbasis = k.ld_model == RR_LD_TABULATED ? k.npb : 1 + c->nldc;
+    const bool p2 = k.ld_model == RR_LD_POWER2 || k.ld_model == RR_LD_POWER2_PM;
+    c->nbasis = k.ld_model == RR_LD_TABULATED ? k.npb : (p2 ? 1 : 1 + c->nldc);
     c->nkp = k.chromatic ? k.npb : 1;
     c->nparam = 6 + c->nkp + k.npb * c->nldc;
     c->dk = k.direct ? 1.0 : (k.k1 - k.k0) / (k.nk - 1);
@@ -341,11 +348,26 @@ rr_status rr_create(const rr_config* cfg, rr_ctx** out) {
         dalloc(&c->d_istar, c->nbasis) || dalloc(&c->d_T64, nT) || dalloc(&c->d_T32, nT) || dalloc(&c->d_DT32, nT) ||
         dalloc(&c->d_tab_off, k.npb + 1) || dalloc(&c->d_err, 1) ||
         (k.direct && (dalloc(&c->d_zef, c->nz + 1) || dalloc(&c->d_basisf, (size_t)c->nbasis * c->nz) ||
-                      dalloc(&c->d_pre64, nP) || dalloc(&c->d_pref, 2 * nP)))) {
+                      dalloc(&c->d_pre64, nP) || dalloc(&c->d_pref, 2 * nP))) ||
+        (p2 && (dalloc(&c->d_lnmu, c->nz) || dalloc(&c->d_lnmuf, c->nz)))) {
         free_all(c);
         delete c;
         cudaGetLastError();
         return fail(nullptr, RR_ENOMEM, "device allocation failed");
+    }
+    if (p2) {
+        std::vector<double> lm(c->nz);
+        std::vector<float> lmf(c->nz);
+        for (int j = 0; j < c->nz; ++j) {
+            lm[j] = std::log(c->mu[j]);
+            lmf[j] = (float)lm[j];
+        }
+        if ((e = cudaMemcpy(c->d_lnmu, lm.data(), c->nz * sizeof(double), cudaMemcpyHostToDevice)) ||
+            (e = cudaMemcpy(c->d_lnmuf, lmf.data(), c->nz * sizeof(float), cudaMemcpyHostToDevice))) {
+            free_all(c);
+            delete c;
+            return cuda_fail(nullptr, e, "upload of ln mu");
+        }
     }
     if ((e = cudaMemcpy(c->d_ze, c->ze.data(), (c->nz + 1) * sizeof(double), cudaMemcpyHostToDevice)) ||
         (e = cudaMemcpy(c->d_mu, c->mu.data(), c->nz * sizeof(double), cudaMemcpyHostToDevice)) ||

@@ -176,6 +176,8 @@ struct rr_ctx {
     double* d_pre64 = nullptr;   // nbasis * (nz + 1)
     float* d_pref = nullptr;     // 2 * nbasis * (nz + 1): FP32 hi, then lo
     double* d_gl = nullptr;      // Gauss-Legendre nodes and weights of rr_exact_flux (on first use)
+    double* d_lnmu = nullptr;    // ln mu of the bin means (power-2 laws, direct model)
+    float* d_lnmuf = nullptr;    // the same in FP32
     int num_sms = 0;
     bool weights_built = false;
     bool tables_built = false;
@@ -203,6 +205,16 @@ namespace rr {
 inline bool shared_weights(const rr_ctx* c) { return c->cfg.shared_weights && c->cfg.chromatic && c->cfg.npb > 1; }
 // rows of the direct model's per-call projections per pv
 inline int direct_rows_per_pv(const rr_ctx* c) { return shared_weights(c) ? 1 : c->nkp; }
+// power-2 laws: the profile is formed per pv inside the direct model's weight pass
+inline bool power2_law(const rr_ctx* c) {
+    return c->cfg.ld_model == RR_LD_POWER2 || c->cfg.ld_model == RR_LD_POWER2_PM;
+}
+// columns of the direct model's projections per row: the profile bases, or for the power-2
+// laws 1 and, per passband the row serves, mu^alpha and mu^alpha ln mu
+inline int direct_cols(const rr_ctx* c) {
+    if (!power2_law(c)) return c->nbasis;
+    return (c->cfg.chromatic && !shared_weights(c)) ? 3 : 1 + 2 * c->cfg.npb;
+}
 // adjoint accumulators per pv: the parameters, plus the mean k with shared weights
 inline int grad_nacc(const rr_ctx* c) { return c->nparam + (shared_weights(c) ? 1 : 0); }
 

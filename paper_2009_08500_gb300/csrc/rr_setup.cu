@@ -401,11 +401,12 @@ __global__ void rr_direct_prefix_kernel(ModelParams mp, const double* __restrict
 constexpr int kDirWarps = 8;
 constexpr int kDirBases = 5;
 
-template <typename A>
+template <typename A, bool P2>
 __global__ void __launch_bounds__(kDirWarps * 32) rr_direct_table_kernel(
         ModelParams mp, const double* __restrict__ params, const A* __restrict__ ze,
         const A* __restrict__ basis, const double* __restrict__ basis64, const A* __restrict__ pre,
-        const float* __restrict__ pre_lo, DirectTables D, int grad) {
+        const float* __restrict__ pre_lo, const A* __restrict__ lnmu, const double* __restrict__ mu64,
+        DirectTables D, int grad) {
     const int ng = mp.ng, nz = mp.nz;
     const int wpr = (ng + 31) >> 5;   // warps per row
     const long long w = (long long)blockIdx.x * kDirWarps + (threadIdx.x >> 5);
@@ -431,9 +432,21 @@ __global__ void __launch_bounds__(kDirWarps * 32) rr_direct_table_kernel(
         kd = params[(size_t)pv * mp.nparam + 6 + slot];
     }
     // bases of the row: every named basis; tabulated, the passband's own
-    // profile when the row is one passband's, else every passband's
-    int b_lo = 0, b_hi = mp.nbasis;
+    // profile when the row is one passband's, else every passband's.  The
+    // power-2 laws: column 0 the constant, then per passband q the row serves
+    // mu^alpha_q and mu^alpha_q ln mu (the latter for the adjoint)
+    constexpr bool p2 = P2;                          // a power-2 law (instantiated apart)
+    const bool p2own = mp.chromatic && !mp.shared;   // a power-2 row serves its own passband only
+    int b_lo = 0, b_hi = p2 ? (p2own ? 3 : 1 + 2 * mp.npb) : mp.nbasis;
     if (mp.ld_model == RR_LD_TABULATED && mp.chromatic && !mp.shared) { b_lo = slot; b_hi = slot + 1; }
+    // power-2 exponent of a column's passband
+    auto p2_alpha = [&](int b) -> double {
+        const int pb = p2own ? slot : (b - 1) >> 1;
+        const double* cf = params + (size_t)pv * mp.nparam + 6 + nkp + pb * 2;
+        if (mp.ld_model == RR_LD_POWER2) return cf[1];
+        const double cc = 1.0 - cf[0] + cf[1];
+        return cc > 0.0 && cf[1] > 0.0 ? log2(cc / cf[1]) : 1.0;   // invalid: flagged by the set-up kernel
+    };
     A* Thi = reinterpret_cast<A*>(D.hi);
     A* Tdk = reinterpret_cast<A*>(D.dk);
     const size_t bstride = (size_t)D.nrows * ng;
@@ -453,7 +466,15 @@ __global__ void __launch_bounds__(kDirWarps * 32) rr_direct_table_kernel(
         // g = 1 (no covered area): the row's limit, all weight in the outermost
         // annulus; rows of invalid k are zero (never read)
         for (int b = b_lo; b < b_hi; ++b) {
-            const double v = valid ? basis64[(size_t)b * nz + nz - 1] : 0.0;
+            double v = 0.0;
+            if (valid) {
+                if (!p2 || b == 0) {
+                    v = p2 ? 1.0 : basis64[(size_t)b * nz + nz - 1];
+                } else {
+                    const double lm = log(mu64[nz - 1]);
+                    v = exp(p2_alpha(b) * lm) * (((b - 1) & 1) ? lm : 1.0);
+                }
+            }
             Thi[b * bstride + o] = (A)v;
             if (D.lo) D.lo[b * bstride + o] = (float)(v - (double)(A)v);
             if (grad) Tdk[b * bstride + o] = A(0);
@@ -467,14 +488,17 @@ __global__ void __launch_bounds__(kDirWarps * 32) rr_direct_table_kernel(
         const int m = (L + H) >> 1;
         if (ze[m] <= lo_r) L = m; else H = m;
     }
-    const int e0 = L;
+    int e0 = L;
     L = e0; H = nz;
     while (H - L > 1) {
         const int m = (L + H) >> 1;
         if (ze[m] >= hi_r) H = m; else L = m;
     }
     const int e1 = H;
-    const bool centre = c < k;   // the disk's centre is covered: annuli below e0 count whole
+    // the disk's centre is covered: annuli below e0 count whole, from the running sums; the
+    // power-2 profiles differ per pv, so there the walk starts at the centre instead
+    const bool centre = c < k && !p2;
+    if (c < k && p2) e0 = 0;
     const A dtot = tk + g * tc;
     for (int bg = b_lo; bg < b_hi; bg += kDirBases) {
         const int nb = min(kDirBases, b_hi - bg);
@@ -482,6 +506,15 @@ __global__ void __launch_bounds__(kDirWarps * 32) rr_direct_table_kernel(
         A dS[kDirBases];
         #pragma unroll
         for (int q = 0; q < kDirBases; ++q) dS[q] = A(0);
+        // power-2 columns: exponent and kind (0: 1, 1: mu^alpha, 2: mu^alpha ln mu)
+        A alpha[kDirBases];
+        int kind[kDirBases];
+        #pragma unroll
+        for (int q = 0; q < kDirBases; ++q) {
+            const int b = bg + q;
+            kind[q] = (!p2 || b == 0 || q >= nb) ? 0 : 1 + ((b - 1) & 1);
+            alpha[q] = kind[q] ? (A)p2_alpha(b) : A(0);
+        }
         A ak, ac;
         A a0 = edge_area(ze[e0], k, c, inv_c, inv4c2, far, ak, ac);
         a0 += ac * c_lo;
@@ -495,7 +528,16 @@ __global__ void __launch_bounds__(kDirWarps * 32) rr_direct_table_kernel(
             #pragma unroll
             for (int q = 0; q < kDirBases; ++q) {
                 if (q < nb) {
-                    const A lbj = basis[(size_t)(bg + q) * nz + j];
+                    A lbj;
+                    if (!p2) {
+                        lbj = basis[(size_t)(bg + q) * nz + j];
+                    } else if (kind[q] == 0) {
+                        lbj = A(1);
+                    } else {
+                        const A lm = lnmu[j];
+                        lbj = exp(alpha[q] * lm);
+                        if (kind[q] == 2) lbj *= lm;
+                    }
                     S[q].add_prod(d, lbj);
                     if (grad) dS[q] += dd * lbj;
                 }
@@ -717,12 +759,21 @@ __global__ void __launch_bounds__(256, 4) rr_pv_setup_kernel(ModelParams mp, PbP
             const double sq = sqrt(fmax(q1, 0.0));
             u[0] = 2.0 * sq * q2;
             u[1] = sq * (1.0 - 2.0 * q2);
+        } else if (mp.ld_model == RR_LD_POWER2 || mp.ld_model == RR_LD_POWER2_PM) {
+            // (c, alpha); from (h1, h2): c = 1 - h1 + h2, alpha = log2(c / h2)
+            const double cc = mp.ld_model == RR_LD_POWER2 ? c[0] : 1.0 - c[0] + c[1];
+            const double al = mp.ld_model == RR_LD_POWER2 ? c[1] : (cc > 0.0 && c[1] > 0.0 ? log2(cc / c[1]) : -1.0);
+            if (!(al > 0.0)) st |= RR_PV_LD_INVALID;
+            u[0] = cc;
+            u[1] = al;
         } else {
             for (int j = 0; j < mp.nldc; ++j) u[j] = c[j];
         }
         double Is;
         if (mp.ld_model == RR_LD_TABULATED) {
             Is = istar[pb];
+        } else if (mp.ld_model == RR_LD_POWER2 || mp.ld_model == RR_LD_POWER2_PM) {
+            Is = CUDART_PI * (1.0 - u[0] * u[1] / (u[1] + 2.0));
         } else {
             Is = istar[0];
             for (int j = 0; j < mp.nldc; ++j) Is += u[j] * istar[1 + j];
@@ -962,9 +1013,69 @@ __global__ void __launch_bounds__(256, 4) rr_pv_setup_kernel(ModelParams mp, PbP
         for (int c = 0; c < 4; ++c) uc[c] = c < nc ? u_s[lp][pb][c] : R(0);
         R Ic[4];   // basis disk integrals, converted once per row
         #pragma unroll
-        for (int c = 0; c < 4; ++c) Ic[c] = (grad && c < nc) ? (R)istar[1 + c] : R(0);
+        // (the power-2 laws have no coefficient bases: their I_star partials are formed per pv)
+        const bool p2law = mp.ld_model == RR_LD_POWER2 || mp.ld_model == RR_LD_POWER2_PM;
+        for (int c = 0; c < 4; ++c) Ic[c] = (grad && c < nc && !p2law) ? (R)istar[1 + c] : R(0);
         const int b0 = named ? 0 : pb;
         if (ik < 0) continue;   // small-planet approximation: rr_small_planet_kernel writes these rows
+        if (mp.direct && (mp.ld_model == RR_LD_POWER2 || mp.ld_model == RR_LD_POWER2_PM)) {
+            // power-2 laws: row = ((1 - c) T0 + c T1) / I_star with T0 = w . 1 and T1 = w . mu^alpha
+            // of this passband; adjoint rows in (c, alpha) with T2 = w . mu^alpha ln mu = dT1/dalpha,
+            // then for (h1, h2) the chain rule through c = 1 - h1 + h2, alpha = log2(c / h2)
+            const size_t ds = (size_t)D.nrows * mp.ng;
+            const int q = (mp.chromatic && !mp.shared) ? 0 : pb;
+            const size_t o0 = (size_t)ik * mp.ng;
+            const R* Hp = reinterpret_cast<const R*>(D.hi) + o0;
+            const float* Lp = D.lo ? D.lo + o0 : nullptr;
+            const R* Kp = grad ? reinterpret_cast<const R*>(D.dk) + o0 : nullptr;
+            const int cl[3] = {0, 1 + 2 * q, 2 + 2 * q};
+            const R cc = uc[0], al = uc[1];
+            // d I_star / d c and d I_star / d alpha
+            const R Ic_c = -Tr<R>::pi() * al / (al + R(2));
+            const R Ic_a = -R(2) * Tr<R>::pi() * cc / ((al + R(2)) * (al + R(2)));
+            auto val = [&](int col, int i) -> R {
+                return Hp[cl[col] * ds + i] + (Lp ? (R)Lp[cl[col] * ds + i] : R(0));
+            };
+            const int ig_end = min(L.ng_pad, 64 * ch + 64);
+            for (int ig = 64 * ch + lane; ig < ig_end; ig += 32) {
+                if (ig >= mp.ng) {
+                    for (int r = 0; r < L.rows_per_pb; ++r) r0[(size_t)r * L.ng_pad + ig] = (R)0;
+                    continue;
+                }
+                const R t0 = val(0, ig), t1 = val(1, ig);
+                const R ldw_n = ((R(1) - cc) * t0 + cc * t1) * invIs;
+                r0[ig] = ldw_n;
+                if (!grad) continue;
+                R dv = 0;
+                if (ig < mp.ng - 1) {
+                    R d0 = Hp[cl[0] * ds + ig + 1] - Hp[cl[0] * ds + ig];
+                    R d1 = Hp[cl[1] * ds + ig + 1] - Hp[cl[1] * ds + ig];
+                    if (Lp) {
+                        d0 += (R)(Lp[cl[0] * ds + ig + 1] - Lp[cl[0] * ds + ig]);
+                        d1 += (R)(Lp[cl[1] * ds + ig + 1] - Lp[cl[1] * ds + ig]);
+                    }
+                    dv = (R(1) - cc) * d0 + cc * d1;
+                }
+                r0[L.ng_pad + ig] = dv * invIs;
+                r0[2 * L.ng_pad + ig] = ((R(1) - cc) * Kp[cl[0] * ds + ig] + cc * Kp[cl[1] * ds + ig]) * invIs;
+                const R t2 = val(2, ig);
+                R Qc = ((t1 - t0) - ldw_n * Ic_c) * invIs;
+                R Qa = (cc * t2 - ldw_n * Ic_a) * invIs;
+                if (mp.ld_model == RR_LD_POWER2_PM) {
+                    // h2 = c 2^-alpha; dc/dh1 = -1, dalpha/dh1 = -1 / (c ln 2),
+                    // dc/dh2 = 1, dalpha/dh2 = (1/c - 1/h2) / ln 2
+                    const R inv_ln2 = R(1.4426950408889634);
+                    const R inv_h2 = exp2(al) / cc;
+                    const R Qh1 = -Qc - Qa * inv_ln2 / cc;
+                    const R Qh2 = Qc + Qa * (R(1) / cc - inv_h2) * inv_ln2;
+                    Qc = Qh1;
+                    Qa = Qh2;
+                }
+                r0[3 * L.ng_pad + ig] = Qc;
+                r0[4 * L.ng_pad + ig] = Qa;
+            }
+            continue;
+        }
         if (mp.direct) {
             // direct model: the pv's own projections (no k interpolation); the
             // in-cell slopes come from the differences of the FP32 pairs
@@ -1121,7 +1232,7 @@ cudaError_t launch_weights(rr_ctx* c, bool need_w, cudaStream_t s) {
 }
 
 size_t direct_bytes(const rr_ctx* c, int npv, bool grad) {
-    const size_t n = (size_t)c->nbasis * npv * direct_rows_per_pv(c) * c->cfg.ng;
+    const size_t n = (size_t)direct_cols(c) * npv * direct_rows_per_pv(c) * c->cfg.ng;
     const size_t rb = c->cfg.precision == RR_PREC_FP64 ? sizeof(double) : sizeof(float);
     size_t b = align256(n * rb);
     if (c->cfg.precision == RR_PREC_MIXED) b += align256(n * sizeof(float));
@@ -1131,7 +1242,7 @@ size_t direct_bytes(const rr_ctx* c, int npv, bool grad) {
 
 DirectTables direct_view(const rr_ctx* c, void* base, int npv, bool grad) {
     DirectTables D;
-    const size_t n = (size_t)c->nbasis * npv * direct_rows_per_pv(c) * c->cfg.ng;
+    const size_t n = (size_t)direct_cols(c) * npv * direct_rows_per_pv(c) * c->cfg.ng;
     const size_t rb = c->cfg.precision == RR_PREC_FP64 ? sizeof(double) : sizeof(float);
     char* p = (char*)base;
     D.hi = p;
@@ -1160,13 +1271,17 @@ cudaError_t launch_direct_tables(rr_ctx* c, const double* params, int npv, bool 
     ModelParams mp = model_params(c);
     const long long warps = (long long)npv * direct_rows_per_pv(c) * ((c->cfg.ng + 31) / 32);
     const unsigned grid = (unsigned)((warps + kDirWarps - 1) / kDirWarps);
-    if (c->cfg.precision == RR_PREC_FP64)
-        rr_direct_table_kernel<double><<<grid, kDirWarps * 32, 0, s>>>(mp, params, c->d_ze, c->d_basis, c->d_basis,
-                                                                       c->d_pre64, nullptr, D, grad ? 1 : 0);
-    else
-        rr_direct_table_kernel<float><<<grid, kDirWarps * 32, 0, s>>>(
-            mp, params, c->d_zef, c->d_basisf, c->d_basis, c->d_pref,
-            c->d_pref + (size_t)c->nbasis * (c->nz + 1), D, grad ? 1 : 0);
+    const bool p2 = power2_law(c);
+    if (c->cfg.precision == RR_PREC_FP64) {
+        auto kern = p2 ? rr_direct_table_kernel<double, true> : rr_direct_table_kernel<double, false>;
+        kern<<<grid, kDirWarps * 32, 0, s>>>(mp, params, c->d_ze, c->d_basis, c->d_basis, c->d_pre64, nullptr,
+                                             c->d_lnmu, c->d_mu, D, grad ? 1 : 0);
+    } else {
+        auto kern = p2 ? rr_direct_table_kernel<float, true> : rr_direct_table_kernel<float, false>;
+        kern<<<grid, kDirWarps * 32, 0, s>>>(mp, params, c->d_zef, c->d_basisf, c->d_basis, c->d_pref,
+                                             c->d_pref + (size_t)c->nbasis * (c->nz + 1), c->d_lnmuf, c->d_mu, D,
+                                             grad ? 1 : 0);
+    }
     c->launches++;
     return cudaGetLastError();
 }

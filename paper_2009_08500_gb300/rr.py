@@ -19,9 +19,10 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "librr.so")
 
 LD_MODELS = {"uniform": 0, "quadratic": 1, "quadratic_tri": 2, "nonlinear": 3, "tabulated": 4, "linear": 5,
-             "general": 6, "logarithmic": 7, "exponential": 8}
+             "general": 6, "logarithmic": 7, "exponential": 8, "power2": 9, "power2_pm": 10}
 PRECISIONS = {"fp64": 0, "mixed": 1}
-STATUS = {0: "RR_OK", 1: "RR_EINVAL", 2: "RR_ENOMEM", 3: "RR_ECUDA", 4: "RR_ESTATE", 6: "RR_ETIMEOUT"}
+STATUS = {0: "RR_OK", 1: "RR_EINVAL", 2: "RR_ENOMEM", 3: "RR_ECUDA", 4: "RR_ESTATE", 5: "RR_EDOMAIN",
+          6: "RR_ETIMEOUT"}
 TABLES = {"ze": 0, "zm": 1, "mu": 2, "weights": 3, "basis": 4, "istar": 5, "proj": 6}
 
 PV_K_RANGE, PV_E_RANGE, PV_B_RANGE, PV_P_RANGE = 1, 2, 4, 8

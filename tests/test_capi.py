@@ -46,7 +46,7 @@ def test_null_handles_are_rejected_without_a_device(lib):
 
 
 @pytest.mark.parametrize("field,value,msg", [("zcut", 1.5, b"zcut"), ("nzin", 0, b"nzin"), ("ng", 1, b"ng"),
-                                             ("k1", 0.001, b"k0"), ("npb", 40, b"npb"), ("ld_model", 9, b"ld_model"),
+                                             ("k1", 0.001, b"k0"), ("npb", 40, b"npb"), ("ld_model", 11, b"ld_model"),
                                              ("precision", 5, b"precision"), ("chromatic", 2, b"chromatic"),
                                              ("direct", 2, b"direct"), ("shared_weights", 3, b"shared_weights"),
                                              ("k_small", -0.1, b"k_small"), ("k_small", float("nan"), b"k_small")])
@@ -68,6 +68,16 @@ def test_direct_model_does_not_check_the_k_grid(lib):
     assert b"nk" not in msg and b"k0" not in msg
     if st == 0:
         lib.rr_destroy(out)
+
+
+@pytest.mark.parametrize("ld_model", [9, 10])
+def test_power2_laws_need_the_direct_model(lib, ld_model):
+    cfg = rr.RRConfig(0.7, 200, 300, 200, 60, 0.005, 0.3, 1, ld_model, 0, 1, 0, 0, 0)
+    out = ctypes.c_void_p()
+    assert lib.rr_create(ctypes.byref(cfg), ctypes.byref(out)) == 1
+    assert b"direct" in lib.rr_last_error(None)
+    cfg.direct, cfg.k_small = 1, 0.05
+    assert lib.rr_create(ctypes.byref(cfg), ctypes.byref(out)) == 1
 
 
 @pytest.mark.parametrize("ld_model,ncoef", [(6, 0), (6, 5), (1, 2), (8, 1)])

@@ -44,7 +44,7 @@ CONFIG_TEXT = {
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch, from one ncu capture
 # of the same kernels (profiles/flux_mixed_c3_population.md, grad_mixed_c3_population.md,
 # flux_mixed_c4_heterogeneous.md); to be cleared whenever those kernels change
-TRAFFIC = {("c3", "flux"): 271_840_000, ("c3", "grad"): 33_965_056}
+TRAFFIC = {("c3", "flux"): 271_840_000, ("c3", "grad"): 33_965_056, ("c4", "flux"): 446_731_776}
 
 
 def parse():
@@ -488,6 +488,7 @@ def run_variant(a, wl, grad, local, dev, flush, **change):
     return {"value": wl.npv * wl.samples_per_pv() / (ms * 1e-3), "unit": "points/s", "ms_per_step": ms,
             "steps": n, "dtype": "f32+f64",
             "direct_table_ms_per_launch": round(dms / max(dn, 1), 5) if dn else None,
+            "kernels_ms_per_launch": {k: round(v[0] / v[1], 5) for k, v in kp.items() if v[1]},
             "note": f"same workload and step with {what}, one GPU"}
 
 

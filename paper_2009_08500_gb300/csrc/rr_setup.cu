@@ -624,8 +624,7 @@ __device__ R mean_anomaly_of_true_r(R f, R e) {
 // the profile at the planet's centre, mu = sqrt(1 - min(c, 1)^2) with
 // c = g_i (1 + k_w), clamped below to mu_min, divided by I_star; with the
 // adjoint also the in-cell difference, d/dk (through mu; 0 where clamped) and
-// the coefficient rows (basis_c - row I_star_c) / I_star.  One thread per
-// (pv, passband, g node).
+// the coefficient rows (basis_c - row I_star_c) / I_star.
 struct SmallPlanetRow {
     double kw;
     double ud[5];   // weights of the bases: 1, then the coefficients
@@ -658,11 +657,14 @@ __global__ void __launch_bounds__(256) rr_small_planet_kernel(ModelParams mp, co
                                                               const double* __restrict__ tab,
                                                               const int* __restrict__ tab_off, RecLayout L, int grad,
                                                               char* __restrict__ records) {
-    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= (long long)npv * mp.npb * mp.ng) return;
-    const int ig = (int)(t % mp.ng);
-    const long long r = t / mp.ng;
-    const int pb = (int)(r % mp.npb), pv = (int)(r / mp.npb);
+    // one warp per (pv, passband) row and 32 consecutive g nodes
+    const int wpr = (mp.ng + 31) >> 5;
+    const long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= (long long)npv * mp.npb * wpr) return;
+    const int chunk = (int)(w % wpr);
+    const long long rw = w / wpr;
+    const int pb = (int)(rw % mp.npb), pv = (int)(rw / mp.npb);
     const double* row = params + (size_t)pv * mp.nparam;
     const int nkp = mp.chromatic ? mp.npb : 1;
     double kw = row[6 + (mp.chromatic ? pb : 0)];
@@ -695,22 +697,28 @@ __global__ void __launch_bounds__(256) rr_small_planet_kernel(ModelParams mp, co
     const double invIs = (double)(R)(1.0 / Is);
     R* r0 = reinterpret_cast<R*>(records + rows_offset(L, npv) + (size_t)pv * L.rows_bytes) +
             (size_t)pb * L.rows_per_pb * L.ng_pad;
-    double vb[5] = {0.0, 0.0, 0.0, 0.0, 0.0}, dk;
-    const double v = small_planet_node(mp, sp, tab, tab_off, ig, vb, dk) * invIs;
-    r0[ig] = (R)v;
-    if (ig == mp.ng - 1)
-        for (int q = mp.ng; q < L.ng_pad; ++q)
+    if (chunk == wpr - 1)
+        for (int q = mp.ng + lane; q < L.ng_pad; q += 32)
             for (int rr = 0; rr < L.rows_per_pb; ++rr) r0[(size_t)rr * L.ng_pad + q] = (R)0;
-    if (!grad) return;
-    double dv = 0.0;
-    if (ig < mp.ng - 1) {
-        double vb1[5], dk1;
-        dv = small_planet_node(mp, sp, tab, tab_off, ig + 1, vb1, dk1) * invIs - v;
+    // each node is evaluated once: the in-cell difference takes the next node's value from the
+    // next lane (the last lane evaluates its next node itself)
+    {
+        const int ig = chunk * 32 + lane;
+        double vb[5] = {0.0, 0.0, 0.0, 0.0, 0.0}, dk = 0.0, v = 0.0;
+        if (ig < mp.ng) v = small_planet_node(mp, sp, tab, tab_off, ig, vb, dk) * invIs;
+        double vn = __shfl_down_sync(0xffffffffu, v, 1);
+        if (grad && lane == 31 && ig + 1 < mp.ng) {
+            double vb1[5], dk1;
+            vn = small_planet_node(mp, sp, tab, tab_off, ig + 1, vb1, dk1) * invIs;
+        }
+        if (ig >= mp.ng) return;
+        r0[ig] = (R)v;
+        if (!grad) return;
+        r0[L.ng_pad + ig] = (R)(ig < mp.ng - 1 ? vn - v : 0.0);
+        r0[2 * L.ng_pad + ig] = (R)(dk * invIs);
+        for (int j = 0; j < sp.nc; ++j)
+            r0[(size_t)(3 + j) * L.ng_pad + ig] = (R)((vb[1 + j] - v * (double)(R)istar[1 + j]) * invIs);
     }
-    r0[L.ng_pad + ig] = (R)dv;
-    r0[2 * L.ng_pad + ig] = (R)(dk * invIs);
-    for (int j = 0; j < sp.nc; ++j)
-        r0[(size_t)(3 + j) * L.ng_pad + ig] = (R)((vb[1 + j] - v * (double)(R)istar[1 + j]) * invIs);
 }
 
 // Pvs per CTA of the set-up kernel: few, so that the launch has several
@@ -1305,8 +1313,8 @@ cudaError_t launch_pv_setup(rr_ctx* c, const double* params, int npv, const PbPa
     c->launches++;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || !(c->cfg.k_small > 0.0) || npv == 0) return e;
-    // rows of the small-planet passbands
-    const long long n = (long long)npv * c->cfg.npb * c->cfg.ng;
+    // rows of the small-planet passbands: one warp per (pv, passband, 32 g nodes)
+    const long long n = (long long)npv * c->cfg.npb * ((c->cfg.ng + 31) / 32) * 32;
     const unsigned nb = (unsigned)((n + 255) / 256);
     if (c->cfg.precision == RR_PREC_FP64)
         rr_small_planet_kernel<double><<<nb, 256, 0, s>>>(mp, params, npv, c->d_istar, c->d_tab, c->d_tab_off,

@@ -1,15 +1,21 @@
 // Internal layout shared by the host code and the kernels of librr.
 //
 // Per-call data flow (all stream-ordered, no host synchronisation):
-//   rr_pv_setup_kernel   params -> one PvRecord per parameter vector in the
+//   rr_direct_table_kernel  (direct model only) per (pv, k slot) and g node the
+//                        weight projections for the pv's own k -> workspace
+//   rr_pv_setup_kernel   params -> one record per parameter vector in the
 //                        caller's workspace (orbit constants, transit window,
-//                        k-interpolated profile rows divided by I_star)
-//   rr_flux_kernel       PvRecords of a pv tile -> shared memory (one bulk
-//                        async copy), times of a point tile -> registers,
-//                        flux[pv][t] for the tile
-//   rr_grad_kernel       same tiling; per-(pv, point tile) partial sums of the
-//                        vector-Jacobian product -> workspace
-//   rr_grad_reduce       partial sums -> grad_params (fixed order)
+//                        profile rows divided by I_star: interpolated in k, or
+//                        the pv's direct projections)
+//   rr_small_planet_kernel  (k_small > 0 only) the rows of passbands below the
+//                        threshold, from the profile at the planet's centre
+//   rr_points_kernel     (mixed form) per-time float-float offsets, passband and
+//                        128-time group summaries
+//   rr_flux_mixed_kernel / rr_flux_fp64_kernel: records of a pv tile -> shared
+//                        memory (one bulk async copy), flux[pv][t] for the tile
+//   rr_grad_mixed_kernel / rr_grad_fp64_kernel: same tiling; per-(pv, chunk)
+//                        partial sums of the vector-Jacobian product -> workspace
+//   rr_grad_finish_kernel  partial sums -> grad_params (fixed order), chain rules
 #pragma once
 
 #include <cstddef>

@@ -1,5 +1,6 @@
 // Set-up kernels: LD profile bases and disk integrals, the (k, g) weight table
-// with its projections, and the per-call, per-parameter-vector records.
+// with its projections, the direct model's per-call weight projections, the
+// small-planet rows, and the per-call, per-parameter-vector records.
 #include <cmath>
 
 #include "rr_device.cuh"

@@ -420,7 +420,7 @@ int64_t rr_launch_count(const rr_ctx* ctx);
 #define RR_KERNEL_FLUX 3
 #define RR_KERNEL_GRAD 4
 #define RR_KERNEL_GRAD_REDUCE 5
-#define RR_KERNEL_POINTS 6
+#define RR_KERNEL_POINTS 6    /* several passbands; with one, the per-time preparation is part of PV_SETUP */
 #define RR_KERNEL_DIRECT 7    /* the direct model's per-call weight projections */
 #define RR_KERNEL_KINDS 8
 

@@ -207,10 +207,17 @@ cudaError_t run_setup(rr_ctx* c, const double* times, const int32_t* pb_index, i
                       int npv, const PbParams& pbp, bool grad, int32_t* pv_status, void* ws, cudaStream_t s) {
     cudaError_t e = run_direct(c, params, npv, grad, ws, s);
     if (e != cudaSuccess) return e;
-    e = timed(c, RR_KERNEL_PV_SETUP, s, [&] { return launch_pv_setup(c, params, npv, pbp, grad, ws, pv_status, s); });
-    if (e != cudaSuccess || c->cfg.precision != RR_PREC_MIXED || npt == 0) return e;
+    // the per-pv set-up and (mixed form) the per-time preparation: one launch for a single
+    // passband (measured: the preparation then costs nothing on the population workload), two
+    // with several (sharing the launch slowed the 8-passband set-up by more than it saved)
     const WsLayout W = ws_layout(c, npv, npt, grad);
     char* wb = (char*)ws;
+    const bool fused = c->cfg.npb == 1;
+    e = timed(c, RR_KERNEL_PV_SETUP, s, [&] {
+        return launch_pv_setup(c, params, npv, pbp, grad, ws, pv_status, s, times, pb_index, fused ? npt : 0,
+                               wb + W.pts_dt, wb + W.pts_pb, wb + W.pts_grp);
+    });
+    if (e != cudaSuccess || fused || c->cfg.precision != RR_PREC_MIXED || npt == 0) return e;
     return timed(c, RR_KERNEL_POINTS, s,
                  [&] { return launch_points(c, times, pb_index, npt, wb + W.pts_dt, wb + W.pts_pb, wb + W.pts_grp, s); });
 }

@@ -548,7 +548,7 @@ __device__ __forceinline__ float delta32(const PvHead<float>& H, const PvPb<floa
 
 // Per-warp group state of the FP32 kernels.  A group is kWarpPts = 128
 // consecutive times, 4 per lane; its float-float times are relative to the
-// group's first time t_g.  The group's summary comes from rr_points_kernel;
+// group's first time t_g.  The group's summary comes from points_group;
 // lane l also holds the phase constants of pv l of the CTA's tile at t_g:
 // A = frac((t_g - T0) / P) as a float pair and the removed integer cycles m.
 struct GroupState {
@@ -820,6 +820,69 @@ __device__ __forceinline__ double ld_basis_mu(const ModelParams& mp, int b, doub
             if (b == 1) { d = 1.0; return -q; }
             d = 2.0 * q;
             return -q * q;
+    }
+}
+
+// Per-point inputs of the FP32 kernels, once per call, for one 128-time group
+// g (thread t = 0..127 of the group): dt = t - t_g as a float pair, t_g = the
+// group's first time (FP64 here, so that the per-(pv, point) work is FP32
+// only), and the passband index with out-of-range values mapped to npb; the
+// group's summary (GroupInfo): the range and largest magnitude of its float
+// offsets, whether it is full with valid passbands, and t_g - t_0.  Every
+// thread of the block calls (one barrier); groups g >= ngroups only take part
+// in the barrier.  red, redf: the group's reduction slots in shared memory.
+__device__ __forceinline__ void points_group(const double* __restrict__ times, const int32_t* __restrict__ pb_index,
+                                             int npt, int npb, float2* __restrict__ dt, int32_t* __restrict__ pbw,
+                                             GroupInfo* __restrict__ grp, int g, int ngroups, int t,
+                                             float (*red)[kWarpPts / 32], int* redf) {
+    const int lane = t & 31, warp = t >> 5;
+    const bool live = g < ngroups;
+    const int p = g * kWarpPts + t;
+    float lo = INFINITY, hi = -INFINITY, mx = 0.0f;
+    int ok = 0;
+    double tg = 0.0;
+    if (live) tg = times[(size_t)g * kWarpPts];
+    if (live && p < npt) {
+        const double d = times[p] - tg;
+        const float h = (float)d;
+        dt[p] = make_float2(h, (float)(d - (double)h));
+        const int pb = pb_index ? pb_index[p] : 0;
+        const int v = (pb >= 0 && pb < npb) ? pb : npb;
+        pbw[p] = v;
+        lo = hi = h;
+        mx = fabsf(h);
+        ok = v < npb;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+        mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    }
+    ok = __all_sync(0xffffffffu, ok);
+    if (lane == 0) {
+        red[0][warp] = lo;
+        red[1][warp] = hi;
+        red[2][warp] = mx;
+        redf[warp] = ok;
+    }
+    __syncthreads();
+    if (t == 0 && live) {
+        GroupInfo gi;
+        gi.wlo = red[0][0];
+        gi.whi = red[1][0];
+        gi.maxdt = red[2][0];
+        gi.full = redf[0];
+        for (int w = 1; w < kWarpPts / 32; ++w) {
+            gi.wlo = fminf(gi.wlo, red[0][w]);
+            gi.whi = fmaxf(gi.whi, red[1][w]);
+            gi.maxdt = fmaxf(gi.maxdt, red[2][w]);
+            gi.full &= redf[w];
+        }
+        const double d0 = tg - times[0];
+        gi.toff_h = (float)d0;
+        gi.toff_l = (float)(d0 - (double)gi.toff_h);
+        gi.pad[0] = gi.pad[1] = 0.0f;
+        grp[g] = gi;
     }
 }
 

@@ -10,7 +10,7 @@
 // tile's pvs, reusing its times from registers.
 //
 // Mixed precision (FP32 bulk):
-//  * per time, once per call (rr_points_kernel): dt = t - t_ref in FP64,
+//  * per time, once per call (points_group): dt = t - t_ref in FP64,
 //    kept as a float pair (dh, dl) -- t_ref is the first time of the tile;
 //  * per (CTA, pv), FP64: A = frac((t_ref - T0) / P) as a float pair;
 //  * per (pv, time): coarse phase psi = A + dh / P with one FMA, rounded
@@ -26,65 +26,24 @@
 
 namespace rr {
 
-// Per-point inputs of the FP32 kernels, once per call: dt = t - t_g as a float
-// pair, t_g = the first time of the point's 128-time group (FP64 here, so that
-// the per-(pv, point) work is FP32 only), and the passband index with
-// out-of-range values mapped to npb.  One CTA per group also writes the
-// group's summary (GroupInfo): the range and largest magnitude of its float
-// offsets, whether it is full with valid passbands, and t_g - t_0.
+// The per-time inputs of the FP32 kernels as a launch of their own (one CTA per
+// 128-time group); single-passband batches carry them in the set-up launch.
 __global__ void __launch_bounds__(kWarpPts) rr_points_kernel(const double* __restrict__ times,
                                                              const int32_t* __restrict__ pb_index, int npt, int npb,
                                                              float2* __restrict__ dt, int32_t* __restrict__ pbw,
-                                                             GroupInfo* __restrict__ grp) {
+                                                             GroupInfo* __restrict__ grp, int ngroups) {
     __shared__ float red[3][kWarpPts / 32];
     __shared__ int redf[kWarpPts / 32];
-    const int g = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int p = g * kWarpPts + tid;
-    const double tg = times[(size_t)g * kWarpPts];
-    float lo = INFINITY, hi = -INFINITY, mx = 0.0f;
-    int ok = 0;
-    if (p < npt) {
-        const double d = times[p] - tg;
-        const float h = (float)d;
-        dt[p] = make_float2(h, (float)(d - (double)h));
-        const int pb = pb_index ? pb_index[p] : 0;
-        const int v = (pb >= 0 && pb < npb) ? pb : npb;
-        pbw[p] = v;
-        lo = hi = h;
-        mx = fabsf(h);
-        ok = v < npb;
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-        lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
-        hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
-        mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    }
-    ok = __all_sync(0xffffffffu, ok);
-    if (lane == 0) {
-        red[0][warp] = lo;
-        red[1][warp] = hi;
-        red[2][warp] = mx;
-        redf[warp] = ok;
-    }
-    __syncthreads();
-    if (tid == 0) {
-        GroupInfo gi;
-        gi.wlo = red[0][0];
-        gi.whi = red[1][0];
-        gi.maxdt = red[2][0];
-        gi.full = redf[0];
-        for (int w = 1; w < kWarpPts / 32; ++w) {
-            gi.wlo = fminf(gi.wlo, red[0][w]);
-            gi.whi = fmaxf(gi.whi, red[1][w]);
-            gi.maxdt = fmaxf(gi.maxdt, red[2][w]);
-            gi.full &= redf[w];
-        }
-        const double d0 = tg - times[0];
-        gi.toff_h = (float)d0;
-        gi.toff_l = (float)(d0 - (double)gi.toff_h);
-        gi.pad[0] = gi.pad[1] = 0.0f;
-        grp[g] = gi;
-    }
+    points_group(times, pb_index, npt, npb, dt, pbw, grp, blockIdx.x, ngroups, threadIdx.x, red, redf);
+}
+
+cudaError_t launch_points(rr_ctx* c, const double* times, const int32_t* pb_index, int npt, void* ws_dt,
+                          void* ws_pb, void* ws_grp, cudaStream_t s) {
+    const int ngroups = (npt + kWarpPts - 1) / kWarpPts;
+    rr_points_kernel<<<ngroups, kWarpPts, 0, s>>>(times, pb_index, npt, c->cfg.npb, (float2*)ws_dt,
+                                                  (int32_t*)ws_pb, (GroupInfo*)ws_grp, ngroups);
+    c->launches++;
+    return cudaGetLastError();
 }
 
 // Stores the 4 outputs of a lane (one 16-byte store when the row is vector-aligned).
@@ -460,15 +419,6 @@ int pv_tile_for(int rec_bytes) {
     if (t < 1) t = 1;
     if (t > kMaxPvTile) t = kMaxPvTile;
     return t;
-}
-
-cudaError_t launch_points(rr_ctx* c, const double* times, const int32_t* pb_index, int npt, void* ws_dt,
-                          void* ws_pb, void* ws_grp, cudaStream_t s) {
-    rr_points_kernel<<<(npt + kWarpPts - 1) / kWarpPts, kWarpPts, 0, s>>>(times, pb_index, npt, c->cfg.npb,
-                                                                          (float2*)ws_dt, (int32_t*)ws_pb,
-                                                                          (GroupInfo*)ws_grp);
-    c->launches++;
-    return cudaGetLastError();
 }
 
 cudaError_t launch_flux(rr_ctx* c, const double* times, const int32_t* pb_index, const void* pts_dt,

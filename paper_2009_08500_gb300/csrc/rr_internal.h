@@ -6,11 +6,12 @@
 //   rr_pv_setup_kernel   params -> one record per parameter vector in the
 //                        caller's workspace (orbit constants, transit window,
 //                        profile rows divided by I_star: interpolated in k, or
-//                        the pv's direct projections)
+//                        the pv's direct projections); in the same launch (mixed
+//                        form, one passband) the per-time float-float offsets,
+//                        passband and 128-time group summaries (rr_points_kernel
+//                        apart with several passbands)
 //   rr_small_planet_kernel  (k_small > 0 only) the rows of passbands below the
 //                        threshold, from the profile at the planet's centre
-//   rr_points_kernel     (mixed form) per-time float-float offsets, passband and
-//                        128-time group summaries
 //   rr_flux_mixed_kernel / rr_flux_fp64_kernel: records of a pv tile -> shared
 //                        memory (one bulk async copy), flux[pv][t] for the tile
 //   rr_grad_mixed_kernel / rr_grad_fp64_kernel: same tiling; per-(pv, chunk)
@@ -40,7 +41,7 @@ constexpr int kMaxBasis = RR_MAX_PB + 4;  // profile bases: 1 + nldc (named) or 
 constexpr double kESwitch = 0.8;          // above this eccentricity Kepler is solved in FP64
 constexpr int kWarpPts = 4 * 32;          // times per group: one warp, 4 consecutive times per lane
 
-// Per 128-time group, written once per call by rr_points_kernel (mixed form):
+// Per 128-time group, written once per call by points_group (mixed form):
 // the range and largest magnitude of the float offsets of its times from the
 // group's first time t_g, whether all 128 times exist with a valid passband,
 // and t_g - t_0 (t_0 = the first time of the call) as a float pair.
@@ -87,6 +88,17 @@ struct alignas(16) PvPb {
     R win_p;          // same, widened by the passband's exposure half-span [rad]
     float win_pc;     // win_p in cycles (phase units of the FP32 point check)
     float pad[3];
+};
+
+// Arguments of the per-time preparation carried by the set-up launch (its
+// first npoints CTAs; none when npt == 0).
+struct PointsArgs {
+    const double* times;
+    const int32_t* pb_index;
+    int32_t npt, ngroups, npoints, pad_;
+    float2* dt;
+    int32_t* pbw;
+    GroupInfo* grp;
 };
 
 // Per-pv records live in two regions of the workspace: the headers (PvHead +
@@ -233,9 +245,15 @@ cudaError_t launch_direct_tables(rr_ctx* c, const double* params, int npv, bool 
                                  cudaStream_t s);
 size_t direct_bytes(const rr_ctx* c, int npv, bool grad);
 DirectTables direct_view(const rr_ctx* c, void* base, int npv, bool grad);
-// records: the workspace (the direct model's projections follow the records)
+cudaError_t launch_points(rr_ctx* c, const double* times, const int32_t* pb_index, int npt, void* ws_dt,
+                          void* ws_pb, void* ws_grp, cudaStream_t s);
+// records: the workspace (the direct model's projections follow the records).  With times
+// (mixed form, npt > 0) the same launch also writes the per-time inputs of the FP32 kernels
+// (float-float offsets, passband, 128-time group summaries) into pts_dt, pts_pb, pts_grp.
 cudaError_t launch_pv_setup(rr_ctx* c, const double* params, int npv, const PbParams& pbp,
-                            bool grad, void* records, int32_t* pv_status, cudaStream_t s);
+                            bool grad, void* records, int32_t* pv_status, cudaStream_t s,
+                            const double* times = nullptr, const int32_t* pb_index = nullptr, int npt = 0,
+                            void* pts_dt = nullptr, void* pts_pb = nullptr, void* pts_grp = nullptr);
 // grad_layout: the records were written in the adjoint's layout (rr_prepare)
 cudaError_t launch_flux(rr_ctx* c, const double* times, const int32_t* pb_index, const void* pts_dt,
                         const void* pts_pb, const void* pts_grp, int npt, int npv, const PbParams& pbp,
@@ -255,8 +273,7 @@ struct WsLayout {
     size_t rec, dir, pts_dt, pts_pb, pts_grp, part, total;
 };
 WsLayout ws_layout(const rr_ctx* c, int npv, int npt, bool grad);
-cudaError_t launch_points(rr_ctx* c, const double* times, const int32_t* pb_index, int npt, void* ws_dt,
-                          void* ws_pb, void* ws_grp, cudaStream_t s);
+
 ModelParams model_params(const rr_ctx* c);
 int pv_tile_for(int rec_bytes);
 void release_host_pipe(rr_ctx* c);

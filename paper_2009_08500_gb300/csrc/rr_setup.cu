@@ -734,7 +734,19 @@ __global__ void __launch_bounds__(256, 4) rr_pv_setup_kernel(ModelParams mp, PbP
                                                           const R* __restrict__ T, const float* __restrict__ DT,
                                                           const double* __restrict__ istar,
                                                           RecLayout L, int grad, char* __restrict__ records,
-                                                          int32_t* __restrict__ pv_status, DirectTables D) {
+                                                          int32_t* __restrict__ pv_status, DirectTables D,
+                                                          PointsArgs pa) {
+    if ((int)blockIdx.x < pa.npoints) {
+        // the per-time inputs of the FP32 kernels, two 128-time groups per CTA, in the same
+        // launch as the per-pv set-up (the two are independent); these short CTAs come first
+        __shared__ float pred[2][3][kWarpPts / 32];
+        __shared__ int predf[2][kWarpPts / 32];
+        const int half = threadIdx.x / kWarpPts;
+        points_group(pa.times, pa.pb_index, pa.npt, mp.npb, pa.dt, pa.pbw, pa.grp, (int)blockIdx.x * 2 + half,
+                     pa.ngroups, threadIdx.x % kWarpPts, pred[half], predf[half]);
+        return;
+    }
+    const int sblock = (int)blockIdx.x - pa.npoints;   // this CTA's index among the set-up CTAs
     constexpr int NP = SetupPvs<R>::N;
     __shared__ R u_s[NP][RR_MAX_PB][4];
     __shared__ R invIs_s[NP][RR_MAX_PB];
@@ -747,7 +759,7 @@ __global__ void __launch_bounds__(256, 4) rr_pv_setup_kernel(ModelParams mp, PbP
     __shared__ int flags_s[NP];
     __shared__ R orb_s[NP][6];     // a, b, e, f0, M0, n
     const int ppc = setup_pvs_per_cta(mp.npb);
-    const int pv0 = blockIdx.x * ppc;
+    const int pv0 = sblock * ppc;
     const int nloc = min(ppc, npv - pv0);
     const int nkp = mp.chromatic ? mp.npb : 1;
     const int tid = threadIdx.x;
@@ -1296,20 +1308,34 @@ cudaError_t launch_direct_tables(rr_ctx* c, const double* params, int npv, bool 
 }
 
 cudaError_t launch_pv_setup(rr_ctx* c, const double* params, int npv, const PbParams& pbp, bool grad,
-                            void* records, int32_t* pv_status, cudaStream_t s) {
+                            void* records, int32_t* pv_status, cudaStream_t s, const double* times,
+                            const int32_t* pb_index, int npt, void* pts_dt, void* pts_pb, void* pts_grp) {
     ModelParams mp = model_params(c);
     DirectTables D = {nullptr, nullptr, nullptr, 0};
     if (c->cfg.direct) D = direct_view(c, (char*)records + align256(records_bytes(c, npv, grad)), npv, grad);
     const int ppc = setup_pvs_per_cta(c->cfg.npb);
-    const int blocks = (npv + ppc - 1) / ppc;
+    PointsArgs pa = {};
+    int blocks = (npv + ppc - 1) / ppc;
+    if (c->cfg.precision == RR_PREC_MIXED && npt > 0 && times) {
+        // the per-time preparation rides in the same launch: two groups per CTA
+        pa.times = times;
+        pa.pb_index = pb_index;
+        pa.npt = npt;
+        pa.ngroups = (npt + kWarpPts - 1) / kWarpPts;
+        pa.dt = (float2*)pts_dt;
+        pa.pbw = (int32_t*)pts_pb;
+        pa.grp = (GroupInfo*)pts_grp;
+        pa.npoints = (pa.ngroups + 1) / 2;
+        blocks += pa.npoints;
+    }
     if (c->cfg.precision == RR_PREC_FP64) {
         RecLayout L = make_layout<double>(c->cfg.npb, c->cfg.ng, c->nldc, grad);
         rr_pv_setup_kernel<double><<<blocks, 256, 0, s>>>(mp, pbp, params, npv, c->d_T64, c->d_DT32, c->d_istar, L,
-                                                          grad ? 1 : 0, (char*)records, pv_status, D);
+                                                          grad ? 1 : 0, (char*)records, pv_status, D, pa);
     } else {
         RecLayout L = make_layout<float>(c->cfg.npb, c->cfg.ng, c->nldc, grad);
         rr_pv_setup_kernel<float><<<blocks, 256, 0, s>>>(mp, pbp, params, npv, c->d_T32, c->d_DT32, c->d_istar, L,
-                                                         grad ? 1 : 0, (char*)records, pv_status, D);
+                                                         grad ? 1 : 0, (char*)records, pv_status, D, pa);
     }
     c->launches++;
     cudaError_t e = cudaGetLastError();

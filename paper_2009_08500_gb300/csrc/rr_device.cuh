@@ -199,6 +199,12 @@ __device__ __forceinline__ void bulk_s2g(void* gdst, const void* ssrc, uint32_t 
                  : "memory");
 }
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// Start fetching [gsrc, gsrc + bytes) of global memory into L2 (a hint: nothing
+// waits for it).  gsrc 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_prefetch_l2(const void* gsrc, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(__cvta_generic_to_global(gsrc)), "r"(bytes)
+                 : "memory");
+}
 // Wait until every bulk group this thread committed has completed (writes done).
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 // Make this thread's generic-proxy writes to shared memory visible to the async proxy.
@@ -654,6 +660,7 @@ __device__ __forceinline__ bool warp_may_transit(const PvHead<float>& H, float4 
 // Shared counters.
 struct TileCounters {
     int next_group, nitems, next_item, producers;
+    unsigned rows_pf;   // pvs of the tile whose rows an L2 prefetch has been issued for (adjoint)
 };
 
 // Work item: phase constants of the pv at the group start (Ah, Al, m, rounding
@@ -681,6 +688,7 @@ __device__ __forceinline__ void queue_init(ItemQueue q, TileCounters* tc, int ca
         tc->nitems = 0;
         tc->next_item = 0;
         tc->producers = blockDim.x >> 5;
+        tc->rows_pf = 0u;
     }
 }
 

@@ -321,7 +321,19 @@ __global__ void __launch_bounds__(kBlock, 3) rr_grad_mixed_kernel(
         unsigned bad;
         float4 cl;
         const unsigned may = group_decide(gs, recs, L.head_bytes, npv_t, bad, cl);
-        if (may) queue_push(queue, tc, may, g, cl);
+        if (may) {
+            queue_push(queue, tc, may, g, cl);
+            if ((may >> lane) & 1u) {
+                // the items of this group read pv `lane`'s rows and cotangent segment, which the
+                // forward pass's output stream has usually evicted from L2: start fetching them
+                // now (rows once per CTA), well before a warp claims the item
+                if (!((atomicOr(&tc->rows_pf, 1u << lane) >> lane) & 1u))
+                    bulk_prefetch_l2(rowsg + (size_t)(pv0 + lane) * L.rows_bytes, (uint32_t)L.rows_bytes);
+                if (vec_g && gs.full)
+                    bulk_prefetch_l2(gflux + (size_t)(pv0 + lane) * npt + (size_t)g * kWarpPts,
+                                     kWarpPts * (uint32_t)sizeof(float));
+            }
+        }
     };
 
     // an item: its sums go to its own (pv, group) slot, so the result does not

@@ -406,6 +406,16 @@ rr_status rr_choose_grid(rr_config* cfg, const double* k, int32_t nk, const doub
  * outputs are incomplete).  Resets the indicator.  Errors: RR_ECUDA. */
 rr_status rr_sync_status(rr_ctx* ctx, void* stream);
 
+/* Failure-detection self-test (no fault, trap or hang): enqueue on `stream` a
+ * one-CTA kernel whose bounded device-side wait runs out on purpose --
+ * which = 0: an mbarrier phase whose expected bytes never arrive (the wait of
+ * the shared-memory staging copies, about one second); which = 1: a work-queue
+ * slot that no producer publishes (the queue's claim wait, tens of ms).  The
+ * kernel records the expiry in the context's error word and returns, so the
+ * next rr_sync_status reports RR_ETIMEOUT and the context stays usable.
+ * Errors: RR_EINVAL (which), RR_ECUDA. */
+rr_status rr_selftest_wait(rr_ctx* ctx, int32_t which, void* stream);
+
 /* Description of the last error on `ctx` (or of the last rr_create failure
  * when ctx is NULL).  Valid until the next call on the same context. */
 const char* rr_last_error(const rr_ctx* ctx);

@@ -412,6 +412,7 @@ rr_status rr_set_ld_profile(rr_ctx* c, int32_t pb, const double* mu, const doubl
 }
 
 rr_status rr_build_weights(rr_ctx* c, void* stream) {
+    NvtxRange nvtx_range("rr_build_weights");
     if (!c) return fail(nullptr, RR_EINVAL, "null context");
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e = cudaSetDevice(c->cfg.device);
@@ -471,6 +472,7 @@ size_t rr_workspace_bytes(const rr_ctx* c, int32_t npv, int32_t npt, int32_t wit
 rr_status rr_evaluate(rr_ctx* c, const double* times, const int32_t* pb_index, int32_t npt, const double* params,
                       int32_t npv, const int32_t* ss, const double* exptime, void* flux, int32_t* pv_status,
                       void* ws, size_t ws_bytes, void* stream) {
+    NvtxRange nvtx_range("rr_evaluate");
     return evaluate_impl(c, times, pb_index, npt, params, npv, ss, exptime, flux, pv_status, ws, ws_bytes, false,
                          stream);
 }
@@ -479,6 +481,7 @@ rr_status rr_evaluate_grad(rr_ctx* c, const double* times, const int32_t* pb_ind
                            const double* params, int32_t npv, const int32_t* ss, const double* exptime,
                            const void* grad_flux, double* grad_params, int32_t* pv_status, void* ws,
                            size_t ws_bytes, void* stream) {
+    NvtxRange nvtx_range("rr_evaluate_grad");
     return evaluate_grad_impl(c, times, pb_index, npt, params, npv, ss, exptime, grad_flux, grad_params, pv_status,
                               ws, ws_bytes, false, stream);
 }
@@ -486,6 +489,7 @@ rr_status rr_evaluate_grad(rr_ctx* c, const double* times, const int32_t* pb_ind
 rr_status rr_prepare(rr_ctx* c, const double* times, const int32_t* pb_index, int32_t npt, const double* params,
                      int32_t npv, const int32_t* ss, const double* exptime, int32_t* pv_status, void* ws,
                      size_t ws_bytes, void* stream) {
+    NvtxRange nvtx_range("rr_prepare");
     PbParams pbp;
     // the workspace stands in for the output pointer: rr_prepare writes only the workspace
     rr_status st = check_eval(c, times, pb_index, npt, params, npv, ss, exptime, ws, ws, ws_bytes, true, pbp);
@@ -503,6 +507,7 @@ rr_status rr_prepare(rr_ctx* c, const double* times, const int32_t* pb_index, in
 rr_status rr_evaluate_prepared(rr_ctx* c, const double* times, const int32_t* pb_index, int32_t npt,
                                const double* params, int32_t npv, const int32_t* ss, const double* exptime,
                                void* flux, int32_t* pv_status, const void* ws, size_t ws_bytes, void* stream) {
+    NvtxRange nvtx_range("rr_evaluate_prepared");
     return evaluate_impl(c, times, pb_index, npt, params, npv, ss, exptime, flux, pv_status, const_cast<void*>(ws),
                          ws_bytes, true, stream);
 }
@@ -511,6 +516,7 @@ rr_status rr_evaluate_grad_prepared(rr_ctx* c, const double* times, const int32_
                                     const double* params, int32_t npv, const int32_t* ss, const double* exptime,
                                     const void* grad_flux, double* grad_params, int32_t* pv_status, const void* ws,
                                     size_t ws_bytes, void* stream) {
+    NvtxRange nvtx_range("rr_evaluate_grad_prepared");
     return evaluate_grad_impl(c, times, pb_index, npt, params, npv, ss, exptime, grad_flux, grad_params, pv_status,
                               const_cast<void*>(ws), ws_bytes, true, stream);
 }
@@ -568,6 +574,15 @@ rr_status rr_sync_status(rr_ctx* c, void* stream) {
         return fail(c, RR_ETIMEOUT, w == kErrQueueTimeout ? "a kernel gave up waiting for its shared work queue"
                                                            : "a kernel gave up waiting for its shared-memory staging copy");
     }
+    return RR_OK;
+}
+
+rr_status rr_selftest_wait(rr_ctx* c, int32_t which, void* stream) {
+    if (!c) return fail(nullptr, RR_EINVAL, "null context");
+    if (which != 0 && which != 1) return fail(c, RR_EINVAL, "which must be 0 (mbarrier) or 1 (work queue)");
+    cudaError_t e = cudaSetDevice(c->cfg.device);
+    if (e == cudaSuccess) e = launch_selftest(c, which, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "rr_selftest_wait");
     return RR_OK;
 }
 

@@ -223,11 +223,24 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 }
 
 // Bounded wait: gives up after ~0.1 s and reports false.
+// Nanoseconds of the GPU's global timer.
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Bounded wait on an mbarrier phase: at most 2^21 polls and about one second
+// (try_wait may suspend the thread for a system-dependent time per poll, so
+// the clock bounds the total).  false when it gave up.
+constexpr uint64_t kWaitLimitNs = 1000000000ull;
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+    const uint64_t t0 = global_ns();
     #pragma unroll 1
     for (int i = 0; i < (1 << 21); ++i) {
         if (mbar_try_wait(bar, parity)) return true;
         if (i > 32) __nanosleep(64);
+        if ((i & 255) == 255 && global_ns() - t0 > kWaitLimitNs) break;
     }
     return false;
 }

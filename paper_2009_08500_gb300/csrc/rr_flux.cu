@@ -421,6 +421,35 @@ int pv_tile_for(int rec_bytes) {
     return t;
 }
 
+// Failure-detection self-test: one bounded wait that nothing completes (see
+// rr_selftest_wait); the expiry is recorded in the error word like any other.
+__global__ void rr_selftest_kernel(int which, int* err) {
+    __shared__ uint64_t bar;
+    __shared__ int slot[1];
+    __shared__ float4 slot_c[1];
+    if (which == 0) {
+        if (threadIdx.x != 0) return;
+        mbar_init(&bar, 1);
+        mbar_expect_tx(&bar, 16);   // this thread arrives; the 16 bytes of transaction never come
+        if (!mbar_wait_bounded(&bar, 0)) atomicExch(err, kErrBarrierTimeout);
+        return;
+    }
+    // a claimed slot whose producer never publishes it; the whole warp takes part
+    // (the claim wait ends in a warp shuffle)
+    if (threadIdx.x == 0) slot[0] = -1;
+    __syncwarp();
+    ItemQueue q;
+    q.c = slot_c;
+    q.gi = slot;
+    if (queue_key(q, 0) < 0 && threadIdx.x == 0) atomicExch(err, kErrQueueTimeout);
+}
+
+cudaError_t launch_selftest(rr_ctx* c, int which, cudaStream_t s) {
+    rr_selftest_kernel<<<1, 32, 0, s>>>(which, c->d_err);
+    c->launches++;
+    return cudaGetLastError();
+}
+
 cudaError_t launch_flux(rr_ctx* c, const double* times, const int32_t* pb_index, const void* pts_dt,
                         const void* pts_pb, const void* pts_grp, int npt, int npv, const PbParams& pbp,
                         const void* records,

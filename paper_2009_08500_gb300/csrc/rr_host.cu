@@ -58,6 +58,7 @@ extern "C" rr_status rr_evaluate_host(rr_ctx* c, const double* times, const int3
                                       const double* params, int32_t npv, const int32_t* ss, const double* exptime,
                                       const void* grad_flux, void* flux, double* grad_params, int32_t* pv_status,
                                       int32_t chunk_pvs) {
+    NvtxRange nvtx_range("rr_evaluate_host");
     if (!c) return RR_EINVAL;
     if (npt < 0 || npv < 0 || chunk_pvs < 0) {
         c->err = "npt, npv and chunk_pvs must be >= 0";
@@ -188,6 +189,7 @@ extern "C" rr_status rr_enqueue_host(rr_ctx* c, const double* times, const int32
                                      const double* params, int32_t npv, const int32_t* ss, const double* exptime,
                                      const void* grad_flux, void* flux, double* grad_params, int32_t* pv_status,
                                      void* scratch, size_t scratch_bytes, void* stream) {
+    NvtxRange nvtx_range("rr_enqueue_host");
     if (!c) return RR_EINVAL;
     if (npt < 0 || npv < 0) {
         c->err = "npt and npv must be >= 0";

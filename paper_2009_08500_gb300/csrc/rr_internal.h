@@ -25,6 +25,7 @@
 #include <vector>
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "../../include/rr.h"
 
@@ -219,6 +220,14 @@ struct rr_ctx {
 };
 
 namespace rr {
+// An NVTX range over a C-ABI call (visible in Nsight timelines; a no-op without a tool).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
 // shared weights in effect: one weight array per pv for several per-passband k
 inline bool shared_weights(const rr_ctx* c) { return c->cfg.shared_weights && c->cfg.chromatic && c->cfg.npb > 1; }
 // rows of the direct model's per-call projections per pv
@@ -245,6 +254,7 @@ cudaError_t launch_direct_tables(rr_ctx* c, const double* params, int npv, bool 
                                  cudaStream_t s);
 size_t direct_bytes(const rr_ctx* c, int npv, bool grad);
 DirectTables direct_view(const rr_ctx* c, void* base, int npv, bool grad);
+cudaError_t launch_selftest(rr_ctx* c, int which, cudaStream_t s);
 cudaError_t launch_points(rr_ctx* c, const double* times, const int32_t* pb_index, int npt, void* ws_dt,
                           void* ws_pb, void* ws_grp, cudaStream_t s);
 // records: the workspace (the direct model's projections follow the records).  With times

@@ -34,7 +34,8 @@ EXPORTS = ["rr_create", "rr_destroy", "rr_set_ld_profile", "rr_build_weights", "
            "rr_sync_status", "rr_last_error", "rr_launch_count", "rr_profile", "rr_profile_read",
            "rr_evaluate_noalloc", "rr_prepare", "rr_evaluate_prepared", "rr_evaluate_grad_prepared",
            "rr_evaluate_host", "rr_request_bytes", "rr_enqueue_host", "rr_server_create", "rr_server_destroy",
-           "rr_server_submit", "rr_server_poll", "rr_server_pending", "rr_exact_flux", "rr_choose_grid"]
+           "rr_server_submit", "rr_server_poll", "rr_server_pending", "rr_exact_flux", "rr_choose_grid",
+           "rr_selftest_wait"]
 KERNELS = {"ld_basis": 0, "weights": 1, "pv_setup": 2, "flux": 3, "grad": 4, "grad_reduce": 5, "points": 6,
            "direct": 7}
 
@@ -105,8 +106,9 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     L.rr_profile.argtypes = [vp, i32]
     L.rr_profile_read.argtypes = [vp, i32, dp, ctypes.POINTER(i64), i32]
     L.rr_exact_flux.argtypes = [vp, vp, vp, i32, dp, i32, vp, vp]
+    L.rr_selftest_wait.argtypes = [vp, i32, vp]
     L.rr_choose_grid.argtypes = [ctypes.POINTER(RRConfig), dp, i32, dp, dp, dp, i32, ctypes.c_double, dp]
-    for name in ("rr_exact_flux", "rr_choose_grid", "rr_create", "rr_destroy", "rr_set_ld_profile", "rr_build_weights", "rr_evaluate",
+    for name in ("rr_exact_flux", "rr_choose_grid", "rr_selftest_wait", "rr_create", "rr_destroy", "rr_set_ld_profile", "rr_build_weights", "rr_evaluate",
                  "rr_evaluate_grad", "rr_sync_status", "rr_profile", "rr_profile_read", "rr_evaluate_noalloc",
                  "rr_prepare", "rr_evaluate_prepared", "rr_evaluate_grad_prepared", "rr_evaluate_host",
                  "rr_enqueue_host"):
@@ -256,6 +258,11 @@ class Model:
 
     def sync_status(self, stream=None):
         self._check(self.lib.rr_sync_status(self._h, _stream_handle(stream)))
+
+    def selftest_wait(self, which: int, stream=None):
+        """Enqueue a bounded device wait that runs out on purpose (0: mbarrier, 1: work queue);
+        the next sync_status raises RR_ETIMEOUT."""
+        self._check(self.lib.rr_selftest_wait(self._h, int(which), _stream_handle(stream)))
 
     # -- evaluation -----------------------------------------------------------
     def _inputs(self, times, params, pb_index):

@@ -44,7 +44,7 @@ CONFIG_TEXT = {
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch, from one ncu capture
 # of the same kernels (profiles/flux_mixed_c3_population.md, grad_mixed_c3_population.md,
 # flux_mixed_c4_heterogeneous.md); to be cleared whenever those kernels change
-TRAFFIC = {("c3", "flux"): 271_917_056, ("c3", "grad"): 38_792_704, ("c4", "flux"): None}
+TRAFFIC = {("c3", "flux"): 271_917_056, ("c3", "grad"): 38_792_704, ("c4", "flux"): 446_281_472}
 
 
 def parse():
@@ -560,8 +560,8 @@ def run_reference(a):
 
 # ----------------------------------------------------------------- serving (C5)
 def run_serving(a):
-    """Closed-loop capacity, then Poisson streams at 0.7x and 1.1x of it."""
-    import threading
+    """Closed-loop capacity, then Poisson streams at 0.7x (three runs) and 1.1x of it."""
+    import gc
 
     import numpy as np
     import torch
@@ -599,6 +599,10 @@ def run_serving(a):
                          pb_index=pin(wl.pb_index, np.int32), supersampling=wl.supersampling, exptime=wl.exptime,
                          grad_flux=gbuf[:wl.npv * wl.npt].view(wl.npv, wl.npt) if grad else None))
     slots = 8
+    # the client is a Python loop: keep the collector's full passes over the
+    # set-up objects (torch, the request pool) out of its timing
+    gc.collect()
+    gc.freeze()
 
     def server():
         return NativeServer(models, slots=slots, mem_budget=64 << 30, device=local)
@@ -625,8 +629,8 @@ def run_serving(a):
         srv.drain()
         closed = srv.stats()
     mean_pts = float(np.mean([ServeRequest(**p).points for p in pool]))
-    runs = {}
-    for load in (0.7, 1.1):
+    runs = []
+    for load in (0.7, 0.7, 0.7, 1.1):
         rate = load * closed["points_per_s"] / mean_pts
         arr = np.cumsum(rng.exponential(1.0 / rate, size=int(rate * a.serve_seconds) + 1))
         with server() as srv:
@@ -635,11 +639,18 @@ def run_serving(a):
                 dt = ta - (time.perf_counter() - t0)
                 if dt > 0:
                     time.sleep(dt)
-                srv.submit(mk(int(rng.integers(0, len(pool)))))
+                r = mk(int(rng.integers(0, len(pool))))
+                r.t_intended = t0 + ta
+                srv.submit(r)
             srv.drain()
-            runs[load] = srv.stats()
-            runs[load]["rate_req_per_s"] = rate
-    line = {"metric": METRIC, "value": runs[0.7]["points_per_s"], "unit": "points/s", "n_gpus": world,
+            st = srv.stats()
+            st["load"] = load
+            st["rate_req_per_s"] = rate
+            runs.append(st)
+    gc.unfreeze()
+    at07 = sorted([r for r in runs if r["load"] == 0.7], key=lambda r: r["latency_p99_ms"])
+    head = at07[len(at07) // 2]          # the run with the median p99
+    line = {"metric": METRIC, "value": head["points_per_s"], "unit": "points/s", "n_gpus": world,
             "steps": None, "warmup": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32+f64", "data": "synthetic (seeded; paper-shaped)",
             "config": {"workload": f"c5: {CONFIG_TEXT['c5']}", "fits": len(fits), "slots": slots,
@@ -647,8 +658,11 @@ def run_serving(a):
                        "request_pool": len(pool), "mean_points_per_request": mean_pts,
                        "serve_seconds": a.serve_seconds},
             "capacity_closed_loop": closed,
-            "latency_ms": {"p50": runs[0.7]["latency_p50_ms"], "p99": runs[0.7]["latency_p99_ms"]},
-            "open_loop": {str(k): v for k, v in runs.items()}}
+            "latency_ms": {"p50": head["latency_p50_ms"], "p99": head["latency_p99_ms"],
+                           "clock": head["latency_clock"], "client_p50": head["client_latency_p50_ms"],
+                           "client_p99": head["client_latency_p99_ms"],
+                           "runs": "open loop at 0.7x of capacity, three runs; the one with the median p99"},
+            "open_loop": runs}
     if rank == 0:
         print(json.dumps(line))
 

@@ -47,6 +47,9 @@ class ServeRequest:
     exptime: Optional[np.ndarray] = None
     grad_flux: Optional[np.ndarray] = None      # cotangent: the request also wants d/d(params)
     deadline_s: Optional[float] = None          # seconds after arrival; expired requests are not admitted
+    # time.perf_counter() at which an open-loop load generator meant to send the
+    # request; the client latency counts from it (so the sender's own lag counts)
+    t_intended: Optional[float] = None
     # filled by the server
     id: int = -1
     nbytes: int = 0
@@ -54,6 +57,7 @@ class ServeRequest:
     t_admit: float = 0.0
     t_launch: float = 0.0
     t_finish: float = 0.0
+    server_ns: Optional[tuple] = None           # library clock: submitted, admitted, finished (ns)
     future: Future = field(default_factory=Future)
 
     @property
@@ -82,10 +86,13 @@ class Done:
     t_arrival: float
     t_admit: float
     t_finish: float
+    t_intended: float
+    server_ns: Optional[tuple] = None
 
 
 def _done_record(req: ServeRequest, ok: bool) -> Done:
-    return Done(req.id, req.points, ok, req.t_arrival, req.t_admit, req.t_finish)
+    t_int = req.t_arrival if req.t_intended is None else req.t_intended
+    return Done(req.id, req.points, ok, req.t_arrival, req.t_admit, req.t_finish, t_int, req.server_ns)
 
 
 class Backend:
@@ -242,17 +249,38 @@ class Server:
 
     # -- metrics ----------------------------------------------------------------
     def stats(self) -> dict:
+        """Throughput and latency of the finished requests.
+
+        latency_*: the scheduler's own clock, from submission to completion --
+        for the native server the library's steady clock (request handed to
+        rr_server_submit until its stream passed it), which no pause of the
+        Python client can stretch.  client_latency_*: from the intended send
+        time (else the submit call) until the poller completed the future, so
+        it also holds the client's own delays.
+        """
         done = [r for r in self.completed if r.ok]
         if not done:
             return {"requests": 0}
-        lat = np.array([r.t_finish - r.t_arrival for r in done])
+        if all(r.server_ns is not None for r in done):
+            lat = np.array([(r.server_ns[2] - r.server_ns[0]) * 1e-9 for r in done])
+            wait = np.array([(r.server_ns[1] - r.server_ns[0]) * 1e-9 for r in done])
+            clock = "library steady clock (rr_server_submit to stream completion)"
+        else:
+            lat = np.array([r.t_finish - r.t_arrival for r in done])
+            wait = np.array([r.t_admit - r.t_arrival for r in done])
+            clock = "scheduler thread (submit to completion)"
+        client = np.array([r.t_finish - r.t_intended for r in done])
         t0 = min(r.t_arrival for r in done)
         t1 = max(r.t_finish for r in done)
         pts = sum(r.points for r in done)
         return {"requests": len(done), "points": pts, "points_per_s": pts / (t1 - t0),
                 "latency_p50_ms": float(np.percentile(lat, 50) * 1e3),
                 "latency_p99_ms": float(np.percentile(lat, 99) * 1e3),
-                "queue_wait_p50_ms": float(np.percentile([r.t_admit - r.t_arrival for r in done], 50) * 1e3),
+                "queue_wait_p50_ms": float(np.percentile(wait, 50) * 1e3),
+                "queue_wait_p99_ms": float(np.percentile(wait, 99) * 1e3),
+                "client_latency_p50_ms": float(np.percentile(client, 50) * 1e3),
+                "client_latency_p99_ms": float(np.percentile(client, 99) * 1e3),
+                "latency_clock": clock,
                 "max_inflight": self.max_inflight_seen, "wall_s": t1 - t0}
 
 
@@ -395,6 +423,7 @@ class NativeServer:
                 with self._lock:
                     req = self._inflight.pop(int(ids[i]))
                 req.t_finish = now
+                req.server_ns = (int(tms[3 * i]), int(tms[3 * i + 1]), int(tms[3 * i + 2]))
                 req.t_admit = req.t_arrival + (tms[3 * i + 1] - tms[3 * i]) * 1e-9
                 h = req._host
                 req._host = None
@@ -437,7 +466,3 @@ class NativeServer:
 
     stats = Server.stats
 
-
-def latency_summary(reqs: List[ServeRequest]) -> dict:
-    lat = np.array([r.t_finish - r.t_arrival for r in reqs])
-    return {"p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3)}

@@ -118,6 +118,9 @@ def test_native_server_results_identical_alone_and_in_the_mix(fits, budget):
             assert np.array_equal(out["grad"], g)
     assert stats["requests"] == len(reqs)
     assert stats["latency_p99_ms"] >= stats["latency_p50_ms"] > 0
+    # latency on the library's clock: never longer than the same requests seen by the client
+    assert stats["latency_clock"].startswith("library")
+    assert stats["client_latency_p99_ms"] >= stats["latency_p50_ms"]
 
 
 def test_native_server_rejects_oversize_requests(fits):

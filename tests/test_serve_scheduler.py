@@ -134,3 +134,16 @@ def test_many_client_threads():
     assert len(results) == 160 and st["requests"] == 160
     assert all(v == float(np.full((4, 9), float(key[0] * 100 + key[1])).sum()) for key, v in results.items())
     assert st["latency_p99_ms"] >= st["latency_p50_ms"] > 0
+
+
+def test_client_latency_counts_from_the_intended_send_time():
+    be = FakeBackend(dur=0.005)
+    with Server(be, slots=2, mem_budget=10_000) as srv:
+        late = _req(1, t_intended=time.perf_counter() - 0.05)    # sent 50 ms after it was due
+        srv.submit(late).result(timeout=10)
+        srv.submit(_req(2)).result(timeout=10)
+        st = srv.stats()
+    assert st["latency_clock"].startswith("scheduler thread")
+    # the scheduler's latency starts at the submit call; the client's at the due time
+    assert st["latency_p99_ms"] < 40 and st["client_latency_p99_ms"] >= 50
+    assert st["client_latency_p50_ms"] >= st["latency_p50_ms"]

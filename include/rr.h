@@ -328,9 +328,17 @@ rr_status rr_enqueue_host(rr_ctx* ctx, const double* times, const int32_t* pb_in
  *   - rr_server_submit copies supersampling / exptime and returns the
  *     request id (>= 0), or a negative rr_status: -RR_EINVAL (arguments),
  *     -RR_ENOMEM (larger than the budget), -RR_ESTATE (server stopping).
+ *   - rr_server_submit_at is rr_server_submit with a release time: the
+ *     request arrives at release_ns (rr_server_now_ns clock; 0 = now) and is
+ *     not admitted before it.  Admission stays in submission order, so a
+ *     caller gives non-decreasing release times.  A release time already past
+ *     counts as the arrival all the same (an open-loop client that submits
+ *     late has its lateness counted in the latency).
+ *   - rr_server_now_ns: the library's steady clock (ns), the clock of every
+ *     server time.
  *   - rr_server_poll hands over up to `max` finished requests (waiting up to
  *     timeout_us for the first): ids, their rr_status, and per request three
- *     steady-clock times in ns (submitted, admitted, finished); returns the
+ *     steady-clock times in ns (arrival, admitted, finished); returns the
  *     count, or a negative rr_status.
  *   - rr_server_destroy finishes every queued request first. */
 typedef struct rr_server rr_server;
@@ -340,6 +348,11 @@ int64_t rr_server_submit(rr_server* server, rr_ctx* fit, const double* times, co
                          int32_t npt, const double* params, int32_t npv, const int32_t* supersampling,
                          const double* exptime, const void* grad_flux, void* flux, double* grad_params,
                          int32_t* pv_status);
+int64_t rr_server_submit_at(rr_server* server, rr_ctx* fit, const double* times, const int32_t* pb_index,
+                            int32_t npt, const double* params, int32_t npv, const int32_t* supersampling,
+                            const double* exptime, const void* grad_flux, void* flux, double* grad_params,
+                            int32_t* pv_status, int64_t release_ns);
+int64_t rr_server_now_ns(void);
 int32_t rr_server_poll(rr_server* server, int64_t* ids, int32_t* status, int64_t* times_ns, int32_t max,
                        int32_t timeout_us);
 /* Requests submitted and not yet handed over by rr_server_poll, minus those finished. */

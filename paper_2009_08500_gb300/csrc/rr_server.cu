@@ -11,6 +11,7 @@
 // are handed to rr_server_poll.  Work of requests admitted at different
 // times overlaps on the device; each request runs the same kernels as it
 // would alone, so its results do not depend on the others.
+#include <algorithm>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -44,7 +45,8 @@ struct Request {
     double* grad = nullptr;
     int32_t* status = nullptr;
     size_t bytes = 0;
-    int64_t t_submit = 0, t_admit = 0, t_done = 0;
+    // t_arrival: the release time (not admitted before it), else the submit call
+    int64_t t_arrival = 0, t_admit = 0, t_done = 0;
     int32_t result = RR_OK;
 };
 
@@ -76,8 +78,10 @@ namespace {
 
 // Admit and launch queued requests while a slot and memory are free (lock held).
 void admit(rr_server* s) {
+    const int64_t now = now_ns();
     while (!s->queue.empty()) {
         Request& r = s->reqs[s->queue.front()];
+        if (r.t_arrival > now) break;                     // in order: not released yet
         if (s->used + r.bytes > s->budget) break;        // in order: wait for memory
         int slot = -1;
         for (size_t i = 0; i < s->slots.size(); ++i)
@@ -130,6 +134,14 @@ void run(rr_server* s) {
         if (!busy && s->queue.empty()) {
             s->cv_work.wait_for(lk, std::chrono::milliseconds(20));
             continue;
+        }
+        if (!busy) {
+            // idle until the head of the queue is released (or a submission wakes the thread)
+            const int64_t wait_ns = s->reqs[s->queue.front()].t_arrival - now_ns();
+            if (wait_ns > 50000) {
+                s->cv_work.wait_for(lk, std::chrono::nanoseconds(std::min<int64_t>(wait_ns - 20000, 20000000)));
+                continue;
+            }
         }
         // requests in flight: poll again shortly (the lock is free meanwhile)
         lk.unlock();
@@ -197,12 +209,14 @@ extern "C" rr_status rr_server_destroy(rr_server* s) {
     return RR_OK;
 }
 
-extern "C" int64_t rr_server_submit(rr_server* s, rr_ctx* fit, const double* times, const int32_t* pb_index,
-                                    int32_t npt, const double* params, int32_t npv, const int32_t* ss,
-                                    const double* exptime, const void* grad_flux, void* flux, double* grad_params,
-                                    int32_t* pv_status) {
+extern "C" int64_t rr_server_now_ns(void) { return now_ns(); }
+
+extern "C" int64_t rr_server_submit_at(rr_server* s, rr_ctx* fit, const double* times, const int32_t* pb_index,
+                                       int32_t npt, const double* params, int32_t npv, const int32_t* ss,
+                                       const double* exptime, const void* grad_flux, void* flux,
+                                       double* grad_params, int32_t* pv_status, int64_t release_ns) {
     if (!s || !fit || !ss || !exptime || npt < 0 || npv < 0 || (npv > 0 && !params) ||
-        (npv > 0 && npt > 0 && (!times || !flux)) || (grad_flux && !grad_params))
+        (npv > 0 && npt > 0 && (!times || !flux)) || (grad_flux && !grad_params) || release_ns < 0)
         return -RR_EINVAL;
     Request r;
     r.fit = fit;
@@ -219,7 +233,7 @@ extern "C" int64_t rr_server_submit(rr_server* s, rr_ctx* fit, const double* tim
     r.status = pv_status;
     r.bytes = rr_request_bytes(fit, npv, npt, grad_flux ? 1 : 0);
     if (r.bytes > s->budget) return -RR_ENOMEM;
-    r.t_submit = now_ns();
+    r.t_arrival = release_ns > 0 ? release_ns : now_ns();
     int64_t id;
     {
         std::lock_guard<std::mutex> lk(s->mu);
@@ -230,6 +244,14 @@ extern "C" int64_t rr_server_submit(rr_server* s, rr_ctx* fit, const double* tim
     }
     s->cv_work.notify_one();
     return id;
+}
+
+extern "C" int64_t rr_server_submit(rr_server* s, rr_ctx* fit, const double* times, const int32_t* pb_index,
+                                    int32_t npt, const double* params, int32_t npv, const int32_t* ss,
+                                    const double* exptime, const void* grad_flux, void* flux, double* grad_params,
+                                    int32_t* pv_status) {
+    return rr_server_submit_at(s, fit, times, pb_index, npt, params, npv, ss, exptime, grad_flux, flux, grad_params,
+                               pv_status, 0);
 }
 
 extern "C" int32_t rr_server_poll(rr_server* s, int64_t* ids, int32_t* status, int64_t* times_ns, int32_t max,
@@ -246,7 +268,7 @@ extern "C" int32_t rr_server_poll(rr_server* s, int64_t* ids, int32_t* status, i
         ids[n] = id;
         if (status) status[n] = it->second.result;
         if (times_ns) {
-            times_ns[3 * n] = it->second.t_submit;
+            times_ns[3 * n] = it->second.t_arrival;
             times_ns[3 * n + 1] = it->second.t_admit;
             times_ns[3 * n + 2] = it->second.t_done;
         }

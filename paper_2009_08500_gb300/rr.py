@@ -34,7 +34,7 @@ EXPORTS = ["rr_create", "rr_destroy", "rr_set_ld_profile", "rr_build_weights", "
            "rr_sync_status", "rr_last_error", "rr_launch_count", "rr_profile", "rr_profile_read",
            "rr_evaluate_noalloc", "rr_prepare", "rr_evaluate_prepared", "rr_evaluate_grad_prepared",
            "rr_evaluate_host", "rr_request_bytes", "rr_enqueue_host", "rr_server_create", "rr_server_destroy",
-           "rr_server_submit", "rr_server_poll", "rr_server_pending", "rr_exact_flux", "rr_choose_grid",
+           "rr_server_submit", "rr_server_submit_at", "rr_server_now_ns", "rr_server_poll", "rr_server_pending", "rr_exact_flux", "rr_choose_grid",
            "rr_selftest_wait"]
 KERNELS = {"ld_basis": 0, "weights": 1, "pv_setup": 2, "flux": 3, "grad": 4, "grad_reduce": 5, "points": 6,
            "direct": 7}
@@ -92,6 +92,10 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     L.rr_server_destroy.restype = ctypes.c_int
     L.rr_server_submit.argtypes = [vp, vp, vp, vp, i32, vp, i32, ctypes.POINTER(i32), dp, vp, vp, vp, vp]
     L.rr_server_submit.restype = i64
+    L.rr_server_submit_at.argtypes = [vp, vp, vp, vp, i32, vp, i32, ctypes.POINTER(i32), dp, vp, vp, vp, vp, i64]
+    L.rr_server_submit_at.restype = i64
+    L.rr_server_now_ns.argtypes = []
+    L.rr_server_now_ns.restype = i64
     L.rr_server_poll.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i32), ctypes.POINTER(i64), i32, i32]
     L.rr_server_poll.restype = i32
     L.rr_server_pending.argtypes = [vp]

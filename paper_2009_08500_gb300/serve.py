@@ -47,8 +47,9 @@ class ServeRequest:
     exptime: Optional[np.ndarray] = None
     grad_flux: Optional[np.ndarray] = None      # cotangent: the request also wants d/d(params)
     deadline_s: Optional[float] = None          # seconds after arrival; expired requests are not admitted
-    # time.perf_counter() at which an open-loop load generator meant to send the
-    # request; the client latency counts from it (so the sender's own lag counts)
+    # time.perf_counter() at which the request arrives (an open-loop client's
+    # schedule): it is not admitted earlier, and its latency counts from then
+    # even when the submit call comes later
     t_intended: Optional[float] = None
     # filled by the server
     id: int = -1
@@ -189,6 +190,8 @@ class Server:
             if req.future.cancelled():
                 self._queue.popleft()
                 continue
+            if req.t_intended is not None and req.t_intended > now:
+                break                                   # in order: not released yet
             if req.deadline_s is not None and now - req.t_arrival > req.deadline_s:
                 self._queue.popleft()
                 req.future.set_exception(TimeoutError(f"request {req.id} expired before admission"))
@@ -251,12 +254,13 @@ class Server:
     def stats(self) -> dict:
         """Throughput and latency of the finished requests.
 
-        latency_*: the scheduler's own clock, from submission to completion --
-        for the native server the library's steady clock (request handed to
-        rr_server_submit until its stream passed it), which no pause of the
-        Python client can stretch.  client_latency_*: from the intended send
-        time (else the submit call) until the poller completed the future, so
-        it also holds the client's own delays.
+        A request arrives at its intended time (ServeRequest.t_intended: the
+        schedule of an open-loop client), else at its submit call.
+        latency_*: the scheduler's own clock, from arrival to completion -- for
+        the native server the library's steady clock (arrival until the
+        request's stream passed it), so a pause of the Python poller does not
+        stretch it, while a client that submits late has its lateness counted.
+        client_latency_*: from arrival until the poller completed the future.
         """
         done = [r for r in self.completed if r.ok]
         if not done:
@@ -266,11 +270,11 @@ class Server:
             wait = np.array([(r.server_ns[1] - r.server_ns[0]) * 1e-9 for r in done])
             clock = "library steady clock (rr_server_submit to stream completion)"
         else:
-            lat = np.array([r.t_finish - r.t_arrival for r in done])
-            wait = np.array([r.t_admit - r.t_arrival for r in done])
-            clock = "scheduler thread (submit to completion)"
+            lat = np.array([r.t_finish - r.t_intended for r in done])
+            wait = np.array([r.t_admit - r.t_intended for r in done])
+            clock = "scheduler thread (arrival to completion)"
         client = np.array([r.t_finish - r.t_intended for r in done])
-        t0 = min(r.t_arrival for r in done)
+        t0 = min(min(r.t_arrival, r.t_intended) for r in done)
         t1 = max(r.t_finish for r in done)
         pts = sum(r.points for r in done)
         return {"requests": len(done), "points": pts, "points_per_s": pts / (t1 - t0),
@@ -375,6 +379,7 @@ class NativeServer:
             raise rr.RRError(st, "rr_server_create failed")
         self._h = h
         self.mem_budget = mem_budget
+        self._clock_off = self._clock_offset()
         self._backend = CudaBackend.__new__(CudaBackend)   # reuse its host-buffer preparation
         self._backend.torch, self._backend.fits = torch, fits
         self._lock = threading.Lock()
@@ -385,10 +390,25 @@ class NativeServer:
         self._poller = threading.Thread(target=self._poll, name="rr-native-serve-poll", daemon=True)
         self._poller.start()
 
+    def _clock_offset(self) -> int:
+        """library steady clock - time.perf_counter_ns(), from the tightest of a few readings."""
+        best = None
+        for _ in range(7):
+            a = time.perf_counter_ns()
+            n = self.lib.rr_server_now_ns()
+            b = time.perf_counter_ns()
+            if best is None or b - a < best[0]:
+                best = (b - a, n - (a + b) // 2)
+        return best[1]
+
     def submit(self, req: ServeRequest) -> Future:
+        """Queue a request.  With req.t_intended (time.perf_counter() seconds) the
+        request arrives then: the library does not admit it earlier, and its
+        latency counts from that time even when the submit call comes later."""
         ctypes, rr = self.ctypes, self.rr
         m = self.fits[req.fit]
         req.t_arrival = time.perf_counter()
+        release = 0 if req.t_intended is None else max(1, int(req.t_intended * 1e9) + self._clock_off)
         self._backend.prepare(req)
         h = req._host
         ss = rr._host_array(req.supersampling, m.npb, np.int32, 1)
@@ -397,10 +417,11 @@ class NativeServer:
         with self._lock:
             if self._stop:
                 raise RuntimeError("server is stopped")
-            rid = self.lib.rr_server_submit(self._h, m._h, rr._ptr(h["t"]), rr._ptr(h["pb"]), req.npt,
-                                            rr._ptr(h["p"]), req.npv, ss.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
-                                            ex.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), rr._ptr(h["g"]),
-                                            rr._ptr(h["flux"]), rr._ptr(h["grad"]), rr._ptr(h["status"]))
+            rid = self.lib.rr_server_submit_at(self._h, m._h, rr._ptr(h["t"]), rr._ptr(h["pb"]), req.npt,
+                                               rr._ptr(h["p"]), req.npv,
+                                               ss.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                               ex.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), rr._ptr(h["g"]),
+                                               rr._ptr(h["flux"]), rr._ptr(h["grad"]), rr._ptr(h["status"]), release)
             if rid < 0:
                 if -rid == 2:
                     raise AdmissionError(f"request larger than the {self.mem_budget}-byte budget")
@@ -424,7 +445,7 @@ class NativeServer:
                     req = self._inflight.pop(int(ids[i]))
                 req.t_finish = now
                 req.server_ns = (int(tms[3 * i]), int(tms[3 * i + 1]), int(tms[3 * i + 2]))
-                req.t_admit = req.t_arrival + (tms[3 * i + 1] - tms[3 * i]) * 1e-9
+                req.t_admit = (tms[3 * i + 1] - self._clock_off) * 1e-9
                 h = req._host
                 req._host = None
                 # the record first: a caller that sees the future done also sees it in the stats

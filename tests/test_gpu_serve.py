@@ -129,3 +129,32 @@ def test_native_server_rejects_oversize_requests(fits):
     with NativeServer({k: v[0] for k, v in fits.items()}, slots=2, mem_budget=1 << 16) as srv:
         with pytest.raises(AdmissionError):
             srv.submit(reqs[0])
+
+
+def test_native_server_release_time(fits):
+    """A request submitted ahead of its arrival is admitted no earlier; its
+    latency counts from the arrival; a late one counts its lateness."""
+    import time
+    reqs = _requests(fits, 3, seed=17)
+    with NativeServer({k: v[0] for k, v in fits.items()}, slots=2, mem_budget=8 << 30) as srv:
+        t_due = time.perf_counter() + 0.08
+        reqs[0].t_intended = t_due
+        f0 = srv.submit(reqs[0])
+        time.sleep(0.03)
+        assert not f0.done()
+        out0 = f0.result(timeout=60)
+        reqs[1].t_intended = time.perf_counter() - 0.05       # already 50 ms late
+        out1 = srv.submit(reqs[1]).result(timeout=60)
+        srv.drain()
+        recs = {r.id: r for r in srv.completed}
+        stats = srv.stats()
+    r0, r1 = recs[reqs[0].id], recs[reqs[1].id]
+    off = srv._clock_off
+    # the library's arrival time is the intended one (clocks mapped to within a millisecond)
+    assert abs((r0.server_ns[0] - off) * 1e-9 - t_due) < 1e-3
+    assert r0.server_ns[1] >= r0.server_ns[0] and r0.t_admit >= t_due - 1e-3
+    assert (r1.server_ns[2] - r1.server_ns[0]) * 1e-9 >= 0.05
+    assert stats["requests"] == 2
+    for r, out in ((reqs[0], out0), (reqs[1], out1)):
+        f, g = _alone(fits, r)
+        assert np.array_equal(out["flux"], f)

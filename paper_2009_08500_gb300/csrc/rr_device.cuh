@@ -526,6 +526,30 @@ __device__ __forceinline__ int build_list_ss1(WarpList* wl, unsigned cand, const
     return total;
 }
 
+// The same list for the adjoint, which needs neither the per-candidate sums
+// nor the sub-exposure offsets: one float4 per candidate (dh, dl, passband
+// index as int bits, gbq), 2 KB per warp instead of 3.6 KB, so that four CTAs
+// fit on an SM.
+__device__ __forceinline__ int build_list_ss1_packed(float4* wl, unsigned cand, const float (&dh)[4],
+                                                     const float (&dl)[4], const int (&pbv)[4],
+                                                     const float (&gbq)[4]) {
+    const int lane = threadIdx.x & 31;
+    const unsigned below = (1u << lane) - 1u;
+    int total = 0, before = 0;
+    #pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const unsigned bal = __ballot_sync(0xffffffffu, (cand >> q) & 1u);
+        before += __popc(bal & below);
+        total += __popc(bal);
+    }
+    #pragma unroll
+    for (int q = 0; q < 4; ++q)
+        if ((cand >> q) & 1u)
+            wl[before + __popc(cand & ((1u << q) - 1u))] = make_float4(dh[q], dl[q], __int_as_float(pbv[q]), gbq[q]);
+    __syncwarp();
+    return total;
+}
+
 // Shared-memory layout common to the FP32 per-point kernels:
 //   [mbarrier 16][reduction 64][per-pv tile constants 16 x kMaxPvTile]
 //   [passband constants][one candidate list per warp][pv records ...]
@@ -535,6 +559,9 @@ constexpr size_t kOffPb = kOffCta + 16 * kMaxPvTile;
 constexpr size_t kOffWl = kOffPb + ((sizeof(PbShared) + 15) / 16) * 16;
 constexpr size_t kWlBytes = ((sizeof(WarpList) + 15) / 16) * 16;
 constexpr size_t kOffRecs32 = kOffWl + (kBlock / 32) * kWlBytes;
+// the adjoint with one sample per time keeps only the packed list (float4 per candidate)
+constexpr size_t kWlBytesPacked = kWarpPts * sizeof(float4);
+constexpr size_t kOffRecs32Packed = kOffWl + (kBlock / 32) * kWlBytesPacked;
 
 // One sub-exposure of one (pv, time): delta = A Ib (Eq. 5 without the 1 -),
 // 0 outside the transit.  Kepler failure: bad = true, NaN.

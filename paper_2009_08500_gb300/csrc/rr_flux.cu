@@ -401,7 +401,7 @@ static size_t flux_smem(int pv_tile, int rec_bytes, bool f64, int gpc) {
     // + two constant rows (1 and NaN) for the bulk stores
     return kOffRecs32 + (size_t)pv_tile * rec_bytes + queue_bytes(pv_tile * gpc) + 2 * kWarpPts * sizeof(float);
 }
-static_assert(kOffRecs32 % 16 == 0, "shared-memory regions must stay 16-byte aligned");
+static_assert(kOffRecs32 % 16 == 0 && kOffRecs32Packed % 16 == 0, "shared-memory regions must stay 16-byte aligned");
 
 // 128-time groups per CTA of the FP32 kernels.  A function of npt only, so
 // the adjoint's summation order for a pv never depends on the other pvs in

@@ -276,7 +276,9 @@ __global__ void __launch_bounds__(kBlock, 3) rr_grad_mixed_kernel(
     extern __shared__ __align__(16) unsigned char smem[];
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
     PbShared* ps = reinterpret_cast<PbShared*>(smem + kOffPb);
-    char* recs = reinterpret_cast<char*>(smem + kOffRecs32);
+    // one sample per time: the packed candidate list (2 KB per warp) and the records after it
+    constexpr size_t kRecsOff = SS1 ? kOffRecs32Packed : kOffRecs32;
+    char* recs = reinterpret_cast<char*>(smem + kRecsOff);
     float* gacc = reinterpret_cast<float*>(recs + (size_t)pv_tile * L.head_bytes);   // [pv][group][nacc]
     float* depcols = gacc + (size_t)pv_tile * groups_per_cta * nacc;
     const ItemQueue queue = queue_at(reinterpret_cast<char*>(depcols + (DEP ? (size_t)(nacc - 6) * kBlock : 0)),
@@ -285,6 +287,7 @@ __global__ void __launch_bounds__(kBlock, 3) rr_grad_mixed_kernel(
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     WarpList* wl = reinterpret_cast<WarpList*>(smem + kOffWl + warp * kWlBytes);
+    float4* wlp = reinterpret_cast<float4*>(smem + kOffWl + warp * kWlBytesPacked);
     const int ngroups = (npt + kWarpPts - 1) / kWarpPts;
     const int gbeg = blockIdx.x * groups_per_cta;
     const int gend = min(ngroups, gbeg + groups_per_cta);
@@ -385,14 +388,13 @@ __global__ void __launch_bounds__(kBlock, 3) rr_grad_mixed_kernel(
         bool any = false, bad = false;
         if constexpr (SS1) {
             // one sample per time: the candidates are the samples
-            int bq[4];
-            const int nc = build_list_ss1(wl, cand, dh, dl, pbv, gbq, bq);
+            const int nc = build_list_ss1_packed(wlp, cand, dh, dl, pbv, gbq);
             #pragma unroll 1
             for (int e0 = 0; e0 < nc; e0 += 32) {
                 const int j = e0 + lane;
                 if (j >= nc) continue;
-                const float4 cd = wl->cand[j];
-                const int pb = wl->pb[j];
+                const float4 cd = wlp[j];
+                const int pb = __float_as_int(cd.z);
                 const Phase32 ph = precise_phase(cd.x, cd.y, c.x, c.y, H.Bh, H.Bl);
                 any |= adjoint_sample<DEP>(H, PB[pb], rows + (size_t)pb * L.rows_per_pb * L.ng_pad, L, ph.fr_h,
                                            ph.fr_l, ph.m, 0.0f, c.z, cd.w, acc, dep, 6 + (chromatic ? pb : 0),
@@ -620,8 +622,9 @@ __global__ void __launch_bounds__(kFinishThreads) rr_grad_finish_kernel(
     }
 }
 
-static size_t grad_smem(int pv_tile, const RecLayout& L, int nacc, bool dep, size_t rsize, int slots) {
-    size_t s = (rsize == 8 ? 16 + 16 * 4 + 16 * kMaxPvTile : kOffRecs32) + (size_t)pv_tile * L.head_bytes +
+static size_t grad_smem(int pv_tile, const RecLayout& L, int nacc, bool dep, size_t rsize, int slots, bool ss1) {
+    size_t s = (rsize == 8 ? 16 + 16 * 4 + 16 * kMaxPvTile : (ss1 ? kOffRecs32Packed : kOffRecs32)) +
+               (size_t)pv_tile * L.head_bytes +
                (size_t)pv_tile * slots * nacc * rsize;
     if (dep) s += (size_t)(nacc - 6) * kBlock * rsize;
     if (rsize == 4) s = ((s + 15) & ~(size_t)15) + queue_bytes(pv_tile * slots);   // FP32 kernel: item queue
@@ -667,7 +670,9 @@ cudaError_t launch_grad(rr_ctx* c, const double* times, const int32_t* pb_index,
     const size_t per_pv = (size_t)L.head_bytes + (size_t)slots * nacc * rsize;
     int pv_tile = (int)(kSmemTarget / per_pv);
     pv_tile = pv_tile < 1 ? 1 : (pv_tile > kMaxPvTile ? kMaxPvTile : pv_tile);
-    const size_t smem = grad_smem(pv_tile, L, nacc, dep, rsize, slots);
+    bool ss1 = true;
+    for (int pb = 0; pb < pbp.npb; ++pb) ss1 = ss1 && pbp.ss[pb] == 1;
+    const size_t smem = grad_smem(pv_tile, L, nacc, dep, rsize, slots, ss1);
     const char* rowsg = (const char*)records + rows_offset(L, npv);
     const int npvt = (npv + pv_tile - 1) / pv_tile;
     const int gpc = groups_per_cta(npt);
@@ -699,8 +704,6 @@ cudaError_t launch_grad(rr_ctx* c, const double* times, const int32_t* pb_index,
                                           vec_g,                                                              \
                                           pv_status, c->d_err);                                               \
     } while (0)
-        bool ss1 = true;
-        for (int pb = 0; pb < pbp.npb; ++pb) ss1 = ss1 && pbp.ss[pb] == 1;
         const int vec_g = (npt % 4 == 0) && (((uintptr_t)grad_flux & 15u) == 0);
         if (dep) {
             if (ss1) RR_LAUNCH_GRAD32((rr_grad_mixed_kernel<true, true>));

@@ -1033,9 +1033,9 @@ __global__ void __launch_bounds__(256, 4) rr_pv_setup_kernel(ModelParams mp, PbP
         #pragma unroll
         for (int c = 0; c < 4; ++c) uc[c] = c < nc ? u_s[lp][pb][c] : R(0);
         R Ic[4];   // basis disk integrals, converted once per row
-        #pragma unroll
         // (the power-2 laws have no coefficient bases: their I_star partials are formed per pv)
         const bool p2law = mp.ld_model == RR_LD_POWER2 || mp.ld_model == RR_LD_POWER2_PM;
+        #pragma unroll
         for (int c = 0; c < 4; ++c) Ic[c] = (grad && c < nc && !p2law) ? (R)istar[1 + c] : R(0);
         const int b0 = named ? 0 : pb;
         if (ik < 0) continue;   // small-planet approximation: rr_small_planet_kernel writes these rows

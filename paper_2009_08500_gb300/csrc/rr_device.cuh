@@ -685,10 +685,13 @@ __device__ __forceinline__ bool warp_may_transit(const PvHead<float>& H, float4 
 // decides for pv l of the tile whether the group's phase interval can hold a
 // transit; a ballot gives the warp the tile's mask.  Pvs outside the mask need
 // no arithmetic (flux exactly 1) and are stored at once; the others become
-// work items (pv, group) in a shared-memory queue.  Between groups, and after
-// the last one, warps claim queued items, so the output stream of some warps
-// overlaps the in-transit arithmetic of others and the in-transit work of the
-// CTA is spread over all its warps whatever groups it falls in.
+// work items (pv, group) in a shared-memory queue.  In the adjoint, warps
+// claim queued items between groups and after the last one.  In the flux
+// kernel a set of stream warps takes all the groups first while the other
+// warps evaluate the items as they appear (with supersampling every warp
+// streams first), so the output stream overlaps the in-transit arithmetic.
+// Either way the in-transit work of the CTA is spread over all its warps
+// whatever groups it falls in.
 //
 // Queue protocol: a producer reserves slots (atomicAdd on nitems), writes the
 // item, then publishes it by writing its key (slots start at -1).  Consumers

@@ -631,12 +631,15 @@ __device__ __forceinline__ void ff_sub(float ah, float al, float bh, float bl, f
     rl = e + (al - bl);
 }
 
-__device__ __forceinline__ void group_load(GroupState& gs, const GroupInfo* __restrict__ grp, int g, int g0,
-                                           const float4* cta_ph, const char* recs, int rec_bytes, int npv_t) {
+// sg: the CTA's copy in shared memory of the summaries of its groups (sg[j]
+// for group gbeg + j, copied with the records); group gbeg is the phase
+// reference of cta_phase.  Plain loads (shared memory).
+__device__ __forceinline__ void group_load(GroupState& gs, const GroupInfo* sg, int j, const float4* cta_ph,
+                                           const char* recs, int rec_bytes, int npv_t) {
     const int lane = threadIdx.x & 31;
-    const float4 s0 = __ldg(reinterpret_cast<const float4*>(grp + g));
-    const float2 tg = __ldg(reinterpret_cast<const float2*>(grp + g) + 2);
-    const float2 t0 = __ldg(reinterpret_cast<const float2*>(grp + g0) + 2);
+    const float4 s0 = *reinterpret_cast<const float4*>(sg + j);
+    const float2 tg = reinterpret_cast<const float2*>(sg + j)[2];
+    const float2 t0 = reinterpret_cast<const float2*>(sg)[2];
     gs.wlo = s0.x;
     gs.whi = s0.y;
     gs.maxdt = s0.z;

@@ -89,8 +89,11 @@ __global__ void __launch_bounds__(kBlock, 4) rr_flux_mixed_kernel(const double* 
     // constant output rows of one group (1 and NaN), sources of the bulk stores
     float* rows1 = reinterpret_cast<float*>(qbase + queue_bytes(pv_tile * groups_per_cta));
     float* rowsnan = rows1 + kWarpPts;
+    // the summaries of the CTA's groups, copied with the records
+    GroupInfo* sgrp = reinterpret_cast<GroupInfo*>(rowsnan + kWarpPts);
     const uint32_t hbytes = (uint32_t)npv_t * (uint32_t)L.head_bytes;
     const uint32_t rbytes = STAGE_ROWS ? (uint32_t)npv_t * (uint32_t)L.rows_bytes : 0u;
+    const uint32_t gbytes = (uint32_t)(gend - gbeg) * (uint32_t)sizeof(GroupInfo);
     queue_init(queue, tc, pv_tile * groups_per_cta, gbeg);
     for (int j = tid; j < kWarpPts; j += blockDim.x) {
         rows1[j] = 1.0f;
@@ -99,7 +102,8 @@ __global__ void __launch_bounds__(kBlock, 4) rr_flux_mixed_kernel(const double* 
     fence_proxy_async_smem();   // the bulk stores read these through the async proxy
     if (tid == 0) {
         mbar_init(bar, 1);
-        mbar_expect_tx(bar, hbytes + rbytes);
+        mbar_expect_tx(bar, hbytes + rbytes + gbytes);
+        bulk_g2s(sgrp, grp + gbeg, gbytes, bar);
         const char* src = records + (size_t)pv0 * L.head_bytes;
         for (uint32_t off = 0; off < hbytes; off += 65536u) {
             const uint32_t n = hbytes - off < 65536u ? hbytes - off : 65536u;
@@ -132,7 +136,7 @@ __global__ void __launch_bounds__(kBlock, 4) rr_flux_mixed_kernel(const double* 
     auto do_group = [&](int g) {
         const int p0 = g * kWarpPts + 4 * lane;
         GroupState gs;
-        group_load(gs, grp, g, gbeg, cta_ph, recs, L.head_bytes, npv_t);
+        group_load(gs, sgrp, g - gbeg, cta_ph, recs, L.head_bytes, npv_t);
         unsigned bad;
         float4 cl;
         const unsigned may = group_decide(gs, recs, L.head_bytes, npv_t, bad, cl);
@@ -403,8 +407,9 @@ __global__ void __launch_bounds__(kBlock) rr_flux_fp64_kernel(const double* __re
 
 static size_t flux_smem(int pv_tile, int rec_bytes, bool f64, int gpc) {
     if (f64) return 16 + 16 * 4 + 16 * kMaxPvTile + (size_t)pv_tile * rec_bytes;
-    // + two constant rows (1 and NaN) for the bulk stores
-    return kOffRecs32 + (size_t)pv_tile * rec_bytes + queue_bytes(pv_tile * gpc) + 2 * kWarpPts * sizeof(float);
+    // + two constant rows (1 and NaN) for the bulk stores + the group summaries
+    return kOffRecs32 + (size_t)pv_tile * rec_bytes + queue_bytes(pv_tile * gpc) + 2 * kWarpPts * sizeof(float) +
+           (size_t)gpc * sizeof(GroupInfo);
 }
 static_assert(kOffRecs32 % 16 == 0 && kOffRecs32Packed % 16 == 0, "shared-memory regions must stay 16-byte aligned");
 

@@ -281,8 +281,10 @@ __global__ void __launch_bounds__(kBlock, 3) rr_grad_mixed_kernel(
     char* recs = reinterpret_cast<char*>(smem + kRecsOff);
     float* gacc = reinterpret_cast<float*>(recs + (size_t)pv_tile * L.head_bytes);   // [pv][group][nacc]
     float* depcols = gacc + (size_t)pv_tile * groups_per_cta * nacc;
-    const ItemQueue queue = queue_at(reinterpret_cast<char*>(depcols + (DEP ? (size_t)(nacc - 6) * kBlock : 0)),
-                                     pv_tile * groups_per_cta);
+    char* qbase = reinterpret_cast<char*>(depcols + (DEP ? (size_t)(nacc - 6) * kBlock : 0));
+    const ItemQueue queue = queue_at(qbase, pv_tile * groups_per_cta);
+    // the summaries of the CTA's groups, copied with the records
+    GroupInfo* sgrp = reinterpret_cast<GroupInfo*>(qbase + queue_bytes(pv_tile * groups_per_cta));
     TileCounters* tc = reinterpret_cast<TileCounters*>(smem + kOffRed);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -294,10 +296,12 @@ __global__ void __launch_bounds__(kBlock, 3) rr_grad_mixed_kernel(
     const int pv0 = blockIdx.y * pv_tile;
     const int npv_t = min(pv_tile, npv - pv0);
     const uint32_t bytes = (uint32_t)npv_t * (uint32_t)L.head_bytes;
+    const uint32_t gbytes = (uint32_t)(gend - gbeg) * (uint32_t)sizeof(GroupInfo);
     queue_init(queue, tc, pv_tile * groups_per_cta, gbeg);
     if (tid == 0) {
         mbar_init(bar, 1);
-        mbar_expect_tx(bar, bytes);
+        mbar_expect_tx(bar, bytes + gbytes);
+        bulk_g2s(sgrp, grp + gbeg, gbytes, bar);
         const char* src = records + (size_t)pv0 * L.head_bytes;
         for (uint32_t off = 0; off < bytes; off += 65536u) {
             const uint32_t n = bytes - off < 65536u ? bytes - off : 65536u;
@@ -320,7 +324,7 @@ __global__ void __launch_bounds__(kBlock, 3) rr_grad_mixed_kernel(
     // a group: the tile's transit mask -> work items
     auto do_group = [&](int g) {
         GroupState gs;
-        group_load(gs, grp, g, gbeg, cta_ph, recs, L.head_bytes, npv_t);
+        group_load(gs, sgrp, g - gbeg, cta_ph, recs, L.head_bytes, npv_t);
         unsigned bad;
         float4 cl;
         const unsigned may = group_decide(gs, recs, L.head_bytes, npv_t, bad, cl);
@@ -627,7 +631,8 @@ static size_t grad_smem(int pv_tile, const RecLayout& L, int nacc, bool dep, siz
                (size_t)pv_tile * L.head_bytes +
                (size_t)pv_tile * slots * nacc * rsize;
     if (dep) s += (size_t)(nacc - 6) * kBlock * rsize;
-    if (rsize == 4) s = ((s + 15) & ~(size_t)15) + queue_bytes(pv_tile * slots);   // FP32 kernel: item queue
+    // FP32 kernel: item queue, then the summaries of the CTA's groups
+    if (rsize == 4) s = ((s + 15) & ~(size_t)15) + queue_bytes(pv_tile * slots) + (size_t)slots * sizeof(GroupInfo);
     return s;
 }
 

@@ -53,6 +53,8 @@ struct alignas(16) GroupInfo {
     float pad[2];
 };
 
+static_assert(sizeof(GroupInfo) % 16 == 0, "group summaries are copied with bulk asynchronous copies");
+
 // device error word values (ctx->d_err)
 constexpr int kErrBarrierTimeout = 1;
 constexpr int kErrQueueTimeout = 2;

@@ -44,7 +44,7 @@ CONFIG_TEXT = {
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch, from one ncu capture
 # of the same kernels (profiles/flux_mixed_c3_population.md, grad_mixed_c3_population.md,
 # flux_mixed_c4_heterogeneous.md); to be cleared whenever those kernels change
-TRAFFIC = {("c3", "flux"): 272_920_320, ("c3", "grad"): 38_802_688, ("c4", "flux"): 446_557_440}
+TRAFFIC = {("c3", "flux"): 272_905_216, ("c3", "grad"): 38_797_824, ("c4", "flux"): 446_751_488}
 
 
 def parse():

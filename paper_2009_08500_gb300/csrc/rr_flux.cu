@@ -1,18 +1,24 @@
 // Fused light-curve kernels: time -> phase -> z -> Eq. 5 -> mean over
 // sub-exposures, for a tile of parameter vectors x a tile of times.
 //
-// Tiling: a CTA of kBlock threads owns kPtTile consecutive times (4
-// consecutive ones per thread in the FP32 kernel, one 16-byte store per
-// thread and pv; strided by kBlock in the FP64 kernel) and `pv_tile`
-// consecutive parameter vectors.  The pv
-// records of the tile are staged into shared memory by one bulk async copy
-// (TMA engine, mbarrier completion); every thread then loops over the
-// tile's pvs, reusing its times from registers.
+// FP32 kernel.  A CTA owns a chunk of consecutive 128-time groups (4
+// consecutive times per lane of a warp) and a tile of up to 32 parameter
+// vectors (lane i of a warp speaks for pv i).  One bulk asynchronous copy
+// (TMA engine, mbarrier completion, bounded wait) stages the tile's pv
+// records and the chunk's group summaries into shared memory.  Stream warps
+// then take the groups: per group one transit test per pv, whole 512-byte
+// row segments of exactly 1 for the pvs outside their windows (bulk
+// asynchronous stores from a constant shared-memory row), and a work item
+// (pv, group) in a shared-memory queue for the others; the remaining warps
+// evaluate the items as they appear (candidate samples compacted per warp,
+// 32 at a time).  FP64 kernel: a tile of kPtTile times strided by kBlock
+// and the same pv tile, every sample in FP64.
 //
 // Mixed precision (FP32 bulk):
-//  * per time, once per call (points_group): dt = t - t_ref in FP64,
-//    kept as a float pair (dh, dl) -- t_ref is the first time of the tile;
-//  * per (CTA, pv), FP64: A = frac((t_ref - T0) / P) as a float pair;
+//  * per time, once per call (points_group): dt = t - t_g in FP64, kept as
+//    a float pair (dh, dl) -- t_g is the first time of the time's group;
+//  * per (CTA, pv), FP64: A = frac((t_ref - T0) / P) as a float pair at the
+//    CTA's first group, carried to each group in float-float;
 //  * per (pv, time): coarse phase psi = A + dh / P with one FMA, rounded
 //    with two additions (no FP64, no conversion per point).  If the
 //    whole exposure lies outside the pv's transit window the point is 1

@@ -12,10 +12,14 @@
 //     z^2 = a^2 P_x^2 + b^2 P_y^2,  P_x, P_y functions of (E, e, w)
 //     dE = (dM + sin E de) / (1 - e cos E),
 //     dM/dT0 = -n, dM/dP = -n (t - T0) / P, dM/de = dM0/de, dM/dw = dM0/dw.
-// Per-thread sums -> warp shuffles -> fixed-order sum over warps (FP64) ->
-// one partial per (pv, time tile) in the workspace -> rr_grad_reduce sums the
-// tiles in order.  The result for a pv is therefore independent of which
-// other pvs share the launch.
+// The FP32 kernel takes the flux kernel's groups and work items (every warp
+// alternates between deciding a group and evaluating an item).  Sums: per
+// lane over an item's samples -> a warp reduce-scatter in a fixed order ->
+// one slot per (pv, group) in shared memory -> per (pv, CTA chunk) in the
+// workspace -> rr_grad_finish_kernel sums the chunks in order in FP64 (and
+// applies the Kipping chain rule).  The chunking depends on npt only, so the
+// result for a pv is independent of which other pvs share the launch and of
+// which warp took which item.
 #include "rr_device.cuh"
 
 namespace rr {

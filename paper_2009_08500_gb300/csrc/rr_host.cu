@@ -29,7 +29,7 @@ cudaError_t ensure_pipe(rr_ctx* c, size_t bytes) {
     for (int i = 0; i < 3 && e == cudaSuccess; ++i)
         if (!c->pipe.s[i]) e = cudaStreamCreateWithFlags(&c->pipe.s[i], cudaStreamNonBlocking);
     for (int b = 0; b < kSlots && e == cudaSuccess; ++b)
-        for (int k = 0; k < 3 && e == cudaSuccess; ++k)
+        for (int k = 0; k < 4 && e == cudaSuccess; ++k)
             if (!c->pipe.ev[b][k]) e = cudaEventCreateWithFlags(&c->pipe.ev[b][k], cudaEventDisableTiming);
     if (e != cudaSuccess || c->pipe.bytes >= bytes) return e;
     // the previous call finished (it synchronised before returning): the old buffer is idle
@@ -47,7 +47,7 @@ void release_host_pipe(rr_ctx* c) {
     for (int i = 0; i < 3; ++i)
         if (c->pipe.s[i]) cudaStreamDestroy(c->pipe.s[i]);
     for (int b = 0; b < kSlots; ++b)
-        for (int k = 0; k < 3; ++k)
+        for (int k = 0; k < 4; ++k)
             if (c->pipe.ev[b][k]) cudaEventDestroy(c->pipe.ev[b][k]);
     if (c->pipe.buf) cudaFree(c->pipe.buf);
     c->pipe = rr_ctx::HostPipe{};
@@ -119,10 +119,25 @@ extern "C" rr_status rr_evaluate_host(rr_ctx* c, const double* times, const int3
             st = pipe_fail(c, e, "rr_evaluate_host copy-in");
             break;
         }
+        // the light curves go out as soon as the forward kernel is done (with a
+        // gradient, their copy runs beside the adjoint, which does not write them)
+        bool flux_out = false;
         if (grad) {
             st = rr_prepare(c, d_t, d_pb, npt, d_p, n, ss, exptime, d_st, d_ws, ws_bytes, s_run);
             if (st == RR_OK)
                 st = rr_evaluate_prepared(c, d_t, d_pb, npt, d_p, n, ss, exptime, d_f, d_st, d_ws, ws_bytes, s_run);
+            if (st == RR_OK && npt > 0) {
+                e = cudaEventRecord(ev[3], s_run);
+                if (e == cudaSuccess) e = cudaStreamWaitEvent(s_out, ev[3], 0);
+                if (e == cudaSuccess)
+                    e = cudaMemcpyAsync((char*)flux + (size_t)c0 * rowb, d_f, (size_t)n * rowb,
+                                        cudaMemcpyDeviceToHost, s_out);
+                if (e != cudaSuccess) {
+                    st = pipe_fail(c, e, "rr_evaluate_host copy-out");
+                    break;
+                }
+                flux_out = true;
+            }
             if (st == RR_OK)
                 st = rr_evaluate_grad_prepared(c, d_t, d_pb, npt, d_p, n, ss, exptime, d_g, d_go, d_st, d_ws, ws_bytes,
                                                s_run);
@@ -132,7 +147,7 @@ extern "C" rr_status rr_evaluate_host(rr_ctx* c, const double* times, const int3
         if (st != RR_OK) break;
         e = cudaEventRecord(ev[1], s_run);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(s_out, ev[1], 0);
-        if (e == cudaSuccess && npt > 0)
+        if (e == cudaSuccess && npt > 0 && !flux_out)
             e = cudaMemcpyAsync((char*)flux + (size_t)c0 * rowb, d_f, (size_t)n * rowb, cudaMemcpyDeviceToHost, s_out);
         if (e == cudaSuccess && pv_status)
             e = cudaMemcpyAsync(pv_status + c0, d_st, (size_t)n * 4, cudaMemcpyDeviceToHost, s_out);

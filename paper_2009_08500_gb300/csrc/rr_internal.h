@@ -215,7 +215,7 @@ struct rr_ctx {
     // streams, per-slot events, one grow-only device buffer
     struct HostPipe {
         cudaStream_t s[3] = {nullptr, nullptr, nullptr};
-        cudaEvent_t ev[3][3] = {};   // [slot][inputs copied, computed, results copied]
+        cudaEvent_t ev[3][4] = {};   // [slot][inputs copied, computed, results copied, flux computed]
         void* buf = nullptr;
         size_t bytes = 0;
     } pipe;

@@ -50,3 +50,19 @@ def test_host_pipeline_status_and_empty(rr):
     assert (st.numpy()[np.arange(9) != 4] == 0).all()
     f0, _, st0 = m.evaluate_host(wl.times, wl.params[:0], wl.pb_index, wl.supersampling, wl.exptime)
     assert f0.shape == (0, 300) and st0.shape == (0,)
+
+
+def test_default_chunking_of_a_large_batch_matches_one_device_call(rr):
+    """The default chunking (about eight chunks of at least 512 pvs) on a batch of several chunks."""
+    import torch
+    wl = W.make_small("quadratic_tri", npv=2100, npt=256, seed=29)
+    m = rr.model_for(wl)
+    t, pb, p = rr.to_device(wl)
+    ref = m.evaluate(t, p, pb, wl.supersampling, wl.exptime).cpu()
+    gbar = np.random.default_rng(7).normal(size=(wl.npv, wl.npt)).astype(np.float32)
+    gref = m.evaluate_grad(t, p, torch.as_tensor(gbar, device=t.device), pb, wl.supersampling, wl.exptime).cpu()
+    f, g, st = m.evaluate_host(wl.times, wl.params, wl.pb_index, wl.supersampling, wl.exptime, grad_flux=gbar)
+    assert torch.equal(f, ref)
+    assert torch.equal(torch.nan_to_num(g, nan=-1.0), torch.nan_to_num(gref, nan=-1.0))
+    f2, _, st2 = m.evaluate_host(wl.times, wl.params, wl.pb_index, wl.supersampling, wl.exptime)
+    assert torch.equal(f2, ref) and torch.equal(st2, st)

@@ -32,6 +32,9 @@ What each module follows (sections and equations of the paper):
                    an exact 1-D radial integral (Sect. 2, Eq. 1-2), 2-D
                    pixel integration over the stellar disk, and a 50-digit
                    mpmath intersection area.
+* ``mandel_agol`` -- the analytic quadratic-law light curve of Mandel & Agol
+                   (2002) in closed form (elliptic integrals): a second,
+                   independent route to what ``exact`` integrates.
 
 Pins (tests/test_oracle_*.py, CPU only) tie every function to something
 other than itself: closed forms, the exact integral within the paper's

@@ -81,6 +81,7 @@ void free_all(rr_ctx* c) {
     cudaFree(c->d_tab);
     cudaFree(c->d_tab_off);
     cudaFree(c->d_err);
+    cudaFree(c->d_svtab);
     cudaFree(c->d_zef);
     cudaFree(c->d_basisf);
     cudaFree(c->d_pre64);
@@ -145,8 +146,11 @@ rr_status check_eval(rr_ctx* c, const double* times, const int32_t* pb_index, in
         pbp.ss[pb] = ss[pb];
         pbp.exptime[pb] = ss[pb] > 1 ? exptime[pb] : 0.0;
         const double step = ss[pb] > 1 ? exptime[pb] / ss[pb] : 0.0;
+        const double first = ss[pb] > 1 ? -0.5 * exptime[pb] + 0.5 * step : 0.0;
         pbp.step[pb] = (float)step;
-        pbp.first[pb] = ss[pb] > 1 ? (float)(-0.5 * exptime[pb] + 0.5 * step) : 0.0f;
+        pbp.first[pb] = (float)first;
+        pbp.step_lo[pb] = (float)(step - (double)pbp.step[pb]);
+        pbp.first_lo[pb] = (float)(first - (double)pbp.first[pb]);
         pbp.inv_ss[pb] = (float)(1.0 / ss[pb]);
     }
     if (npt == 0 || npv == 0) return RR_OK;
@@ -354,6 +358,7 @@ rr_status rr_create(const rr_config* cfg, rr_ctx** out) {
     if (dalloc(&c->d_ze, c->nz + 1) || dalloc(&c->d_mu, c->nz) || dalloc(&c->d_basis, (size_t)c->nbasis * c->nz) ||
         dalloc(&c->d_istar, c->nbasis) || dalloc(&c->d_T64, nT) || dalloc(&c->d_T32, nT) || dalloc(&c->d_DT32, nT) ||
         dalloc(&c->d_tab_off, k.npb + 1) || dalloc(&c->d_err, 1) ||
+        (k.precision == RR_PREC_MIXED && dalloc(&c->d_svtab, kSvTabLen)) ||
         (k.direct && (dalloc(&c->d_zef, c->nz + 1) || dalloc(&c->d_basisf, (size_t)c->nbasis * c->nz) ||
                       dalloc(&c->d_pre64, nP) || dalloc(&c->d_pref, 2 * nP))) ||
         (p2 && (dalloc(&c->d_lnmu, c->nz) || dalloc(&c->d_lnmuf, c->nz)))) {
@@ -374,6 +379,21 @@ rr_status rr_create(const rr_config* cfg, rr_ctx** out) {
             free_all(c);
             delete c;
             return cuda_fail(nullptr, e, "upload of ln mu");
+        }
+    }
+    if (c->d_svtab) {
+        // sin x0 and 1 - cos x0 = 2 sin^2(x0 / 2) in FP64 on the host, as float pairs
+        std::vector<float4> tab(kSvTabLen);
+        for (int j = 0; j < kSvTabLen; ++j) {
+            const double x0 = (double)(j - kSvTabRes) / kSvTabRes;
+            const double S = std::sin(x0), h = std::sin(0.5 * x0), V = 2.0 * h * h;
+            const float Sh = (float)S, Vh = (float)V;
+            tab[j] = make_float4(Sh, (float)(S - (double)Sh), Vh, (float)(V - (double)Vh));
+        }
+        if ((e = cudaMemcpy(c->d_svtab, tab.data(), kSvTabLen * sizeof(float4), cudaMemcpyHostToDevice))) {
+            free_all(c);
+            delete c;
+            return cuda_fail(nullptr, e, "upload of the sine table");
         }
     }
     if ((e = cudaMemcpy(c->d_ze, c->ze.data(), (c->nz + 1) * sizeof(double), cudaMemcpyHostToDevice)) ||

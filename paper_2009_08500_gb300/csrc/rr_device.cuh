@@ -38,8 +38,11 @@ __device__ __forceinline__ double d_rcp(double x) { return 1.0 / x; }
 // of the triangle (1, k, z) built from differences, and the half-angles as
 // atan2(K, .) -- accurate near both contact points.  dA/dz = -K/z (minus the
 // common chord), dA/dk = 2 k kappa1 (planet rim inside the star).
+// The contact factors f1 = 1 + k - z (outer contact) and f3 = z - (1 - k)
+// (inner contact) are arguments: the mixed adjoint passes them from FP64 near
+// the contacts, where K ~ sqrt(f1 f3) amplifies their rounding.
 template <typename R, bool GRAD>
-__device__ __forceinline__ R covered_area(R k, R z, R& dAdz, R& dAdk) {
+__device__ __forceinline__ R covered_area_f13(R k, R z, R f1, R f3, R& dAdz, R& dAdk) {
     const R one = R(1);
     if (z <= fabs(one - k)) {
         if (GRAD) dAdz = R(0);
@@ -50,9 +53,7 @@ __device__ __forceinline__ R covered_area(R k, R z, R& dAdz, R& dAdk) {
         if (GRAD) dAdk = R(0);
         return Tr<R>::pi();
     }
-    const R f1 = (one + k) - z;
     const R f2 = z + (one - k);
-    const R f3 = z - (one - k);
     const R f4 = z + (one + k);
     R h = (f1 * f2) * (f3 * f4);
     h = h > R(0) ? h : R(0);
@@ -65,6 +66,11 @@ __device__ __forceinline__ R covered_area(R k, R z, R& dAdz, R& dAdk) {
         dAdk = R(2) * k * kap1;
     }
     return kap0 + kk * kap1 - R(0.5) * K;
+}
+
+template <typename R, bool GRAD>
+__device__ __forceinline__ R covered_area(R k, R z, R& dAdz, R& dAdk) {
+    return covered_area_f13<R, GRAD>(k, z, (R(1) + k) - z, z - (R(1) - k), dAdz, dAdk);
 }
 
 // Linear interpolation of a profile row over the g nodes g_i = i / (ng - 1):
@@ -304,6 +310,7 @@ __device__ __forceinline__ Phase32 precise_phase(float dh, float dl, float Ah, f
 
 struct Orbit32 {
     float z, Px, Py, S, V;
+    float x;            // eccentric-anomaly offset E - E0 (= dM on a circular orbit)
     bool front, ok;
 };
 
@@ -315,14 +322,17 @@ __device__ __forceinline__ Orbit32 orbit32(const PvHead<float>& H, float dM, dou
     float x;
     if (H.flags & kPvCircular) {
         half_angle_SV(dM, o.S, o.V);
+        x = dM;
     } else if (H.flags & kPvKepler64) {
         double xd, Sd, Vd;
         o.ok = kepler_offset_f64(dMd, H.ecE0d, H.esE0d, H.inv_den0d, xd, Sd, Vd);
         o.S = (float)Sd;
         o.V = (float)Vd;
+        x = (float)xd;
     } else {
         o.ok = kepler_offset_f32(dM, H.ecE0, H.esE0, H.inv_den0, H.kep2, H.kep3, H.kepC, x, o.S, o.V);
     }
+    o.x = x;
     o.Px = fmaf(H.ax1, o.V, H.ax2 * o.S);
     o.Py = H.rho0 + fmaf(H.ay1, o.V, H.ay2 * o.S);
     o.z = sqrtf(fmaf(H.a2 * o.Px, o.Px, H.b2 * o.Py * o.Py));
@@ -352,6 +362,111 @@ __device__ __forceinline__ Orbit64 orbit64(const PvHead<double>& H, double dM) {
     o.z = sqrt(fma(H.a2 * o.Px, o.Px, H.b2 * o.Py * o.Py));
     o.front = o.Py > 0.0;
     return o;
+}
+
+// ---- float-float arithmetic: a value as the unevaluated sum h + l of two
+// floats (about 48 significant bits), from the error-free transformations of
+// Knuth (two-sum), Dekker (fast two-sum) and the FMA product error.  The
+// intrinsics keep the compiler from fusing or reassociating them. ----
+struct FF {
+    float h, l;
+};
+
+// s + e == a + b exactly
+__device__ __forceinline__ FF ff_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+// s + e == a + b exactly when |a| >= |b| (or a == 0)
+__device__ __forceinline__ FF ff_fast_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ FF ff_add(FF a, FF b) {
+    const FF s = ff_two_sum(a.h, b.h);
+    return ff_fast_two_sum(s.h, __fadd_rn(s.l, __fadd_rn(a.l, b.l)));
+}
+__device__ __forceinline__ FF ff_sub(FF a, FF b) { return ff_add(a, FF{-b.h, -b.l}); }
+__device__ __forceinline__ FF ff_add_f(FF a, float b) {
+    const FF s = ff_two_sum(a.h, b);
+    return ff_fast_two_sum(s.h, __fadd_rn(s.l, a.l));
+}
+__device__ __forceinline__ FF ff_mul(FF a, FF b) {
+    const float p = __fmul_rn(a.h, b.h);
+    float e = fmaf(a.h, b.h, -p);
+    e = fmaf(a.h, b.l, e);
+    e = fmaf(a.l, b.h, e);
+    return ff_fast_two_sum(p, e);
+}
+__device__ __forceinline__ FF ff_mul_f(FF a, float b) {
+    const float p = __fmul_rn(a.h, b);
+    return ff_fast_two_sum(p, fmaf(a.l, b, fmaf(a.h, b, -p)));
+}
+__device__ __forceinline__ FF ff_ld(const float* v) { return FF{v[0], v[1]}; }
+
+// A rational constant as a float pair: hi = the nearest float, lo = the rest.
+struct FFConst {
+    float h, l;
+};
+constexpr FFConst ff_const(double v) { return FFConst{(float)v, (float)(v - (double)(float)v)}; }
+__device__ __forceinline__ FF ff_c(FFConst c) { return FF{c.h, c.l}; }
+
+// S = sin x and V = 1 - cos x as float pairs for a float |x| <= 1: x = x0 +
+// d with x0 = j / kSvTabRes the nearest table node (d exact, |d| <= 1/128),
+//   sin x = S0 (1 - Vd) + (1 - V0) Sd,  1 - cos x = V0 + (1 - V0) Vd + S0 Sd,
+// Sd = d - d^3/6 + d^5/120 and Vd = d^2/2 - d^4/24 + d^6/720 (d^2 exact as a
+// pair, the rest in FP32: below 8e-8, truncation below 2e-16).  Absolute
+// error ~1e-13.
+__device__ __forceinline__ void ff_sin_vers(float x, const float4* __restrict__ tab, FF& S, FF& V) {
+    const int j = __float2int_rn(x * (float)kSvTabRes);
+    const float4 t = __ldg(tab + j + kSvTabRes);
+    const float d = x - (float)j * (1.0f / (float)kSvTabRes);   // exact
+    const float d2 = __fmul_rn(d, d);
+    const FF Sd = ff_fast_two_sum(d, d * d2 * fmaf(d2, 1.0f / 120.0f, -1.0f / 6.0f));
+    const FF Vd = ff_add_f(FF{0.5f * d2, 0.5f * fmaf(d, d, -d2)}, d2 * d2 * fmaf(d2, 1.0f / 720.0f, -1.0f / 24.0f));
+    const FF S0{t.x, t.y}, V0{t.z, t.w};
+    const FF C0 = ff_sub(FF{1.0f, 0.0f}, V0);
+    S = ff_add(ff_sub(S0, ff_mul(S0, Vd)), ff_mul(C0, Sd));
+    V = ff_add(V0, ff_add(ff_mul(C0, Vd), ff_mul(S0, Sd)));
+}
+
+// Projected distance as a float pair for a sample near a contact point (the
+// mixed adjoint).  xc: the sample's phase from the conjunction in cycles as a
+// float pair; x32: the FP32 orbit's eccentric-anomaly offset, |x32| <= 1.
+// S and V are evaluated at x32 and turned by the Newton correction dx of the
+// float-float Kepler residual (one step: the FP32 x is within ~1e-7 relative,
+// so ~1e-14 remains; S(x + dx) = S + dx (1 - V) and V(x + dx) = V + dx S to
+// first order, dx^2 ~ 1e-15); on a circular orbit x = dM, evaluated at its
+// high part and turned by its low part.  Error of z ~1e-12.
+__device__ __forceinline__ FF contact_z_ff(const PvOrbitFF& O, const float4* __restrict__ svtab, bool circular, FF xc,
+                                          float x32) {
+    constexpr FFConst two_pi = ff_const(6.283185307179586476925);
+    const FF dM = ff_mul(ff_c(two_pi), xc);
+    const float xe = circular ? dM.h : x32;
+    FF S, V;
+    ff_sin_vers(xe, svtab, S, V);
+    float dx;
+    if (circular) {
+        dx = dM.l;
+    } else {
+        // f(x) = x - dM - ecE0 S + esE0 V, f'(x) = 1 - ecE0 (1 - V) + esE0 S
+        const FF ec = ff_ld(O.ecE0), es = ff_ld(O.esE0);
+        const FF fx = ff_sub(ff_add(ff_add_f(FF{-dM.h, -dM.l}, xe), ff_mul(es, V)), ff_mul(ec, S));
+        const float fp = fmaf(ec.h, V.h - 1.0f, 1.0f) + es.h * S.h;
+        dx = -__fdividef(fx.h + fx.l, fp);
+    }
+    const float Sh = S.h, Vh = V.h;
+    S = ff_add_f(S, dx * (1.0f - Vh));
+    V = ff_add_f(V, dx * Sh);
+    const FF Px = ff_add(ff_mul(ff_ld(O.ax1), V), ff_mul(ff_ld(O.ax2), S));
+    const FF Py = ff_add(ff_ld(O.rho0), ff_add(ff_mul(ff_ld(O.ay1), V), ff_mul(ff_ld(O.ay2), S)));
+    const FF z2 = ff_add(ff_mul(ff_ld(O.a2), ff_mul(Px, Px)), ff_mul(ff_ld(O.b2), ff_mul(Py, Py)));
+    // square root: the FP32 root and one Newton correction (z2 - zf^2) / (2 zf)
+    const float zf = sqrtf(z2.h);
+    const float p = __fmul_rn(zf, zf);
+    const float r = (__fsub_rn(z2.h, p) - fmaf(zf, zf, -p)) + z2.l;
+    return ff_fast_two_sum(zf, r * (0.5f / zf));
 }
 
 __device__ __forceinline__ float warp_max(float v) {
@@ -449,6 +564,7 @@ __device__ __forceinline__ int chunk_cand(ChunkWalk& cw, const int* soff, int nc
 struct PbShared {
     int ss[RR_MAX_PB];
     float first[RR_MAX_PB], step[RR_MAX_PB], inv_ss[RR_MAX_PB];
+    float first_lo[RR_MAX_PB], step_lo[RR_MAX_PB];   // low parts (the mixed adjoint's contact refinement)
 };
 
 __device__ __forceinline__ void stage_pb(const PbParams& pbp, PbShared* ps) {
@@ -457,6 +573,8 @@ __device__ __forceinline__ void stage_pb(const PbParams& pbp, PbShared* ps) {
         ps->first[j] = pbp.first[j];
         ps->step[j] = pbp.step[j];
         ps->inv_ss[j] = pbp.inv_ss[j];
+        ps->first_lo[j] = pbp.first_lo[j];
+        ps->step_lo[j] = pbp.step_lo[j];
     }
 }
 

@@ -33,20 +33,18 @@ struct GradAcc {
 
 // Contribution of one sub-exposure; gb = -gbar / ss.  rowblk points to
 // global memory (read through the read-only data path).
+// f1 = 1 + k - z and f3 = z - (1 - k): the contact factors of the covered
+// area; i and al: the g cell of the sample (the lower cell on a node, clamped
+// to ng - 2) and its position in the cell (both from float-float near the
+// contacts and the cell edges in the mixed adjoint).
 template <typename R, bool DEP>
 __device__ __forceinline__ void grad_sample(const PvHead<R>& H, const PvPb<R>& pbc,
-                                            const R* __restrict__ rowblk, const RecLayout& L, R z,
-                                            R Px, R Py, R S, R V, R psi_tot, R gb, GradAcc<R>& acc,
+                                            const R* __restrict__ rowblk, const RecLayout& L, R z, R f1, R f3,
+                                            int i, R al, R Px, R Py, R S, R V, R psi_tot, R gb, GradAcc<R>& acc,
                                             R* dep, int kslot, int uslot) {
     const R one = R(1);
     R dAdz, dAdk;
-    const R A = covered_area<R, true>(pbc.k, z, dAdz, dAdk);
-    const R g = z * pbc.inv1pk;
-    // g cell (lower cell on a node, clamped to ng - 2) and in-cell position
-    const R xg = g * R(L.ng - 1);
-    int i = (int)xg;
-    i = i < L.ng - 2 ? i : L.ng - 2;
-    const R al = xg - R(i);
+    const R A = covered_area_f13<R, true>(pbc.k, z, f1, f3, dAdz, dAdk);
     const R d = __ldg(rowblk + L.ng_pad + i);         // row[i+1] - row[i]
     const R Ib = __ldg(rowblk + i) + al * d;
     const R dIdg = d * R(L.ng - 1);
@@ -237,12 +235,30 @@ __device__ __forceinline__ void cta_partials_groups(const float* gacc, const cha
 
 // One sample of the FP32 adjoint: the phase fr_h + fr_l cycles from the
 // conjunction m + mg cycles after the group's epoch (mg: the pv's cycles at
-// the group start), shifted by the sub-exposure offset `off` (cycles); gb is
-// the cotangent weight.  Adds to `acc`; returns whether the sample is in
-// transit; sets `bad` on a Kepler failure.
+// the group start), shifted by the sub-exposure offset `off` (cycles; sub-
+// exposure s of passband pb); gb is the cotangent weight.  Adds to `acc`;
+// returns whether the sample is in transit; sets `bad` on a Kepler failure.
+//
+// Refinement: within kContactBand of a contact point the area's z-derivative
+// -K/z varies like sqrt(1 + k - z) (or sqrt(z - 1 + k)), so the ~1e-7 FP32
+// rounding of z moves the per-sample derivative by ~1e-7 / (2 (1 + k - z))
+// relative (5e-5 at 1e-3 from contact): the largest share of the FP32
+// adjoint's error against the FP64 chain rule.  And within kNodeBand of a
+// g-node the rounding of g can put the sample in the neighbouring cell,
+// whose slope (the derivative of the piecewise-linear profile) differs.  For
+// those samples (about 2% of in-transit samples on the population workload)
+// z, the contact factors 1 + k - z, z - (1 - k) and the g cell are recomputed
+// in float-float (contact_z_ff) from the pv's orbit block `orb` (float pairs
+// at the end of its header, in shared memory), on the FP32 pipe: FP64 issues at 1/64 of the FP32 rate
+// here, and a lane takes the branch alone.  Orbits whose near-contact
+// samples lie more than 1 rad of eccentric anomaly from conjunction
+// (a (1 - e) below about 1.2 (1 + k)) keep the FP32 values.
 template <bool DEP>
 __device__ __forceinline__ bool adjoint_sample(const PvHead<float>& H, const PvPb<float>& pbr,
-                                               const float* __restrict__ rowblk, const RecLayout& L, float fr_h,
+                                               const float* __restrict__ rowblk,
+                                               const PvOrbitFF* __restrict__ orb,
+                                               const float4* __restrict__ svtab, int pb, int s,
+                                               const PbShared* ps, const RecLayout& L, float fr_h,
                                                float fr_l, float m, float off, float mg, float gb, GradAcc<float>& acc,
                                                float* dep, int kslot, int uslot, bool& bad) {
     const PvPb<float> pbc = pbr;
@@ -264,8 +280,38 @@ __device__ __forceinline__ bool adjoint_sample(const PvHead<float>& H, const PvP
     }
     const float gz = o.z * pbc.inv1pk;
     if (!o.front || gz >= 1.0f) return false;
+    float z = o.z;
+    float f1 = (1.0f + pbc.k) - z, f3 = z - (1.0f - pbc.k);
+    float xg = gz * (float)(L.ng - 1);
+    int cell = min((int)xg, L.ng - 2);
+    float al = xg - (float)cell;
+    if (orb != nullptr && (fminf(f1, fabsf(f3)) < kContactBand || fabsf(xg - rintf(xg)) < kNodeBand) &&
+        fabsf(o.x) <= 1.0f) {
+        // the sample's phase from the conjunction (cycles) as a float pair, with the exact
+        // sub-exposure offset (first + s step) / P
+        FF xc = ff_two_sum(fr_h - r, fr_l);
+        if (ps->ss[pb] > 1) {
+            const FF step{ps->step[pb], ps->step_lo[pb]};
+            const FF od = ff_add(FF{ps->first[pb], ps->first_lo[pb]}, ff_mul_f(step, (float)s));
+            xc = ff_add(xc, ff_mul(od, FF{H.Bh, H.Bl}));
+        }
+        const FF zz = contact_z_ff(*orb, svtab, (H.flags & kPvCircular) != 0, xc, o.x);
+        const PvContactFF kc = reinterpret_cast<const PvContactFF*>(orb + 1)[pb];
+        const FF d1 = ff_sub(ff_ld(kc.opk), zz), d3 = ff_sub(zz, ff_ld(kc.omk));
+        z = zz.h;
+        f1 = d1.h + d1.l;
+        f3 = d3.h + d3.l;
+        // the g cell from g (ng - 1) = z (ng - 1) / (1 + k) as a float pair: its high part is
+        // an integer with a negative low part just below a node
+        const FF xf = ff_mul(zz, ff_ld(kc.gsc));
+        int c = (int)floorf(xf.h);
+        if (xf.h == (float)c && xf.l < 0.0f) --c;
+        cell = min(c, L.ng - 2);
+        al = (xf.h - (float)cell) + xf.l;
+    }
     const float psi_tot = ((mg + m) + r) + x;   // (t_s - T0) / P
-    grad_sample<float, DEP>(H, pbc, rowblk, L, o.z, o.Px, o.Py, o.S, o.V, psi_tot, gb, acc, dep, kslot, uslot);
+    grad_sample<float, DEP>(H, pbc, rowblk, L, z, f1, f3, cell, al, o.Px, o.Py, o.S, o.V, psi_tot, gb, acc, dep,
+                            kslot, uslot);
     return true;
 }
 
@@ -275,7 +321,7 @@ __global__ void __launch_bounds__(kBlock, 3) rr_grad_mixed_kernel(
     const GroupInfo* __restrict__ grp, int npt,
     int npv, PbParams pbp, RecLayout L, int pv_tile, int groups_per_cta, const char* __restrict__ records,
     const char* __restrict__ rowsg, const float* __restrict__ gflux, float* __restrict__ partials, int nacc,
-    int chromatic, int vec_g,
+    int chromatic, int vec_g, const float4* __restrict__ svtab,
     int32_t* __restrict__ pv_status, int* err) {
     extern __shared__ __align__(16) unsigned char smem[];
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
@@ -362,6 +408,7 @@ __global__ void __launch_bounds__(kBlock, 3) rr_grad_mixed_kernel(
         const PvHead<float>& H = *reinterpret_cast<const PvHead<float>*>(rec);
         const PvPb<float>* PB = reinterpret_cast<const PvPb<float>*>(rec + L.off_pb);
         const float* rows = reinterpret_cast<const float*>(rowsg + (size_t)(pv0 + i) * L.rows_bytes);
+        const PvOrbitFF* orb = L.orb_off >= 0 ? reinterpret_cast<const PvOrbitFF*>(rec + L.orb_off) : nullptr;
         const float* gf = gflux + (size_t)(pv0 + i) * npt + p0;
         unsigned cand = 0;
         float gbq[4], gv[4];
@@ -404,9 +451,9 @@ __global__ void __launch_bounds__(kBlock, 3) rr_grad_mixed_kernel(
                 const float4 cd = wlp[j];
                 const int pb = __float_as_int(cd.z);
                 const Phase32 ph = precise_phase(cd.x, cd.y, c.x, c.y, H.Bh, H.Bl);
-                any |= adjoint_sample<DEP>(H, PB[pb], rows + (size_t)pb * L.rows_per_pb * L.ng_pad, L, ph.fr_h,
-                                           ph.fr_l, ph.m, 0.0f, c.z, cd.w, acc, dep, 6 + (chromatic ? pb : 0),
-                                           6 + nkp + pb * L.nldc, bad);
+                any |= adjoint_sample<DEP>(H, PB[pb], rows + (size_t)pb * L.rows_per_pb * L.ng_pad, orb, svtab, pb, 0,
+                                           ps, L, ph.fr_h, ph.fr_l, ph.m, 0.0f, c.z, cd.w, acc, dep,
+                                           6 + (chromatic ? pb : 0), 6 + nkp + pb * L.nldc, bad);
             }
         } else {
             int nc, base;
@@ -419,9 +466,10 @@ __global__ void __launch_bounds__(kBlock, 3) rr_grad_mixed_kernel(
                 if (e >= ns) continue;
                 const int pb = wl->pb[j];
                 const float4 cd = wl->cand[j];
-                const float off = fmaf((float)(e - wl->soff[j]), ps->step[pb], ps->first[pb]) * H.Bh;
-                any |= adjoint_sample<DEP>(H, PB[pb], rows + (size_t)pb * L.rows_per_pb * L.ng_pad, L, cd.x, cd.y,
-                                           cd.z, off, c.z, cd.w, acc, dep, 6 + (chromatic ? pb : 0),
+                const int sub = e - wl->soff[j];
+                const float off = fmaf((float)sub, ps->step[pb], ps->first[pb]) * H.Bh;
+                any |= adjoint_sample<DEP>(H, PB[pb], rows + (size_t)pb * L.rows_per_pb * L.ng_pad, orb, svtab, pb, sub,
+                                           ps, L, cd.x, cd.y, cd.z, off, c.z, cd.w, acc, dep, 6 + (chromatic ? pb : 0),
                                            6 + nkp + pb * L.nldc, bad);
             }
         }
@@ -556,8 +604,11 @@ __global__ void __launch_bounds__(kBlock) rr_grad_fp64_kernel(
                 const double g = o.z * pbc.inv1pk;
                 if (!o.front || g >= 1.0) continue;
                 const double psi_tot = m + tr * H.invP;
-                grad_sample<double, DEP>(H, pbc, rowblk, L, o.z, o.Px, o.Py, o.S, o.V, psi_tot, gb, acc, dep,
-                                         kslot, uslot);
+                const double xg = g * (double)(L.ng - 1);
+                const int cell = min((int)xg, L.ng - 2);
+                grad_sample<double, DEP>(H, pbc, rowblk, L, o.z, (1.0 + pbc.k) - o.z, o.z - (1.0 - pbc.k), cell,
+                                         xg - (double)cell, o.Px, o.Py, o.S, o.V, psi_tot, gb, acc, dep, kslot,
+                                         uslot);
                 any = true;
             }
         }
@@ -710,7 +761,7 @@ cudaError_t launch_grad(rr_ctx* c, const double* times, const int32_t* pb_index,
                                           (const GroupInfo*)pts_grp, npt, npv, pbp,                           \
                                           L, pv_tile, gpc, (const char*)records, rowsg,                       \
                                           (const float*)grad_flux, (float*)partials, nacc, c->cfg.chromatic,  \
-                                          vec_g,                                                              \
+                                          vec_g, c->d_svtab,                                                  \
                                           pv_status, c->d_err);                                               \
     } while (0)
         const int vec_g = (npt % 4 == 0) && (((uintptr_t)grad_flux & 15u) == 0);

@@ -40,6 +40,9 @@ constexpr int kMaxNz = 4096;
 constexpr size_t kMaxSmem = 227 * 1024;   // dynamic shared memory per CTA on sm_103a
 constexpr int kMaxBasis = RR_MAX_PB + 4;  // profile bases: 1 + nldc (named) or npb (tabulated)
 constexpr double kESwitch = 0.8;          // above this eccentricity Kepler is solved in FP64
+constexpr float kContactBand = 5e-3f;     // mixed adjoint: samples with min(1 + k - z, |z - (1 - k)|) below
+                                          // this get z and the contact factors in float-float (adjoint_sample)
+constexpr float kNodeBand = 1e-4f;        // ... and so do samples within this of a g-node (in units of cells)
 constexpr int kWarpPts = 4 * 32;          // times per group: one warp, 4 consecutive times per lane
 
 // Per 128-time group, written once per call by points_group (mixed form):
@@ -104,6 +107,30 @@ struct PointsArgs {
     GroupInfo* grp;
 };
 
+// Orbit constants of a pv as float pairs (hi + lo of the FP64 value) for the
+// mixed adjoint's contact refinement (mixed form, adjoint layout only): a
+// block at the end of the pv's header (staged into shared memory with it),
+// followed by one PvContactFF per passband.
+// Read only for the few samples within kContactBand of a contact point, where
+// the derivative of the covered area behaves like sqrt(1 + k - z) and the FP32
+// rounding of z (~1e-7) would reach the gradient with a large factor (see
+// adjoint_sample).
+struct alignas(16) PvOrbitFF {
+    float ax1[2], ax2[2], ay1[2], ay2[2];   // P_x = ax1 V + ax2 S, P_y = rho0 + ay1 V + ay2 S (as in PvHead)
+    float rho0[2], a2[2], b2[2];            // z^2 = a2 P_x^2 + b2 P_y^2
+    float ecE0[2], esE0[2];                 // Kepler: x - ecE0 S + esE0 V = dM
+    float pad[2];
+};
+struct alignas(16) PvContactFF {
+    float opk[2], omk[2];                   // 1 + k and 1 - k of the passband's radius ratio
+    float gsc[2], pad[2];                   // (ng - 1) / (1 + k): g-node coordinate per unit of z
+};
+
+// Table of sin x0 and 1 - cos x0 (float pairs: S hi, S lo, V hi, V lo) at
+// x0 = j / kSvTabRes, j = -kSvTabRes .. kSvTabRes (the float-float sine of the
+// mixed adjoint's contact refinement).
+constexpr int kSvTabRes = 64;
+constexpr int kSvTabLen = 2 * kSvTabRes + 1;
 // Per-pv records live in two regions of the workspace: the headers (PvHead +
 // one PvPb per passband; staged into shared memory by the kernels) and the
 // profile rows (read through the cache hierarchy where a transit needs them).
@@ -112,6 +139,7 @@ struct RecLayout {
     int32_t nldc, off_pb;                  // byte offset of the PvPb array in a header
     int32_t head_bytes, rows_bytes;        // per-pv strides of the two regions (multiples of 16)
     int32_t kbar_slot;                     // adjoint accumulator of the shared weights' mean k, else -1
+    int32_t orb_off;                       // byte offset of the PvOrbitFF block in a header, else -1
 };
 
 template <typename R>
@@ -123,7 +151,13 @@ inline RecLayout make_layout(int npb, int ng, int nldc, bool grad) {
     L.nldc = nldc;
     L.rows_per_pb = grad ? 3 + nldc : 1;
     L.off_pb = (int32_t)sizeof(PvHead<R>);
-    L.head_bytes = (int32_t)(((size_t)L.off_pb + npb * sizeof(PvPb<R>) + 15) & ~(size_t)15);
+    size_t head = ((size_t)L.off_pb + npb * sizeof(PvPb<R>) + 15) & ~(size_t)15;
+    L.orb_off = -1;
+    if (grad && sizeof(R) == sizeof(float)) {
+        L.orb_off = (int32_t)head;
+        head += sizeof(PvOrbitFF) + (size_t)npb * sizeof(PvContactFF);
+    }
+    L.head_bytes = (int32_t)head;
     L.rows_bytes = (int32_t)(((size_t)npb * L.rows_per_pb * L.ng_pad * sizeof(R) + 15) & ~(size_t)15);
     L.kbar_slot = -1;
     return L;
@@ -144,6 +178,8 @@ struct PbParams {
     float first[RR_MAX_PB];     // offset of sub-sample s = first + s * step [days]
     float step[RR_MAX_PB];
     float inv_ss[RR_MAX_PB];
+    float first_lo[RR_MAX_PB];  // FP64 first and step minus their floats (first + first_lo, step + step_lo)
+    float step_lo[RR_MAX_PB];
 };
 
 // Model constants for the kernels (by value).
@@ -190,6 +226,7 @@ struct rr_ctx {
     double* d_tab = nullptr;     // tabulated profiles, concatenated (mu then I per passband)
     int* d_tab_off = nullptr;    // npb + 1 offsets (in nodes)
     int* d_err = nullptr;        // device error word
+    float4* d_svtab = nullptr;   // kSvTabLen entries (mixed form): sin and 1 - cos as float pairs
     // direct model: FP32 copies of the edges and profiles, and per basis the
     // running sums P[b][m] = sum_{j<m} pi (ze[j+1]^2 - ze[j]^2) l_b[j]
     float* d_zef = nullptr;      // nz + 1

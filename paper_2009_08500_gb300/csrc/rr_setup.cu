@@ -1002,6 +1002,45 @@ __global__ void __launch_bounds__(256, 4) rr_pv_setup_kernel(ModelParams mp, PbP
     }
     }   // warp 0
 
+    if (warp == 1 && L.orb_off >= 0 && lane < nloc) {
+        // the orbit constants and radius ratios of the mixed adjoint's contact refinement as
+        // float pairs (FP64 arithmetic: here, beside warp 0's orbit and window work, rather than
+        // on its path; pvs that (2a) finds invalid get values that are never read)
+        const int pv = pv0 + lane;
+        const double* row = params + (size_t)pv * mp.nparam;
+        const double ad = row[2], bd = row[3], ed = row[4], wd = row[5];
+        double swd, cwd;
+        sincos(wd, &swd, &cwd);
+        const double sed = sqrt(fmax(1.0 - ed * ed, 0.0));
+        const double qd = 1.0 / (1.0 + ed * swd);
+        const double cE0d = (ed + swd) * qd, sE0d = sed * cwd * qd, den0d = (1.0 - ed * ed) * qd;
+        char* blk = records + (size_t)pv * L.head_bytes + L.orb_off;
+        PvOrbitFF* O = reinterpret_cast<PvOrbitFF*>(blk);
+        auto split = [](float* d, double v) {
+            d[0] = (float)v;
+            d[1] = (float)(v - (double)d[0]);
+        };
+        const bool circ = ed == 0.0;
+        split(O->ax1, circ ? 0.0 : -cwd * cE0d + swd * sed * sE0d);
+        split(O->ax2, circ ? -1.0 : -cwd * sE0d - swd * sed * cE0d);
+        split(O->ay1, circ ? -1.0 : -swd * cE0d - cwd * sed * sE0d);
+        split(O->ay2, circ ? 0.0 : -swd * sE0d + cwd * sed * cE0d);
+        split(O->rho0, circ ? 1.0 : den0d);
+        split(O->a2, ad * ad);
+        split(O->b2, bd * bd);
+        split(O->ecE0, ed * cE0d);
+        split(O->esE0, ed * sE0d);
+        O->pad[0] = O->pad[1] = 0.0f;
+        PvContactFF* C = reinterpret_cast<PvContactFF*>(O + 1);
+        for (int pb = 0; pb < mp.npb; ++pb) {
+            const double k = row[6 + (mp.chromatic ? pb : 0)];
+            split(C[pb].opk, 1.0 + k);
+            split(C[pb].omk, 1.0 - k);
+            split(C[pb].gsc, (double)(mp.ng - 1) / (1.0 + k));
+            C[pb].pad[0] = C[pb].pad[1] = 0.0f;
+        }
+    }
+
     // (3) profile rows of all pvs of the CTA: the k-interpolated combination of
     // the basis projections times 1 / I_star (arithmetic in R)
     const size_t kstride = (size_t)mp.ng;

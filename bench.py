@@ -1,11 +1,18 @@
 #!/usr/bin/env python
 """Throughput benchmark of the GB300 RoadRunner light-curve path.
 
-One step = one pass of the hot path over one batch: rr_evaluate (per-pv
-set-up, fused flux + supersample kernel) and, for the population workload,
-rr_evaluate_grad (adjoint with all 9 parameters).  Inputs are resident in
-HBM; L2 is flushed (a 256 MiB write) before every timed step, and every step
-is timed with CUDA events on the launching stream.
+Headline (default): the heterogeneous time series of Sect. 4.2 -- 2,048
+parameter vectors x 60,000 mixed-cadence times in 8 passbands with
+tabulated profiles and supersampling 1/10/30 (1.43e9 samples per step), the
+largest single-GPU workload.  One step = rr_evaluate (per-pv set-up, the
+per-time preparation, the fused flux + supersample kernel).  Beside it, as
+sub-records of the same JSON line: the population workload (4,096 pvs x
+20,000 times, one step = a shared set-up, the light curves and the adjoint
+w.r.t. 9 parameters), with its rooflines and model variants, and the
+serving workload (Poisson requests from 64 fits; points/s, p50/p99
+latency).  Inputs are resident in HBM; L2 is flushed (a 256 MiB write)
+before every timed step, and every step is timed with CUDA events on the
+launching stream.
 
 Metric: light-curve points/s = npv x npt x supersamples per step / step time,
 summed over ranks (each rank evaluates its own batch: weak scaling).
@@ -47,14 +54,71 @@ CONFIG_TEXT = {
 TRAFFIC = {("c4", "flux"): 446_751_488}
 
 
+# Algorithmic FP32 operations (add, multiply, fused multiply-add: one each) and MUFU operations
+# (reciprocal, reciprocal square root) per unit of work, counted from the kernel source with every
+# per-pv or per-passband subexpression (1 + k, k^2, 2 pi k, ...) left out as loop-invariant; a
+# square root or a quotient counts as 1 MUFU + 1 FP32 (its least form).  The units are the
+# counters of the kernels' counting form (rr_count_read):
+#   phase      precise_phase: the float-float phase of a candidate time                 15
+#   sample     sub-exposure offset, reduction to the nearest conjunction, dM           7
+#   orbit      P_x, P_y, z^2, square root, g                                            11 + 1 MUFU
+#   kepler     start of the FP32 solve (series inversion)                              4
+#   newton     one Newton step (S, V series, f, f', quotient, rotation, stop test)       26 + 1 MUFU
+#   circ       S and V series of a circular orbit                                      13
+#   transit    forward: the g-lerp of the profile row and the product (a planet wholly
+#              on the disk has the constant area pi k^2)                               5
+#   lens       forward, on the limb: Heron factors, square root, two upper-half-plane
+#              arctangents (quotient + degree-8 polynomial each), the lens sum         39 + 3 MUFU
+#   transit_adj  adjoint: the lerps, the area and orbit partials, 9 accumulations      98 + 2 MUFU
+#   lens_adj   adjoint on the limb: the lens and its z- and k-derivatives              40 + 4 MUFU
+#   refined    float-float z, contact factors and g cell (contact_z_ff)                340 + 3 MUFU
+FP32_OPS = {"phase": 15, "sample": 7, "orbit": 11, "kepler": 4, "newton": 26, "circ": 13, "transit": 5,
+            "lens": 39, "transit_adj": 98, "lens_adj": 40, "refined": 340}
+MUFU_OPS = {"orbit": 1, "newton": 1, "lens": 3, "transit_adj": 2, "lens_adj": 4, "refined": 3}
+FP32_LANES_PER_SM, MUFU_LANES_PER_SM = 128, 16
+
+
+def alu_ops(kind, c):
+    """(FP32 ops, MUFU ops) of one launch from its sample counts (rr_count_read)."""
+    ecc = c["orbit"] - c["circular"]
+    f = (FP32_OPS["phase"] * c["cand"] + FP32_OPS["sample"] * c["samples"] + FP32_OPS["orbit"] * c["orbit"] +
+         FP32_OPS["kepler"] * ecc + FP32_OPS["newton"] * c["newton"] + FP32_OPS["circ"] * c["circular"])
+    m = MUFU_OPS["orbit"] * c["orbit"] + MUFU_OPS["newton"] * c["newton"]
+    if kind == "flux":
+        f += FP32_OPS["transit"] * c["transit"] + FP32_OPS["lens"] * c["lens"]
+        m += MUFU_OPS["lens"] * c["lens"]
+    else:
+        f += (FP32_OPS["transit_adj"] * c["transit"] + FP32_OPS["lens_adj"] * c["lens"] +
+              FP32_OPS["refined"] * c["refined"])
+        m += (MUFU_OPS["transit_adj"] * c["transit"] + MUFU_OPS["lens_adj"] * c["lens"] +
+              MUFU_OPS["refined"] * c["refined"])
+    return f, m
+
+
+def alu_peaks(dev):
+    """FP32 and MUFU operations/s of the GPU: SMs x lanes per SM x the measured maximum SM clock."""
+    import torch
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz, kind = 2070.0, "fallback 2,070 MHz"
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            mhz, kind = float(json.load(fh)["sm_max_mhz"]), "measured sm_max_mhz"
+    except (OSError, KeyError, ValueError):
+        pass
+    src = f"derived: {sms} SMs x {{}} lanes per SM x {mhz:.0f} MHz ({kind})"
+    return (sms * FP32_LANES_PER_SM * mhz * 1e6, src.format(FP32_LANES_PER_SM),
+            sms * MUFU_LANES_PER_SM * mhz * 1e6, src.format(MUFU_LANES_PER_SM))
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["c1", "c2", "c3", "c4", "c5", "ts", "accuracy"], default="c3")
+    ap.add_argument("--workload", choices=["c1", "c2", "c3", "c4", "c5", "ts", "accuracy"], default="c4")
     ap.add_argument("--serve-seconds", type=float, default=3.0)
+    ap.add_argument("--no-sub", action="store_true", help="headline only (no population / serving sub-records)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64-form", action="store_true")
@@ -196,7 +260,8 @@ class OraclePool:
         kind = "forward + adjoint" if with_grad(self.name) else "forward"
         return {"value": pts / wall, "unit": "points/s", "cores": min(self.cores, len(jobs)), "kind": "oracle",
                 "sample": f"{done} of {npv} pvs x {self.wl.npt} times ({kind}); "
-                          f"{min(self.cores, len(jobs))} processes, <= {budget_s:.2g} s of work each"}
+                          f"{min(self.cores, len(jobs))} processes, <= {budget_s:.2g} s of work each",
+                "points": pts, "wall_s": wall}
 
     def close(self):
         self.pool.close()
@@ -207,32 +272,32 @@ def oracle_rate(name, budget_s=8.0):
     """Points/s of the FP64 oracle on all host cores (a bounded sample of the workload)."""
     op = OraclePool(name)
     try:
-        return op.rate(budget_s)
+        r = op.rate(budget_s)
     finally:
         op.close()
+    return {k: v for k, v in r.items() if k not in ("points", "wall_s")}
 
 
 # ----------------------------------------------------------------- ours
-def run_ours(a):
-    import numpy as np
+def config_for(name, wl, world):
+    """The `config` object of a workload's line (the same in both arms)."""
+    pts = wl.npv * wl.samples_per_pv()
+    return {"workload": f"{name}: {CONFIG_TEXT[name]}", "npv": wl.npv, "npt": wl.npt,
+            "supersamples_per_pv": wl.samples_per_pv(), "global_batch": world * pts,
+            "precision": wl.precision, "parallelism": f"replicas x{world} (pv batches, no collective)",
+            "l2": "flushed (256 MiB write) before every timed step"}
+
+
+def measure(a, name, steps, world, local, dev, flush):
+    """Time `steps` steps of a workload (CUDA events on the launching stream, L2 flushed before
+    each), then the same steps with per-kernel events; returns the numbers of its line."""
     import torch
 
     from paper_2009_08500_gb300 import rr
-
-    rank, world, local = dist_env()
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    cpu_base = None
-    if rank == 0 and world == 1 and not a.no_cpu_baseline:
-        cpu_base = oracle_rate(a.workload)     # spawned before any GPU work
-
-    wl = make_workload(a.workload)
+    wl = make_workload(name)
     model = rr.model_for(wl, device=local)
     t, pb, p = rr.to_device(wl, local)
-    grad = with_grad(a.workload)
+    grad = with_grad(name)
     flux = torch.empty((wl.npv, wl.npt), dtype=model.dtype, device=dev)
     ws_f = model.workspace(wl.npv, wl.npt, False)
     if grad:
@@ -240,7 +305,6 @@ def run_ours(a):
         gbar = torch.randn((wl.npv, wl.npt), dtype=model.dtype, device=dev,
                            generator=torch.Generator(device=dev).manual_seed(1234))
         gout = torch.empty((wl.npv, model.nparam), dtype=torch.float64, device=dev)
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     ss, ex = wl.supersampling, wl.exptime
 
     def step():
@@ -255,9 +319,6 @@ def run_ours(a):
     for _ in range(max(a.warmup, 3)):
         step()
     torch.cuda.synchronize()
-    clocks = ClockSampler(local)
-    clocks.start()
-    time.sleep(0.1)
     n_launch0 = model.launch_count
 
     def timed_steps(k):
@@ -274,30 +335,24 @@ def run_ours(a):
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    t0 = time.time()
-    step_ms = timed_steps(a.steps)
+    step_ms = timed_steps(steps)
     if world > 1:
         torch.distributed.barrier()
-    t1 = time.time()
     launches = model.launch_count - n_launch0
     # the same K steps again with CUDA events around every kernel launch (per-kernel
-    # durations for the roofline; the events themselves lengthen these steps a little)
+    # durations for the rooflines; the events themselves lengthen these steps a little)
     model.profile(True)
     model.profile_read(reset=True)
-    prof_ms = timed_steps(a.steps)
+    prof_ms = timed_steps(steps)
     kprof = model.profile_read(reset=True)
     model.profile(False)
-    clk = clocks.stop(t0, t1)
     tot_ms = sum(step_ms)
     if world > 1:
         tt = torch.tensor([tot_ms], dtype=torch.float64, device=dev)
         torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
         tot_ms = float(tt.item())
-    ms_per_step = tot_ms / a.steps
+    ms_per_step = tot_ms / steps
     pts = wl.npv * wl.samples_per_pv()
-    value = world * pts / (ms_per_step * 1e-3)
-
-    # roofline (HBM) of the dominant kernel and of the flux kernel: algorithmic bytes per launch
     esize = 8 if model.dtype == torch.float64 else 4
     peak, peak_kind = measured_peak_hbm()
 
@@ -309,25 +364,99 @@ def run_ours(a):
         return {"kernel": f"rr_{kind}_{'fp64' if esize == 8 else 'mixed'}_kernel", "bound": "hbm",
                 "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
                 "peak_source": f"{peak_kind} hbm_gbs (copy bandwidth)", "algorithmic_bytes_per_launch": int(alg),
-                "avg_launch_ms": round(kavg, 5), "traffic": TRAFFIC.get((a.workload, kind))}
+                "avg_launch_ms": round(kavg, 5), "traffic": TRAFFIC.get((name, kind))}
 
     names = ["flux", "grad"] if grad else ["flux"]
-    dom = max(names, key=lambda k: kprof[k][0])
-    roof = roofline(dom)
-    roof_flux = roofline("flux")
+    # one more step in the kernels' counting form (not timed): the work units of a launch
+    counts = {}
+    if esize == 4:
+        model.count_samples(True)
+        step()
+        model.count_samples(False)
+        counts = {k: model.count_read(k) for k in names}
+        model.count_read("flux", reset=True)
+    fp32_peak, fp32_src, mufu_peak, mufu_src = alu_peaks(dev)
+
+    def roofline_alu(kind):
+        kms, kn = kprof[kind]
+        kavg = kms / max(kn, 1)
+        f, mu = alu_ops(kind, counts[kind])
+        af, am = f / (kavg * 1e-3), mu / (kavg * 1e-3)
+        fp32 = {"achieved": round(af / 1e9, 1), "peak": round(fp32_peak / 1e9, 1), "frac": round(af / fp32_peak, 4),
+                "ops_per_launch": int(f), "peak_source": fp32_src}
+        mufu = {"achieved": round(am / 1e9, 1), "peak": round(mufu_peak / 1e9, 1), "frac": round(am / mufu_peak, 4),
+                "ops_per_launch": int(mu), "peak_source": mufu_src}
+        top = fp32 if fp32["frac"] >= mufu["frac"] else mufu
+        return {"kernel": f"rr_{kind}_mixed_kernel", "bound": "alu", "pipe": "fp32" if top is fp32 else "mufu",
+                "achieved": top["achieved"], "peak": top["peak"], "unit": "Gop/s", "frac": top["frac"],
+                "fp32": fp32, "mufu": mufu, "units_per_launch": counts[kind], "avg_launch_ms": round(kavg, 5),
+                "ops": "algorithmic operations per unit counted from the kernel source (bench.FP32_OPS, MUFU_OPS)",
+                "traffic": TRAFFIC.get((name, kind))}
+
     kernels = {k: {"ms_per_launch": round(v[0] / max(v[1], 1), 5), "launches": v[1]} for k, v in kprof.items() if v[1]}
     # share of outputs with any in-transit sample (out-of-transit points cost no arithmetic)
     model.evaluate(t, p, pb, ss, ex, out=flux, workspace=ws_f)
     in_transit = float((flux != 1).float().mean().item())
+    srt = sorted(step_ms)
+    out = {"name": name, "wl": wl, "model": model, "grad": grad, "pts": pts, "esize": esize,
+           "value": world * pts / (ms_per_step * 1e-3), "ms_per_step": ms_per_step, "steps": steps,
+           "latency_ms": {"p50": srt[len(srt) // 2], "p99": srt[min(len(srt) - 1, int(0.99 * len(srt)))]},
+           "ms_per_step_with_kernel_events": sum(prof_ms) / len(prof_ms),
+           "points_per_s_without_supersamples": world * wl.npv * wl.npt / (ms_per_step * 1e-3),
+           "in_transit_fraction": in_transit, "kernels": kernels, "gpu_launches": launches,
+           "rooflines_hbm": {k: roofline(k) for k in names},
+           "rooflines_alu": {k: roofline_alu(k) for k in names} if counts else {},
+           "dominant": max(names, key=lambda k: kprof[k][0])}
+    # the dominant kernel's binding roofline: the resource whose minimum time is the larger share
+    hb = out["rooflines_hbm"][out["dominant"]]
+    al = out["rooflines_alu"].get(out["dominant"])
+    out["roofline"] = al if (al is not None and al["frac"] > hb["frac"]) else hb
+    del flux, ws_f, t, pb, p
+    if grad:
+        del ws_g, gbar, gout
+    return out
+
+
+def sub_record(a, m, world, local, dev, flush):
+    """A workload measured beside the headline, with its rooflines, the FP64 form and variants."""
+    rec = {"value": m["value"], "unit": "points/s", "ms_per_step": m["ms_per_step"], "steps": m["steps"],
+           "config": config_for(m["name"], m["wl"], world), "latency_ms": m["latency_ms"],
+           "in_transit_fraction": m["in_transit_fraction"], "kernels": m["kernels"],
+           "roofline": m["roofline"], "rooflines_hbm": m["rooflines_hbm"], "rooflines_alu": m["rooflines_alu"],
+           "gpu_launches": m["gpu_launches"]}
+    return rec
+
+
+def run_ours(a):
+    import torch
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    cpu_base = None
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        cpu_base = oracle_rate(a.workload)     # spawned before any GPU work
+
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.1)
+    t0 = time.time()
+    m = measure(a, a.workload, a.steps, world, local, dev, flush)
+    t1 = time.time()
+    wl, model, grad, esize = m["wl"], m["model"], m["grad"], m["esize"]
+    value = m["value"]
     fp64 = None
     if not a.no_fp64_form and esize == 4:
         fp64 = run_fp64_form(a, wl, grad, local, dev, flush)
-    direct = per_pb = None
-    if not a.no_direct and esize == 4 and not wl.direct:
+    direct = per_pb = small = None
+    if not a.no_direct and esize == 4 and not wl.direct and a.workload == "c3":
         direct = run_variant(a, wl, grad, local, dev, flush, direct=True)
     if wl.shared_weights:
         per_pb = run_variant(a, wl, grad, local, dev, flush, shared_weights=False)
-    small = None
     if not a.no_direct and esize == 4 and a.workload == "c3":
         # small-planet approximation below k = 0.05 (about a fifth of the population's pvs)
         small = run_variant(a, wl, grad, local, dev, flush, k_small=0.05)
@@ -340,28 +469,48 @@ def run_ours(a):
             tt = torch.tensor([e2e["_ms"]], dtype=torch.float64, device=dev)
             torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
             e2e["_ms"] = float(tt.item())
-        e2e["value"] = world * pts / (e2e.pop("_ms") * 1e-3)
+        e2e["value"] = world * m["pts"] / (e2e.pop("_ms") * 1e-3)
 
-    srt = sorted(step_ms)
+    # beside the headline (one GPU): the population workload (forward + adjoint, its rooflines,
+    # its FP64 form and model variants) and the serving workload
+    subs = {}
+    if world == 1 and a.workload == "c4" and not a.no_sub:
+        m3 = measure(a, "c3", a.steps, world, local, dev, flush)
+        c3 = sub_record(a, m3, world, local, dev, flush)
+        if not a.no_fp64_form:
+            f3 = run_fp64_form(a, m3["wl"], True, local, dev, flush)
+            c3["fp64_form"] = dict(f3, speedup_of_mixed=m3["value"] / f3["value"])
+        if not a.no_direct:
+            c3["direct_model"] = run_variant(a, m3["wl"], True, local, dev, flush, direct=True)
+            sp = run_variant(a, m3["wl"], True, local, dev, flush, k_small=0.05)
+            sp["pvs_below_threshold"] = int((m3["wl"].params[:, 6] < 0.05).sum())
+            c3["small_planet"] = sp
+        subs["c3"] = c3
+        del m3
+        torch.cuda.empty_cache()
+        subs["c5"] = serving(a, local, min(a.serve_seconds, 2.0))
+    clk = clocks.stop(t0, t1)
+    if clk is not None:
+        clk["window"] = "the whole run after the oracle's baseline: warm-up, timed steps and sub-records (50 ms sampling)"
+
     line = {
         "metric": METRIC, "value": value, "unit": "points/s", "n_gpus": world, "steps": a.steps,
-        "warmup": max(a.warmup, 3), "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "warmup": max(a.warmup, 3), "ms_per_step": m["ms_per_step"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64" if esize == 4 else "f64", "data": "synthetic (seeded; paper-shaped)",
-        "config": {"workload": f"{a.workload}: {CONFIG_TEXT[a.workload]}", "npv": wl.npv, "npt": wl.npt,
-                   "supersamples_per_pv": wl.samples_per_pv(), "global_batch": world * pts,
-                   "precision": wl.precision, "parallelism": f"replicas x{world} (pv batches, no collective)",
-                   "l2": "flushed (256 MiB write) before every timed step"},
-        "latency_ms": {"p50": srt[len(srt) // 2], "p99": srt[min(len(srt) - 1, int(0.99 * len(srt)))]},
-        "ms_per_step_with_kernel_events": sum(prof_ms) / len(prof_ms),
-        "points_per_s_without_supersamples": world * wl.npv * wl.npt / (ms_per_step * 1e-3),
-        "in_transit_fraction": in_transit,
-        "roofline": roof, "roofline_flux": roof_flux, "kernels": kernels, "cpu_baseline": cpu_base,
+        "config": config_for(a.workload, wl, world),
+        "latency_ms": m["latency_ms"],
+        "ms_per_step_with_kernel_events": m["ms_per_step_with_kernel_events"],
+        "points_per_s_without_supersamples": m["points_per_s_without_supersamples"],
+        "in_transit_fraction": m["in_transit_fraction"],
+        "roofline": m["roofline"], "rooflines_hbm": m["rooflines_hbm"], "rooflines_alu": m["rooflines_alu"],
+        "kernels": m["kernels"], "cpu_baseline": cpu_base,
         "fp64_form": None if fp64 is None else dict(fp64, speedup_of_mixed=value / world / fp64["value"]),
         "direct_model": direct,
         "per_passband_weights": per_pb,
         "small_planet": small,
-        "e2e": e2e, "clocks": clk, "gpu_launches": launches,
+        "e2e": e2e, "clocks": clk, "gpu_launches": m["gpu_launches"],
     }
+    line.update(subs)
     if rank == 0:
         print(json.dumps(line))
     if world > 1:
@@ -531,7 +680,10 @@ def run_e2e(a, model, wl, grad, dev):
 
 # ----------------------------------------------------------------- reference arm
 def run_reference(a):
-    """The FP64 CPU oracle as it stands, on the host cores, same workload and metric."""
+    """The FP64 CPU oracle as it stands, on the host cores: the same workload, metric and config.
+    Every step evaluates a bounded sample of the workload's parameter vectors (all cores, a few
+    seconds at most); ms_per_step is the measured wall time of a step and value = points done /
+    wall time, so that the whole run ends within a few minutes."""
     rank, world, _ = dist_env()
     if rank != 0:
         return
@@ -543,26 +695,41 @@ def run_reference(a):
         steps = [op.rate(budget) for _ in range(a.steps)]
     finally:
         op.close()
-    vals = [r["value"] for r in steps]
-    value = statistics.median(vals)
+    done = sum(r["points"] for r in steps)
+    wall = sum(r["wall_s"] for r in steps)
+    value = done / wall
     wl = op.wl
-    pts = wl.npv * wl.samples_per_pv()
-    cb = dict(steps[-1])
+    cb = {k: v for k, v in steps[-1].items() if k not in ("points", "wall_s")}
     cb["value"] = value
-    cb["sample"] = f"per step: {cb['sample']}; value = median over {a.steps} steps"
+    cb["sample"] = f"per step: {cb['sample']}; value = points done / wall time over {a.steps} steps"
+    config = config_for(a.workload, wl, world)     # the GPU arm's config; the oracle computes in FP64 (dtype)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "points/s", "n_gpus": world,
-            "steps": a.steps, "warmup": a.warmup, "ms_per_step": pts / value * 1e3, "higher_is_better": True,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": wall / a.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded; paper-shaped)",
-            "config": {"workload": f"{a.workload}: {CONFIG_TEXT[a.workload]}", "npv": wl.npv, "npt": wl.npt,
-                       "supersamples_per_pv": wl.samples_per_pv(), "precision": "fp64 (CPU oracle)"},
-            "cpu_baseline": cb,
+            "config": config, "cpu_baseline": cb,
             "e2e": {"value": value, "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
 
 # ----------------------------------------------------------------- serving (C5)
 def run_serving(a):
-    """Closed-loop capacity, then Poisson streams at 0.7x (three runs) and 1.1x of it."""
+    """The serving workload as a line of its own."""
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    rec = serving(a, local, a.serve_seconds)
+    line = {"metric": METRIC, "value": rec["value"], "unit": "points/s", "n_gpus": world, "steps": None,
+            "warmup": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+            "data": "synthetic (seeded; paper-shaped)"}
+    line.update({k: v for k, v in rec.items() if k != "value"})
+    if rank == 0:
+        print(json.dumps(line))
+
+
+def serving(a, local, seconds):
+    """Closed-loop capacity, then Poisson streams at 0.7x (three runs) and 1.1x of it, through the
+    library's server; returns the record (value = served points/s at 0.7x, the run with the
+    median p99)."""
     import gc
 
     import numpy as np
@@ -572,8 +739,6 @@ def run_serving(a):
     from paper_2009_08500_gb300 import workloads as W
     from paper_2009_08500_gb300.serve import NativeServer, ServeRequest
 
-    rank, world, local = dist_env()
-    torch.cuda.set_device(local)
     fits = W.make_c5_fits()
     models = {}
     for i, f in enumerate(fits):
@@ -617,9 +782,9 @@ def run_serving(a):
         for k in range(len(pool)):
             srv.submit(mk(k))
         srv.drain()
-    # capacity: keep 2 x slots requests outstanding for serve_seconds
+    # capacity: keep 2 x slots requests outstanding for `seconds`
     with server() as srv:
-        t_end = time.perf_counter() + a.serve_seconds
+        t_end = time.perf_counter() + seconds
         k = 0
         outstanding = []
         while time.perf_counter() < t_end:
@@ -631,10 +796,11 @@ def run_serving(a):
         srv.drain()
         closed = srv.stats()
     mean_pts = float(np.mean([ServeRequest(**p).points for p in pool]))
+    npool = len(pool)
     runs = []
     for load in (0.7, 0.7, 0.7, 1.1):
         rate = load * closed["points_per_s"] / mean_pts
-        arr = np.cumsum(rng.exponential(1.0 / rate, size=int(rate * a.serve_seconds) + 1))
+        arr = np.cumsum(rng.exponential(1.0 / rate, size=int(rate * seconds) + 1))
         with server() as srv:
             # each request goes in up to `ahead` seconds before its arrival time and the
             # library releases it then: the client's own jitter does not bunch arrivals
@@ -655,23 +821,22 @@ def run_serving(a):
     gc.unfreeze()
     at07 = sorted([r for r in runs if r["load"] == 0.7], key=lambda r: r["latency_p99_ms"])
     head = at07[len(at07) // 2]          # the run with the median p99
-    line = {"metric": METRIC, "value": head["points_per_s"], "unit": "points/s", "n_gpus": world,
-            "steps": None, "warmup": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32+f64", "data": "synthetic (seeded; paper-shaped)",
+    del pool, gbuf, models
+    gc.collect()
+    torch.cuda.empty_cache()
+    return {"value": head["points_per_s"], "unit": "points/s",
             "config": {"workload": f"c5: {CONFIG_TEXT['c5']}", "fits": len(fits), "slots": slots,
                        "server": "rr_server (scheduler thread in the library)",
-                       "request_pool": len(pool), "mean_points_per_request": mean_pts,
+                       "request_pool": npool, "mean_points_per_request": mean_pts,
                        "client": "Python open-loop generator: Poisson arrival times, each request submitted up to "
                                  "20 ms ahead and released by the library at its arrival time",
-                       "serve_seconds": a.serve_seconds},
+                       "serve_seconds": seconds},
             "capacity_closed_loop": closed,
             "latency_ms": {"p50": head["latency_p50_ms"], "p99": head["latency_p99_ms"],
                            "clock": head["latency_clock"], "client_p50": head["client_latency_p50_ms"],
                            "client_p99": head["client_latency_p99_ms"],
                            "runs": "open loop at 0.7x of capacity, three runs; the one with the median p99"},
             "open_loop": runs}
-    if rank == 0:
-        print(json.dumps(line))
 
 
 def run_accuracy(a):

@@ -455,6 +455,38 @@ int64_t rr_launch_count(const rr_ctx* ctx);
 rr_status rr_profile(rr_ctx* ctx, int32_t enable);
 rr_status rr_profile_read(rr_ctx* ctx, int32_t kind, double* total_ms, int64_t* count, int32_t reset);
 
+/* Sample counts (measurement aid; the paper has no counterpart): while
+ * enabled, the mixed-precision flux and adjoint kernels run in a counting form
+ * (same results) that adds the work of every sample into per-kind counters:
+ *   RR_COUNT_TIMES     candidate times (times whose exposure can overlap a
+ *                      transit window): the float-float phase
+ *   RR_COUNT_SAMPLES   their exposure sub-samples: offset and window test
+ *   RR_COUNT_ORBIT     of those, samples inside the window: the orbit
+ *   RR_COUNT_CIRCULAR  of the orbits, circular ones (no Kepler solve)
+ *   RR_COUNT_NEWTON    Newton iterations of the FP32 Kepler solves
+ *   RR_COUNT_TRANSIT   samples in transit: covered area and profile lookup
+ *                      (the adjoint: with every partial derivative)
+ *   RR_COUNT_LENS      of those, samples on the stellar limb (ingress and
+ *                      egress: the lens area with its square root and two
+ *                      arctangents; the others have the planet's whole area)
+ *   RR_COUNT_REFINED   adjoint samples recomputed in float-float near a
+ *                      contact point or a g-node
+ * rr_count_read copies the counters of kernel kind RR_KERNEL_FLUX or
+ * RR_KERNEL_GRAD into counts[RR_COUNT_KINDS] (synchronising the device) and
+ * optionally resets all of them.  The counting form is slower: time the
+ * kernels with counting off.  Errors: RR_EINVAL, RR_ENOMEM, RR_ECUDA. */
+#define RR_COUNT_TIMES 0
+#define RR_COUNT_SAMPLES 1
+#define RR_COUNT_ORBIT 2
+#define RR_COUNT_CIRCULAR 3
+#define RR_COUNT_NEWTON 4
+#define RR_COUNT_TRANSIT 5
+#define RR_COUNT_REFINED 6
+#define RR_COUNT_LENS 7
+#define RR_COUNT_KINDS 8
+rr_status rr_count_samples(rr_ctx* ctx, int32_t enable);
+rr_status rr_count_read(rr_ctx* ctx, int32_t kind, int64_t* counts, int32_t reset);
+
 #ifdef __cplusplus
 }
 #endif

@@ -82,6 +82,7 @@ void free_all(rr_ctx* c) {
     cudaFree(c->d_tab_off);
     cudaFree(c->d_err);
     cudaFree(c->d_svtab);
+    cudaFree(c->d_counts);
     cudaFree(c->d_zef);
     cudaFree(c->d_basisf);
     cudaFree(c->d_pre64);
@@ -609,6 +610,36 @@ rr_status rr_selftest_wait(rr_ctx* c, int32_t which, void* stream) {
 const char* rr_last_error(const rr_ctx* c) { return c ? c->err.c_str() : g_create_err.c_str(); }
 
 int64_t rr_launch_count(const rr_ctx* c) { return c ? c->launches : 0; }
+
+rr_status rr_count_samples(rr_ctx* c, int32_t enable) {
+    if (!c) return fail(nullptr, RR_EINVAL, "null context");
+    cudaSetDevice(c->cfg.device);
+    if (enable && !c->d_counts) {
+        const size_t n = (size_t)RR_KERNEL_KINDS * RR_COUNT_KINDS;
+        cudaError_t e = cudaMalloc((void**)&c->d_counts, n * sizeof(unsigned long long));
+        if (e != cudaSuccess) return cuda_fail(c, e, "allocation of the sample counters");
+        if ((e = cudaMemset(c->d_counts, 0, n * sizeof(unsigned long long))) != cudaSuccess)
+            return cuda_fail(c, e, "clearing the sample counters");
+    }
+    c->counting = enable != 0;
+    return RR_OK;
+}
+
+rr_status rr_count_read(rr_ctx* c, int32_t kind, int64_t* counts, int32_t reset) {
+    if (!c || !counts) return fail(c, RR_EINVAL, "null argument");
+    if (kind != RR_KERNEL_FLUX && kind != RR_KERNEL_GRAD) return fail(c, RR_EINVAL, "counted kinds: flux, grad");
+    for (int j = 0; j < RR_COUNT_KINDS; ++j) counts[j] = 0;
+    if (!c->d_counts) return RR_OK;
+    cudaSetDevice(c->cfg.device);
+    unsigned long long h[(size_t)RR_KERNEL_KINDS * RR_COUNT_KINDS];
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(h, c->d_counts, sizeof h, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e, "reading the sample counters");
+    for (int j = 0; j < RR_COUNT_KINDS; ++j) counts[j] = (int64_t)h[(size_t)kind * RR_COUNT_KINDS + j];
+    if (reset && (e = cudaMemset(c->d_counts, 0, sizeof h)) != cudaSuccess)
+        return cuda_fail(c, e, "clearing the sample counters");
+    return RR_OK;
+}
 
 rr_status rr_profile(rr_ctx* c, int32_t enable) {
     if (!c) return fail(nullptr, RR_EINVAL, "null context");

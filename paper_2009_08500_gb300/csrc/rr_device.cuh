@@ -18,9 +18,40 @@ template <> struct Tr<double> {
     static __device__ __forceinline__ double two_pi() { return 2.0 * CUDART_PI; }
 };
 
+// Angle of the point (x, y), y >= 0, in [0, pi] (atan2 for the upper half
+// plane): folded onto t = min(y, |x|) / max(y, |x|) in [0, 1], where
+// atan(t) = t P(t^2) with P(u) = 1 + c1 u + ... + c8 u^8.  The coefficients
+// minimise the largest relative error over [0, 1] (1.67e-8 in exact
+// arithmetic): Lawson's iteration (least squares on 2,000 Chebyshev nodes,
+// each weight multiplied by its node's error every round, which converges to
+// the minimax polynomial), in FP64, rounded to FP32 -- a CPU test repeats the
+// fit and compares.  Evaluated in FP32 the result is within 1.4 ulp of atan,
+// 4 ulp with the fast quotient.  Then atan = pi/2 - atan(1/t) above the
+// diagonal and pi - angle for x < 0.
+__device__ __forceinline__ float atan2_upper(float y, float x) {
+    const float ax = fabsf(x);
+    const float mx = fmaxf(y, ax), mn = fminf(y, ax);
+    const float t = mx > 1e-30f ? __fdividef(mn, mx) : 0.0f;
+    const float u = t * t;
+    float p = 2.920693019e-03f;
+    p = fmaf(p, u, -1.636793092e-02f);
+    p = fmaf(p, u, 4.321186617e-02f);
+    p = fmaf(p, u, -7.552214712e-02f);
+    p = fmaf(p, u, 1.066600457e-01f);
+    p = fmaf(p, u, -1.421105564e-01f);
+    p = fmaf(p, u, 1.999377310e-01f);
+    p = fmaf(p, u, -3.333315253e-01f);
+    p = fmaf(p, u, 1.0f);
+    float a = t * p;
+    if (y > ax) a = CUDART_PIO2_F - a;
+    if (x < 0.0f) a = CUDART_PI_F - a;
+    return a;
+}
+
 __device__ __forceinline__ float d_sqrt(float x) { return sqrtf(x); }
 __device__ __forceinline__ double d_sqrt(double x) { return sqrt(x); }
-__device__ __forceinline__ float d_atan2(float y, float x) { return atan2f(y, x); }
+// the covered area's half-angles: the upper-half-plane arctangent (y = K >= 0)
+__device__ __forceinline__ float d_atan2(float y, float x) { return atan2_upper(y, x); }
 __device__ __forceinline__ double d_atan2(double y, double x) { return atan2(y, x); }
 __device__ __forceinline__ void d_sincos(float x, float* s, float* c) { sincosf(x, s, c); }
 __device__ __forceinline__ void d_sincos(double x, double* s, double* c) { sincos(x, s, c); }
@@ -120,7 +151,7 @@ __device__ __forceinline__ void half_angle_SV(float x, float& S, float& V) {
 // by a first-order rotation, whose error dx^2 / 2 is below the same bound.
 // On return S = sin x, V = 1 - cos x.  Returns false if not converged.
 __device__ __forceinline__ bool kepler_offset_f32(float dM, float ecE0, float esE0, float inv_den0, float kep2,
-                                                  float kep3, float kepC, float& x, float& S, float& V) {
+                                                  float kep3, float kepC, float& x, float& S, float& V, int& iters) {
     const float y = dM * inv_den0;
     x = fmaf(fmaf(kep3, y, kep2), y * y, y);
     #pragma unroll 1
@@ -133,6 +164,7 @@ __device__ __forceinline__ bool kepler_offset_f32(float dM, float ecE0, float es
         const float S_old = S;
         S -= dx * (1.0f - V);
         V -= dx * S_old;
+        iters = it + 1;
         if (kepC * dx * dx <= 1.5e-8f * fabsf(x) + 1e-37f) return true;
     }
     return false;
@@ -315,10 +347,12 @@ struct Orbit32 {
 };
 
 // Projected distance from the mean-anomaly offset dM = M - M0 (radians).
-// dMd: the same offset in FP64, used when e > kESwitch.
-__device__ __forceinline__ Orbit32 orbit32(const PvHead<float>& H, float dM, double dMd) {
+// dMd: the same offset in FP64, used when e > kESwitch.  iters: the Newton
+// iterations of the FP32 Kepler solve (0 otherwise).
+__device__ __forceinline__ Orbit32 orbit32(const PvHead<float>& H, float dM, double dMd, int& iters) {
     Orbit32 o;
     o.ok = true;
+    iters = 0;
     float x;
     if (H.flags & kPvCircular) {
         half_angle_SV(dM, o.S, o.V);
@@ -330,7 +364,7 @@ __device__ __forceinline__ Orbit32 orbit32(const PvHead<float>& H, float dM, dou
         o.V = (float)Vd;
         x = (float)xd;
     } else {
-        o.ok = kepler_offset_f32(dM, H.ecE0, H.esE0, H.inv_den0, H.kep2, H.kep3, H.kepC, x, o.S, o.V);
+        o.ok = kepler_offset_f32(dM, H.ecE0, H.esE0, H.inv_den0, H.kep2, H.kep3, H.kepC, x, o.S, o.V, iters);
     }
     o.x = x;
     o.Px = fmaf(H.ax1, o.V, H.ax2 * o.S);
@@ -681,10 +715,28 @@ constexpr size_t kOffRecs32 = kOffWl + (kBlock / 32) * kWlBytes;
 constexpr size_t kWlBytesPacked = kWarpPts * sizeof(float4);
 constexpr size_t kOffRecs32Packed = kOffWl + (kBlock / 32) * kWlBytesPacked;
 
+// Per-thread sample counts of the counting form of the FP32 kernels (indices
+// RR_COUNT_*); added into the context's counters when the kernel ends.
+struct Tally {
+    unsigned n[RR_COUNT_KINDS];
+};
+
+__device__ __forceinline__ void tally_flush(const Tally& t, unsigned long long* counts) {
+    #pragma unroll
+    for (int j = 0; j < RR_COUNT_KINDS; ++j) {
+        const unsigned v = __reduce_add_sync(0xffffffffu, t.n[j]);
+        if ((threadIdx.x & 31) == 0 && v) atomicAdd(counts + j, (unsigned long long)v);
+    }
+}
+
 // One sub-exposure of one (pv, time): delta = A Ib (Eq. 5 without the 1 -),
-// 0 outside the transit.  Kepler failure: bad = true, NaN.
+// 0 outside the transit.  Kepler failure: bad = true, NaN.  COUNT: add the
+// sample's work to `tl`.
+template <bool COUNT = false>
 __device__ __forceinline__ float delta32(const PvHead<float>& H, const PvPb<float>& pbc, const float* __restrict__ row,
-                                         int ng, float fr_h, float fr_l, int s, float first, float step, bool& bad) {
+                                         int ng, float fr_h, float fr_l, int s, float first, float step, bool& bad,
+                                         Tally* tl = nullptr) {
+    if (COUNT) ++tl->n[RR_COUNT_SAMPLES];
     const float off = fmaf((float)s, step, first) * H.Bh;   // sub-exposure offset, cycles
     float x = (fr_h + off) + fr_l;
     x -= round_nearest(x);
@@ -696,13 +748,23 @@ __device__ __forceinline__ float delta32(const PvHead<float>& H, const PvPb<floa
         xd -= rint(xd);
         dMd = 6.283185307179586476925 * xd;
     }
-    const Orbit32 o = orbit32(H, dM, dMd);
+    int iters;
+    const Orbit32 o = orbit32(H, dM, dMd, iters);
+    if (COUNT) {
+        ++tl->n[RR_COUNT_ORBIT];
+        if (H.flags & kPvCircular) ++tl->n[RR_COUNT_CIRCULAR];
+        tl->n[RR_COUNT_NEWTON] += iters;
+    }
     if (!o.ok) {
         bad = true;
         return __int_as_float(0x7fc00000);
     }
     const float g = o.z * pbc.inv1pk;
     if (!o.front || g >= 1.0f) return 0.0f;
+    if (COUNT) {
+        ++tl->n[RR_COUNT_TRANSIT];
+        if (o.z > fabsf(1.0f - pbc.k)) ++tl->n[RR_COUNT_LENS];
+    }
     float d0, d1, sl;
     int cell;
     const float A = covered_area<float, false>(pbc.k, o.z, d0, d1);

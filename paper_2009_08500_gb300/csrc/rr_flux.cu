@@ -63,7 +63,7 @@ __device__ __forceinline__ void store4(float* out, const float (&f)[4], const in
     }
 }
 
-template <bool STAGE_ROWS, bool SS1>
+template <bool STAGE_ROWS, bool SS1, bool COUNT>
 __global__ void __launch_bounds__(kBlock, 4) rr_flux_mixed_kernel(const double* __restrict__ times,
                                                                const float2* __restrict__ pdt,
                                                                const int32_t* __restrict__ ppb,
@@ -74,7 +74,8 @@ __global__ void __launch_bounds__(kBlock, 4) rr_flux_mixed_kernel(const double* 
                                                                const char* __restrict__ rowsg,
                                                                float* __restrict__ flux,
                                                                int32_t* __restrict__ pv_status, int vec_store,
-                                                               int stream_warps, int* err) {
+                                                               int stream_warps, unsigned long long* counts,
+                                                               int* err) {
     extern __shared__ __align__(16) unsigned char smem[];
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
     PbShared* ps = reinterpret_cast<PbShared*>(smem + kOffPb);
@@ -136,6 +137,7 @@ __global__ void __launch_bounds__(kBlock, 4) rr_flux_mixed_kernel(const double* 
     const float nanf_ = __int_as_float(0x7fc00000);
     const float zero4[4] = {0.f, 0.f, 0.f, 0.f};
     const uint64_t l2_pol = l2_evict_first_policy();
+    Tally tl{};   // the counting form's per-thread sample counts
 
     // a group: the tile's transit mask; every pv outside it is 1 (NaN for an
     // invalid pv or passband index) without arithmetic, the others are queued
@@ -215,8 +217,9 @@ __global__ void __launch_bounds__(kBlock, 4) rr_flux_mixed_kernel(const double* 
                     const int pb = wl->pb[j];
                     const float4 cd = wl->cand[j];
                     const Phase32 ph = precise_phase(cd.x, cd.y, c.x, c.y, H.Bh, H.Bl);
-                    wl->pacc[j] = delta32(H, PB[pb], rows + (size_t)pb * L.rows_per_pb * L.ng_pad, L.ng, ph.fr_h,
-                                          ph.fr_l, 0, 0.0f, 0.0f, bad);
+                    if (COUNT) ++tl.n[RR_COUNT_TIMES];
+                    wl->pacc[j] = delta32<COUNT>(H, PB[pb], rows + (size_t)pb * L.rows_per_pb * L.ng_pad, L.ng,
+                                                 ph.fr_h, ph.fr_l, 0, 0.0f, 0.0f, bad, &tl);
                 }
             }
             __syncwarp();
@@ -228,6 +231,7 @@ __global__ void __launch_bounds__(kBlock, 4) rr_flux_mixed_kernel(const double* 
         } else if (__any_sync(0xffffffffu, cand != 0)) {
             int nc, base;
             const int ns = build_list(wl, cand, dh, dl, pbv, zero4, c.x, c.y, H.Bh, H.Bl, ps, nc, base);
+            if (COUNT && lane == 0) tl.n[RR_COUNT_TIMES] += nc;
             ChunkWalk cw{0};
             #pragma unroll 1
             for (int e0 = 0; e0 < ns; e0 += 32) {
@@ -239,8 +243,8 @@ __global__ void __launch_bounds__(kBlock, 4) rr_flux_mixed_kernel(const double* 
                 if (valid) {
                     const int pb = wl->pb[j];
                     const float4 cd = wl->cand[j];
-                    d = delta32(H, PB[pb], rows + (size_t)pb * L.rows_per_pb * L.ng_pad, L.ng, cd.x, cd.y,
-                                e - wl->soff[j], ps->first[pb], ps->step[pb], bad);
+                    d = delta32<COUNT>(H, PB[pb], rows + (size_t)pb * L.rows_per_pb * L.ng_pad, L.ng, cd.x, cd.y,
+                                       e - wl->soff[j], ps->first[pb], ps->step[pb], bad, &tl);
                 }
                 if (ns == nc) {
                     // one sample per candidate: nothing to sum
@@ -318,6 +322,7 @@ __global__ void __launch_bounds__(kBlock, 4) rr_flux_mixed_kernel(const double* 
         }
         __nanosleep(64);
     }
+    if (COUNT) tally_flush(tl, counts);
     bulk_wait_all();   // the bulk stores read shared memory that ends with the CTA
 }
 
@@ -504,15 +509,24 @@ cudaError_t launch_flux(rr_ctx* c, const double* times, const int32_t* pb_index,
     } else {
         bool ss1 = true;
         for (int pb = 0; pb < pbp.npb; ++pb) ss1 = ss1 && pbp.ss[pb] == 1;
-        auto kern = stage_rows ? (ss1 ? rr_flux_mixed_kernel<true, true> : rr_flux_mixed_kernel<true, false>)
-                               : (ss1 ? rr_flux_mixed_kernel<false, true> : rr_flux_mixed_kernel<false, false>);
+        auto kern = c->counting
+                        ? (stage_rows ? (ss1 ? rr_flux_mixed_kernel<true, true, true>
+                                             : rr_flux_mixed_kernel<true, false, true>)
+                                      : (ss1 ? rr_flux_mixed_kernel<false, true, true>
+                                             : rr_flux_mixed_kernel<false, false, true>))
+                        : (stage_rows ? (ss1 ? rr_flux_mixed_kernel<true, true, false>
+                                             : rr_flux_mixed_kernel<true, false, false>)
+                                      : (ss1 ? rr_flux_mixed_kernel<false, true, false>
+                                             : rr_flux_mixed_kernel<false, false, false>));
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         const int vec = (npt % 4 == 0) && (((uintptr_t)flux & 15u) == 0);
         kern<<<grid, kBlock, smem, s>>>(times, (const float2*)pts_dt, (const int32_t*)pts_pb,
                                         (const GroupInfo*)pts_grp, npt, npv, pbp, L,
                                         pv_tile, gpc, (const char*)records, rowsg, (float*)flux, pv_status, vec,
-                                        ss1 ? kStreamWarpsSS1 : (kBlock >> 5), c->d_err);
+                                        ss1 ? kStreamWarpsSS1 : (kBlock >> 5),
+                                        c->d_counts ? c->d_counts + (size_t)RR_KERNEL_FLUX * RR_COUNT_KINDS : nullptr,
+                                        c->d_err);
     }
     c->launches++;
     return cudaGetLastError();

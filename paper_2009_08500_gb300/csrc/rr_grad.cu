@@ -253,14 +253,15 @@ __device__ __forceinline__ void cta_partials_groups(const float* gacc, const cha
 // here, and a lane takes the branch alone.  Orbits whose near-contact
 // samples lie more than 1 rad of eccentric anomaly from conjunction
 // (a (1 - e) below about 1.2 (1 + k)) keep the FP32 values.
-template <bool DEP>
+template <bool DEP, bool COUNT>
 __device__ __forceinline__ bool adjoint_sample(const PvHead<float>& H, const PvPb<float>& pbr,
                                                const float* __restrict__ rowblk,
                                                const PvOrbitFF* __restrict__ orb,
                                                const float4* __restrict__ svtab, int pb, int s,
                                                const PbShared* ps, const RecLayout& L, float fr_h,
                                                float fr_l, float m, float off, float mg, float gb, GradAcc<float>& acc,
-                                               float* dep, int kslot, int uslot, bool& bad) {
+                                               float* dep, int kslot, int uslot, bool& bad, Tally& tl) {
+    if (COUNT) ++tl.n[RR_COUNT_SAMPLES];
     const PvPb<float> pbc = pbr;
     const float xr = (fr_h + off) + fr_l;
     const float r = round_nearest(xr);
@@ -273,13 +274,20 @@ __device__ __forceinline__ bool adjoint_sample(const PvHead<float>& H, const PvP
         xd -= rint(xd);
         dMd = 6.283185307179586476925 * xd;
     }
-    const Orbit32 o = orbit32(H, dM, dMd);
+    int iters;
+    const Orbit32 o = orbit32(H, dM, dMd, iters);
+    if (COUNT) {
+        ++tl.n[RR_COUNT_ORBIT];
+        if (H.flags & kPvCircular) ++tl.n[RR_COUNT_CIRCULAR];
+        tl.n[RR_COUNT_NEWTON] += iters;
+    }
     if (!o.ok) {
         bad = true;
         return false;
     }
     const float gz = o.z * pbc.inv1pk;
     if (!o.front || gz >= 1.0f) return false;
+    if (COUNT) ++tl.n[RR_COUNT_TRANSIT];
     float z = o.z;
     float f1 = (1.0f + pbc.k) - z, f3 = z - (1.0f - pbc.k);
     float xg = gz * (float)(L.ng - 1);
@@ -287,6 +295,7 @@ __device__ __forceinline__ bool adjoint_sample(const PvHead<float>& H, const PvP
     float al = xg - (float)cell;
     if (orb != nullptr && (fminf(f1, fabsf(f3)) < kContactBand || fabsf(xg - rintf(xg)) < kNodeBand) &&
         fabsf(o.x) <= 1.0f) {
+        if (COUNT) ++tl.n[RR_COUNT_REFINED];
         // the sample's phase from the conjunction (cycles) as a float pair, with the exact
         // sub-exposure offset (first + s step) / P
         FF xc = ff_two_sum(fr_h - r, fr_l);
@@ -309,19 +318,20 @@ __device__ __forceinline__ bool adjoint_sample(const PvHead<float>& H, const PvP
         cell = min(c, L.ng - 2);
         al = (xf.h - (float)cell) + xf.l;
     }
+    if (COUNT && z > fabsf(1.0f - pbc.k)) ++tl.n[RR_COUNT_LENS];
     const float psi_tot = ((mg + m) + r) + x;   // (t_s - T0) / P
     grad_sample<float, DEP>(H, pbc, rowblk, L, z, f1, f3, cell, al, o.Px, o.Py, o.S, o.V, psi_tot, gb, acc, dep,
                             kslot, uslot);
     return true;
 }
 
-template <bool DEP, bool SS1>
+template <bool DEP, bool SS1, bool COUNT>
 __global__ void __launch_bounds__(kBlock, 3) rr_grad_mixed_kernel(
     const double* __restrict__ times, const float2* __restrict__ pdt, const int32_t* __restrict__ ppb,
     const GroupInfo* __restrict__ grp, int npt,
     int npv, PbParams pbp, RecLayout L, int pv_tile, int groups_per_cta, const char* __restrict__ records,
     const char* __restrict__ rowsg, const float* __restrict__ gflux, float* __restrict__ partials, int nacc,
-    int chromatic, int vec_g, const float4* __restrict__ svtab,
+    int chromatic, int vec_g, const float4* __restrict__ svtab, unsigned long long* counts,
     int32_t* __restrict__ pv_status, int* err) {
     extern __shared__ __align__(16) unsigned char smem[];
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
@@ -397,6 +407,7 @@ __global__ void __launch_bounds__(kBlock, 3) rr_grad_mixed_kernel(
     // depend on which warp took which item
     const int nkp = chromatic ? L.npb : 1;
     float* dep = DEP ? depcols + tid : nullptr;
+    Tally tl{};   // the counting form's per-thread sample counts
     auto do_item = [&](int it, int key) {
         const float4 c = queue.c[it];
         const int g = key >> 5, i = key & 31;
@@ -451,13 +462,15 @@ __global__ void __launch_bounds__(kBlock, 3) rr_grad_mixed_kernel(
                 const float4 cd = wlp[j];
                 const int pb = __float_as_int(cd.z);
                 const Phase32 ph = precise_phase(cd.x, cd.y, c.x, c.y, H.Bh, H.Bl);
-                any |= adjoint_sample<DEP>(H, PB[pb], rows + (size_t)pb * L.rows_per_pb * L.ng_pad, orb, svtab, pb, 0,
+                if (COUNT) ++tl.n[RR_COUNT_TIMES];
+                any |= adjoint_sample<DEP, COUNT>(H, PB[pb], rows + (size_t)pb * L.rows_per_pb * L.ng_pad, orb, svtab, pb, 0,
                                            ps, L, ph.fr_h, ph.fr_l, ph.m, 0.0f, c.z, cd.w, acc, dep,
-                                           6 + (chromatic ? pb : 0), 6 + nkp + pb * L.nldc, bad);
+                                           6 + (chromatic ? pb : 0), 6 + nkp + pb * L.nldc, bad, tl);
             }
         } else {
             int nc, base;
             const int ns = build_list(wl, cand, dh, dl, pbv, gbq, c.x, c.y, H.Bh, H.Bl, ps, nc, base);
+            if (COUNT && lane == 0) tl.n[RR_COUNT_TIMES] += nc;
             ChunkWalk cw{0};
             #pragma unroll 1
             for (int e0 = 0; e0 < ns; e0 += 32) {
@@ -468,9 +481,9 @@ __global__ void __launch_bounds__(kBlock, 3) rr_grad_mixed_kernel(
                 const float4 cd = wl->cand[j];
                 const int sub = e - wl->soff[j];
                 const float off = fmaf((float)sub, ps->step[pb], ps->first[pb]) * H.Bh;
-                any |= adjoint_sample<DEP>(H, PB[pb], rows + (size_t)pb * L.rows_per_pb * L.ng_pad, orb, svtab, pb, sub,
+                any |= adjoint_sample<DEP, COUNT>(H, PB[pb], rows + (size_t)pb * L.rows_per_pb * L.ng_pad, orb, svtab, pb, sub,
                                            ps, L, cd.x, cd.y, cd.z, off, c.z, cd.w, acc, dep, 6 + (chromatic ? pb : 0),
-                                           6 + nkp + pb * L.nldc, bad);
+                                           6 + nkp + pb * L.nldc, bad, tl);
             }
         }
         __syncwarp();
@@ -523,6 +536,7 @@ __global__ void __launch_bounds__(kBlock, 3) rr_grad_mixed_kernel(
         }
         __nanosleep(64);
     }
+    if (COUNT) tally_flush(tl, counts);
     cta_partials_groups(gacc, recs, L.head_bytes, npv_t, nacc, groups_per_cta, pv0, blockIdx.x, gridDim.x,
                         partials);
 }
@@ -761,16 +775,25 @@ cudaError_t launch_grad(rr_ctx* c, const double* times, const int32_t* pb_index,
                                           (const GroupInfo*)pts_grp, npt, npv, pbp,                           \
                                           L, pv_tile, gpc, (const char*)records, rowsg,                       \
                                           (const float*)grad_flux, (float*)partials, nacc, c->cfg.chromatic,  \
-                                          vec_g, c->d_svtab,                                                  \
+                                          vec_g, c->d_svtab, counts,                                          \
                                           pv_status, c->d_err);                                               \
     } while (0)
         const int vec_g = (npt % 4 == 0) && (((uintptr_t)grad_flux & 15u) == 0);
-        if (dep) {
-            if (ss1) RR_LAUNCH_GRAD32((rr_grad_mixed_kernel<true, true>));
-            else RR_LAUNCH_GRAD32((rr_grad_mixed_kernel<true, false>));
+        unsigned long long* counts = c->d_counts ? c->d_counts + (size_t)RR_KERNEL_GRAD * RR_COUNT_KINDS : nullptr;
+        if (c->counting) {
+            if (dep) {
+                if (ss1) RR_LAUNCH_GRAD32((rr_grad_mixed_kernel<true, true, true>));
+                else RR_LAUNCH_GRAD32((rr_grad_mixed_kernel<true, false, true>));
+            } else {
+                if (ss1) RR_LAUNCH_GRAD32((rr_grad_mixed_kernel<false, true, true>));
+                else RR_LAUNCH_GRAD32((rr_grad_mixed_kernel<false, false, true>));
+            }
+        } else if (dep) {
+            if (ss1) RR_LAUNCH_GRAD32((rr_grad_mixed_kernel<true, true, false>));
+            else RR_LAUNCH_GRAD32((rr_grad_mixed_kernel<true, false, false>));
         } else {
-            if (ss1) RR_LAUNCH_GRAD32((rr_grad_mixed_kernel<false, true>));
-            else RR_LAUNCH_GRAD32((rr_grad_mixed_kernel<false, false>));
+            if (ss1) RR_LAUNCH_GRAD32((rr_grad_mixed_kernel<false, true, false>));
+            else RR_LAUNCH_GRAD32((rr_grad_mixed_kernel<false, false, false>));
         }
 #undef RR_LAUNCH_GRAD32
     }

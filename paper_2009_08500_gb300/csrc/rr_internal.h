@@ -227,6 +227,8 @@ struct rr_ctx {
     int* d_tab_off = nullptr;    // npb + 1 offsets (in nodes)
     int* d_err = nullptr;        // device error word
     float4* d_svtab = nullptr;   // kSvTabLen entries (mixed form): sin and 1 - cos as float pairs
+    unsigned long long* d_counts = nullptr;   // RR_KERNEL_KINDS x RR_COUNT_KINDS sample counters
+    bool counting = false;
     // direct model: FP32 copies of the edges and profiles, and per basis the
     // running sums P[b][m] = sum_{j<m} pi (ze[j+1]^2 - ze[j]^2) l_b[j]
     float* d_zef = nullptr;      // nz + 1

@@ -223,34 +223,6 @@ __device__ __forceinline__ float sum3_small(float x, float y, float z) {
     return __fadd_rn(__fsub_rn(s, z), e);
 }
 
-// Angle of the point (x, y), y >= 0, in [0, pi] (atan2 for the upper half
-// plane): folded onto t = min(y, |x|) / max(y, |x|) in [0, 1], where
-// atan(t) = t P(t^2) with a degree-8 polynomial P whose coefficients were
-// fitted here to minimise the largest relative error over [0, 1] (weighted
-// least squares on Chebyshev nodes, reweighted by the error); evaluated in
-// FP32 it stays within 2 ulp of atan, and within 4 ulp with the fast
-// quotient.  Then atan = pi/2 - atan(1/t) above the diagonal and
-// pi - angle for x < 0.
-__device__ __forceinline__ float atan2_upper(float y, float x) {
-    const float ax = fabsf(x);
-    const float mx = fmaxf(y, ax), mn = fminf(y, ax);
-    const float t = mx > 1e-30f ? __fdividef(mn, mx) : 0.0f;
-    const float u = t * t;
-    float p = 2.849952085e-03f;
-    p = fmaf(p, u, -1.606889814e-02f);
-    p = fmaf(p, u, 4.269199818e-02f);
-    p = fmaf(p, u, -7.504339516e-02f);
-    p = fmaf(p, u, 1.064095795e-01f);
-    p = fmaf(p, u, -1.420365125e-01f);
-    p = fmaf(p, u, 1.999262124e-01f);
-    p = fmaf(p, u, -3.333307207e-01f);
-    p = fmaf(p, u, 1.0f);
-    float a = t * p;
-    if (y > ax) a = CUDART_PIO2_F - a;
-    if (x < 0.0f) a = CUDART_PI_F - a;
-    return a;
-}
-
 // Area common to the radius-r disk and the planet (radius k, centre at
 // distance c) with its partials d a / d k (the planet's rim inside the disk,
 // 2 k kappa_1) and d a / d c (minus the common chord, -K / c); inv_c = 1 / c

@@ -35,9 +35,11 @@ EXPORTS = ["rr_create", "rr_destroy", "rr_set_ld_profile", "rr_build_weights", "
            "rr_evaluate_noalloc", "rr_prepare", "rr_evaluate_prepared", "rr_evaluate_grad_prepared",
            "rr_evaluate_host", "rr_request_bytes", "rr_enqueue_host", "rr_server_create", "rr_server_destroy",
            "rr_server_submit", "rr_server_submit_at", "rr_server_now_ns", "rr_server_poll", "rr_server_pending", "rr_exact_flux", "rr_choose_grid",
-           "rr_selftest_wait"]
+           "rr_selftest_wait", "rr_count_samples", "rr_count_read"]
 KERNELS = {"ld_basis": 0, "weights": 1, "pv_setup": 2, "flux": 3, "grad": 4, "grad_reduce": 5, "points": 6,
            "direct": 7}
+#: sample counters of the counting form (include/rr.h RR_COUNT_*)
+COUNTS = ["cand", "samples", "orbit", "circular", "newton", "transit", "refined", "lens"]
 
 
 class RRConfig(ctypes.Structure):
@@ -111,11 +113,13 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     L.rr_profile_read.argtypes = [vp, i32, dp, ctypes.POINTER(i64), i32]
     L.rr_exact_flux.argtypes = [vp, vp, vp, i32, dp, i32, vp, vp]
     L.rr_selftest_wait.argtypes = [vp, i32, vp]
+    L.rr_count_samples.argtypes = [vp, i32]
+    L.rr_count_read.argtypes = [vp, i32, ctypes.POINTER(i64), i32]
     L.rr_choose_grid.argtypes = [ctypes.POINTER(RRConfig), dp, i32, dp, dp, dp, i32, ctypes.c_double, dp]
     for name in ("rr_exact_flux", "rr_choose_grid", "rr_selftest_wait", "rr_create", "rr_destroy", "rr_set_ld_profile", "rr_build_weights", "rr_evaluate",
                  "rr_evaluate_grad", "rr_sync_status", "rr_profile", "rr_profile_read", "rr_evaluate_noalloc",
                  "rr_prepare", "rr_evaluate_prepared", "rr_evaluate_grad_prepared", "rr_evaluate_host",
-                 "rr_enqueue_host"):
+                 "rr_enqueue_host", "rr_count_samples", "rr_count_read"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -259,6 +263,16 @@ class Model:
         if reset:
             self._check(self.lib.rr_profile_read(self._h, 0, None, None, 1))
         return out
+
+    def count_samples(self, enable: bool = True):
+        """Run the flux and adjoint kernels in their counting form (measurement aid)."""
+        self._check(self.lib.rr_count_samples(self._h, int(enable)))
+
+    def count_read(self, kind: str, reset: bool = False) -> dict:
+        """{counter: value} of kernel kind 'flux' or 'grad' (include/rr.h RR_COUNT_*)."""
+        buf = (ctypes.c_int64 * len(COUNTS))()
+        self._check(self.lib.rr_count_read(self._h, KERNELS[kind], buf, int(reset)))
+        return dict(zip(COUNTS, buf))
 
     def sync_status(self, stream=None):
         self._check(self.lib.rr_sync_status(self._h, _stream_handle(stream)))

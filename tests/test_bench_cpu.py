@@ -44,6 +44,14 @@ def test_reference_arm_prints_one_contract_line():
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
     assert d["config"]["workload"].startswith("c1")
+    # the GPU arm's config object, key for key
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("bench_under_test", os.path.join(ROOT, "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    assert d["config"] == bench.config_for("c1", bench.make_workload("c1"), 1)
+    # a step is a bounded sample: its measured wall time, not an extrapolation to the whole batch
+    assert d["ms_per_step"] < 60e3
 
 
 def _free_port():

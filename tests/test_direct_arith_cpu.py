@@ -15,13 +15,13 @@ import pytest
 
 from oracle.area import intersection_area
 
-SRC = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
-                   "paper_2009_08500_gb300", "csrc", "rr_setup.cu")
+CSRC = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_2009_08500_gb300", "csrc")
+SOURCES = [os.path.join(CSRC, f) for f in ("rr_setup.cu", "rr_device.cuh")]
 f32 = np.float32
 
 
 def _function_body(name):
-    src = open(SRC).read()
+    src = next(t for t in (open(f).read() for f in SOURCES) if "__forceinline__ float " + name + "(" in t)
     i = src.index(name + "(")
     j = src.index("{", i)
     depth, k = 0, j
@@ -89,7 +89,37 @@ def test_arctangent_polynomial_within_two_ulp():
     got = (t * p).astype(f32)
     ref = np.arctan(t.astype(np.float64))
     ulp = np.abs(got - ref)[1:] / np.spacing(ref[1:].astype(f32))
-    assert ulp.max() < 2.5
+    assert ulp.max() < 1.5
+
+
+def lawson_arctangent_fit(nodes=2000, rounds=1000):
+    """Coefficients c8 .. c1, 1 of P(u), atan(t) ~ t P(t^2), minimising the largest relative error
+    over [0, 1]: least squares on Chebyshev nodes, each node's weight multiplied by its error
+    every round (Lawson's iteration, which converges to the minimax solution)."""
+    k = np.arange(nodes)
+    t = 0.5 * (1.0 - np.cos(np.pi * (k + 0.5) / nodes))
+    u, at = t * t, np.arctan(t)
+    A = np.stack([t * u ** j / at for j in range(1, 9)], axis=1)    # relative error = A c - b
+    b = 1.0 - t / at
+    w = np.full(nodes, 1.0 / nodes)
+    for _ in range(rounds):
+        sw = np.sqrt(w)
+        c, *_ = np.linalg.lstsq(A * sw[:, None], b * sw, rcond=None)
+        e = A @ c - b
+        w = w * np.abs(e)
+        w /= w.sum()
+    return np.concatenate([c[::-1], [1.0]]), np.abs(e).max()
+
+
+def test_arctangent_coefficients_are_the_minimax_fit():
+    """The kernel's coefficients are the FP64 minimax fit of the relative error, rounded to FP32."""
+    cf = np.array(_atan_coefficients(), np.float64)
+    fit, err = lawson_arctangent_fit()
+    assert err < 1.7e-8
+    assert np.all(np.abs(cf - fit) <= 2 * np.spacing(np.abs(fit).astype(f32)))
+    # the converged fit: more rounds or nodes change nothing at FP32 precision
+    fit2, _ = lawson_arctangent_fit(nodes=3000, rounds=2000)
+    assert np.all(np.abs(fit2 - fit) <= np.spacing(np.abs(fit).astype(f32)))
 
 
 def test_upper_half_plane_folding_matches_atan2():

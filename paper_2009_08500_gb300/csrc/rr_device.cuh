@@ -702,6 +702,87 @@ __device__ __forceinline__ int build_list_ss1_packed(float4* wl, unsigned cand, 
     return total;
 }
 
+// The forward kernel's per-warp candidate list, 16 bytes per candidate so that
+// four CTAs fit on an SM: the candidate's phase pair (with supersampling the
+// precise phase fr_h, fr_l in cycles; with one sample per time the raw offsets
+// dh, dl), its passband and first flattened sample packed as (soff << 5) | pb
+// (pb < RR_MAX_PB = 32; ps[nc] = ns << 5), and its sum over sub-exposures.
+struct FluxList {
+    float2 cand[kWarpPts];
+    int ps[kWarpPts + 1];
+    float pacc[kWarpPts];
+};
+
+__device__ __forceinline__ int chunk_cand_ps(ChunkWalk& cw, const int* ps, int nc, int e0) {
+    const int lane = threadIdx.x & 31;
+    if (cw.jf + 1 < nc && (ps[cw.jf + 1] >> 5) <= e0) ++cw.jf;   // warp-uniform
+    const int jn = cw.jf + 1 + lane;
+    unsigned bit = 0u;
+    if (jn < nc) {
+        const int pos = (ps[jn] >> 5) - e0;
+        if (pos > 0 && pos < 32) bit = 1u << pos;
+    }
+    const unsigned starts = __reduce_or_sync(0xffffffffu, bit);
+    const unsigned upto = lane == 31 ? 0xffffffffu : ((2u << lane) - 1u);
+    const int j = cw.jf + __popc(starts & upto);
+    cw.jf = __shfl_sync(0xffffffffu, j, 31);
+    return j;
+}
+
+// build_list for the forward kernel (FluxList; returns the flattened sample count).
+__device__ __forceinline__ int build_list_flux(FluxList* fl, unsigned cand, const float (&dh)[4], const float (&dl)[4],
+                                               const int (&pbv)[4], float Ah, float Al, float Bh, float Bl,
+                                               const PbShared* ps, int& nc, int& base) {
+    const int lane = threadIdx.x & 31;
+    int ns_l = 0;
+    #pragma unroll
+    for (int q = 0; q < 4; ++q)
+        if (cand & (1u << q)) ns_l += ps->ss[pbv[q]];
+    base = warp_excl_scan(__popc(cand), nc);
+    int ns;
+    int soff = warp_excl_scan(ns_l, ns);
+    int j = base;
+    #pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        if (cand & (1u << q)) {
+            const Phase32 ph = precise_phase(dh[q], dl[q], Ah, Al, Bh, Bl);
+            fl->cand[j] = make_float2(ph.fr_h, ph.fr_l);
+            fl->ps[j] = (soff << 5) | pbv[q];
+            fl->pacc[j] = 0.0f;
+            soff += ps->ss[pbv[q]];
+            ++j;
+        }
+    }
+    if (lane == 0) fl->ps[nc] = ns << 5;
+    __syncwarp();
+    return ns;
+}
+
+// build_list_ss1 for the forward kernel (FluxList: ps[j] = passband).
+__device__ __forceinline__ int build_list_ss1_flux(FluxList* fl, unsigned cand, const float (&dh)[4],
+                                                   const float (&dl)[4], const int (&pbv)[4], int (&bq)[4]) {
+    const int lane = threadIdx.x & 31;
+    const unsigned below = (1u << lane) - 1u;
+    int total = 0, before = 0;
+    #pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const unsigned bal = __ballot_sync(0xffffffffu, (cand >> q) & 1u);
+        before += __popc(bal & below);
+        total += __popc(bal);
+    }
+    #pragma unroll
+    for (int q = 0; q < 4; ++q) bq[q] = before + __popc(cand & ((1u << q) - 1u));
+    #pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        if ((cand >> q) & 1u) {
+            fl->cand[bq[q]] = make_float2(dh[q], dl[q]);
+            fl->ps[bq[q]] = pbv[q];
+        }
+    }
+    __syncwarp();
+    return total;
+}
+
 // Shared-memory layout common to the FP32 per-point kernels:
 //   [mbarrier 16][reduction 64][per-pv tile constants 16 x kMaxPvTile]
 //   [passband constants][one candidate list per warp][pv records ...]
@@ -711,6 +792,9 @@ constexpr size_t kOffPb = kOffCta + 16 * kMaxPvTile;
 constexpr size_t kOffWl = kOffPb + ((sizeof(PbShared) + 15) / 16) * 16;
 constexpr size_t kWlBytes = ((sizeof(WarpList) + 15) / 16) * 16;
 constexpr size_t kOffRecs32 = kOffWl + (kBlock / 32) * kWlBytes;
+// the forward kernel: FluxList
+constexpr size_t kFlBytes = ((sizeof(FluxList) + 15) / 16) * 16;
+constexpr size_t kOffRecsFlux = kOffWl + (kBlock / 32) * kFlBytes;
 // the adjoint with one sample per time keeps only the packed list (float4 per candidate)
 constexpr size_t kWlBytesPacked = kWarpPts * sizeof(float4);
 constexpr size_t kOffRecs32Packed = kOffWl + (kBlock / 32) * kWlBytesPacked;

@@ -79,11 +79,11 @@ __global__ void __launch_bounds__(kBlock, 4) rr_flux_mixed_kernel(const double* 
     extern __shared__ __align__(16) unsigned char smem[];
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
     PbShared* ps = reinterpret_cast<PbShared*>(smem + kOffPb);
-    char* recs = reinterpret_cast<char*>(smem + kOffRecs32);
+    char* recs = reinterpret_cast<char*>(smem + kOffRecsFlux);
     TileCounters* tc = reinterpret_cast<TileCounters*>(smem + kOffRed);
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    WarpList* wl = reinterpret_cast<WarpList*>(smem + kOffWl + warp * kWlBytes);
+    FluxList* wl = reinterpret_cast<FluxList*>(smem + kOffWl + warp * kFlBytes);
     const int ngroups = (npt + kWarpPts - 1) / kWarpPts;
     const int gbeg = blockIdx.x * groups_per_cta;
     const int gend = min(ngroups, gbeg + groups_per_cta);
@@ -135,7 +135,6 @@ __global__ void __launch_bounds__(kBlock, 4) rr_flux_mixed_kernel(const double* 
     __syncthreads();
 
     const float nanf_ = __int_as_float(0x7fc00000);
-    const float zero4[4] = {0.f, 0.f, 0.f, 0.f};
     const uint64_t l2_pol = l2_evict_first_policy();
     Tally tl{};   // the counting form's per-thread sample counts
 
@@ -209,13 +208,13 @@ __global__ void __launch_bounds__(kBlock, 4) rr_flux_mixed_kernel(const double* 
           if (__any_sync(0xffffffffu, cand != 0)) {
             // one sample per time: the candidates are the samples
             int bq[4];
-            const int nc = build_list_ss1(wl, cand, dh, dl, pbv, zero4, bq);
+            const int nc = build_list_ss1_flux(wl, cand, dh, dl, pbv, bq);
             #pragma unroll 1
             for (int e0 = 0; e0 < nc; e0 += 32) {
                 const int j = e0 + lane;
                 if (j < nc) {
-                    const int pb = wl->pb[j];
-                    const float4 cd = wl->cand[j];
+                    const int pb = wl->ps[j];
+                    const float2 cd = wl->cand[j];
                     const Phase32 ph = precise_phase(cd.x, cd.y, c.x, c.y, H.Bh, H.Bl);
                     if (COUNT) ++tl.n[RR_COUNT_TIMES];
                     wl->pacc[j] = delta32<COUNT>(H, PB[pb], rows + (size_t)pb * L.rows_per_pb * L.ng_pad, L.ng,
@@ -230,21 +229,22 @@ __global__ void __launch_bounds__(kBlock, 4) rr_flux_mixed_kernel(const double* 
           }
         } else if (__any_sync(0xffffffffu, cand != 0)) {
             int nc, base;
-            const int ns = build_list(wl, cand, dh, dl, pbv, zero4, c.x, c.y, H.Bh, H.Bl, ps, nc, base);
+            const int ns = build_list_flux(wl, cand, dh, dl, pbv, c.x, c.y, H.Bh, H.Bl, ps, nc, base);
             if (COUNT && lane == 0) tl.n[RR_COUNT_TIMES] += nc;
             ChunkWalk cw{0};
             #pragma unroll 1
             for (int e0 = 0; e0 < ns; e0 += 32) {
                 const int e = e0 + lane;
                 const bool valid = e < ns;
-                const int jc = chunk_cand(cw, wl->soff, nc, e0);
+                const int jc = chunk_cand_ps(cw, wl->ps, nc, e0);
                 const int j = valid ? jc : -1;
                 float d = 0.0f;
                 if (valid) {
-                    const int pb = wl->pb[j];
-                    const float4 cd = wl->cand[j];
+                    const int pw = wl->ps[j];
+                    const int pb = pw & 31;
+                    const float2 cd = wl->cand[j];
                     d = delta32<COUNT>(H, PB[pb], rows + (size_t)pb * L.rows_per_pb * L.ng_pad, L.ng, cd.x, cd.y,
-                                       e - wl->soff[j], ps->first[pb], ps->step[pb], bad, &tl);
+                                       e - (pw >> 5), ps->first[pb], ps->step[pb], bad, &tl);
                 }
                 if (ns == nc) {
                     // one sample per candidate: nothing to sum
@@ -419,10 +419,11 @@ __global__ void __launch_bounds__(kBlock) rr_flux_fp64_kernel(const double* __re
 static size_t flux_smem(int pv_tile, int rec_bytes, bool f64, int gpc) {
     if (f64) return 16 + 16 * 4 + 16 * kMaxPvTile + (size_t)pv_tile * rec_bytes;
     // + two constant rows (1 and NaN) for the bulk stores + the group summaries
-    return kOffRecs32 + (size_t)pv_tile * rec_bytes + queue_bytes(pv_tile * gpc) + 2 * kWarpPts * sizeof(float) +
+    return kOffRecsFlux + (size_t)pv_tile * rec_bytes + queue_bytes(pv_tile * gpc) + 2 * kWarpPts * sizeof(float) +
            (size_t)gpc * sizeof(GroupInfo);
 }
-static_assert(kOffRecs32 % 16 == 0 && kOffRecs32Packed % 16 == 0, "shared-memory regions must stay 16-byte aligned");
+static_assert(kOffRecs32 % 16 == 0 && kOffRecs32Packed % 16 == 0 && kOffRecsFlux % 16 == 0,
+              "shared-memory regions must stay 16-byte aligned");
 
 // 128-time groups per CTA of the FP32 kernels.  A function of npt only, so
 // the adjoint's summation order for a pv never depends on the other pvs in

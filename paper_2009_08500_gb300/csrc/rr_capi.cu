@@ -190,6 +190,9 @@ WsLayout ws_layout(const rr_ctx* c, int npv, int npt, bool grad) {
     if (c->cfg.precision == RR_PREC_MIXED) off += align256((size_t)npt * 4);
     w.pts_grp = off;
     if (c->cfg.precision == RR_PREC_MIXED) off += align256((size_t)((npt + kWarpPts - 1) / kWarpPts) * sizeof(GroupInfo));
+    w.pts_ord = off;
+    if (c->cfg.precision == RR_PREC_MIXED && c->cfg.npb > 1)
+        off += align256((size_t)time_chunks(npt, groups_per_cta(npt)) * sizeof(int));
     w.part = off;
     if (grad) off += align256(partials_bytes(c, npv, npt));
     w.total = off > 0 ? off : 256;
@@ -224,7 +227,10 @@ cudaError_t run_setup(rr_ctx* c, const double* times, const int32_t* pb_index, i
     });
     if (e != cudaSuccess || fused || c->cfg.precision != RR_PREC_MIXED || npt == 0) return e;
     return timed(c, RR_KERNEL_POINTS, s,
-                 [&] { return launch_points(c, times, pb_index, npt, wb + W.pts_dt, wb + W.pts_pb, wb + W.pts_grp, s); });
+                 [&] {
+                     return launch_points(c, times, pb_index, npt, pbp, wb + W.pts_dt, wb + W.pts_pb, wb + W.pts_grp,
+                                          wb + W.pts_ord, s);
+                 });
 }
 
 // Validity words only (npt == 0 with a pv_status array): the set-up kernel alone.
@@ -260,8 +266,9 @@ rr_status evaluate_impl(rr_ctx* c, const double* times, const int32_t* pb_index,
     const WsLayout W = ws_layout(c, npv, npt, prepared);
     char* wb = (char*)ws;
     if ((e = timed(c, RR_KERNEL_FLUX, s, [&] {
-             return launch_flux(c, times, pb_index, wb + W.pts_dt, wb + W.pts_pb, wb + W.pts_grp, npt, npv, pbp, ws, flux,
-                                pv_status, prepared, s);
+             return launch_flux(c, times, pb_index, wb + W.pts_dt, wb + W.pts_pb, wb + W.pts_grp,
+                                c->cfg.npb > 1 ? wb + W.pts_ord : nullptr, npt, npv, pbp, ws, flux, pv_status,
+                                prepared, s);
          })) != cudaSuccess)
         return cuda_fail(c, e, "flux kernel");
     return RR_OK;
@@ -292,8 +299,9 @@ rr_status evaluate_grad_impl(rr_ctx* c, const double* times, const int32_t* pb_i
     char* wb = (char*)ws;
     void* partials = wb + W.part;
     if ((e = timed(c, RR_KERNEL_GRAD, s, [&] {
-             return launch_grad(c, times, pb_index, wb + W.pts_dt, wb + W.pts_pb, wb + W.pts_grp, npt, npv, pbp, ws, grad_flux,
-                                partials, pv_status, s);
+             return launch_grad(c, times, pb_index, wb + W.pts_dt, wb + W.pts_pb, wb + W.pts_grp,
+                                c->cfg.npb > 1 ? wb + W.pts_ord : nullptr, npt, npv, pbp, ws, grad_flux, partials,
+                                pv_status, s);
          })) != cudaSuccess)
         return cuda_fail(c, e, "adjoint kernel");
     if ((e = timed(c, RR_KERNEL_GRAD_REDUCE, s, [&] {

@@ -1146,17 +1146,19 @@ __device__ __forceinline__ double ld_basis_mu(const ModelParams& mp, int b, doub
 // group's first time (FP64 here, so that the per-(pv, point) work is FP32
 // only), and the passband index with out-of-range values mapped to npb; the
 // group's summary (GroupInfo): the range and largest magnitude of its float
-// offsets, whether it is full with valid passbands, and t_g - t_0.  Every
-// thread of the block calls (one barrier); groups g >= ngroups only take part
-// in the barrier.  red, redf: the group's reduction slots in shared memory.
+// offsets, whether it is full with valid passbands, t_g - t_0, and its weight
+// (the sum over its times of ss[passband], ss in shared memory, or the count
+// of valid times when ss is null).  Every thread of the block calls (one
+// barrier); groups g >= ngroups only take part in the barrier.  red, redf:
+// the group's reduction slots in shared memory.
 __device__ __forceinline__ void points_group(const double* __restrict__ times, const int32_t* __restrict__ pb_index,
                                              int npt, int npb, float2* __restrict__ dt, int32_t* __restrict__ pbw,
                                              GroupInfo* __restrict__ grp, int g, int ngroups, int t,
-                                             float (*red)[kWarpPts / 32], int* redf) {
+                                             float (*red)[kWarpPts / 32], int* redf, const int* ss) {
     const int lane = t & 31, warp = t >> 5;
     const bool live = g < ngroups;
     const int p = g * kWarpPts + t;
-    float lo = INFINITY, hi = -INFINITY, mx = 0.0f;
+    float lo = INFINITY, hi = -INFINITY, mx = 0.0f, wt = 0.0f;
     int ok = 0;
     double tg = 0.0;
     if (live) tg = times[(size_t)g * kWarpPts];
@@ -1170,17 +1172,20 @@ __device__ __forceinline__ void points_group(const double* __restrict__ times, c
         lo = hi = h;
         mx = fabsf(h);
         ok = v < npb;
+        if (ok) wt = ss ? (float)ss[v] : 1.0f;
     }
     for (int o = 16; o > 0; o >>= 1) {
         lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
         hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
         mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        wt += __shfl_xor_sync(0xffffffffu, wt, o);
     }
     ok = __all_sync(0xffffffffu, ok);
     if (lane == 0) {
         red[0][warp] = lo;
         red[1][warp] = hi;
         red[2][warp] = mx;
+        red[3][warp] = wt;
         redf[warp] = ok;
     }
     __syncthreads();
@@ -1190,16 +1195,18 @@ __device__ __forceinline__ void points_group(const double* __restrict__ times, c
         gi.whi = red[1][0];
         gi.maxdt = red[2][0];
         gi.full = redf[0];
+        gi.weight = red[3][0];
         for (int w = 1; w < kWarpPts / 32; ++w) {
             gi.wlo = fminf(gi.wlo, red[0][w]);
             gi.whi = fmaxf(gi.whi, red[1][w]);
             gi.maxdt = fmaxf(gi.maxdt, red[2][w]);
+            gi.weight += red[3][w];
             gi.full &= redf[w];
         }
         const double d0 = tg - times[0];
         gi.toff_h = (float)d0;
         gi.toff_l = (float)(d0 - (double)gi.toff_h);
-        gi.pad[0] = gi.pad[1] = 0.0f;
+        gi.pad = 0.0f;
         grp[g] = gi;
     }
 }

@@ -37,17 +37,56 @@ namespace rr {
 __global__ void __launch_bounds__(kWarpPts) rr_points_kernel(const double* __restrict__ times,
                                                              const int32_t* __restrict__ pb_index, int npt, int npb,
                                                              float2* __restrict__ dt, int32_t* __restrict__ pbw,
-                                                             GroupInfo* __restrict__ grp, int ngroups) {
-    __shared__ float red[3][kWarpPts / 32];
+                                                             GroupInfo* __restrict__ grp, int ngroups, PbParams pbp) {
+    __shared__ float red[4][kWarpPts / 32];
     __shared__ int redf[kWarpPts / 32];
-    points_group(times, pb_index, npt, npb, dt, pbw, grp, blockIdx.x, ngroups, threadIdx.x, red, redf);
+    __shared__ int ss[RR_MAX_PB];
+    for (int j = threadIdx.x; j < npb; j += blockDim.x) ss[j] = pbp.ss[j];
+    __syncthreads();
+    points_group(times, pb_index, npt, npb, dt, pbw, grp, blockIdx.x, ngroups, threadIdx.x, red, redf, ss);
 }
 
-cudaError_t launch_points(rr_ctx* c, const double* times, const int32_t* pb_index, int npt, void* ws_dt,
-                          void* ws_pb, void* ws_grp, cudaStream_t s) {
+// Order of the time chunks of the FP32 per-point kernels, heaviest first (one
+// CTA): chunk i (groups i gpc .. i gpc + gpc - 1) weighs the exposure
+// sub-samples of its groups; order[rank] = i, ties in index order.  With
+// passbands of different supersampling the chunks' work differs several-fold
+// (a chunk of 30-sub-exposure times against one of single samples), and the
+// heaviest CTAs are best started first: the last wave then holds light ones.
+// More than 1024 chunks: index order.
+__global__ void __launch_bounds__(1024) rr_chunk_order_kernel(const GroupInfo* __restrict__ grp, int ngroups,
+                                                              int gpc, int nchunks, int* __restrict__ order) {
+    __shared__ float w[1024];
+    const int i = threadIdx.x;
+    if (nchunks > 1024) {
+        for (int j = i; j < nchunks; j += blockDim.x) order[j] = j;
+        return;
+    }
+    if (i < nchunks) {
+        float s = 0.0f;
+        const int g1 = min(ngroups, (i + 1) * gpc);
+        for (int g = i * gpc; g < g1; ++g) s += grp[g].weight;
+        w[i] = s;
+    }
+    __syncthreads();
+    if (i < nchunks) {
+        const float wi = w[i];
+        int rank = 0;
+        for (int j = 0; j < nchunks; ++j) rank += (w[j] > wi) || (w[j] == wi && j < i);
+        order[rank] = i;
+    }
+}
+
+cudaError_t launch_points(rr_ctx* c, const double* times, const int32_t* pb_index, int npt, const PbParams& pbp,
+                          void* ws_dt, void* ws_pb, void* ws_grp, void* ws_ord, cudaStream_t s) {
     const int ngroups = (npt + kWarpPts - 1) / kWarpPts;
     rr_points_kernel<<<ngroups, kWarpPts, 0, s>>>(times, pb_index, npt, c->cfg.npb, (float2*)ws_dt,
-                                                  (int32_t*)ws_pb, (GroupInfo*)ws_grp, ngroups);
+                                                  (int32_t*)ws_pb, (GroupInfo*)ws_grp, ngroups, pbp);
+    c->launches++;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || !ws_ord) return e;
+    const int gpc = groups_per_cta(npt);
+    rr_chunk_order_kernel<<<1, 1024, 0, s>>>((const GroupInfo*)ws_grp, ngroups, gpc, time_chunks(npt, gpc),
+                                             (int*)ws_ord);
     c->launches++;
     return cudaGetLastError();
 }
@@ -75,7 +114,7 @@ __global__ void __launch_bounds__(kBlock, 4) rr_flux_mixed_kernel(const double* 
                                                                float* __restrict__ flux,
                                                                int32_t* __restrict__ pv_status, int vec_store,
                                                                int stream_warps, unsigned long long* counts,
-                                                               int* err) {
+                                                               const int* __restrict__ chunk_order, int* err) {
     extern __shared__ __align__(16) unsigned char smem[];
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
     PbShared* ps = reinterpret_cast<PbShared*>(smem + kOffPb);
@@ -85,9 +124,11 @@ __global__ void __launch_bounds__(kBlock, 4) rr_flux_mixed_kernel(const double* 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     FluxList* wl = reinterpret_cast<FluxList*>(smem + kOffWl + warp * kFlBytes);
     const int ngroups = (npt + kWarpPts - 1) / kWarpPts;
-    const int gbeg = blockIdx.x * groups_per_cta;
+    // grid: x = pv tile, y = time chunk (in launch order; chunk_order: heaviest first)
+    const int chunk = chunk_order ? __ldg(chunk_order + blockIdx.y) : (int)blockIdx.y;
+    const int gbeg = chunk * groups_per_cta;
     const int gend = min(ngroups, gbeg + groups_per_cta);
-    const int pv0 = blockIdx.y * pv_tile;
+    const int pv0 = blockIdx.x * pv_tile;
     const int npv_t = min(pv_tile, npv - pv0);
     // staged: headers of the tile, then (STAGE_ROWS) their profile rows, then the item queue
     char* srows = recs + (size_t)pv_tile * L.head_bytes;
@@ -480,8 +521,8 @@ cudaError_t launch_selftest(rr_ctx* c, int which, cudaStream_t s) {
 constexpr int kStreamWarpsSS1 = 2;
 
 cudaError_t launch_flux(rr_ctx* c, const double* times, const int32_t* pb_index, const void* pts_dt,
-                        const void* pts_pb, const void* pts_grp, int npt, int npv, const PbParams& pbp,
-                        const void* records,
+                        const void* pts_pb, const void* pts_grp, const void* pts_ord, int npt, int npv,
+                        const PbParams& pbp, const void* records,
                         void* flux, int32_t* pv_status, bool grad_layout, cudaStream_t s) {
     const bool f64 = c->cfg.precision == RR_PREC_FP64;
     RecLayout L = f64 ? make_layout<double>(c->cfg.npb, c->cfg.ng, c->nldc, grad_layout)
@@ -498,7 +539,7 @@ cudaError_t launch_flux(rr_ctx* c, const double* times, const int32_t* pb_index,
     const char* rowsg = (const char*)records + rows_offset(L, npv);
     const int npvt = (npv + pv_tile - 1) / pv_tile;
     const int ngroups = (npt + kWarpPts - 1) / kWarpPts;
-    dim3 grid(f64 ? (npt + kPtTile - 1) / kPtTile : (ngroups + gpc - 1) / gpc, npvt);
+    dim3 grid = f64 ? dim3((npt + kPtTile - 1) / kPtTile, npvt) : dim3(npvt, (ngroups + gpc - 1) / gpc);
     if (smem > kMaxSmem || grid.y > 65535u) return cudaErrorInvalidConfiguration;
     cudaError_t e;
     if (f64) {
@@ -527,7 +568,7 @@ cudaError_t launch_flux(rr_ctx* c, const double* times, const int32_t* pb_index,
                                         pv_tile, gpc, (const char*)records, rowsg, (float*)flux, pv_status, vec,
                                         ss1 ? kStreamWarpsSS1 : (kBlock >> 5),
                                         c->d_counts ? c->d_counts + (size_t)RR_KERNEL_FLUX * RR_COUNT_KINDS : nullptr,
-                                        c->d_err);
+                                        (const int*)pts_ord, c->d_err);
     }
     c->launches++;
     return cudaGetLastError();

@@ -332,7 +332,7 @@ __global__ void __launch_bounds__(kBlock, 3) rr_grad_mixed_kernel(
     int npv, PbParams pbp, RecLayout L, int pv_tile, int groups_per_cta, const char* __restrict__ records,
     const char* __restrict__ rowsg, const float* __restrict__ gflux, float* __restrict__ partials, int nacc,
     int chromatic, int vec_g, const float4* __restrict__ svtab, unsigned long long* counts,
-    int32_t* __restrict__ pv_status, int* err) {
+    const int* __restrict__ chunk_order, int32_t* __restrict__ pv_status, int* err) {
     extern __shared__ __align__(16) unsigned char smem[];
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
     PbShared* ps = reinterpret_cast<PbShared*>(smem + kOffPb);
@@ -351,9 +351,11 @@ __global__ void __launch_bounds__(kBlock, 3) rr_grad_mixed_kernel(
     WarpList* wl = reinterpret_cast<WarpList*>(smem + kOffWl + warp * kWlBytes);
     float4* wlp = reinterpret_cast<float4*>(smem + kOffWl + warp * kWlBytesPacked);
     const int ngroups = (npt + kWarpPts - 1) / kWarpPts;
-    const int gbeg = blockIdx.x * groups_per_cta;
+    // grid: x = pv tile, y = time chunk (in launch order; chunk_order: heaviest first)
+    const int chunk = chunk_order ? __ldg(chunk_order + blockIdx.y) : (int)blockIdx.y;
+    const int gbeg = chunk * groups_per_cta;
     const int gend = min(ngroups, gbeg + groups_per_cta);
-    const int pv0 = blockIdx.y * pv_tile;
+    const int pv0 = blockIdx.x * pv_tile;
     const int npv_t = min(pv_tile, npv - pv0);
     const uint32_t bytes = (uint32_t)npv_t * (uint32_t)L.head_bytes;
     const uint32_t gbytes = (uint32_t)(gend - gbeg) * (uint32_t)sizeof(GroupInfo);
@@ -537,8 +539,7 @@ __global__ void __launch_bounds__(kBlock, 3) rr_grad_mixed_kernel(
         __nanosleep(64);
     }
     if (COUNT) tally_flush(tl, counts);
-    cta_partials_groups(gacc, recs, L.head_bytes, npv_t, nacc, groups_per_cta, pv0, blockIdx.x, gridDim.x,
-                        partials);
+    cta_partials_groups(gacc, recs, L.head_bytes, npv_t, nacc, groups_per_cta, pv0, chunk, gridDim.y, partials);
 }
 
 template <bool DEP>
@@ -729,8 +730,8 @@ static bool grad_dep(const rr_ctx* c) {
 }
 
 cudaError_t launch_grad(rr_ctx* c, const double* times, const int32_t* pb_index, const void* pts_dt,
-                        const void* pts_pb, const void* pts_grp, int npt, int npv, const PbParams& pbp,
-                        const void* records,
+                        const void* pts_pb, const void* pts_grp, const void* pts_ord, int npt, int npv,
+                        const PbParams& pbp, const void* records,
                         const void* grad_flux, void* partials, int32_t* pv_status, cudaStream_t s) {
     const bool f64 = c->cfg.precision == RR_PREC_FP64;
     RecLayout L = f64 ? make_layout<double>(c->cfg.npb, c->cfg.ng, c->nldc, true)
@@ -750,7 +751,7 @@ cudaError_t launch_grad(rr_ctx* c, const double* times, const int32_t* pb_index,
     const char* rowsg = (const char*)records + rows_offset(L, npv);
     const int npvt = (npv + pv_tile - 1) / pv_tile;
     const int gpc = groups_per_cta(npt);
-    dim3 grid(grad_chunks(c, npt), npvt);
+    dim3 grid = f64 ? dim3(grad_chunks(c, npt), npvt) : dim3(npvt, grad_chunks(c, npt));
     if (smem > kMaxSmem || grid.y > 65535u) return cudaErrorInvalidConfiguration;
     cudaError_t e;
     if (f64) {
@@ -775,7 +776,7 @@ cudaError_t launch_grad(rr_ctx* c, const double* times, const int32_t* pb_index,
                                           (const GroupInfo*)pts_grp, npt, npv, pbp,                           \
                                           L, pv_tile, gpc, (const char*)records, rowsg,                       \
                                           (const float*)grad_flux, (float*)partials, nacc, c->cfg.chromatic,  \
-                                          vec_g, c->d_svtab, counts,                                          \
+                                          vec_g, c->d_svtab, counts, (const int*)pts_ord,                     \
                                           pv_status, c->d_err);                                               \
     } while (0)
         const int vec_g = (npt % 4 == 0) && (((uintptr_t)grad_flux & 15u) == 0);

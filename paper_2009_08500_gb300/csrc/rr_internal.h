@@ -48,12 +48,14 @@ constexpr int kWarpPts = 4 * 32;          // times per group: one warp, 4 consec
 // Per 128-time group, written once per call by points_group (mixed form):
 // the range and largest magnitude of the float offsets of its times from the
 // group's first time t_g, whether all 128 times exist with a valid passband,
-// and t_g - t_0 (t_0 = the first time of the call) as a float pair.
+// t_g - t_0 (t_0 = the first time of the call) as a float pair, and the
+// group's weight: its exposure sub-samples (the sum of ss over its times).
 struct alignas(16) GroupInfo {
     float wlo, whi, maxdt;
     int32_t full;                 // 1: 128 times, every passband index valid
     float toff_h, toff_l;
-    float pad[2];
+    float weight;
+    float pad;
 };
 
 static_assert(sizeof(GroupInfo) % 16 == 0, "group summaries are copied with bulk asynchronous copies");
@@ -296,8 +298,9 @@ cudaError_t launch_direct_tables(rr_ctx* c, const double* params, int npv, bool 
 size_t direct_bytes(const rr_ctx* c, int npv, bool grad);
 DirectTables direct_view(const rr_ctx* c, void* base, int npv, bool grad);
 cudaError_t launch_selftest(rr_ctx* c, int which, cudaStream_t s);
-cudaError_t launch_points(rr_ctx* c, const double* times, const int32_t* pb_index, int npt, void* ws_dt,
-                          void* ws_pb, void* ws_grp, cudaStream_t s);
+// with several passbands also the order of the CTA time chunks, heaviest first (ws_ord)
+cudaError_t launch_points(rr_ctx* c, const double* times, const int32_t* pb_index, int npt, const PbParams& pbp,
+                          void* ws_dt, void* ws_pb, void* ws_grp, void* ws_ord, cudaStream_t s);
 // records: the workspace (the direct model's projections follow the records).  With times
 // (mixed form, npt > 0) the same launch also writes the per-time inputs of the FP32 kernels
 // (float-float offsets, passband, 128-time group summaries) into pts_dt, pts_pb, pts_grp.
@@ -306,14 +309,17 @@ cudaError_t launch_pv_setup(rr_ctx* c, const double* params, int npv, const PbPa
                             const double* times = nullptr, const int32_t* pb_index = nullptr, int npt = 0,
                             void* pts_dt = nullptr, void* pts_pb = nullptr, void* pts_grp = nullptr);
 // grad_layout: the records were written in the adjoint's layout (rr_prepare)
+// pts_ord: the order of the time chunks (several passbands), or null (in index order)
 cudaError_t launch_flux(rr_ctx* c, const double* times, const int32_t* pb_index, const void* pts_dt,
-                        const void* pts_pb, const void* pts_grp, int npt, int npv, const PbParams& pbp,
-                        const void* records,
+                        const void* pts_pb, const void* pts_grp, const void* pts_ord, int npt, int npv,
+                        const PbParams& pbp, const void* records,
                         void* flux, int32_t* pv_status, bool grad_layout, cudaStream_t s);
 cudaError_t launch_grad(rr_ctx* c, const double* times, const int32_t* pb_index, const void* pts_dt,
-                        const void* pts_pb, const void* pts_grp, int npt, int npv, const PbParams& pbp,
-                        const void* records,
+                        const void* pts_pb, const void* pts_grp, const void* pts_ord, int npt, int npv,
+                        const PbParams& pbp, const void* records,
                         const void* grad_flux, void* partials, int32_t* pv_status, cudaStream_t s);
+// time chunks of the FP32 per-point kernels
+inline int time_chunks(int npt, int gpc) { return ((npt + kWarpPts - 1) / kWarpPts + gpc - 1) / gpc; }
 cudaError_t launch_grad_reduce(rr_ctx* c, int npt, const double* params, int npv, const void* records,
                                const void* partials, double* grad_params, cudaStream_t s);
 size_t records_bytes(const rr_ctx* c, int npv, bool grad);
@@ -321,7 +327,7 @@ size_t partials_bytes(const rr_ctx* c, int npv, int npt);
 // workspace layout: [records | direct-model projections | per-point float-float times + passband,
 //                    per-group summaries (mixed form) | partial sums]
 struct WsLayout {
-    size_t rec, dir, pts_dt, pts_pb, pts_grp, part, total;
+    size_t rec, dir, pts_dt, pts_pb, pts_grp, pts_ord, part, total;
 };
 WsLayout ws_layout(const rr_ctx* c, int npv, int npt, bool grad);
 

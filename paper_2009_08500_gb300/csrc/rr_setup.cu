@@ -711,11 +711,11 @@ __global__ void __launch_bounds__(256, 4) rr_pv_setup_kernel(ModelParams mp, PbP
     if ((int)blockIdx.x < pa.npoints) {
         // the per-time inputs of the FP32 kernels, two 128-time groups per CTA, in the same
         // launch as the per-pv set-up (the two are independent); these short CTAs come first
-        __shared__ float pred[2][3][kWarpPts / 32];
+        __shared__ float pred[2][4][kWarpPts / 32];
         __shared__ int predf[2][kWarpPts / 32];
         const int half = threadIdx.x / kWarpPts;
         points_group(pa.times, pa.pb_index, pa.npt, mp.npb, pa.dt, pa.pbw, pa.grp, (int)blockIdx.x * 2 + half,
-                     pa.ngroups, threadIdx.x % kWarpPts, pred[half], predf[half]);
+                     pa.ngroups, threadIdx.x % kWarpPts, pred[half], predf[half], nullptr);
         return;
     }
     const int sblock = (int)blockIdx.x - pa.npoints;   // this CTA's index among the set-up CTAs

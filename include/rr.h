@@ -169,7 +169,12 @@ int32_t rr_nparam(const rr_ctx* ctx);
  * times.  0 on bad arguments. */
 size_t rr_workspace_bytes(const rr_ctx* ctx, int32_t npv, int32_t npt, int32_t with_grad);
 
-/* Evaluate light curves: flux[pv][t] for every parameter vector and time.
+/* Evaluate light curves: flux[pv][t] for every parameter vector and time --
+ * Eq. 5 for each exposure sub-sample, with the mean covered brightness
+ * interpolated in (k, g) from the tables of Sect. 3.1.2 (in g only for the
+ * direct model), averaged over the sub-exposures of Sect. 4.1; the orbit of
+ * the parameters of Sect. 4.1 (Keplerian, conjunction at T0); the passband of
+ * each time as in the heterogeneous series of Sect. 4.2.
  *   times        device, double[npt]: mid-exposure times
  *   pb_index     device, int32[npt]: passband of each time, 0 <= . < npb
  *                (NULL allowed when npb == 1)
@@ -208,14 +213,19 @@ rr_status rr_evaluate(rr_ctx* ctx, const double* times, const int32_t* pb_index,
  *     reads before reading it, so nothing needs clearing.
  *   - The first call on a device looks up the array's device address
  *     (cudaGetSymbolAddress, with that device made current); make that first
- *     call before any stream capture on that device.
+ *     call before any stream capture on that device.  The address is kept
+ *     for the life of the process: it does not survive cudaDeviceReset (or
+ *     any other teardown of the device's primary context), after which this
+ *     entry point must not be called.
  * Errors: as rr_evaluate, plus RR_EINVAL for oversize batches. */
 #define RR_NOALLOC_SCRATCH_BYTES (32u << 20)
 rr_status rr_evaluate_noalloc(rr_ctx* ctx, const double* times, const int32_t* pb_index, int32_t npt,
                               const double* params, int32_t npv, const int32_t* supersampling,
                               const double* exptime, void* flux, int32_t* pv_status, void* stream);
 
-/* Vector-Jacobian product of rr_evaluate (hand-written adjoint):
+/* Vector-Jacobian product of rr_evaluate (hand-written adjoint; the paper has
+ * no adjoint: this differentiates Eq. 5, the interpolants of Sect. 3.1.2 and
+ * the orbit of Sect. 4.1 by the chain rule):
  *   grad_params[pv][j] = sum_t grad_flux[pv][t] * d flux[pv][t] / d params[pv][j]
  * Same inputs as rr_evaluate, plus
  *   grad_flux    device, [npv][npt], float (MIXED) or double (FP64)

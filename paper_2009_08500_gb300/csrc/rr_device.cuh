@@ -286,7 +286,11 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
 // Stage `bytes` (multiple of 16) from global memory into shared memory with
 // one elected thread issuing the copy; every thread waits (bounded).  On a
 // timeout the device error word is set, the wait is retried once more
-// (bounded) so that no copy is left in flight, and false is returned.
+// (bounded) and false is returned: the CTA then leaves.  The copies are at
+// most 64 KB each from global memory, which a working GPU completes in
+// microseconds, so a copy still in flight after two waits of about a second
+// each means a device that has stopped making progress; the retry only gives
+// a slow copy its chance to land before the CTA's shared memory is released.
 __device__ __forceinline__ bool stage_to_smem(void* dst, const void* src, uint32_t bytes,
                                               uint64_t* bar, int* err) {
     if (threadIdx.x == 0) {

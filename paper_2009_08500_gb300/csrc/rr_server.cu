@@ -7,11 +7,16 @@
 // workspace: rr_request_bytes) fit in the memory budget; it takes that memory
 // from a stream-ordered pool on the request's stream, enqueues the request
 // (rr_enqueue_host), records an event, and returns the memory on the same
-// stream.  Completion is detected by polling the events; finished requests
-// are handed to rr_server_poll.  Work of requests admitted at different
-// times overlaps on the device; each request runs the same kernels as it
-// would alone, so its results do not depend on the others.
+// stream.  After the request's copies the context's device error word is
+// copied to a pinned word of the slot and cleared, so that a bounded device
+// wait that gave up inside the request is reported as its RR_ETIMEOUT.  A
+// host callback at the end of each request's stream work wakes the worker,
+// which then reaps finished requests (event queries) and hands them to
+// rr_server_poll.  Work of requests admitted at different times overlaps on
+// the device; each request runs the same kernels as it would alone, so its
+// results do not depend on the others.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -53,7 +58,8 @@ struct Request {
 struct Slot {
     cudaStream_t stream = nullptr;
     cudaEvent_t done = nullptr;
-    int64_t req = -1;   // request in flight, -1 = free
+    int64_t req = -1;          // request in flight, -1 = free
+    int* err_word = nullptr;   // pinned: the fit's device error word after the request
 };
 
 }  // namespace
@@ -70,11 +76,22 @@ struct rr_server {
     std::unordered_map<int64_t, Request> reqs;       // every request not yet released
     int64_t next_id = 0;
     bool stop = false;
+    std::atomic<bool> woken{false};                  // a request's stream work has ended (callback)
     std::thread worker;
     std::string err;
 };
 
 namespace {
+
+// Host callback enqueued after each request: wakes the worker.  It takes no
+// lock and makes no CUDA call (the worker may hold the lock inside CUDA calls);
+// a wake-up that comes between the worker's check and its wait is lost, and
+// the worker's bounded wait (1 ms) covers it.
+void CUDART_CB wake_worker(void* arg) {
+    rr_server* s = static_cast<rr_server*>(arg);
+    s->woken.store(true, std::memory_order_release);
+    s->cv_work.notify_one();
+}
 
 // Admit and launch queued requests while a slot and memory are free (lock held).
 void admit(rr_server* s) {
@@ -97,10 +114,20 @@ void admit(rr_server* s) {
                                        r.grad_flux, r.flux, r.grad, r.status, scratch, r.bytes > 0 ? r.bytes : 256,
                                        sl.stream);
             cudaFreeAsync(scratch, sl.stream);
+            // the fit's error word after the request, then cleared for the next one (a wait that
+            // gave up in another request of the same fit in flight at the same time is reported
+            // by whichever of them copies the word first)
+            *sl.err_word = 0;
+            if (r.result == RR_OK &&
+                (cudaMemcpyAsync(sl.err_word, r.fit->d_err, sizeof(int), cudaMemcpyDeviceToHost, sl.stream) !=
+                     cudaSuccess ||
+                 cudaMemsetAsync(r.fit->d_err, 0, sizeof(int), sl.stream) != cudaSuccess))
+                r.result = RR_ECUDA;
         } else {
             r.result = RR_ENOMEM;
         }
         if ((e = cudaEventRecord(sl.done, sl.stream)) != cudaSuccess && r.result == RR_OK) r.result = RR_ECUDA;
+        cudaLaunchHostFunc(sl.stream, wake_worker, s);
         s->used += r.bytes;
         sl.req = r.id;
     }
@@ -114,6 +141,7 @@ void reap(rr_server* s) {
         if (q == cudaErrorNotReady) continue;
         Request& r = s->reqs[sl.req];
         if (q != cudaSuccess && r.result == RR_OK) r.result = RR_ECUDA;
+        if (r.result == RR_OK && *sl.err_word != 0) r.result = RR_ETIMEOUT;
         r.t_done = now_ns();
         s->used -= r.bytes;
         s->finished.push_back(r.id);
@@ -143,10 +171,11 @@ void run(rr_server* s) {
                 continue;
             }
         }
-        // requests in flight: poll again shortly (the lock is free meanwhile)
-        lk.unlock();
-        std::this_thread::sleep_for(std::chrono::microseconds(20));
-        lk.lock();
+        // requests in flight: sleep until a request's callback (or at most 1 ms: the
+        // release time of the next queued request may come first)
+        s->cv_work.wait_for(lk, std::chrono::microseconds(1000),
+                            [s] { return s->woken.load(std::memory_order_acquire) || s->stop; });
+        s->woken.store(false, std::memory_order_relaxed);
     }
 }
 
@@ -175,11 +204,13 @@ extern "C" rr_status rr_server_create(int32_t device, int32_t slots, size_t mem_
     for (Slot& sl : s->slots) {
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaHostAlloc((void**)&sl.err_word, sizeof(int), cudaHostAllocDefault);
     }
     if (e != cudaSuccess) {
         for (Slot& sl : s->slots) {
             if (sl.stream) cudaStreamDestroy(sl.stream);
             if (sl.done) cudaEventDestroy(sl.done);
+            if (sl.err_word) cudaFreeHost(sl.err_word);
         }
         if (s->pool) cudaMemPoolDestroy(s->pool);
         delete s;
@@ -203,6 +234,7 @@ extern "C" rr_status rr_server_destroy(rr_server* s) {
         cudaStreamSynchronize(sl.stream);
         cudaStreamDestroy(sl.stream);
         cudaEventDestroy(sl.done);
+        cudaFreeHost(sl.err_word);
     }
     cudaMemPoolDestroy(s->pool);
     delete s;

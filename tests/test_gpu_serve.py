@@ -158,3 +158,26 @@ def test_native_server_release_time(fits):
     for r, out in ((reqs[0], out0), (reqs[1], out1)):
         f, g = _alone(fits, r)
         assert np.array_equal(out["flux"], f)
+
+
+def test_a_device_wait_that_gave_up_is_reported_by_the_request(fits):
+    """A bounded device wait that runs out (the failure self-test's queue-slot wait, on a flag that
+    nothing sets) sets the fit's error word; the next request of that fit through the server
+    reports RR_ETIMEOUT, and the word is cleared for the one after it."""
+    import torch
+    from paper_2009_08500_gb300 import rr
+    m, tmpl = fits["a"]
+    m.selftest_wait(1)
+    torch.cuda.synchronize()
+    wl = W.make_small(tmpl.ld_model, npv=3, npt=900, seed=5)
+
+    def req():
+        return ServeRequest(fit="a", times=wl.times, params=wl.params, pb_index=wl.pb_index,
+                            supersampling=wl.supersampling, exptime=wl.exptime)
+
+    with NativeServer({"a": m}, slots=2, mem_budget=1 << 30, device=m.device.index or 0) as srv:
+        with pytest.raises(rr.RRError) as ei:
+            srv.submit(req()).result(timeout=60)
+        assert ei.value.status == 6
+        out = srv.submit(req()).result(timeout=60)
+    assert out["flux"].shape == (3, 900) and np.all(out["pv_status"] == 0)

@@ -5,10 +5,13 @@ code running where CUDA allocation calls are not allowed, or an application
 that has handed all device memory to its own allocator); this entry point
 uses scratch memory that the library holds in a fixed array instead of a
 caller-provided workspace.  The test calls it through the C ABI twice in a
-row, on different inputs (so the second call runs over the first call's
-leftovers in the shared array), and compares each result with rr_evaluate
-within the tolerances of the other parity tests.  It sits in a file of its
-own that pytest collects last.
+row, on different inputs, the second batch smaller than the first (so the
+second call runs over the first call's leftovers in the shared array), and
+compares each result with rr_evaluate bitwise (the same kernels, on the
+fixed array instead of a workspace); it also checks that a call changes
+neither the device's free memory nor torch's allocated bytes.  The cases
+cover the interpolated and direct models and a batch of 8 passbands.  It
+sits in a file of its own that pytest collects last.
 """
 import ctypes
 
@@ -18,8 +21,6 @@ import pytest
 from paper_2009_08500_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
-
-TOL = {"fp64": 1e-12, "mixed": 1e-6}
 
 
 @pytest.fixture(scope="module")
@@ -43,11 +44,29 @@ def _call_noalloc(rr, m, t, pb, p, wl, out, status):
     return st
 
 
+def _cases(kind):
+    """Two batches for one model, the second smaller than the first (so that it runs over the
+    first call's leftovers in the shared array)."""
+    if kind == "interpolated":
+        return [W.make_small("quadratic_tri", npv=40, npt=3000, seed=3, ss=(5,), exptime=(0.01,)),
+                W.make_small("quadratic_tri", npv=7, npt=1100, seed=4)]
+    if kind == "direct":
+        return [W.make_small("quadratic", npv=30, npt=2500, seed=5, ss=(3,), exptime=(0.01,), direct=True),
+                W.make_small("quadratic", npv=6, npt=900, seed=6, direct=True)]
+    ss, ex = (1, 3, 5, 1, 3, 5, 1, 3), (0.0, 0.01, 0.02, 0.0, 0.01, 0.02, 0.0, 0.01)
+    first = W.make_small("tabulated", npv=24, npt=4000, npb=8, seed=7, ss=ss, exptime=ex)
+    second = W.make_small("tabulated", npv=5, npt=1500, npb=8, seed=8, ss=ss, exptime=ex)
+    second.profiles = first.profiles      # one model: the first batch's profiles
+    return [first, second]
+
+
 @pytest.mark.parametrize("precision", ["mixed", "fp64"])
-def test_noalloc_matches_evaluate_on_two_calls_in_a_row(rr, precision):
+@pytest.mark.parametrize("kind", ["interpolated", "direct", "8 passbands"])
+def test_noalloc_matches_evaluate_on_two_calls_in_a_row(rr, kind, precision):
+    """Bitwise the light curves of rr_evaluate (the same kernels on another scratch address), and
+    no allocation: the device's free memory and torch's allocated bytes unchanged by each call."""
     import torch
-    cases = [W.make_small("quadratic_tri", npv=40, npt=3000, seed=3, ss=(5,), exptime=(0.01,)),
-             W.make_small("quadratic_tri", npv=7, npt=1100, seed=4)]
+    cases = _cases(kind)
     m = None
     for wl in cases:
         wl.precision = precision
@@ -57,10 +76,17 @@ def test_noalloc_matches_evaluate_on_two_calls_in_a_row(rr, precision):
         ref = m.evaluate(t, p, pb, wl.supersampling, wl.exptime)
         out = torch.full_like(ref, -7.0)
         status = torch.full((wl.npv,), -1, dtype=torch.int32, device=t.device)
+        # the first call on the device looks up the array's address (and may load the module)
         assert _call_noalloc(rr, m, t, pb, p, wl, out, status) == 0, m.lib.rr_last_error(m._h)
         torch.cuda.synchronize()
+        out.fill_(-7.0)
+        status.fill_(-1)
+        free0, alloc0 = torch.cuda.mem_get_info()[0], torch.cuda.memory_allocated()
+        assert _call_noalloc(rr, m, t, pb, p, wl, out, status) == 0, m.lib.rr_last_error(m._h)
+        torch.cuda.synchronize()
+        assert torch.cuda.mem_get_info()[0] == free0 and torch.cuda.memory_allocated() == alloc0
         assert torch.all(status == 0)
-        assert (out.double() - ref.double()).abs().max().item() <= TOL[precision]
+        assert torch.equal(out, ref)
         assert (ref < 1).sum().item() > 50
 
 

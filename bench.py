@@ -765,6 +765,21 @@ def serving(a, local, seconds):
         pool.append(dict(fit=fi, times=pin(wl.times, np.float64), params=pin(wl.params, np.float64),
                          pb_index=pin(wl.pb_index, np.int32), supersampling=wl.supersampling, exptime=wl.exptime,
                          grad_flux=gbuf[:wl.npv * wl.npt].view(wl.npv, wl.npt) if grad else None))
+        pool[-1]["npoints"] = ServeRequest(**pool[-1]).points
+    # the client's pinned result buffers: a free list per pooled request, refilled when a
+    # request finishes; a new set is pinned only when every set of that request is in flight
+    free_out = [[] for _ in pool]
+
+    def out_set(k):
+        q = pool[k]
+        o = {"flux": torch.empty((q["params"].shape[0], q["times"].shape[0]), dtype=torch.float32).pin_memory(),
+             "status": torch.empty(q["params"].shape[0], dtype=torch.int32).pin_memory()}
+        if q["grad_flux"] is not None:
+            o["grad"] = torch.empty((q["params"].shape[0], models[q["fit"]].nparam), dtype=torch.float64).pin_memory()
+        return o
+
+    for k in range(len(pool)):
+        free_out[k].append(out_set(k))
     slots = 8
     # the client is a Python loop: keep the collector's full passes over the
     # set-up objects (torch, the request pool) out of its timing
@@ -775,7 +790,12 @@ def serving(a, local, seconds):
         return NativeServer(models, slots=slots, mem_budget=64 << 30, device=local)
 
     def mk(k):
-        return ServeRequest(**pool[k % len(pool)])
+        k %= len(pool)
+        fl = free_out[k]
+        o = fl.pop() if fl else out_set(k)
+        r = ServeRequest(**pool[k], out=o)
+        r.future.add_done_callback(lambda _f: fl.append(o))
+        return r
 
     # warm-up (pinned-memory caches, kernels)
     with server() as srv:
@@ -795,7 +815,7 @@ def serving(a, local, seconds):
             time.sleep(2e-4)
         srv.drain()
         closed = srv.stats()
-    mean_pts = float(np.mean([ServeRequest(**p).points for p in pool]))
+    mean_pts = float(np.mean([p["npoints"] for p in pool]))
     npool = len(pool)
     runs = []
     for load in (0.7, 0.7, 0.7, 1.1):
@@ -821,7 +841,7 @@ def serving(a, local, seconds):
     gc.unfreeze()
     at07 = sorted([r for r in runs if r["load"] == 0.7], key=lambda r: r["latency_p99_ms"])
     head = at07[len(at07) // 2]          # the run with the median p99
-    del pool, gbuf, models
+    del pool, gbuf, models, free_out
     gc.collect()
     torch.cuda.empty_cache()
     return {"value": head["points_per_s"], "unit": "points/s",

@@ -51,6 +51,12 @@ class ServeRequest:
     # schedule): it is not admitted earlier, and its latency counts from then
     # even when the submit call comes later
     t_intended: Optional[float] = None
+    # caller-owned pinned host result buffers {"flux", "status"[, "grad"]} of the request's
+    # shapes and types, written instead of buffers allocated on submit (a client that reuses its
+    # buffers); the caller leaves them alone until the future is done
+    out: Optional[dict] = None
+    # light-curve samples of the request, when the caller knows them; else counted on first use
+    npoints: Optional[int] = None
     # filled by the server
     id: int = -1
     nbytes: int = 0
@@ -71,11 +77,20 @@ class ServeRequest:
 
     @property
     def points(self) -> int:
-        if self.supersampling is None:
-            return self.npv * self.npt
-        ss = np.asarray(self.supersampling)
-        pb = np.zeros(self.npt, int) if self.pb_index is None else np.asarray(self.pb_index)
-        return int(self.npv * ss[pb].sum())
+        """npv x the sum over times of the supersampling factor of each time's passband (counted
+        once, and without a pass over the times when every passband has the same factor)."""
+        if self.npoints is None:
+            if self.supersampling is None:
+                per_pv = self.npt
+            else:
+                ss = np.asarray(self.supersampling, dtype=np.int64).reshape(-1)
+                if self.pb_index is None or ss.size == 1 or np.all(ss == ss[0]):
+                    per_pv = self.npt * int(ss[0])
+                else:
+                    counts = np.bincount(np.asarray(self.pb_index).reshape(-1), minlength=ss.size)
+                    per_pv = int(counts[:ss.size] @ ss)
+            self.npoints = self.npv * per_pv
+        return self.npoints
 
 
 @dataclass
@@ -146,6 +161,7 @@ class Server:
         req.nbytes = self.backend.nbytes(req)
         if req.nbytes > self.mem_budget:
             raise AdmissionError(f"request needs {req.nbytes} bytes, more than the {self.mem_budget}-byte budget")
+        req.points
         self.backend.prepare(req)
         with self._lock:
             if self._stop:
@@ -318,13 +334,24 @@ class CudaBackend(Backend):
                 return t if t.is_pinned() else t.pin_memory()
             return torch.from_numpy(np.ascontiguousarray(a, dt)).pin_memory()
 
+        given = req.out or {}
+
+        def result(name, shape, dt):
+            b = given.get(name)
+            if b is None:
+                return torch.empty(shape, dtype=dt, pin_memory=True)
+            if not (isinstance(b, torch.Tensor) and b.dtype == dt and tuple(b.shape) == shape
+                    and b.is_contiguous() and b.is_pinned()):
+                raise ValueError(f"out[{name!r}] must be a pinned contiguous {dt} tensor of shape {shape}")
+            return b
+
         h = {"t": pin(req.times, np.float64), "p": pin(req.params, np.float64),
              "pb": None if req.pb_index is None else pin(req.pb_index, np.int32),
-             "flux": torch.empty((req.npv, req.npt), dtype=m.dtype, pin_memory=True),
-             "status": torch.empty(req.npv, dtype=torch.int32, pin_memory=True), "g": None, "grad": None}
+             "flux": result("flux", (req.npv, req.npt), m.dtype),
+             "status": result("status", (req.npv,), torch.int32), "g": None, "grad": None}
         if req.grad_flux is not None:
             h["g"] = pin(req.grad_flux, np.float32 if m.precision == "mixed" else np.float64)
-            h["grad"] = torch.empty((req.npv, m.nparam), dtype=torch.float64, pin_memory=True)
+            h["grad"] = result("grad", (req.npv, m.nparam), torch.float64)
         req._host = h
 
     def launch(self, req: ServeRequest, slot: int):
@@ -409,6 +436,7 @@ class NativeServer:
         m = self.fits[req.fit]
         req.t_arrival = time.perf_counter()
         release = 0 if req.t_intended is None else max(1, int(req.t_intended * 1e9) + self._clock_off)
+        req.points
         self._backend.prepare(req)
         h = req._host
         ss = rr._host_array(req.supersampling, m.npb, np.int32, 1)

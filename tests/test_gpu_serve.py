@@ -123,6 +123,33 @@ def test_native_server_results_identical_alone_and_in_the_mix(fits, budget):
     assert stats["client_latency_p99_ms"] >= stats["latency_p50_ms"]
 
 
+def test_native_server_writes_caller_result_buffers(fits):
+    """Results land in the caller's pinned buffers when it passes them; a buffer of the wrong
+    shape or not pinned is refused at submit."""
+    import torch
+    reqs = _requests(fits, 4, seed=23)
+    with NativeServer({k: v[0] for k, v in fits.items()}, slots=2, mem_budget=8 << 30) as srv:
+        for r in reqs:
+            m = fits[r.fit][0]
+            r.out = {"flux": torch.full((r.npv, r.npt), -3.0, dtype=torch.float32).pin_memory(),
+                     "status": torch.full((r.npv,), -1, dtype=torch.int32).pin_memory()}
+            if r.grad_flux is not None:
+                r.out["grad"] = torch.zeros((r.npv, m.nparam), dtype=torch.float64).pin_memory()
+            out = srv.submit(r).result(timeout=60)
+            assert out["flux"].ctypes.data == r.out["flux"].data_ptr()
+            f, g = _alone(fits, r)
+            assert np.array_equal(r.out["flux"].numpy(), f) and not r.out["status"].any()
+            if g is not None:
+                assert np.array_equal(r.out["grad"].numpy(), g)
+        bad = _requests(fits, 1, seed=24)[0]
+        bad.out = {"flux": torch.empty((bad.npv, bad.npt + 1), dtype=torch.float32).pin_memory()}
+        with pytest.raises(ValueError):
+            srv.submit(bad)
+        bad.out = {"flux": torch.empty((bad.npv, bad.npt), dtype=torch.float32)}
+        with pytest.raises(ValueError):
+            srv.submit(bad)
+
+
 def test_native_server_rejects_oversize_requests(fits):
     from paper_2009_08500_gb300.serve import AdmissionError
     reqs = _requests(fits, 2, seed=3)

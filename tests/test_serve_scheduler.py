@@ -158,3 +158,17 @@ def test_request_is_not_admitted_before_its_arrival():
         st = srv.stats()
     rec = srv.completed[0]
     assert rec.t_admit >= t_due and st["latency_p50_ms"] < 60
+
+
+@pytest.mark.parametrize("ss,npb", [(None, 1), ((3,), 1), ((1, 5, 2), 3), ((4, 4, 4, 4), 4)])
+def test_request_points_is_the_sample_count(ss, npb):
+    """points = npv x the sum over times of the supersampling factor of each time's passband,
+    counted by brute force here; a caller-given count is used as it is."""
+    rng = np.random.default_rng(npb)
+    npv, npt = 7, 1001
+    pb = rng.integers(0, npb, npt).astype(np.int32)
+    r = ServeRequest(fit=0, times=np.zeros(npt), params=np.zeros((npv, 9)), pb_index=pb,
+                     supersampling=None if ss is None else np.array(ss, np.int32))
+    brute = npv * sum(1 if ss is None else ss[b] for b in pb)
+    assert r.points == brute
+    assert ServeRequest(fit=0, times=np.zeros(npt), params=np.zeros((npv, 9)), npoints=12).points == 12

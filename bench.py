@@ -643,10 +643,59 @@ def run_variant(a, wl, grad, local, dev, flush, **change):
             "note": f"same workload and step with {what}, one GPU"}
 
 
+def link_peaks(dev, nbytes=256 << 20):
+    """Pinned host <-> device copy rates (GB/s) of plain asynchronous copies: host to device,
+    device to host, and both at once on two streams; median of 7 after 3 warm-ups."""
+    import torch
+    h0 = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+    h1 = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+    d0 = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    d1 = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    s0, s1 = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
+
+    def rate(fn, moved):
+        v = []
+        for i in range(10):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s0)
+            s1.wait_event(e0)
+            fn()
+            j = torch.cuda.Event()
+            j.record(s1)
+            s0.wait_event(j)
+            e1.record(s0)
+            e1.synchronize()
+            if i >= 3:
+                v.append(moved / (e0.elapsed_time(e1) * 1e-3) / 1e9)
+        return float(statistics.median(v))
+
+    def h2d():
+        with torch.cuda.stream(s0):
+            d0.copy_(h0, non_blocking=True)
+
+    def d2h():
+        with torch.cuda.stream(s0):
+            h1.copy_(d1, non_blocking=True)
+
+    def both():
+        with torch.cuda.stream(s0):
+            d0.copy_(h0, non_blocking=True)
+        with torch.cuda.stream(s1):
+            h1.copy_(d1, non_blocking=True)
+
+    out = {"h2d_gbs": rate(h2d, nbytes), "d2h_gbs": rate(d2h, nbytes), "both_gbs": rate(both, 2 * nbytes),
+           "bytes_per_copy": nbytes, "how": "torch copy_ between pinned host and device tensors (one "
+                                            "cudaMemcpyAsync each), CUDA events, median of 7"}
+    del h0, h1, d0, d1
+    return out
+
+
 def run_e2e(a, model, wl, grad, dev):
-    """Same metric through the public host-buffer API (Model.evaluate_host): every step copies
-    the step's inputs from pinned host memory to the device and the results back, pipelined
-    over chunks of pvs on separate copy and compute streams."""
+    """Same metric through the public host-buffer API (Model.evaluate_host) on pinned host
+    buffers: every step the kernels read the step's inputs and write its results in host memory
+    over the host-device link (the library's in-place path), and the call returns once the
+    results are there.  Also reports the link's plain-copy rates and the e2e rate as a fraction
+    of the rate those copies would allow for the step's bytes."""
     import torch
     h_t = torch.as_tensor(wl.times, dtype=torch.float64).pin_memory()
     h_pb = torch.as_tensor(wl.pb_index, dtype=torch.int32).pin_memory()
@@ -674,8 +723,16 @@ def run_e2e(a, model, wl, grad, dev):
     for _ in range(n):
         step()                      # returns once the results are in host memory
     ms = (time.perf_counter() - t0) * 1e3 / n
+    link = link_peaks(dev)
+    # the fastest the step's bytes can cross the link by plain copies (either direction alone, or
+    # both together at the bidirectional rate)
+    bound_ms = 1e3 * max(bi / (link["h2d_gbs"] * 1e9), bo / (link["d2h_gbs"] * 1e9),
+                         (bi + bo) / (link["both_gbs"] * 1e9))
     return {"_ms": ms, "unit": "points/s", "h2d_bytes_per_step": int(bi), "d2h_bytes_per_step": int(bo),
-            "steps": n, "api": "Model.evaluate_host (pinned host buffers, pv chunks pipelined over 3 streams)"}
+            "steps": n, "api": "Model.evaluate_host on pinned host buffers (kernels read and write them in place "
+                               "over the host-device link)",
+            "path": model.host_path, "link": link, "copy_bound_ms_per_step": round(bound_ms, 4),
+            "frac_of_copy_bound": round(bound_ms / ms, 4)}
 
 
 # ----------------------------------------------------------------- reference arm
@@ -779,62 +836,81 @@ def serving(a, local, seconds):
         return o
 
     for k in range(len(pool)):
-        free_out[k].append(out_set(k))
+        free_out[k] += [out_set(k) for _ in range(6)]
     slots = 8
     # the client is a Python loop: keep the collector's full passes over the
-    # set-up objects (torch, the request pool) out of its timing
+    # set-up objects (torch, the request pool) out of its timing, and pause it
+    # during each timed window (it runs between windows)
     gc.collect()
     gc.freeze()
 
-    def server():
-        return NativeServer(models, slots=slots, mem_budget=64 << 30, device=local)
+    pinned_in_run = [0]
 
     def mk(k):
         k %= len(pool)
         fl = free_out[k]
+        if not fl:
+            pinned_in_run[0] += 1
         o = fl.pop() if fl else out_set(k)
         r = ServeRequest(**pool[k], out=o)
-        r.future.add_done_callback(lambda _f: fl.append(o))
+        r.future.add_done_callback(lambda _f: fl.append(o))   # the client does not read the results
         return r
 
-    # warm-up (pinned-memory caches, kernels)
-    with server() as srv:
-        for k in range(len(pool)):
-            srv.submit(mk(k))
+    def window(srv, fn):
         srv.drain()
-    # capacity: keep 2 x slots requests outstanding for `seconds`
-    with server() as srv:
-        t_end = time.perf_counter() + seconds
-        k = 0
-        outstanding = []
-        while time.perf_counter() < t_end:
-            outstanding = [f for f in outstanding if not f.done()]
-            while len(outstanding) < 2 * slots:
-                outstanding.append(srv.submit(mk(k)))
-                k += 1
-            time.sleep(2e-4)
-        srv.drain()
-        closed = srv.stats()
-    mean_pts = float(np.mean([p["npoints"] for p in pool]))
-    npool = len(pool)
-    runs = []
-    for load in (0.7, 0.7, 0.7, 1.1):
-        rate = load * closed["points_per_s"] / mean_pts
-        arr = np.cumsum(rng.exponential(1.0 / rate, size=int(rate * seconds) + 1))
-        with server() as srv:
-            # each request goes in up to `ahead` seconds before its arrival time and the
-            # library releases it then: the client's own jitter does not bunch arrivals
-            ahead = 0.02
-            t0 = time.perf_counter() + ahead
-            for ta in arr:
-                dt = t0 + ta - ahead - time.perf_counter()
-                if dt > 0:
-                    time.sleep(dt)
-                r = mk(int(rng.integers(0, len(pool))))
-                r.t_intended = t0 + ta
-                srv.submit(r)
+        gc.collect()
+        srv.reset_stats()
+        pinned_in_run[0] = 0
+        gc.disable()
+        try:
+            fn()
             srv.drain()
-            st = srv.stats()
+        finally:
+            gc.enable()
+        st = srv.stats()
+        st["client_buffer_sets_pinned_in_window"] = pinned_in_run[0]
+        return st
+
+    runs = []
+    # one long-lived server, as in serving: warm-up, capacity, then the open-loop windows
+    with NativeServer(models, slots=slots, mem_budget=64 << 30, device=local) as srv:
+        for k in range(2 * len(pool)):
+            srv.submit(mk(k))
+
+        def closed_loop():
+            # capacity: keep 4 x slots requests outstanding for `seconds`
+            t_end = time.perf_counter() + seconds
+            k = 0
+            outstanding = []
+            while time.perf_counter() < t_end:
+                outstanding = [f for f in outstanding if not f.done()]
+                while len(outstanding) < 4 * slots:
+                    outstanding.append(srv.submit(mk(k)))
+                    k += 1
+                time.sleep(2e-4)
+
+        closed = window(srv, closed_loop)
+        mean_pts = float(np.mean([p["npoints"] for p in pool]))
+        npool = len(pool)
+        for load in (0.7, 0.7, 0.7, 1.1):
+            rate = load * closed["points_per_s"] / mean_pts
+            arr = np.cumsum(rng.exponential(1.0 / rate, size=int(rate * seconds) + 1))
+            picks = rng.integers(0, len(pool), size=len(arr))
+
+            def open_loop():
+                # each request goes in up to `ahead` seconds before its arrival time and the
+                # library releases it then: the client's own jitter does not bunch arrivals
+                ahead = 0.005
+                t0 = time.perf_counter() + ahead
+                for ta, k in zip(arr, picks):
+                    dt = t0 + ta - ahead - time.perf_counter()
+                    if dt > 0:
+                        time.sleep(dt)
+                    r = mk(int(k))
+                    r.t_intended = t0 + ta
+                    srv.submit(r)
+
+            st = window(srv, open_loop)
             st["load"] = load
             st["rate_req_per_s"] = rate
             runs.append(st)
@@ -849,7 +925,13 @@ def serving(a, local, seconds):
                        "server": "rr_server (scheduler thread in the library)",
                        "request_pool": npool, "mean_points_per_request": mean_pts,
                        "client": "Python open-loop generator: Poisson arrival times, each request submitted up to "
-                                 "20 ms ahead and released by the library at its arrival time",
+                                 "5 ms ahead and released by the library at its arrival time; pinned result "
+                                 "buffers reused (6 sets per pooled request, pinned before the timed windows); the "
+                                 "client's garbage collector paused in each timed window",
+                       "server_lifetime": "one server for the warm-up, the capacity window and the open-loop windows",
+                       "deviations": "requests capped at 2^25 points (the stated log-uniform square reaches "
+                                     "4096 x 2e5 = 8.2e8 points); 96 requests drawn once from that distribution "
+                                     "and reused, picked at random for each arrival",
                        "serve_seconds": seconds},
             "capacity_closed_loop": closed,
             "latency_ms": {"p50": head["latency_p50_ms"], "p99": head["latency_p99_ms"],

@@ -49,7 +49,8 @@ typedef enum {
     RR_ECUDA = 3,     /* a CUDA runtime call or kernel launch failed */
     RR_ESTATE = 4,    /* call out of order (e.g. evaluate before rr_build_weights) */
     RR_EDOMAIN = 5,   /* a requested accuracy cannot be met (rr_choose_grid) */
-    RR_ETIMEOUT = 6   /* a bounded device-side wait gave up (see rr_last_error) */
+    RR_ETIMEOUT = 6,  /* a bounded device-side wait gave up (see rr_last_error) */
+    RR_EPAGEABLE = 7  /* a host buffer given to the server is not page-locked */
 } rr_status;
 
 /* Limb-darkening laws (Sect. 3.2.1, in their usual forms; all affine in their
@@ -279,10 +280,17 @@ rr_status rr_evaluate_grad_prepared(rr_ctx* ctx, const double* times, const int3
  * curves (Eq. 5 with the supersampling of Sect. 4.1) and, when grad_flux is
  * given, the adjoint of rr_evaluate_grad, for data that live in host memory.
  * The paper has no counterpart (its models take and return host arrays, with
- * the GPU model copying them whole).  The batch is cut into chunks of
- * chunk_pvs parameter vectors (0: npv / 8, at least 512); the copies of
- * chunk c to the device, the kernels of chunk c-1 and the copies of chunk
- * c-2 back to the host run on three streams of the context, so they overlap.
+ * the GPU model copying them whole).
+ *   In place: when every host array is page-locked memory mapped for the
+ *   device (cudaHostAlloc, cudaHostRegister on a unified address space;
+ *   both ends of each array are checked with cudaPointerGetAttributes), the
+ *   kernels read the inputs and write the results where they are, over the
+ *   host-device link, with no staging copies (the adjoint reads only the
+ *   cotangent rows of the samples that may transit); chunk_pvs is unused.
+ *   Staged: otherwise the batch is cut into chunks of chunk_pvs parameter
+ *   vectors (0: npv / 8, at least 512); the copies of chunk c to the device,
+ *   the kernels of chunk c-1 and the copies of chunk c-2 back to the host
+ *   run on three streams of the context, so they overlap.
  *   times, pb_index, params, supersampling, exptime   host, as rr_evaluate
  *   grad_flux    host, [npv][npt] float (MIXED) / double (FP64), or NULL
  *                (no adjoint; grad_params is then not written)
@@ -292,7 +300,8 @@ rr_status rr_evaluate_grad_prepared(rr_ctx* ctx, const double* times, const int3
  * Host arrays should be page-locked (cudaHostAlloc / cudaHostRegister):
  * copies from pageable memory are staged by the driver and do not overlap.
  * The call is synchronous: it returns when every result is in host memory.
- * The context keeps one device buffer for the chunks (grown when a call
+ * The context keeps one device buffer for the chunks or the in-place
+ * workspace (grown when a call
  * needs more, freed by rr_destroy) and three streams; calls on one context
  * must not overlap in time (as for every entry point).  Results are bitwise
  * those of rr_evaluate / rr_evaluate_grad on the whole batch.
@@ -304,14 +313,19 @@ rr_status rr_evaluate_host(rr_ctx* ctx, const double* times, const int32_t* pb_i
                            int32_t* pv_status, int32_t chunk_pvs);
 
 /* One request from host buffers, asynchronous (serving: many requests in
- * flight on different streams).  Enqueues on `stream`: the copies of the
- * host inputs into `scratch`, the evaluation (with one shared set-up and the
- * adjoint when grad_flux != NULL), and the copies of flux, pv_status and
- * grad_params back to host memory; returns once everything is enqueued.
+ * flight on different streams).  Enqueues on `stream` the evaluation (with
+ * one shared set-up and the adjoint when grad_flux != NULL) and returns once
+ * everything is enqueued.  In place, as rr_evaluate_host, when every host
+ * buffer is mapped page-locked memory (the kernels read and write them over
+ * the host-device link; scratch holds the workspace only); otherwise staged:
+ * copies of the host inputs into `scratch`, the kernels, and copies of
+ * flux, pv_status and grad_params back to host memory.
  * The paper has no counterpart.  Arguments as rr_evaluate_host, plus
  *   scratch      device, >= rr_request_bytes(ctx, npv, npt, with_grad)
- *                bytes, 256-byte aligned, owned by the caller and not to be
- *                reused until the stream has passed this request
+ *                bytes (in place, the workspace rr_workspace_bytes rounded
+ *                up to 256 bytes suffices), 256-byte aligned, owned by the
+ *                caller and not to be reused until the stream has passed
+ *                this request
  * Host buffers must be page-locked for the copies to be asynchronous, and
  * must stay untouched until the stream has passed the request (an event
  * recorded after the call tells when).  Results are bitwise those of
@@ -325,19 +339,23 @@ rr_status rr_enqueue_host(rr_ctx* ctx, const double* times, const int32_t* pb_in
 
 /* Continuous-batching server (no counterpart in the paper): a worker thread
  * in the library admits queued requests in arrival order whenever one of its
- * `slots` streams is free and the request's device bytes (rr_request_bytes)
- * fit in `mem_budget`; each admitted request is enqueued with
- * rr_enqueue_host on its own stream, with device memory from a stream-ordered
- * pool of the server; completion is detected by polling events.  Work of
+ * `slots` streams is free and the request's device bytes (its workspace,
+ * since a served request runs in place) fit in `mem_budget`; each admitted
+ * request is enqueued with rr_enqueue_host on its own stream, with device
+ * memory from a stream-ordered pool of the server; completion is detected
+ * by polling events.  Work of
  * requests admitted at different times overlaps on the device, and a
  * request's results are those it would have alone.
  *   - While a context is used by a server, no other thread may call the
  *     library with that context.
- *   - Host buffers: page-locked, untouched by the caller until the request
- *     is reported finished by rr_server_poll.
+ *   - Host buffers: page-locked and mapped for the device (cudaHostAlloc,
+ *     cudaHostRegister), untouched by the caller until the request is
+ *     reported finished by rr_server_poll.
  *   - rr_server_submit copies supersampling / exptime and returns the
  *     request id (>= 0), or a negative rr_status: -RR_EINVAL (arguments),
- *     -RR_ENOMEM (larger than the budget), -RR_ESTATE (server stopping).
+ *     -RR_EPAGEABLE (a host buffer, checked at both ends, is not page-locked
+ *     memory mapped for the device), -RR_ENOMEM (larger than the budget),
+ *     -RR_ESTATE (server stopping).
  *   - rr_server_submit_at is rr_server_submit with a release time: the
  *     request arrives at release_ns (rr_server_now_ns clock; 0 = now) and is
  *     not admitted before it.  Admission stays in submission order, so a
@@ -496,6 +514,14 @@ rr_status rr_profile_read(rr_ctx* ctx, int32_t kind, double* total_ms, int64_t* 
 #define RR_COUNT_KINDS 8
 rr_status rr_count_samples(rr_ctx* ctx, int32_t enable);
 rr_status rr_count_read(rr_ctx* ctx, int32_t kind, int64_t* counts, int32_t reset);
+
+/* How the last rr_evaluate_host / rr_enqueue_host call on the context ran:
+ * RR_HOST_IN_PLACE (the kernels read and wrote the mapped page-locked host
+ * buffers), RR_HOST_STAGED (copies through device buffers), or 0 (no such
+ * call yet, or ctx NULL).  Introspection only; no counterpart in the paper. */
+#define RR_HOST_IN_PLACE 1
+#define RR_HOST_STAGED 2
+int32_t rr_host_path(const rr_ctx* ctx);
 
 #ifdef __cplusplus
 }

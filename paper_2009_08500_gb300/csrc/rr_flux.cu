@@ -194,14 +194,14 @@ __global__ void __launch_bounds__(kBlock, 4) rr_flux_mixed_kernel(const double* 
         float fb[4];
         #pragma unroll
         for (int q = 0; q < 4; ++q) fb[q] = pbv[q] < L.npb ? 1.0f : nanf_;
-        const bool full = vec_store && (p0 + 3 < npt);
+        const bool full = (vec_store & 1) && (p0 + 3 < npt);
         float* out = flux + (size_t)pv0 * npt + p0;
         // the pvs of the tile that need no arithmetic
         unsigned rest = (npv_t >= 32 ? 0xffffffffu : ((1u << npv_t) - 1u)) & ~may;
-        if (vec_store && gs.full) {
+        if ((vec_store & 2) && gs.full) {
             // a whole 512-byte row segment per pv from a constant row in shared
             // memory, one bulk asynchronous store per lane (lane i: pv i); the
-            // addresses are 16-byte aligned (npt % 4 == 0, aligned flux)
+            // addresses are 16-byte aligned (npt % 4 == 0, aligned flux in device memory)
             if ((rest >> lane) & 1u) {
                 bulk_s2g(flux + (size_t)(pv0 + lane) * npt + (size_t)g * kWarpPts,
                          ((bad >> lane) & 1u) ? rowsnan : rows1, kWarpPts * sizeof(float), l2_pol);
@@ -314,7 +314,7 @@ __global__ void __launch_bounds__(kBlock, 4) rr_flux_mixed_kernel(const double* 
             __syncwarp();
         }
         if (bad && pv_status) atomicOr(pv_status + pv0 + i, RR_PV_KEPLER);
-        store4(flux + (size_t)(pv0 + i) * npt + p0, f, pbv, vec_store && (p0 + 3 < npt));
+        store4(flux + (size_t)(pv0 + i) * npt + p0, f, pbv, (vec_store & 1) && (p0 + 3 < npt));
     };
 
     // Warps below stream_warps first take the groups (the output stream) and
@@ -562,7 +562,8 @@ cudaError_t launch_flux(rr_ctx* c, const double* times, const int32_t* pb_index,
                                              : rr_flux_mixed_kernel<false, false, false>));
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        const int vec = (npt % 4 == 0) && (((uintptr_t)flux & 15u) == 0);
+        // bit 0: 16-byte stores; bit 1: bulk stores of constant rows (flux in device memory)
+        const int vec = (npt % 4 == 0) && (((uintptr_t)flux & 15u) == 0) ? (in_device_memory(flux) ? 3 : 1) : 0;
         kern<<<grid, kBlock, smem, s>>>(times, (const float2*)pts_dt, (const int32_t*)pts_pb,
                                         (const GroupInfo*)pts_grp, npt, npv, pbp, L,
                                         pv_tile, gpc, (const char*)records, rowsg, (float*)flux, pv_status, vec,

@@ -398,7 +398,7 @@ __global__ void __launch_bounds__(kBlock, 3) rr_grad_mixed_kernel(
                 // now (rows once per CTA), well before a warp claims the item
                 if (!((atomicOr(&tc->rows_pf, 1u << lane) >> lane) & 1u))
                     bulk_prefetch_l2(rowsg + (size_t)(pv0 + lane) * L.rows_bytes, (uint32_t)L.rows_bytes);
-                if (vec_g && gs.full)
+                if ((vec_g & 2) && gs.full)
                     bulk_prefetch_l2(gflux + (size_t)(pv0 + lane) * npt + (size_t)g * kWarpPts,
                                      kWarpPts * (uint32_t)sizeof(float));
             }
@@ -425,7 +425,7 @@ __global__ void __launch_bounds__(kBlock, 3) rr_grad_mixed_kernel(
         const float* gf = gflux + (size_t)(pv0 + i) * npt + p0;
         unsigned cand = 0;
         float gbq[4], gv[4];
-        if (vec_g && p0 + 3 < npt) {
+        if ((vec_g & 1) && p0 + 3 < npt) {
             const float4 v = __ldg(reinterpret_cast<const float4*>(gf));
             gv[0] = v.x; gv[1] = v.y; gv[2] = v.z; gv[3] = v.w;
         } else {
@@ -779,7 +779,9 @@ cudaError_t launch_grad(rr_ctx* c, const double* times, const int32_t* pb_index,
                                           vec_g, c->d_svtab, counts, (const int*)pts_ord,                     \
                                           pv_status, c->d_err);                                               \
     } while (0)
-        const int vec_g = (npt % 4 == 0) && (((uintptr_t)grad_flux & 15u) == 0);
+        // bit 0: 16-byte loads; bit 1: L2 prefetches of cotangent rows (grad_flux in device memory)
+        const int vec_g = (npt % 4 == 0) && (((uintptr_t)grad_flux & 15u) == 0)
+                              ? (in_device_memory(grad_flux) ? 3 : 1) : 0;
         unsigned long long* counts = c->d_counts ? c->d_counts + (size_t)RR_KERNEL_GRAD * RR_COUNT_KINDS : nullptr;
         if (c->counting) {
             if (dep) {

@@ -1,4 +1,15 @@
-// Host-buffer evaluation (rr_evaluate_host): the batch is cut into chunks of
+// Host-buffer evaluation (rr_evaluate_host, rr_enqueue_host).
+//
+// In place: when every caller buffer is page-locked host memory mapped for
+// the device (cudaHostAlloc, or registered memory, on a unified address
+// space), the kernels read the times, parameters and cotangent and write the
+// light curves, validity words and gradient where they are, over the
+// host-device link (NVLink-C2C on a Grace host): no staging copies, and the
+// adjoint reads only the cotangent rows of the (pv, group) items that may
+// transit.  The kernels keep the bulk asynchronous copy engine to device
+// memory and reach host memory with plain loads and stores.
+//
+// Staged (any other host memory): the batch is cut into chunks of
 // parameter vectors; chunk c's inputs are copied to the device on one stream
 // while chunk c-1 is evaluated on a second and chunk c-2's results are copied
 // back on a third, with three device slots per array, so both copy
@@ -43,6 +54,57 @@ cudaError_t ensure_pipe(rr_ctx* c, size_t bytes) {
 }  // namespace
 
 namespace rr {
+const void* mapped_host(const void* p, size_t bytes) {
+    if (!p || bytes == 0) return nullptr;
+    cudaPointerAttributes a, b;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess ||
+        cudaPointerGetAttributes(&b, (const char*)p + bytes - 1) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (a.type != cudaMemoryTypeHost || b.type != cudaMemoryTypeHost || !a.devicePointer || !b.devicePointer)
+        return nullptr;
+    if ((const char*)b.devicePointer - (const char*)a.devicePointer != (ptrdiff_t)(bytes - 1)) return nullptr;
+    return a.devicePointer;
+}
+}  // namespace rr
+
+namespace {
+
+}  // namespace
+
+namespace rr {
+InPlace map_in_place(const rr_ctx* c, const double* times, const int32_t* pb_index, int32_t npt,
+                     const double* params, int32_t npv, const void* grad_flux, void* flux, double* grad_params,
+                     int32_t* pv_status) {
+    InPlace m;
+    if (npt <= 0 || npv <= 0) return m;
+    const size_t es = c->cfg.precision == RR_PREC_FP64 ? sizeof(double) : sizeof(float);
+    const size_t np = (size_t)c->nparam, pts = (size_t)npv * npt;
+    if (!(m.t = (const double*)mapped_host(times, (size_t)npt * 8))) return m;
+    if (pb_index && !(m.pb = (const int32_t*)mapped_host(pb_index, (size_t)npt * 4))) return m;
+    if (!(m.p = (const double*)mapped_host(params, (size_t)npv * np * 8))) return m;
+    if (!(m.f = (void*)mapped_host(flux, pts * es))) return m;
+    if (pv_status && !(m.st = (int32_t*)mapped_host(pv_status, (size_t)npv * 4))) return m;
+    if (grad_flux) {
+        if (!(m.g = mapped_host(grad_flux, pts * es))) return m;
+        if (!(m.go = (double*)mapped_host(grad_params, (size_t)npv * np * 8))) return m;
+    }
+    m.ok = true;
+    return m;
+}
+
+// One evaluation (and adjoint) on the mapped buffers, enqueued on s.
+rr_status run_in_place(rr_ctx* c, const InPlace& m, int32_t npt, int32_t npv, const int32_t* ss,
+                       const double* exptime, void* ws, size_t ws_bytes, cudaStream_t s) {
+    if (!m.g) return rr_evaluate(c, m.t, m.pb, npt, m.p, npv, ss, exptime, m.f, m.st, ws, ws_bytes, s);
+    rr_status st = rr_prepare(c, m.t, m.pb, npt, m.p, npv, ss, exptime, m.st, ws, ws_bytes, s);
+    if (st == RR_OK) st = rr_evaluate_prepared(c, m.t, m.pb, npt, m.p, npv, ss, exptime, m.f, m.st, ws, ws_bytes, s);
+    if (st == RR_OK)
+        st = rr_evaluate_grad_prepared(c, m.t, m.pb, npt, m.p, npv, ss, exptime, m.g, m.go, m.st, ws, ws_bytes, s);
+    return st;
+}
+
 void release_host_pipe(rr_ctx* c) {
     for (int i = 0; i < 3; ++i)
         if (c->pipe.s[i]) cudaStreamDestroy(c->pipe.s[i]);
@@ -73,6 +135,22 @@ extern "C" rr_status rr_evaluate_host(rr_ctx* c, const double* times, const int3
     const bool f64 = c->cfg.precision == RR_PREC_FP64;
     const size_t es = f64 ? sizeof(double) : sizeof(float);
     const int np = c->nparam;
+    {
+        cudaError_t e = cudaSetDevice(c->cfg.device);
+        if (e != cudaSuccess) return pipe_fail(c, e, "rr_evaluate_host set-up");
+        const InPlace m = map_in_place(c, times, pb_index, npt, params, npv, grad_flux, flux, grad_params, pv_status);
+        c->host_path = m.ok ? RR_HOST_IN_PLACE : RR_HOST_STAGED;
+        if (m.ok) {
+            const size_t wsb = up256(rr_workspace_bytes(c, npv, npt, grad ? 1 : 0));
+            if ((e = ensure_pipe(c, wsb)) != cudaSuccess) return pipe_fail(c, e, "rr_evaluate_host set-up");
+            cudaStream_t s = c->pipe.s[1];
+            const rr_status st = run_in_place(c, m, npt, npv, ss, exptime, c->pipe.buf, wsb, s);
+            e = cudaStreamSynchronize(s);
+            if (st != RR_OK) return st;
+            if (e != cudaSuccess) return pipe_fail(c, e, "rr_evaluate_host");
+            return rr_sync_status(c, s);
+        }
+    }
     // default: 8 chunks, each large enough to fill the GPU on its own (small chunks
     // leave the kernels short of parallelism and pay the per-chunk launches)
     const int cp = chunk_pvs > 0 ? std::min(chunk_pvs, npv) : std::max(std::min(512, npv), (npv + 7) / 8);
@@ -200,6 +278,14 @@ extern "C" size_t rr_request_bytes(const rr_ctx* c, int32_t npv, int32_t npt, in
     return req_layout(c, npv, npt, with_grad != 0).total;
 }
 
+extern "C" int32_t rr_host_path(const rr_ctx* c) { return c ? c->host_path : 0; }
+
+namespace rr {
+size_t request_bytes_in_place(const rr_ctx* c, int npv, int npt, bool grad) {
+    return npv > 0 && npt > 0 ? req_layout(c, npv, npt, grad).ws_bytes : req_layout(c, npv, npt, grad).total;
+}
+}  // namespace rr
+
 extern "C" rr_status rr_enqueue_host(rr_ctx* c, const double* times, const int32_t* pb_index, int32_t npt,
                                      const double* params, int32_t npv, const int32_t* ss, const double* exptime,
                                      const void* grad_flux, void* flux, double* grad_params, int32_t* pv_status,
@@ -217,10 +303,16 @@ extern "C" rr_status rr_enqueue_host(rr_ctx* c, const double* times, const int32
         return RR_EINVAL;
     }
     const ReqLayout L = req_layout(c, npv, npt, grad);
-    if (!scratch || scratch_bytes < L.total || ((uintptr_t)scratch & 255u)) {
+    cudaError_t e = cudaSetDevice(c->cfg.device);
+    if (e != cudaSuccess) return pipe_fail(c, e, "rr_enqueue_host");
+    const InPlace m = map_in_place(c, times, pb_index, npt, params, npv, grad_flux, flux, grad_params, pv_status);
+    // in place, the scratch holds the workspace only
+    if (!scratch || scratch_bytes < (m.ok ? L.ws_bytes : L.total) || ((uintptr_t)scratch & 255u)) {
         c->err = "rr_enqueue_host: scratch too small or not 256-byte aligned";
         return RR_EINVAL;
     }
+    c->host_path = m.ok ? RR_HOST_IN_PLACE : RR_HOST_STAGED;
+    if (m.ok) return run_in_place(c, m, npt, npv, ss, exptime, scratch, L.ws_bytes, (cudaStream_t)stream);
     const size_t es = c->cfg.precision == RR_PREC_FP64 ? sizeof(double) : sizeof(float);
     const int np = c->nparam;
     char* b = (char*)scratch;
@@ -233,8 +325,7 @@ extern "C" rr_status rr_enqueue_host(rr_ctx* c, const double* times, const int32
     void* d_g = b + L.g;
     double* d_go = (double*)(b + L.go);
     cudaStream_t s = (cudaStream_t)stream;
-    cudaError_t e = cudaSetDevice(c->cfg.device);
-    if (e == cudaSuccess && npt > 0) e = cudaMemcpyAsync(d_t, times, (size_t)npt * 8, cudaMemcpyHostToDevice, s);
+    if (npt > 0) e = cudaMemcpyAsync(d_t, times, (size_t)npt * 8, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess && d_pb && npt > 0) e = cudaMemcpyAsync(d_pb, pb_index, (size_t)npt * 4, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_p, params, (size_t)npv * np * 8, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess && grad && npt > 0)

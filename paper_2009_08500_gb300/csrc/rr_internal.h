@@ -231,6 +231,7 @@ struct rr_ctx {
     float4* d_svtab = nullptr;   // kSvTabLen entries (mixed form): sin and 1 - cos as float pairs
     unsigned long long* d_counts = nullptr;   // RR_KERNEL_KINDS x RR_COUNT_KINDS sample counters
     bool counting = false;
+    int host_path = 0;   // RR_HOST_IN_PLACE / RR_HOST_STAGED of the last host-buffer call
     // direct model: FP32 copies of the edges and profiles, and per basis the
     // running sums P[b][m] = sum_{j<m} pi (ze[j+1]^2 - ze[j]^2) l_b[j]
     float* d_zef = nullptr;      // nz + 1
@@ -320,6 +321,44 @@ cudaError_t launch_grad(rr_ctx* c, const double* times, const int32_t* pb_index,
                         const void* grad_flux, void* partials, int32_t* pv_status, cudaStream_t s);
 // time chunks of the FP32 per-point kernels
 inline int time_chunks(int npt, int gpc) { return ((npt + kWarpPts - 1) / kWarpPts + gpc - 1) / gpc; }
+// Whether p is device memory.  A caller's buffer may also be page-locked host memory, which the
+// kernels reach in place over the host link with plain loads and stores; the bulk asynchronous
+// copy engine (stores from shared memory, L2 prefetches) is used on device memory only.
+// The device address of a caller's buffer [p, p + bytes) when it is page-locked host memory
+// that kernels on the current device can reach in place (both ends mapped, in one mapping);
+// nullptr otherwise.
+const void* mapped_host(const void* p, size_t bytes);
+// Device scratch of one request whose host buffers are all mapped page-locked memory (the
+// workspace alone; rr_request_bytes is the staged figure).
+size_t request_bytes_in_place(const rr_ctx* c, int npv, int npt, bool grad);
+// Device addresses of every caller buffer of one evaluation, when all of them are mapped
+// page-locked memory (ok; looked up for the current device); a batch with no times or no pvs
+// is staged.
+struct InPlace {
+    const double* t = nullptr;
+    const int32_t* pb = nullptr;
+    const double* p = nullptr;
+    const void* g = nullptr;
+    void* f = nullptr;
+    double* go = nullptr;
+    int32_t* st = nullptr;
+    bool ok = false;
+};
+InPlace map_in_place(const rr_ctx* c, const double* times, const int32_t* pb_index, int32_t npt,
+                     const double* params, int32_t npv, const void* grad_flux, void* flux, double* grad_params,
+                     int32_t* pv_status);
+// One evaluation (with the adjoint when m.g is set) on mapped buffers, enqueued on s; ws is a
+// device workspace of ws_bytes >= rr_workspace_bytes.
+rr_status run_in_place(rr_ctx* c, const InPlace& m, int32_t npt, int32_t npv, const int32_t* ss,
+                       const double* exptime, void* ws, size_t ws_bytes, cudaStream_t s);
+inline bool in_device_memory(const void* p) {
+    cudaPointerAttributes a;
+    if (!p || cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice;
+}
 cudaError_t launch_grad_reduce(rr_ctx* c, int npt, const double* params, int npv, const void* records,
                                const void* partials, double* grad_params, cudaStream_t s);
 size_t records_bytes(const rr_ctx* c, int npv, bool grad);

@@ -2,19 +2,24 @@
 //
 // Requests (one fit's light curves for a batch of parameter vectors, host
 // buffers, optionally with a cotangent for the adjoint) are queued by any
-// host thread.  The worker admits them in arrival order whenever one of the
-// server's streams is free and the request's device bytes (inputs, outputs,
-// workspace: rr_request_bytes) fit in the memory budget; it takes that memory
-// from a stream-ordered pool on the request's stream, enqueues the request
-// (rr_enqueue_host), records an event, and returns the memory on the same
-// stream.  After the request's copies the context's device error word is
-// copied to a pinned word of the slot and cleared, so that a bounded device
-// wait that gave up inside the request is reported as its RR_ETIMEOUT.  A
-// host callback at the end of each request's stream work wakes the worker,
-// which then reaps finished requests (event queries) and hands them to
-// rr_server_poll.  Work of requests admitted at different times overlaps on
-// the device; each request runs the same kernels as it would alone, so its
-// results do not depend on the others.
+// host thread; the buffers must be page-locked memory mapped for the device,
+// and their device addresses are looked up once, at submission.  The worker
+// admits requests in arrival order whenever one of the server's streams is
+// free and the request's device bytes (its workspace: the kernels read and
+// write the host buffers in place) fit in the memory budget; it takes that
+// memory from a stream-ordered pool on the request's stream (the pool keeps
+// up to the budget, and reserves min(budget, 1 GiB) at creation), enqueues
+// the request's kernels, records an event, and returns the memory on the
+// same stream.  The choice of request and slot is made under the server's
+// lock, the CUDA calls outside it.  After the request's kernels a one-thread
+// kernel moves the context's device error word into a mapped word of the
+// slot and clears it, so that a bounded device wait that gave up inside the
+// request is reported as its RR_ETIMEOUT.  A host callback at the end of
+// each request's stream work wakes the worker, which then reaps finished
+// requests (event queries) and hands them to rr_server_poll.  Work of
+// requests admitted at different times overlaps on the device; each request
+// runs the same kernels as it would alone, so its results do not depend on
+// the others.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -50,6 +55,7 @@ struct Request {
     double* grad = nullptr;
     int32_t* status = nullptr;
     size_t bytes = 0;
+    rr::InPlace in_place;      // the buffers' device addresses (all mapped page-locked memory)
     // t_arrival: the release time (not admitted before it), else the submit call
     int64_t t_arrival = 0, t_admit = 0, t_done = 0;
     int32_t result = RR_OK;
@@ -93,12 +99,44 @@ void CUDART_CB wake_worker(void* arg) {
     s->cv_work.notify_one();
 }
 
-// Admit and launch queued requests while a slot and memory are free (lock held).
-void admit(rr_server* s) {
-    const int64_t now = now_ns();
+// The fit's device error word after a request, into the slot's mapped host word, and cleared
+// for the next request (a wait that gave up in another request of the same fit in flight at the
+// same time is reported by whichever of them takes the word first).
+__global__ void take_error_kernel(int* dev_word, int* host_word) { *host_word = atomicExch(dev_word, 0); }
+
+// Enqueue one admitted request on its slot's stream (lock not held).
+void enqueue(rr_server* s, Request& r, Slot& sl) {
+    void* scratch = nullptr;
+    const size_t bytes = r.bytes > 0 ? r.bytes : 256;
+    cudaError_t e = cudaMallocFromPoolAsync(&scratch, bytes, s->pool, sl.stream);
+    if (e == cudaSuccess) {
+        r.result = r.in_place.ok
+                       ? rr::run_in_place(r.fit, r.in_place, r.npt, r.npv, r.ss.data(), r.exptime.data(), scratch,
+                                          bytes, sl.stream)
+                       : rr_enqueue_host(r.fit, r.times, r.pb, r.npt, r.params, r.npv, r.ss.data(),
+                                         r.exptime.data(), r.grad_flux, r.flux, r.grad, r.status, scratch, bytes,
+                                         sl.stream);
+        cudaFreeAsync(scratch, sl.stream);
+        *sl.err_word = 0;
+        if (r.result == RR_OK) {
+            take_error_kernel<<<1, 1, 0, sl.stream>>>(r.fit->d_err, sl.err_word);
+            if (cudaGetLastError() != cudaSuccess) r.result = RR_ECUDA;
+        }
+    } else {
+        r.result = RR_ENOMEM;
+    }
+    if ((e = cudaEventRecord(sl.done, sl.stream)) != cudaSuccess && r.result == RR_OK) r.result = RR_ECUDA;
+    cudaLaunchHostFunc(sl.stream, wake_worker, s);
+}
+
+// Admit and launch queued requests while a slot and memory are free.  The choice is made under
+// the lock; the CUDA calls that enqueue a request run without it, so that submissions and polls
+// do not wait for them (only this thread touches the slots, and an admitted request stays in
+// `reqs` until it has been reported finished).
+void admit(rr_server* s, std::unique_lock<std::mutex>& lk) {
     while (!s->queue.empty()) {
         Request& r = s->reqs[s->queue.front()];
-        if (r.t_arrival > now) break;                     // in order: not released yet
+        if (r.t_arrival > now_ns()) break;                // in order: not released yet
         if (s->used + r.bytes > s->budget) break;        // in order: wait for memory
         int slot = -1;
         for (size_t i = 0; i < s->slots.size(); ++i)
@@ -107,29 +145,11 @@ void admit(rr_server* s) {
         s->queue.pop_front();
         Slot& sl = s->slots[slot];
         r.t_admit = now_ns();
-        void* scratch = nullptr;
-        cudaError_t e = cudaMallocFromPoolAsync(&scratch, r.bytes > 0 ? r.bytes : 256, s->pool, sl.stream);
-        if (e == cudaSuccess) {
-            r.result = rr_enqueue_host(r.fit, r.times, r.pb, r.npt, r.params, r.npv, r.ss.data(), r.exptime.data(),
-                                       r.grad_flux, r.flux, r.grad, r.status, scratch, r.bytes > 0 ? r.bytes : 256,
-                                       sl.stream);
-            cudaFreeAsync(scratch, sl.stream);
-            // the fit's error word after the request, then cleared for the next one (a wait that
-            // gave up in another request of the same fit in flight at the same time is reported
-            // by whichever of them copies the word first)
-            *sl.err_word = 0;
-            if (r.result == RR_OK &&
-                (cudaMemcpyAsync(sl.err_word, r.fit->d_err, sizeof(int), cudaMemcpyDeviceToHost, sl.stream) !=
-                     cudaSuccess ||
-                 cudaMemsetAsync(r.fit->d_err, 0, sizeof(int), sl.stream) != cudaSuccess))
-                r.result = RR_ECUDA;
-        } else {
-            r.result = RR_ENOMEM;
-        }
-        if ((e = cudaEventRecord(sl.done, sl.stream)) != cudaSuccess && r.result == RR_OK) r.result = RR_ECUDA;
-        cudaLaunchHostFunc(sl.stream, wake_worker, s);
         s->used += r.bytes;
         sl.req = r.id;
+        lk.unlock();
+        enqueue(s, r, sl);
+        lk.lock();
     }
 }
 
@@ -155,7 +175,7 @@ void run(rr_server* s) {
     std::unique_lock<std::mutex> lk(s->mu);
     while (true) {
         reap(s);
-        admit(s);
+        admit(s, lk);
         bool busy = false;
         for (const Slot& sl : s->slots) busy = busy || sl.req >= 0;
         if (s->stop && !busy && s->queue.empty()) return;
@@ -206,6 +226,15 @@ extern "C" rr_status rr_server_create(int32_t device, int32_t slots, size_t mem_
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaHostAlloc((void**)&sl.err_word, sizeof(int), cudaHostAllocDefault);
     }
+    if (e == cudaSuccess) {
+        // reserve min(budget, 1 GiB) of pool memory now, so that the first requests do not wait
+        // for the pool to grow (it keeps what it holds, up to the budget)
+        void* p = nullptr;
+        const size_t reserve = std::min<size_t>(mem_budget, (size_t)1 << 30);
+        e = cudaMallocFromPoolAsync(&p, reserve, s->pool, s->slots[0].stream);
+        if (e == cudaSuccess) e = cudaFreeAsync(p, s->slots[0].stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s->slots[0].stream);
+    }
     if (e != cudaSuccess) {
         for (Slot& sl : s->slots) {
             if (sl.stream) cudaStreamDestroy(sl.stream);
@@ -243,6 +272,14 @@ extern "C" rr_status rr_server_destroy(rr_server* s) {
 
 extern "C" int64_t rr_server_now_ns(void) { return now_ns(); }
 
+namespace {
+
+// [p, p + bytes) in page-locked host memory mapped for the device (both ends):
+// the kernels of a served request read and write its buffers in place.
+bool page_locked(const void* p, size_t bytes) { return !p || bytes == 0 || rr::mapped_host(p, bytes) != nullptr; }
+
+}  // namespace
+
 extern "C" int64_t rr_server_submit_at(rr_server* s, rr_ctx* fit, const double* times, const int32_t* pb_index,
                                        int32_t npt, const double* params, int32_t npv, const int32_t* ss,
                                        const double* exptime, const void* grad_flux, void* flux,
@@ -250,7 +287,30 @@ extern "C" int64_t rr_server_submit_at(rr_server* s, rr_ctx* fit, const double* 
     if (!s || !fit || !ss || !exptime || npt < 0 || npv < 0 || (npv > 0 && !params) ||
         (npv > 0 && npt > 0 && (!times || !flux)) || (grad_flux && !grad_params) || release_ns < 0)
         return -RR_EINVAL;
+    rr::InPlace in_place;
+    if (npv > 0) {
+        // the mapping is looked up for the fit's device, current on this thread for the check only
+        // (cudaSetDevice also binds the device's context to a thread that has made no CUDA call
+        // yet; without one, no device address is reported)
+        int prev = -1;
+        if (cudaGetDevice(&prev) != cudaSuccess || cudaSetDevice(fit->cfg.device) != cudaSuccess) {
+            cudaGetLastError();
+            return -RR_ECUDA;
+        }
+        struct Restore {
+            int d, now;
+            ~Restore() {
+                if (d != now) cudaSetDevice(d);
+            }
+        } restore{prev, fit->cfg.device};
+        // a request with times runs in place; one without (validity words only) is staged
+        in_place = rr::map_in_place(fit, times, pb_index, npt, params, npv, grad_flux, flux, grad_params, pv_status);
+        if (npt > 0 ? !in_place.ok
+                    : !page_locked(params, (size_t)npv * fit->nparam * 8) || !page_locked(pv_status, (size_t)npv * 4))
+            return -RR_EPAGEABLE;
+    }
     Request r;
+    r.in_place = in_place;
     r.fit = fit;
     r.times = times;
     r.pb = pb_index;
@@ -263,7 +323,7 @@ extern "C" int64_t rr_server_submit_at(rr_server* s, rr_ctx* fit, const double* 
     r.flux = flux;
     r.grad = grad_params;
     r.status = pv_status;
-    r.bytes = rr_request_bytes(fit, npv, npt, grad_flux ? 1 : 0);
+    r.bytes = rr::request_bytes_in_place(fit, npv, npt, grad_flux != nullptr);
     if (r.bytes > s->budget) return -RR_ENOMEM;
     r.t_arrival = release_ns > 0 ? release_ns : now_ns();
     int64_t id;

@@ -22,7 +22,7 @@ LD_MODELS = {"uniform": 0, "quadratic": 1, "quadratic_tri": 2, "nonlinear": 3, "
              "general": 6, "logarithmic": 7, "exponential": 8, "power2": 9, "power2_pm": 10}
 PRECISIONS = {"fp64": 0, "mixed": 1}
 STATUS = {0: "RR_OK", 1: "RR_EINVAL", 2: "RR_ENOMEM", 3: "RR_ECUDA", 4: "RR_ESTATE", 5: "RR_EDOMAIN",
-          6: "RR_ETIMEOUT"}
+          6: "RR_ETIMEOUT", 7: "RR_EPAGEABLE"}
 TABLES = {"ze": 0, "zm": 1, "mu": 2, "weights": 3, "basis": 4, "istar": 5, "proj": 6}
 
 PV_K_RANGE, PV_E_RANGE, PV_B_RANGE, PV_P_RANGE = 1, 2, 4, 8
@@ -35,7 +35,7 @@ EXPORTS = ["rr_create", "rr_destroy", "rr_set_ld_profile", "rr_build_weights", "
            "rr_evaluate_noalloc", "rr_prepare", "rr_evaluate_prepared", "rr_evaluate_grad_prepared",
            "rr_evaluate_host", "rr_request_bytes", "rr_enqueue_host", "rr_server_create", "rr_server_destroy",
            "rr_server_submit", "rr_server_submit_at", "rr_server_now_ns", "rr_server_poll", "rr_server_pending", "rr_exact_flux", "rr_choose_grid",
-           "rr_selftest_wait", "rr_count_samples", "rr_count_read"]
+           "rr_selftest_wait", "rr_count_samples", "rr_count_read", "rr_host_path"]
 KERNELS = {"ld_basis": 0, "weights": 1, "pv_setup": 2, "flux": 3, "grad": 4, "grad_reduce": 5, "points": 6,
            "direct": 7}
 #: sample counters of the counting form (include/rr.h RR_COUNT_*)
@@ -102,6 +102,15 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     L.rr_server_poll.restype = i32
     L.rr_server_pending.argtypes = [vp]
     L.rr_server_pending.restype = i32
+    # the server's submission and clock through a handle that keeps the GIL during the call:
+    # they take microseconds and never block for long, and releasing and retaking the GIL
+    # around them costs more than the call when other Python threads are busy
+    H = ctypes.PyDLL(path)
+    H.rr_server_submit_at.argtypes = L.rr_server_submit_at.argtypes
+    H.rr_server_submit_at.restype = i64
+    H.rr_server_now_ns.argtypes = []
+    H.rr_server_now_ns.restype = i64
+    L.held = H
     L.rr_read_table.argtypes = [vp, i32, dp, i64]
     L.rr_read_table.restype = i64
     L.rr_sync_status.argtypes = [vp, vp]
@@ -115,6 +124,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     L.rr_selftest_wait.argtypes = [vp, i32, vp]
     L.rr_count_samples.argtypes = [vp, i32]
     L.rr_count_read.argtypes = [vp, i32, ctypes.POINTER(i64), i32]
+    L.rr_host_path.argtypes = [vp]
+    L.rr_host_path.restype = i32
     L.rr_choose_grid.argtypes = [ctypes.POINTER(RRConfig), dp, i32, dp, dp, dp, i32, ctypes.c_double, dp]
     for name in ("rr_exact_flux", "rr_choose_grid", "rr_selftest_wait", "rr_create", "rr_destroy", "rr_set_ld_profile", "rr_build_weights", "rr_evaluate",
                  "rr_evaluate_grad", "rr_sync_status", "rr_profile", "rr_profile_read", "rr_evaluate_noalloc",
@@ -274,6 +285,11 @@ class Model:
         self._check(self.lib.rr_count_read(self._h, KERNELS[kind], buf, int(reset)))
         return dict(zip(COUNTS, buf))
 
+    @property
+    def host_path(self) -> str:
+        """How the last evaluate_host / enqueue_host call ran: 'in place', 'staged' or 'none'."""
+        return {1: "in place", 2: "staged"}.get(int(self.lib.rr_host_path(self._h)), "none")
+
     def sync_status(self, stream=None):
         self._check(self.lib.rr_sync_status(self._h, _stream_handle(stream)))
 
@@ -384,12 +400,13 @@ class Model:
                       chunk_pvs: Optional[int] = None, out=None, grad_out=None, status_out=None):
         """Host arrays in, host arrays out: (flux, grad_params or None, pv_status) (rr_evaluate_host).
 
-        The library cuts the batch into chunks of pvs and overlaps the copies
-        to the device, the kernels and the copies back on three streams.
-        Results are bitwise those of one :meth:`evaluate` / :meth:`evaluate_grad`
-        call on the whole batch.  Inputs not in pinned memory are first copied
-        to pinned memory; out / grad_out / status_out are optional pinned CPU
-        tensors for the results.
+        Inputs not in pinned memory are first copied to pinned memory, and the
+        kernels then read and write the pinned buffers in place over the
+        host-device link (the library's staged path, chunks of pvs with copies
+        overlapped on three streams, serves other host memory through the C
+        ABI).  Results are bitwise those of one :meth:`evaluate` /
+        :meth:`evaluate_grad` call on the whole batch.  out / grad_out /
+        status_out are optional pinned CPU tensors for the results.
         """
         def pinned(x, dt):
             t = x if isinstance(x, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(x))

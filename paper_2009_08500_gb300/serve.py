@@ -422,7 +422,7 @@ class NativeServer:
         best = None
         for _ in range(7):
             a = time.perf_counter_ns()
-            n = self.lib.rr_server_now_ns()
+            n = self.lib.held.rr_server_now_ns()
             b = time.perf_counter_ns()
             if best is None or b - a < best[0]:
                 best = (b - a, n - (a + b) // 2)
@@ -432,32 +432,75 @@ class NativeServer:
         """Queue a request.  With req.t_intended (time.perf_counter() seconds) the
         request arrives then: the library does not admit it earlier, and its
         latency counts from that time even when the submit call comes later."""
-        ctypes, rr = self.ctypes, self.rr
+        rr = self.rr
         m = self.fits[req.fit]
         req.t_arrival = time.perf_counter()
         release = 0 if req.t_intended is None else max(1, int(req.t_intended * 1e9) + self._clock_off)
         req.points
-        self._backend.prepare(req)
-        h = req._host
-        ss = rr._host_array(req.supersampling, m.npb, np.int32, 1)
-        ex = rr._host_array(req.exptime, m.npb, np.float64, 0.0)
+        ss = self._small(req.supersampling, m.npb, np.int32, 1)
+        ex = self._small(req.exptime, m.npb, np.float64, 0.0)
         req._ssex = (ss, ex)
+        # torch CPU tensors of the right type and layout go to the library as they are (it checks that
+        # they are page-locked); anything else, or a buffer the library finds pageable, is copied into
+        # pinned memory first
+        h = self._as_given(req, m)
+        rid = -7 if h is None else self._submit_c(req, m, h, ss, ex, release)
+        if rid == -7:
+            self._backend.prepare(req)
+            h = req._host
+            rid = self._submit_c(req, m, h, ss, ex, release)
+        if rid < 0:
+            if -rid == 2:
+                raise AdmissionError(f"request larger than the {self.mem_budget}-byte budget")
+            raise rr.RRError(-rid, "rr_server_submit rejected the request")
+        return req.future
+
+    @staticmethod
+    def _small(x, n, dtype, default):
+        if type(x) is np.ndarray and x.dtype == dtype and x.shape == (n,) and x.flags.c_contiguous:
+            return x
+        return np.ascontiguousarray(np.broadcast_to(np.asarray(default if x is None else x, dtype=dtype), (n,)))
+
+    def _as_given(self, req, m):
+        """The request's host buffers without conversion, or None when one needs converting."""
+        torch = self.torch
+        T = torch.Tensor
+
+        def ok(a, dt, shape):
+            return (type(a) is T and a.dtype == dt and a.device.type == "cpu" and a.is_contiguous()
+                    and tuple(a.shape) == shape)
+
+        npv, npt = req.npv, req.npt
+        out = req.out or {}
+        h = {"t": req.times, "p": req.params, "pb": req.pb_index, "g": req.grad_flux,
+             "flux": out.get("flux"), "status": out.get("status"), "grad": out.get("grad")}
+        if not (ok(h["t"], torch.float64, (npt,)) and ok(h["p"], torch.float64, (npv, m.nparam))
+                and (h["pb"] is None or ok(h["pb"], torch.int32, (npt,)))
+                and ok(h["flux"], m.dtype, (npv, npt)) and ok(h["status"], torch.int32, (npv,))):
+            return None
+        if req.grad_flux is None:
+            h["grad"] = None
+        elif not (ok(h["g"], m.dtype, (npv, npt)) and ok(h["grad"], torch.float64, (npv, m.nparam))):
+            return None
+        req._host = h
+        return h
+
+    def _submit_c(self, req, m, h, ss, ex, release):
+        ctypes, rr = self.ctypes, self.rr
         with self._lock:
             if self._stop:
                 raise RuntimeError("server is stopped")
-            rid = self.lib.rr_server_submit_at(self._h, m._h, rr._ptr(h["t"]), rr._ptr(h["pb"]), req.npt,
-                                               rr._ptr(h["p"]), req.npv,
-                                               ss.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
-                                               ex.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), rr._ptr(h["g"]),
-                                               rr._ptr(h["flux"]), rr._ptr(h["grad"]), rr._ptr(h["status"]), release)
-            if rid < 0:
-                if -rid == 2:
-                    raise AdmissionError(f"request larger than the {self.mem_budget}-byte budget")
-                raise rr.RRError(-rid, "rr_server_submit rejected the request")
-            req.id = int(rid)
-            self._inflight[req.id] = req
-            self.max_inflight_seen = max(self.max_inflight_seen, len(self._inflight))
-        return req.future
+            rid = self.lib.held.rr_server_submit_at(self._h, m._h, rr._ptr(h["t"]), rr._ptr(h["pb"]), req.npt,
+                                                    rr._ptr(h["p"]), req.npv,
+                                                    ss.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                                    ex.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                                    rr._ptr(h["g"]), rr._ptr(h["flux"]), rr._ptr(h["grad"]),
+                                                    rr._ptr(h["status"]), release)
+            if rid >= 0:
+                req.id = int(rid)
+                self._inflight[req.id] = req
+                self.max_inflight_seen = max(self.max_inflight_seen, len(self._inflight))
+        return rid
 
     def _poll(self):
         ctypes = self.ctypes
@@ -468,9 +511,9 @@ class NativeServer:
         while True:
             got = self.lib.rr_server_poll(self._h, ids, sts, tms, n, 20000)
             now = time.perf_counter()
-            for i in range(max(got, 0)):
-                with self._lock:
-                    req = self._inflight.pop(int(ids[i]))
+            with self._lock:
+                reqs = [self._inflight.pop(int(ids[i])) for i in range(max(got, 0))]
+            for i, req in enumerate(reqs):
                 req.t_finish = now
                 req.server_ns = (int(tms[3 * i]), int(tms[3 * i + 1]), int(tms[3 * i + 2]))
                 req.t_admit = (tms[3 * i + 1] - self._clock_off) * 1e-9
@@ -488,6 +531,12 @@ class NativeServer:
             with self._lock:
                 if self._stop and not self._inflight:
                     return
+
+    def reset_stats(self):
+        """Forget the finished requests (a new measurement window on a running server)."""
+        with self._lock:
+            self.completed = []
+            self.max_inflight_seen = len(self._inflight)
 
     def drain(self, timeout_s: float = 600.0):
         t0 = time.perf_counter()

@@ -150,10 +150,40 @@ def test_native_server_writes_caller_result_buffers(fits):
             srv.submit(bad)
 
 
+def test_native_server_checks_that_host_buffers_are_page_locked(fits):
+    """The library refuses pageable host buffers (RR_EPAGEABLE, checked at both ends of each); the
+    Python server then copies them into pinned memory, so pageable torch inputs still give the
+    results of the model alone."""
+    import torch
+    r = _requests(fits, 1, seed=29)[0]
+    m = fits[r.fit][0]
+    t, p = torch.from_numpy(np.ascontiguousarray(r.times)), torch.from_numpy(np.ascontiguousarray(r.params))
+    pb = torch.from_numpy(np.ascontiguousarray(r.pb_index, np.int32))
+    with NativeServer({k: v[0] for k, v in fits.items()}, slots=2, mem_budget=8 << 30) as srv:
+        ss = srv._small(r.supersampling, m.npb, np.int32, 1)
+        ex = srv._small(r.exptime, m.npb, np.float64, 0.0)
+        flux = torch.empty((r.npv, r.npt), dtype=torch.float32).pin_memory()
+        status = torch.empty(r.npv, dtype=torch.int32).pin_memory()
+        h = {"t": t, "p": p.pin_memory(), "pb": pb.pin_memory(), "g": None, "flux": flux, "status": status,
+             "grad": None}
+        assert srv._submit_c(r, m, h, ss, ex, 0) == -7           # times pageable
+        # the same times inside a larger pinned block are accepted
+        big = torch.zeros(8 << 20, dtype=torch.float64).pin_memory()
+        big[: r.npt] = t
+        r._host = dict(h, t=big[: r.npt])
+        assert srv._submit_c(r, m, r._host, ss, ex, 0) >= 0
+        srv.drain()
+        req = ServeRequest(fit=r.fit, times=t, params=p, pb_index=pb, supersampling=r.supersampling,
+                           exptime=r.exptime, grad_flux=r.grad_flux)
+        out = srv.submit(req).result(timeout=60)
+    f, _ = _alone(fits, r)
+    assert np.array_equal(out["flux"], f)
+
+
 def test_native_server_rejects_oversize_requests(fits):
     from paper_2009_08500_gb300.serve import AdmissionError
     reqs = _requests(fits, 2, seed=3)
-    with NativeServer({k: v[0] for k, v in fits.items()}, slots=2, mem_budget=1 << 16) as srv:
+    with NativeServer({k: v[0] for k, v in fits.items()}, slots=2, mem_budget=1 << 10) as srv:
         with pytest.raises(AdmissionError):
             srv.submit(reqs[0])
 

@@ -458,7 +458,7 @@ __device__ __forceinline__ FF ff_c(FFConst c) { return FF{c.h, c.l}; }
 // error ~1e-13.
 __device__ __forceinline__ void ff_sin_vers(float x, const float4* __restrict__ tab, FF& S, FF& V) {
     const int j = __float2int_rn(x * (float)kSvTabRes);
-    const float4 t = __ldg(tab + j + kSvTabRes);
+    const float4 t = tab[j + kSvTabRes];   // a generic load: the table may be in shared or global memory
     const float d = x - (float)j * (1.0f / (float)kSvTabRes);   // exact
     const float d2 = __fmul_rn(d, d);
     const FF Sd = ff_fast_two_sum(d, d * d2 * fmaf(d2, 1.0f / 120.0f, -1.0f / 6.0f));

@@ -272,37 +272,66 @@ __global__ void __launch_bounds__(kBlock, 4) rr_flux_mixed_kernel(const double* 
             int nc, base;
             const int ns = build_list_flux(wl, cand, dh, dl, pbv, c.x, c.y, H.Bh, H.Bl, ps, nc, base);
             if (COUNT && lane == 0) tl.n[RR_COUNT_TIMES] += nc;
-            ChunkWalk cw{0};
-            #pragma unroll 1
-            for (int e0 = 0; e0 < ns; e0 += 32) {
-                const int e = e0 + lane;
-                const bool valid = e < ns;
-                const int jc = chunk_cand_ps(cw, wl->ps, nc, e0);
-                const int j = valid ? jc : -1;
-                float d = 0.0f;
-                if (valid) {
-                    const int pw = wl->ps[j];
-                    const int pb = pw & 31;
-                    const float2 cd = wl->cand[j];
-                    d = delta32<COUNT>(H, PB[pb], rows + (size_t)pb * L.rows_per_pb * L.ng_pad, L.ng, cd.x, cd.y,
-                                       e - (pw >> 5), ps->first[pb], ps->step[pb], bad, &tl);
+            // The item's flattened samples [0, ns) in 32 contiguous runs of run = ceil(ns / 32),
+            // one per lane.  A lane walks its run in order, summing the sub-exposures of the
+            // candidate at hand: the sum of a candidate that starts and ends inside the run is
+            // final; the candidate at the run's start (head) and the one at its end (tail) may
+            // go on in the neighbouring runs, and are combined once per item, in lane order.
+            const int run = (ns + 31) >> 5;
+            const int e_beg = min(lane * run, ns), e_end = min(e_beg + run, ns);
+            int jh = -1, jt = -1;          // head and tail candidates of the run (-1: none)
+            float ph = 0.0f, pt = 0.0f;    // their partial sums over the run
+            if (e_beg < e_end) {
+                // the candidate holding sample e_beg: the last j with soff(j) <= e_beg
+                int lo = 0, hi = nc - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if ((wl->ps[mid] >> 5) <= e_beg) lo = mid; else hi = mid - 1;
                 }
-                if (ns == nc) {
-                    // one sample per candidate: nothing to sum
-                    if (valid) wl->pacc[j] = d;
-                } else {
-                    // sum over the sub-exposures of each time: segmented scan along the lanes
-                    #pragma unroll
-                    for (int o = 1; o < 32; o <<= 1) {
-                        const float y = __shfl_up_sync(0xffffffffu, d, o);
-                        const int ky = __shfl_up_sync(0xffffffffu, j, o);
-                        if (lane >= o && ky == j) d += y;
+                int j = lo;
+                int pw = wl->ps[j];
+                int next = wl->ps[j + 1] >> 5;     // first sample of candidate j + 1 (ps[nc] = ns << 5)
+                int pb = pw & 31;
+                float2 cd = wl->cand[j];
+                int sub = e_beg - (pw >> 5);
+                float part = 0.0f;
+                jh = j;
+                #pragma unroll 1
+                for (int e = e_beg; e < e_end; ++e) {
+                    if (e == next) {
+                        // candidate j ends inside the run: the head's sum, or a final one
+                        if (j == jh) ph = part; else wl->pacc[j] = part;
+                        ++j;
+                        pw = wl->ps[j];
+                        next = wl->ps[j + 1] >> 5;
+                        pb = pw & 31;
+                        cd = wl->cand[j];
+                        sub = 0;
+                        part = 0.0f;
                     }
-                    const int jn = __shfl_down_sync(0xffffffffu, j, 1);
-                    if (valid && (lane == 31 || jn != j)) wl->pacc[j] += d;
+                    part += delta32<COUNT>(H, PB[pb], rows + (size_t)pb * L.rows_per_pb * L.ng_pad, L.ng, cd.x, cd.y,
+                                           sub, ps->first[pb], ps->step[pb], bad, &tl);
+                    ++sub;
                 }
-                __syncwarp();
+                if (j == jh) ph = part; else { jt = j; pt = part; }
             }
+            // a tail that goes on into the next run is added in front of that run's head
+            const int tprev_j = __shfl_up_sync(0xffffffffu, jt, 1);
+            const float tprev_p = __shfl_up_sync(0xffffffffu, pt, 1);
+            if (lane > 0 && jh >= 0 && tprev_j == jh) ph = tprev_p + ph;
+            const int hnext_j = __shfl_down_sync(0xffffffffu, jh, 1);
+            if (jt >= 0 && (lane == 31 || hnext_j != jt)) wl->pacc[jt] = pt;   // the tail ends with the run
+            // heads: segmented inclusive scan over the lanes by candidate (fixed order); the last
+            // lane of each segment holds the candidate's sum
+            float v = ph;
+            #pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const float y = __shfl_up_sync(0xffffffffu, v, o);
+                const int ky = __shfl_up_sync(0xffffffffu, jh, o);
+                if (lane >= o && ky == jh) v = y + v;
+            }
+            if (jh >= 0 && (lane == 31 || hnext_j != jh)) wl->pacc[jh] = v;
+            __syncwarp();
             int jj = base;
             #pragma unroll
             for (int q = 0; q < 4; ++q) {

@@ -343,8 +343,10 @@ __global__ void __launch_bounds__(kBlock, 3) rr_grad_mixed_kernel(
     float* depcols = gacc + (size_t)pv_tile * groups_per_cta * nacc;
     char* qbase = reinterpret_cast<char*>(depcols + (DEP ? (size_t)(nacc - 6) * kBlock : 0));
     const ItemQueue queue = queue_at(qbase, pv_tile * groups_per_cta);
-    // the summaries of the CTA's groups, copied with the records
+    // the summaries of the CTA's groups, copied with the records, then the sine table of the
+    // refinement (read by a lane alone, where an L2 read would hold its warp)
     GroupInfo* sgrp = reinterpret_cast<GroupInfo*>(qbase + queue_bytes(pv_tile * groups_per_cta));
+    float4* ssv = reinterpret_cast<float4*>(sgrp + groups_per_cta);
     TileCounters* tc = reinterpret_cast<TileCounters*>(smem + kOffRed);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -372,6 +374,8 @@ __global__ void __launch_bounds__(kBlock, 3) rr_grad_mixed_kernel(
     }
     stage_pb(pbp, ps);
     for (int j = tid; j < pv_tile * groups_per_cta * nacc; j += kBlock) gacc[j] = 0.0f;
+    if (L.orb_off >= 0)
+        for (int j = tid; j < kSvTabLen; j += kBlock) ssv[j] = __ldg(svtab + j);
     __syncthreads();
     bool ok = mbar_wait_bounded(bar, 0);
     if (!ok) {
@@ -465,7 +469,7 @@ __global__ void __launch_bounds__(kBlock, 3) rr_grad_mixed_kernel(
                 const int pb = __float_as_int(cd.z);
                 const Phase32 ph = precise_phase(cd.x, cd.y, c.x, c.y, H.Bh, H.Bl);
                 if (COUNT) ++tl.n[RR_COUNT_TIMES];
-                any |= adjoint_sample<DEP, COUNT>(H, PB[pb], rows + (size_t)pb * L.rows_per_pb * L.ng_pad, orb, svtab, pb, 0,
+                any |= adjoint_sample<DEP, COUNT>(H, PB[pb], rows + (size_t)pb * L.rows_per_pb * L.ng_pad, orb, ssv, pb, 0,
                                            ps, L, ph.fr_h, ph.fr_l, ph.m, 0.0f, c.z, cd.w, acc, dep,
                                            6 + (chromatic ? pb : 0), 6 + nkp + pb * L.nldc, bad, tl);
             }
@@ -483,7 +487,7 @@ __global__ void __launch_bounds__(kBlock, 3) rr_grad_mixed_kernel(
                 const float4 cd = wl->cand[j];
                 const int sub = e - wl->soff[j];
                 const float off = fmaf((float)sub, ps->step[pb], ps->first[pb]) * H.Bh;
-                any |= adjoint_sample<DEP, COUNT>(H, PB[pb], rows + (size_t)pb * L.rows_per_pb * L.ng_pad, orb, svtab, pb, sub,
+                any |= adjoint_sample<DEP, COUNT>(H, PB[pb], rows + (size_t)pb * L.rows_per_pb * L.ng_pad, orb, ssv, pb, sub,
                                            ps, L, cd.x, cd.y, cd.z, off, c.z, cd.w, acc, dep, 6 + (chromatic ? pb : 0),
                                            6 + nkp + pb * L.nldc, bad, tl);
             }
@@ -701,8 +705,10 @@ static size_t grad_smem(int pv_tile, const RecLayout& L, int nacc, bool dep, siz
                (size_t)pv_tile * L.head_bytes +
                (size_t)pv_tile * slots * nacc * rsize;
     if (dep) s += (size_t)(nacc - 6) * kBlock * rsize;
-    // FP32 kernel: item queue, then the summaries of the CTA's groups
-    if (rsize == 4) s = ((s + 15) & ~(size_t)15) + queue_bytes(pv_tile * slots) + (size_t)slots * sizeof(GroupInfo);
+    // FP32 kernel: item queue, then the summaries of the CTA's groups and the sine table
+    if (rsize == 4)
+        s = ((s + 15) & ~(size_t)15) + queue_bytes(pv_tile * slots) + (size_t)slots * sizeof(GroupInfo) +
+            (size_t)kSvTabLen * sizeof(float4);
     return s;
 }
 

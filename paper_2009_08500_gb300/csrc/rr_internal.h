@@ -195,6 +195,8 @@ struct ModelParams {
     double dg;       // 1 / (ng - 1)
     double k_small;  // small-planet approximation threshold (0 = off)
     double mu_min;   // mu of the outermost bin mean (the small-planet approximation's limb clamp)
+    const double* tab;   // tabulated profiles (device): per passband mu nodes then intensities
+    const int* tab_off;  // node offsets of the passbands in tab (npb + 1)
 };
 
 // Per-call projections of the direct model (the workspace region after the

@@ -592,8 +592,8 @@ __device__ R mean_anomaly_of_true_r(R f, R e) {
 }
 
 // Small-planet approximation (Sect. 3.4): the rows of the (pv, passband)
-// pairs whose weights' radius ratio k_w is below k_small, written after the
-// set-up kernel (which leaves them out), in FP64.  At g node i the row holds
+// pairs whose weights' radius ratio k_w is below k_small, written by the
+// set-up kernel in place of the interpolated rows.  At g node i the row holds
 // the profile at the planet's centre, mu = sqrt(1 - min(c, 1)^2) with
 // c = g_i (1 + k_w), clamped below to mu_min, divided by I_star; with the
 // adjoint also the in-cell difference, d/dk (through mu; 0 where clamped) and
@@ -624,73 +624,88 @@ __device__ double small_planet_node(const ModelParams& mp, const SmallPlanetRow&
     return v;
 }
 
-template <typename R>
-__global__ void __launch_bounds__(256) rr_small_planet_kernel(ModelParams mp, const double* __restrict__ params,
-                                                              int npv, const double* __restrict__ istar,
-                                                              const double* __restrict__ tab,
-                                                              const int* __restrict__ tab_off, RecLayout L, int grad,
-                                                              char* __restrict__ records) {
-    // one warp per (pv, passband) row and 32 consecutive g nodes
-    const int wpr = (mp.ng + 31) >> 5;
-    const long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (w >= (long long)npv * mp.npb * wpr) return;
-    const int chunk = (int)(w % wpr);
-    const long long rw = w / wpr;
-    const int pb = (int)(rw % mp.npb), pv = (int)(rw / mp.npb);
-    const double* row = params + (size_t)pv * mp.nparam;
-    const int nkp = mp.chromatic ? mp.npb : 1;
-    double kw = row[6 + (mp.chromatic ? pb : 0)];
-    if (mp.shared) {
-        kw = 0.0;
-        for (int j = 0; j < nkp; ++j) kw += row[6 + j];
-        kw /= nkp;
-    }
-    if (!(kw < mp.k_small)) return;            // the set-up kernel wrote this passband's rows
-    // coefficients and I_star as in the set-up kernel
-    const bool named = mp.ld_model != RR_LD_TABULATED;
-    const double* c = row + 6 + nkp + pb * mp.nldc;
-    SmallPlanetRow sp;
-    sp.kw = kw;
-    sp.b0 = named ? 0 : pb;
-    sp.nc = named ? mp.nldc : 0;
-    sp.ud[0] = 1.0;
-    for (int j = 0; j < 4; ++j) sp.ud[1 + j] = 0.0;
-    if (mp.ld_model == RR_LD_QUADRATIC_TRI) {
-        const double sq = sqrt(fmax(c[0], 0.0));
-        sp.ud[1] = 2.0 * sq * c[1];
-        sp.ud[2] = sq * (1.0 - 2.0 * c[1]);
-    } else {
-        for (int j = 0; j < sp.nc; ++j) sp.ud[1 + j] = c[j];
-    }
-    double Is = named ? istar[0] : istar[pb];
-    if (named)
-        for (int j = 0; j < mp.nldc; ++j) Is += sp.ud[1 + j] * istar[1 + j];
-    // the set-up kernel's 1 / I_star, rounded to R as there
-    const double invIs = (double)(R)(1.0 / Is);
-    R* r0 = reinterpret_cast<R*>(records + rows_offset(L, npv) + (size_t)pv * L.rows_bytes) +
-            (size_t)pb * L.rows_per_pb * L.ng_pad;
-    if (chunk == wpr - 1)
-        for (int q = mp.ng + lane; q < L.ng_pad; q += 32)
-            for (int rr = 0; rr < L.rows_per_pb; ++rr) r0[(size_t)rr * L.ng_pad + q] = (R)0;
-    // each node is evaluated once: the in-cell difference takes the next node's value from the
-    // next lane (the last lane evaluates its next node itself)
-    {
-        const int ig = chunk * 32 + lane;
-        double vb[5] = {0.0, 0.0, 0.0, 0.0, 0.0}, dk = 0.0, v = 0.0;
-        if (ig < mp.ng) v = small_planet_node(mp, sp, tab, tab_off, ig, vb, dk) * invIs;
-        double vn = __shfl_down_sync(0xffffffffu, v, 1);
-        if (grad && lane == 31 && ig + 1 < mp.ng) {
-            double vb1[5], dk1;
-            vn = small_planet_node(mp, sp, tab, tab_off, ig + 1, vb1, dk1) * invIs;
+// FP32 twins of ld_basis_mu and small_planet_node, for rows stored in FP32 (the mixed form):
+// FP64 issues at a small fraction of the FP32 rate on this GPU, and the rows keep 24 bits.
+// 1 - c^2 as (1 - c)(1 + c), and the exponential law's 1 - e^mu as -expm1(mu), keep the
+// relative precision at the limb.
+__device__ __forceinline__ float ld_basis_mu_f(const ModelParams& mp, int b, float m, const double* __restrict__ tab,
+                                               const int* __restrict__ tab_off, float& d) {
+    if (mp.ld_model == RR_LD_TABULATED) {
+        const int o0 = tab_off[b], n = tab_off[b + 1] - o0;
+        const double* tmu = tab + 2 * o0;
+        const double* tI = tmu + n;
+        if (m < (float)tmu[0]) { d = 0.0f; return (float)tI[0]; }
+        if (m >= (float)tmu[n - 1]) { d = 0.0f; return (float)tI[n - 1]; }
+        int lo = 0, hi = n - 1;   // tmu[lo] <= m < tmu[hi]
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if ((float)tmu[mid] <= m) lo = mid; else hi = mid;
         }
-        if (ig >= mp.ng) return;
-        r0[ig] = (R)v;
-        if (!grad) return;
-        r0[L.ng_pad + ig] = (R)(ig < mp.ng - 1 ? vn - v : 0.0);
-        r0[2 * L.ng_pad + ig] = (R)(dk * invIs);
-        for (int j = 0; j < sp.nc; ++j)
-            r0[(size_t)(3 + j) * L.ng_pad + ig] = (R)((vb[1 + j] - v * (double)(R)istar[1 + j]) * invIs);
+        const float m0 = (float)tmu[lo], i0 = (float)tI[lo];
+        d = ((float)tI[lo + 1] - i0) / ((float)tmu[lo + 1] - m0);
+        return i0 + d * (m - m0);
+    }
+    if (b == 0) { d = 0.0f; return 1.0f; }
+    const float q = 1.0f - m;
+    switch (mp.ld_model) {
+        case RR_LD_NONLINEAR: {
+            const float sq = sqrtf(m);
+            const float p = b == 1 ? sq : (b == 2 ? m : (b == 3 ? m * sq : m * m));
+            d = b == 1 ? 0.5f / sq : (b == 2 ? 1.0f : (b == 3 ? 1.5f * sq : 2.0f * m));
+            return -(1.0f - p);
+        }
+        case RR_LD_GENERAL: {
+            float p = 1.0f;
+            for (int j = 1; j < b; ++j) p *= q;
+            d = b * p;
+            return -p * q;
+        }
+        case RR_LD_LOGARITHMIC:
+            if (b == 1) { d = 1.0f; return -q; }
+            d = -(logf(m) + 1.0f);
+            return -m * logf(m);
+        case RR_LD_EXPONENTIAL:
+            if (b == 1) { d = 1.0f; return -q; }
+            {
+                const float em1 = expm1f(m), r = -1.0f / em1;   // 1 / (1 - e^mu)
+                d = -(em1 + 1.0f) * r * r;
+                return -r;
+            }
+        default:
+            if (b == 1) { d = 1.0f; return -q; }
+            d = 2.0f * q;
+            return -q * q;
+    }
+}
+
+__device__ __forceinline__ float small_planet_node_f(const ModelParams& mp, const SmallPlanetRow& sp,
+                                                     const double* tab, const int* tab_off, int i, float* vb,
+                                                     float& dk) {
+    const float gi = (float)(i * mp.dg), cc = gi * (1.0f + (float)sp.kw);
+    const float cm = fminf(cc, 1.0f);
+    const float m0 = sqrtf(fmaxf((1.0f - cm) * (1.0f + cm), 0.0f));
+    const bool free = cc < 1.0f && m0 > (float)mp.mu_min;
+    const float m = free ? m0 : (float)mp.mu_min;
+    const float dmdk = free ? -cc * gi / m : 0.0f;
+    float v = 0.0f, dv = 0.0f;
+    for (int c = 0; c <= sp.nc; ++c) {
+        float dd;
+        const float bv = ld_basis_mu_f(mp, sp.b0 + c, m, tab, tab_off, dd);
+        vb[c] = bv;
+        v += (float)sp.ud[c] * bv;
+        dv += (float)sp.ud[c] * dd;
+    }
+    dk = dv * dmdk;
+    return v;
+}
+
+// A small-planet node in the arithmetic of the rows: FP32 for the mixed form, FP64 otherwise.
+template <typename R>
+__device__ __forceinline__ R small_planet_node_r(const ModelParams& mp, const SmallPlanetRow& sp, int i, R* vb, R& dk) {
+    if constexpr (sizeof(R) == sizeof(float)) {
+        return small_planet_node_f(mp, sp, mp.tab, mp.tab_off, i, vb, dk);
+    } else {
+        return small_planet_node(mp, sp, mp.tab, mp.tab_off, i, vb, dk);
     }
 }
 
@@ -724,6 +739,7 @@ __global__ void __launch_bounds__(256, 4) rr_pv_setup_kernel(ModelParams mp, PbP
     __shared__ R invIs_s[NP][RR_MAX_PB];
     __shared__ R ak_s[NP][RR_MAX_PB];
     __shared__ int ik_s[NP][RR_MAX_PB];       // k cell or direct row; -1: small-planet approximation
+                                              // (ak_s then holds the weights' radius ratio)
     __shared__ int st_s[NP];       // validity after (1): LD coefficients, I_star, k
     __shared__ int st2_s[NP];      // full validity after (2a)
     __shared__ int rows_next;
@@ -789,7 +805,7 @@ __global__ void __launch_bounds__(256, 4) rr_pv_setup_kernel(ModelParams mp, PbP
         double ak;
         if (small) {
             ik = -1;
-            ak = 0.0;
+            ak = kw;   // the small-planet rows' radius ratio
         } else if (mp.direct) {
             // the row of this (pv, k slot) in the per-call projections
             ik = mp.shared ? pv0 + lp : (pv0 + lp) * nkp + (mp.chromatic ? pb : 0);
@@ -1049,7 +1065,33 @@ __global__ void __launch_bounds__(256, 4) rr_pv_setup_kernel(ModelParams mp, PbP
         #pragma unroll
         for (int c = 0; c < 4; ++c) Ic[c] = (grad && c < nc && !p2law) ? (R)istar[1 + c] : R(0);
         const int b0 = named ? 0 : pb;
-        if (ik < 0) continue;   // small-planet approximation: rr_small_planet_kernel writes these rows
+        if (ik < 0) {
+            // small-planet approximation (Sect. 3.4): the profile at the planet's centre at each
+            // g node (small_planet_node), in the rows' arithmetic R
+            SmallPlanetRow sp;
+            sp.kw = (double)ak;
+            sp.b0 = b0;
+            sp.nc = nc;
+            sp.ud[0] = 1.0;
+            #pragma unroll
+            for (int c = 0; c < 4; ++c) sp.ud[1 + c] = (double)uc[c];
+            const int ig_end = min(L.ng_pad, 64 * ch + 64);
+            for (int ig = 64 * ch + lane; ig < ig_end; ig += 32) {
+                if (ig >= mp.ng) {
+                    for (int r = 0; r < L.rows_per_pb; ++r) r0[(size_t)r * L.ng_pad + ig] = (R)0;
+                    continue;
+                }
+                R vb[5] = {R(0), R(0), R(0), R(0), R(0)}, dk = R(0), vb1[5], dk1;
+                const R v = small_planet_node_r<R>(mp, sp, ig, vb, dk) * invIs;
+                r0[ig] = v;
+                if (!grad) continue;
+                const R vn = ig < mp.ng - 1 ? small_planet_node_r<R>(mp, sp, ig + 1, vb1, dk1) * invIs : v;
+                r0[L.ng_pad + ig] = vn - v;
+                r0[2 * L.ng_pad + ig] = dk * invIs;
+                for (int j = 0; j < nc; ++j) r0[(size_t)(3 + j) * L.ng_pad + ig] = (vb[1 + j] - v * Ic[j]) * invIs;
+            }
+            continue;
+        }
         if (mp.direct && (mp.ld_model == RR_LD_POWER2 || mp.ld_model == RR_LD_POWER2_PM)) {
             // power-2 laws: row = ((1 - c) T0 + c T1) / I_star with T0 = w . 1 and T1 = w . mu^alpha
             // of this passband; adjoint rows in (c, alpha) with T2 = w . mu^alpha ln mu = dT1/dalpha,
@@ -1227,6 +1269,8 @@ ModelParams model_params(const rr_ctx* c) {
     mp.k_small = c->cfg.k_small;
     mp.mu_min = c->mu.empty() ? 0.0 : c->mu.back();
     mp.nz = c->nz;
+    mp.tab = c->d_tab;
+    mp.tab_off = c->d_tab_off;
     // int_0^1 mu / (e^mu - 1) dmu = pi^2/6 - Li2(1/e) + ln(1 - 1/e) (expand 1/(e^mu - 1) = sum_k e^(-k mu));
     // Li2(1/e) = sum_k e^(-k) / k^2, 40 terms below 1e-18
     double li2 = 0.0, p = 1.0;
@@ -1348,20 +1392,6 @@ cudaError_t launch_pv_setup(rr_ctx* c, const double* params, int npv, const PbPa
         rr_pv_setup_kernel<float><<<blocks, 256, 0, s>>>(mp, pbp, params, npv, c->d_T32, c->d_DT32, c->d_istar, L,
                                                          grad ? 1 : 0, (char*)records, pv_status, D, pa);
     }
-    c->launches++;
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess || !(c->cfg.k_small > 0.0) || npv == 0) return e;
-    // rows of the small-planet passbands: one warp per (pv, passband, 32 g nodes)
-    const long long n = (long long)npv * c->cfg.npb * ((c->cfg.ng + 31) / 32) * 32;
-    const unsigned nb = (unsigned)((n + 255) / 256);
-    if (c->cfg.precision == RR_PREC_FP64)
-        rr_small_planet_kernel<double><<<nb, 256, 0, s>>>(mp, params, npv, c->d_istar, c->d_tab, c->d_tab_off,
-                                                          make_layout<double>(c->cfg.npb, c->cfg.ng, c->nldc, grad),
-                                                          grad ? 1 : 0, (char*)records);
-    else
-        rr_small_planet_kernel<float><<<nb, 256, 0, s>>>(mp, params, npv, c->d_istar, c->d_tab, c->d_tab_off,
-                                                         make_layout<float>(c->cfg.npb, c->cfg.ng, c->nldc, grad),
-                                                         grad ? 1 : 0, (char*)records);
     c->launches++;
     return cudaGetLastError();
 }

@@ -711,9 +711,12 @@ __device__ __forceinline__ R small_planet_node_r(const ModelParams& mp, const Sm
 
 // Pvs per CTA of the set-up kernel: few, so that the launch has several
 // CTAs per SM and the per-pv scalar chains of many CTAs overlap; the rows
-// and windows are spread over the whole CTA.
+// and windows are spread over the whole CTA.  At most N; fewer with more
+// passbands (each pv then has that many rows), so that the launch spreads
+// over the SMs (8 passbands: 2 per CTA, measured 49.7 -> 39.6 us for 2,048
+// pvs; 1 per CTA was slower again).
 template <typename R> struct SetupPvs { static constexpr int N = 8; };
-__host__ __device__ inline int setup_pvs_per_cta(int) { return 8; }
+__host__ __device__ inline int setup_pvs_per_cta(int npb) { return npb >= 4 ? 2 : (npb >= 2 ? 4 : 8); }
 
 template <typename R>
 __global__ void __launch_bounds__(256, 4) rr_pv_setup_kernel(ModelParams mp, PbParams pbp,

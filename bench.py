@@ -477,6 +477,10 @@ def run_ours(a):
     if world == 1 and a.workload == "c4" and not a.no_sub:
         m3 = measure(a, "c3", a.steps, world, local, dev, flush)
         c3 = sub_record(a, m3, world, local, dev, flush)
+        if not a.no_e2e:
+            e3 = run_e2e(a, m3["model"], m3["wl"], True, dev)
+            e3["value"] = m3["pts"] / (e3.pop("_ms") * 1e-3)
+            c3["e2e"] = e3
         if not a.no_fp64_form:
             f3 = run_fp64_form(a, m3["wl"], True, local, dev, flush)
             c3["fp64_form"] = dict(f3, speedup_of_mixed=m3["value"] / f3["value"])

@@ -260,7 +260,6 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     return ok != 0;
 }
 
-// Bounded wait: gives up after ~0.1 s and reports false.
 // Nanoseconds of the GPU's global timer.
 __device__ __forceinline__ uint64_t global_ns() {
     uint64_t t;

@@ -117,6 +117,28 @@ def test_in_place_and_staged_paths_agree_with_one_device_call(rr, ld, npb, ss):
             assert nan_eq(torch.from_numpy(gp), gref)
 
 
+@pytest.mark.parametrize("case", [dict(ld_model="quadratic", precision="fp64", ss=(3,), exptime=(0.01,)),
+                                  dict(ld_model="nonlinear", direct=True, ss=(1,), exptime=(0.0,)),
+                                  dict(ld_model="quadratic", npb=2, chromatic=True, ss=(1, 5), exptime=(0.0, 0.02)),
+                                  dict(ld_model="tabulated", npb=2, ss=(1, 4), exptime=(0.0, 0.01), precision="fp64")],
+                         ids=["fp64", "direct", "chromatic", "tabulated-fp64"])
+def test_in_place_matches_device_call_across_forms(rr, case):
+    """In place on pinned buffers for the FP64 kernels (which read each time through the read-only
+    path), the direct model and chromatic radius ratios: bitwise the device entry points."""
+    import torch
+    precision = case.pop("precision", "mixed")
+    wl = W.make_small(npv=23, npt=1703, seed=19, **case)
+    wl.precision = precision
+    m = rr.model_for(wl)
+    t, pb, p = rr.to_device(wl)
+    ref = m.evaluate(t, p, pb, wl.supersampling, wl.exptime).cpu()
+    gbar = np.random.default_rng(2).normal(size=(wl.npv, wl.npt)).astype(np.float32 if precision == "mixed" else np.float64)
+    gref = m.evaluate_grad(t, p, torch.as_tensor(gbar, device=t.device), pb, wl.supersampling, wl.exptime).cpu()
+    f, g, st = m.evaluate_host(wl.times, wl.params, wl.pb_index, wl.supersampling, wl.exptime, grad_flux=gbar)
+    assert m.host_path == "in place"
+    assert torch.equal(f, ref) and torch.equal(g, gref) and not st.any()
+
+
 def test_enqueue_host_in_place_and_staged(rr):
     """rr_enqueue_host on pinned tensors (in place) and on pageable numpy buffers (staged copies)."""
     import torch

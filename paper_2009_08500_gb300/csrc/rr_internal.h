@@ -5,13 +5,12 @@
 //                        weight projections for the pv's own k -> workspace
 //   rr_pv_setup_kernel   params -> one record per parameter vector in the
 //                        caller's workspace (orbit constants, transit window,
-//                        profile rows divided by I_star: interpolated in k, or
-//                        the pv's direct projections); in the same launch (mixed
-//                        form, one passband) the per-time float-float offsets,
-//                        passband and 128-time group summaries (rr_points_kernel
-//                        apart with several passbands)
-//   rr_small_planet_kernel  (k_small > 0 only) the rows of passbands below the
-//                        threshold, from the profile at the planet's centre
+//                        profile rows divided by I_star: interpolated in k, the
+//                        pv's direct projections, or below k_small the profile at
+//                        the planet's centre); in the same launch (mixed form,
+//                        one passband) the per-time float-float offsets, passband
+//                        and 128-time group summaries (rr_points_kernel apart with
+//                        several passbands, then rr_chunk_order_kernel)
 //   rr_flux_mixed_kernel / rr_flux_fp64_kernel: records of a pv tile -> shared
 //                        memory (one bulk async copy), flux[pv][t] for the tile
 //   rr_grad_mixed_kernel / rr_grad_fp64_kernel: same tiling; per-(pv, chunk)

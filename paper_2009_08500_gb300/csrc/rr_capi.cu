@@ -215,22 +215,19 @@ cudaError_t run_setup(rr_ctx* c, const double* times, const int32_t* pb_index, i
                       int npv, const PbParams& pbp, bool grad, int32_t* pv_status, void* ws, cudaStream_t s) {
     cudaError_t e = run_direct(c, params, npv, grad, ws, s);
     if (e != cudaSuccess) return e;
-    // the per-pv set-up and (mixed form) the per-time preparation: one launch for a single
-    // passband (measured: the preparation then costs nothing on the population workload), two
-    // with several (sharing the launch slowed the 8-passband set-up by more than it saved)
+    // the per-pv set-up and (mixed form) the per-time preparation in one launch (measured: the
+    // preparation then costs nothing on the population workload; with 8 passbands the set-up
+    // grows by 1.5 us and the step saves 4 us against a launch of its own); with several
+    // passbands the chunk ordering follows
     const WsLayout W = ws_layout(c, npv, npt, grad);
     char* wb = (char*)ws;
-    const bool fused = c->cfg.npb == 1;
     e = timed(c, RR_KERNEL_PV_SETUP, s, [&] {
-        return launch_pv_setup(c, params, npv, pbp, grad, ws, pv_status, s, times, pb_index, fused ? npt : 0,
+        return launch_pv_setup(c, params, npv, pbp, grad, ws, pv_status, s, times, pb_index, npt,
                                wb + W.pts_dt, wb + W.pts_pb, wb + W.pts_grp);
     });
-    if (e != cudaSuccess || fused || c->cfg.precision != RR_PREC_MIXED || npt == 0) return e;
+    if (e != cudaSuccess || c->cfg.npb == 1 || c->cfg.precision != RR_PREC_MIXED || npt == 0) return e;
     return timed(c, RR_KERNEL_POINTS, s,
-                 [&] {
-                     return launch_points(c, times, pb_index, npt, pbp, wb + W.pts_dt, wb + W.pts_pb, wb + W.pts_grp,
-                                          wb + W.pts_ord, s);
-                 });
+                 [&] { return launch_chunk_order(c, npt, wb + W.pts_grp, wb + W.pts_ord, s); });
 }
 
 // Validity words only (npt == 0 with a pv_status array): the set-up kernel alone.

@@ -32,20 +32,6 @@
 
 namespace rr {
 
-// The per-time inputs of the FP32 kernels as a launch of their own (one CTA per
-// 128-time group); single-passband batches carry them in the set-up launch.
-__global__ void __launch_bounds__(kWarpPts) rr_points_kernel(const double* __restrict__ times,
-                                                             const int32_t* __restrict__ pb_index, int npt, int npb,
-                                                             float2* __restrict__ dt, int32_t* __restrict__ pbw,
-                                                             GroupInfo* __restrict__ grp, int ngroups, PbParams pbp) {
-    __shared__ float red[4][kWarpPts / 32];
-    __shared__ int redf[kWarpPts / 32];
-    __shared__ int ss[RR_MAX_PB];
-    for (int j = threadIdx.x; j < npb; j += blockDim.x) ss[j] = pbp.ss[j];
-    __syncthreads();
-    points_group(times, pb_index, npt, npb, dt, pbw, grp, blockIdx.x, ngroups, threadIdx.x, red, redf, ss);
-}
-
 // Order of the time chunks of the FP32 per-point kernels, heaviest first (one
 // CTA): chunk i (groups i gpc .. i gpc + gpc - 1) weighs the exposure
 // sub-samples of its groups; order[rank] = i, ties in index order.  With
@@ -76,14 +62,8 @@ __global__ void __launch_bounds__(1024) rr_chunk_order_kernel(const GroupInfo* _
     }
 }
 
-cudaError_t launch_points(rr_ctx* c, const double* times, const int32_t* pb_index, int npt, const PbParams& pbp,
-                          void* ws_dt, void* ws_pb, void* ws_grp, void* ws_ord, cudaStream_t s) {
+cudaError_t launch_chunk_order(rr_ctx* c, int npt, void* ws_grp, void* ws_ord, cudaStream_t s) {
     const int ngroups = (npt + kWarpPts - 1) / kWarpPts;
-    rr_points_kernel<<<ngroups, kWarpPts, 0, s>>>(times, pb_index, npt, c->cfg.npb, (float2*)ws_dt,
-                                                  (int32_t*)ws_pb, (GroupInfo*)ws_grp, ngroups, pbp);
-    c->launches++;
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess || !ws_ord) return e;
     const int gpc = groups_per_cta(npt);
     rr_chunk_order_kernel<<<1, 1024, 0, s>>>((const GroupInfo*)ws_grp, ngroups, gpc, time_chunks(npt, gpc),
                                              (int*)ws_ord);

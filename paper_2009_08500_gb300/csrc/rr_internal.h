@@ -7,10 +7,10 @@
 //                        caller's workspace (orbit constants, transit window,
 //                        profile rows divided by I_star: interpolated in k, the
 //                        pv's direct projections, or below k_small the profile at
-//                        the planet's centre); in the same launch (mixed form,
-//                        one passband) the per-time float-float offsets, passband
-//                        and 128-time group summaries (rr_points_kernel apart with
-//                        several passbands, then rr_chunk_order_kernel)
+//                        the planet's centre); in the same launch (mixed form)
+//                        the per-time float-float offsets, passband and 128-time
+//                        group summaries; with several passbands then
+//                        rr_chunk_order_kernel (time chunks heaviest first)
 //   rr_flux_mixed_kernel / rr_flux_fp64_kernel: records of a pv tile -> shared
 //                        memory (one bulk async copy), flux[pv][t] for the tile
 //   rr_grad_mixed_kernel / rr_grad_fp64_kernel: same tiling; per-(pv, chunk)
@@ -301,8 +301,6 @@ size_t direct_bytes(const rr_ctx* c, int npv, bool grad);
 DirectTables direct_view(const rr_ctx* c, void* base, int npv, bool grad);
 cudaError_t launch_selftest(rr_ctx* c, int which, cudaStream_t s);
 // with several passbands also the order of the CTA time chunks, heaviest first (ws_ord)
-cudaError_t launch_points(rr_ctx* c, const double* times, const int32_t* pb_index, int npt, const PbParams& pbp,
-                          void* ws_dt, void* ws_pb, void* ws_grp, void* ws_ord, cudaStream_t s);
 // records: the workspace (the direct model's projections follow the records).  With times
 // (mixed form, npt > 0) the same launch also writes the per-time inputs of the FP32 kernels
 // (float-float offsets, passband, 128-time group summaries) into pts_dt, pts_pb, pts_grp.
@@ -320,6 +318,7 @@ cudaError_t launch_grad(rr_ctx* c, const double* times, const int32_t* pb_index,
                         const void* pts_pb, const void* pts_grp, const void* pts_ord, int npt, int npv,
                         const PbParams& pbp, const void* records,
                         const void* grad_flux, void* partials, int32_t* pv_status, cudaStream_t s);
+cudaError_t launch_chunk_order(rr_ctx* c, int npt, void* ws_grp, void* ws_ord, cudaStream_t s);
 // time chunks of the FP32 per-point kernels
 inline int time_chunks(int npt, int gpc) { return ((npt + kWarpPts - 1) / kWarpPts + gpc - 1) / gpc; }
 // Whether p is device memory.  A caller's buffer may also be page-locked host memory, which the

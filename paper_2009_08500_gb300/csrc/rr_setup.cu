@@ -731,9 +731,12 @@ __global__ void __launch_bounds__(256, 4) rr_pv_setup_kernel(ModelParams mp, PbP
         // launch as the per-pv set-up (the two are independent); these short CTAs come first
         __shared__ float pred[2][4][kWarpPts / 32];
         __shared__ int predf[2][kWarpPts / 32];
+        __shared__ int ss_s[RR_MAX_PB];
         const int half = threadIdx.x / kWarpPts;
+        for (int j = threadIdx.x; j < mp.npb; j += blockDim.x) ss_s[j] = pbp.ss[j];
+        __syncthreads();
         points_group(pa.times, pa.pb_index, pa.npt, mp.npb, pa.dt, pa.pbw, pa.grp, (int)blockIdx.x * 2 + half,
-                     pa.ngroups, threadIdx.x % kWarpPts, pred[half], predf[half], nullptr);
+                     pa.ngroups, threadIdx.x % kWarpPts, pred[half], predf[half], mp.npb > 1 ? ss_s : nullptr);
         return;
     }
     const int sblock = (int)blockIdx.x - pa.npoints;   // this CTA's index among the set-up CTAs

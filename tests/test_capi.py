@@ -43,6 +43,15 @@ def test_null_handles_are_rejected_without_a_device(lib):
     out = ctypes.c_void_p()
     assert lib.rr_create(None, ctypes.byref(out)) == 1
     assert b"cfg" in lib.rr_last_error(None)
+    assert lib.rr_host_path(None) == 0
+    assert lib.rr_request_bytes(None, 4, 4, 0) == 0
+    # the server's entry points refuse a null server before any CUDA call
+    ss, ex = (ctypes.c_int32 * 1)(1), (ctypes.c_double * 1)(0.0)
+    assert lib.rr_server_submit_at(None, None, None, None, 4, None, 1, ss, ex, None, None, None, None, 0) == -1
+    ids, sts = (ctypes.c_int64 * 1)(), (ctypes.c_int32 * 1)()
+    assert lib.rr_server_poll(None, ids, sts, None, 1, 0) == -1
+    assert lib.rr_server_pending(None) == -1
+    assert lib.rr_server_destroy(None) == 0
 
 
 @pytest.mark.parametrize("field,value,msg", [("zcut", 1.5, b"zcut"), ("nzin", 0, b"nzin"), ("ng", 1, b"ng"),

@@ -106,6 +106,20 @@ class Done:
     server_ns: Optional[tuple] = None
 
 
+def _check_shapes(req: ServeRequest, nparam: int) -> None:
+    """The array shapes a model's request must have (its rows are read with these strides)."""
+    ps = req.params.shape
+    if len(ps) != 2 or ps[1] != nparam:
+        raise ValueError(f"params must have shape (npv, {nparam})")
+    npt = req.times.shape[0]
+    pb = req.pb_index
+    if pb is not None and (len(pb.shape) != 1 or pb.shape[0] != npt):
+        raise ValueError("pb_index must have one entry per time")
+    g = req.grad_flux
+    if g is not None and (len(g.shape) != 2 or g.shape[0] != ps[0] or g.shape[1] != npt):
+        raise ValueError(f"grad_flux must have shape ({ps[0]}, {npt})")
+
+
 def _done_record(req: ServeRequest, ok: bool) -> Done:
     t_int = req.t_arrival if req.t_intended is None else req.t_intended
     return Done(req.id, req.points, ok, req.t_arrival, req.t_admit, req.t_finish, t_int, req.server_ns)
@@ -319,7 +333,9 @@ class CudaBackend(Backend):
 
     def nbytes(self, req: ServeRequest) -> int:
         """Device bytes of the request: its scratch for rr_enqueue_host (inputs, outputs, workspace)."""
-        return self.fits[req.fit].request_bytes(req.npv, req.npt, req.grad_flux is not None)
+        m = self.fits[req.fit]
+        _check_shapes(req, m.nparam)
+        return m.request_bytes(req.npv, req.npt, req.grad_flux is not None)
 
     def prepare(self, req: ServeRequest) -> None:
         """Pinned host inputs and pinned result buffers (submitting thread).  Inputs
@@ -434,6 +450,7 @@ class NativeServer:
         latency counts from that time even when the submit call comes later."""
         rr = self.rr
         m = self.fits[req.fit]
+        _check_shapes(req, m.nparam)
         req.t_arrival = time.perf_counter()
         release = 0 if req.t_intended is None else max(1, int(req.t_intended * 1e9) + self._clock_off)
         req.points

@@ -172,3 +172,16 @@ def test_request_points_is_the_sample_count(ss, npb):
     brute = npv * sum(1 if ss is None else ss[b] for b in pb)
     assert r.points == brute
     assert ServeRequest(fit=0, times=np.zeros(npt), params=np.zeros((npv, 9)), npoints=12).points == 12
+
+
+def test_request_shapes_are_checked():
+    from paper_2009_08500_gb300.serve import _check_shapes
+    ok = ServeRequest(fit=0, times=np.zeros(10), params=np.zeros((3, 9)), pb_index=np.zeros(10, np.int32),
+                      grad_flux=np.zeros((3, 10)))
+    _check_shapes(ok, 9)
+    with pytest.raises(ValueError, match="params"):
+        _check_shapes(ok, 11)
+    with pytest.raises(ValueError, match="pb_index"):
+        _check_shapes(ServeRequest(fit=0, times=np.zeros(10), params=np.zeros((3, 9)), pb_index=np.zeros(9)), 9)
+    with pytest.raises(ValueError, match="grad_flux"):
+        _check_shapes(ServeRequest(fit=0, times=np.zeros(10), params=np.zeros((3, 9)), grad_flux=np.zeros((3, 9))), 9)

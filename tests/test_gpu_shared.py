@@ -135,3 +135,22 @@ def test_transmission_workload_full_launch_sampled_rows(rr):
     sub.params = wl.params[rows]
     ref = om.evaluate_workload(sub)
     assert np.abs(f[rows] - ref).max() <= 1e-6
+
+
+def test_transmission_workload_full_launch_sampled_rows(rr):
+    """The full transmission-spectroscopy launch the benchmark times (2,048 pvs x 8 channels x
+    2,500 times, direct model, shared weights, mixed form): flux of sampled rows against the
+    oracle at 1e-6, and every row valid."""
+    import torch
+    wl = W.make_ts()
+    m = rr.model_for(wl)
+    t, pb, p = rr.to_device(wl)
+    st = torch.full((wl.npv,), -1, dtype=torch.int32, device=t.device)
+    f = m.evaluate(t, p, pb, wl.supersampling, wl.exptime, pv_status=st).double().cpu().numpy()
+    assert f.shape == (2048, 20000) and not st.cpu().numpy().any()
+    rows = np.random.default_rng(2).choice(2048, 5, replace=False)
+    sub = wl.subset(2048)
+    sub.params = wl.params[rows]
+    ref = om.evaluate_workload(sub, _setup(sub))
+    assert (ref < 1).sum() > 100
+    assert np.abs(f[rows] - ref).max() <= 1e-6

@@ -854,6 +854,12 @@ def serving(a, local, seconds):
 
     def mk(k):
         k %= len(pool)
+        # a pooled request whose result sets are all in flight gives way to the next one with a
+        # free set (pinning a new set, up to 134 MB, inside a timed window stalls the client)
+        for d in range(len(pool)):
+            if free_out[(k + d) % len(pool)]:
+                k = (k + d) % len(pool)
+                break
         fl = free_out[k]
         if not fl:
             pinned_in_run[0] += 1
@@ -932,8 +938,9 @@ def serving(a, local, seconds):
                        "request_pool": npool, "mean_points_per_request": mean_pts,
                        "client": "Python open-loop generator: Poisson arrival times, each request submitted up to "
                                  "5 ms ahead and released by the library at its arrival time; pinned result "
-                                 "buffers reused (6 sets per pooled request, pinned before the timed windows); the "
-                                 "client's garbage collector paused in each timed window",
+                                 "buffers reused (6 sets per pooled request, pinned before the timed windows; a "
+                                 "pick whose sets are all in flight takes the next pooled request with a free set); "
+                                 "the client's garbage collector paused in each timed window",
                        "server_lifetime": "one server for the warm-up, the capacity window and the open-loop windows",
                        "deviations": "requests capped at 2^25 points (the stated log-uniform square reaches "
                                      "4096 x 2e5 = 8.2e8 points); 96 requests drawn once from that distribution "

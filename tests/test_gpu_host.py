@@ -1,5 +1,8 @@
 """Host buffers in and out (rr_evaluate_host, rr_enqueue_host).
 
+The Python binding pins what it is given, so its calls take the in-place
+path; the staged path is reached through the C ABI with numpy buffers.
+
 Page-locked buffers are read and written in place by the kernels; any other
 host memory goes through the staged path (pv chunks pipelined over copy and
 compute streams).  Both must give bitwise the results of one device call on
@@ -33,13 +36,14 @@ def test_host_pipeline_matches_one_device_call(rr, ld, npb, ss, chunk):
     ref = m.evaluate(t, p, pb, wl.supersampling, wl.exptime).cpu()
     gbar = np.random.default_rng(3).normal(size=(wl.npv, wl.npt)).astype(np.float32)
     gref = m.evaluate_grad(t, p, torch.as_tensor(gbar, device=t.device), pb, wl.supersampling, wl.exptime).cpu()
-    # pageable numpy inputs, ragged last chunk
+    # numpy inputs (the binding pins them: the in-place path, chunk_pvs unused)
     f, g, st = m.evaluate_host(wl.times, wl.params, wl.pb_index, wl.supersampling, wl.exptime, grad_flux=gbar,
                                chunk_pvs=chunk)
+    assert m.host_path == "in place"
     assert torch.equal(f, ref)
     assert torch.equal(g, gref)
     assert not st.any()
-    # forward only, pinned result buffers, one chunk
+    # forward only, pinned result buffers
     out = torch.empty_like(ref).pin_memory()
     f2, g2, _ = m.evaluate_host(wl.times, wl.params, wl.pb_index, wl.supersampling, wl.exptime, out=out,
                                 chunk_pvs=1000)
@@ -58,7 +62,8 @@ def test_host_pipeline_status_and_empty(rr):
 
 
 def test_default_chunking_of_a_large_batch_matches_one_device_call(rr):
-    """The default chunking (about eight chunks of at least 512 pvs) on a batch of several chunks."""
+    """A batch of several default chunks (about eight chunks of at least 512 pvs): in place through
+    the binding, and staged (pageable buffers through the C ABI, default chunking)."""
     import torch
     wl = W.make_small("quadratic_tri", npv=2100, npt=256, seed=29)
     m = rr.model_for(wl)
@@ -71,6 +76,14 @@ def test_default_chunking_of_a_large_batch_matches_one_device_call(rr):
     assert torch.equal(torch.nan_to_num(g, nan=-1.0), torch.nan_to_num(gref, nan=-1.0))
     f2, _, st2 = m.evaluate_host(wl.times, wl.params, wl.pb_index, wl.supersampling, wl.exptime)
     assert torch.equal(f2, ref) and torch.equal(st2, st)
+    g64 = gbar.astype(np.float32)
+    flux = np.zeros((wl.npv, wl.npt), np.float32)
+    gp = np.zeros((wl.npv, m.nparam))
+    status = np.full(wl.npv, -1, np.int32)
+    assert _c_host_call(m, wl, g64, flux, gp, status, 0) == 0
+    assert m.host_path == "staged"
+    assert torch.equal(torch.from_numpy(flux), ref)
+    assert torch.equal(torch.nan_to_num(torch.from_numpy(gp), nan=-1.0), torch.nan_to_num(gref, nan=-1.0))
 
 
 def _c_host_call(m, wl, gbar, flux, grad, status, chunk):

@@ -309,24 +309,34 @@ def measure(a, name, steps, world, local, dev, flush):
 
     def step():
         if grad:
-            # a fit step: one shared set-up, the light curves, then the adjoint
+            # a fit step with its cotangent: one shared set-up, then the light curves and the
+            # adjoint (on the context's second stream, beside the forward kernel)
+            model.prepare(t, p, pb, ss, ex, workspace=ws_g)
+            model.evaluate_both(t, p, gbar, ws_g, pb, ss, ex, out=flux, grad_out=gout)
+        else:
+            model.evaluate(t, p, pb, ss, ex, out=flux, workspace=ws_f)
+
+    def step_one_stream():
+        # the same work with every kernel on the launching stream (each kernel's own duration
+        # for the rooflines, without the other kernel beside it)
+        if grad:
             model.prepare(t, p, pb, ss, ex, workspace=ws_g)
             model.evaluate(t, p, pb, ss, ex, out=flux, prepared=ws_g)
             model.evaluate_grad(t, p, gbar, pb, ss, ex, out=gout, prepared=ws_g)
         else:
-            model.evaluate(t, p, pb, ss, ex, out=flux, workspace=ws_f)
+            step()
 
     for _ in range(max(a.warmup, 3)):
         step()
     torch.cuda.synchronize()
     n_launch0 = model.launch_count
 
-    def timed_steps(k):
+    def timed_steps(k, fn=step):
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
         for i in range(k):
             flush.fill_(i & 0xFF)               # L2 flush between steps
             ev[i][0].record()
-            step()
+            fn()
             ev[i][1].record()
         torch.cuda.synchronize()
         return [s.elapsed_time(e) for s, e in ev]
@@ -340,10 +350,11 @@ def measure(a, name, steps, world, local, dev, flush):
         torch.distributed.barrier()
     launches = model.launch_count - n_launch0
     # the same K steps again with CUDA events around every kernel launch (per-kernel
-    # durations for the rooflines; the events themselves lengthen these steps a little)
+    # durations for the rooflines; the events themselves lengthen these steps a little), every
+    # kernel on one stream so that each duration is the kernel's own
     model.profile(True)
     model.profile_read(reset=True)
-    prof_ms = timed_steps(steps)
+    prof_ms = timed_steps(steps, step_one_stream)
     kprof = model.profile_read(reset=True)
     model.profile(False)
     tot_ms = sum(step_ms)
@@ -608,30 +619,38 @@ def run_variant(a, wl, grad, local, dev, flush, **change):
     def step():
         if grad:
             md.prepare(t, p, pb, ss, ex, workspace=ws_g)
+            md.evaluate_both(t, p, gbar, ws_g, pb, ss, ex, out=flux, grad_out=gout)
+        else:
+            md.evaluate(t, p, pb, ss, ex, out=flux, workspace=ws_f)
+
+    def step_one_stream():
+        if grad:
+            md.prepare(t, p, pb, ss, ex, workspace=ws_g)
             md.evaluate(t, p, pb, ss, ex, out=flux, prepared=ws_g)
             md.evaluate_grad(t, p, gbar, pb, ss, ex, out=gout, prepared=ws_g)
         else:
-            md.evaluate(t, p, pb, ss, ex, out=flux, workspace=ws_f)
+            step()
 
     for _ in range(3):
         step()
     n = 10
 
-    def run(k):
+    def run(k, fn=step):
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
         torch.cuda.synchronize()
         for i in range(k):
             flush.fill_(i & 0xFF)
             ev[i][0].record()
-            step()
+            fn()
             ev[i][1].record()
         torch.cuda.synchronize()
         return sum(s.elapsed_time(e) for s, e in ev) / k
 
     ms = run(n)
+    # per-kernel durations with every kernel on one stream (each kernel's own time)
     md.profile(True)
     md.profile_read(reset=True)
-    run(n)
+    run(n, step_one_stream)
     kp = md.profile_read(reset=True)
     md.profile(False)
     dms, dn = kp["direct"]

@@ -276,6 +276,24 @@ rr_status rr_evaluate_grad_prepared(rr_ctx* ctx, const double* times, const int3
                                     const void* grad_flux, double* grad_params, int32_t* pv_status,
                                     const void* workspace, size_t workspace_bytes, void* stream);
 
+/* The light curves and the adjoint of a prepared batch for a cotangent known
+ * in advance (Eq. 5 and the vector-Jacobian product of rr_evaluate_grad):
+ * rr_evaluate_prepared and rr_evaluate_grad_prepared in one call, the adjoint
+ * on a second stream of the context that forks from `stream` and joins it
+ * again, so that the adjoint (latency-bound) runs beside the forward kernel
+ * (an output stream).  Arguments as the two calls; flux and grad_params both
+ * written; results bitwise those of the two calls.  The paper has no
+ * counterpart.  The context's second stream is created on first use and
+ * freed by rr_destroy; like every entry point, calls on one context must not
+ * overlap in time.  Errors: as the two calls, plus RR_ECUDA for the stream
+ * or its events. */
+rr_status rr_evaluate_both_prepared(rr_ctx* ctx, const double* times, const int32_t* pb_index,
+                                    int32_t npt, const double* params, int32_t npv,
+                                    const int32_t* supersampling, const double* exptime,
+                                    const void* grad_flux, void* flux, double* grad_params,
+                                    int32_t* pv_status, const void* workspace, size_t workspace_bytes,
+                                    void* stream);
+
 /* Evaluate host-resident batches: host arrays in, host arrays out.  Light
  * curves (Eq. 5 with the supersampling of Sect. 4.1) and, when grad_flux is
  * given, the adjoint of rr_evaluate_grad, for data that live in host memory.

@@ -66,6 +66,11 @@ cudaError_t dalloc(T** p, size_t n) {
 
 void free_all(rr_ctx* c) {
     release_host_pipe(c);
+    if (c->aux) cudaStreamDestroy(c->aux);
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
+    c->aux = nullptr;
+    c->ev_fork = c->ev_join = nullptr;
     for (auto& t : c->timed) { cudaEventDestroy(t.a); cudaEventDestroy(t.b); }
     for (auto e : c->ev_pool) cudaEventDestroy(e);
     c->timed.clear();
@@ -545,6 +550,36 @@ rr_status rr_evaluate_grad_prepared(rr_ctx* c, const double* times, const int32_
     NvtxRange nvtx_range("rr_evaluate_grad_prepared");
     return evaluate_grad_impl(c, times, pb_index, npt, params, npv, ss, exptime, grad_flux, grad_params, pv_status,
                               const_cast<void*>(ws), ws_bytes, true, stream);
+}
+
+rr_status rr_evaluate_both_prepared(rr_ctx* c, const double* times, const int32_t* pb_index, int32_t npt,
+                                    const double* params, int32_t npv, const int32_t* ss, const double* exptime,
+                                    const void* grad_flux, void* flux, double* grad_params, int32_t* pv_status,
+                                    const void* ws, size_t ws_bytes, void* stream) {
+    NvtxRange nvtx_range("rr_evaluate_both_prepared");
+    if (!c) return fail(nullptr, RR_EINVAL, "null context");
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaSetDevice(c->cfg.device);
+    if (e == cudaSuccess && !c->aux) e = cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking);
+    if (e == cudaSuccess && !c->ev_fork) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess && !c->ev_join) e = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
+    // the adjoint (and its finish kernel) on the second stream, after everything before on s
+    if (e == cudaSuccess) e = cudaEventRecord(c->ev_fork, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(c->aux, c->ev_fork, 0);
+    if (e != cudaSuccess) return cuda_fail(c, e, "rr_evaluate_both_prepared");
+    // the adjoint first: it is the longer of the two, and the forward kernel's CTAs fill in
+    rr_status st = evaluate_grad_impl(c, times, pb_index, npt, params, npv, ss, exptime, grad_flux, grad_params,
+                                      pv_status, const_cast<void*>(ws), ws_bytes, true, c->aux);
+    const rr_status st2 = st == RR_OK ? evaluate_impl(c, times, pb_index, npt, params, npv, ss, exptime, flux,
+                                                      pv_status, const_cast<void*>(ws), ws_bytes, true, stream)
+                                      : st;
+    // s waits for the second stream whatever happened, so that nothing of this call is left behind it
+    e = cudaEventRecord(c->ev_join, c->aux);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, c->ev_join, 0);
+    if (st != RR_OK) return st;
+    if (st2 != RR_OK) return st2;
+    if (e != cudaSuccess) return cuda_fail(c, e, "rr_evaluate_both_prepared");
+    return RR_OK;
 }
 
 int64_t rr_read_table(rr_ctx* c, int32_t which, double* out, int64_t capacity) {

@@ -96,9 +96,12 @@ InPlace map_in_place(const rr_ctx* c, const double* times, const int32_t* pb_ind
 
 // One evaluation (and adjoint) on the mapped buffers, enqueued on s.
 rr_status run_in_place(rr_ctx* c, const InPlace& m, int32_t npt, int32_t npv, const int32_t* ss,
-                       const double* exptime, void* ws, size_t ws_bytes, cudaStream_t s) {
+                       const double* exptime, void* ws, size_t ws_bytes, cudaStream_t s, bool overlap) {
     if (!m.g) return rr_evaluate(c, m.t, m.pb, npt, m.p, npv, ss, exptime, m.f, m.st, ws, ws_bytes, s);
     rr_status st = rr_prepare(c, m.t, m.pb, npt, m.p, npv, ss, exptime, m.st, ws, ws_bytes, s);
+    if (st == RR_OK && overlap)
+        return rr_evaluate_both_prepared(c, m.t, m.pb, npt, m.p, npv, ss, exptime, m.g, m.f, m.go, m.st, ws, ws_bytes,
+                                         s);
     if (st == RR_OK) st = rr_evaluate_prepared(c, m.t, m.pb, npt, m.p, npv, ss, exptime, m.f, m.st, ws, ws_bytes, s);
     if (st == RR_OK)
         st = rr_evaluate_grad_prepared(c, m.t, m.pb, npt, m.p, npv, ss, exptime, m.g, m.go, m.st, ws, ws_bytes, s);
@@ -144,7 +147,7 @@ extern "C" rr_status rr_evaluate_host(rr_ctx* c, const double* times, const int3
             const size_t wsb = up256(rr_workspace_bytes(c, npv, npt, grad ? 1 : 0));
             if ((e = ensure_pipe(c, wsb)) != cudaSuccess) return pipe_fail(c, e, "rr_evaluate_host set-up");
             cudaStream_t s = c->pipe.s[1];
-            const rr_status st = run_in_place(c, m, npt, npv, ss, exptime, c->pipe.buf, wsb, s);
+            const rr_status st = run_in_place(c, m, npt, npv, ss, exptime, c->pipe.buf, wsb, s, true);
             e = cudaStreamSynchronize(s);
             if (st != RR_OK) return st;
             if (e != cudaSuccess) return pipe_fail(c, e, "rr_evaluate_host");
@@ -312,7 +315,7 @@ extern "C" rr_status rr_enqueue_host(rr_ctx* c, const double* times, const int32
         return RR_EINVAL;
     }
     c->host_path = m.ok ? RR_HOST_IN_PLACE : RR_HOST_STAGED;
-    if (m.ok) return run_in_place(c, m, npt, npv, ss, exptime, scratch, L.ws_bytes, (cudaStream_t)stream);
+    if (m.ok) return run_in_place(c, m, npt, npv, ss, exptime, scratch, L.ws_bytes, (cudaStream_t)stream, false);
     const size_t es = c->cfg.precision == RR_PREC_FP64 ? sizeof(double) : sizeof(float);
     const int np = c->nparam;
     char* b = (char*)scratch;

@@ -254,6 +254,10 @@ struct rr_ctx {
     std::vector<Timed> timed;
     double prof_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     long long prof_n[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    // second stream of rr_evaluate_both_prepared (the adjoint beside the forward kernel) and its
+    // fork and join events, created on first use
+    cudaStream_t aux = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     // host-buffer pipeline (rr_evaluate_host): copy-in, compute and copy-out
     // streams, per-slot events, one grow-only device buffer
     struct HostPipe {
@@ -348,9 +352,10 @@ InPlace map_in_place(const rr_ctx* c, const double* times, const int32_t* pb_ind
                      const double* params, int32_t npv, const void* grad_flux, void* flux, double* grad_params,
                      int32_t* pv_status);
 // One evaluation (with the adjoint when m.g is set) on mapped buffers, enqueued on s; ws is a
-// device workspace of ws_bytes >= rr_workspace_bytes.
+// device workspace of ws_bytes >= rr_workspace_bytes.  overlap: the forward and adjoint kernels
+// on s and the context's second stream (rr_evaluate_both_prepared).
 rr_status run_in_place(rr_ctx* c, const InPlace& m, int32_t npt, int32_t npv, const int32_t* ss,
-                       const double* exptime, void* ws, size_t ws_bytes, cudaStream_t s);
+                       const double* exptime, void* ws, size_t ws_bytes, cudaStream_t s, bool overlap);
 inline bool in_device_memory(const void* p) {
     cudaPointerAttributes a;
     if (!p || cudaPointerGetAttributes(&a, p) != cudaSuccess) {

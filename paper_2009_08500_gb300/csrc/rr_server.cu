@@ -112,7 +112,7 @@ void enqueue(rr_server* s, Request& r, Slot& sl) {
     if (e == cudaSuccess) {
         r.result = r.in_place.ok
                        ? rr::run_in_place(r.fit, r.in_place, r.npt, r.npv, r.ss.data(), r.exptime.data(), scratch,
-                                          bytes, sl.stream)
+                                          bytes, sl.stream, false)
                        : rr_enqueue_host(r.fit, r.times, r.pb, r.npt, r.params, r.npv, r.ss.data(),
                                          r.exptime.data(), r.grad_flux, r.flux, r.grad, r.status, scratch, bytes,
                                          sl.stream);

@@ -35,7 +35,7 @@ EXPORTS = ["rr_create", "rr_destroy", "rr_set_ld_profile", "rr_build_weights", "
            "rr_evaluate_noalloc", "rr_prepare", "rr_evaluate_prepared", "rr_evaluate_grad_prepared",
            "rr_evaluate_host", "rr_request_bytes", "rr_enqueue_host", "rr_server_create", "rr_server_destroy",
            "rr_server_submit", "rr_server_submit_at", "rr_server_now_ns", "rr_server_poll", "rr_server_pending", "rr_exact_flux", "rr_choose_grid",
-           "rr_selftest_wait", "rr_count_samples", "rr_count_read", "rr_host_path"]
+           "rr_selftest_wait", "rr_count_samples", "rr_count_read", "rr_host_path", "rr_evaluate_both_prepared"]
 KERNELS = {"ld_basis": 0, "weights": 1, "pv_setup": 2, "flux": 3, "grad": 4, "grad_reduce": 5, "points": 6,
            "direct": 7}
 #: sample counters of the counting form (include/rr.h RR_COUNT_*)
@@ -85,6 +85,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     L.rr_evaluate_grad_prepared.argtypes = [vp, vp, vp, i32, vp, i32, ctypes.POINTER(i32), dp, vp, vp, vp, vp, sz,
                                             vp]
     L.rr_evaluate_host.argtypes = [vp, vp, vp, i32, vp, i32, ctypes.POINTER(i32), dp, vp, vp, vp, vp, i32]
+    L.rr_evaluate_both_prepared.argtypes = [vp, vp, vp, i32, vp, i32, ctypes.POINTER(i32), dp, vp, vp, vp, vp, vp,
+                                            sz, vp]
     L.rr_request_bytes.argtypes = [vp, i32, i32, i32]
     L.rr_request_bytes.restype = sz
     L.rr_enqueue_host.argtypes = [vp, vp, vp, i32, vp, i32, ctypes.POINTER(i32), dp, vp, vp, vp, vp, vp, sz, vp]
@@ -130,7 +132,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     for name in ("rr_exact_flux", "rr_choose_grid", "rr_selftest_wait", "rr_create", "rr_destroy", "rr_set_ld_profile", "rr_build_weights", "rr_evaluate",
                  "rr_evaluate_grad", "rr_sync_status", "rr_profile", "rr_profile_read", "rr_evaluate_noalloc",
                  "rr_prepare", "rr_evaluate_prepared", "rr_evaluate_grad_prepared", "rr_evaluate_host",
-                 "rr_enqueue_host", "rr_count_samples", "rr_count_read"):
+                 "rr_enqueue_host", "rr_count_samples", "rr_count_read", "rr_evaluate_both_prepared"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -395,6 +397,30 @@ class Model:
                 _stream_handle(stream))
         self._check(st)
         return out
+
+    def evaluate_both(self, times: torch.Tensor, params: torch.Tensor, grad_flux: torch.Tensor,
+                      prepared: torch.Tensor, pb_index: Optional[torch.Tensor] = None, supersampling=None,
+                      exptime=None, out: Optional[torch.Tensor] = None, grad_out: Optional[torch.Tensor] = None,
+                      pv_status: Optional[torch.Tensor] = None, stream=None):
+        """(flux, grad_params) of a batch prepared by :meth:`prepare`, for a cotangent known in advance
+        (rr_evaluate_both_prepared): the adjoint on a second stream of the context, beside the
+        forward kernel; bitwise :meth:`evaluate` and :meth:`evaluate_grad` with ``prepared``."""
+        npt, npv = self._inputs(times, params, pb_index)
+        if not (grad_flux.dtype == self.dtype and grad_flux.is_contiguous() and grad_flux.shape == (npv, npt)):
+            raise TypeError(f"grad_flux must be a contiguous {self.dtype} tensor of shape ({npv}, {npt})")
+        ss = _host_array(supersampling, self.npb, np.int32, 1)
+        ex = _host_array(exptime, self.npb, np.float64, 0.0)
+        if out is None:
+            out = torch.empty((npv, npt), dtype=self.dtype, device=self.device)
+        if grad_out is None:
+            grad_out = torch.empty((npv, self.nparam), dtype=torch.float64, device=self.device)
+        st = self.lib.rr_evaluate_both_prepared(self._h, _ptr(times), _ptr(pb_index), npt, _ptr(params), npv,
+                                                ss.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                                ex.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                                _ptr(grad_flux), _ptr(out), _ptr(grad_out), _ptr(pv_status),
+                                                _ptr(prepared), prepared.numel(), _stream_handle(stream))
+        self._check(st)
+        return out, grad_out
 
     def evaluate_host(self, times, params, pb_index=None, supersampling=None, exptime=None, grad_flux=None,
                       chunk_pvs: Optional[int] = None, out=None, grad_out=None, status_out=None):

@@ -168,6 +168,41 @@ def test_c4_heterogeneous_full_launch_sampled_rows(rr):
     assert np.abs(f[rows] - ref).max() <= 1e-6
 
 
+def _sampled_rows(rr, wl, rows):
+    """Evaluate the whole batch on the device; bring back only ``rows`` and the status words."""
+    import torch
+    m = rr.model_for(wl)
+    t, pb, p = rr.to_device(wl)
+    st = torch.full((wl.npv,), -1, dtype=torch.int32, device=t.device)
+    f = m.evaluate(t, p, pb, wl.supersampling, wl.exptime, pv_status=st)
+    torch.cuda.synchronize()
+    m.sync_status()
+    idx = torch.as_tensor(rows, device=f.device)
+    out = f[idx].double().cpu().numpy(), st.cpu().numpy(), f.shape, int((f < 1).sum())
+    del f
+    torch.cuda.empty_cache()
+    return out
+
+
+def _rows_oracle(wl, rows):
+    sub = wl.subset(len(rows))
+    sub.params = wl.params[rows].copy()
+    return oracle_flux(sub)[0]
+
+
+@pytest.mark.parametrize("npv,npt", [(300_000, 640), (40_000, 60_000)])
+def test_large_batches_sampled_rows(rr, npv, npt):
+    """Large batches: 300,000 pvs (9,375 pv tiles on the grid) and 40,000 pvs x 60,000 times
+    (2.4e9 flux elements, past 2^31, so the last rows sit beyond any 32-bit element offset).
+    Sampled rows, the first and the last pv among them, against the oracle."""
+    wl = W.make_small("quadratic_tri", npv=npv, npt=npt, seed=41, span=3.0, eccentric=False)
+    rows = np.concatenate([[0, npv - 1], np.sort(np.random.default_rng(5).choice(npv - 1, 10, replace=False))])
+    f, st, shape, n_in = _sampled_rows(rr, wl, rows)
+    assert tuple(shape) == (npv, npt) and not st.any()
+    assert np.abs(f - _rows_oracle(wl, rows)).max() <= TOL["mixed"]
+    assert n_in > npv                      # every pv transits within the 3-day span
+
+
 def test_out_of_transit_is_exactly_one(rr):
     wl = W.make_small("nonlinear", npv=16, npt=3000, seed=9, span=10.0)
     f, _ = gpu_flux(rr, wl, "mixed")

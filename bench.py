@@ -51,7 +51,7 @@ CONFIG_TEXT = {
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch, from one ncu capture
 # of the same kernels (profiles/flux_mixed_c4_heterogeneous.md, flux_mixed_c3_population.md,
 # grad_mixed_c3_population.md); to be cleared whenever those kernels change
-TRAFFIC = {("c4", "flux"): 449_894_912, ("c3", "flux"): 273_600_256, ("c3", "grad"): 39_271_936}
+TRAFFIC = {}
 
 
 # Algorithmic FP32 operations (add, multiply, fused multiply-add: one each) and MUFU operations

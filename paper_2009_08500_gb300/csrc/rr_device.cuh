@@ -48,8 +48,20 @@ __device__ __forceinline__ float atan2_upper(float y, float x) {
     return a;
 }
 
+// FP32 square root by the approximate instruction (relative error of order
+// 2^-23, against half an ulp for the rounding-exact sqrtf, whose special-case
+// handling costs issue slots on every sample): z and the lens chord K carry
+// several ulp of orbit rounding already.
+__device__ __forceinline__ float sqrt_approx(float x) {
+    float r;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
 __device__ __forceinline__ float d_sqrt(float x) { return sqrtf(x); }
 __device__ __forceinline__ double d_sqrt(double x) { return sqrt(x); }
+// the per-sample square roots (z, the lens chord): approximate in FP32
+__device__ __forceinline__ float d_sqrt_sample(float x) { return sqrt_approx(x); }
+__device__ __forceinline__ double d_sqrt_sample(double x) { return sqrt(x); }
 // the covered area's half-angles: the upper-half-plane arctangent (y = K >= 0)
 __device__ __forceinline__ float d_atan2(float y, float x) { return atan2_upper(y, x); }
 __device__ __forceinline__ double d_atan2(double y, double x) { return atan2(y, x); }
@@ -88,7 +100,7 @@ __device__ __forceinline__ R covered_area_f13(R k, R z, R f1, R f3, R& dAdz, R& 
     const R f4 = z + (one + k);
     R h = (f1 * f2) * (f3 * f4);
     h = h > R(0) ? h : R(0);
-    const R K = d_sqrt(h);
+    const R K = d_sqrt_sample(h);
     const R zz = z * z, kk = k * k;
     const R kap0 = d_atan2(K, zz + (one - kk));
     const R kap1 = d_atan2(K, zz + (kk - one));
@@ -372,7 +384,7 @@ __device__ __forceinline__ Orbit32 orbit32(const PvHead<float>& H, float dM, dou
     o.x = x;
     o.Px = fmaf(H.ax1, o.V, H.ax2 * o.S);
     o.Py = H.rho0 + fmaf(H.ay1, o.V, H.ay2 * o.S);
-    o.z = sqrtf(fmaf(H.a2 * o.Px, o.Px, H.b2 * o.Py * o.Py));
+    o.z = sqrt_approx(fmaf(H.a2 * o.Px, o.Px, H.b2 * o.Py * o.Py));
     o.front = o.Py > 0.0f;
     return o;
 }

@@ -364,27 +364,51 @@ struct Orbit32 {
 // Projected distance from the mean-anomaly offset dM = M - M0 (radians).
 // dMd: the same offset in FP64, used when e > kESwitch.  iters: the Newton
 // iterations of the FP32 Kepler solve (0 otherwise).
+// The FP32 header's per-sample constants sit in aligned quadruples, each read
+// with one 16-byte load (the header is 16-byte aligned in shared or global
+// memory: records are multiples of 16 bytes from a 16-byte aligned base).
+static_assert(offsetof(PvHead<float>, wmax_c) % 16 == 0 && offsetof(PvHead<float>, kepC) == offsetof(PvHead<float>, wmax_c) + 12,
+              "wmax_c, kep2, kep3, kepC: one quadruple");
+static_assert(offsetof(PvHead<float>, a) % 16 == 0 && offsetof(PvHead<float>, b2) == offsetof(PvHead<float>, a) + 12,
+              "a, b, a2, b2: one quadruple");
+static_assert(offsetof(PvHead<float>, e) % 16 == 0 && offsetof(PvHead<float>, inv_den0) == offsetof(PvHead<float>, e) + 12,
+              "e, ecE0, esE0, inv_den0: one quadruple");
+static_assert(offsetof(PvHead<float>, ax1) % 16 == 0 && offsetof(PvHead<float>, ay2) == offsetof(PvHead<float>, ax1) + 12,
+              "ax1, ax2, ay1, ay2: one quadruple");
+static_assert(offsetof(PvHead<float>, rho0) % 16 == 0 && offsetof(PvHead<float>, Bl) == offsetof(PvHead<float>, rho0) + 12,
+              "rho0, n, Bh, Bl: one quadruple");
+static_assert(sizeof(PvHead<float>) % 16 == 0 && alignof(PvHead<float>) == 16, "16-byte header");
+static_assert(offsetof(PvPb<float>, k) == 0 && offsetof(PvPb<float>, win_p) == 12 && alignof(PvPb<float>) == 16,
+              "k, inv1pk, win_s, win_p: one quadruple");
+__device__ __forceinline__ float4 quad(const float& first) { return *reinterpret_cast<const float4*>(&first); }
+
 __device__ __forceinline__ Orbit32 orbit32(const PvHead<float>& H, float dM, double dMd, int& iters) {
     Orbit32 o;
     o.ok = true;
     iters = 0;
     float x;
-    if (H.flags & kPvCircular) {
+    const int flags = H.flags;
+    if (flags & kPvCircular) {
         half_angle_SV(dM, o.S, o.V);
         x = dM;
-    } else if (H.flags & kPvKepler64) {
+    } else if (flags & kPvKepler64) {
         double xd, Sd, Vd;
         o.ok = kepler_offset_f64(dMd, H.ecE0d, H.esE0d, H.inv_den0d, xd, Sd, Vd);
         o.S = (float)Sd;
         o.V = (float)Vd;
         x = (float)xd;
     } else {
-        o.ok = kepler_offset_f32(dM, H.ecE0, H.esE0, H.inv_den0, H.kep2, H.kep3, H.kepC, x, o.S, o.V, iters);
+        const float4 ke = quad(H.e);        // e, ecE0, esE0, inv_den0
+        const float4 ks = quad(H.wmax_c);   // wmax_c, kep2, kep3, kepC
+        o.ok = kepler_offset_f32(dM, ke.y, ke.z, ke.w, ks.y, ks.z, ks.w, x, o.S, o.V, iters);
     }
     o.x = x;
-    o.Px = fmaf(H.ax1, o.V, H.ax2 * o.S);
-    o.Py = H.rho0 + fmaf(H.ay1, o.V, H.ay2 * o.S);
-    o.z = sqrt_approx(fmaf(H.a2 * o.Px, o.Px, H.b2 * o.Py * o.Py));
+    const float4 ax = quad(H.ax1);          // ax1, ax2, ay1, ay2
+    const float4 ab = quad(H.a);            // a, b, a2, b2
+    const float rho0 = H.rho0;
+    o.Px = fmaf(ax.x, o.V, ax.y * o.S);
+    o.Py = rho0 + fmaf(ax.z, o.V, ax.w * o.S);
+    o.z = sqrt_approx(fmaf(ab.z * o.Px, o.Px, ab.w * o.Py * o.Py));
     o.front = o.Py > 0.0f;
     return o;
 }
@@ -833,10 +857,10 @@ __device__ __forceinline__ void tally_flush(const Tally& t, unsigned long long* 
 // sample's work to `tl`.
 template <bool COUNT = false>
 __device__ __forceinline__ float delta32(const PvHead<float>& H, const PvPb<float>& pbc, const float* __restrict__ row,
-                                         int ng, float fr_h, float fr_l, int s, float first, float step, bool& bad,
+                                         int ng, float fr_h, float fr_l, float s, float first, float step, bool& bad,
                                          Tally* tl = nullptr) {
     if (COUNT) ++tl->n[RR_COUNT_SAMPLES];
-    const float off = fmaf((float)s, step, first) * H.Bh;   // sub-exposure offset, cycles
+    const float off = fmaf(s, step, first) * H.Bh;   // sub-exposure s (exact integer), offset in cycles
     float x = (fr_h + off) + fr_l;
     x -= round_nearest(x);
     const float dM = 6.28318530717958647692f * x;
@@ -858,15 +882,16 @@ __device__ __forceinline__ float delta32(const PvHead<float>& H, const PvPb<floa
         bad = true;
         return __int_as_float(0x7fc00000);
     }
-    const float g = o.z * pbc.inv1pk;
+    const float2 pq = *reinterpret_cast<const float2*>(&pbc.k);   // k, inv1pk
+    const float g = o.z * pq.y;
     if (!o.front || g >= 1.0f) return 0.0f;
     if (COUNT) {
         ++tl->n[RR_COUNT_TRANSIT];
-        if (o.z > fabsf(1.0f - pbc.k)) ++tl->n[RR_COUNT_LENS];
+        if (o.z > fabsf(1.0f - pq.x)) ++tl->n[RR_COUNT_LENS];
     }
     float d0, d1, sl;
     int cell;
-    const float A = covered_area<float, false>(pbc.k, o.z, d0, d1);
+    const float A = covered_area<float, false>(pq.x, o.z, d0, d1);
     return A * lerp_row<float>(row, ng, g, sl, cell);
 }
 

@@ -239,7 +239,7 @@ __global__ void __launch_bounds__(kBlock, 4) rr_flux_mixed_kernel(const double* 
                     const Phase32 ph = precise_phase(cd.x, cd.y, c.x, c.y, H.Bh, H.Bl);
                     if (COUNT) ++tl.n[RR_COUNT_TIMES];
                     wl->pacc[j] = delta32<COUNT>(H, PB[pb], rows + (size_t)pb * L.rows_per_pb * L.ng_pad, L.ng,
-                                                 ph.fr_h, ph.fr_l, 0, 0.0f, 0.0f, bad, &tl);
+                                                 ph.fr_h, ph.fr_l, 0.0f, 0.0f, 0.0f, bad, &tl);
                 }
             }
             __syncwarp();
@@ -271,9 +271,11 @@ __global__ void __launch_bounds__(kBlock, 4) rr_flux_mixed_kernel(const double* 
                 int j = lo;
                 int pw = wl->ps[j];
                 int next = wl->ps[j + 1] >> 5;     // first sample of candidate j + 1 (ps[nc] = ns << 5)
+                // the candidate's passband: its constants, profile row and sub-exposure spacing,
+                // looked up once per candidate rather than per sample
                 int pb = pw & 31;
                 float2 cd = wl->cand[j];
-                int sub = e_beg - (pw >> 5);
+                float sub = (float)(e_beg - (pw >> 5));
                 float part = 0.0f;
                 jh = j;
                 #pragma unroll 1
@@ -286,12 +288,12 @@ __global__ void __launch_bounds__(kBlock, 4) rr_flux_mixed_kernel(const double* 
                         next = wl->ps[j + 1] >> 5;
                         pb = pw & 31;
                         cd = wl->cand[j];
-                        sub = 0;
+                        sub = 0.0f;
                         part = 0.0f;
                     }
                     part += delta32<COUNT>(H, PB[pb], rows + (size_t)pb * L.rows_per_pb * L.ng_pad, L.ng, cd.x, cd.y,
                                            sub, ps->first[pb], ps->step[pb], bad, &tl);
-                    ++sub;
+                    sub += 1.0f;
                 }
                 if (j == jh) ph = part; else { jt = j; pt = part; }
             }

@@ -69,10 +69,15 @@ __device__ __forceinline__ void d_sincos(float x, float* s, float* c) { sincosf(
 __device__ __forceinline__ void d_sincos(double x, double* s, double* c) { sincos(x, s, c); }
 __device__ __forceinline__ float d_rint(float x) { return rintf(x); }
 __device__ __forceinline__ double d_rint(double x) { return rint(x); }
-// Reciprocal: correctly rounded single-instruction-sequence form in FP32 (the
-// FP32 adjoint's tolerance is far above its one-ulp difference from a true
-// division), an exact IEEE division in FP64.
-__device__ __forceinline__ float d_rcp(float x) { return __frcp_rn(x); }
+// Reciprocal: the approximate instruction in FP32 (within about an ulp; the
+// adjoint's per-sample 1 / z and 1 / (1 - e cos E), far from zero and from
+// the FP32 range limits, where the rounding-exact form's special-case handling
+// costs issue slots), an exact IEEE division in FP64.
+__device__ __forceinline__ float d_rcp(float x) {
+    float r;
+    asm("rcp.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
 __device__ __forceinline__ double d_rcp(double x) { return 1.0 / x; }
 
 // Area covered by a planet of radius k at centre distance z on a unit stellar

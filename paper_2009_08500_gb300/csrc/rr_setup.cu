@@ -602,6 +602,11 @@ struct SmallPlanetRow {
     double kw;
     double ud[5];   // weights of the bases: 1, then the coefficients
     int b0, nc;
+    // FP32 copies for the FP32 rows, converted once per row (FP64 issues at a small
+    // fraction of the FP32 rate on this GPU, conversions included)
+    float kw1f;     // 1 + kw
+    float udf[5];
+    float mu_minf, dgf;
 };
 
 __device__ double small_planet_node(const ModelParams& mp, const SmallPlanetRow& sp, const double* tab,
@@ -681,19 +686,19 @@ __device__ __forceinline__ float ld_basis_mu_f(const ModelParams& mp, int b, flo
 __device__ __forceinline__ float small_planet_node_f(const ModelParams& mp, const SmallPlanetRow& sp,
                                                      const double* tab, const int* tab_off, int i, float* vb,
                                                      float& dk) {
-    const float gi = (float)(i * mp.dg), cc = gi * (1.0f + (float)sp.kw);
+    const float gi = (float)i * sp.dgf, cc = gi * sp.kw1f;
     const float cm = fminf(cc, 1.0f);
     const float m0 = sqrtf(fmaxf((1.0f - cm) * (1.0f + cm), 0.0f));
-    const bool free = cc < 1.0f && m0 > (float)mp.mu_min;
-    const float m = free ? m0 : (float)mp.mu_min;
+    const bool free = cc < 1.0f && m0 > sp.mu_minf;
+    const float m = free ? m0 : sp.mu_minf;
     const float dmdk = free ? -cc * gi / m : 0.0f;
     float v = 0.0f, dv = 0.0f;
     for (int c = 0; c <= sp.nc; ++c) {
         float dd;
         const float bv = ld_basis_mu_f(mp, sp.b0 + c, m, tab, tab_off, dd);
         vb[c] = bv;
-        v += (float)sp.ud[c] * bv;
-        dv += (float)sp.ud[c] * dd;
+        v += sp.udf[c] * bv;
+        dv += sp.udf[c] * dd;
     }
     dk = dv * dmdk;
     return v;
@@ -1081,6 +1086,11 @@ __global__ void __launch_bounds__(256, 4) rr_pv_setup_kernel(ModelParams mp, PbP
             sp.ud[0] = 1.0;
             #pragma unroll
             for (int c = 0; c < 4; ++c) sp.ud[1 + c] = (double)uc[c];
+            sp.kw1f = 1.0f + (float)ak;
+            #pragma unroll
+            for (int c = 0; c < 5; ++c) sp.udf[c] = (float)sp.ud[c];
+            sp.mu_minf = (float)mp.mu_min;
+            sp.dgf = (float)mp.dg;
             const int ig_end = min(L.ng_pad, 64 * ch + 64);
             for (int ig = 64 * ch + lane; ig < ig_end; ig += 32) {
                 if (ig >= mp.ng) {

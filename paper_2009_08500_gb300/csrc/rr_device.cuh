@@ -59,7 +59,7 @@ __device__ __forceinline__ float sqrt_approx(float x) {
 }
 __device__ __forceinline__ float d_sqrt(float x) { return sqrtf(x); }
 __device__ __forceinline__ double d_sqrt(double x) { return sqrt(x); }
-// the per-sample square roots (z, the lens chord): approximate in FP32
+// the forward kernel's per-sample square roots (z, the lens chord): approximate in FP32
 __device__ __forceinline__ float d_sqrt_sample(float x) { return sqrt_approx(x); }
 __device__ __forceinline__ double d_sqrt_sample(double x) { return sqrt(x); }
 // the covered area's half-angles: the upper-half-plane arctangent (y = K >= 0)
@@ -105,7 +105,7 @@ __device__ __forceinline__ R covered_area_f13(R k, R z, R f1, R f3, R& dAdz, R& 
     const R f4 = z + (one + k);
     R h = (f1 * f2) * (f3 * f4);
     h = h > R(0) ? h : R(0);
-    const R K = d_sqrt_sample(h);
+    const R K = GRAD ? d_sqrt(h) : d_sqrt_sample(h);   // the adjoint keeps the rounding-exact root
     const R zz = z * z, kk = k * k;
     const R kap0 = d_atan2(K, zz + (one - kk));
     const R kap1 = d_atan2(K, zz + (kk - one));
@@ -387,6 +387,11 @@ static_assert(offsetof(PvPb<float>, k) == 0 && offsetof(PvPb<float>, win_p) == 1
               "k, inv1pk, win_s, win_p: one quadruple");
 __device__ __forceinline__ float4 quad(const float& first) { return *reinterpret_cast<const float4*>(&first); }
 
+// APPROX_Z: z by the approximate square root (the forward kernel, where z's
+// rounding reaches the flux with a factor below 1); the adjoint takes the
+// rounding-exact one, since near a contact point its z-derivative amplifies
+// z's rounding by 1 / (2 (1 + k - z)).
+template <bool APPROX_Z = true>
 __device__ __forceinline__ Orbit32 orbit32(const PvHead<float>& H, float dM, double dMd, int& iters) {
     Orbit32 o;
     o.ok = true;
@@ -413,7 +418,8 @@ __device__ __forceinline__ Orbit32 orbit32(const PvHead<float>& H, float dM, dou
     const float rho0 = H.rho0;
     o.Px = fmaf(ax.x, o.V, ax.y * o.S);
     o.Py = rho0 + fmaf(ax.z, o.V, ax.w * o.S);
-    o.z = sqrt_approx(fmaf(ab.z * o.Px, o.Px, ab.w * o.Py * o.Py));
+    const float z2 = fmaf(ab.z * o.Px, o.Px, ab.w * o.Py * o.Py);
+    o.z = APPROX_Z ? sqrt_approx(z2) : sqrtf(z2);
     o.front = o.Py > 0.0f;
     return o;
 }

@@ -239,7 +239,9 @@ __device__ __forceinline__ void cta_partials_groups(const float* gacc, const cha
 // exposure s of passband pb); gb is the cotangent weight.  Adds to `acc`;
 // returns whether the sample is in transit; sets `bad` on a Kepler failure.
 //
-// Refinement: within kContactBand of a contact point the area's z-derivative
+// Refinement: within the contact band of a contact point (kContactBand; for
+// a grazing transit, whose samples are all near the outer contact,
+// kContactBandGrazing) the area's z-derivative
 // -K/z varies like sqrt(1 + k - z) (or sqrt(z - 1 + k)), so the ~1e-7 FP32
 // rounding of z moves the per-sample derivative by ~1e-7 / (2 (1 + k - z))
 // relative (5e-5 at 1e-3 from contact): the largest share of the FP32
@@ -275,7 +277,7 @@ __device__ __forceinline__ bool adjoint_sample(const PvHead<float>& H, const PvP
         dMd = 6.283185307179586476925 * xd;
     }
     int iters;
-    const Orbit32 o = orbit32(H, dM, dMd, iters);
+    const Orbit32 o = orbit32<false>(H, dM, dMd, iters);
     if (COUNT) {
         ++tl.n[RR_COUNT_ORBIT];
         if (H.flags & kPvCircular) ++tl.n[RR_COUNT_CIRCULAR];
@@ -293,7 +295,7 @@ __device__ __forceinline__ bool adjoint_sample(const PvHead<float>& H, const PvP
     float xg = gz * (float)(L.ng - 1);
     int cell = min((int)xg, L.ng - 2);
     float al = xg - (float)cell;
-    if (orb != nullptr && (fminf(f1, fabsf(f3)) < kContactBand || fabsf(xg - rintf(xg)) < kNodeBand) &&
+    if (orb != nullptr && (fminf(f1, fabsf(f3)) < pbc.cband || fabsf(xg - rintf(xg)) < kNodeBand) &&
         fabsf(o.x) <= 1.0f) {
         if (COUNT) ++tl.n[RR_COUNT_REFINED];
         // the sample's phase from the conjunction (cycles) as a float pair, with the exact

@@ -41,6 +41,8 @@ constexpr int kMaxBasis = RR_MAX_PB + 4;  // profile bases: 1 + nldc (named) or 
 constexpr double kESwitch = 0.8;          // above this eccentricity Kepler is solved in FP64
 constexpr float kContactBand = 5e-3f;     // mixed adjoint: samples with min(1 + k - z, |z - (1 - k)|) below
                                           // this get z and the contact factors in float-float (adjoint_sample)
+constexpr float kContactBandGrazing = 1e-2f;  // the same for a grazing (pv, passband): z at conjunction above
+                                              // 1 - k, every in-transit sample near the outer contact
 constexpr float kNodeBand = 1e-4f;        // ... and so do samples within this of a g-node (in units of cells)
 constexpr int kWarpPts = 4 * 32;          // times per group: one warp, 4 consecutive times per lane
 
@@ -94,7 +96,8 @@ struct alignas(16) PvPb {
     R win_s;          // |dM| bound of a possible transit for one sample [rad]
     R win_p;          // same, widened by the passband's exposure half-span [rad]
     float win_pc;     // win_p in cycles (phase units of the FP32 point check)
-    float pad[3];
+    float cband;      // the mixed adjoint's contact band: kContactBand, or kContactBandGrazing
+    float pad[2];
 };
 
 // Arguments of the per-time preparation carried by the set-up launch (its

@@ -756,7 +756,7 @@ __global__ void __launch_bounds__(256, 4) rr_pv_setup_kernel(ModelParams mp, PbP
     __shared__ int rows_next;
     __shared__ int wmax_s[NP];     // largest point window over the passbands (float bits, -1 = none)
     __shared__ int flags_s[NP];
-    __shared__ R orb_s[NP][6];     // a, b, e, f0, M0, n
+    __shared__ R orb_s[NP][7];     // a, b, e, f0, M0, n, z at conjunction (b r0 / a)
     const int ppc = setup_pvs_per_cta(mp.npb);
     const int pv0 = sblock * ppc;
     const int nloc = min(ppc, npv - pv0);
@@ -924,7 +924,7 @@ __global__ void __launch_bounds__(256, 4) rr_pv_setup_kernel(ModelParams mp, PbP
             if (ed > kESwitch) flags |= kPvKepler64;
             flags_s[tid] = flags;
             orb_s[tid][0] = a; orb_s[tid][1] = b; orb_s[tid][2] = e; orb_s[tid][3] = f0;
-            orb_s[tid][4] = M0; orb_s[tid][5] = n;
+            orb_s[tid][4] = M0; orb_s[tid][5] = n; orb_s[tid][6] = b * rho0;
         }
     }
     __syncwarp();
@@ -969,7 +969,10 @@ __global__ void __launch_bounds__(256, 4) rr_pv_setup_kernel(ModelParams mp, PbP
         }
         PB[pb].k = k;
         PB[pb].inv1pk = R(1) / (R(1) + k);
-        PB[pb].pad[0] = PB[pb].pad[1] = PB[pb].pad[2] = 0.0f;
+        PB[pb].pad[0] = PB[pb].pad[1] = 0.0f;
+        // grazing: the planet never wholly on the disk, every in-transit sample near the
+        // outer contact (where the adjoint's z rounding is amplified): a wider band
+        PB[pb].cband = (float)orb_s[lp][6] > 1.0f - (float)kw ? kContactBandGrazing : kContactBand;
         if (none) {            // the orbit never brings the planet over the disk
             PB[pb].win_s = R(-1);
             PB[pb].win_p = R(-1);

@@ -181,10 +181,10 @@ SIGN_CASES = CASES + [dict(ld_model="quadratic_tri", eccentric=True, c3_rows=Tru
 def test_adjoint_within_1e5_relative_of_the_oracle(rr, case, precision):
     case = dict(case)
     if case.pop("c3_rows", False):
-        # population-workload pvs (Kipping q1 >= 1e-3), the full time grid
+        # 128 population-workload pvs (Kipping q1 >= 1e-3), the full time grid
         full = W.make_c3(q1_min=1e-3)
         wl = full.subset(4096)
-        wl.params = full.params[np.arange(3, 4096, 97)[:32]]
+        wl.params = full.params[np.arange(3, 4096, 16)[:128]]
     else:
         wl = W.make_small(npv=19, npt=2100, seed=17, span=6.0, **case)
     s = _setup(wl)

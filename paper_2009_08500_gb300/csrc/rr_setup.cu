@@ -603,7 +603,7 @@ struct SmallPlanetRow {
     double ud[5];   // weights of the bases: 1, then the coefficients
     int b0, nc;
     // FP32 copies for the FP32 rows, converted once per row (FP64 issues at a small
-    // fraction of the FP32 rate on this GPU, conversions included)
+    // fraction of the FP32 rate on GB300, conversions included)
     float kw1f;     // 1 + kw
     float udf[5];
     float mu_minf, dgf;
@@ -630,7 +630,7 @@ __device__ double small_planet_node(const ModelParams& mp, const SmallPlanetRow&
 }
 
 // FP32 twins of ld_basis_mu and small_planet_node, for rows stored in FP32 (the mixed form):
-// FP64 issues at a small fraction of the FP32 rate on this GPU, and the rows keep 24 bits.
+// FP64 issues at a small fraction of the FP32 rate on GB300, and the rows keep 24 bits.
 // 1 - c^2 as (1 - c)(1 + c), and the exponential law's 1 - e^mu as -expm1(mu), keep the
 // relative precision at the limb.
 __device__ __forceinline__ float ld_basis_mu_f(const ModelParams& mp, int b, float m, const double* __restrict__ tab,
@@ -937,7 +937,7 @@ __global__ void __launch_bounds__(256, 4) rr_pv_setup_kernel(ModelParams mp, PbP
         const double* row = params + (size_t)pv * mp.nparam;
         PvPb<R>* PB = reinterpret_cast<PvPb<R>*>(records + (size_t)pv * L.head_bytes + L.off_pb);
         // the window is a conservative bound with explicit margins: FP32 in both
-        // forms (dependent FP64 transcendentals are slow on this GPU)
+        // forms (dependent FP64 transcendentals are slow on GB300)
         using W = float;
         const W a = (W)orb_s[lp][0], b = (W)orb_s[lp][1], e = (W)orb_s[lp][2], f0 = (W)orb_s[lp][3];
         const W M0 = (W)orb_s[lp][4], n = (W)orb_s[lp][5];

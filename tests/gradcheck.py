@@ -6,7 +6,7 @@ import numpy as np
 from oracle import model
 
 
-def survey_rel(g, ref):
+def gradient_rel(g, ref):
     """|g - ref| / max(|ref|, 1e-6 max_theta |ref|) per component (last axis = parameters)."""
     ref = np.asarray(ref, np.float64)
     floor = 1e-6 * np.abs(ref).max(axis=-1, keepdims=True)

@@ -30,7 +30,7 @@ from oracle import grad as og
 from oracle import model as om
 from paper_2009_08500_gb300 import workloads as W
 
-from gradcheck import smooth_points, survey_rel
+from gradcheck import smooth_points, gradient_rel
 
 pytestmark = pytest.mark.gpu
 
@@ -194,7 +194,7 @@ def test_adjoint_within_1e5_relative_of_the_oracle(rr, case, precision):
     ref = np.stack([np.abs(j).sum(0) for j in J])
     transits = ref.max(axis=1) > 0
     assert transits.sum() >= 0.5 * wl.npv
-    rel = survey_rel(g[transits], ref[transits])
+    rel = gradient_rel(g[transits], ref[transits])
     bound = 1e-5 if precision == "mixed" else 1e-8
     if precision == "mixed" and case["ld_model"] == "exponential":
         bound = 1e-4

@@ -79,7 +79,8 @@ typedef enum {
 typedef enum {
     RR_PREC_FP64 = 0,   /* every step in FP64; flux and grad_flux are double */
     RR_PREC_MIXED = 1   /* FP64 setup, phase reduction and normalisation; FP32 bulk;
-                           flux and grad_flux are float */
+                           flux and grad_flux are float.  Flux within 1e-6 absolute
+                           of the FP64 form (Kepler in FP64 above e = 0.8) */
 } rr_precision;
 
 /* Per-pv status bits written to pv_status (0 = valid). */
@@ -235,6 +236,12 @@ rr_status rr_evaluate_noalloc(rr_ctx* ctx, const double* times, const int32_t* p
  * cell holding the point (the lower cell on a node).  The sum over times is
  * deterministic (fixed tiling and order), so a pv's gradient does not
  * depend on the other pvs evaluated with it.  Invalid pvs get NaN rows.
+ * Accuracy (MIXED): a component that is a sum of same-sign terms (for
+ * example the cotangent sign(d flux / d params[j]) for component j) is
+ * within 1e-5 relative of the exact chain rule, 1e-4 for the exponential
+ * law (unbounded at the limb); samples near a contact point or a g node are
+ * recomputed in float-float for this.  A component that is a cancelling sum
+ * carries the absolute error of its terms instead.
  * workspace >= rr_workspace_bytes(ctx, npv, npt, 1).  Errors as rr_evaluate. */
 rr_status rr_evaluate_grad(rr_ctx* ctx, const double* times, const int32_t* pb_index, int32_t npt,
                            const double* params, int32_t npv, const int32_t* supersampling,

@@ -173,18 +173,21 @@ def _diag(g, npv, nparam):
     return g.reshape(npv, nparam, nparam)[:, np.arange(nparam), np.arange(nparam)]
 
 
-SIGN_CASES = CASES + [dict(ld_model="quadratic_tri", eccentric=True, c3_rows=True)]
+SIGN_CASES = CASES + [dict(ld_model="quadratic_tri", eccentric=True, c3_rows=128),
+                      dict(ld_model="quadratic_tri", eccentric=True, c3_rows=512)]
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 @pytest.mark.parametrize("case", SIGN_CASES, ids=lambda c: "-".join(str(v) for v in c.values()))
 def test_adjoint_within_1e5_relative_of_the_oracle(rr, case, precision):
     case = dict(case)
-    if case.pop("c3_rows", False):
-        # 128 population-workload pvs (Kipping q1 >= 1e-3), the full time grid
+    rows = case.pop("c3_rows", 0)
+    if rows:
+        # population-workload pvs (Kipping q1 >= 1e-3), the full time grid: 128 every 16th
+        # from the 4th, or 512 every 8th from the 6th (grazing transits among them)
         full = W.make_c3(q1_min=1e-3)
         wl = full.subset(4096)
-        wl.params = full.params[np.arange(3, 4096, 16)[:128]]
+        wl.params = full.params[np.arange(3, 4096, 16)[:128] if rows == 128 else np.arange(5, 4096, 8)[:512]]
     else:
         wl = W.make_small(npv=19, npt=2100, seed=17, span=6.0, **case)
     s = _setup(wl)
